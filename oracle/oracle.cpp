@@ -1,0 +1,711 @@
+// FP64 CPU oracle for batched 3D Gaussian Splatting RGB + depth rendering.
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or call this file:
+// it exists so that tests/, the smoke check and the benchmark's CPU-baseline leg can check
+// and time the CUDA renderer against an independent, slow, obviously correct definition.
+// It shares no code, header or constant table with the CUDA library.
+//
+// What it computes (the plain definition the tile-binned GPU method must reproduce):
+//   * Sec. III-B (Asset Formatting): every env holds a background node plus interactive
+//     nodes; a node's Gaussians move rigidly with its world_from_node pose.
+//   * Sec. III-A (Renderer): the native 3DGS pipeline -- per-Gaussian EWA "splatting" of the
+//     3D covariance to a 2D conic, spherical-harmonics colour evaluation, depth ordering
+//     ("sorting") and front-to-back alpha-blending.
+//   * Sec. III-C (Sensor): RGB and depth are both produced by alpha-compositing, the colour
+//     and the camera-space z of the intersected Gaussians respectively.
+// For every pixel the oracle takes every Gaussian (of every node present in the env) whose
+// centre is in front of the near plane and whose 3-sigma ellipse contains the pixel centre,
+// sorts them by (depth, global id) and composites them front to back.  There is no tiling.
+//
+// Readings fixed where the paper is silent (every constant is an option in oracle_opts):
+//   pixel centre (x+1/2, y+1/2); u = fx*tx/tz + cx; Sigma2D += lowpass*I; cull if tz <= z_near
+//   or det(Sigma2D) <= 0; Jacobian evaluated at (tx/tz, ty/tz) clamped to +-guard*half-FOV
+//   tangent; a Gaussian touches a pixel iff d^T conic d <= q_max (3 sigma -> 9);
+//   alpha = min(alpha_max, opacity * exp(-q/2)); skip if alpha < alpha_min; T_next = T(1-alpha),
+//   stop without compositing if T_next < t_min; RGB = sum w_i rgb_i + bg*T_final,
+//   D = sum w_i z_i (unnormalised), A = 1 - T_final; real SH (Condon-Shortley phase) up to
+//   degree 3, colour = max(0, sum c_lm Y_lm(d) + 1/2), d = unit view direction expressed in
+//   the node frame.
+//
+// Depth order and near-plane cull are integer decisions taken on an FP32 key, the same on
+// both sides (the method keeps its sort keys in FP32): z32 = camera-space z of the centre,
+// evaluated in binary32 round-to-nearest, one rounding per multiply and per add, no fused
+// multiply-add, in this order:
+//   M2j = ((W20*R0j + W21*R1j) + W22*R2j)               j = 0,1,2   (camera_from_node row 2)
+//   M23 = (((W20*t0 + W21*t1) + W22*t2) + tc2)
+//   z32 = (((M20*mx + M21*my) + M22*mz) + M23)
+// with [W|tc] = cam_from_world, [R|t] = world_from_node, (mx,my,mz) the node-frame mean.
+// Candidates are sorted by (z32, global id), global id = node_base[node] + local index, and
+// culled when z32 <= float(z_near).  Every other quantity is FP64.
+//
+// Decisions whose FP64 quantity lies within a relative band eps_rel of its threshold
+// (ellipse, alpha_min, t_min) are "ambiguous": an FP32 implementation may legitimately take
+// the other branch.  The forward pass enumerates
+// up to max_flips such flips per pixel and returns every branch's result; beyond that it
+// widens the pixel's tolerance by T * max|value| per unexplored flip (the two branches agree
+// on the first 1-T of the composite and both stay inside the convex hull of the rest).
+//
+// The backward pass is the analytic adjoint of the primary branch (decisions held fixed).
+// It is pinned by FP64 central finite differences of the forward pass in the tests.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+extern "C" {
+
+typedef struct {
+    int32_t n_nodes;
+    const int64_t* node_n;        // [n_nodes]
+    const int32_t* node_deg;      // [n_nodes] SH degree 0..3
+    const double* mean;           // [G,3]   G = sum(node_n), node-major
+    const double* log_scale;      // [G,3]
+    const double* quat;           // [G,4]   (w,x,y,z)
+    const double* opacity_logit;  // [G]
+    const double* sh;             // [G,16,3] (zero padded above the node's degree)
+    int32_t E, K, C;
+    const int32_t* env_node_ids;  // [E,K]   -1 = empty slot
+    const double* node_poses;     // [E,K,12] world_from_node, row-major 3x4
+    const int32_t* cams_per_env;  // [E]
+    const double* cam_intr;       // [E,C,4] fx fy cx cy
+    const int32_t* cam_res;       // [E,C,2] width height
+    const double* cam_pose;       // [E,C,12] cam_from_world, row-major 3x4
+} oracle_scene;
+
+typedef struct {
+    double z_near, lowpass, alpha_min, alpha_max, t_min, q_max, guard;
+    double bg[3];
+    double eps_rel;     // relative ambiguity band of thresholded decisions
+    int32_t max_flips;  // branches enumerated per pixel (<= 6)
+    int32_t nthreads;   // 0 = hardware concurrency
+    int32_t bruteforce; // 1 = test every Gaussian at every pixel (no AABB candidate lists)
+    int32_t order64;    // 1 = decide depth order and near cull on the FP64 depth instead of z32
+} oracle_opts;
+
+}  // extern "C"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+int n_threads(const oracle_opts* o) {
+    if (o->nthreads > 0) return o->nthreads;
+    unsigned h = std::thread::hardware_concurrency();
+    return h ? (int)h : 1;
+}
+
+template <class F>
+void parallel_for(int64_t n, int nth, F&& f) {
+    if (n <= 0) return;
+    std::atomic<int64_t> next(0);
+    auto worker = [&](int tid) {
+        for (;;) {
+            int64_t i = next.fetch_add(1);
+            if (i >= n) break;
+            f(i, tid);
+        }
+    };
+    nth = (int)std::max<int64_t>(1, std::min<int64_t>(nth, n));
+    std::vector<std::thread> ts;
+    for (int t = 1; t < nth; ++t) ts.emplace_back(worker, t);
+    worker(0);
+    for (auto& t : ts) t.join();
+}
+
+// ------------------------------------------------------------------ real spherical harmonics
+// Y_lm for l <= 3 from the associated Legendre functions with the Condon-Shortley phase,
+// written through Cartesian polynomials on the unit sphere:
+//   P_l^m(cos t) e^{i m phi} = (-1)^m Q_l^m(z) (x + i y)^m,   Q_l^m = d^m P_l / dz^m,
+//   Y_l0 = N_l0 Q_l^0,  Y_lm = sqrt2 N_lm (-1)^m Q_l^m Re[(x+iy)^m],
+//   Y_l,-m = sqrt2 N_lm (-1)^m Q_l^m Im[(x+iy)^m],  N_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!).
+// Index k = l^2 + l + m.  The gradient is that of this polynomial extension to R^3; only its
+// tangential part is used (after the normalisation Jacobian), which is unique.
+double fact(int n) { double r = 1; for (int i = 2; i <= n; ++i) r *= i; return r; }
+
+void sh_basis(int deg, const double d[3], double Y[16], double dY[16][3]) {
+    const double x = d[0], y = d[1], z = d[2];
+    double Q[5][5] = {{0}};   // Q[l][m] = m-th derivative of Legendre P_l at z (l<=3, m<=4)
+    for (int m = 0; m <= 4; ++m) {
+        for (int l = 0; l <= 3; ++l) {
+            if (l < m) { Q[l][m] = 0; continue; }
+            if (l == m) { double df = 1; for (int k = 2 * m - 1; k > 1; k -= 2) df *= k; Q[l][m] = df; continue; }
+            if (l == m + 1) { Q[l][m] = (2 * m + 1) * z * Q[m][m]; continue; }
+            Q[l][m] = ((2 * l - 1) * z * Q[l - 1][m] - (l + m - 1) * Q[l - 2][m]) / (l - m);
+        }
+    }
+    double Cm[4], Sm[4];       // (x + i y)^m = Cm + i Sm
+    Cm[0] = 1; Sm[0] = 0;
+    for (int m = 1; m <= 3; ++m) { Cm[m] = Cm[m - 1] * x - Sm[m - 1] * y; Sm[m] = Cm[m - 1] * y + Sm[m - 1] * x; }
+    for (int k = 0; k < 16; ++k) { Y[k] = 0; if (dY) dY[k][0] = dY[k][1] = dY[k][2] = 0; }
+    for (int l = 0; l <= deg; ++l) {
+        for (int m = -l; m <= l; ++m) {
+            const int am = m < 0 ? -m : m;
+            const int k = l * l + l + m;
+            const double N = std::sqrt((2 * l + 1) / (4 * kPi) * fact(l - am) / fact(l + am));
+            if (m == 0) {
+                Y[k] = N * Q[l][0];
+                if (dY) { dY[k][2] = N * Q[l][1]; }
+                continue;
+            }
+            const double s = std::sqrt(2.0) * N * ((am & 1) ? -1.0 : 1.0);
+            const double P = Q[l][am], dP = Q[l][am + 1];
+            if (m > 0) {
+                Y[k] = s * P * Cm[am];
+                if (dY) { dY[k][0] = s * P * am * Cm[am - 1]; dY[k][1] = -s * P * am * Sm[am - 1]; dY[k][2] = s * dP * Cm[am]; }
+            } else {
+                Y[k] = s * P * Sm[am];
+                if (dY) { dY[k][0] = s * P * am * Sm[am - 1]; dY[k][1] = s * P * am * Cm[am - 1]; dY[k][2] = s * dP * Sm[am]; }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ projection of one instance
+struct Geo {
+    int64_t gid;                 // global id = node_base + local
+    int64_t g;                   // row in the concatenated attribute arrays (== gid)
+    int slot, deg;
+    double Rn[3][3], tn[3], mu[3], muw[3];
+    double q[4], qlen, qn[4], Rq[3][3], sc[3], M[3][3], Sig[3][3], Sigw[3][3];
+    double Wc[3][3], tc[3], t[3];
+    double fx, fy, cx, cy, limx, limy, xr, yr, xc, yc;
+    bool clx, cly;
+    double J[2][3], T[2][3], cov[2][2], det, Q[2][2];
+    double u, v, z, logit, opac;
+    float z32;                   // FP32 depth key (order + near cull)
+    double ocam[3], oloc[3], dir[3], dlen, d[3], Y[16], dY[16][3];
+    double raw[3], rgb[3];
+    bool present, near_amb, valid;
+    double hx, hy;               // half extents of the ellipse's axis-aligned box (with band margin)
+};
+
+void rot_from_quat(const double q[4], double R[3][3]) {
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - w * z); R[0][2] = 2 * (x * z + w * y);
+    R[1][0] = 2 * (x * y + w * z); R[1][1] = 1 - 2 * (x * x + z * z); R[1][2] = 2 * (y * z - w * x);
+    R[2][0] = 2 * (x * z - w * y); R[2][1] = 2 * (y * z + w * x); R[2][2] = 1 - 2 * (x * x + y * y);
+}
+
+// The FP32 depth key (see the file header).  Inputs are binary32 values held in doubles, so
+// the conversions are exact; the file is compiled with -ffp-contract=off.
+float depth_key32(const double Wc[3][3], const double tc[3], const double Rn[3][3], const double tn[3],
+                  const double mu[3]) {
+    float M[4];
+    for (int j = 0; j < 3; ++j) {
+        float a = (float)Wc[2][0] * (float)Rn[0][j];
+        float b = (float)Wc[2][1] * (float)Rn[1][j];
+        float c = (float)Wc[2][2] * (float)Rn[2][j];
+        M[j] = (a + b) + c;
+    }
+    {
+        float a = (float)Wc[2][0] * (float)tn[0];
+        float b = (float)Wc[2][1] * (float)tn[1];
+        float c = (float)Wc[2][2] * (float)tn[2];
+        M[3] = ((a + b) + c) + (float)tc[2];
+    }
+    float a = M[0] * (float)mu[0];
+    float b = M[1] * (float)mu[1];
+    float c = M[2] * (float)mu[2];
+    return ((a + b) + c) + M[3];
+}
+
+// Projects Gaussian g (row in attribute arrays) of the node in `slot` of env e into camera
+// (e, c).  Fills every intermediate.  valid=false if the 2D covariance is not positive.
+void project(const oracle_scene* s, const oracle_opts* o, int e, int c, int slot, int64_t g, int deg, Geo& G) {
+    G.g = g; G.gid = g; G.slot = slot; G.deg = deg;
+    const double* P = s->node_poses + ((int64_t)e * s->K + slot) * 12;
+    for (int i = 0; i < 3; ++i) { for (int j = 0; j < 3; ++j) G.Rn[i][j] = P[i * 4 + j]; G.tn[i] = P[i * 4 + 3]; }
+    const double* CP = s->cam_pose + ((int64_t)e * s->C + c) * 12;
+    for (int i = 0; i < 3; ++i) { for (int j = 0; j < 3; ++j) G.Wc[i][j] = CP[i * 4 + j]; G.tc[i] = CP[i * 4 + 3]; }
+    const double* I = s->cam_intr + ((int64_t)e * s->C + c) * 4;
+    G.fx = I[0]; G.fy = I[1]; G.cx = I[2]; G.cy = I[3];
+    const int32_t* res = s->cam_res + ((int64_t)e * s->C + c) * 2;
+    G.limx = o->guard * 0.5 * res[0] / G.fx;
+    G.limy = o->guard * 0.5 * res[1] / G.fy;
+
+    for (int i = 0; i < 3; ++i) G.mu[i] = s->mean[g * 3 + i];
+    for (int i = 0; i < 3; ++i) G.muw[i] = G.Rn[i][0] * G.mu[0] + G.Rn[i][1] * G.mu[1] + G.Rn[i][2] * G.mu[2] + G.tn[i];
+    // 3D covariance in the node frame: Sigma = R(q) S S^T R(q)^T, S = diag(exp(log_scale)).
+    for (int i = 0; i < 4; ++i) G.q[i] = s->quat[g * 4 + i];
+    G.qlen = std::sqrt(G.q[0] * G.q[0] + G.q[1] * G.q[1] + G.q[2] * G.q[2] + G.q[3] * G.q[3]);
+    for (int i = 0; i < 4; ++i) G.qn[i] = G.q[i] / G.qlen;
+    rot_from_quat(G.qn, G.Rq);
+    for (int i = 0; i < 3; ++i) G.sc[i] = std::exp(s->log_scale[g * 3 + i]);
+    for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) G.M[i][j] = G.Rq[i][j] * G.sc[j];
+    for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) {
+        double a = 0; for (int k = 0; k < 3; ++k) a += G.M[i][k] * G.M[j][k]; G.Sig[i][j] = a; }
+    // World covariance Sigma_w = Rn Sigma Rn^T.
+    double tmp[3][3];
+    for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) {
+        double a = 0; for (int k = 0; k < 3; ++k) a += G.Rn[i][k] * G.Sig[k][j]; tmp[i][j] = a; }
+    for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) {
+        double a = 0; for (int k = 0; k < 3; ++k) a += tmp[i][k] * G.Rn[j][k]; G.Sigw[i][j] = a; }
+    // Camera space.
+    for (int i = 0; i < 3; ++i) G.t[i] = G.Wc[i][0] * G.muw[0] + G.Wc[i][1] * G.muw[1] + G.Wc[i][2] * G.muw[2] + G.tc[i];
+    G.z = G.t[2];
+    G.z32 = depth_key32(G.Wc, G.tc, G.Rn, G.tn, G.mu);
+    G.present = o->order64 ? G.z > o->z_near : G.z32 > (float)o->z_near;
+    G.near_amb = false;
+    G.valid = true;
+    if (!G.present) { G.valid = false; return; }
+    // EWA: Jacobian of the pinhole projection at t (guarded), Sigma2D = J Wc Sigma_w Wc^T J^T + lp I.
+    G.xr = G.t[0] / G.t[2]; G.yr = G.t[1] / G.t[2];
+    G.xc = std::min(G.limx, std::max(-G.limx, G.xr)); G.clx = G.xc != G.xr;
+    G.yc = std::min(G.limy, std::max(-G.limy, G.yr)); G.cly = G.yc != G.yr;
+    G.J[0][0] = G.fx / G.t[2]; G.J[0][1] = 0; G.J[0][2] = -G.fx * G.xc / G.t[2];
+    G.J[1][0] = 0; G.J[1][1] = G.fy / G.t[2]; G.J[1][2] = -G.fy * G.yc / G.t[2];
+    for (int i = 0; i < 2; ++i) for (int j = 0; j < 3; ++j) {
+        double a = 0; for (int k = 0; k < 3; ++k) a += G.J[i][k] * G.Wc[k][j]; G.T[i][j] = a; }
+    double TS[2][3];
+    for (int i = 0; i < 2; ++i) for (int j = 0; j < 3; ++j) {
+        double a = 0; for (int k = 0; k < 3; ++k) a += G.T[i][k] * G.Sigw[k][j]; TS[i][j] = a; }
+    for (int i = 0; i < 2; ++i) for (int j = 0; j < 2; ++j) {
+        double a = 0; for (int k = 0; k < 3; ++k) a += TS[i][k] * G.T[j][k]; G.cov[i][j] = a; }
+    G.cov[0][0] += o->lowpass; G.cov[1][1] += o->lowpass;
+    G.det = G.cov[0][0] * G.cov[1][1] - G.cov[0][1] * G.cov[1][0];
+    if (!(G.det > 0)) { G.valid = false; return; }
+    G.Q[0][0] = G.cov[1][1] / G.det; G.Q[1][1] = G.cov[0][0] / G.det;
+    G.Q[0][1] = G.Q[1][0] = -G.cov[0][1] / G.det;
+    G.u = G.fx * G.xr + G.cx; G.v = G.fy * G.yr + G.cy;
+    // Bounding box of {d : d^T Q d <= q_max (1+eps)}: half extents sqrt(q_max (1+eps) Sigma_ii).
+    const double qb = o->q_max * (1.0 + 2.0 * o->eps_rel);
+    G.hx = std::sqrt(qb * G.cov[0][0]) * (1 + 1e-12) + 1e-12;
+    G.hy = std::sqrt(qb * G.cov[1][1]) * (1 + 1e-12) + 1e-12;
+    // Opacity.
+    G.logit = s->opacity_logit[g];
+    G.opac = 1.0 / (1.0 + std::exp(-G.logit));
+    // View direction in the node frame: camera centre o = -Wc^T tc, o_local = Rn^T (o - tn).
+    for (int i = 0; i < 3; ++i) G.ocam[i] = -(G.Wc[0][i] * G.tc[0] + G.Wc[1][i] * G.tc[1] + G.Wc[2][i] * G.tc[2]);
+    for (int i = 0; i < 3; ++i) {
+        double a = 0; for (int k = 0; k < 3; ++k) a += G.Rn[k][i] * (G.ocam[k] - G.tn[k]); G.oloc[i] = a; }
+    for (int i = 0; i < 3; ++i) G.dir[i] = G.mu[i] - G.oloc[i];
+    G.dlen = std::sqrt(G.dir[0] * G.dir[0] + G.dir[1] * G.dir[1] + G.dir[2] * G.dir[2]);
+    for (int i = 0; i < 3; ++i) G.d[i] = G.dir[i] / G.dlen;
+    sh_basis(deg, G.d, G.Y, G.dY);
+    const double* sh = s->sh + g * 48;
+    for (int ch = 0; ch < 3; ++ch) {
+        double a = 0.5;
+        for (int k = 0; k < (deg + 1) * (deg + 1); ++k) a += sh[k * 3 + ch] * G.Y[k];
+        G.raw[ch] = a; G.rgb[ch] = a > 0 ? a : 0.0;
+    }
+}
+
+struct ViewData {
+    int W = 0, H = 0;
+    std::vector<Geo> geo;        // instances that are present or near-ambiguous and valid
+    std::vector<int64_t> node_base;
+};
+
+bool build_view(const oracle_scene* s, const oracle_opts* o, int e, int c, ViewData& V) {
+    if (e < 0 || e >= s->E || c < 0 || c >= s->cams_per_env[e]) return false;
+    const int32_t* res = s->cam_res + ((int64_t)e * s->C + c) * 2;
+    V.W = res[0]; V.H = res[1];
+    V.node_base.assign(s->n_nodes + 1, 0);
+    for (int k = 0; k < s->n_nodes; ++k) V.node_base[k + 1] = V.node_base[k] + s->node_n[k];
+    // Instances in slot order; the id used for ordering is the global id.
+    std::vector<std::pair<int, int64_t>> items;   // (slot, g)
+    for (int j = 0; j < s->K; ++j) {
+        int k = s->env_node_ids[(int64_t)e * s->K + j];
+        if (k < 0) continue;
+        for (int64_t i = 0; i < s->node_n[k]; ++i) items.emplace_back(j, V.node_base[k] + i);
+    }
+    std::vector<Geo> all(items.size());
+    std::vector<char> keep(items.size(), 0);
+    parallel_for((int64_t)items.size(), n_threads(o), [&](int64_t i, int) {
+        const int slot = items[i].first;
+        const int k = s->env_node_ids[(int64_t)e * s->K + slot];
+        project(s, o, e, c, slot, items[i].second, s->node_deg[k], all[i]);
+        keep[i] = all[i].valid;
+    });
+    V.geo.clear();
+    for (size_t i = 0; i < all.size(); ++i) if (keep[i]) V.geo.push_back(all[i]);
+    return true;
+}
+
+// Per-pixel candidate: a Gaussian whose band-widened ellipse contains the pixel centre.
+struct Cand { int idx; double key; int64_t gid; double q, dx, dy; };
+
+void pixel_candidates(const ViewData& V, const oracle_opts* o, const std::vector<int>& pool, int px, int py,
+                      std::vector<Cand>& out) {
+    out.clear();
+    const double X = px + 0.5, Yc = py + 0.5;
+    const double qlim = o->q_max * (1.0 + o->eps_rel);
+    for (int idx : pool) {
+        const Geo& G = V.geo[idx];
+        const double dx = X - G.u, dy = Yc - G.v;
+        const double q = G.Q[0][0] * dx * dx + 2 * G.Q[0][1] * dx * dy + G.Q[1][1] * dy * dy;
+        if (q <= qlim) out.push_back({idx, o->order64 ? G.z : (double)G.z32, G.gid, q, dx, dy});
+    }
+    std::sort(out.begin(), out.end(), [](const Cand& a, const Cand& b) {
+        return a.key < b.key || (a.key == b.key && a.gid < b.gid); });
+}
+
+struct Leaf { double r, g, b, d, a; };
+
+struct PixelResult {
+    Leaf primary;
+    std::vector<Leaf> alts;
+    double tol_rgb = 0, tol_d = 0;
+    bool ambiguous = false;
+    uint64_t hash = 1469598103934665603ull;
+};
+
+inline uint64_t mix(uint64_t h, uint64_t v) { h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2); return h * 1099511628211ull; }
+
+// Front-to-back composite of one pixel, branching on ambiguous decisions.
+// A candidate's action is SKIP unless it is in front of the near plane, inside the ellipse and
+// has alpha >= alpha_min; then it is STOP if T(1-alpha) < t_min, else COMPOSITE.  Flipping one
+// ambiguous decision that changes the action starts an alternative branch.
+enum Act { SKIP = 0, COMP = 1, STOP = 2 };
+
+inline Act action(bool near_ok, bool ell_ok, bool keep, bool stop) {
+    if (!(near_ok && ell_ok && keep)) return SKIP;
+    return stop ? STOP : COMP;
+}
+
+struct Compositor {
+    const ViewData& V; const oracle_opts* o;
+    double Mc, Mz;
+    PixelResult* R;
+
+    void widen(double T) { R->tol_rgb += T * Mc; R->tol_d += T * Mz; }
+
+    void run(const std::vector<Cand>& order, size_t pos, double T, double C0, double C1, double C2, double D,
+             int flips, bool primary) {
+        const double eps = o->eps_rel;
+        for (; pos < order.size(); ++pos) {
+            const Cand& cd = order[pos];
+            const Geo& G = V.geo[cd.idx];
+            const double a_raw = G.opac * std::exp(-0.5 * cd.q);
+            const double alpha = std::min(o->alpha_max, a_raw);
+            const double Tn = T * (1.0 - alpha);
+            const bool d[4] = {G.present, cd.q <= o->q_max, alpha >= o->alpha_min, Tn < o->t_min};
+            const bool amb[4] = {G.near_amb, std::fabs(cd.q - o->q_max) <= eps * o->q_max,
+                                 std::fabs(alpha - o->alpha_min) <= eps * o->alpha_min,
+                                 std::fabs(Tn - o->t_min) <= eps * o->t_min};
+            const Act act = action(d[0], d[1], d[2], d[3]);
+            for (int k = 0; k < 4; ++k) {
+                if (!amb[k]) continue;
+                bool f[4] = {d[0], d[1], d[2], d[3]};
+                f[k] = !f[k];
+                const Act alt = action(f[0], f[1], f[2], f[3]);
+                if (alt == act) continue;
+                R->ambiguous = true;
+                if (flips >= o->max_flips) { widen(T); continue; }
+                if (alt == SKIP) run(order, pos + 1, T, C0, C1, C2, D, flips + 1, false);
+                else if (alt == STOP) emit(T, C0, C1, C2, D, false);
+                else {
+                    const double w = alpha * T;
+                    run(order, pos + 1, Tn, C0 + w * G.rgb[0], C1 + w * G.rgb[1], C2 + w * G.rgb[2], D + w * G.z,
+                        flips + 1, false);
+                }
+            }
+            if (primary) {
+                uint64_t code = (uint64_t)act;
+                if (act != SKIP) code += 4 * (a_raw > o->alpha_max) + 8 * (G.clx || G.cly) + 16 * (G.raw[0] <= 0) +
+                                         32 * (G.raw[1] <= 0) + 64 * (G.raw[2] <= 0);
+                R->hash = mix(R->hash, (uint64_t)cd.gid * 128 + code);
+            }
+            if (act == SKIP) continue;
+            if (act == STOP) break;
+            const double w = alpha * T;
+            C0 += w * G.rgb[0]; C1 += w * G.rgb[1]; C2 += w * G.rgb[2]; D += w * G.z;
+            T = Tn;
+        }
+        emit(T, C0, C1, C2, D, primary);
+    }
+    void emit(double T, double C0, double C1, double C2, double D, bool primary) {
+        Leaf L{C0 + o->bg[0] * T, C1 + o->bg[1] * T, C2 + o->bg[2] * T, D, 1.0 - T};
+        if (primary) R->primary = L; else R->alts.push_back(L);
+    }
+};
+
+// Row buckets: for every pixel row, the instances whose box covers a pixel centre of that row.
+void row_pools(const ViewData& V, const oracle_opts* o, std::vector<std::vector<int>>& rows) {
+    rows.assign(V.H, {});
+    for (int i = 0; i < (int)V.geo.size(); ++i) {
+        const Geo& G = V.geo[i];
+        if (o->bruteforce) { for (int y = 0; y < V.H; ++y) rows[y].push_back(i); continue; }
+        // rows y with |y + 0.5 - v| <= hy
+        double lo = std::ceil(G.v - G.hy - 0.5), hi = std::floor(G.v + G.hy - 0.5);
+        if (hi < 0 || lo > V.H - 1) continue;
+        int y0 = (int)std::max(0.0, lo), y1 = (int)std::min((double)V.H - 1, hi);
+        for (int y = y0; y <= y1; ++y) rows[y].push_back(i);
+    }
+}
+
+void cols_pool(const ViewData& V, const oracle_opts* o, const std::vector<int>& row, std::vector<std::vector<int>>& cols) {
+    for (auto& c : cols) c.clear();
+    for (int i : row) {
+        const Geo& G = V.geo[i];
+        if (o->bruteforce) { for (int x = 0; x < V.W; ++x) cols[x].push_back(i); continue; }
+        double lo = std::ceil(G.u - G.hx - 0.5), hi = std::floor(G.u + G.hx - 0.5);
+        if (hi < 0 || lo > V.W - 1) continue;
+        int x0 = (int)std::max(0.0, lo), x1 = (int)std::min((double)V.W - 1, hi);
+        for (int x = x0; x <= x1; ++x) cols[x].push_back(i);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int oracle_abi_version() { return 1; }
+
+// Real SH basis Y[16] (entries above the degree are 0) and its gradient dY[16][3] at d.
+void oracle_sh_basis(int deg, const double* d, double* Y, double* dY) {
+    double y[16], dy[16][3];
+    sh_basis(deg, d, y, dy);
+    for (int k = 0; k < 16; ++k) { Y[k] = y[k]; if (dY) for (int j = 0; j < 3; ++j) dY[k * 3 + j] = dy[k][j]; }
+}
+
+// The FP32 depth key of a node-frame point (poses row-major 3x4 in doubles holding floats).
+float oracle_depth_key32(const double* cam_from_world, const double* world_from_node, const double* mu) {
+    double Wc[3][3], tc[3], Rn[3][3], tn[3];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) { Wc[i][j] = cam_from_world[i * 4 + j]; Rn[i][j] = world_from_node[i * 4 + j]; }
+        tc[i] = cam_from_world[i * 4 + 3]; tn[i] = world_from_node[i * 4 + 3];
+    }
+    return depth_key32(Wc, tc, Rn, tn, mu);
+}
+
+// Projection of every Gaussian of view (e, c), for closed-form checks.
+// out[n, 16]: gid, u, v, z, conic a, b, c, cov xx, xy, yy, opacity, r, g, b, present, near_amb.
+// Returns the number of valid instances written (<= cap), or -1 on bad arguments.
+int64_t oracle_project_view(const oracle_scene* s, const oracle_opts* o, int e, int c, double* out, int64_t cap) {
+    ViewData V;
+    if (!build_view(s, o, e, c, V)) return -1;
+    int64_t n = 0;
+    for (const Geo& G : V.geo) {
+        if (n >= cap) break;
+        double* r = out + n * 16;
+        r[0] = (double)G.gid; r[1] = G.u; r[2] = G.v; r[3] = G.z;
+        r[4] = G.Q[0][0]; r[5] = G.Q[0][1]; r[6] = G.Q[1][1];
+        r[7] = G.cov[0][0]; r[8] = G.cov[0][1]; r[9] = G.cov[1][1];
+        r[10] = G.opac; r[11] = G.rgb[0]; r[12] = G.rgb[1]; r[13] = G.rgb[2];
+        r[14] = G.present; r[15] = G.near_amb;
+        ++n;
+    }
+    return (int64_t)V.geo.size();
+}
+
+// Renders view (e, c).  rgb [H*W*3], depth/alpha [H*W]: the primary branch.
+// tol_rgb/tol_d [H*W]: extra tolerance from flips beyond max_flips.  n_alt [H*W]: number
+// of alternative branches of each pixel; alt [alt_cap*5] receives them (r,g,b,d,a) in pixel
+// order.  stats[0] = alternatives needed, stats[1] = ambiguous pixels, stats[2] = decision
+// hash (as bits), stats[3] = instances projected.  Returns 0, or -1 on bad arguments, or 1 if
+// alt_cap was too small (outputs other than alt are still complete).
+int oracle_render_view(const oracle_scene* s, const oracle_opts* o, int e, int c,
+                       double* rgb, double* depth, double* alpha, double* tol_rgb, double* tol_d,
+                       int32_t* n_alt, double* alt, int64_t alt_cap, int64_t* stats) {
+    ViewData V;
+    if (!build_view(s, o, e, c, V)) return -1;
+    std::vector<std::vector<int>> rows;
+    row_pools(V, o, rows);
+    const int W = V.W, H = V.H;
+    std::vector<std::vector<Leaf>> row_alts(H);
+    std::vector<int64_t> row_amb(H, 0);
+    std::vector<uint64_t> row_hash(H, 0);
+    parallel_for(H, n_threads(o), [&](int64_t y, int) {
+        std::vector<std::vector<int>> cols(W);
+        cols_pool(V, o, rows[y], cols);
+        std::vector<Cand> cand;
+        uint64_t hsum = 0;
+        for (int x = 0; x < W; ++x) {
+            pixel_candidates(V, o, cols[x], x, (int)y, cand);
+            double Mc = std::max({std::fabs(o->bg[0]), std::fabs(o->bg[1]), std::fabs(o->bg[2])}), Mz = 0;
+            for (const Cand& cd : cand) {
+                const Geo& G = V.geo[cd.idx];
+                Mc = std::max({Mc, G.rgb[0], G.rgb[1], G.rgb[2]});
+                Mz = std::max(Mz, std::fabs(G.z));
+            }
+            PixelResult R;
+            Compositor comp{V, o, Mc, Mz, &R};
+            comp.run(cand, 0, 1.0, 0, 0, 0, 0, 0, true);
+            const int64_t p = y * W + x;
+            rgb[p * 3 + 0] = R.primary.r; rgb[p * 3 + 1] = R.primary.g; rgb[p * 3 + 2] = R.primary.b;
+            depth[p] = R.primary.d; if (alpha) alpha[p] = R.primary.a;
+            if (tol_rgb) tol_rgb[p] = R.tol_rgb;
+            if (tol_d) tol_d[p] = R.tol_d;
+            if (n_alt) n_alt[p] = (int32_t)R.alts.size();
+            for (auto& L : R.alts) row_alts[y].push_back(L);
+            row_amb[y] += R.ambiguous;
+            hsum += mix(R.hash, (uint64_t)p);
+        }
+        row_hash[y] = hsum;
+    });
+    int64_t need = 0, amb = 0; uint64_t h = 0;
+    for (int y = 0; y < H; ++y) { need += (int64_t)row_alts[y].size(); amb += row_amb[y]; h += row_hash[y]; }
+    if (stats) { stats[0] = need; stats[1] = amb; std::memcpy(&stats[2], &h, 8); stats[3] = (int64_t)V.geo.size(); }
+    if (alt && need <= alt_cap) {
+        int64_t k = 0;
+        for (int y = 0; y < H; ++y) for (auto& L : row_alts[y]) {
+            alt[k * 5 + 0] = L.r; alt[k * 5 + 1] = L.g; alt[k * 5 + 2] = L.b; alt[k * 5 + 3] = L.d; alt[k * 5 + 4] = L.a; ++k; }
+        return 0;
+    }
+    return need <= alt_cap ? 0 : 1;
+}
+
+// Adjoint of oracle_render_view's primary branch for L = sum grad_rgb . RGB + grad_depth . D.
+// Accumulates (+=) into the gradient arrays, which are laid out like the scene arrays
+// (g_sh is [G,16,3]; g_pose is [E,K,12]).  Returns 0, or -1 on bad arguments.
+int oracle_backward_view(const oracle_scene* s, const oracle_opts* o, int e, int c,
+                         const double* grad_rgb, const double* grad_depth,
+                         double* g_mean, double* g_log_scale, double* g_quat, double* g_logit,
+                         double* g_sh, double* g_pose) {
+    ViewData V;
+    if (!build_view(s, o, e, c, V)) return -1;
+    std::vector<std::vector<int>> rows;
+    row_pools(V, o, rows);
+    const int W = V.W, H = V.H;
+    const int nth = n_threads(o);
+    const size_t NG = V.geo.size();
+    // Per-instance adjoints: du, dv, da, db, dc, dopac, dr, dg, db, dz  (10 per instance)
+    std::vector<std::vector<double>> acc(nth, std::vector<double>(NG * 10, 0.0));
+    parallel_for(H, nth, [&](int64_t y, int tid) {
+        std::vector<std::vector<int>> cols(W);
+        cols_pool(V, o, rows[y], cols);
+        std::vector<Cand> cand;
+        std::vector<int> ci; std::vector<double> al, Ti, ex;
+        double* A = acc[tid].data();
+        for (int x = 0; x < W; ++x) {
+            pixel_candidates(V, o, cols[x], x, (int)y, cand);
+            // Primary forward, recording the contributors.
+            ci.clear(); al.clear(); Ti.clear(); ex.clear();
+            double T = 1.0;
+            for (const Cand& cd : cand) {
+                const Geo& G = V.geo[cd.idx];
+                if (!G.present || cd.q > o->q_max) continue;
+                const double e1 = std::exp(-0.5 * cd.q);
+                const double a = std::min(o->alpha_max, G.opac * e1);
+                if (a < o->alpha_min) continue;
+                const double Tn = T * (1 - a);
+                if (Tn < o->t_min) break;
+                ci.push_back((int)(&cd - cand.data())); al.push_back(a); Ti.push_back(T); ex.push_back(e1);
+                T = Tn;
+            }
+            const int64_t p = y * W + x;
+            const double gC[3] = {grad_rgb[p * 3], grad_rgb[p * 3 + 1], grad_rgb[p * 3 + 2]};
+            const double gD = grad_depth ? grad_depth[p] : 0.0;
+            // Suffix sums behind contributor i (including the background term bg*T_final).
+            double S[3] = {o->bg[0] * T, o->bg[1] * T, o->bg[2] * T}, SD = 0;
+            for (int n = (int)ci.size() - 1; n >= 0; --n) {
+                const Cand& cd = cand[ci[n]];
+                const Geo& G = V.geo[cd.idx];
+                const double a = al[n], Tb = Ti[n], w = a * Tb, Ta = Tb * (1 - a);
+                double* r = A + (size_t)cd.idx * 10;
+                r[6] += w * gC[0]; r[7] += w * gC[1]; r[8] += w * gC[2]; r[9] += w * gD;
+                // dL/dalpha = T_i [ gC . (rgb_i - S_i/T_{i+1}) + gD (z_i - SD_i/T_{i+1}) ]
+                double ga = 0;
+                for (int ch = 0; ch < 3; ++ch) ga += gC[ch] * (G.rgb[ch] - S[ch] / Ta);
+                ga += gD * (G.z - SD / Ta);
+                ga *= Tb;
+                for (int ch = 0; ch < 3; ++ch) S[ch] += w * G.rgb[ch];
+                SD += w * G.z;
+                if (G.opac * ex[n] > o->alpha_max) continue;   // clamped: no gradient to opacity or q
+                r[5] += ga * ex[n];
+                const double gq = ga * (-0.5 * a);
+                const double dx = cd.dx, dy = cd.dy;           // d = pixel - u
+                r[2] += gq * dx * dx; r[3] += gq * 2 * dx * dy; r[4] += gq * dy * dy;
+                r[0] += gq * (-2.0) * (G.Q[0][0] * dx + G.Q[0][1] * dy);
+                r[1] += gq * (-2.0) * (G.Q[0][1] * dx + G.Q[1][1] * dy);
+            }
+        }
+    });
+    std::vector<double> tot(NG * 10, 0.0);
+    for (int t = 0; t < nth; ++t) for (size_t i = 0; i < NG * 10; ++i) tot[i] += acc[t][i];
+    // Chain rule through projection, colour and pose (serial: deterministic accumulation).
+    for (size_t i = 0; i < NG; ++i) {
+        const Geo& G = V.geo[i];
+        const double* r = &tot[i * 10];
+        bool any = false; for (int k = 0; k < 10; ++k) any |= r[k] != 0; if (!any) continue;
+        const int64_t g = G.g;
+        double gRn[3][3] = {{0}}, gtn[3] = {0}, gmu[3] = {0};
+        // opacity
+        g_logit[g] += r[5] * G.opac * (1 - G.opac);
+        // colour: rgb = max(0, sum c_k Y_k(d) + 1/2)
+        double gd[3] = {0, 0, 0};
+        const int nc = (G.deg + 1) * (G.deg + 1);
+        for (int ch = 0; ch < 3; ++ch) {
+            if (!(G.raw[ch] > 0)) continue;
+            const double gr = r[6 + ch];
+            for (int k = 0; k < nc; ++k) {
+                g_sh[g * 48 + k * 3 + ch] += gr * G.Y[k];
+                const double cf = s->sh[g * 48 + k * 3 + ch];
+                for (int j = 0; j < 3; ++j) gd[j] += gr * cf * G.dY[k][j];
+            }
+        }
+        const double dd = gd[0] * G.d[0] + gd[1] * G.d[1] + gd[2] * G.d[2];
+        double gdir[3];
+        for (int j = 0; j < 3; ++j) gdir[j] = (gd[j] - G.d[j] * dd) / G.dlen;
+        for (int j = 0; j < 3; ++j) gmu[j] += gdir[j];
+        // dir = mu - o_local, o_local = Rn^T (o - tn)
+        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) gRn[a][b] += (G.ocam[a] - G.tn[a]) * (-gdir[b]);
+        for (int a = 0; a < 3; ++a) { double v = 0; for (int b = 0; b < 3; ++b) v += G.Rn[a][b] * (-gdir[b]); gtn[a] -= v; }
+        // conic -> 2D covariance: gCov = -Q G Q with G = [[ga, gb/2],[gb/2, gc]]
+        const double Gm[2][2] = {{r[2], 0.5 * r[3]}, {0.5 * r[3], r[4]}};
+        double QG[2][2], gCov[2][2];
+        for (int a = 0; a < 2; ++a) for (int b = 0; b < 2; ++b) QG[a][b] = G.Q[a][0] * Gm[0][b] + G.Q[a][1] * Gm[1][b];
+        for (int a = 0; a < 2; ++a) for (int b = 0; b < 2; ++b) gCov[a][b] = -(QG[a][0] * G.Q[0][b] + QG[a][1] * G.Q[1][b]);
+        // Cov = T Sigma_w T^T + lp I:  gSigma_w = T^T gCov T,  gT = 2 gCov T Sigma_w
+        double gSigw[3][3], gT[2][3];
+        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) {
+            double v = 0; for (int m = 0; m < 2; ++m) for (int n = 0; n < 2; ++n) v += G.T[m][a] * gCov[m][n] * G.T[n][b];
+            gSigw[a][b] = v; }
+        for (int a = 0; a < 2; ++a) for (int b = 0; b < 3; ++b) {
+            double v = 0;
+            for (int m = 0; m < 2; ++m) for (int k = 0; k < 3; ++k) v += gCov[a][m] * G.T[m][k] * G.Sigw[k][b];
+            gT[a][b] = 2 * v; }
+        // T = J Wc: gJ = gT Wc^T
+        double gJ[2][3];
+        for (int a = 0; a < 2; ++a) for (int b = 0; b < 3; ++b) {
+            double v = 0; for (int k = 0; k < 3; ++k) v += gT[a][k] * G.Wc[b][k]; gJ[a][b] = v; }
+        double gt[3] = {0, 0, 0};
+        const double tx = G.t[0], ty = G.t[1], tz = G.t[2];
+        gt[2] += gJ[0][0] * (-G.fx / (tz * tz)) + gJ[1][1] * (-G.fy / (tz * tz));
+        if (!G.clx) { gt[2] += gJ[0][2] * (2 * G.fx * tx / (tz * tz * tz)); gt[0] += gJ[0][2] * (-G.fx / (tz * tz)); }
+        else { gt[2] += gJ[0][2] * (G.fx * G.xc / (tz * tz)); }
+        if (!G.cly) { gt[2] += gJ[1][2] * (2 * G.fy * ty / (tz * tz * tz)); gt[1] += gJ[1][2] * (-G.fy / (tz * tz)); }
+        else { gt[2] += gJ[1][2] * (G.fy * G.yc / (tz * tz)); }
+        // mean in pixels and depth
+        gt[0] += r[0] * G.fx / tz; gt[2] += -r[0] * G.fx * tx / (tz * tz);
+        gt[1] += r[1] * G.fy / tz; gt[2] += -r[1] * G.fy * ty / (tz * tz);
+        gt[2] += r[9];
+        // t = Wc mu_w + tc; mu_w = Rn mu + tn
+        double gmuw[3];
+        for (int a = 0; a < 3; ++a) gmuw[a] = G.Wc[0][a] * gt[0] + G.Wc[1][a] * gt[1] + G.Wc[2][a] * gt[2];
+        for (int a = 0; a < 3; ++a) { gtn[a] += gmuw[a]; for (int b = 0; b < 3; ++b) { gRn[a][b] += gmuw[a] * G.mu[b]; gmu[b] += G.Rn[a][b] * gmuw[a]; } }
+        // Sigma_w = Rn Sigma Rn^T: gSigma = Rn^T gSigw Rn, gRn += 2 gSigw Rn Sigma
+        double gSig[3][3], tmp[3][3];
+        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) { double v = 0; for (int k = 0; k < 3; ++k) v += gSigw[a][k] * G.Rn[k][b]; tmp[a][b] = v; }
+        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) { double v = 0; for (int k = 0; k < 3; ++k) v += G.Rn[k][a] * tmp[k][b]; gSig[a][b] = v; }
+        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) { double v = 0; for (int k = 0; k < 3; ++k) v += tmp[a][k] * G.Sig[k][b]; gRn[a][b] += 2 * v; }
+        // Sigma = M M^T, M = Rq diag(sc): gM = 2 gSigma M
+        double gM[3][3];
+        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) { double v = 0; for (int k = 0; k < 3; ++k) v += gSig[a][k] * G.M[k][b]; gM[a][b] = 2 * v; }
+        for (int j = 0; j < 3; ++j) { double v = 0; for (int i2 = 0; i2 < 3; ++i2) v += G.Rq[i2][j] * gM[i2][j]; g_log_scale[g * 3 + j] += v * G.sc[j]; }
+        double gRq[3][3];
+        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) gRq[a][b] = gM[a][b] * G.sc[b];
+        // Rq(qn) -> qn
+        const double w = G.qn[0], x = G.qn[1], yq = G.qn[2], zq = G.qn[3];
+        const double dRw[3][3] = {{0, -2 * zq, 2 * yq}, {2 * zq, 0, -2 * x}, {-2 * yq, 2 * x, 0}};
+        const double dRx[3][3] = {{0, 2 * yq, 2 * zq}, {2 * yq, -4 * x, -2 * w}, {2 * zq, 2 * w, -4 * x}};
+        const double dRy[3][3] = {{-4 * yq, 2 * x, 2 * w}, {2 * x, 0, 2 * zq}, {-2 * w, 2 * zq, -4 * yq}};
+        const double dRz[3][3] = {{-4 * zq, -2 * w, 2 * x}, {2 * w, -4 * zq, 2 * yq}, {2 * x, 2 * yq, 0}};
+        double gqn[4] = {0, 0, 0, 0};
+        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) {
+            gqn[0] += gRq[a][b] * dRw[a][b]; gqn[1] += gRq[a][b] * dRx[a][b];
+            gqn[2] += gRq[a][b] * dRy[a][b]; gqn[3] += gRq[a][b] * dRz[a][b]; }
+        const double qd = gqn[0] * G.qn[0] + gqn[1] * G.qn[1] + gqn[2] * G.qn[2] + gqn[3] * G.qn[3];
+        for (int k = 0; k < 4; ++k) g_quat[g * 4 + k] += (gqn[k] - G.qn[k] * qd) / G.qlen;
+        for (int k = 0; k < 3; ++k) g_mean[g * 3 + k] += gmu[k];
+        double* gp = g_pose + ((int64_t)e * s->K + G.slot) * 12;
+        for (int a = 0; a < 3; ++a) { for (int b = 0; b < 3; ++b) gp[a * 4 + b] += gRn[a][b]; gp[a * 4 + 3] += gtn[a]; }
+    }
+    return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,309 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test states what fixes the expected value: a library routine (scipy's complex spherical
+harmonics, scipy's rotation matrices), a closed form of the EWA projection of an isotropic
+Gaussian, compositing invariants (weights + transmittance = 1), rigid-motion invariance,
+brute force, or finite differences.  No GPU is needed.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+from scipy.special import sph_harm_y
+
+import oracle as O
+from paper_2507_21981_gb300 import scenes as S
+from tests import scene_utils as U
+
+BASE = O.OracleOptions(nthreads=4)
+
+
+def opts(**kw):
+    d = dict(BASE.__dict__)
+    d.update(kw)
+    return O.OracleOptions(**d)
+
+
+# --------------------------------------------------------------------------- spherical harmonics
+def _real_sh_scipy(l, m, d):
+    """Real SH with the Condon-Shortley phase from scipy's complex Y_l^m (which includes it)."""
+    theta = math.acos(max(-1.0, min(1.0, d[2])))
+    phi = math.atan2(d[1], d[0]) % (2 * math.pi)
+    if m == 0:
+        return sph_harm_y(l, 0, theta, phi).real
+    Y = sph_harm_y(l, abs(m), theta, phi)
+    return math.sqrt(2) * (Y.real if m > 0 else Y.imag)
+
+
+def test_sh_matches_scipy_complex_harmonics():
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        Y, _ = O.sh_basis(3, d)
+        for l in range(4):
+            for m in range(-l, l + 1):
+                assert Y[l * l + l + m] == pytest.approx(_real_sh_scipy(l, m, d), abs=1e-13)
+
+
+def test_sh_degree_one_closed_form():
+    rng = np.random.default_rng(1)
+    c = math.sqrt(3 / (4 * math.pi))
+    for _ in range(20):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        Y, _ = O.sh_basis(1, d)
+        np.testing.assert_allclose(Y[1:4], c * np.array([-d[1], d[2], -d[0]]), atol=1e-15)
+        assert np.all(Y[4:] == 0)
+
+
+def test_sh_orthonormal_on_sphere():
+    # Gauss-Legendre in z (exact to degree 15) x uniform azimuth (exact for |m| <= 7).
+    zs, wz = np.polynomial.legendre.leggauss(8)
+    phis = np.arange(16) * 2 * np.pi / 16
+    Gram = np.zeros((16, 16))
+    for z, w in zip(zs, wz):
+        r = math.sqrt(1 - z * z)
+        for ph in phis:
+            Y, _ = O.sh_basis(3, np.array([r * math.cos(ph), r * math.sin(ph), z]))
+            Gram += w * (2 * np.pi / 16) * np.outer(Y, Y)
+    np.testing.assert_allclose(Gram, np.eye(16), atol=1e-13)
+
+
+def test_sh_tangential_gradient_matches_fd():
+    rng = np.random.default_rng(2)
+    for _ in range(10):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        _, dY = O.sh_basis(3, d)
+        P = np.eye(3) - np.outer(d, d)
+        for j in range(3):
+            h = 1e-6
+            e = np.zeros(3); e[j] = h
+            Yp, _ = O.sh_basis(3, (d + e) / np.linalg.norm(d + e))
+            Ym, _ = O.sh_basis(3, (d - e) / np.linalg.norm(d - e))
+            fd = (Yp - Ym) / (2 * h)
+            np.testing.assert_allclose((dY @ P)[:, j], fd, atol=1e-8)
+
+
+def test_degree_zero_colour_is_view_independent():
+    rng = np.random.default_rng(3)
+    nd = U.node([[0, 0, 5.0]], sh=U.colour_sh([[0.2, 0.6, 0.9]]), deg=0)
+    for _ in range(5):
+        cam = U.rigid(Rotation.random(random_state=rng).as_matrix(), rng.normal(size=3))
+        # place the camera so the Gaussian is in front of it: move it along its own z axis
+        R = cam[:, :3]
+        centre = np.array([0, 0, 5.0]) - 3.0 * R[2]
+        cam = U.rigid(R, -R @ centre)
+        sc = U.single_view([nd], cam=cam)
+        p = O.project_view(sc, 0, 0, BASE)
+        np.testing.assert_allclose(p[0, 11:14], [0.2, 0.6, 0.9], atol=1e-7)
+
+
+def test_colour_uses_node_frame_direction():
+    """Rotating a node together with the camera leaves its SH colour unchanged."""
+    rng = np.random.default_rng(4)
+    sh = rng.normal(0, 0.2, (1, 16, 3))
+    nd = U.node([[0.1, -0.2, 0.3]], sh=sh, deg=3, dtype=np.float64)
+    cam0 = U.rigid(np.eye(3), [0, 0, 4.0])
+    base = O.project_view(U.single_view([nd], cam=cam0), 0, 0, BASE)[0, 11:14]
+    for _ in range(5):
+        G = U.rigid(Rotation.random(random_state=rng).as_matrix(), rng.normal(size=3))
+        sc = U.single_view([nd], poses=[G], cam=U.compose(cam0, U.inverse(G)))
+        np.testing.assert_allclose(O.project_view(sc, 0, 0, BASE)[0, 11:14], base, atol=1e-12)
+
+
+# --------------------------------------------------------------------------- projection
+@pytest.mark.parametrize("lowpass", [0.0, 0.3])
+def test_isotropic_projection_closed_form(lowpass):
+    sigma, f = 0.05, 60.0
+    pts = [[0.0, 0.0, 4.0], [0.5, -0.3, 3.0], [-0.8, 0.6, 5.0]]
+    nd = U.node(pts, log_scales=np.full((3, 3), math.log(sigma)), dtype=np.float64)
+    sc = U.single_view([nd], f=f, W=64, H=64, cx=32.0, cy=30.0)
+    p = O.project_view(sc, 0, 0, opts(lowpass=lowpass))
+    assert p.shape[0] == 3
+    for row, (x, y, z) in zip(p, pts):
+        # J J^T sigma^2 for J = f/z [[1, 0, -x/z], [0, 1, -y/z]]
+        k = (f * sigma / z) ** 2
+        cov = k * np.array([[1 + x * x / z / z, x * y / z / z], [x * y / z / z, 1 + y * y / z / z]]) + lowpass * np.eye(2)
+        np.testing.assert_allclose(row[[7, 8, 9]], [cov[0, 0], cov[0, 1], cov[1, 1]], rtol=1e-12)
+        inv = np.linalg.inv(cov)
+        np.testing.assert_allclose(row[[4, 5, 6]], [inv[0, 0], inv[0, 1], inv[1, 1]], rtol=1e-11)
+        np.testing.assert_allclose(row[[1, 2, 3]], [f * x / z + 32.0, f * y / z + 30.0, z], rtol=1e-14)
+
+
+def test_anisotropic_projection_matches_rotation_library():
+    rng = np.random.default_rng(5)
+    n = 20
+    q = rng.normal(size=(n, 4))                       # (w,x,y,z), not normalised
+    ls = rng.normal(-2.5, 0.5, (n, 3))
+    mu = rng.uniform(-0.5, 0.5, (n, 3))
+    nd = U.node(mu, log_scales=ls, quats=q, dtype=np.float64)
+    pose = U.rigid(Rotation.random(random_state=rng).as_matrix(), [0.1, 0.2, 0.3])
+    cam = U.rigid(np.eye(3), [0, 0, 3.0])
+    fx = 80.0
+    sc = U.single_view([nd], poses=[pose], cam=cam, f=fx, W=96, H=96)
+    p = O.project_view(sc, 0, 0, opts(lowpass=0.0))
+    assert p.shape[0] == n
+    for row in p:
+        g = int(row[0])
+        R = Rotation.from_quat([q[g, 1], q[g, 2], q[g, 3], q[g, 0]]).as_matrix()   # scipy is scalar-last
+        Sig = R @ np.diag(np.exp(2 * ls[g])) @ R.T
+        Rn, tn = pose[:, :3], pose[:, 3]
+        t = cam[:, :3] @ (Rn @ mu[g] + tn) + cam[:, 3]
+        J = np.array([[fx / t[2], 0, -fx * t[0] / t[2] ** 2], [0, fx / t[2], -fx * t[1] / t[2] ** 2]])
+        Tm = J @ cam[:, :3] @ Rn
+        cov = Tm @ Sig @ Tm.T
+        np.testing.assert_allclose(row[[7, 8, 9]], [cov[0, 0], cov[0, 1], cov[1, 1]], rtol=1e-10, atol=1e-14)
+
+
+def test_depth_key32_is_binary32_evaluation():
+    """z32 equals the specified sequence of binary32 operations evaluated by numpy."""
+    rng = np.random.default_rng(6)
+    f4 = np.float32
+    for _ in range(200):
+        W = U.rigid(Rotation.random(random_state=rng).as_matrix(), rng.normal(size=3) * 3).astype(f4)
+        P = U.rigid(Rotation.random(random_state=rng).as_matrix(), rng.normal(size=3)).astype(f4)
+        mu = rng.normal(size=3).astype(f4)
+        M = [f4(f4(W[2, 0] * P[0, j]) + f4(W[2, 1] * P[1, j])) + f4(W[2, 2] * P[2, j]) for j in range(3)]
+        M3 = f4(f4(f4(f4(W[2, 0] * P[0, 3]) + f4(W[2, 1] * P[1, 3])) + f4(W[2, 2] * P[2, 3])) + W[2, 3])
+        z = f4(f4(f4(f4(M[0] * mu[0]) + f4(M[1] * mu[1])) + f4(M[2] * mu[2])) + M3)
+        assert O.depth_key32(W.astype(np.float64), P.astype(np.float64), mu.astype(np.float64)) == z
+
+
+# --------------------------------------------------------------------------- compositing
+def test_peak_alpha_at_centre_pixel():
+    for logit, expect in [(0.3, 1 / (1 + math.exp(-0.3))), (8.0, 0.99), (-2.0, 1 / (1 + math.exp(2.0)))]:
+        nd = U.node([[0.0, 0.0, 4.0]], logits=[logit], sh=U.colour_sh([[0.7, 0.2, 0.4]]))
+        sc = U.single_view([nd], W=32, H=32, cx=16.5, cy=16.5)        # centre lands on pixel (16,16)
+        for bg in [(0, 0, 0), (0.1, 0.5, 1.0)]:
+            r = O.render_view(sc, 0, 0, opts(bg=bg))
+            a = r.alpha[16, 16]
+            assert a == pytest.approx(min(0.99, expect), rel=1e-7)      # logits are stored as float32
+            colour = np.array([0.7, 0.2, 0.4], np.float32).astype(np.float64)
+            np.testing.assert_allclose(r.rgb[16, 16], colour * a + (1 - a) * np.array(bg), rtol=1e-6)
+
+
+def test_single_gaussian_closed_form_image():
+    sigma, f, z, opac = 0.08, 50.0, 4.0, 0.8
+    nd = U.node([[0.0, 0.0, z]], log_scales=np.full((1, 3), math.log(sigma)), logits=[math.log(opac / (1 - opac))],
+                sh=U.colour_sh([[0.3, 0.6, 0.9]]), dtype=np.float64)
+    sc = U.single_view([nd], f=f, W=24, H=24, cx=12.0, cy=12.0)
+    lp = 0.3
+    r = O.render_view(sc, 0, 0, opts(lowpass=lp, bg=(0.2, 0.2, 0.2)))
+    s2 = (f * sigma / z) ** 2 + lp
+    ys, xs = np.mgrid[0:24, 0:24]
+    q = ((xs + 0.5 - 12.0) ** 2 + (ys + 0.5 - 12.0) ** 2) / s2
+    a = np.minimum(0.99, opac * np.exp(-0.5 * q))
+    keep = (q <= 9) & (a >= 1 / 255)
+    a = np.where(keep, a, 0)
+    np.testing.assert_allclose(r.alpha, a, atol=1e-13)
+    np.testing.assert_allclose(r.depth, a * z, atol=1e-12)
+    np.testing.assert_allclose(r.rgb, a[..., None] * [0.3, 0.6, 0.9] + (1 - a[..., None]) * 0.2, atol=1e-12)
+
+
+def test_weights_and_transmittance_sum_to_one():
+    sc = S.config1(seed=7, n_bg=600, n_obj=150, res=48, f=41.25)
+    for nd in sc.nodes:
+        nd.sh[:] = U.colour_sh([[1.0, 1.0, 1.0]])[0]
+    r0 = O.render_view(sc, 0, 0, opts(bg=(0, 0, 0)))
+    r1 = O.render_view(sc, 0, 0, opts(bg=(1, 1, 1)))
+    assert r0.alpha.max() > 0.5
+    for ch in range(3):
+        np.testing.assert_allclose(r0.rgb[..., ch], r0.alpha, atol=1e-12)
+        np.testing.assert_allclose(r1.rgb[..., ch], 1.0, atol=1e-12)
+
+
+def test_depth_of_a_fronto_parallel_layer():
+    rng = np.random.default_rng(8)
+    z = 3.0
+    mu = np.c_[rng.uniform(-0.6, 0.6, (80, 2)), np.full(80, z)]
+    nd = U.node(mu, log_scales=rng.normal(-2.5, 0.3, (80, 3)), logits=rng.normal(0, 1, 80),
+                sh=U.colour_sh(rng.random((80, 3))))
+    sc = U.single_view([nd], f=40.0)
+    r = O.render_view(sc, 0, 0, BASE)
+    np.testing.assert_allclose(r.depth, z * r.alpha, rtol=1e-12, atol=1e-14)
+
+
+def test_termination_stops_without_compositing():
+    # four coincident-footprint Gaussians on the axis at increasing depth, alpha 0.95 each at
+    # the centre pixel: T = 1, .05, .0025, 1.25e-4, then 6.25e-6 < 1e-4 -> stop before the 4th.
+    cols = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1]], np.float64)
+    logit = math.log(0.95 / 0.05)
+    nd = U.node([[0, 0, 3.0], [0, 0, 3.1], [0, 0, 3.2], [0, 0, 3.3]], log_scales=np.full((4, 3), math.log(0.3)),
+                logits=[logit] * 4, sh=U.colour_sh(cols), dtype=np.float64)
+    sc = U.single_view([nd], W=16, H=16, cx=8.5, cy=8.5)
+    r = O.render_view(sc, 0, 0, opts(bg=(0.5, 0.5, 0.5)))
+    T, C, D = 1.0, np.zeros(3), 0.0
+    for i in range(3):
+        C += 0.95 * T * cols[i]; D += 0.95 * T * [3.0, 3.1, 3.2][i]; T *= 0.05
+    np.testing.assert_allclose(r.rgb[8, 8], C + 0.5 * T, rtol=1e-12)
+    assert r.depth[8, 8] == pytest.approx(D, rel=1e-12)
+    assert r.alpha[8, 8] == pytest.approx(1 - T, rel=1e-12)
+
+
+def test_faint_gaussian_is_skipped_not_terminal():
+    nd = U.node([[0, 0, 3.0], [0, 0, 4.0]], log_scales=np.full((2, 3), math.log(0.3)),
+                logits=[math.log(0.003 / 0.997), 1.0], sh=U.colour_sh([[1, 0, 0], [0, 1, 0]]), dtype=np.float64)
+    sc = U.single_view([nd], W=16, H=16, cx=8.5, cy=8.5)
+    r = O.render_view(sc, 0, 0, BASE)
+    a = 1 / (1 + math.exp(-1.0))
+    np.testing.assert_allclose(r.rgb[8, 8], [0, a, 0], atol=1e-12)
+
+
+def test_storage_order_does_not_matter_for_distinct_depths():
+    sc = S.config1(seed=9, n_bg=300, n_obj=100, res=32, f=27.5)
+    r = O.render_view(sc, 0, 0, BASE)
+    swapped = S.scene_from_lists("swap", [sc.nodes[1], sc.nodes[0]], [[0, 1]],
+                                 [[sc.node_poses[0, 1], sc.node_poses[0, 0]]],
+                                 [[(*sc.cam_intr[0, 0], *sc.cam_res[0, 0], sc.cam_pose[0, 0])]])
+    r2 = O.render_view(swapped, 0, 0, BASE)
+    np.testing.assert_allclose(r2.rgb, r.rgb, atol=1e-13)
+    np.testing.assert_allclose(r2.depth, r.depth, atol=1e-13)
+
+
+def test_zero_opacity_gives_background():
+    sc = S.config1(seed=10, n_bg=200, n_obj=50, res=32, f=27.5)
+    for nd in sc.nodes:
+        nd.opacity_logit[:] = -40.0
+    r = O.render_view(sc, 0, 0, opts(bg=(0.25, 0.5, 0.75)))
+    np.testing.assert_allclose(r.rgb, np.broadcast_to([0.25, 0.5, 0.75], r.rgb.shape), atol=0)
+    assert np.all(r.depth == 0) and np.all(r.alpha == 0)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_bruteforce_agrees_with_candidate_lists(seed):
+    sc = S.config1(seed=seed, n_bg=40, n_obj=10, res=16, f=13.75)
+    a = O.render_view(sc, 0, 0, BASE)
+    b = O.render_view(sc, 0, 0, opts(bruteforce=1))
+    assert a.instances == b.instances
+    assert np.array_equal(a.rgb, b.rgb) and np.array_equal(a.depth, b.depth) and np.array_equal(a.alpha, b.alpha)
+    assert a.decision_hash == b.decision_hash
+
+
+def test_bruteforce_agrees_on_fd_subset():
+    sc = S.fd_subset(seed=4)
+    a = O.render_view(sc, 0, 0, BASE)
+    b = O.render_view(sc, 0, 0, opts(bruteforce=1))
+    assert np.array_equal(a.rgb, b.rgb) and np.array_equal(a.depth, b.depth)
+
+
+def test_rigid_motion_of_scene_and_camera_leaves_image_unchanged():
+    rng = np.random.default_rng(11)
+    sc = S.config1(seed=11, n_bg=800, n_obj=200, res=40, f=34.4)
+    o = opts(order64=1)
+    r = O.render_view(sc, 0, 0, o)
+    for _ in range(3):
+        G = U.rigid(Rotation.random(random_state=rng).as_matrix(), rng.normal(size=3) * 2)
+        poses = np.stack([U.compose(G, sc.node_poses[0, j].astype(np.float64)) for j in range(2)])[None]
+        cam = U.compose(sc.cam_pose[0, 0].astype(np.float64), U.inverse(G))[None, None]
+        moved = S.Scene("moved", sc.nodes, sc.env_node_ids, poses, sc.cams_per_env, sc.cam_intr, sc.cam_res, cam)
+        r2 = O.render_view(moved, 0, 0, o)
+        np.testing.assert_allclose(r2.rgb, r.rgb, atol=1e-10)
+        np.testing.assert_allclose(r2.depth, r.depth, atol=1e-10)
+
+
+def test_ambiguity_fraction_is_small_on_config1():
+    r = O.render_view(S.config1(seed=1), 0, 0, BASE)
+    assert r.ambiguous_pixels / r.rgb[..., 0].size < 1e-3
