@@ -1,0 +1,179 @@
+/*
+ * dgs.h -- C ABI of libdgs, a batched 3D Gaussian Splatting RGB + depth renderer for many
+ * parallel environments on one GB300 (sm_103a).
+ *
+ * What is rendered (DISCOVERSE, Sec. III-A "Renderer", Sec. III-B "Asset Formatting",
+ * Sec. III-C "Sensor"): each environment holds a background Gaussian node plus interactive
+ * nodes (objects, robot links) whose Gaussians move rigidly with the node's pose; the
+ * renderer is the native tile-based 3DGS pipeline (EWA splatting, spherical-harmonics colour,
+ * depth sorting, front-to-back alpha-blending) and produces RGB and depth by
+ * alpha-compositing the colour and the camera-space z of the Gaussians.
+ *
+ * Conventions (fixed readings; every numeric constant is a field of dgs_options):
+ *   - Poses are row-major 3x4 [R|t] FP32 matrices.  node poses are world_from_node, camera
+ *     extrinsics cam_from_world.  Cameras are pinhole, OpenCV axes (x right, y down, z
+ *     forward); pixel (x, y) samples the point (x + 1/2, y + 1/2); u = fx*tx/tz + cx.
+ *   - Quaternions are (w, x, y, z), need not be unit (normalised inside).  Scales are natural
+ *     logs of the per-axis standard deviations.  Opacity = sigmoid(logit).
+ *   - Colour = max(0, sum_k sh[k] Y_k(d) + 1/2) with the real SH basis (Condon-Shortley
+ *     phase, k = l^2 + l + m, degree <= 3) and d the unit direction from the camera centre to
+ *     the Gaussian, expressed in the node frame.
+ *   - A Gaussian touches a pixel iff d^T conic d <= q_max (default 9, the 3-sigma ellipse);
+ *     alpha = min(alpha_max, opacity*exp(-q/2)); alpha < alpha_min is skipped; compositing
+ *     stops, without the current Gaussian, once T*(1-alpha) < t_min.
+ *     RGB = sum w_i rgb_i + bg*T_final, depth = sum w_i z_i (not normalised), alpha = 1 - T.
+ *   - Depth order and near-plane cull use the FP32 key z32 = camera-space z evaluated in
+ *     binary32 without fused multiply-adds in a fixed order (camera_from_node row 2 composed
+ *     first); equal keys are ordered by global id = (sum of sizes of the preceding nodes in
+ *     the node array) + index in the node.  Keys beyond 2^32 * 2^floor(log2 z_near) compare
+ *     equal.
+ *
+ * Memory: every array pointer marked DEVICE is a CUDA device pointer owned by the caller
+ * and must stay valid until the work queued on `stream` has finished.  Arrays marked HOST are
+ * read during the call only.  The library owns only the workspace inside a context.
+ * Errors: every call returns a dgs_status; nothing throws across the ABI.  Argument
+ * validation failures return synchronously and queue no work.  dgs_last_error() describes
+ * the most recent failure of a context.  A context is not thread-safe: one host thread at a
+ * time.
+ */
+#ifndef DGS_H
+#define DGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DGS_ABI_VERSION 1
+
+typedef enum dgs_status {
+    DGS_OK = 0,
+    DGS_ERR_INVALID_ARG = 1, /* bad shape, null pointer, bad enum, non-finite or non-rigid pose */
+    DGS_ERR_CUDA = 2,        /* a CUDA runtime call failed; see dgs_last_error */
+    DGS_ERR_OOM = 3,         /* workspace allocation failed */
+    DGS_ERR_CAPACITY = 4,    /* a batch exceeds a hard limit (2^30 tile pairs per view group) */
+    DGS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (results are invalid) */
+    DGS_ERR_UNSUPPORTED = 6  /* the call is not available for these arguments */
+} dgs_status;
+
+typedef enum dgs_dtype { DGS_F32 = 0, DGS_BF16 = 1, DGS_F16 = 2 } dgs_dtype;
+
+typedef enum dgs_mode {
+    DGS_MODE_PLAIN = 0,   /* every view runs its own projection/binning/sort/composite sequence */
+    DGS_MODE_BATCHED = 1  /* all views of a call share one sequence; attributes read once per group */
+} dgs_mode;
+
+/* One scene node: structure-of-arrays Gaussians in the node's own frame. */
+typedef struct dgs_node {
+    const float* mean;          /* DEVICE [n,3] FP32 */
+    const void* log_scale;      /* DEVICE [n,3] of `dtype` */
+    const void* quat;           /* DEVICE [n,4] of `dtype`, (w,x,y,z) */
+    const float* opacity_logit; /* DEVICE [n] FP32 */
+    const void* sh;             /* DEVICE [n,(sh_degree+1)^2,3] of `dtype`, coefficient-major */
+    int64_t n;                  /* number of Gaussians, >= 0 */
+    int32_t sh_degree;          /* 0..3 */
+    int32_t dtype;              /* dgs_dtype of log_scale, quat and sh */
+} dgs_node;
+
+/* Pinhole camera.  width, height >= 1. */
+typedef struct dgs_camera {
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float cam_from_world[12];   /* row-major [R|t] */
+} dgs_camera;
+
+typedef struct dgs_options {
+    int32_t mode;               /* dgs_mode, default DGS_MODE_BATCHED */
+    int32_t tile_w, tile_h;     /* tile shape in pixels; w*h in {64,128,256}, default 16x16 */
+    int32_t exact_tile_test;    /* 1 = bin a Gaussian only to tiles its ellipse reaches (default) */
+    float z_near;               /* default 0.01; must be > 0 */
+    float lowpass;              /* screen-space dilation added to the 2D covariance, default 0.3 px^2 */
+    float alpha_min;            /* default 1/255 */
+    float alpha_max;            /* default 0.99 */
+    float t_min;                /* default 1e-4 */
+    float q_max;                /* default 9 */
+    float guard;                /* Jacobian clamp: |tx/tz| <= guard * (W/2)/fx, default 1.3 */
+    float bg[3];                /* background colour, default 0 */
+    int32_t profile;            /* 1 = time each kernel class with CUDA events (dgs_kernel_times) */
+    int32_t views_per_group;    /* batched mode: max views per group, 0 = automatic */
+} dgs_options;
+
+typedef struct dgs_ctx dgs_ctx;
+
+/* Per-call statistics of the most recent dgs_render on a context. */
+typedef struct dgs_stats {
+    int64_t n_views;
+    int64_t n_pixels;
+    int64_t n_instances;        /* (Gaussian, view) pairs considered */
+    int64_t n_visible;          /* instances that passed the cull */
+    int64_t n_pairs;            /* (instance, tile) pairs sorted */
+    int32_t n_groups;           /* view groups (batched) or views (plain) */
+    int32_t key_bits;           /* significant sort-key bits of the largest group */
+} dgs_stats;
+
+/* Kernel classes timed when dgs_options.profile = 1 (milliseconds, summed over the call). */
+typedef enum dgs_kernel_class {
+    DGS_K_SETUP = 0, DGS_K_COUNT = 1, DGS_K_SCAN = 2, DGS_K_EMIT = 3, DGS_K_SORT = 4,
+    DGS_K_RANGES = 5, DGS_K_COMPOSITE = 6, DGS_K_BACKWARD = 7, DGS_K_COUNT_CLASSES = 8
+} dgs_kernel_class;
+
+/* Fills *opt with the defaults listed above. */
+void dgs_default_options(dgs_options* opt);
+
+/* Creates a context on the current CUDA device.  Allocates no device memory yet.
+ * Returns DGS_ERR_INVALID_ARG for a null `out` or invalid options. */
+int dgs_context_create(dgs_ctx** out, const dgs_options* opt);
+
+/* Frees the context and its workspace (synchronises the device first).  Null is a no-op. */
+int dgs_context_destroy(dgs_ctx* ctx);
+
+/* Message of the most recent failure on `ctx` ("" if none); valid until the next call. */
+const char* dgs_last_error(const dgs_ctx* ctx);
+
+/* Bytes of device workspace currently held by the context. */
+int dgs_workspace_query(const dgs_ctx* ctx, size_t* bytes);
+
+/*
+ * Renders every view of a batch of environments.
+ *
+ *   nodes[n_nodes]                HOST array of node descriptors (attribute arrays DEVICE).
+ *   env_node_ids[n_envs*max_nodes] HOST, node drawn in slot j of env e, -1 = empty; a node id
+ *                                 appears at most once per env.
+ *   node_poses[n_envs*max_nodes*12] DEVICE, world_from_node of slot j of env e (FP32).
+ *   cams[n_envs*max_cams]         HOST, camera c of env e (only c < cams_per_env[e] are read).
+ *   cams_per_env[n_envs]          HOST, 0..max_cams.
+ *   View v enumerates (e, c) env-major.  Outputs are flat over views: view v occupies pixels
+ *   [off_v, off_v + W_v*H_v) in row-major order, off_v = view_pixel_offset[v] (HOST [V]) or,
+ *   if view_pixel_offset is NULL, the sum of the sizes of the preceding views.
+ *   out_rgb   DEVICE FP32 [total_pixels,3] (interleaved RGB), required.
+ *   out_depth DEVICE FP32 [total_pixels], required.
+ *   out_alpha DEVICE FP32 [total_pixels] or NULL.
+ *   stream    a cudaStream_t (NULL = legacy default stream).
+ *
+ * Work is queued on `stream`.  The call reads per-view counts back once (one stream
+ * synchronisation) to size the workspace, and synchronises again before returning so that
+ * device-side error flags (invalid pose, timeout, capacity) are reported in the return code.
+ */
+int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes,
+               const int32_t* env_node_ids, int32_t n_envs, int32_t max_nodes,
+               const float* node_poses,
+               const dgs_camera* cams, const int32_t* cams_per_env, int32_t max_cams,
+               float* out_rgb, float* out_depth, float* out_alpha,
+               const int64_t* view_pixel_offset, void* stream);
+
+/* Statistics of the most recent successful dgs_render on ctx. */
+int dgs_last_stats(const dgs_ctx* ctx, dgs_stats* out);
+
+/* Per-kernel-class device time (ms) of the most recent call with profile = 1;
+ * ms[DGS_K_COUNT_CLASSES]. */
+int dgs_kernel_times(const dgs_ctx* ctx, float* ms);
+
+/* Launches of library kernels queued by the most recent call. */
+int64_t dgs_last_launches(const dgs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGS_H */

@@ -1,0 +1,591 @@
+// libdgs C ABI: contexts, argument validation, workspace and the render sequence.
+//
+// A call renders every (env, camera) view of a batch (Sec. III-C: RGB and depth sensors of
+// many parallel environments, Sec. III-B: background + posed interactive nodes):
+//   setup     camera_from_node per (view, slot), pose validation            (K0)
+//   count     per (view, 32-Gaussian chunk): visible instances, tile pairs    (K1)
+//   scan      exclusive offsets of that table; per-view totals read back once
+//   per view group: emit records + pairs (K2), radix sort (K3), tile ranges (K4),
+//                   composite RGB + depth (K5)
+// Plain mode makes every view its own group and launches its count/emit per view; batched
+// mode counts all views in one launch (each Gaussian's attributes read once) and emits,
+// sorts and composites as few groups as the 2^30-pair limit of the sort allows.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dgs_internal.cuh"
+
+using namespace dgs;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct TimedRange {
+    int cls;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct dgs_ctx {
+    dgs_options opt{};
+    std::string err;
+    int device = 0;
+    DevBuf meta, counts, inst_off, pair_off, parts, records, keys0, vals0, keys1, vals1, hist, status, counters, ranges,
+        errword, readback;
+    void* h_meta = nullptr;
+    size_t h_meta_bytes = 0;
+    void* h_read = nullptr;
+    size_t h_read_bytes = 0;
+    dgs_stats stats{};
+    float ktimes[DGS_K_COUNT_CLASSES] = {};
+    int64_t launches = 0;
+    std::vector<cudaEvent_t> events;
+    std::vector<TimedRange> ranges_timed;
+    size_t next_event = 0;
+};
+
+namespace {
+
+int fail(dgs_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_fail(dgs_ctx* ctx, cudaError_t e, const char* what) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? DGS_ERR_OOM : DGS_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define DGS_CUDA(ctx, call)                                        \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
+    } while (0)
+
+int ensure(dgs_ctx* ctx, DevBuf& b, size_t bytes) {
+    if (bytes <= b.bytes) return DGS_OK;
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFree");
+    }
+    size_t want = std::max<size_t>(bytes + bytes / 4, 256);
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(ctx, e, "cudaMalloc");
+    }
+    b.bytes = want;
+    return DGS_OK;
+}
+
+int ensure_host(dgs_ctx* ctx, void*& p, size_t& have, size_t bytes) {
+    if (bytes <= have) return DGS_OK;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    have = 0;
+    size_t want = std::max<size_t>(bytes + bytes / 4, 4096);
+    cudaError_t e = cudaMallocHost(&p, want);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMallocHost");
+    have = want;
+    return DGS_OK;
+}
+
+void free_buf(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool finite(float x) { return std::isfinite(x); }
+
+int check_options(const dgs_options* o, std::string& why) {
+    if (o->mode != DGS_MODE_PLAIN && o->mode != DGS_MODE_BATCHED) { why = "mode"; return 0; }
+    const int area = o->tile_w * o->tile_h;
+    if (o->tile_w < 1 || o->tile_h < 1 || (area != 64 && area != 128 && area != 256)) { why = "tile shape"; return 0; }
+    if (!(o->z_near > 0) || !finite(o->z_near)) { why = "z_near"; return 0; }
+    if (!(o->lowpass >= 0) || !finite(o->lowpass)) { why = "lowpass"; return 0; }
+    if (!(o->alpha_min >= 0) || !(o->alpha_max > 0) || !(o->alpha_max <= 1)) { why = "alpha limits"; return 0; }
+    if (!(o->t_min >= 0) || !(o->t_min < 1)) { why = "t_min"; return 0; }
+    if (!(o->q_max > 0) || !finite(o->q_max)) { why = "q_max"; return 0; }
+    if (!(o->guard > 0) || !finite(o->guard)) { why = "guard"; return 0; }
+    for (int i = 0; i < 3; ++i) if (!finite(o->bg[i])) { why = "bg"; return 0; }
+    if (o->views_per_group < 0) { why = "views_per_group"; return 0; }
+    return 1;
+}
+
+cudaEvent_t take_event(dgs_ctx* ctx) {
+    if (ctx->next_event == ctx->events.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        ctx->events.push_back(e);
+    }
+    return ctx->events[ctx->next_event++];
+}
+
+struct Timer {
+    dgs_ctx* ctx;
+    cudaStream_t s;
+    bool on;
+    cudaEvent_t a{};
+    int cls = -1;
+    void begin(int c) {
+        if (!on) return;
+        cls = c;
+        a = take_event(ctx);
+        cudaEventRecord(a, s);
+    }
+    void end() {
+        if (!on || cls < 0) return;
+        cudaEvent_t b = take_event(ctx);
+        cudaEventRecord(b, s);
+        ctx->ranges_timed.push_back({cls, a, b});
+        cls = -1;
+    }
+};
+
+__global__ void k_view_totals(const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off,
+                              const int64_t* __restrict__ view_tab, int n, uint64_t* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = inst_off[view_tab[i]];
+    out[n + i] = pair_off[view_tab[i]];
+}
+
+int bits_for(uint64_t n) {   // smallest b with 2^b >= n (n >= 1)
+    int b = 0;
+    while (b < 63 && (1ull << b) < n) ++b;
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dgs_default_options(dgs_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->mode = DGS_MODE_BATCHED;
+    o->tile_w = 16;
+    o->tile_h = 16;
+    o->exact_tile_test = 1;
+    o->z_near = 0.01f;
+    o->lowpass = 0.3f;
+    o->alpha_min = 1.0f / 255.0f;
+    o->alpha_max = 0.99f;
+    o->t_min = 1e-4f;
+    o->q_max = 9.0f;
+    o->guard = 1.3f;
+    o->profile = 0;
+    o->views_per_group = 0;
+}
+
+int dgs_context_create(dgs_ctx** out, const dgs_options* opt) {
+    if (!out) return DGS_ERR_INVALID_ARG;
+    *out = nullptr;
+    dgs_options o;
+    if (opt) o = *opt; else dgs_default_options(&o);
+    std::string why;
+    if (!check_options(&o, why)) return DGS_ERR_INVALID_ARG;
+    dgs_ctx* ctx = new dgs_ctx();
+    ctx->opt = o;
+    cudaGetDevice(&ctx->device);
+    *out = ctx;
+    return DGS_OK;
+}
+
+int dgs_context_destroy(dgs_ctx* ctx) {
+    if (!ctx) return DGS_OK;
+    cudaDeviceSynchronize();
+    DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->records,
+                      &ctx->keys0, &ctx->vals0, &ctx->keys1, &ctx->vals1, &ctx->hist, &ctx->status, &ctx->counters,
+                      &ctx->ranges, &ctx->errword, &ctx->readback};
+    for (DevBuf* b : bufs) free_buf(*b);
+    if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
+    if (ctx->h_read) cudaFreeHost(ctx->h_read);
+    for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+    delete ctx;
+    return DGS_OK;
+}
+
+const char* dgs_last_error(const dgs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int dgs_workspace_query(const dgs_ctx* ctx, size_t* bytes) {
+    if (!ctx || !bytes) return DGS_ERR_INVALID_ARG;
+    const DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->records,
+                            &ctx->keys0, &ctx->vals0, &ctx->keys1, &ctx->vals1, &ctx->hist, &ctx->status,
+                            &ctx->counters, &ctx->ranges, &ctx->errword, &ctx->readback};
+    size_t s = 0;
+    for (const DevBuf* b : bufs) s += b->bytes;
+    *bytes = s;
+    return DGS_OK;
+}
+
+int dgs_last_stats(const dgs_ctx* ctx, dgs_stats* out) {
+    if (!ctx || !out) return DGS_ERR_INVALID_ARG;
+    *out = ctx->stats;
+    return DGS_OK;
+}
+
+int dgs_kernel_times(const dgs_ctx* ctx, float* ms) {
+    if (!ctx || !ms) return DGS_ERR_INVALID_ARG;
+    for (int i = 0; i < DGS_K_COUNT_CLASSES; ++i) ms[i] = ctx->ktimes[i];
+    return DGS_OK;
+}
+
+int64_t dgs_last_launches(const dgs_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids, int32_t n_envs,
+               int32_t max_nodes, const float* node_poses, const dgs_camera* cams, const int32_t* cams_per_env,
+               int32_t max_cams, float* out_rgb, float* out_depth, float* out_alpha,
+               const int64_t* view_pixel_offset, void* stream_) {
+    if (!ctx) return DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    ctx->launches = 0;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    const dgs_options& o = ctx->opt;
+    // ---------------------------------------------------------------- validation (synchronous)
+    if (n_nodes < 1 || !nodes) return fail(ctx, DGS_ERR_INVALID_ARG, "nodes: need n_nodes >= 1 and a node array");
+    if (n_envs < 1 || max_nodes < 1 || max_cams < 1) return fail(ctx, DGS_ERR_INVALID_ARG, "n_envs, max_nodes, max_cams must be >= 1");
+    if (!env_node_ids || !cams || !cams_per_env || !node_poses) return fail(ctx, DGS_ERR_INVALID_ARG, "null table pointer");
+    if (!out_rgb || !out_depth) return fail(ctx, DGS_ERR_INVALID_ARG, "out_rgb and out_depth are required");
+    int64_t total_gauss = 0;
+    for (int k = 0; k < n_nodes; ++k) {
+        const dgs_node& nd = nodes[k];
+        if (nd.n < 0 || nd.sh_degree < 0 || nd.sh_degree > 3 || nd.dtype < 0 || nd.dtype > 2)
+            return fail(ctx, DGS_ERR_INVALID_ARG, "node " + std::to_string(k) + ": bad n, sh_degree or dtype");
+        if (nd.n > 0 && (!nd.mean || !nd.log_scale || !nd.quat || !nd.opacity_logit || !nd.sh))
+            return fail(ctx, DGS_ERR_INVALID_ARG, "node " + std::to_string(k) + ": null attribute pointer");
+        total_gauss += nd.n;
+    }
+    if (total_gauss >= (1ll << 32)) return fail(ctx, DGS_ERR_INVALID_ARG, "more than 2^32 Gaussians");
+    const int E = n_envs, K = max_nodes, C = max_cams;
+    std::vector<int> seen(n_nodes, -1);
+    for (int e = 0; e < E; ++e) {
+        for (int j = 0; j < K; ++j) {
+            const int k = env_node_ids[(int64_t)e * K + j];
+            if (k < -1 || k >= n_nodes) return fail(ctx, DGS_ERR_INVALID_ARG, "env_node_ids out of range");
+            if (k >= 0) {
+                if (seen[k] == e) return fail(ctx, DGS_ERR_INVALID_ARG, "a node appears twice in one env");
+                seen[k] = e;
+            }
+        }
+        if (cams_per_env[e] < 0 || cams_per_env[e] > C) return fail(ctx, DGS_ERR_INVALID_ARG, "cams_per_env out of range");
+    }
+    // views
+    std::vector<ViewDesc> views;
+    std::vector<int> view_env, view_cam;
+    int64_t tiles_total = 0, pix_total = 0;
+    for (int e = 0; e < E; ++e)
+        for (int c = 0; c < cams_per_env[e]; ++c) {
+            const dgs_camera& cm = cams[(int64_t)e * C + c];
+            if (cm.width < 1 || cm.height < 1 || cm.width > 32768 || cm.height > 32768)
+                return fail(ctx, DGS_ERR_INVALID_ARG, "camera resolution");
+            if (!(cm.fx > 0) || !(cm.fy > 0) || !finite(cm.fx) || !finite(cm.fy) || !finite(cm.cx) || !finite(cm.cy))
+                return fail(ctx, DGS_ERR_INVALID_ARG, "camera intrinsics");
+            for (int a = 0; a < 12; ++a)
+                if (!finite(cm.cam_from_world[a])) return fail(ctx, DGS_ERR_INVALID_ARG, "camera pose not finite");
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double s = 0;
+                    for (int r = 0; r < 3; ++r) s += (double)cm.cam_from_world[r * 4 + a] * cm.cam_from_world[r * 4 + b];
+                    if (std::fabs(s - (a == b ? 1.0 : 0.0)) > 1e-4) return fail(ctx, DGS_ERR_INVALID_ARG, "camera rotation not orthonormal");
+                }
+            ViewDesc vd{};
+            vd.fx = cm.fx; vd.fy = cm.fy; vd.cx = cm.cx; vd.cy = cm.cy;
+            vd.limx = o.guard * 0.5f * (float)cm.width / cm.fx;
+            vd.limy = o.guard * 0.5f * (float)cm.height / cm.fy;
+            vd.W = cm.width; vd.H = cm.height;
+            vd.tiles_x = (cm.width + o.tile_w - 1) / o.tile_w;
+            vd.tiles_y = (cm.height + o.tile_h - 1) / o.tile_h;
+            vd.env = e;
+            vd.tile_base = (int32_t)tiles_total;
+            std::memcpy(vd.cam, cm.cam_from_world, sizeof(vd.cam));
+            tiles_total += (int64_t)vd.tiles_x * vd.tiles_y;
+            if (tiles_total >= (1ll << 31)) return fail(ctx, DGS_ERR_INVALID_ARG, "too many tiles");
+            const int64_t v = (int64_t)views.size();
+            vd.pix_off = view_pixel_offset ? view_pixel_offset[v] : pix_total;
+            if (vd.pix_off < 0) return fail(ctx, DGS_ERR_INVALID_ARG, "negative view_pixel_offset");
+            pix_total += (int64_t)cm.width * cm.height;
+            views.push_back(vd);
+            view_env.push_back(e);
+            view_cam.push_back(c);
+        }
+    const int V = (int)views.size();
+    ctx->stats = dgs_stats{};
+    ctx->stats.n_views = V;
+    ctx->stats.n_pixels = pix_total;
+    for (float& t : ctx->ktimes) t = 0.f;
+    ctx->ranges_timed.clear();
+    ctx->next_event = 0;
+    if (V == 0) return DGS_OK;
+
+    // ---------------------------------------------------------------- host tables
+    std::vector<NodeDesc> nd(n_nodes);
+    int dtype_mask = 0;
+    int64_t chunk_total = 0, gbase = 0;
+    for (int k = 0; k < n_nodes; ++k) {
+        nd[k].mean = nodes[k].mean; nd[k].log_scale = nodes[k].log_scale; nd[k].quat = nodes[k].quat;
+        nd[k].opac = nodes[k].opacity_logit; nd[k].sh = nodes[k].sh;
+        nd[k].n = nodes[k].n; nd[k].gbase = gbase; nd[k].deg = nodes[k].sh_degree; nd[k].dtype = nodes[k].dtype;
+        nd[k].chunk0 = (int32_t)chunk_total;
+        nd[k].nchunks = (int32_t)((nodes[k].n + kChunk - 1) / kChunk);
+        chunk_total += nd[k].nchunks;
+        gbase += nodes[k].n;
+        if (nodes[k].n > 0) dtype_mask |= 1 << nodes[k].dtype;
+    }
+    if (chunk_total >= (1ll << 31)) return fail(ctx, DGS_ERR_INVALID_ARG, "too many Gaussians");
+    // count table: per view, the chunks of its nodes in node-id order
+    std::vector<int32_t> slot_node((size_t)V * K, -1);
+    std::vector<int64_t> vnode_tab((size_t)V * K, 0), view_tab(V + 1, 0);
+    std::vector<int32_t> pmap((size_t)V * (2 * K + 1), 0);
+    std::vector<std::vector<NodeView>> per_node(n_nodes);
+    int64_t tab = 0, n_instances = 0;
+    for (int v = 0; v < V; ++v) {
+        const int e = view_env[v];
+        std::vector<std::pair<int, int>> present;   // (node, slot)
+        for (int j = 0; j < K; ++j) {
+            const int k = env_node_ids[(int64_t)e * K + j];
+            slot_node[(size_t)v * K + j] = k;
+            if (k >= 0) present.push_back({k, j});
+        }
+        std::sort(present.begin(), present.end());
+        view_tab[v] = tab;
+        int32_t* pm = &pmap[(size_t)v * (2 * K + 1)];
+        int32_t pre = 0;
+        for (size_t i = 0; i < present.size(); ++i) {
+            const int k = present[i].first, j = present[i].second;
+            vnode_tab[(size_t)v * K + j] = tab;
+            pm[i] = pre;
+            pm[K + 1 + i] = j;
+            pre += nd[k].nchunks;
+            tab += nd[k].nchunks;
+            n_instances += nd[k].n;
+            per_node[k].push_back({v, j});
+        }
+        for (int i = (int)present.size(); i <= K; ++i) pm[i] = pre;
+        for (int i = (int)present.size(); i < K; ++i) pm[K + 1 + i] = present.empty() ? 0 : present[0].second;
+    }
+    view_tab[V] = tab;
+    const int64_t T = tab;
+    std::vector<int32_t> nv_off(n_nodes + 1, 0);
+    std::vector<NodeView> nv;
+    for (int k = 0; k < n_nodes; ++k) {
+        nv_off[k] = (int32_t)nv.size();
+        nv.insert(nv.end(), per_node[k].begin(), per_node[k].end());
+    }
+    nv_off[n_nodes] = (int32_t)nv.size();
+    ctx->stats.n_instances = n_instances;
+
+    // ---------------------------------------------------------------- upload (one copy)
+    size_t off = 0;
+    auto place = [&](size_t bytes) { size_t at = align_up(off, 256); off = at + bytes; return at; };
+    const size_t o_nodes = place(sizeof(NodeDesc) * n_nodes);
+    const size_t o_views = place(sizeof(ViewDesc) * V);
+    const size_t o_slot = place(sizeof(int32_t) * V * K);
+    const size_t o_vtab = place(sizeof(int64_t) * V * K);
+    const size_t o_nv = place(sizeof(NodeView) * std::max<size_t>(1, nv.size()));
+    const size_t o_nvoff = place(sizeof(int32_t) * (n_nodes + 1));
+    const size_t o_pmap = place(sizeof(int32_t) * pmap.size());
+    const size_t o_viewtab = place(sizeof(int64_t) * (V + 1));
+    const size_t upload_bytes = off;
+    const size_t o_vnodes = place(sizeof(VNode) * V * K);
+    const size_t meta_bytes = off;
+    int rc;
+    if ((rc = ensure(ctx, ctx->meta, meta_bytes))) return rc;
+    if ((rc = ensure_host(ctx, ctx->h_meta, ctx->h_meta_bytes, upload_bytes))) return rc;
+    // the previous call's upload may still be in flight from this staging buffer
+    DGS_CUDA(ctx, cudaStreamSynchronize(stream));
+    char* hm = static_cast<char*>(ctx->h_meta);
+    std::memcpy(hm + o_nodes, nd.data(), sizeof(NodeDesc) * n_nodes);
+    std::memcpy(hm + o_views, views.data(), sizeof(ViewDesc) * V);
+    std::memcpy(hm + o_slot, slot_node.data(), sizeof(int32_t) * V * K);
+    std::memcpy(hm + o_vtab, vnode_tab.data(), sizeof(int64_t) * V * K);
+    if (!nv.empty()) std::memcpy(hm + o_nv, nv.data(), sizeof(NodeView) * nv.size());
+    std::memcpy(hm + o_nvoff, nv_off.data(), sizeof(int32_t) * (n_nodes + 1));
+    std::memcpy(hm + o_pmap, pmap.data(), sizeof(int32_t) * pmap.size());
+    std::memcpy(hm + o_viewtab, view_tab.data(), sizeof(int64_t) * (V + 1));
+    char* dm = static_cast<char*>(ctx->meta.p);
+    const NodeDesc* d_nodes = reinterpret_cast<const NodeDesc*>(dm + o_nodes);
+    const ViewDesc* d_views = reinterpret_cast<const ViewDesc*>(dm + o_views);
+    const int32_t* d_slot = reinterpret_cast<const int32_t*>(dm + o_slot);
+    const int64_t* d_vtab = reinterpret_cast<const int64_t*>(dm + o_vtab);
+    const NodeView* d_nv = reinterpret_cast<const NodeView*>(dm + o_nv);
+    const int32_t* d_nvoff = reinterpret_cast<const int32_t*>(dm + o_nvoff);
+    const int32_t* d_pmap = reinterpret_cast<const int32_t*>(dm + o_pmap);
+    const int64_t* d_viewtab = reinterpret_cast<const int64_t*>(dm + o_viewtab);
+    VNode* d_vnodes = reinterpret_cast<VNode*>(dm + o_vnodes);
+
+    if ((rc = ensure(ctx, ctx->errword, 64))) return rc;
+    if ((rc = ensure(ctx, ctx->counts, sizeof(uint2) * std::max<int64_t>(T, 1)))) return rc;
+    if ((rc = ensure(ctx, ctx->inst_off, sizeof(uint32_t) * (T + 1)))) return rc;
+    if ((rc = ensure(ctx, ctx->pair_off, sizeof(uint64_t) * (T + 1)))) return rc;
+    const int64_t n_parts = (T + 4095) / 4096;
+    if ((rc = ensure(ctx, ctx->parts, sizeof(ulonglong2) * (n_parts + 1)))) return rc;
+    if ((rc = ensure(ctx, ctx->readback, sizeof(uint64_t) * 2 * (V + 1) + 64))) return rc;
+    if ((rc = ensure_host(ctx, ctx->h_read, ctx->h_read_bytes, sizeof(uint64_t) * 2 * (V + 1) + 64))) return rc;
+    uint32_t* d_err = static_cast<uint32_t*>(ctx->errword.p);
+
+    DGS_CUDA(ctx, cudaMemcpyAsync(dm, hm, upload_bytes, cudaMemcpyHostToDevice, stream));
+    DGS_CUDA(ctx, cudaMemsetAsync(d_err, 0, 64, stream));
+
+    Params P{};
+    P.z_near = o.z_near; P.lowpass = o.lowpass; P.alpha_min = o.alpha_min; P.alpha_max = o.alpha_max;
+    P.t_min = o.t_min; P.q_max = o.q_max; P.guard = o.guard;
+    P.bg0 = o.bg[0]; P.bg1 = o.bg[1]; P.bg2 = o.bg[2];
+    P.qbin = o.q_max * 1.001f + 1e-3f;
+    P.tile_w = o.tile_w; P.tile_h = o.tile_h;
+    P.exact_tile_test = o.exact_tile_test;
+    P.tile0 = 0;
+    P.err = nullptr;
+    {
+        uint32_t b;
+        std::memcpy(&b, &o.z_near, 4);
+        P.zbase = b & 0x7F800000u;   // 2^floor(log2 z_near)
+    }
+    P.err = d_err;
+    const bool batched = o.mode == DGS_MODE_BATCHED;
+    Launch L{stream, &ctx->launches};
+    Timer tm{ctx, stream, o.profile != 0};
+
+    tm.begin(DGS_K_SETUP);
+    launch_setup_views(L, d_views, V, node_poses, d_slot, K, d_vnodes, d_vtab, d_err);
+    tm.end();
+    uint2* d_counts = static_cast<uint2*>(ctx->counts.p);
+    uint32_t* d_inst_off = static_cast<uint32_t*>(ctx->inst_off.p);
+    uint64_t* d_pair_off = static_cast<uint64_t*>(ctx->pair_off.p);
+    tm.begin(DGS_K_COUNT);
+    if (batched) {
+        launch_count(L, dtype_mask, d_nodes, n_nodes, d_views, d_vnodes, K, d_nv, d_nvoff, (int)chunk_total, P, 0, V,
+                     true, nullptr, 0, d_counts);
+    } else {
+        for (int v = 0; v < V; ++v)
+            launch_count(L, dtype_mask, d_nodes, n_nodes, d_views, d_vnodes, K, d_nv, d_nvoff, (int)chunk_total, P, v,
+                         v + 1, false, d_pmap + (size_t)v * (2 * K + 1), view_tab[v + 1] - view_tab[v], d_counts);
+    }
+    tm.end();
+    tm.begin(DGS_K_SCAN);
+    launch_scan(L, d_counts, T, d_inst_off, d_pair_off, static_cast<ulonglong2*>(ctx->parts.p), n_parts + 1);
+    {
+        uint64_t* d_rb = static_cast<uint64_t*>(ctx->readback.p);
+        k_view_totals<<<(V + 1 + 127) / 128, 128, 0, stream>>>(d_inst_off, d_pair_off, d_viewtab, V + 1, d_rb);
+        ++ctx->launches;
+        DGS_CUDA(ctx, cudaMemcpyAsync(d_rb + 2 * (V + 1), d_err, sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream));
+        DGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_read, d_rb, sizeof(uint64_t) * 2 * (V + 1) + 8, cudaMemcpyDeviceToHost, stream));
+    }
+    tm.end();
+    DGS_CUDA(ctx, cudaGetLastError());
+    DGS_CUDA(ctx, cudaStreamSynchronize(stream));
+    const uint64_t* h_rb = static_cast<const uint64_t*>(ctx->h_read);
+    const uint64_t* inst_at = h_rb;
+    const uint64_t* pair_at = h_rb + (V + 1);
+    uint32_t errw = (uint32_t)(h_rb[2 * (V + 1)] & 0xFFFFFFFFu);
+    if (errw & kErrPose) return fail(ctx, DGS_ERR_INVALID_ARG, "a node pose is not finite or not rigid");
+    ctx->stats.n_visible = (int64_t)inst_at[V];
+    ctx->stats.n_pairs = (int64_t)pair_at[V];
+    if (inst_at[V] >= (1ull << 32)) return fail(ctx, DGS_ERR_CAPACITY, "more than 2^32 visible instances");
+
+    // ---------------------------------------------------------------- groups
+    std::vector<std::pair<int, int>> groups;
+    if (!batched) {
+        for (int v = 0; v < V; ++v) groups.push_back({v, v + 1});
+    } else {
+        int v0 = 0;
+        const int cap_views = o.views_per_group > 0 ? o.views_per_group : V;
+        for (int v = 0; v < V; ++v) {
+            if (pair_at[v + 1] - pair_at[v] > kMaxPairs)
+                return fail(ctx, DGS_ERR_CAPACITY, "one view has more than 2^30 tile pairs");
+            if (v > v0 && (pair_at[v + 1] - pair_at[v0] > kMaxPairs || v - v0 >= cap_views)) {
+                groups.push_back({v0, v});
+                v0 = v;
+            }
+        }
+        groups.push_back({v0, V});
+    }
+    uint64_t max_inst = 1, max_pairs = 1;
+    int64_t max_tiles = 1;
+    int max_bits = 0;
+    for (auto& g : groups) {
+        max_inst = std::max<uint64_t>(max_inst, inst_at[g.second] - inst_at[g.first]);
+        max_pairs = std::max<uint64_t>(max_pairs, pair_at[g.second] - pair_at[g.first]);
+        const int64_t t0 = views[g.first].tile_base;
+        const int64_t t1 = g.second < V ? views[g.second].tile_base : tiles_total;
+        max_tiles = std::max<int64_t>(max_tiles, t1 - t0);
+        if (pair_at[g.second] - pair_at[g.first] > kMaxPairs)
+            return fail(ctx, DGS_ERR_CAPACITY, "view group exceeds 2^30 tile pairs");
+    }
+    max_bits = kZBits + std::max(1, bits_for((uint64_t)max_tiles));
+    if (max_bits > 64) return fail(ctx, DGS_ERR_CAPACITY, "sort key wider than 64 bits");
+    ctx->stats.n_groups = (int32_t)groups.size();
+    ctx->stats.key_bits = max_bits;
+    if ((rc = ensure(ctx, ctx->records, sizeof(Record) * max_inst))) return rc;
+    if ((rc = ensure(ctx, ctx->keys0, sizeof(uint64_t) * max_pairs))) return rc;
+    if ((rc = ensure(ctx, ctx->keys1, sizeof(uint64_t) * max_pairs))) return rc;
+    if ((rc = ensure(ctx, ctx->vals0, sizeof(uint32_t) * max_pairs))) return rc;
+    if ((rc = ensure(ctx, ctx->vals1, sizeof(uint32_t) * max_pairs))) return rc;
+    if ((rc = ensure(ctx, ctx->hist, sizeof(uint32_t) * 256 * 8))) return rc;
+    if ((rc = ensure(ctx, ctx->counters, sizeof(uint32_t) * 8))) return rc;
+    if ((rc = ensure(ctx, ctx->status, sizeof(uint32_t) * sort_status_words((uint32_t)max_pairs)))) return rc;
+    if ((rc = ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)max_tiles))) return rc;
+    Record* d_rec = static_cast<Record*>(ctx->records.p);
+
+    for (auto& g : groups) {
+        const int v0 = g.first, v1 = g.second;
+        const uint32_t n_pairs = (uint32_t)(pair_at[v1] - pair_at[v0]);
+        const int32_t tile0 = views[v0].tile_base;
+        const int n_tiles = (int)((v1 < V ? views[v1].tile_base : tiles_total) - tile0);
+        Params Pg = P;
+        Pg.tile0 = tile0;
+        tm.begin(DGS_K_EMIT);
+        launch_emit(L, dtype_mask, d_nodes, n_nodes, d_views, d_vnodes, K, d_nv, d_nvoff, (int)chunk_total, Pg, v0, v1,
+                    batched, d_pmap + (size_t)v0 * (2 * K + 1), view_tab[v0 + 1] - view_tab[v0], d_inst_off, d_pair_off,
+                    (uint32_t)inst_at[v0], pair_at[v0], d_rec, static_cast<uint64_t*>(ctx->keys0.p),
+                    static_cast<uint32_t*>(ctx->vals0.p));
+        tm.end();
+        tm.begin(DGS_K_SORT);
+        uint64_t* skeys;
+        uint32_t* svals;
+        const int bits = kZBits + std::max(1, bits_for((uint64_t)n_tiles));
+        launch_sort(L, static_cast<uint64_t*>(ctx->keys0.p), static_cast<uint32_t*>(ctx->vals0.p),
+                    static_cast<uint64_t*>(ctx->keys1.p), static_cast<uint32_t*>(ctx->vals1.p), n_pairs, bits,
+                    static_cast<uint32_t*>(ctx->hist.p), static_cast<uint32_t*>(ctx->status.p),
+                    static_cast<uint32_t*>(ctx->counters.p), d_err, &skeys, &svals, nullptr, nullptr);
+        tm.end();
+        tm.begin(DGS_K_RANGES);
+        launch_ranges(L, skeys, n_pairs, static_cast<uint2*>(ctx->ranges.p), n_tiles);
+        tm.end();
+        tm.begin(DGS_K_COMPOSITE);
+        launch_composite(L, d_views, v0, v1 - v0, n_tiles, static_cast<uint2*>(ctx->ranges.p), svals, d_rec, Pg,
+                         out_rgb, out_depth, out_alpha);
+        tm.end();
+        DGS_CUDA(ctx, cudaGetLastError());
+    }
+    uint32_t* h_err = reinterpret_cast<uint32_t*>(static_cast<char*>(ctx->h_read) + sizeof(uint64_t) * 2 * (V + 1));
+    DGS_CUDA(ctx, cudaMemcpyAsync(h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+    DGS_CUDA(ctx, cudaStreamSynchronize(stream));
+    errw = *h_err;
+    if (o.profile) {
+        for (const TimedRange& r : ctx->ranges_timed) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) ctx->ktimes[r.cls] += ms;
+        }
+    }
+    if (errw & kErrTimeout) return fail(ctx, DGS_ERR_TIMEOUT, "a bounded device wait timed out (sort look-back)");
+    if (errw & kErrMismatch) return fail(ctx, DGS_ERR_CUDA, "internal: count and emit passes disagree");
+    if (errw & kErrPose) return fail(ctx, DGS_ERR_INVALID_ARG, "a node pose is not finite or not rigid");
+    return DGS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,132 @@
+// Internal device structures and helpers of libdgs (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "dgs.h"
+
+namespace dgs {
+
+constexpr int kWarp = 32;
+constexpr int kChunk = 32;           // Gaussians per chunk: one warp projects one chunk
+constexpr int kZBits = 28;           // bits of the depth field of a sort key
+constexpr uint32_t kMaxPairs = (1u << 30) - 1;   // per view group (30-bit scan counters)
+
+// Device error word bits (ctx status).
+constexpr uint32_t kErrPose = 1u;       // non-finite or non-rigid node pose
+constexpr uint32_t kErrTimeout = 2u;    // a bounded spin gave up
+constexpr uint32_t kErrCapacity = 4u;   // a count exceeded its buffer
+constexpr uint32_t kErrMismatch = 8u;   // count and emit passes disagreed on a chunk
+
+struct NodeDesc {
+    const float* mean;
+    const void* log_scale;
+    const void* quat;
+    const float* opac;
+    const void* sh;
+    int64_t n;
+    int64_t gbase;        // global id of the node's first Gaussian
+    int32_t deg;
+    int32_t dtype;
+    int32_t chunk0;       // first chunk of the node in the node-major chunk numbering
+    int32_t nchunks;
+};
+
+struct ViewDesc {
+    float fx, fy, cx, cy;
+    float limx, limy;     // Jacobian clamp of tx/tz and ty/tz
+    int32_t W, H;
+    int32_t tiles_x, tiles_y;
+    int32_t env;
+    int32_t tile_base;    // first global tile of the view within its group
+    int64_t pix_off;      // first output pixel
+    float cam[12];        // cam_from_world
+};
+
+// Per (view, slot): the node and its camera_from_node transform.
+struct VNode {
+    float M[12];          // camera_from_node; row 2 composed in binary32 without FMA
+    float o[3];           // camera centre in the node frame
+    int32_t node;         // -1 = empty slot
+    int64_t tab;          // count-table index of the node's first chunk in this view
+};
+
+struct Params {
+    float z_near, lowpass, alpha_min, alpha_max, t_min, q_max, guard;
+    float bg0, bg1, bg2;
+    float qbin;           // binning limit on d^T conic d (q_max with an FP32 safety margin)
+    int32_t tile_w, tile_h;
+    int32_t exact_tile_test;
+    uint32_t zbase;       // float bits of 2^floor(log2 z_near)
+    int32_t tile0;        // first global tile of the current view group
+    uint32_t* err;        // device error word
+};
+
+// Projected instance as stored for compositing: 48 bytes.
+//   r0 = (u, v, opacity, z), r1 = (conic a, b, c, gid bits), r2 = (r, g, b, view bits)
+struct Record {
+    float4 r0, r1, r2;
+};
+
+// (view, slot) entries of node k: node_views[node_view_off[k] .. node_view_off[k+1])
+struct NodeView {
+    int32_t view;
+    int32_t slot;
+};
+
+template <int DT>
+__device__ __forceinline__ float ld_attr(const void* p, int64_t i) {
+    if constexpr (DT == DGS_F32) return __ldg(reinterpret_cast<const float*>(p) + i);
+    else if constexpr (DT == DGS_BF16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[i]);
+    else return __half2float(reinterpret_cast<const __half*>(p)[i]);
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ------------------------------------------------------------------ launchers (host side)
+struct Launch {
+    cudaStream_t stream;
+    int64_t* launches;    // incremented per kernel launch
+};
+
+void launch_setup_views(const Launch& L, const ViewDesc* views, int n_views, const float* node_poses,
+                        const int32_t* view_slots_node, int K, VNode* vnodes, const int64_t* vnode_tab,
+                        uint32_t* err);
+
+void launch_count(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_nodes, const ViewDesc* views,
+                  const VNode* vnodes, int K, const NodeView* node_views, const int32_t* node_view_off,
+                  int n_chunks_total, const Params& P, int v0, int v1, bool batched, const int32_t* view_chunk_nodes,
+                  int64_t view_chunks, uint2* counts);
+
+void launch_scan(const Launch& L, const uint2* counts, int64_t n, uint32_t* inst_off, uint64_t* pair_off,
+                 ulonglong2* parts, int64_t n_parts_cap);
+
+void launch_emit(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_nodes, const ViewDesc* views,
+                 const VNode* vnodes, int K, const NodeView* node_views, const int32_t* node_view_off,
+                 int n_chunks_total, const Params& P, int v0, int v1, bool batched, const int32_t* view_chunk_nodes,
+                 int64_t view_chunks, const uint32_t* inst_off, const uint64_t* pair_off, uint32_t inst_base,
+                 uint64_t pair_base, Record* records, uint64_t* keys, uint32_t* vals);
+
+void launch_sort(const Launch& L, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                 uint32_t n, int key_bits, uint32_t* hist, uint32_t* status, uint32_t* counters, uint32_t* err,
+                 uint64_t** keys_out, uint32_t** vals_out, float* sort_ms_slot, cudaEvent_t* evs);
+
+void launch_ranges(const Launch& L, const uint64_t* keys, uint32_t n, uint2* ranges, int n_tiles);
+
+void launch_composite(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
+                      const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,
+                      float* out_rgb, float* out_depth, float* out_alpha);
+
+size_t sort_status_words(uint32_t n);
+int sort_passes(int key_bits);
+
+}  // namespace dgs

@@ -1,0 +1,599 @@
+// Projection and tile binning (kernels K1 and K2 of the renderer).
+//
+// Sec. III-A ("Renderer"): the native 3DGS pipeline splats every Gaussian by EWA projection
+// of its 3D covariance, evaluates its spherical-harmonics colour and bins it to the screen
+// tiles it overlaps before depth sorting.  Sec. III-B: interactive nodes carry their own
+// rigid pose, so every Gaussian is first moved by its node's world_from_node transform; here
+// node pose and camera are composed once per (view, slot) into camera_from_node.
+//
+// Work decomposition: a warp owns a chunk of 32 consecutive Gaussians of one node.  The
+// count pass projects the chunk (no colour) and writes, per (view, chunk), the number of
+// visible instances and of (instance, tile) pairs.  After an exclusive scan of that table the
+// emit pass projects again, evaluates colour and writes the instance records and sort pairs
+// at their scanned offsets.  The order is therefore deterministic: within a view, instances
+// and pairs follow the global id, which makes a stable radix sort break depth ties by id.
+// Batched mode: a warp loads its Gaussians' attributes once and loops over every view that
+// contains the node.  Plain mode: one launch per view, attributes read again for every view.
+#include <math.h>
+
+#include "dgs_internal.cuh"
+
+namespace dgs {
+namespace {
+
+// ------------------------------------------------------------------ setup: camera_from_node
+// One thread per (view, slot).  Row 2 of camera_from_node is composed in binary32 with one
+// rounding per multiply and per add (no FMA), in the order of the depth-key definition.
+__global__ void k_setup_views(const ViewDesc* __restrict__ views, int n_views, const float* __restrict__ poses,
+                              const int32_t* __restrict__ slot_node, int K, VNode* __restrict__ vnodes,
+                              const int64_t* __restrict__ vnode_tab, uint32_t* err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_views * K) return;
+    const int v = i / K, j = i % K;
+    const ViewDesc& vd = views[v];
+    VNode out;
+    out.node = slot_node[i];
+    out.tab = vnode_tab[i];
+    const float* P = poses + ((int64_t)vd.env * K + j) * 12;
+    float R[9], t[3];
+    bool bad = false;
+    if (out.node >= 0) {
+        for (int a = 0; a < 3; ++a) {
+            for (int b = 0; b < 3; ++b) R[a * 3 + b] = P[a * 4 + b];
+            t[a] = P[a * 4 + 3];
+        }
+        for (int a = 0; a < 12; ++a) bad |= !isfinite(P[a]);
+        // rigidity: R^T R = I within 1e-4
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                float s = R[0 * 3 + a] * R[0 * 3 + b] + R[1 * 3 + a] * R[1 * 3 + b] + R[2 * 3 + a] * R[2 * 3 + b];
+                bad |= fabsf(s - (a == b ? 1.f : 0.f)) > 1e-4f;
+            }
+    } else {
+        for (int a = 0; a < 9; ++a) R[a] = (a % 4 == 0) ? 1.f : 0.f;
+        t[0] = t[1] = t[2] = 0.f;
+    }
+    if (bad) atomicOr(err, kErrPose);
+    const float* W = vd.cam;   // rows of [Wc | tc]
+    for (int a = 0; a < 3; ++a) {
+        for (int b = 0; b < 3; ++b) {
+            const float x = __fmul_rn(W[a * 4 + 0], R[0 * 3 + b]);
+            const float y = __fmul_rn(W[a * 4 + 1], R[1 * 3 + b]);
+            const float z = __fmul_rn(W[a * 4 + 2], R[2 * 3 + b]);
+            out.M[a * 4 + b] = __fadd_rn(__fadd_rn(x, y), z);
+        }
+        const float x = __fmul_rn(W[a * 4 + 0], t[0]);
+        const float y = __fmul_rn(W[a * 4 + 1], t[1]);
+        const float z = __fmul_rn(W[a * 4 + 2], t[2]);
+        out.M[a * 4 + 3] = __fadd_rn(__fadd_rn(__fadd_rn(x, y), z), W[a * 4 + 3]);
+    }
+    // camera centre in the node frame: o = -M_R^T M_t
+    for (int b = 0; b < 3; ++b)
+        out.o[b] = -(out.M[0 * 4 + b] * out.M[3] + out.M[1 * 4 + b] * out.M[7] + out.M[2 * 4 + b] * out.M[11]);
+    vnodes[i] = out;
+}
+
+// ------------------------------------------------------------------ per-Gaussian geometry
+struct Gauss {
+    float mx, my, mz;
+    float s00, s01, s02, s11, s12, s22;   // node-frame 3D covariance
+    float opac;
+};
+
+template <int DT>
+__device__ __forceinline__ void load_geometry(const NodeDesc& nd, int64_t i, Gauss& g) {
+    g.mx = __ldg(nd.mean + i * 3 + 0);
+    g.my = __ldg(nd.mean + i * 3 + 1);
+    g.mz = __ldg(nd.mean + i * 3 + 2);
+    const float sx = __expf(2.f * ld_attr<DT>(nd.log_scale, i * 3 + 0));
+    const float sy = __expf(2.f * ld_attr<DT>(nd.log_scale, i * 3 + 1));
+    const float sz = __expf(2.f * ld_attr<DT>(nd.log_scale, i * 3 + 2));
+    float w = ld_attr<DT>(nd.quat, i * 4 + 0), x = ld_attr<DT>(nd.quat, i * 4 + 1);
+    float y = ld_attr<DT>(nd.quat, i * 4 + 2), z = ld_attr<DT>(nd.quat, i * 4 + 3);
+    const float inv = rsqrtf(w * w + x * x + y * y + z * z);
+    w *= inv; x *= inv; y *= inv; z *= inv;
+    // rotation matrix of the unit quaternion (w,x,y,z)
+    const float r00 = 1.f - 2.f * (y * y + z * z), r01 = 2.f * (x * y - w * z), r02 = 2.f * (x * z + w * y);
+    const float r10 = 2.f * (x * y + w * z), r11 = 1.f - 2.f * (x * x + z * z), r12 = 2.f * (y * z - w * x);
+    const float r20 = 2.f * (x * z - w * y), r21 = 2.f * (y * z + w * x), r22 = 1.f - 2.f * (x * x + y * y);
+    // Sigma = R diag(s^2) R^T
+    g.s00 = r00 * r00 * sx + r01 * r01 * sy + r02 * r02 * sz;
+    g.s01 = r00 * r10 * sx + r01 * r11 * sy + r02 * r12 * sz;
+    g.s02 = r00 * r20 * sx + r01 * r21 * sy + r02 * r22 * sz;
+    g.s11 = r10 * r10 * sx + r11 * r11 * sy + r12 * r12 * sz;
+    g.s12 = r10 * r20 * sx + r11 * r21 * sy + r12 * r22 * sz;
+    g.s22 = r20 * r20 * sx + r21 * r21 * sy + r22 * r22 * sz;
+}
+
+struct Splat {
+    float u, v, z;
+    float a, b, c;        // conic (inverse 2D covariance)
+    int tx0, tx1, ty0, ty1;
+    int x0, x1, y0, y1;   // pixel bounds of the ellipse box, clamped to the image
+};
+
+// EWA projection of one Gaussian into one view.  Returns false if culled (near plane,
+// degenerate covariance or off screen).
+__device__ __forceinline__ bool project(const Gauss& g, const VNode& vn, const ViewDesc& vd, const Params& P, Splat& s) {
+    const float* M = vn.M;
+    // depth key: binary32, one rounding per operation, fixed order
+    const float z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[8], g.mx), __fmul_rn(M[9], g.my)), __fmul_rn(M[10], g.mz)), M[11]);
+    if (!(z > P.z_near)) return false;
+    const float tx = fmaf(M[0], g.mx, fmaf(M[1], g.my, fmaf(M[2], g.mz, M[3])));
+    const float ty = fmaf(M[4], g.mx, fmaf(M[5], g.my, fmaf(M[6], g.mz, M[7])));
+    const float iz = 1.f / z;
+    const float xr = tx * iz, yr = ty * iz;
+    const float xc = fminf(vd.limx, fmaxf(-vd.limx, xr));
+    const float yc = fminf(vd.limy, fmaxf(-vd.limy, yr));
+    // rows of T = J * M_R:  T0 = fx/z (M_R row0 - xc * M_R row2),  T1 = fy/z (M_R row1 - yc * M_R row2)
+    const float fxz = vd.fx * iz, fyz = vd.fy * iz;
+    const float t00 = fxz * fmaf(-xc, M[8], M[0]), t01 = fxz * fmaf(-xc, M[9], M[1]), t02 = fxz * fmaf(-xc, M[10], M[2]);
+    const float t10 = fyz * fmaf(-yc, M[8], M[4]), t11 = fyz * fmaf(-yc, M[9], M[5]), t12 = fyz * fmaf(-yc, M[10], M[6]);
+    // Sigma * T0, Sigma * T1
+    const float a0 = g.s00 * t00 + g.s01 * t01 + g.s02 * t02;
+    const float a1 = g.s01 * t00 + g.s11 * t01 + g.s12 * t02;
+    const float a2 = g.s02 * t00 + g.s12 * t01 + g.s22 * t02;
+    const float b0 = g.s00 * t10 + g.s01 * t11 + g.s02 * t12;
+    const float b1 = g.s01 * t10 + g.s11 * t11 + g.s12 * t12;
+    const float b2 = g.s02 * t10 + g.s12 * t11 + g.s22 * t12;
+    const float cxx = t00 * a0 + t01 * a1 + t02 * a2 + P.lowpass;
+    const float cxy = t10 * a0 + t11 * a1 + t12 * a2;
+    const float cyy = t10 * b0 + t11 * b1 + t12 * b2 + P.lowpass;
+    const float det = cxx * cyy - cxy * cxy;
+    if (!(det > 0.f)) return false;
+    const float idet = 1.f / det;
+    s.a = cyy * idet;
+    s.b = -cxy * idet;
+    s.c = cxx * idet;
+    s.u = fmaf(vd.fx, xr, vd.cx);
+    s.v = fmaf(vd.fy, yr, vd.cy);
+    s.z = z;
+    // box of {d : d^T conic d <= qbin}: half extents sqrt(qbin * Sigma_ii); pixel centres x + 1/2
+    const float hx = sqrtf(P.qbin * cxx), hy = sqrtf(P.qbin * cyy);
+    const float fx0 = ceilf(s.u - hx - 0.5f), fx1 = floorf(s.u + hx - 0.5f);
+    const float fy0 = ceilf(s.v - hy - 0.5f), fy1 = floorf(s.v + hy - 0.5f);
+    if (!(fx1 >= 0.f && fy1 >= 0.f && fx0 <= (float)(vd.W - 1) && fy0 <= (float)(vd.H - 1) && fx0 <= fx1 && fy0 <= fy1))
+        return false;
+    s.x0 = (int)fmaxf(fx0, 0.f);
+    s.x1 = (int)fminf(fx1, (float)(vd.W - 1));
+    s.y0 = (int)fmaxf(fy0, 0.f);
+    s.y1 = (int)fminf(fy1, (float)(vd.H - 1));
+    s.tx0 = s.x0 / P.tile_w; s.tx1 = s.x1 / P.tile_w;
+    s.ty0 = s.y0 / P.tile_h; s.ty1 = s.y1 / P.tile_h;
+    return true;
+}
+
+// Does the ellipse {d^T conic d <= qlim} reach a pixel centre of the rectangle
+// [X0,X1] x [Y0,Y1] (coordinates relative to the mean)?  Minimum of the convex quadratic over
+// the rectangle: 0 if the mean is inside, else the smallest of the four edge minima.
+__device__ __forceinline__ bool ellipse_meets_rect(float a, float b, float c, float qlim, float X0, float X1, float Y0, float Y1) {
+    if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return true;
+    float m = INFINITY;
+    const float ia = 1.f / a, ic = 1.f / c;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float X = e ? X1 : X0;
+        const float Y = fminf(Y1, fmaxf(Y0, -b * X * ic));
+        m = fminf(m, fmaf(a * X, X, fmaf(2.f * b * X, Y, c * Y * Y)));
+        const float Yh = e ? Y1 : Y0;
+        const float Xh = fminf(X1, fmaxf(X0, -b * Yh * ia));
+        m = fminf(m, fmaf(a * Xh, Xh, fmaf(2.f * b * Xh, Yh, c * Yh * Yh)));
+    }
+    return m <= qlim;
+}
+
+__device__ __forceinline__ bool tile_hit(const Splat& s, const ViewDesc& vd, const Params& P, int tx, int ty) {
+    if (!P.exact_tile_test) return true;
+    const int px0 = max(tx * P.tile_w, s.x0), px1 = min(tx * P.tile_w + P.tile_w - 1, s.x1);
+    const int py0 = max(ty * P.tile_h, s.y0), py1 = min(ty * P.tile_h + P.tile_h - 1, s.y1);
+    return ellipse_meets_rect(s.a, s.b, s.c, P.qbin, (float)px0 + 0.5f - s.u, (float)px1 + 0.5f - s.u,
+                              (float)py0 + 0.5f - s.v, (float)py1 + 0.5f - s.v);
+}
+
+__device__ __forceinline__ uint32_t count_tiles(const Splat& s, const ViewDesc& vd, const Params& P) {
+    if (!P.exact_tile_test) return (uint32_t)((s.tx1 - s.tx0 + 1) * (s.ty1 - s.ty0 + 1));
+    uint32_t n = 0;
+    for (int ty = s.ty0; ty <= s.ty1; ++ty)
+        for (int tx = s.tx0; tx <= s.tx1; ++tx) n += tile_hit(s, vd, P, tx, ty);
+    return n;
+}
+
+// ------------------------------------------------------------------ spherical harmonics colour
+// Real SH, Condon-Shortley phase, k = l^2 + l + m, for a unit direction (x, y, z):
+//   l0: 1/(2 sqrt(pi));  l1: sqrt(3/(4pi)) (-y, z, -x);
+//   l2: c2a xy, -c2a yz, c2b (3z^2-1), -c2a xz, c2c (x^2-y^2)
+//   l3: -c3a y(3x^2-y^2), c3b xyz, -c3c y(5z^2-1), c3d z(5z^2-3), -c3c x(5z^2-1), c3e z(x^2-y^2),
+//       -c3a x(x^2-3y^2)
+// with c2a = sqrt(15/(4pi)), c2b = sqrt(5/(16pi)), c2c = sqrt(15/(16pi)), c3a = sqrt(35/(32pi)),
+// c3b = sqrt(105/(4pi)), c3c = sqrt(21/(32pi)), c3d = sqrt(7/(16pi)), c3e = sqrt(105/(16pi)).
+constexpr float kY00 = 0.28209479177387814f;
+constexpr float kC1 = 0.4886025119029199f;
+constexpr float kC2a = 1.0925484305920792f, kC2b = 0.31539156525252005f, kC2c = 0.5462742152960396f;
+constexpr float kC3a = 0.5900435899266435f, kC3b = 2.890611442640554f, kC3c = 0.4570457994644658f;
+constexpr float kC3d = 0.3731763325901154f, kC3e = 1.445305721320277f;
+
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float Y[16]) {
+    Y[0] = kY00;
+    if (deg < 1) return;
+    Y[1] = -kC1 * y; Y[2] = kC1 * z; Y[3] = -kC1 * x;
+    if (deg < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = kC2a * x * y; Y[5] = -kC2a * y * z; Y[6] = kC2b * (3.f * zz - 1.f); Y[7] = -kC2a * x * z;
+    Y[8] = kC2c * (xx - yy);
+    if (deg < 3) return;
+    Y[9] = -kC3a * y * (3.f * xx - yy);
+    Y[10] = kC3b * x * y * z;
+    Y[11] = -kC3c * y * (5.f * zz - 1.f);
+    Y[12] = kC3d * z * (5.f * zz - 3.f);
+    Y[13] = -kC3c * x * (5.f * zz - 1.f);
+    Y[14] = kC3e * z * (xx - yy);
+    Y[15] = -kC3a * x * (xx - 3.f * yy);
+}
+
+template <int DT>
+__device__ __forceinline__ void sh_colour(const NodeDesc& nd, int64_t i, const Gauss& g, const VNode& vn, float rgb[3]) {
+    float dx = g.mx - vn.o[0], dy = g.my - vn.o[1], dz = g.mz - vn.o[2];
+    const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= inv; dy *= inv; dz *= inv;
+    float Y[16];
+    sh_basis(nd.deg, dx, dy, dz, Y);
+    const int nc = (nd.deg + 1) * (nd.deg + 1);
+    float r = 0.5f, gg = 0.5f, b = 0.5f;
+    const int64_t base = i * nc * 3;
+    for (int k = 0; k < nc; ++k) {
+        r = fmaf(Y[k], ld_attr<DT>(nd.sh, base + k * 3 + 0), r);
+        gg = fmaf(Y[k], ld_attr<DT>(nd.sh, base + k * 3 + 1), gg);
+        b = fmaf(Y[k], ld_attr<DT>(nd.sh, base + k * 3 + 2), b);
+    }
+    rgb[0] = fmaxf(r, 0.f); rgb[1] = fmaxf(gg, 0.f); rgb[2] = fmaxf(b, 0.f);
+}
+
+__device__ __forceinline__ int find_node(const NodeDesc* nodes, int n_nodes, int chunk) {
+    int lo = 0, hi = n_nodes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (nodes[mid].chunk0 <= chunk) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x) {
+    const uint32_t lane = lane_id();
+    uint32_t s = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= (uint32_t)o) s += y;
+    }
+    return s - x;
+}
+
+// ------------------------------------------------------------------ count pass
+template <int DT>
+__device__ __forceinline__ void count_chunk(const NodeDesc& nd, int c, int lane, const VNode& vn, const ViewDesc& vd,
+                                            const Params& P, const Gauss& g, bool valid, uint2* counts) {
+    uint32_t nt = 0;
+    if (valid) {
+        Splat s;
+        if (project(g, vn, vd, P, s)) nt = count_tiles(s, vd, P);
+    }
+    const uint32_t vis = __reduce_add_sync(0xffffffffu, nt > 0 ? 1u : 0u);
+    const uint32_t pairs = __reduce_add_sync(0xffffffffu, nt);
+    if (lane == 0) counts[vn.tab + c] = make_uint2(vis, pairs);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) k_count_batched(const NodeDesc* __restrict__ nodes, int n_nodes,
+        const ViewDesc* __restrict__ views, const VNode* __restrict__ vnodes, int K, const NodeView* __restrict__ nv,
+        const int32_t* __restrict__ nv_off, int n_chunks, Params P, int v0, int v1, uint2* counts) {
+    const int chunk = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (chunk >= n_chunks) return;
+    const int lane = (int)lane_id();
+    const int k = find_node(nodes, n_nodes, chunk);
+    const NodeDesc& nd = nodes[k];
+    if (nd.dtype != DT) return;
+    const int c = chunk - nd.chunk0;
+    const int64_t i = (int64_t)c * kChunk + lane;
+    const bool valid = i < nd.n;
+    Gauss g;
+    if (valid) load_geometry<DT>(nd, i, g);
+    for (int e = nv_off[k]; e < nv_off[k + 1]; ++e) {
+        const NodeView w = nv[e];
+        if (w.view < v0 || w.view >= v1) continue;
+        count_chunk<DT>(nd, c, lane, vnodes[w.view * K + w.slot], views[w.view], P, g, valid, counts);
+    }
+}
+
+// Plain mode: the chunks of one view.  pmap = [K+1 prefix chunk counts in node-id order, K slots].
+template <int DT>
+__global__ void __launch_bounds__(256) k_count_plain(const NodeDesc* __restrict__ nodes, const ViewDesc* __restrict__ views,
+        const VNode* __restrict__ vnodes, int K, Params P, int v, const int32_t* __restrict__ pmap, int n_view_chunks,
+        uint2* counts) {
+    const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (w >= n_view_chunks) return;
+    const int lane = (int)lane_id();
+    int lo = 0, hi = K - 1;
+    while (lo < hi) { const int mid = (lo + hi + 1) >> 1; if (pmap[mid] <= w) lo = mid; else hi = mid - 1; }
+    const int slot = pmap[K + 1 + lo];
+    const VNode& vn = vnodes[v * K + slot];
+    const NodeDesc& nd = nodes[vn.node];
+    if (nd.dtype != DT) return;
+    const int c = w - pmap[lo];
+    const int64_t i = (int64_t)c * kChunk + lane;
+    const bool valid = i < nd.n;
+    Gauss g;
+    if (valid) load_geometry<DT>(nd, i, g);
+    count_chunk<DT>(nd, c, lane, vn, views[v], P, g, valid, counts);
+}
+
+// ------------------------------------------------------------------ emit pass
+template <int DT>
+__device__ __forceinline__ void emit_chunk(const NodeDesc& nd, int c, int lane, int view, const VNode& vn,
+                                           const ViewDesc& vd, const Params& P, const Gauss& g, bool valid, int64_t i,
+                                           const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off,
+                                           uint32_t inst_base, uint64_t pair_base, Record* __restrict__ rec,
+                                           uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    Splat s;
+    uint32_t nt = 0;
+    if (valid && project(g, vn, vd, P, s)) nt = count_tiles(s, vd, P);
+    const int64_t t = vn.tab + c;
+    const uint32_t vis = nt > 0 ? 1u : 0u;
+    const uint32_t vis_pre = __popc(__ballot_sync(0xffffffffu, vis) & ((1u << lane) - 1u));
+    const uint32_t nt_pre = warp_excl_scan(nt);
+    const uint32_t nt_tot = __shfl_sync(0xffffffffu, nt_pre + nt, 31);
+    const uint32_t vis_tot = __popc(__ballot_sync(0xffffffffu, vis));
+    // the count pass must have produced the same totals; otherwise write nothing (the
+    // table's slots are then filled with dead pairs that sort to the end)
+    const uint64_t p0 = pair_off[t] - pair_base, p1 = pair_off[t + 1] - pair_base;
+    if ((uint64_t)nt_tot != p1 - p0 || vis_tot != inst_off[t + 1] - inst_off[t]) {
+        for (uint64_t p = p0 + lane; p < p1; p += 32) { keys[p] = ~0ull; vals[p] = 0; }
+        if (lane == 0) atomicOr(P.err, kErrMismatch);
+        return;
+    }
+    if (!vis) return;
+    const uint32_t r = inst_off[t] - inst_base + vis_pre;
+    float rgb[3];
+    sh_colour<DT>(nd, i, g, vn, rgb);
+    const float op = 1.f / (1.f + __expf(-__ldg(nd.opac + i)));
+    Record R;
+    R.r0 = make_float4(s.u, s.v, op, s.z);
+    R.r1 = make_float4(s.a, s.b, s.c, __uint_as_float((uint32_t)(nd.gbase + i)));
+    R.r2 = make_float4(rgb[0], rgb[1], rgb[2], __int_as_float(view));
+    rec[r] = R;
+    uint32_t zk = __float_as_uint(s.z) - P.zbase;
+    zk = min(zk, (1u << kZBits) - 1u);
+    uint64_t p = p0 + nt_pre;
+    const uint64_t p_end = p + nt;      // never write past this instance's pairs
+    for (int ty = s.ty0; ty <= s.ty1 && p < p_end; ++ty)
+        for (int tx = s.tx0; tx <= s.tx1 && p < p_end; ++tx) {
+            if (!tile_hit(s, vd, P, tx, ty)) continue;
+            const uint64_t gt = (uint64_t)(vd.tile_base - P.tile0 + ty * vd.tiles_x + tx);
+            keys[p] = (gt << kZBits) | zk;
+            vals[p] = r;
+            ++p;
+        }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) k_emit_batched(const NodeDesc* __restrict__ nodes, int n_nodes,
+        const ViewDesc* __restrict__ views, const VNode* __restrict__ vnodes, int K, const NodeView* __restrict__ nv,
+        const int32_t* __restrict__ nv_off, int n_chunks, Params P, int v0, int v1,
+        const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off, uint32_t inst_base,
+        uint64_t pair_base, Record* __restrict__ rec, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    const int chunk = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (chunk >= n_chunks) return;
+    const int lane = (int)lane_id();
+    const int k = find_node(nodes, n_nodes, chunk);
+    const NodeDesc& nd = nodes[k];
+    if (nd.dtype != DT) return;
+    const int c = chunk - nd.chunk0;
+    const int64_t i = (int64_t)c * kChunk + lane;
+    const bool valid = i < nd.n;
+    Gauss g;
+    if (valid) load_geometry<DT>(nd, i, g);
+    for (int e = nv_off[k]; e < nv_off[k + 1]; ++e) {
+        const NodeView w = nv[e];
+        if (w.view < v0 || w.view >= v1) continue;
+        emit_chunk<DT>(nd, c, lane, w.view, vnodes[w.view * K + w.slot], views[w.view], P, g, valid, i, inst_off,
+                       pair_off, inst_base, pair_base, rec, keys, vals);
+    }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) k_emit_plain(const NodeDesc* __restrict__ nodes, const ViewDesc* __restrict__ views,
+        const VNode* __restrict__ vnodes, int K, Params P, int v, const int32_t* __restrict__ pmap, int n_view_chunks,
+        const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off, uint32_t inst_base,
+        uint64_t pair_base, Record* __restrict__ rec, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (w >= n_view_chunks) return;
+    const int lane = (int)lane_id();
+    int lo = 0, hi = K - 1;
+    while (lo < hi) { const int mid = (lo + hi + 1) >> 1; if (pmap[mid] <= w) lo = mid; else hi = mid - 1; }
+    const int slot = pmap[K + 1 + lo];
+    const VNode& vn = vnodes[v * K + slot];
+    const NodeDesc& nd = nodes[vn.node];
+    if (nd.dtype != DT) return;
+    const int c = w - pmap[lo];
+    const int64_t i = (int64_t)c * kChunk + lane;
+    const bool valid = i < nd.n;
+    Gauss g;
+    if (valid) load_geometry<DT>(nd, i, g);
+    emit_chunk<DT>(nd, c, lane, v, vn, views[v], P, g, valid, i, inst_off, pair_off, inst_base, pair_base, rec, keys,
+                   vals);
+}
+
+// ------------------------------------------------------------------ exclusive scan of the count table
+constexpr int kScanThreads = 256, kScanItems = 16, kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ void block_excl_scan2(uint64_t& a, uint64_t& b, uint64_t& tot_a, uint64_t& tot_b) {
+    __shared__ uint64_t sa[kScanThreads / 32], sb[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t xa = a, xb = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t ya = __shfl_up_sync(0xffffffffu, xa, o), yb = __shfl_up_sync(0xffffffffu, xb, o);
+        if (lane >= o) { xa += ya; xb += yb; }
+    }
+    if (lane == 31) { sa[wid] = xa; sb[wid] = xb; }
+    __syncthreads();
+    uint64_t wa = 0, wb = 0;
+    tot_a = tot_b = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        if (w < wid) { wa += sa[w]; wb += sb[w]; }
+        tot_a += sa[w]; tot_b += sb[w];
+    }
+    a = wa + xa - a;
+    b = wb + xb - b;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_partial(const uint2* __restrict__ counts, int64_t n, ulonglong2* parts) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint64_t a = 0, b = 0;
+    for (int j = 0; j < kScanItems; ++j) {
+        const int64_t i = base + j;
+        if (i < n) { const uint2 c = counts[i]; a += c.x; b += c.y; }
+    }
+    uint64_t ta, tb;
+    block_excl_scan2(a, b, ta, tb);
+    if (threadIdx.x == 0) parts[blockIdx.x] = make_ulonglong2(ta, tb);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_parts(ulonglong2* parts, int64_t n_parts) {
+    // single block: exclusive scan of the per-tile totals, in place; parts[n_parts] = grand total
+    __shared__ uint64_t carry_a, carry_b;
+    if (threadIdx.x == 0) { carry_a = 0; carry_b = 0; }
+    __syncthreads();
+    for (int64_t base = 0; base < n_parts; base += kScanThreads) {
+        const int64_t i = base + threadIdx.x;
+        uint64_t a = 0, b = 0;
+        if (i < n_parts) { a = parts[i].x; b = parts[i].y; }
+        uint64_t ta, tb;
+        block_excl_scan2(a, b, ta, tb);
+        if (i < n_parts) parts[i] = make_ulonglong2(a + carry_a, b + carry_b);
+        __syncthreads();
+        if (threadIdx.x == 0) { carry_a += ta; carry_b += tb; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) parts[n_parts] = make_ulonglong2(carry_a, carry_b);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_final(const uint2* __restrict__ counts, int64_t n,
+                                                            const ulonglong2* __restrict__ parts, uint32_t* inst_off,
+                                                            uint64_t* pair_off) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint2 c[kScanItems];
+    uint64_t a = 0, b = 0;
+    for (int j = 0; j < kScanItems; ++j) {
+        const int64_t i = base + j;
+        c[j] = i < n ? counts[i] : make_uint2(0, 0);
+        a += c[j].x; b += c[j].y;
+    }
+    uint64_t ta, tb;
+    block_excl_scan2(a, b, ta, tb);
+    a += parts[blockIdx.x].x;
+    b += parts[blockIdx.x].y;
+    for (int j = 0; j < kScanItems; ++j) {
+        const int64_t i = base + j;
+        if (i < n) { inst_off[i] = (uint32_t)a; pair_off[i] = b; }
+        if (i == n) { inst_off[i] = (uint32_t)a; pair_off[i] = b; }
+        a += c[j].x; b += c[j].y;
+    }
+    if (n % kScanTile == 0 && blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) {
+        inst_off[n] = (uint32_t)a; pair_off[n] = b;
+    }
+}
+
+template <int DT>
+void count_launch(const Launch& L, const NodeDesc* nodes, int n_nodes, const ViewDesc* views, const VNode* vnodes, int K,
+                  const NodeView* nv, const int32_t* nv_off, int n_chunks, const Params& P, int v0, int v1,
+                  bool batched, const int32_t* pmap, int64_t view_chunks, uint2* counts) {
+    if (batched) {
+        const int blocks = (int)(((int64_t)n_chunks * 32 + 255) / 256);
+        if (blocks == 0) return;
+        k_count_batched<DT><<<blocks, 256, 0, L.stream>>>(nodes, n_nodes, views, vnodes, K, nv, nv_off, n_chunks, P,
+                                                          v0, v1, counts);
+    } else {
+        const int blocks = (int)((view_chunks * 32 + 255) / 256);
+        if (blocks == 0) return;
+        k_count_plain<DT><<<blocks, 256, 0, L.stream>>>(nodes, views, vnodes, K, P, v0, pmap, (int)view_chunks, counts);
+    }
+    ++*L.launches;
+}
+
+template <int DT>
+void emit_launch(const Launch& L, const NodeDesc* nodes, int n_nodes, const ViewDesc* views, const VNode* vnodes, int K,
+                 const NodeView* nv, const int32_t* nv_off, int n_chunks, const Params& P, int v0, int v1, bool batched,
+                 const int32_t* pmap, int64_t view_chunks, const uint32_t* inst_off, const uint64_t* pair_off,
+                 uint32_t inst_base, uint64_t pair_base, Record* rec, uint64_t* keys, uint32_t* vals) {
+    if (batched) {
+        const int blocks = (int)(((int64_t)n_chunks * 32 + 255) / 256);
+        if (blocks == 0) return;
+        k_emit_batched<DT><<<blocks, 256, 0, L.stream>>>(nodes, n_nodes, views, vnodes, K, nv, nv_off, n_chunks, P, v0,
+                                                         v1, inst_off, pair_off, inst_base, pair_base, rec, keys, vals);
+    } else {
+        const int blocks = (int)((view_chunks * 32 + 255) / 256);
+        if (blocks == 0) return;
+        k_emit_plain<DT><<<blocks, 256, 0, L.stream>>>(nodes, views, vnodes, K, P, v0, pmap, (int)view_chunks, inst_off,
+                                                       pair_off, inst_base, pair_base, rec, keys, vals);
+    }
+    ++*L.launches;
+}
+
+}  // namespace
+
+void launch_setup_views(const Launch& L, const ViewDesc* views, int n_views, const float* node_poses,
+                        const int32_t* slot_node, int K, VNode* vnodes, const int64_t* vnode_tab, uint32_t* err) {
+    const int n = n_views * K;
+    if (n == 0) return;
+    k_setup_views<<<(n + 127) / 128, 128, 0, L.stream>>>(views, n_views, node_poses, slot_node, K, vnodes, vnode_tab, err);
+    ++*L.launches;
+}
+
+void launch_count(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_nodes, const ViewDesc* views,
+                  const VNode* vnodes, int K, const NodeView* node_views, const int32_t* node_view_off,
+                  int n_chunks_total, const Params& P, int v0, int v1, bool batched, const int32_t* pmap,
+                  int64_t view_chunks, uint2* counts) {
+    if (dtype_mask & (1 << DGS_F32))
+        count_launch<DGS_F32>(L, nodes, n_nodes, views, vnodes, K, node_views, node_view_off, n_chunks_total, P, v0, v1,
+                              batched, pmap, view_chunks, counts);
+    if (dtype_mask & (1 << DGS_BF16))
+        count_launch<DGS_BF16>(L, nodes, n_nodes, views, vnodes, K, node_views, node_view_off, n_chunks_total, P, v0, v1,
+                               batched, pmap, view_chunks, counts);
+    if (dtype_mask & (1 << DGS_F16))
+        count_launch<DGS_F16>(L, nodes, n_nodes, views, vnodes, K, node_views, node_view_off, n_chunks_total, P, v0, v1,
+                              batched, pmap, view_chunks, counts);
+}
+
+void launch_emit(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_nodes, const ViewDesc* views,
+                 const VNode* vnodes, int K, const NodeView* node_views, const int32_t* node_view_off,
+                 int n_chunks_total, const Params& P, int v0, int v1, bool batched, const int32_t* pmap,
+                 int64_t view_chunks, const uint32_t* inst_off, const uint64_t* pair_off, uint32_t inst_base,
+                 uint64_t pair_base, Record* records, uint64_t* keys, uint32_t* vals) {
+    if (dtype_mask & (1 << DGS_F32))
+        emit_launch<DGS_F32>(L, nodes, n_nodes, views, vnodes, K, node_views, node_view_off, n_chunks_total, P, v0, v1,
+                             batched, pmap, view_chunks, inst_off, pair_off, inst_base, pair_base, records, keys, vals);
+    if (dtype_mask & (1 << DGS_BF16))
+        emit_launch<DGS_BF16>(L, nodes, n_nodes, views, vnodes, K, node_views, node_view_off, n_chunks_total, P, v0, v1,
+                              batched, pmap, view_chunks, inst_off, pair_off, inst_base, pair_base, records, keys, vals);
+    if (dtype_mask & (1 << DGS_F16))
+        emit_launch<DGS_F16>(L, nodes, n_nodes, views, vnodes, K, node_views, node_view_off, n_chunks_total, P, v0, v1,
+                             batched, pmap, view_chunks, inst_off, pair_off, inst_base, pair_base, records, keys, vals);
+}
+
+void launch_scan(const Launch& L, const uint2* counts, int64_t n, uint32_t* inst_off, uint64_t* pair_off,
+                 ulonglong2* parts, int64_t n_parts_cap) {
+    const int64_t n_parts = (n + kScanTile - 1) / kScanTile;
+    (void)n_parts_cap;
+    if (n_parts == 0) {
+        cudaMemsetAsync(inst_off, 0, sizeof(uint32_t), L.stream);
+        cudaMemsetAsync(pair_off, 0, sizeof(uint64_t), L.stream);
+        return;
+    }
+    k_scan_partial<<<(unsigned)n_parts, kScanThreads, 0, L.stream>>>(counts, n, parts);
+    k_scan_parts<<<1, kScanThreads, 0, L.stream>>>(parts, n_parts);
+    k_scan_final<<<(unsigned)n_parts, kScanThreads, 0, L.stream>>>(counts, n, parts, inst_off, pair_off);
+    *L.launches += 3;
+}
+
+}  // namespace dgs

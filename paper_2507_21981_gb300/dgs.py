@@ -1,0 +1,159 @@
+"""ctypes binding of libdgs (include/dgs.h): the same names, argument marshalling only.
+
+Every step of rendering runs in the CUDA library; this module only converts Python values to
+the C structures and calls the exported functions.  It raises if libdgs.so cannot be loaded:
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdgs.so")
+
+DGS_OK, DGS_ERR_INVALID_ARG, DGS_ERR_CUDA, DGS_ERR_OOM, DGS_ERR_CAPACITY, DGS_ERR_TIMEOUT, DGS_ERR_UNSUPPORTED = range(7)
+DGS_F32, DGS_BF16, DGS_F16 = 0, 1, 2
+DGS_MODE_PLAIN, DGS_MODE_BATCHED = 0, 1
+KERNEL_CLASSES = ("setup", "count", "scan", "emit", "sort", "ranges", "composite", "backward")
+STATUS_NAMES = {0: "DGS_OK", 1: "DGS_ERR_INVALID_ARG", 2: "DGS_ERR_CUDA", 3: "DGS_ERR_OOM", 4: "DGS_ERR_CAPACITY",
+                5: "DGS_ERR_TIMEOUT", 6: "DGS_ERR_UNSUPPORTED"}
+
+
+class dgs_node(C.Structure):
+    _fields_ = [("mean", C.c_void_p), ("log_scale", C.c_void_p), ("quat", C.c_void_p),
+                ("opacity_logit", C.c_void_p), ("sh", C.c_void_p), ("n", C.c_int64),
+                ("sh_degree", C.c_int32), ("dtype", C.c_int32)]
+
+
+class dgs_camera(C.Structure):
+    _fields_ = [("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32), ("cam_from_world", C.c_float * 12)]
+
+
+class dgs_options(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("tile_w", C.c_int32), ("tile_h", C.c_int32), ("exact_tile_test", C.c_int32),
+                ("z_near", C.c_float), ("lowpass", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
+                ("t_min", C.c_float), ("q_max", C.c_float), ("guard", C.c_float), ("bg", C.c_float * 3),
+                ("profile", C.c_int32), ("views_per_group", C.c_int32)]
+
+
+class dgs_stats(C.Structure):
+    _fields_ = [("n_views", C.c_int64), ("n_pixels", C.c_int64), ("n_instances", C.c_int64),
+                ("n_visible", C.c_int64), ("n_pairs", C.c_int64), ("n_groups", C.c_int32), ("key_bits", C.c_int32)]
+
+
+EXPORTED = ("dgs_default_options", "dgs_context_create", "dgs_context_destroy", "dgs_last_error",
+            "dgs_workspace_query", "dgs_render", "dgs_last_stats", "dgs_kernel_times", "dgs_last_launches")
+
+_lib = None
+_lock = threading.Lock()
+
+
+class DgsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load(path: str | None = None) -> C.CDLL:
+    """Loads libdgs.so (built in-tree by build.py).  Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libdgs.so not found at {p}: build it with paper_2507_21981_gb300.build.build()")
+        lib = C.CDLL(p)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        lib.dgs_default_options.restype = None
+        lib.dgs_default_options.argtypes = [C.POINTER(dgs_options)]
+        lib.dgs_context_create.restype = C.c_int
+        lib.dgs_context_create.argtypes = [C.POINTER(vp), C.POINTER(dgs_options)]
+        lib.dgs_context_destroy.restype = C.c_int
+        lib.dgs_context_destroy.argtypes = [vp]
+        lib.dgs_last_error.restype = C.c_char_p
+        lib.dgs_last_error.argtypes = [vp]
+        lib.dgs_workspace_query.restype = C.c_int
+        lib.dgs_workspace_query.argtypes = [vp, C.POINTER(C.c_size_t)]
+        lib.dgs_render.restype = C.c_int
+        lib.dgs_render.argtypes = [vp, C.POINTER(dgs_node), i32, vp, i32, i32, vp, C.POINTER(dgs_camera), vp, i32,
+                                   vp, vp, vp, vp, vp]
+        lib.dgs_last_stats.restype = C.c_int
+        lib.dgs_last_stats.argtypes = [vp, C.POINTER(dgs_stats)]
+        lib.dgs_kernel_times.restype = C.c_int
+        lib.dgs_kernel_times.argtypes = [vp, C.POINTER(C.c_float)]
+        lib.dgs_last_launches.restype = C.c_int64
+        lib.dgs_last_launches.argtypes = [vp]
+        if path is None:
+            _lib = lib
+        return lib
+
+
+# ----------------------------------------------------------------------------- same-name wrappers
+def dgs_default_options() -> dgs_options:
+    o = dgs_options()
+    load().dgs_default_options(C.byref(o))
+    return o
+
+
+def dgs_context_create(opt: dgs_options | None = None) -> C.c_void_p:
+    h = C.c_void_p()
+    rc = load().dgs_context_create(C.byref(h), C.byref(opt) if opt is not None else None)
+    if rc != DGS_OK:
+        raise DgsError(rc, "dgs_context_create")
+    return h
+
+
+def dgs_context_destroy(ctx) -> int:
+    return load().dgs_context_destroy(ctx)
+
+
+def dgs_last_error(ctx) -> str:
+    s = load().dgs_last_error(ctx)
+    return s.decode() if s else ""
+
+
+def dgs_workspace_query(ctx) -> int:
+    b = C.c_size_t()
+    load().dgs_workspace_query(ctx, C.byref(b))
+    return int(b.value)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    if isinstance(a, int):
+        return a
+    return a.data_ptr()          # torch tensor
+
+
+def dgs_render(ctx, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env, max_cams,
+               out_rgb, out_depth, out_alpha, view_pixel_offset, stream) -> int:
+    """Direct call of dgs_render.  Host tables are numpy arrays (or ctypes arrays), device
+    buffers are torch tensors or integer device addresses, stream an integer cudaStream_t."""
+    return load().dgs_render(ctx, nodes, int(n_nodes), _ptr(env_node_ids), int(n_envs), int(max_nodes),
+                             _ptr(node_poses), cams, _ptr(cams_per_env), int(max_cams), _ptr(out_rgb),
+                             _ptr(out_depth), _ptr(out_alpha), _ptr(view_pixel_offset), stream)
+
+
+def dgs_last_stats(ctx) -> dict:
+    s = dgs_stats()
+    load().dgs_last_stats(ctx, C.byref(s))
+    return {k: getattr(s, k) for k, _ in dgs_stats._fields_}
+
+
+def dgs_kernel_times(ctx) -> dict:
+    a = (C.c_float * 8)()
+    load().dgs_kernel_times(ctx, a)
+    return dict(zip(KERNEL_CLASSES, [float(x) for x in a]))
+
+
+def dgs_last_launches(ctx) -> int:
+    return int(load().dgs_last_launches(ctx))

@@ -1,0 +1,125 @@
+"""Torch-facing wrapper of libdgs: device memory and streams come from PyTorch, every render
+step runs in the CUDA library (dgs.py marshals the arguments)."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import dgs as D
+
+_TORCH_DTYPES = {"f32": (torch.float32, D.DGS_F32), "bf16": (torch.bfloat16, D.DGS_BF16),
+                 "f16": (torch.float16, D.DGS_F16)}
+
+
+class DeviceScene:
+    """A scene's nodes resident on the GPU plus the host tables of one batch of envs x cameras.
+
+    Attribute storage: `dtype` in {"f32", "bf16", "f16"} applies to log-scales, quaternions
+    and SH coefficients; means and opacity logits stay FP32.
+    """
+
+    def __init__(self, scene, device="cuda", dtype: str = "f32"):
+        tdt, code = _TORCH_DTYPES[dtype]
+        self.dtype = dtype
+        self.device = torch.device(device)
+        self.tensors = []
+        self.nodes = (D.dgs_node * len(scene.nodes))()
+        for k, nd in enumerate(scene.nodes):
+            t = dict(mean=torch.as_tensor(np.ascontiguousarray(nd.mean, np.float32), device=self.device),
+                     log_scale=torch.as_tensor(np.ascontiguousarray(nd.log_scale, np.float32)).to(self.device, tdt),
+                     quat=torch.as_tensor(np.ascontiguousarray(nd.quat, np.float32)).to(self.device, tdt),
+                     opacity_logit=torch.as_tensor(np.ascontiguousarray(nd.opacity_logit, np.float32), device=self.device),
+                     sh=torch.as_tensor(np.ascontiguousarray(nd.sh, np.float32)).to(self.device, tdt).contiguous())
+            self.tensors.append(t)
+            n = self.nodes[k]
+            n.mean, n.log_scale, n.quat = t["mean"].data_ptr(), t["log_scale"].data_ptr(), t["quat"].data_ptr()
+            n.opacity_logit, n.sh = t["opacity_logit"].data_ptr(), t["sh"].data_ptr()
+            n.n, n.sh_degree, n.dtype = nd.n, nd.sh_degree, code
+        self.n_nodes = len(scene.nodes)
+        self.env_node_ids = np.ascontiguousarray(scene.env_node_ids, np.int32)
+        self.n_envs, self.max_nodes = self.env_node_ids.shape
+        self.cams_per_env = np.ascontiguousarray(scene.cams_per_env, np.int32)
+        self.max_cams = int(scene.cam_res.shape[1])
+        E, Cm = self.n_envs, self.max_cams
+        self.cams = (D.dgs_camera * (E * Cm))()
+        self.view_res = []
+        for e in range(E):
+            for c in range(Cm):
+                cam = self.cams[e * Cm + c]
+                fx, fy, cx, cy = (float(x) for x in scene.cam_intr[e, c])
+                cam.fx, cam.fy, cam.cx, cam.cy = fx, fy, cx, cy
+                w, h = (int(x) for x in scene.cam_res[e, c])
+                cam.width, cam.height = max(w, 1), max(h, 1)
+                cam.cam_from_world[:] = [float(x) for x in np.asarray(scene.cam_pose[e, c], np.float64).reshape(12)]
+                if c < self.cams_per_env[e]:
+                    self.view_res.append((w, h))
+        self.n_views = len(self.view_res)
+        self.n_pixels = int(sum(w * h for w, h in self.view_res))
+        self.view_offsets = np.concatenate([[0], np.cumsum([w * h for w, h in self.view_res])]).astype(np.int64)
+        self.node_poses = torch.as_tensor(np.ascontiguousarray(scene.node_poses, np.float32).reshape(E, self.max_nodes, 12),
+                                          device=self.device)
+
+    def set_poses(self, node_poses):
+        """Replace the per-env node poses ([E,K,3,4] or [E,K,12]) with a device copy."""
+        self.node_poses = torch.as_tensor(node_poses, dtype=torch.float32, device=self.device).reshape(
+            self.n_envs, self.max_nodes, 12).contiguous()
+
+    def view_slice(self, v: int):
+        return slice(int(self.view_offsets[v]), int(self.view_offsets[v + 1]))
+
+
+class Renderer:
+    """A libdgs context.  Options are the fields of dgs_options (see include/dgs.h)."""
+
+    def __init__(self, mode: str = "batched", tile=(16, 16), profile: bool = False, **opts):
+        o = D.dgs_default_options()
+        o.mode = D.DGS_MODE_BATCHED if mode == "batched" else D.DGS_MODE_PLAIN
+        o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
+        o.profile = int(bool(profile))
+        for k, v in opts.items():
+            if k == "bg":
+                o.bg = (C.c_float * 3)(*[float(x) for x in v])
+            else:
+                setattr(o, k, v)
+        self.options = o
+        self.ctx = D.dgs_context_create(o)
+
+    def close(self):
+        if self.ctx:
+            D.dgs_context_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def render(self, ds: DeviceScene, out=None, with_alpha: bool = True, stream=None):
+        """Renders every view of `ds`; returns (rgb [P,3], depth [P], alpha [P] or None), flat over views."""
+        if out is None:
+            rgb = torch.empty((ds.n_pixels, 3), dtype=torch.float32, device=ds.device)
+            depth = torch.empty((ds.n_pixels,), dtype=torch.float32, device=ds.device)
+            alpha = torch.empty((ds.n_pixels,), dtype=torch.float32, device=ds.device) if with_alpha else None
+        else:
+            rgb, depth, alpha = out
+        s = stream if stream is not None else torch.cuda.current_stream(ds.device)
+        rc = D.dgs_render(self.ctx, ds.nodes, ds.n_nodes, ds.env_node_ids, ds.n_envs, ds.max_nodes, ds.node_poses,
+                          ds.cams, ds.cams_per_env, ds.max_cams, rgb, depth, alpha, None, s.cuda_stream)
+        if rc != D.DGS_OK:
+            raise D.DgsError(rc, D.dgs_last_error(self.ctx))
+        return rgb, depth, alpha
+
+    def stats(self) -> dict:
+        return D.dgs_last_stats(self.ctx)
+
+    def kernel_times(self) -> dict:
+        return D.dgs_kernel_times(self.ctx)
+
+    def launches(self) -> int:
+        return D.dgs_last_launches(self.ctx)
+
+    def workspace_bytes(self) -> int:
+        return D.dgs_workspace_query(self.ctx)

@@ -1,0 +1,146 @@
+"""The C-ABI library loads, exports every function include/dgs.h declares, and validates
+arguments on the host (no GPU needed: only calls that return before any device work)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2507_21981_gb300 import build as B
+from paper_2507_21981_gb300 import dgs as D
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return D.load()
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(dgs_\w+)\s*\(", src, re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_render_calls():
+    names = declared_functions()
+    for n in ("dgs_render", "dgs_context_create", "dgs_context_destroy", "dgs_last_error"):
+        assert n in names
+
+
+def test_every_declared_function_is_exported(lib):
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_every_export(lib):
+    for n in declared_functions():
+        assert n in D.EXPORTED, n
+
+
+def test_default_options(lib):
+    o = D.dgs_default_options()
+    assert (o.tile_w, o.tile_h, o.mode) == (16, 16, D.DGS_MODE_BATCHED)
+    assert o.alpha_min == pytest.approx(1 / 255) and o.alpha_max == pytest.approx(0.99)
+    assert o.t_min == pytest.approx(1e-4) and o.q_max == 9.0 and o.lowpass == pytest.approx(0.3)
+    assert o.z_near == pytest.approx(0.01) and o.guard == pytest.approx(1.3)
+
+
+def test_struct_sizes_match_header(lib):
+    assert C.sizeof(D.dgs_node) == 56
+    assert C.sizeof(D.dgs_camera) == 72
+    assert C.sizeof(D.dgs_options) == 64
+    assert C.sizeof(D.dgs_stats) == 48
+
+
+def test_invalid_options_rejected(lib):
+    o = D.dgs_default_options()
+    o.tile_w = 10
+    h = C.c_void_p()
+    assert lib.dgs_context_create(C.byref(h), C.byref(o)) == D.DGS_ERR_INVALID_ARG
+    o = D.dgs_default_options()
+    o.z_near = 0.0
+    assert lib.dgs_context_create(C.byref(h), C.byref(o)) == D.DGS_ERR_INVALID_ARG
+    assert lib.dgs_context_create(None, None) == D.DGS_ERR_INVALID_ARG
+
+
+def _ctx(lib):
+    h = C.c_void_p()
+    assert lib.dgs_context_create(C.byref(h), None) == D.DGS_OK
+    return h
+
+
+def _args(n_nodes=1, E=1, K=1, Cm=1):
+    nodes = (D.dgs_node * n_nodes)()
+    for k in range(n_nodes):
+        nodes[k].n = 0
+        nodes[k].sh_degree = 0
+        nodes[k].dtype = D.DGS_F32
+    ids = np.zeros((E, K), np.int32)
+    cams = (D.dgs_camera * (E * Cm))()
+    for i in range(E * Cm):
+        cams[i].fx = cams[i].fy = 10.0
+        cams[i].width = cams[i].height = 8
+        cams[i].cam_from_world[:] = [1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0]
+    cpe = np.ones(E, np.int32)
+    return nodes, ids, cams, cpe
+
+
+FAKE_DEV = 0x10000   # never dereferenced: every case below fails host validation first
+
+
+def _render(lib, ctx, nodes, n_nodes, ids, E, K, cams, cpe, Cm, poses=FAKE_DEV, rgb=FAKE_DEV, depth=FAKE_DEV):
+    return lib.dgs_render(ctx, nodes, n_nodes, ids.ctypes.data, E, K, poses, cams, cpe.ctypes.data, Cm, rgb, depth,
+                          None, None, None)
+
+
+def test_render_validates_arguments_on_host(lib):
+    ctx = _ctx(lib)
+    try:
+        nodes, ids, cams, cpe = _args()
+        assert lib.dgs_render(None, nodes, 1, ids.ctypes.data, 1, 1, FAKE_DEV, cams, cpe.ctypes.data, 1, FAKE_DEV,
+                              FAKE_DEV, None, None, None) == D.DGS_ERR_INVALID_ARG
+        # missing outputs
+        assert _render(lib, ctx, nodes, 1, ids, 1, 1, cams, cpe, 1, rgb=None) == D.DGS_ERR_INVALID_ARG
+        assert "out_rgb" in D.dgs_last_error(ctx)
+        # node id out of range / duplicated in one env
+        bad = ids.copy(); bad[0, 0] = 5
+        assert _render(lib, ctx, nodes, 1, bad, 1, 1, cams, cpe, 1) == D.DGS_ERR_INVALID_ARG
+        n2, ids2, cams2, cpe2 = _args(n_nodes=1, K=2)
+        assert _render(lib, ctx, n2, 1, ids2, 1, 2, cams2, cpe2, 1) == D.DGS_ERR_INVALID_ARG
+        assert "twice" in D.dgs_last_error(ctx)
+        # bad SH degree and dtype
+        nodes[0].sh_degree = 4
+        assert _render(lib, ctx, nodes, 1, ids, 1, 1, cams, cpe, 1) == D.DGS_ERR_INVALID_ARG
+        nodes[0].sh_degree = 0; nodes[0].dtype = 7
+        assert _render(lib, ctx, nodes, 1, ids, 1, 1, cams, cpe, 1) == D.DGS_ERR_INVALID_ARG
+        nodes[0].dtype = 0
+        # a non-empty node with null attribute pointers
+        nodes[0].n = 10
+        assert _render(lib, ctx, nodes, 1, ids, 1, 1, cams, cpe, 1) == D.DGS_ERR_INVALID_ARG
+        nodes[0].n = 0
+        # camera: non-rigid rotation, non-positive focal length, zero size, too many cameras
+        cams[0].cam_from_world[0] = 2.0
+        assert _render(lib, ctx, nodes, 1, ids, 1, 1, cams, cpe, 1) == D.DGS_ERR_INVALID_ARG
+        cams[0].cam_from_world[0] = 1.0; cams[0].fx = -1.0
+        assert _render(lib, ctx, nodes, 1, ids, 1, 1, cams, cpe, 1) == D.DGS_ERR_INVALID_ARG
+        cams[0].fx = 10.0; cams[0].width = 0
+        assert _render(lib, ctx, nodes, 1, ids, 1, 1, cams, cpe, 1) == D.DGS_ERR_INVALID_ARG
+        cams[0].width = 8
+        cpe[0] = 2
+        assert _render(lib, ctx, nodes, 1, ids, 1, 1, cams, cpe, 1) == D.DGS_ERR_INVALID_ARG
+        cpe[0] = 1
+        cams[0].cam_from_world[3] = float("nan")
+        assert _render(lib, ctx, nodes, 1, ids, 1, 1, cams, cpe, 1) == D.DGS_ERR_INVALID_ARG
+    finally:
+        lib.dgs_context_destroy(ctx)
+
+
+def test_build_flags_target_sm103a():
+    assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

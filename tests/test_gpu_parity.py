@@ -1,0 +1,112 @@
+"""GPU (libdgs through the C ABI) vs the FP64 oracle, pixel by pixel, on seeded scenes."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2507_21981_gb300 import scenes as S
+from tests.parity import compare_view
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+OPTS = O.OracleOptions()
+
+
+def _render(sc, mode="batched", dtype="f32", **kw):
+    from paper_2507_21981_gb300.render import DeviceScene, Renderer
+    ds = DeviceScene(sc, device="cuda:0", dtype=dtype)
+    r = Renderer(mode=mode, **kw)
+    rgb, depth, alpha = r.render(ds)
+    torch.cuda.synchronize()
+    out = rgb.cpu().numpy(), depth.cpu().numpy(), alpha.cpu().numpy()
+    stats, launches = r.stats(), r.launches()
+    r.close()
+    return ds, out, stats, launches
+
+
+def _check_views(sc, ds, out, views, opts=OPTS, packed=None):
+    rgb, depth, alpha = out
+    reports = []
+    for v in views:
+        e, c = sc.views[v]
+        ref = O.render_view(sc, e, c, opts, packed)
+        H, W = ref.depth.shape
+        sl = ds.view_slice(v)
+        bad, rep = compare_view(rgb[sl].reshape(H, W, 3), depth[sl].reshape(H, W), ref, alpha[sl].reshape(H, W))
+        rep["view"] = v
+        reports.append(rep)
+        assert bad == 0, rep
+    return reports
+
+
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_config1_every_pixel(mode):
+    sc = S.config1(seed=1)
+    ds, out, st, launches = _render(sc, mode)
+    assert launches > 0 and st["n_visible"] > 0
+    reps = _check_views(sc, ds, out, [0])
+    assert reps[0]["ambiguous"] / reps[0]["pixels"] < 1e-2
+
+
+@pytest.mark.parametrize("seed", [2, 3])
+def test_config1_more_seeds_and_background(seed):
+    sc = S.config1(seed=seed)
+    ds, out, _, _ = _render(sc, "batched", bg=(0.2, 0.4, 0.6))
+    _check_views(sc, ds, out, [0], O.OracleOptions(bg=(0.2, 0.4, 0.6)))
+
+
+def test_config2_reduced_all_views():
+    # the config-2 law at reduced size: 4 envs x 2 cameras 160x120, 60k room + 4 x 2k objects
+    sc = S.config2(seed=1, n_envs=4, n_bg=60_000, n_obj=2_000, width=160, height=120, f=125.0)
+    ds, out, st, _ = _render(sc, "batched")
+    assert st["n_views"] == 8
+    _check_views(sc, ds, out, range(8))
+
+
+def test_batched_equals_plain_bitwise():
+    sc = S.config2(seed=2, n_envs=3, n_bg=40_000, n_obj=1_500, width=160, height=120, f=125.0)
+    _, a, _, _ = _render(sc, "batched")
+    _, b, _, _ = _render(sc, "plain")
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_config3_reduced_ragged_views():
+    sc = S.config3(seed=1, n_envs=6, n_bg=30_000, n_assets=8, asset_lo=500, asset_hi=4_000, max_nodes=4,
+                   resolutions=((80, 60), (160, 120), (200, 110)))
+    ds, out, st, _ = _render(sc, "batched")
+    _check_views(sc, ds, out, range(sc.n_views))
+
+
+def test_ragged_tiles_and_tile_shapes():
+    sc = S.config1(seed=4, res=100, f=86.0)     # 100x100: partial tiles at the right/bottom
+    for tile in [(16, 16), (32, 8), (8, 32), (16, 8), (8, 8)]:
+        ds, out, _, _ = _render(sc, "batched", tile=tile)
+        _check_views(sc, ds, out, [0])
+
+
+def test_views_per_group_split_matches_single_group():
+    sc = S.config2(seed=3, n_envs=3, n_bg=20_000, n_obj=1_000, width=96, height=64, f=75.0)
+    _, a, st1, _ = _render(sc, "batched")
+    _, b, st2, _ = _render(sc, "batched", views_per_group=2)
+    assert st1["n_groups"] == 1 and st2["n_groups"] == 3
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_empty_nodes_and_env_without_cameras():
+    sc = S.config2(seed=4, n_envs=3, n_bg=5_000, n_obj=500, width=64, height=48, f=50.0)
+    sc.cams_per_env[1] = 0                       # an env with no camera
+    sc.nodes[2] = sc.nodes[2].subset(slice(0, 0))  # an empty node
+    ds, out, st, _ = _render(sc, "batched")
+    assert st["n_views"] == 4
+    _check_views(sc, ds, out, range(4))
+
+
+def test_all_transparent_scene_gives_background():
+    sc = S.config1(seed=5)
+    for nd in sc.nodes:
+        nd.opacity_logit[:] = -30.0
+    ds, out, st, _ = _render(sc, "batched", bg=(0.1, 0.2, 0.3))
+    rgb, depth, alpha = out
+    assert np.allclose(rgb, [0.1, 0.2, 0.3], atol=1e-7) and np.all(depth == 0) and np.all(alpha == 0)
