@@ -38,9 +38,14 @@
 // Candidates are sorted by (z32, global id), global id = node_base[node] + local index, and
 // culled when z32 <= float(z_near).  Every other quantity is FP64.
 //
-// Decisions whose FP64 quantity lies within a relative band eps_rel of its threshold
-// (ellipse, alpha_min, t_min) are "ambiguous": an FP32 implementation may legitimately take
-// the other branch.  The forward pass enumerates
+// Decisions whose FP64 quantity lies within the FP32 error band of its threshold (ellipse,
+// alpha_min, t_min) are "ambiguous": an FP32 implementation may legitimately take the other
+// branch.  The band is twice an error bound of the FP32 evaluation of that quantity
+// (u = 2^-24): the projected centre carries dU ~ fx (d_tx + |x/z| d_tz)/z + 2u(|u| + |cx|)
+// with d_t ~ 8u (|M_R| |mu| + |t_n| + |t_c|); d_q = 2|dq/du| dU + 2|dq/dv| dV + 32u q (+ the
+// error of the factored form); alpha moves by alpha (d_q/2 + (8 + 1.2|logit| + 0.6 q) u); the
+// transmittance accumulates sum alpha/(1-alpha) d_alpha/alpha + 2u per step.  eps_rel adds a
+// relative floor to every band.  The forward pass enumerates
 // up to max_flips such flips per pixel and returns every branch's result; beyond that it
 // widens the pixel's tolerance by T * max|value| per unexplored flip (the two branches agree
 // on the first 1-T of the composite and both stay inside the convex hull of the rest).
@@ -78,7 +83,7 @@ typedef struct {
 typedef struct {
     double z_near, lowpass, alpha_min, alpha_max, t_min, q_max, guard;
     double bg[3];
-    double eps_rel;     // relative ambiguity band of thresholded decisions
+    double eps_rel;     // relative floor added to the FP32 error band of every decision
     int32_t max_flips;  // branches enumerated per pixel (<= 6)
     int32_t nthreads;   // 0 = hardware concurrency
     int32_t bruteforce; // 1 = test every Gaussian at every pixel (no AABB candidate lists)
@@ -180,6 +185,8 @@ struct Geo {
     double raw[3], rgb[3];
     bool present, near_amb, valid;
     double hx, hy;               // half extents of the ellipse's axis-aligned box (with band margin)
+    double du, dv;               // FP32 error bound of the projected centre (pixels)
+    double dqb;                  // FP32 error bound of the factored form's cross coefficient
 };
 
 void rot_from_quat(const double q[4], double R[3][3]) {
@@ -270,8 +277,25 @@ void project(const oracle_scene* s, const oracle_opts* o, int e, int c, int slot
     G.Q[0][0] = G.cov[1][1] / G.det; G.Q[1][1] = G.cov[0][0] / G.det;
     G.Q[0][1] = G.Q[1][0] = -G.cov[0][1] / G.det;
     G.u = G.fx * G.xr + G.cx; G.v = G.fy * G.yr + G.cy;
-    // Bounding box of {d : d^T Q d <= q_max (1+eps)}: half extents sqrt(q_max (1+eps) Sigma_ii).
-    const double qb = o->q_max * (1.0 + 2.0 * o->eps_rel);
+    {   // FP32 error model of the projected centre
+        const double g32 = 5.9604644775390625e-08;
+        double MR[3][3];
+        for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) {
+            double a = 0; for (int k = 0; k < 3; ++k) a += G.Wc[i][k] * G.Rn[k][j]; MR[i][j] = a; }
+        const double tnn = std::sqrt(G.tn[0] * G.tn[0] + G.tn[1] * G.tn[1] + G.tn[2] * G.tn[2]);
+        double S[3];
+        for (int i = 0; i < 3; ++i)
+            S[i] = std::fabs(MR[i][0] * G.mu[0]) + std::fabs(MR[i][1] * G.mu[1]) + std::fabs(MR[i][2] * G.mu[2]) +
+                   tnn + std::fabs(G.tc[i]);
+        const double dtx = 8 * g32 * S[0], dty = 8 * g32 * S[1], dtz = 8 * g32 * S[2];
+        const double dxr = (dtx + std::fabs(G.xr) * dtz) / G.t[2] + 2 * g32 * std::fabs(G.xr);
+        const double dyr = (dty + std::fabs(G.yr) * dtz) / G.t[2] + 2 * g32 * std::fabs(G.yr);
+        G.du = G.fx * dxr + 2 * g32 * (std::fabs(G.fx * G.xr) + std::fabs(G.cx));
+        G.dv = G.fy * dyr + 2 * g32 * (std::fabs(G.fy * G.yr) + std::fabs(G.cy));
+        G.dqb = 8 * g32 * std::sqrt(G.cov[0][0] / G.cov[1][1]);
+    }
+    // Bounding box of {d : d^T Q d <= qb}, a superset of every candidate whose band reaches q_max.
+    const double qb = o->q_max * (1.01 + 2.0 * o->eps_rel) + 0.1;
     G.hx = std::sqrt(qb * G.cov[0][0]) * (1 + 1e-12) + 1e-12;
     G.hy = std::sqrt(qb * G.cov[1][1]) * (1 + 1e-12) + 1e-12;
     // Opacity.
@@ -326,18 +350,24 @@ bool build_view(const oracle_scene* s, const oracle_opts* o, int e, int c, ViewD
 }
 
 // Per-pixel candidate: a Gaussian whose band-widened ellipse contains the pixel centre.
-struct Cand { int idx; double key; int64_t gid; double q, dx, dy; };
+struct Cand { int idx; double key; int64_t gid; double q, dx, dy, dq; };
 
 void pixel_candidates(const ViewData& V, const oracle_opts* o, const std::vector<int>& pool, int px, int py,
                       std::vector<Cand>& out) {
     out.clear();
     const double X = px + 0.5, Yc = py + 0.5;
-    const double qlim = o->q_max * (1.0 + o->eps_rel);
+    const double qlim = o->q_max * (1.01 + 2.0 * o->eps_rel) + 0.1;
+    const double g32 = 5.9604644775390625e-08;
     for (int idx : pool) {
         const Geo& G = V.geo[idx];
         const double dx = X - G.u, dy = Yc - G.v;
         const double q = G.Q[0][0] * dx * dx + 2 * G.Q[0][1] * dx * dy + G.Q[1][1] * dy * dy;
-        if (q <= qlim) out.push_back({idx, o->order64 ? G.z : (double)G.z32, G.gid, q, dx, dy});
+        if (q > qlim) continue;
+        // FP32 error bound of q at this pixel: centre error, factored-form coefficient, rounding
+        const double t = dx - (G.cov[0][1] / G.cov[1][1]) * dy;
+        const double dq = 2 * (std::fabs(G.Q[0][0] * dx + G.Q[0][1] * dy) * G.du + std::fabs(G.Q[0][1] * dx + G.Q[1][1] * dy) * G.dv) +
+                          2 * G.Q[0][0] * std::fabs(t * dy) * G.dqb + 32 * g32 * q + 1e-9;
+        out.push_back({idx, o->order64 ? G.z : (double)G.z32, G.gid, q, dx, dy, dq});
     }
     std::sort(out.begin(), out.end(), [](const Cand& a, const Cand& b) {
         return a.key < b.key || (a.key == b.key && a.gid < b.gid); });
@@ -350,6 +380,7 @@ struct PixelResult {
     std::vector<Leaf> alts;
     double tol_rgb = 0, tol_d = 0;
     bool ambiguous = false;
+    int64_t amb_kind[4] = {0, 0, 0, 0};   // near, ellipse, alpha, transmittance
     uint64_t hash = 1469598103934665603ull;
 };
 
@@ -374,18 +405,22 @@ struct Compositor {
     void widen(double T) { R->tol_rgb += T * Mc; R->tol_d += T * Mz; }
 
     void run(const std::vector<Cand>& order, size_t pos, double T, double C0, double C1, double C2, double D,
-             int flips, bool primary) {
+             int flips, bool primary, double dT) {
         const double eps = o->eps_rel;
+        const double g32 = 5.9604644775390625e-08;
         for (; pos < order.size(); ++pos) {
             const Cand& cd = order[pos];
             const Geo& G = V.geo[cd.idx];
             const double a_raw = G.opac * std::exp(-0.5 * cd.q);
             const double alpha = std::min(o->alpha_max, a_raw);
             const double Tn = T * (1.0 - alpha);
+            // relative FP32 error bounds of alpha and of T after this Gaussian
+            const double da = (a_raw > o->alpha_max) ? 4 * g32 : 0.5 * cd.dq + (8 + 1.2 * std::fabs(G.logit) + 0.6 * cd.q) * g32;
+            const double dTn = dT + alpha / (1.0 - alpha) * da + 2 * g32;
             const bool d[4] = {G.present, cd.q <= o->q_max, alpha >= o->alpha_min, Tn < o->t_min};
-            const bool amb[4] = {G.near_amb, std::fabs(cd.q - o->q_max) <= eps * o->q_max,
-                                 std::fabs(alpha - o->alpha_min) <= eps * o->alpha_min,
-                                 std::fabs(Tn - o->t_min) <= eps * o->t_min};
+            const bool amb[4] = {G.near_amb, std::fabs(cd.q - o->q_max) <= 2 * cd.dq + eps * o->q_max,
+                                 std::fabs(alpha - o->alpha_min) <= 2 * alpha * da + eps * o->alpha_min,
+                                 std::fabs(Tn - o->t_min) <= 2 * Tn * dTn + eps * o->t_min};
             const Act act = action(d[0], d[1], d[2], d[3]);
             for (int k = 0; k < 4; ++k) {
                 if (!amb[k]) continue;
@@ -394,13 +429,14 @@ struct Compositor {
                 const Act alt = action(f[0], f[1], f[2], f[3]);
                 if (alt == act) continue;
                 R->ambiguous = true;
+                if (primary) R->amb_kind[k]++;
                 if (flips >= o->max_flips) { widen(T); continue; }
-                if (alt == SKIP) run(order, pos + 1, T, C0, C1, C2, D, flips + 1, false);
+                if (alt == SKIP) run(order, pos + 1, T, C0, C1, C2, D, flips + 1, false, dT);
                 else if (alt == STOP) emit(T, C0, C1, C2, D, false);
                 else {
                     const double w = alpha * T;
                     run(order, pos + 1, Tn, C0 + w * G.rgb[0], C1 + w * G.rgb[1], C2 + w * G.rgb[2], D + w * G.z,
-                        flips + 1, false);
+                        flips + 1, false, dTn);
                 }
             }
             if (primary) {
@@ -414,6 +450,7 @@ struct Compositor {
             const double w = alpha * T;
             C0 += w * G.rgb[0]; C1 += w * G.rgb[1]; C2 += w * G.rgb[2]; D += w * G.z;
             T = Tn;
+            dT = dTn;
         }
         emit(T, C0, C1, C2, D, primary);
     }
@@ -496,7 +533,8 @@ int64_t oracle_project_view(const oracle_scene* s, const oracle_opts* o, int e, 
 // tol_rgb/tol_d [H*W]: extra tolerance from flips beyond max_flips.  n_alt [H*W]: number
 // of alternative branches of each pixel; alt [alt_cap*5] receives them (r,g,b,d,a) in pixel
 // order.  stats[0] = alternatives needed, stats[1] = ambiguous pixels, stats[2] = decision
-// hash (as bits), stats[3] = instances projected.  Returns 0, or -1 on bad arguments, or 1 if
+// hash (as bits), stats[3] = instances projected, stats[4..7] = ambiguous decisions on the
+// primary branch by kind (near plane, ellipse, alpha_min, t_min); stats needs 8 entries.  Returns 0, or -1 on bad arguments, or 1 if
 // alt_cap was too small (outputs other than alt are still complete).
 int oracle_render_view(const oracle_scene* s, const oracle_opts* o, int e, int c,
                        double* rgb, double* depth, double* alpha, double* tol_rgb, double* tol_d,
@@ -509,6 +547,7 @@ int oracle_render_view(const oracle_scene* s, const oracle_opts* o, int e, int c
     std::vector<std::vector<Leaf>> row_alts(H);
     std::vector<int64_t> row_amb(H, 0);
     std::vector<uint64_t> row_hash(H, 0);
+    std::vector<int64_t> row_kind((size_t)H * 4, 0);
     parallel_for(H, n_threads(o), [&](int64_t y, int) {
         std::vector<std::vector<int>> cols(W);
         cols_pool(V, o, rows[y], cols);
@@ -524,7 +563,7 @@ int oracle_render_view(const oracle_scene* s, const oracle_opts* o, int e, int c
             }
             PixelResult R;
             Compositor comp{V, o, Mc, Mz, &R};
-            comp.run(cand, 0, 1.0, 0, 0, 0, 0, 0, true);
+            comp.run(cand, 0, 1.0, 0, 0, 0, 0, 0, true, 0.0);
             const int64_t p = y * W + x;
             rgb[p * 3 + 0] = R.primary.r; rgb[p * 3 + 1] = R.primary.g; rgb[p * 3 + 2] = R.primary.b;
             depth[p] = R.primary.d; if (alpha) alpha[p] = R.primary.a;
@@ -533,13 +572,17 @@ int oracle_render_view(const oracle_scene* s, const oracle_opts* o, int e, int c
             if (n_alt) n_alt[p] = (int32_t)R.alts.size();
             for (auto& L : R.alts) row_alts[y].push_back(L);
             row_amb[y] += R.ambiguous;
+            for (int k = 0; k < 4; ++k) row_kind[(size_t)y * 4 + k] += R.amb_kind[k];
             hsum += mix(R.hash, (uint64_t)p);
         }
         row_hash[y] = hsum;
     });
     int64_t need = 0, amb = 0; uint64_t h = 0;
     for (int y = 0; y < H; ++y) { need += (int64_t)row_alts[y].size(); amb += row_amb[y]; h += row_hash[y]; }
-    if (stats) { stats[0] = need; stats[1] = amb; std::memcpy(&stats[2], &h, 8); stats[3] = (int64_t)V.geo.size(); }
+    if (stats) {
+        stats[0] = need; stats[1] = amb; std::memcpy(&stats[2], &h, 8); stats[3] = (int64_t)V.geo.size();
+        for (int k = 0; k < 4; ++k) { int64_t s = 0; for (int y = 0; y < H; ++y) s += row_kind[(size_t)y * 4 + k]; stats[4 + k] = s; }
+    }
     if (alt && need <= alt_cap) {
         int64_t k = 0;
         for (int y = 0; y < H; ++y) for (auto& L : row_alts[y]) {

@@ -57,7 +57,7 @@ class OracleOptions:
     q_max: float = 9.0
     guard: float = 1.3
     bg: tuple = (0.0, 0.0, 0.0)
-    eps_rel: float = 1e-5
+    eps_rel: float = 1e-7
     max_flips: int = 4
     nthreads: int = 0
     bruteforce: int = 0
@@ -112,7 +112,7 @@ class _Packed:
         sh = np.zeros((G, 16, 3), f8)
         off = 0
         for nd in nodes:
-            s = np.asarray(get(nd, "sh"), f8).reshape(nd.n, -1, 3)
+            s = np.asarray(get(nd, "sh"), f8).reshape(nd.n, (nd.sh_degree + 1) ** 2, 3)
             sh[off:off + nd.n, : s.shape[1]] = s
             off += nd.n
         self.sh = sh
@@ -166,6 +166,7 @@ class ViewResult:
     ambiguous_pixels: int
     decision_hash: int
     instances: int
+    ambiguous_by_kind: dict = field(default=None)
     alt_offsets: np.ndarray = field(default=None)
 
     def alternatives(self, p: int) -> np.ndarray:
@@ -181,7 +182,7 @@ def render_view(scene, e: int, c: int, opts: OracleOptions | None = None, packed
     W, H = (int(x) for x in scene.cam_res[e, c])
     rgb = np.zeros((H, W, 3)); depth = np.zeros((H, W)); alpha = np.zeros((H, W))
     tr = np.zeros((H, W)); td = np.zeros((H, W)); na = np.zeros((H, W), np.int32)
-    stats = np.zeros(4, np.int64)
+    stats = np.zeros(8, np.int64)
     cap = max(1024, W * H // 8)
     alt = np.zeros((cap, 5))
     rc = lib.oracle_render_view(C.byref(pk.c), C.byref(o), e, c, _p(rgb), _p(depth), _p(alpha), _p(tr), _p(td),
@@ -193,8 +194,9 @@ def render_view(scene, e: int, c: int, opts: OracleOptions | None = None, packed
                                     _p(na), _p(alt), cap, _p(stats))
     if rc != 0:
         raise ValueError(f"oracle_render_view failed ({rc})")
+    kinds = dict(zip(("near", "ellipse", "alpha", "transmittance"), (int(x) for x in stats[4:8])))
     return ViewResult(rgb, depth, alpha, tr, td, na, alt[: int(stats[0])], int(stats[1]),
-                      int(np.uint64(stats[2].view(np.uint64))), int(stats[3]))
+                      int(np.uint64(stats[2].view(np.uint64))), int(stats[3]), kinds)
 
 
 def _grad_buffers(pk, scene):

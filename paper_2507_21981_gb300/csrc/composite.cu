@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(256) k_composite(const ViewDesc* __restrict__ 
         for (int j = 0; j < cnt && !done; ++j) {
             const float4 a = s0[j], c = s1[j];
             const float dx = fx - a.x, dy = fy - a.y;
-            const float q = fmaf(c.x * dx, dx, fmaf(2.f * c.y * dx, dy, c.z * dy * dy));
+            const float t = fmaf(c.y, dy, dx);
+            const float q = fmaf(c.x * t, t, c.z * dy * dy);
             if (q > P.q_max) continue;
             const float alpha = fminf(P.alpha_max, a.z * __expf(-0.5f * q));
             if (alpha < P.alpha_min) continue;

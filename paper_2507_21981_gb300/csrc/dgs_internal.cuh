@@ -66,7 +66,8 @@ struct Params {
 };
 
 // Projected instance as stored for compositing: 48 bytes.
-//   r0 = (u, v, opacity, z), r1 = (conic a, b, c, gid bits), r2 = (r, g, b, view bits)
+//   r0 = (u, v, opacity, z), r1 = (qa, qb, qc, gid bits), r2 = (r, g, b, view bits), with
+//   d^T conic d = qa (dx + qb dy)^2 + qc dy^2
 struct Record {
     float4 r0, r1, r2;
 };

@@ -76,8 +76,8 @@ __global__ void k_setup_views(const ViewDesc* __restrict__ views, int n_views, c
 // ------------------------------------------------------------------ per-Gaussian geometry
 struct Gauss {
     float mx, my, mz;
-    float s00, s01, s02, s11, s12, s22;   // node-frame 3D covariance
-    float opac;
+    float r00, r01, r02, r10, r11, r12, r20, r21, r22;   // rotation of the unit quaternion
+    float s0, s1, s2;                                      // squared scales exp(2 log s)
 };
 
 template <int DT>
@@ -85,35 +85,34 @@ __device__ __forceinline__ void load_geometry(const NodeDesc& nd, int64_t i, Gau
     g.mx = __ldg(nd.mean + i * 3 + 0);
     g.my = __ldg(nd.mean + i * 3 + 1);
     g.mz = __ldg(nd.mean + i * 3 + 2);
-    const float sx = __expf(2.f * ld_attr<DT>(nd.log_scale, i * 3 + 0));
-    const float sy = __expf(2.f * ld_attr<DT>(nd.log_scale, i * 3 + 1));
-    const float sz = __expf(2.f * ld_attr<DT>(nd.log_scale, i * 3 + 2));
+    g.s0 = __expf(2.f * ld_attr<DT>(nd.log_scale, i * 3 + 0));
+    g.s1 = __expf(2.f * ld_attr<DT>(nd.log_scale, i * 3 + 1));
+    g.s2 = __expf(2.f * ld_attr<DT>(nd.log_scale, i * 3 + 2));
     float w = ld_attr<DT>(nd.quat, i * 4 + 0), x = ld_attr<DT>(nd.quat, i * 4 + 1);
     float y = ld_attr<DT>(nd.quat, i * 4 + 2), z = ld_attr<DT>(nd.quat, i * 4 + 3);
     const float inv = rsqrtf(w * w + x * x + y * y + z * z);
     w *= inv; x *= inv; y *= inv; z *= inv;
-    // rotation matrix of the unit quaternion (w,x,y,z)
-    const float r00 = 1.f - 2.f * (y * y + z * z), r01 = 2.f * (x * y - w * z), r02 = 2.f * (x * z + w * y);
-    const float r10 = 2.f * (x * y + w * z), r11 = 1.f - 2.f * (x * x + z * z), r12 = 2.f * (y * z - w * x);
-    const float r20 = 2.f * (x * z - w * y), r21 = 2.f * (y * z + w * x), r22 = 1.f - 2.f * (x * x + y * y);
-    // Sigma = R diag(s^2) R^T
-    g.s00 = r00 * r00 * sx + r01 * r01 * sy + r02 * r02 * sz;
-    g.s01 = r00 * r10 * sx + r01 * r11 * sy + r02 * r12 * sz;
-    g.s02 = r00 * r20 * sx + r01 * r21 * sy + r02 * r22 * sz;
-    g.s11 = r10 * r10 * sx + r11 * r11 * sy + r12 * r12 * sz;
-    g.s12 = r10 * r20 * sx + r11 * r21 * sy + r12 * r22 * sz;
-    g.s22 = r20 * r20 * sx + r21 * r21 * sy + r22 * r22 * sz;
+    g.r00 = 1.f - 2.f * (y * y + z * z); g.r01 = 2.f * (x * y - w * z); g.r02 = 2.f * (x * z + w * y);
+    g.r10 = 2.f * (x * y + w * z); g.r11 = 1.f - 2.f * (x * x + z * z); g.r12 = 2.f * (y * z - w * x);
+    g.r20 = 2.f * (x * z - w * y); g.r21 = 2.f * (y * z + w * x); g.r22 = 1.f - 2.f * (x * x + y * y);
 }
 
 struct Splat {
     float u, v, z;
-    float a, b, c;        // conic (inverse 2D covariance)
+    float a, b, c;        // conic (inverse 2D covariance), used for binning
+    float qa, qb, qc;     // q = qa (dx + qb dy)^2 + qc dy^2, used for compositing
     int tx0, tx1, ty0, ty1;
     int x0, x1, y0, y1;   // pixel bounds of the ellipse box, clamped to the image
 };
 
 // EWA projection of one Gaussian into one view.  Returns false if culled (near plane,
 // degenerate covariance or off screen).
+//
+// Numerics: with A = J M_R R (2x3) and S = diag(s^2), Sigma2D = A S A^T + lowpass I.  Its
+// entries are sums of products with the positive weights s_k^2, and its determinant is
+// evaluated by Cauchy-Binet as a sum of positive terms, so thin (flattened) Gaussians do not
+// lose their small eigenvalue to cancellation.  The quadratic form is stored factored,
+// q = (cyy/det) (dx - (cxy/cyy) dy)^2 + dy^2 / cyy, a sum of two non-negative terms.
 __device__ __forceinline__ bool project(const Gauss& g, const VNode& vn, const ViewDesc& vd, const Params& P, Splat& s) {
     const float* M = vn.M;
     // depth key: binary32, one rounding per operation, fixed order
@@ -129,22 +128,31 @@ __device__ __forceinline__ bool project(const Gauss& g, const VNode& vn, const V
     const float fxz = vd.fx * iz, fyz = vd.fy * iz;
     const float t00 = fxz * fmaf(-xc, M[8], M[0]), t01 = fxz * fmaf(-xc, M[9], M[1]), t02 = fxz * fmaf(-xc, M[10], M[2]);
     const float t10 = fyz * fmaf(-yc, M[8], M[4]), t11 = fyz * fmaf(-yc, M[9], M[5]), t12 = fyz * fmaf(-yc, M[10], M[6]);
-    // Sigma * T0, Sigma * T1
-    const float a0 = g.s00 * t00 + g.s01 * t01 + g.s02 * t02;
-    const float a1 = g.s01 * t00 + g.s11 * t01 + g.s12 * t02;
-    const float a2 = g.s02 * t00 + g.s12 * t01 + g.s22 * t02;
-    const float b0 = g.s00 * t10 + g.s01 * t11 + g.s02 * t12;
-    const float b1 = g.s01 * t10 + g.s11 * t11 + g.s12 * t12;
-    const float b2 = g.s02 * t10 + g.s12 * t11 + g.s22 * t12;
-    const float cxx = t00 * a0 + t01 * a1 + t02 * a2 + P.lowpass;
-    const float cxy = t10 * a0 + t11 * a1 + t12 * a2;
-    const float cyy = t10 * b0 + t11 * b1 + t12 * b2 + P.lowpass;
-    const float det = cxx * cyy - cxy * cxy;
-    if (!(det > 0.f)) return false;
+    // A = T R
+    const float a00 = fmaf(t00, g.r00, fmaf(t01, g.r10, t02 * g.r20));
+    const float a01 = fmaf(t00, g.r01, fmaf(t01, g.r11, t02 * g.r21));
+    const float a02 = fmaf(t00, g.r02, fmaf(t01, g.r12, t02 * g.r22));
+    const float a10 = fmaf(t10, g.r00, fmaf(t11, g.r10, t12 * g.r20));
+    const float a11 = fmaf(t10, g.r01, fmaf(t11, g.r11, t12 * g.r21));
+    const float a12 = fmaf(t10, g.r02, fmaf(t11, g.r12, t12 * g.r22));
+    const float sa0 = g.s0 * a00, sa1 = g.s1 * a01, sa2 = g.s2 * a02;
+    const float cxx0 = fmaf(sa0, a00, fmaf(sa1, a01, sa2 * a02));
+    const float cxy = fmaf(sa0, a10, fmaf(sa1, a11, sa2 * a12));
+    const float cyy0 = fmaf(g.s0 * a10, a10, fmaf(g.s1 * a11, a11, g.s2 * a12 * a12));
+    const float m01 = fmaf(a00, a11, -a01 * a10), m02 = fmaf(a00, a12, -a02 * a10), m12 = fmaf(a01, a12, -a02 * a11);
+    const float det0 = fmaf(g.s0 * g.s1 * m01, m01, fmaf(g.s0 * g.s2 * m02, m02, g.s1 * g.s2 * m12 * m12));
+    const float lp = P.lowpass;
+    const float cxx = cxx0 + lp, cyy = cyy0 + lp;
+    const float det = fmaf(lp, cxx0 + cyy0 + lp, det0);
+    if (!(det > 0.f) || !(cyy > 0.f)) return false;
     const float idet = 1.f / det;
     s.a = cyy * idet;
     s.b = -cxy * idet;
     s.c = cxx * idet;
+    const float icyy = 1.f / cyy;
+    s.qa = s.a;
+    s.qb = -cxy * icyy;
+    s.qc = icyy;
     s.u = fmaf(vd.fx, xr, vd.cx);
     s.v = fmaf(vd.fy, yr, vd.cy);
     s.z = z;
@@ -357,7 +365,7 @@ __device__ __forceinline__ void emit_chunk(const NodeDesc& nd, int c, int lane, 
     const float op = 1.f / (1.f + __expf(-__ldg(nd.opac + i)));
     Record R;
     R.r0 = make_float4(s.u, s.v, op, s.z);
-    R.r1 = make_float4(s.a, s.b, s.c, __uint_as_float((uint32_t)(nd.gbase + i)));
+    R.r1 = make_float4(s.qa, s.qb, s.qc, __uint_as_float((uint32_t)(nd.gbase + i)));
     R.r2 = make_float4(rgb[0], rgb[1], rgb[2], __int_as_float(view));
     rec[r] = R;
     uint32_t zk = __float_as_uint(s.z) - P.zbase;

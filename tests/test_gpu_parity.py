@@ -110,3 +110,19 @@ def test_all_transparent_scene_gives_background():
     ds, out, st, _ = _render(sc, "batched", bg=(0.1, 0.2, 0.3))
     rgb, depth, alpha = out
     assert np.allclose(rgb, [0.1, 0.2, 0.3], atol=1e-7) and np.all(depth == 0) and np.all(alpha == 0)
+
+
+def test_config2_full_size_sampled_views():
+    """Full workload of the benchmark (64 envs x 2 cams 640x480, 1.08M Gaussians); the oracle
+    checks two seeded sampled views pixel by pixel."""
+    sc = S.config2(seed=1)
+    ds, out, st, _ = _render(sc, "batched")
+    assert st["n_views"] == 128 and st["n_groups"] >= 1
+    views = sorted(int(v) for v in np.random.default_rng(7).choice(sc.n_views, 2, replace=False))
+    _check_views(sc, ds, out, views, packed=O.oracle._Packed(sc))
+
+
+def test_config4_full_view():
+    sc = S.config4(seed=1)
+    ds, out, st, _ = _render(sc, "batched")
+    _check_views(sc, ds, out, [0])
