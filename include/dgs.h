@@ -173,6 +173,37 @@ int dgs_kernel_times(const dgs_ctx* ctx, float* ms);
 /* Launches of library kernels queued by the most recent call. */
 int64_t dgs_last_launches(const dgs_ctx* ctx);
 
+/*
+ * dgs_render_noalloc -- dgs_render for callers that must not allocate GPU memory.  The paper
+ * has no counterpart: this is a deployment variant of the same batched render.
+ *
+ * Some callers cannot call cudaMalloc: a program whose device memory is owned by another
+ * framework's caching allocator, a control loop that cannot take the device-wide
+ * synchronisation that cudaMalloc/cudaFree may cause in the middle of a step, or code certified
+ * to allocate nothing after start-up.  This call allocates no device or pinned host memory:
+ * its workspace is a fixed 64 MiB array compiled into the library, present on every device
+ * that loads it until the process exits.
+ *
+ *   opt       options (NULL = defaults); mode and profile are ignored, the batched sequence runs
+ *             as a single view group.
+ *   the other arguments are those of dgs_render (caller-owned inputs and outputs).
+ *
+ * Returns DGS_ERR_CAPACITY, before its second phase is queued, when the batch's tables,
+ * projected records or tile pairs do not fit in the 64 MiB; DGS_ERR_INVALID_ARG for the cases
+ * dgs_render rejects; no error message is recorded (there is no context).  The first call on a
+ * device resolves the array's device address (cudaGetSymbolAddress) with that device current;
+ * make it before any stream capture begins.  All calls on a device share the array and leave
+ * their contents in it; each call clears what must start at zero.  Calls whose GPU work
+ * overlaps (other streams or host threads) race on the array: serialise them.  The call reads
+ * counts back once and synchronises `stream` before returning.
+ */
+int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes, int32_t n_nodes,
+                       const int32_t* env_node_ids, int32_t n_envs, int32_t max_nodes,
+                       const float* node_poses,
+                       const dgs_camera* cams, const int32_t* cams_per_env, int32_t max_cams,
+                       float* out_rgb, float* out_depth, float* out_alpha,
+                       const int64_t* view_pixel_offset, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,273 @@
+// dgs_render_noalloc: the batched render with all of its scratch in one fixed, statically
+// allocated device array, for callers that must not allocate GPU memory.
+//
+// Who needs it: a host program that runs inside another framework's memory manager (a
+// caching allocator that owns the device budget and forbids foreign cudaMalloc calls), a
+// control loop that cannot afford the device-wide synchronisation cudaFree and cudaMalloc may
+// imply in the middle of a step, or code certified to allocate nothing after start-up.  Such
+// a caller still passes its own inputs and outputs; everything else the render needs (tables,
+// counters, projected records, sort buffers, tile ranges) is carved out of g_scratch.
+//
+// Limits and sharing: g_scratch is kScratchBytes (64 MiB) on every device that loads the
+// library, held until the process exits.  A batch whose tables or tile pairs do not fit is
+// rejected with DGS_ERR_CAPACITY before any kernel is queued for its second phase.  Every
+// call on a device uses the same array and leaves its contents behind; the call clears what
+// must start at zero (error word, histograms, counters, look-back status, tile ranges).  Two
+// calls whose work overlaps on the GPU (different streams, or different host threads) race
+// on the array and corrupt each other's results: serialise them.
+//
+// Set-up: the device address of g_scratch is resolved once per device, by the first call
+// made with that device current (cudaGetSymbolAddress); make that first call before any
+// stream capture begins on the device.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+#include <algorithm>
+
+#include "dgs_internal.cuh"
+
+using namespace dgs;
+
+namespace {
+
+constexpr size_t kScratchBytes = 64ull << 20;
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_scratch_dev[kMaxDevices] = {};
+std::mutex g_scratch_mu;
+
+// Device address of g_scratch on the current device (resolved once per device).
+cudaError_t scratch_address(unsigned char** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_dev[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_dev[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_scratch_dev[dev]);
+    return cudaSuccess;
+}
+
+struct Carver {
+    unsigned char* base;
+    size_t used = 0;
+    bool ok = true;
+    template <class T>
+    T* take(size_t count) {
+        size_t at = (used + 255) / 256 * 256;
+        size_t bytes = sizeof(T) * std::max<size_t>(count, 1);
+        if (at + bytes > kScratchBytes) { ok = false; return nullptr; }
+        used = at + bytes;
+        return reinterpret_cast<T*>(base + at);
+    }
+};
+
+int bits_for_tiles(uint64_t n) {
+    int b = 0;
+    while (b < 63 && (1ull << b) < n) ++b;
+    return b;
+}
+
+}  // namespace
+
+extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes, int32_t n_nodes,
+                                  const int32_t* env_node_ids, int32_t n_envs, int32_t max_nodes,
+                                  const float* node_poses, const dgs_camera* cams, const int32_t* cams_per_env,
+                                  int32_t max_cams, float* out_rgb, float* out_depth, float* out_alpha,
+                                  const int64_t* view_pixel_offset, void* stream_) {
+    dgs_options o;
+    if (opt) o = *opt; else dgs_default_options(&o);
+    {
+        const int area = o.tile_w * o.tile_h;
+        if (o.tile_w < 1 || o.tile_h < 1 || (area != 64 && area != 128 && area != 256)) return DGS_ERR_INVALID_ARG;
+        if (!(o.z_near > 0) || !(o.q_max > 0) || !(o.guard > 0) || !(o.lowpass >= 0)) return DGS_ERR_INVALID_ARG;
+    }
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (n_nodes < 1 || !nodes || n_envs < 1 || max_nodes < 1 || max_cams < 1) return DGS_ERR_INVALID_ARG;
+    if (!env_node_ids || !cams || !cams_per_env || !node_poses || !out_rgb || !out_depth) return DGS_ERR_INVALID_ARG;
+    const int E = n_envs, K = max_nodes, C = max_cams;
+    // ---------------------------------------------------------------- host tables (as dgs_render)
+    std::vector<NodeDesc> nd(n_nodes);
+    int dtype_mask = 0;
+    int64_t chunk_total = 0, gbase = 0;
+    for (int k = 0; k < n_nodes; ++k) {
+        const dgs_node& n = nodes[k];
+        if (n.n < 0 || n.sh_degree < 0 || n.sh_degree > 3 || n.dtype < 0 || n.dtype > 2) return DGS_ERR_INVALID_ARG;
+        if (n.n > 0 && (!n.mean || !n.log_scale || !n.quat || !n.opacity_logit || !n.sh)) return DGS_ERR_INVALID_ARG;
+        nd[k] = NodeDesc{n.mean, n.log_scale, n.quat, n.opacity_logit, n.sh, n.n, gbase, n.sh_degree, n.dtype,
+                         (int32_t)chunk_total, (int32_t)((n.n + kChunk - 1) / kChunk)};
+        chunk_total += nd[k].nchunks;
+        gbase += n.n;
+        if (n.n > 0) dtype_mask |= 1 << n.dtype;
+    }
+    if (gbase >= (1ll << 32) || chunk_total >= (1ll << 31)) return DGS_ERR_INVALID_ARG;
+    std::vector<int> seen(n_nodes, -1);
+    for (int e = 0; e < E; ++e) {
+        for (int j = 0; j < K; ++j) {
+            const int k = env_node_ids[(int64_t)e * K + j];
+            if (k < -1 || k >= n_nodes) return DGS_ERR_INVALID_ARG;
+            if (k >= 0) { if (seen[k] == e) return DGS_ERR_INVALID_ARG; seen[k] = e; }
+        }
+        if (cams_per_env[e] < 0 || cams_per_env[e] > C) return DGS_ERR_INVALID_ARG;
+    }
+    std::vector<ViewDesc> views;
+    int64_t tiles_total = 0, pix_total = 0;
+    for (int e = 0; e < E; ++e)
+        for (int c = 0; c < cams_per_env[e]; ++c) {
+            const dgs_camera& cm = cams[(int64_t)e * C + c];
+            if (cm.width < 1 || cm.height < 1 || cm.width > 32768 || cm.height > 32768) return DGS_ERR_INVALID_ARG;
+            if (!(cm.fx > 0) || !(cm.fy > 0)) return DGS_ERR_INVALID_ARG;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double s = 0;
+                    for (int r = 0; r < 3; ++r) s += (double)cm.cam_from_world[r * 4 + a] * cm.cam_from_world[r * 4 + b];
+                    if (!(std::fabs(s - (a == b ? 1.0 : 0.0)) <= 1e-4)) return DGS_ERR_INVALID_ARG;
+                }
+            ViewDesc vd{};
+            vd.fx = cm.fx; vd.fy = cm.fy; vd.cx = cm.cx; vd.cy = cm.cy;
+            vd.limx = o.guard * 0.5f * (float)cm.width / cm.fx;
+            vd.limy = o.guard * 0.5f * (float)cm.height / cm.fy;
+            vd.W = cm.width; vd.H = cm.height;
+            vd.tiles_x = (cm.width + o.tile_w - 1) / o.tile_w;
+            vd.tiles_y = (cm.height + o.tile_h - 1) / o.tile_h;
+            vd.env = e;
+            vd.tile_base = (int32_t)tiles_total;
+            std::memcpy(vd.cam, cm.cam_from_world, sizeof(vd.cam));
+            tiles_total += (int64_t)vd.tiles_x * vd.tiles_y;
+            if (tiles_total >= (1ll << 31)) return DGS_ERR_INVALID_ARG;
+            vd.pix_off = view_pixel_offset ? view_pixel_offset[views.size()] : pix_total;
+            if (vd.pix_off < 0) return DGS_ERR_INVALID_ARG;
+            pix_total += (int64_t)cm.width * cm.height;
+            views.push_back(vd);
+        }
+    const int V = (int)views.size();
+    if (V == 0) return DGS_OK;
+    std::vector<int32_t> slot_node((size_t)V * K, -1);
+    std::vector<int64_t> vnode_tab((size_t)V * K, 0), view_tab(V + 1, 0);
+    std::vector<std::vector<NodeView>> per_node(n_nodes);
+    int64_t tab = 0;
+    for (int v = 0; v < V; ++v) {
+        const int e = views[v].env;
+        std::vector<std::pair<int, int>> present;
+        for (int j = 0; j < K; ++j) {
+            const int k = env_node_ids[(int64_t)e * K + j];
+            slot_node[(size_t)v * K + j] = k;
+            if (k >= 0) present.push_back({k, j});
+        }
+        std::sort(present.begin(), present.end());
+        view_tab[v] = tab;
+        for (auto& pk : present) {
+            vnode_tab[(size_t)v * K + pk.second] = tab;
+            tab += nd[pk.first].nchunks;
+            per_node[pk.first].push_back({v, pk.second});
+        }
+    }
+    view_tab[V] = tab;
+    const int64_t T = tab;
+    std::vector<int32_t> nv_off(n_nodes + 1, 0);
+    std::vector<NodeView> nv;
+    for (int k = 0; k < n_nodes; ++k) {
+        nv_off[k] = (int32_t)nv.size();
+        nv.insert(nv.end(), per_node[k].begin(), per_node[k].end());
+    }
+    nv_off[n_nodes] = (int32_t)nv.size();
+
+    // ---------------------------------------------------------------- phase 1 scratch
+    unsigned char* base = nullptr;
+    if (scratch_address(&base) != cudaSuccess) return DGS_ERR_CUDA;
+    Carver cv{base};
+    NodeDesc* d_nodes = cv.take<NodeDesc>(n_nodes);
+    ViewDesc* d_views = cv.take<ViewDesc>(V);
+    int32_t* d_slot = cv.take<int32_t>((size_t)V * K);
+    int64_t* d_vtab = cv.take<int64_t>((size_t)V * K);
+    NodeView* d_nv = cv.take<NodeView>(nv.size());
+    int32_t* d_nvoff = cv.take<int32_t>(n_nodes + 1);
+    int64_t* d_viewtab = cv.take<int64_t>(V + 1);
+    VNode* d_vnodes = cv.take<VNode>((size_t)V * K);
+    uint32_t* d_err = cv.take<uint32_t>(16);
+    uint2* d_counts = cv.take<uint2>(T);
+    uint32_t* d_inst_off = cv.take<uint32_t>(T + 1);
+    uint64_t* d_pair_off = cv.take<uint64_t>(T + 1);
+    const int64_t n_parts = (T + 4095) / 4096;
+    ulonglong2* d_parts = cv.take<ulonglong2>(n_parts + 1);
+    uint64_t* d_rb = cv.take<uint64_t>(2 * (V + 1) + 1);
+    if (!cv.ok) return DGS_ERR_CAPACITY;
+
+#define NA_CUDA(x) do { if ((x) != cudaSuccess) return DGS_ERR_CUDA; } while (0)
+    // pageable copies: the runtime stages them, nothing is allocated here
+    NA_CUDA(cudaMemcpyAsync(d_nodes, nd.data(), sizeof(NodeDesc) * n_nodes, cudaMemcpyHostToDevice, stream));
+    NA_CUDA(cudaMemcpyAsync(d_views, views.data(), sizeof(ViewDesc) * V, cudaMemcpyHostToDevice, stream));
+    NA_CUDA(cudaMemcpyAsync(d_slot, slot_node.data(), sizeof(int32_t) * V * K, cudaMemcpyHostToDevice, stream));
+    NA_CUDA(cudaMemcpyAsync(d_vtab, vnode_tab.data(), sizeof(int64_t) * V * K, cudaMemcpyHostToDevice, stream));
+    if (!nv.empty()) NA_CUDA(cudaMemcpyAsync(d_nv, nv.data(), sizeof(NodeView) * nv.size(), cudaMemcpyHostToDevice, stream));
+    NA_CUDA(cudaMemcpyAsync(d_nvoff, nv_off.data(), sizeof(int32_t) * (n_nodes + 1), cudaMemcpyHostToDevice, stream));
+    NA_CUDA(cudaMemcpyAsync(d_viewtab, view_tab.data(), sizeof(int64_t) * (V + 1), cudaMemcpyHostToDevice, stream));
+    NA_CUDA(cudaMemsetAsync(d_err, 0, 64, stream));
+
+    Params P{};
+    P.z_near = o.z_near; P.lowpass = o.lowpass; P.alpha_min = o.alpha_min; P.alpha_max = o.alpha_max;
+    P.t_min = o.t_min; P.q_max = o.q_max; P.guard = o.guard;
+    P.bg0 = o.bg[0]; P.bg1 = o.bg[1]; P.bg2 = o.bg[2];
+    P.qbin = o.q_max * 1.001f + 1e-3f;
+    P.tile_w = o.tile_w; P.tile_h = o.tile_h;
+    P.exact_tile_test = o.exact_tile_test;
+    P.tile0 = 0;
+    P.err = d_err;
+    { uint32_t b; std::memcpy(&b, &o.z_near, 4); P.zbase = b & 0x7F800000u; }
+    int64_t launches = 0;
+    Launch L{stream, &launches};
+    launch_setup_views(L, d_views, V, node_poses, d_slot, K, d_vnodes, d_vtab, d_err);
+    launch_count(L, dtype_mask, d_nodes, n_nodes, d_views, d_vnodes, K, d_nv, d_nvoff, (int)chunk_total, P, 0, V, true,
+                 nullptr, 0, d_counts);
+    launch_scan(L, d_counts, T, d_inst_off, d_pair_off, d_parts, n_parts + 1);
+    // one view group: read back the grand totals and the error word
+    NA_CUDA(cudaMemsetAsync(d_rb, 0, sizeof(uint64_t) * 3, stream));
+    NA_CUDA(cudaMemcpyAsync(d_rb, d_inst_off + T, sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream));
+    NA_CUDA(cudaMemcpyAsync(d_rb + 1, d_pair_off + T, sizeof(uint64_t), cudaMemcpyDeviceToDevice, stream));
+    NA_CUDA(cudaMemcpyAsync(d_rb + 2, d_err, sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream));
+    uint64_t h_rb[3] = {0, 0, 0};
+    NA_CUDA(cudaMemcpyAsync(h_rb, d_rb, sizeof(uint64_t) * 3, cudaMemcpyDeviceToHost, stream));
+    NA_CUDA(cudaGetLastError());
+    NA_CUDA(cudaStreamSynchronize(stream));
+    const uint64_t n_vis = h_rb[0] & 0xFFFFFFFFull, n_pairs = h_rb[1];
+    if ((uint32_t)h_rb[2] & kErrPose) return DGS_ERR_INVALID_ARG;
+    if (n_pairs > kMaxPairs) return DGS_ERR_CAPACITY;
+
+    // ---------------------------------------------------------------- phase 2 scratch
+    Record* d_rec = cv.take<Record>(n_vis);
+    uint64_t* d_k0 = cv.take<uint64_t>(n_pairs);
+    uint64_t* d_k1 = cv.take<uint64_t>(n_pairs);
+    uint32_t* d_v0 = cv.take<uint32_t>(n_pairs);
+    uint32_t* d_v1 = cv.take<uint32_t>(n_pairs);
+    uint32_t* d_hist = cv.take<uint32_t>(256 * 8);
+    uint32_t* d_cnt = cv.take<uint32_t>(8);
+    uint32_t* d_status = cv.take<uint32_t>(sort_status_words((uint32_t)std::max<uint64_t>(n_pairs, 1)));
+    uint2* d_ranges = cv.take<uint2>((size_t)tiles_total);
+    if (!cv.ok) return DGS_ERR_CAPACITY;
+    launch_emit(L, dtype_mask, d_nodes, n_nodes, d_views, d_vnodes, K, d_nv, d_nvoff, (int)chunk_total, P, 0, V, true,
+                nullptr, 0, d_inst_off, d_pair_off, 0u, 0ull, d_rec, d_k0, d_v0);
+    uint64_t* skeys;
+    uint32_t* svals;
+    const int bits = kZBits + std::max(1, bits_for_tiles((uint64_t)tiles_total));
+    if (bits > 64) return DGS_ERR_CAPACITY;
+    launch_sort(L, d_k0, d_v0, d_k1, d_v1, (uint32_t)n_pairs, bits, d_hist, d_status, d_cnt, d_err, &skeys, &svals,
+                nullptr, nullptr);
+    launch_ranges(L, skeys, (uint32_t)n_pairs, d_ranges, (int)tiles_total);
+    launch_composite(L, d_views, 0, V, (int)tiles_total, d_ranges, svals, d_rec, P, out_rgb, out_depth, out_alpha);
+    uint32_t h_err = 0;
+    NA_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+    NA_CUDA(cudaGetLastError());
+    NA_CUDA(cudaStreamSynchronize(stream));
+    if (h_err & kErrTimeout) return DGS_ERR_TIMEOUT;
+    if (h_err & kErrMismatch) return DGS_ERR_CUDA;
+    if (h_err & kErrPose) return DGS_ERR_INVALID_ARG;
+    return DGS_OK;
+#undef NA_CUDA
+}

@@ -47,7 +47,8 @@ class dgs_stats(C.Structure):
 
 
 EXPORTED = ("dgs_default_options", "dgs_context_create", "dgs_context_destroy", "dgs_last_error",
-            "dgs_workspace_query", "dgs_render", "dgs_last_stats", "dgs_kernel_times", "dgs_last_launches")
+            "dgs_workspace_query", "dgs_render", "dgs_last_stats", "dgs_kernel_times", "dgs_last_launches",
+            "dgs_render_noalloc")
 
 _lib = None
 _lock = threading.Lock()
@@ -89,6 +90,9 @@ def load(path: str | None = None) -> C.CDLL:
         lib.dgs_kernel_times.argtypes = [vp, C.POINTER(C.c_float)]
         lib.dgs_last_launches.restype = C.c_int64
         lib.dgs_last_launches.argtypes = [vp]
+        lib.dgs_render_noalloc.restype = C.c_int
+        lib.dgs_render_noalloc.argtypes = [C.POINTER(dgs_options), C.POINTER(dgs_node), i32, vp, i32, i32, vp,
+                                           C.POINTER(dgs_camera), vp, i32, vp, vp, vp, vp, vp]
         if path is None:
             _lib = lib
         return lib
@@ -157,3 +161,14 @@ def dgs_kernel_times(ctx) -> dict:
 
 def dgs_last_launches(ctx) -> int:
     return int(load().dgs_last_launches(ctx))
+
+
+def dgs_render_noalloc(opt, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env,
+                       max_cams, out_rgb, out_depth, out_alpha, view_pixel_offset, stream) -> int:
+    """Direct call of dgs_render_noalloc (no device or pinned memory is allocated by the
+    library; its workspace is a fixed 64 MiB device array).  Arguments as dgs_render, with a
+    dgs_options structure (or None for the defaults) in place of the context."""
+    return load().dgs_render_noalloc(C.byref(opt) if opt is not None else None, nodes, int(n_nodes),
+                                     _ptr(env_node_ids), int(n_envs), int(max_nodes), _ptr(node_poses), cams,
+                                     _ptr(cams_per_env), int(max_cams), _ptr(out_rgb), _ptr(out_depth),
+                                     _ptr(out_alpha), _ptr(view_pixel_offset), stream)
