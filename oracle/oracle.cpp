@@ -8,9 +8,9 @@
 // What it computes (the plain definition the tile-binned GPU method must reproduce):
 //   * Sec. III-B (Asset Formatting): every env holds a background node plus interactive
 //     nodes; a node's Gaussians move rigidly with its world_from_node pose.
-//   * Sec. III-A (Renderer): the native 3DGS pipeline -- per-Gaussian EWA "splatting" of the
-//     3D covariance to a 2D conic, spherical-harmonics colour evaluation, depth ordering
-//     ("sorting") and front-to-back alpha-blending.
+//   * Sec. III-A (Renderer): the native 3DGS pipeline -- per-Gaussian EWA splatting of the
+//     3D covariance to a 2D conic, spherical-harmonics colour evaluation, depth ordering and
+//     front-to-back alpha-blending.
 //   * Sec. III-C (Sensor): RGB and depth are both produced by alpha-compositing, the colour
 //     and the camera-space z of the intersected Gaussians respectively.
 // For every pixel the oracle takes every Gaussian (of every node present in the env) whose

@@ -1,7 +1,7 @@
 // Stable LSD radix sort of (64-bit key, 32-bit value) pairs in the onesweep style (kernel K3).
 //
-// Sec. III-A: the 3DGS rasterizer orders the (tile, depth) pairs of every view by "efficient
-// sorting" before blending.  Keys are (global tile << 28) | depth-key, values the instance
+// Sec. III-A: the 3DGS rasterizer orders the (tile, depth) pairs of every view with a fast
+// GPU sort before blending.  Keys are (global tile << 28) | depth-key, values the instance
 // index; emission in global-id order plus stability breaks equal depths by id.
 //
 // Structure: one upfront pass builds the 256-bin histograms of every digit at once; then
