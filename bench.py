@@ -142,6 +142,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--envs", type=int, default=64, help="envs per rank (64 = the benchmark workload)")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="time the batched render only (no e2e, plain or CPU legs): small profiling runs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -158,7 +161,7 @@ def main():
     from paper_2507_21981_gb300 import scenes
     from paper_2507_21981_gb300.render import DeviceScene, Renderer
 
-    sc = scenes.config2(seed=1 + rank)
+    sc = scenes.config2(seed=1 + rank, n_envs=args.envs)
     ds = DeviceScene(sc, device=dev)
     stream = torch.cuda.current_stream(dev)
     px_per_step = ds.n_pixels
@@ -190,6 +193,12 @@ def main():
         barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     stats = rb.stats()
+    if args.only_batched:
+        if rank == 0:
+            print(json.dumps({"value_mpix_s": px_per_step / (ms / 1e3) / 1e6, "ms_per_step": ms, "envs": args.envs,
+                              "kernel_ms_per_step": {k: v / args.steps for k, v in ktimes.items()},
+                              "render_stats": stats}))
+        return 0
     if world > 1:
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)

@@ -190,20 +190,75 @@ __device__ __forceinline__ bool ellipse_meets_rect(float a, float b, float c, fl
     return m <= qlim;
 }
 
-__device__ __forceinline__ bool tile_hit(const Splat& s, const ViewDesc& vd, const Params& P, int tx, int ty) {
-    if (!P.exact_tile_test) return true;
-    const int px0 = max(tx * P.tile_w, s.x0), px1 = min(tx * P.tile_w + P.tile_w - 1, s.x1);
-    const int py0 = max(ty * P.tile_h, s.y0), py1 = min(ty * P.tile_h + P.tile_h - 1, s.y1);
-    return ellipse_meets_rect(s.a, s.b, s.c, P.qbin, (float)px0 + 0.5f - s.u, (float)px1 + 0.5f - s.u,
-                              (float)py0 + 0.5f - s.v, (float)py1 + 0.5f - s.v);
+// Per-warp shared state of the cooperative tile enumeration: the splats of the warp's 32
+// lanes for the current view.
+struct WarpSplats {
+    float u[32], v[32], a[32], b[32], c[32];
+    int32_t tx0[32], ty0[32], tw[32], x0[32], x1[32], y0[32], y1[32];
+    uint32_t excl[32];     // exclusive prefix of the lanes' tile-rectangle areas
+    uint32_t zk[32];       // depth key of the lane's instance (emit only)
+    uint32_t rec[32];      // record index of the lane's instance (emit only)
+};
+
+__device__ __forceinline__ void stash_splat(WarpSplats& S, int lane, const Splat& s, uint32_t excl) {
+    S.u[lane] = s.u; S.v[lane] = s.v; S.a[lane] = s.a; S.b[lane] = s.b; S.c[lane] = s.c;
+    S.tx0[lane] = s.tx0; S.ty0[lane] = s.ty0; S.tw[lane] = s.tx1 - s.tx0 + 1;
+    S.x0[lane] = s.x0; S.x1[lane] = s.x1; S.y0[lane] = s.y0; S.y1[lane] = s.y1;
+    S.excl[lane] = excl;
 }
 
-__device__ __forceinline__ uint32_t count_tiles(const Splat& s, const ViewDesc& vd, const Params& P) {
-    if (!P.exact_tile_test) return (uint32_t)((s.tx1 - s.tx0 + 1) * (s.ty1 - s.ty0 + 1));
-    uint32_t n = 0;
-    for (int ty = s.ty0; ty <= s.ty1; ++ty)
-        for (int tx = s.tx0; tx <= s.tx1; ++tx) n += tile_hit(s, vd, P, tx, ty);
-    return n;
+// Walks the union of the warp's tile rectangles, flattened in (lane, row-major tile) order,
+// 32 candidates at a time, and returns the number of (instance, tile) pairs whose tile the
+// instance's ellipse reaches.  With EMIT, pair j of the walk is written at pbase + j.  The
+// count and emit passes run this same walk, so they agree on every total and position.
+template <bool EMIT>
+__device__ __forceinline__ uint32_t walk_tiles(const WarpSplats& S, int lane, uint32_t total, const ViewDesc& vd,
+                                               const Params& P, uint64_t* __restrict__ keys,
+                                               uint32_t* __restrict__ vals, uint64_t pbase, uint64_t pend) {
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t count = 0;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t f = base + (uint32_t)lane;
+        bool hit = false;
+        int o = 0, tx = 0, ty = 0;
+        if (f < total) {
+            // owner: last lane whose rectangle starts at or before f
+            int lo = 0, hi = 31;
+#pragma unroll
+            for (int it = 0; it < 5; ++it) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (S.excl[mid] <= f) lo = mid; else hi = mid - 1;
+            }
+            o = lo;
+            const uint32_t r = f - S.excl[o];
+            const uint32_t w = (uint32_t)S.tw[o];
+            const uint32_t row = r / w;
+            tx = S.tx0[o] + (int)(r - row * w);
+            ty = S.ty0[o] + (int)row;
+            if (P.exact_tile_test) {
+                const int px0 = max(tx * P.tile_w, S.x0[o]), px1 = min(tx * P.tile_w + P.tile_w - 1, S.x1[o]);
+                const int py0 = max(ty * P.tile_h, S.y0[o]), py1 = min(ty * P.tile_h + P.tile_h - 1, S.y1[o]);
+                const float u = S.u[o], v = S.v[o];
+                hit = ellipse_meets_rect(S.a[o], S.b[o], S.c[o], P.qbin, (float)px0 + 0.5f - u, (float)px1 + 0.5f - u,
+                                         (float)py0 + 0.5f - v, (float)py1 + 0.5f - v);
+            } else {
+                hit = true;
+            }
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, hit);
+        if constexpr (EMIT) {
+            if (hit) {
+                const uint64_t pos = pbase + count + __popc(m & lt);
+                if (pos < pend) {
+                    const uint64_t gt = (uint64_t)(vd.tile_base - P.tile0 + ty * vd.tiles_x + tx);
+                    keys[pos] = (gt << kZBits) | S.zk[o];
+                    vals[pos] = S.rec[o];
+                }
+            }
+        }
+        count += __popc(m);
+    }
+    return count;
 }
 
 // ------------------------------------------------------------------ spherical harmonics colour
@@ -238,22 +293,40 @@ __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, flo
     Y[15] = -kC3a * x * (xx - 3.f * yy);
 }
 
-template <int DT>
-__device__ __forceinline__ void sh_colour(const NodeDesc& nd, int64_t i, const Gauss& g, const VNode& vn, float rgb[3]) {
+// Colour of one instance from the warp's staged coefficients (stride kShStride floats per lane).
+constexpr int kShStride = 49;   // 48 coefficients + 1 pad: conflict-free lane-strided reads
+
+__device__ __forceinline__ void sh_colour(int deg, const float* __restrict__ coef, const Gauss& g, const VNode& vn,
+                                          float rgb[3]) {
     float dx = g.mx - vn.o[0], dy = g.my - vn.o[1], dz = g.mz - vn.o[2];
     const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
     dx *= inv; dy *= inv; dz *= inv;
     float Y[16];
-    sh_basis(nd.deg, dx, dy, dz, Y);
-    const int nc = (nd.deg + 1) * (nd.deg + 1);
+    sh_basis(deg, dx, dy, dz, Y);
     float r = 0.5f, gg = 0.5f, b = 0.5f;
-    const int64_t base = i * nc * 3;
-    for (int k = 0; k < nc; ++k) {
-        r = fmaf(Y[k], ld_attr<DT>(nd.sh, base + k * 3 + 0), r);
-        gg = fmaf(Y[k], ld_attr<DT>(nd.sh, base + k * 3 + 1), gg);
-        b = fmaf(Y[k], ld_attr<DT>(nd.sh, base + k * 3 + 2), b);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        if (k < (deg + 1) * (deg + 1)) {
+            r = fmaf(Y[k], coef[k * 3 + 0], r);
+            gg = fmaf(Y[k], coef[k * 3 + 1], gg);
+            b = fmaf(Y[k], coef[k * 3 + 2], b);
+        }
     }
     rgb[0] = fmaxf(r, 0.f); rgb[1] = fmaxf(gg, 0.f); rgb[2] = fmaxf(b, 0.f);
+}
+
+// Stages the SH coefficients of the warp's chunk (lane l -> Gaussian chunk*32 + l) as FP32.
+template <int DT>
+__device__ __forceinline__ void stage_sh(const NodeDesc& nd, int c, int lane, float* __restrict__ sh_smem) {
+    const int nc3 = (nd.deg + 1) * (nd.deg + 1) * 3;
+    const int64_t g0 = (int64_t)c * kChunk;
+    const int cnt = (int)min((int64_t)kChunk, nd.n - g0);
+    const int64_t base = g0 * nc3;
+    for (int idx = lane; idx < cnt * nc3; idx += 32) {
+        const int gl = idx / nc3, k = idx - gl * nc3;
+        sh_smem[gl * kShStride + k] = ld_attr<DT>(nd.sh, base + idx);
+    }
+    __syncwarp();
 }
 
 __device__ __forceinline__ int find_node(const NodeDesc* nodes, int n_nodes, int chunk) {
@@ -277,26 +350,30 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x) {
 }
 
 // ------------------------------------------------------------------ count pass
-template <int DT>
-__device__ __forceinline__ void count_chunk(const NodeDesc& nd, int c, int lane, const VNode& vn, const ViewDesc& vd,
-                                            const Params& P, const Gauss& g, bool valid, uint2* counts) {
-    uint32_t nt = 0;
-    if (valid) {
-        Splat s;
-        if (project(g, vn, vd, P, s)) nt = count_tiles(s, vd, P);
-    }
-    const uint32_t vis = __reduce_add_sync(0xffffffffu, nt > 0 ? 1u : 0u);
-    const uint32_t pairs = __reduce_add_sync(0xffffffffu, nt);
-    if (lane == 0) counts[vn.tab + c] = make_uint2(vis, pairs);
+__device__ __forceinline__ void count_chunk(int c, int lane, const VNode& vn, const ViewDesc& vd, const Params& P,
+                                            const Gauss& g, bool valid, WarpSplats& S, uint2* counts) {
+    Splat s;
+    const bool vis = valid && project(g, vn, vd, P, s);
+    const uint32_t area = vis ? (uint32_t)((s.tx1 - s.tx0 + 1) * (s.ty1 - s.ty0 + 1)) : 0u;
+    const uint32_t excl = warp_excl_scan(area);
+    const uint32_t total = __shfl_sync(0xffffffffu, excl + area, 31);
+    if (vis) stash_splat(S, lane, s, excl); else S.excl[lane] = excl;
+    __syncwarp();
+    const uint32_t pairs = walk_tiles<false>(S, lane, total, vd, P, nullptr, nullptr, 0, 0);
+    const uint32_t nvis = __popc(__ballot_sync(0xffffffffu, vis));
+    if (lane == 0) counts[vn.tab + c] = make_uint2(nvis, pairs);
+    __syncwarp();
 }
 
 template <int DT>
 __global__ void __launch_bounds__(256) k_count_batched(const NodeDesc* __restrict__ nodes, int n_nodes,
         const ViewDesc* __restrict__ views, const VNode* __restrict__ vnodes, int K, const NodeView* __restrict__ nv,
         const int32_t* __restrict__ nv_off, int n_chunks, Params P, int v0, int v1, uint2* counts) {
+    __shared__ WarpSplats wsp[8];
     const int chunk = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (chunk >= n_chunks) return;
     const int lane = (int)lane_id();
+    WarpSplats& S = wsp[threadIdx.x >> 5];
     const int k = find_node(nodes, n_nodes, chunk);
     const NodeDesc& nd = nodes[k];
     if (nd.dtype != DT) return;
@@ -308,7 +385,7 @@ __global__ void __launch_bounds__(256) k_count_batched(const NodeDesc* __restric
     for (int e = nv_off[k]; e < nv_off[k + 1]; ++e) {
         const NodeView w = nv[e];
         if (w.view < v0 || w.view >= v1) continue;
-        count_chunk<DT>(nd, c, lane, vnodes[w.view * K + w.slot], views[w.view], P, g, valid, counts);
+        count_chunk(c, lane, vnodes[w.view * K + w.slot], views[w.view], P, g, valid, S, counts);
     }
 }
 
@@ -317,9 +394,11 @@ template <int DT>
 __global__ void __launch_bounds__(256) k_count_plain(const NodeDesc* __restrict__ nodes, const ViewDesc* __restrict__ views,
         const VNode* __restrict__ vnodes, int K, Params P, int v, const int32_t* __restrict__ pmap, int n_view_chunks,
         uint2* counts) {
+    __shared__ WarpSplats wsp[8];
     const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (w >= n_view_chunks) return;
     const int lane = (int)lane_id();
+    WarpSplats& S = wsp[threadIdx.x >> 5];
     int lo = 0, hi = K - 1;
     while (lo < hi) { const int mid = (lo + hi + 1) >> 1; if (pmap[mid] <= w) lo = mid; else hi = mid - 1; }
     const int slot = pmap[K + 1 + lo];
@@ -331,66 +410,70 @@ __global__ void __launch_bounds__(256) k_count_plain(const NodeDesc* __restrict_
     const bool valid = i < nd.n;
     Gauss g;
     if (valid) load_geometry<DT>(nd, i, g);
-    count_chunk<DT>(nd, c, lane, vn, views[v], P, g, valid, counts);
+    count_chunk(c, lane, vn, views[v], P, g, valid, S, counts);
 }
 
 // ------------------------------------------------------------------ emit pass
-template <int DT>
 __device__ __forceinline__ void emit_chunk(const NodeDesc& nd, int c, int lane, int view, const VNode& vn,
                                            const ViewDesc& vd, const Params& P, const Gauss& g, bool valid, int64_t i,
+                                           const float* __restrict__ coef, WarpSplats& S,
                                            const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off,
                                            uint32_t inst_base, uint64_t pair_base, Record* __restrict__ rec,
                                            uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
     Splat s;
-    uint32_t nt = 0;
-    if (valid && project(g, vn, vd, P, s)) nt = count_tiles(s, vd, P);
+    const bool vis = valid && project(g, vn, vd, P, s);
     const int64_t t = vn.tab + c;
-    const uint32_t vis = nt > 0 ? 1u : 0u;
-    const uint32_t vis_pre = __popc(__ballot_sync(0xffffffffu, vis) & ((1u << lane) - 1u));
-    const uint32_t nt_pre = warp_excl_scan(nt);
-    const uint32_t nt_tot = __shfl_sync(0xffffffffu, nt_pre + nt, 31);
-    const uint32_t vis_tot = __popc(__ballot_sync(0xffffffffu, vis));
-    // the count pass must have produced the same totals; otherwise write nothing (the
-    // table's slots are then filled with dead pairs that sort to the end)
+    const uint32_t vmask = __ballot_sync(0xffffffffu, vis);
+    const uint32_t area = vis ? (uint32_t)((s.tx1 - s.tx0 + 1) * (s.ty1 - s.ty0 + 1)) : 0u;
+    const uint32_t excl = warp_excl_scan(area);
+    const uint32_t total = __shfl_sync(0xffffffffu, excl + area, 31);
     const uint64_t p0 = pair_off[t] - pair_base, p1 = pair_off[t + 1] - pair_base;
-    if ((uint64_t)nt_tot != p1 - p0 || vis_tot != inst_off[t + 1] - inst_off[t]) {
+    const uint32_t i0 = inst_off[t] - inst_base, i1 = inst_off[t + 1] - inst_base;
+    // the count pass must have produced the same number of instances; otherwise write nothing
+    // but dead pairs, which sort past every real tile
+    if ((uint32_t)__popc(vmask) != i1 - i0) {
         for (uint64_t p = p0 + lane; p < p1; p += 32) { keys[p] = ~0ull; vals[p] = 0; }
         if (lane == 0) atomicOr(P.err, kErrMismatch);
         return;
     }
-    if (!vis) return;
-    const uint32_t r = inst_off[t] - inst_base + vis_pre;
-    float rgb[3];
-    sh_colour<DT>(nd, i, g, vn, rgb);
-    const float op = 1.f / (1.f + __expf(-__ldg(nd.opac + i)));
-    Record R;
-    R.r0 = make_float4(s.u, s.v, op, s.z);
-    R.r1 = make_float4(s.qa, s.qb, s.qc, __uint_as_float((uint32_t)(nd.gbase + i)));
-    R.r2 = make_float4(rgb[0], rgb[1], rgb[2], __int_as_float(view));
-    rec[r] = R;
-    uint32_t zk = __float_as_uint(s.z) - P.zbase;
-    zk = min(zk, (1u << kZBits) - 1u);
-    uint64_t p = p0 + nt_pre;
-    const uint64_t p_end = p + nt;      // never write past this instance's pairs
-    for (int ty = s.ty0; ty <= s.ty1 && p < p_end; ++ty)
-        for (int tx = s.tx0; tx <= s.tx1 && p < p_end; ++tx) {
-            if (!tile_hit(s, vd, P, tx, ty)) continue;
-            const uint64_t gt = (uint64_t)(vd.tile_base - P.tile0 + ty * vd.tiles_x + tx);
-            keys[p] = (gt << kZBits) | zk;
-            vals[p] = r;
-            ++p;
-        }
+    const uint32_t r = i0 + __popc(vmask & ((1u << lane) - 1u));
+    if (vis) {
+        float rgb[3];
+        sh_colour(nd.deg, coef, g, vn, rgb);
+        const float op = 1.f / (1.f + __expf(-__ldg(nd.opac + i)));
+        Record R;
+        R.r0 = make_float4(s.u, s.v, op, s.z);
+        R.r1 = make_float4(s.qa, s.qb, s.qc, __uint_as_float((uint32_t)(nd.gbase + i)));
+        R.r2 = make_float4(rgb[0], rgb[1], rgb[2], __int_as_float(view));
+        rec[r] = R;
+        stash_splat(S, lane, s, excl);
+        S.zk[lane] = min(__float_as_uint(s.z) - P.zbase, (1u << kZBits) - 1u);
+        S.rec[lane] = r;
+    } else {
+        S.excl[lane] = excl;
+    }
+    __syncwarp();
+    const uint32_t written = walk_tiles<true>(S, lane, total, vd, P, keys, vals, p0, p1);
+    if ((uint64_t)written != p1 - p0) {
+        if (lane == 0) atomicOr(P.err, kErrMismatch);
+        for (uint64_t p = p0 + written + lane; p < p1; p += 32) { keys[p] = ~0ull; vals[p] = 0; }
+    }
+    __syncwarp();
 }
 
+constexpr int kEmitWarps = 4;
+
 template <int DT>
-__global__ void __launch_bounds__(256) k_emit_batched(const NodeDesc* __restrict__ nodes, int n_nodes,
+__global__ void __launch_bounds__(kEmitWarps * 32) k_emit_batched(const NodeDesc* __restrict__ nodes, int n_nodes,
         const ViewDesc* __restrict__ views, const VNode* __restrict__ vnodes, int K, const NodeView* __restrict__ nv,
         const int32_t* __restrict__ nv_off, int n_chunks, Params P, int v0, int v1,
         const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off, uint32_t inst_base,
         uint64_t pair_base, Record* __restrict__ rec, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    __shared__ WarpSplats wsp[kEmitWarps];
+    __shared__ float shc[kEmitWarps][kChunk * kShStride];
     const int chunk = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (chunk >= n_chunks) return;
-    const int lane = (int)lane_id();
+    const int lane = (int)lane_id(), wib = threadIdx.x >> 5;
     const int k = find_node(nodes, n_nodes, chunk);
     const NodeDesc& nd = nodes[k];
     if (nd.dtype != DT) return;
@@ -399,22 +482,27 @@ __global__ void __launch_bounds__(256) k_emit_batched(const NodeDesc* __restrict
     const bool valid = i < nd.n;
     Gauss g;
     if (valid) load_geometry<DT>(nd, i, g);
+    stage_sh<DT>(nd, c, lane, shc[wib]);
+    const float* coef = shc[wib] + lane * kShStride;
     for (int e = nv_off[k]; e < nv_off[k + 1]; ++e) {
         const NodeView w = nv[e];
         if (w.view < v0 || w.view >= v1) continue;
-        emit_chunk<DT>(nd, c, lane, w.view, vnodes[w.view * K + w.slot], views[w.view], P, g, valid, i, inst_off,
-                       pair_off, inst_base, pair_base, rec, keys, vals);
+        emit_chunk(nd, c, lane, w.view, vnodes[w.view * K + w.slot], views[w.view], P, g, valid, i, coef, wsp[wib],
+                   inst_off, pair_off, inst_base, pair_base, rec, keys, vals);
     }
 }
 
 template <int DT>
-__global__ void __launch_bounds__(256) k_emit_plain(const NodeDesc* __restrict__ nodes, const ViewDesc* __restrict__ views,
-        const VNode* __restrict__ vnodes, int K, Params P, int v, const int32_t* __restrict__ pmap, int n_view_chunks,
-        const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off, uint32_t inst_base,
-        uint64_t pair_base, Record* __restrict__ rec, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+__global__ void __launch_bounds__(kEmitWarps * 32) k_emit_plain(const NodeDesc* __restrict__ nodes,
+        const ViewDesc* __restrict__ views, const VNode* __restrict__ vnodes, int K, Params P, int v,
+        const int32_t* __restrict__ pmap, int n_view_chunks, const uint32_t* __restrict__ inst_off,
+        const uint64_t* __restrict__ pair_off, uint32_t inst_base, uint64_t pair_base, Record* __restrict__ rec,
+        uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    __shared__ WarpSplats wsp[kEmitWarps];
+    __shared__ float shc[kEmitWarps][kChunk * kShStride];
     const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (w >= n_view_chunks) return;
-    const int lane = (int)lane_id();
+    const int lane = (int)lane_id(), wib = threadIdx.x >> 5;
     int lo = 0, hi = K - 1;
     while (lo < hi) { const int mid = (lo + hi + 1) >> 1; if (pmap[mid] <= w) lo = mid; else hi = mid - 1; }
     const int slot = pmap[K + 1 + lo];
@@ -426,8 +514,9 @@ __global__ void __launch_bounds__(256) k_emit_plain(const NodeDesc* __restrict__
     const bool valid = i < nd.n;
     Gauss g;
     if (valid) load_geometry<DT>(nd, i, g);
-    emit_chunk<DT>(nd, c, lane, v, vn, views[v], P, g, valid, i, inst_off, pair_off, inst_base, pair_base, rec, keys,
-                   vals);
+    stage_sh<DT>(nd, c, lane, shc[wib]);
+    emit_chunk(nd, c, lane, v, vn, views[v], P, g, valid, i, shc[wib] + lane * kShStride, wsp[wib], inst_off,
+               pair_off, inst_base, pair_base, rec, keys, vals);
 }
 
 // ------------------------------------------------------------------ exclusive scan of the count table
@@ -535,14 +624,14 @@ void emit_launch(const Launch& L, const NodeDesc* nodes, int n_nodes, const View
                  const int32_t* pmap, int64_t view_chunks, const uint32_t* inst_off, const uint64_t* pair_off,
                  uint32_t inst_base, uint64_t pair_base, Record* rec, uint64_t* keys, uint32_t* vals) {
     if (batched) {
-        const int blocks = (int)(((int64_t)n_chunks * 32 + 255) / 256);
+        const int blocks = (int)(((int64_t)n_chunks + kEmitWarps - 1) / kEmitWarps);
         if (blocks == 0) return;
-        k_emit_batched<DT><<<blocks, 256, 0, L.stream>>>(nodes, n_nodes, views, vnodes, K, nv, nv_off, n_chunks, P, v0,
+        k_emit_batched<DT><<<blocks, kEmitWarps * 32, 0, L.stream>>>(nodes, n_nodes, views, vnodes, K, nv, nv_off, n_chunks, P, v0,
                                                          v1, inst_off, pair_off, inst_base, pair_base, rec, keys, vals);
     } else {
-        const int blocks = (int)((view_chunks * 32 + 255) / 256);
+        const int blocks = (int)((view_chunks + kEmitWarps - 1) / kEmitWarps);
         if (blocks == 0) return;
-        k_emit_plain<DT><<<blocks, 256, 0, L.stream>>>(nodes, views, vnodes, K, P, v0, pmap, (int)view_chunks, inst_off,
+        k_emit_plain<DT><<<blocks, kEmitWarps * 32, 0, L.stream>>>(nodes, views, vnodes, K, P, v0, pmap, (int)view_chunks, inst_off,
                                                        pair_off, inst_base, pair_base, rec, keys, vals);
     }
     ++*L.launches;
