@@ -3,7 +3,7 @@
 // A call renders every (env, camera) view of a batch (Sec. III-C: RGB and depth sensors of
 // many parallel environments, Sec. III-B: background + posed interactive nodes):
 //   setup     camera_from_node per (view, slot), pose validation            (K0)
-//   count     per (view, 32-Gaussian chunk): visible instances, tile pairs    (K1)
+//   count     per (view, 32-Gaussian chunk): mask of visible lanes, tile pairs (K1)
 //   scan      exclusive offsets of that table; per-view totals read back once
 //   per view group: emit records + pairs (K2), radix sort (K3), tile ranges (K4),
 //                   composite RGB + depth (K5)
@@ -550,7 +550,8 @@ int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32
         Pg.tile0 = tile0;
         tm.begin(DGS_K_EMIT);
         launch_emit(L, dtype_mask, d_nodes, n_nodes, d_views, d_vnodes, K, d_nv, d_nvoff, (int)chunk_total, Pg, v0, v1,
-                    batched, d_pmap + (size_t)v0 * (2 * K + 1), view_tab[v0 + 1] - view_tab[v0], d_inst_off, d_pair_off,
+                    batched, d_pmap + (size_t)v0 * (2 * K + 1), view_tab[v0 + 1] - view_tab[v0], d_counts, d_inst_off,
+                    d_pair_off,
                     (uint32_t)inst_at[v0], pair_at[v0], d_rec, static_cast<uint64_t*>(ctx->keys0.p),
                     static_cast<uint32_t*>(ctx->vals0.p));
         tm.end();

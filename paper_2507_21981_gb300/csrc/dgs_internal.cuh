@@ -114,7 +114,8 @@ void launch_scan(const Launch& L, const uint2* counts, int64_t n, uint32_t* inst
 void launch_emit(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_nodes, const ViewDesc* views,
                  const VNode* vnodes, int K, const NodeView* node_views, const int32_t* node_view_off,
                  int n_chunks_total, const Params& P, int v0, int v1, bool batched, const int32_t* view_chunk_nodes,
-                 int64_t view_chunks, const uint32_t* inst_off, const uint64_t* pair_off, uint32_t inst_base,
+                 int64_t view_chunks, const uint2* counts, const uint32_t* inst_off, const uint64_t* pair_off,
+                 uint32_t inst_base,
                  uint64_t pair_base, Record* records, uint64_t* keys, uint32_t* vals);
 
 void launch_sort(const Launch& L, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,

@@ -78,7 +78,24 @@ struct Gauss {
     float mx, my, mz;
     float r00, r01, r02, r10, r11, r12, r20, r21, r22;   // rotation of the unit quaternion
     float s0, s1, s2;                                      // squared scales exp(2 log s)
+    float smax;                                            // largest squared scale
 };
+
+constexpr int kGeoStride = 17;   // 16 floats of Gauss + 1 pad: conflict-free reads by other lanes
+
+__device__ __forceinline__ void put_geo(float* __restrict__ row, const Gauss& g) {
+    row[0] = g.mx; row[1] = g.my; row[2] = g.mz;
+    row[3] = g.r00; row[4] = g.r01; row[5] = g.r02; row[6] = g.r10; row[7] = g.r11; row[8] = g.r12;
+    row[9] = g.r20; row[10] = g.r21; row[11] = g.r22; row[12] = g.s0; row[13] = g.s1; row[14] = g.s2;
+    row[15] = g.smax;
+}
+
+__device__ __forceinline__ void get_geo(const float* __restrict__ row, Gauss& g) {
+    g.mx = row[0]; g.my = row[1]; g.mz = row[2];
+    g.r00 = row[3]; g.r01 = row[4]; g.r02 = row[5]; g.r10 = row[6]; g.r11 = row[7]; g.r12 = row[8];
+    g.r20 = row[9]; g.r21 = row[10]; g.r22 = row[11]; g.s0 = row[12]; g.s1 = row[13]; g.s2 = row[14];
+    g.smax = row[15];
+}
 
 template <int DT>
 __device__ __forceinline__ void load_geometry(const NodeDesc& nd, int64_t i, Gauss& g) {
@@ -95,6 +112,7 @@ __device__ __forceinline__ void load_geometry(const NodeDesc& nd, int64_t i, Gau
     g.r00 = 1.f - 2.f * (y * y + z * z); g.r01 = 2.f * (x * y - w * z); g.r02 = 2.f * (x * z + w * y);
     g.r10 = 2.f * (x * y + w * z); g.r11 = 1.f - 2.f * (x * x + z * z); g.r12 = 2.f * (y * z - w * x);
     g.r20 = 2.f * (x * z - w * y); g.r21 = 2.f * (y * z + w * x); g.r22 = 1.f - 2.f * (x * x + y * y);
+    g.smax = fmaxf(g.s0, fmaxf(g.s1, g.s2));
 }
 
 struct Splat {
@@ -171,6 +189,30 @@ __device__ __forceinline__ bool project(const Gauss& g, const VNode& vn, const V
     return true;
 }
 
+// Conservative screen-space cull: false only if project() would certainly return false.  The
+// 2D covariance satisfies Sigma_xx <= |T0|^2 smax + lowpass with |T0|^2 = (fx/z)^2 (1 + xc^2)
+// for the orthonormal rows of camera_from_node, so the ellipse box is bounded by
+// sqrt(qbin ((fx/z)^2 (1 + xc^2) smax + lowpass)) (2 % + 1e-3 px of slack for rounding).  The
+// centre u and the depth key are computed exactly as in project().
+__device__ __forceinline__ bool may_be_visible(const Gauss& g, const VNode& vn, const ViewDesc& vd, const Params& P) {
+    const float* M = vn.M;
+    const float z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[8], g.mx), __fmul_rn(M[9], g.my)), __fmul_rn(M[10], g.mz)), M[11]);
+    if (!(z > P.z_near)) return false;
+    const float tx = fmaf(M[0], g.mx, fmaf(M[1], g.my, fmaf(M[2], g.mz, M[3])));
+    const float ty = fmaf(M[4], g.mx, fmaf(M[5], g.my, fmaf(M[6], g.mz, M[7])));
+    const float iz = 1.f / z;
+    const float xr = tx * iz, yr = ty * iz;
+    const float xc = fminf(vd.limx, fmaxf(-vd.limx, xr));
+    const float yc = fminf(vd.limy, fmaxf(-vd.limy, yr));
+    const float fxz = vd.fx * iz, fyz = vd.fy * iz;
+    const float s = 1.02f * g.smax;
+    const float hx = sqrtf(P.qbin * fmaf(fxz * fxz * fmaf(xc, xc, 1.f), s, P.lowpass)) + 1e-3f;
+    const float hy = sqrtf(P.qbin * fmaf(fyz * fyz * fmaf(yc, yc, 1.f), s, P.lowpass)) + 1e-3f;
+    const float u = fmaf(vd.fx, xr, vd.cx), v = fmaf(vd.fy, yr, vd.cy);
+    return u + hx - 0.5f >= 0.f && v + hy - 0.5f >= 0.f && u - hx - 0.5f <= (float)(vd.W - 1) &&
+           v - hy - 0.5f <= (float)(vd.H - 1);
+}
+
 // Does the ellipse {d^T conic d <= qlim} reach a pixel centre of the rectangle
 // [X0,X1] x [Y0,Y1] (coordinates relative to the mean)?  Minimum of the convex quadratic over
 // the rectangle: 0 if the mean is inside, else the smallest of the four edge minima.
@@ -190,14 +232,34 @@ __device__ __forceinline__ bool ellipse_meets_rect(float a, float b, float c, fl
     return m <= qlim;
 }
 
-// Per-warp shared state of the cooperative tile enumeration: the splats of the warp's 32
-// lanes for the current view.
+// Walks the union of the warp's tile rectangles, flattened in (lane, row-major tile) order,
+// 32 candidates at a time.  Lane l of the flush holds one (Gaussian, view) item; items are in
+// view-major, Gaussian order.  COUNT: adds each item's hit count to S.hits[l].  EMIT: writes
+// the hits of view j at S.pbase[j] + S.run[j] + rank, in walk order, and advances S.run[j].
+// The count and emit passes walk the same items in the same order.
 struct WarpSplats {
     float u[32], v[32], a[32], b[32], c[32];
     int32_t tx0[32], ty0[32], tw[32], x0[32], x1[32], y0[32], y1[32];
-    uint32_t excl[32];     // exclusive prefix of the lanes' tile-rectangle areas
-    uint32_t zk[32];       // depth key of the lane's instance (emit only)
-    uint32_t rec[32];      // record index of the lane's instance (emit only)
+    uint32_t excl[32];     // exclusive prefix of the items' tile-rectangle areas
+    uint32_t zk[32];       // depth key of the item (emit)
+    uint32_t rec[32];      // record index of the item (emit)
+    int32_t vj[32];        // view slot (0..kViewBlock-1) of the item
+    uint32_t hits[32];     // hit count of the item (count)
+};
+
+constexpr int kViewBlock = 8;
+
+struct WarpViews {
+    uint64_t pbase[kViewBlock];   // first pair of (view j, chunk) relative to the group (emit)
+    uint64_t pend[kViewBlock];
+    int64_t tab[kViewBlock];      // count-table entry of (view j, chunk)
+    uint32_t run[kViewBlock];     // pairs written so far for view j (emit)
+    int32_t tile_base[kViewBlock];
+    int32_t tiles_x[kViewBlock];
+    uint32_t mask[kViewBlock];    // survivor lanes of view j
+    int32_t vv[kViewBlock];       // (view, slot) index of view j, -1 = none
+    uint32_t vis[kViewBlock];     // count pass: lanes whose projection succeeded
+    uint32_t hits[kViewBlock];    // count pass: pairs of view j
 };
 
 __device__ __forceinline__ void stash_splat(WarpSplats& S, int lane, const Splat& s, uint32_t excl) {
@@ -207,22 +269,16 @@ __device__ __forceinline__ void stash_splat(WarpSplats& S, int lane, const Splat
     S.excl[lane] = excl;
 }
 
-// Walks the union of the warp's tile rectangles, flattened in (lane, row-major tile) order,
-// 32 candidates at a time, and returns the number of (instance, tile) pairs whose tile the
-// instance's ellipse reaches.  With EMIT, pair j of the walk is written at pbase + j.  The
-// count and emit passes run this same walk, so they agree on every total and position.
 template <bool EMIT>
-__device__ __forceinline__ uint32_t walk_tiles(const WarpSplats& S, int lane, uint32_t total, const ViewDesc& vd,
-                                               const Params& P, uint64_t* __restrict__ keys,
-                                               uint32_t* __restrict__ vals, uint64_t pbase, uint64_t pend) {
+__device__ __forceinline__ void walk_tiles(WarpSplats& S, WarpViews& WV, int lane, uint32_t total, const Params& P,
+                                           uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
     const uint32_t lt = (1u << lane) - 1u;
-    uint32_t count = 0;
     for (uint32_t base = 0; base < total; base += 32) {
         const uint32_t f = base + (uint32_t)lane;
         bool hit = false;
-        int o = 0, tx = 0, ty = 0;
+        int o = -1, tx = 0, ty = 0;
         if (f < total) {
-            // owner: last lane whose rectangle starts at or before f
+            // owner: last item whose rectangle starts at or before f
             int lo = 0, hi = 31;
 #pragma unroll
             for (int it = 0; it < 5; ++it) {
@@ -245,20 +301,25 @@ __device__ __forceinline__ uint32_t walk_tiles(const WarpSplats& S, int lane, ui
                 hit = true;
             }
         }
-        const uint32_t m = __ballot_sync(0xffffffffu, hit);
-        if constexpr (EMIT) {
+        if constexpr (!EMIT) {
+            const uint32_t peers = __match_any_sync(0xffffffffu, hit ? o : -1);
+            if (hit && (peers & lt) == 0) S.hits[o] += __popc(peers);
+        } else {
+            const int j = hit ? S.vj[o] : -1;
+            const uint32_t peers = __match_any_sync(0xffffffffu, j);
             if (hit) {
-                const uint64_t pos = pbase + count + __popc(m & lt);
-                if (pos < pend) {
-                    const uint64_t gt = (uint64_t)(vd.tile_base - P.tile0 + ty * vd.tiles_x + tx);
+                const uint64_t pos = WV.pbase[j] + WV.run[j] + __popc(peers & lt);
+                if (pos < WV.pend[j]) {
+                    const uint64_t gt = (uint64_t)(WV.tile_base[j] - P.tile0 + ty * WV.tiles_x[j] + tx);
                     keys[pos] = (gt << kZBits) | S.zk[o];
                     vals[pos] = S.rec[o];
                 }
             }
+            __syncwarp();
+            if (hit && (peers & lt) == 0) WV.run[j] += __popc(peers);
         }
-        count += __popc(m);
+        __syncwarp();
     }
-    return count;
 }
 
 // ------------------------------------------------------------------ spherical harmonics colour
@@ -349,174 +410,259 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x) {
     return s - x;
 }
 
-// ------------------------------------------------------------------ count pass
-__device__ __forceinline__ void count_chunk(int c, int lane, const VNode& vn, const ViewDesc& vd, const Params& P,
-                                            const Gauss& g, bool valid, WarpSplats& S, uint2* counts) {
-    Splat s;
-    const bool vis = valid && project(g, vn, vd, P, s);
-    const uint32_t area = vis ? (uint32_t)((s.tx1 - s.tx0 + 1) * (s.ty1 - s.ty0 + 1)) : 0u;
-    const uint32_t excl = warp_excl_scan(area);
-    const uint32_t total = __shfl_sync(0xffffffffu, excl + area, 31);
-    if (vis) stash_splat(S, lane, s, excl); else S.excl[lane] = excl;
-    __syncwarp();
-    const uint32_t pairs = walk_tiles<false>(S, lane, total, vd, P, nullptr, nullptr, 0, 0);
-    const uint32_t nvis = __popc(__ballot_sync(0xffffffffu, vis));
-    if (lane == 0) counts[vn.tab + c] = make_uint2(nvis, pairs);
-    __syncwarp();
+// ------------------------------------------------------------------ count and emit passes
+// A warp owns a chunk of 32 consecutive Gaussians of one node and walks the (view, slot)
+// entries of that node in blocks of kViewBlock views:
+//   1. survivors: count pass -- a conservative cull of every (lane, view) pair, one ballot per
+//      view; emit pass -- the exact visible-lane masks the count pass stored;
+//   2. the survivors, queued view-major in Gaussian order, are projected 32 at a time (one
+//      per lane) and their tiles walked cooperatively;
+//   3. count pass -- per view, the mask of lanes whose projection succeeded and the number of
+//      (instance, tile) pairs go to the count table; emit pass -- records and pairs were
+//      written at the scanned offsets of each (view, chunk) entry.
+struct WarpWork {
+    WarpSplats S;
+    WarpViews WV;
+    float geo[kChunk * kGeoStride];     // staged geometry of the chunk's Gaussians
+};
+
+// Position of the n-th (0-based) set bit of m; requires n < popc(m).
+__device__ __forceinline__ int nth_set_bit(uint32_t m, uint32_t n) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const uint32_t low = __popc(m & ((1u << w) - 1u));
+        if (n >= low) { n -= low; m >>= w; pos += w; }
+    }
+    return pos;
+}
+
+// Item `idx` (< total survivors) of a view block: the first view j whose survivors reach past
+// idx, and the Gaussian lane g of its (idx - before)-th survivor.
+__device__ __forceinline__ void decode_item(uint32_t idx, const WarpViews& WV, int nvb, int& j, int& g) {
+    uint32_t before = 0;
+    j = 0;
+    for (int t = 0; t < nvb; ++t) {
+        const uint32_t c = __popc(WV.mask[t]);
+        if (idx < before + c) { j = t; break; }
+        before += c;
+    }
+    g = nth_set_bit(WV.mask[j], idx - before);
+}
+
+template <bool EMIT>
+__device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lane, const NodeView* __restrict__ entries,
+                                              int n_entries, int v0, int v1, const ViewDesc* __restrict__ views,
+                                              const VNode* __restrict__ vnodes, int K, const Params& P, const Gauss& gme,
+                                              bool valid, WarpWork& W, const float* __restrict__ shc,
+                                              uint2* __restrict__ counts, const uint32_t* __restrict__ inst_off,
+                                              const uint64_t* __restrict__ pair_off, uint32_t inst_base,
+                                              uint64_t pair_base, Record* __restrict__ rec,
+                                              uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    WarpViews& WV = W.WV;
+    for (int eb = 0; eb < n_entries; eb += kViewBlock) {
+        const int nvb = min(kViewBlock, n_entries - eb);
+        // 1. survivors of each view of the block
+        for (int j = 0; j < nvb; ++j) {
+            const NodeView w = entries[eb + j];
+            const bool in = w.view >= v0 && w.view < v1;
+            const int vvj = in ? w.view * K + w.slot : -1;
+            uint32_t m = 0;
+            int64_t t = 0;
+            if (in) {
+                const VNode& vn = vnodes[vvj];
+                t = vn.tab + c;
+                if constexpr (!EMIT) m = __ballot_sync(0xffffffffu, valid && may_be_visible(gme, vn, views[w.view], P));
+                else m = counts[t].x;
+            }
+            if (lane == j) {
+                WV.mask[j] = m; WV.vv[j] = vvj; WV.tab[j] = t; WV.vis[j] = 0; WV.hits[j] = 0; WV.run[j] = 0;
+                if constexpr (EMIT) {
+                    if (in) {
+                        const ViewDesc& vd = views[w.view];
+                        WV.pbase[j] = pair_off[t] - pair_base;
+                        WV.pend[j] = pair_off[t + 1] - pair_base;
+                        WV.tile_base[j] = vd.tile_base;
+                        WV.tiles_x[j] = vd.tiles_x;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        uint32_t n_items = 0;
+        for (int j = 0; j < nvb; ++j) n_items += __popc(WV.mask[j]);
+        // 2. project the survivors 32 at a time and walk their tiles
+        for (uint32_t it = 0; it < n_items; it += 32) {
+            const uint32_t idx = it + (uint32_t)lane;
+            const bool act = idx < n_items;
+            int j = 0, g = 0;
+            if (act) decode_item(idx, WV, nvb, j, g);
+            Splat s;
+            bool vis = false;
+            Gauss gg;
+            const int vvj = act ? WV.vv[j] : 0;
+            if (act) {
+                get_geo(W.geo + g * kGeoStride, gg);
+                vis = project(gg, vnodes[vvj], views[vvj / K], P, s);
+            }
+            const uint32_t area = vis ? (uint32_t)((s.tx1 - s.tx0 + 1) * (s.ty1 - s.ty0 + 1)) : 0u;
+            const uint32_t excl = warp_excl_scan(area);
+            const uint32_t total = __shfl_sync(0xffffffffu, excl + area, 31);
+            if (vis) stash_splat(W.S, lane, s, excl); else W.S.excl[lane] = excl;
+            W.S.vj[lane] = j;
+            W.S.hits[lane] = 0;
+            if constexpr (EMIT) {
+                if (act && !vis) atomicOr(P.err, kErrMismatch);
+                if (vis) {
+                    const uint32_t r = inst_off[WV.tab[j]] - inst_base + __popc(WV.mask[j] & ((1u << g) - 1u));
+                    float rgb[3];
+                    sh_colour(nd.deg, shc + g * kShStride, gg, vnodes[vvj], rgb);
+                    const int64_t i = (int64_t)c * kChunk + g;
+                    const float op = 1.f / (1.f + __expf(-__ldg(nd.opac + i)));
+                    Record R;
+                    R.r0 = make_float4(s.u, s.v, op, s.z);
+                    R.r1 = make_float4(s.qa, s.qb, s.qc, __uint_as_float((uint32_t)(nd.gbase + i)));
+                    R.r2 = make_float4(rgb[0], rgb[1], rgb[2], __int_as_float(vvj / K));
+                    rec[r] = R;
+                    W.S.zk[lane] = min(__float_as_uint(s.z) - P.zbase, (1u << kZBits) - 1u);
+                    W.S.rec[lane] = r;
+                }
+            }
+            __syncwarp();
+            walk_tiles<EMIT>(W.S, WV, lane, total, P, keys, vals);
+            if constexpr (!EMIT) {
+                // per-view totals of this flush: items are view-sorted, reduce each view's run
+                const uint32_t peers = __match_any_sync(0xffffffffu, act ? j : -1);
+                const uint32_t h = __reduce_add_sync(peers, act ? W.S.hits[lane] : 0u);
+                const uint32_t bits = __reduce_or_sync(peers, vis ? (1u << g) : 0u);
+                if (act && (peers & ((1u << lane) - 1u)) == 0) { WV.hits[j] += h; WV.vis[j] |= bits; }
+            }
+            __syncwarp();
+        }
+        // 3. results of the block
+        if (lane < nvb && WV.vv[lane] >= 0) {
+            const int j = lane;
+            if constexpr (!EMIT) {
+                counts[WV.tab[j]] = make_uint2(WV.vis[j], WV.hits[j]);
+            } else {
+                const uint64_t want = WV.pend[j] - WV.pbase[j];
+                if ((uint64_t)WV.run[j] != want) {
+                    atomicOr(P.err, kErrMismatch);
+                    for (uint64_t q = WV.pbase[j] + WV.run[j]; q < WV.pend[j]; ++q) { keys[q] = ~0ull; vals[q] = 0; }
+                }
+            }
+        }
+        __syncwarp();
+    }
 }
 
 template <int DT>
-__global__ void __launch_bounds__(256) k_count_batched(const NodeDesc* __restrict__ nodes, int n_nodes,
+__device__ __forceinline__ void stage_geometry(const NodeDesc& nd, int c, int lane, WarpWork& W, Gauss& g, bool& valid) {
+    const int64_t i = (int64_t)c * kChunk + lane;
+    valid = i < nd.n;
+    if (valid) load_geometry<DT>(nd, i, g);
+    else { g = Gauss{}; g.s0 = g.s1 = g.s2 = g.smax = 1.f; g.r00 = g.r11 = g.r22 = 1.f; }
+    put_geo(W.geo + lane * kGeoStride, g);
+    __syncwarp();
+}
+
+constexpr int kCountWarps = 8;
+constexpr int kEmitWarps = 4;
+
+template <int DT>
+__global__ void __launch_bounds__(kCountWarps * 32) k_count_batched(const NodeDesc* __restrict__ nodes, int n_nodes,
         const ViewDesc* __restrict__ views, const VNode* __restrict__ vnodes, int K, const NodeView* __restrict__ nv,
         const int32_t* __restrict__ nv_off, int n_chunks, Params P, int v0, int v1, uint2* counts) {
-    __shared__ WarpSplats wsp[8];
+    __shared__ WarpWork ww[kCountWarps];
     const int chunk = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (chunk >= n_chunks) return;
     const int lane = (int)lane_id();
-    WarpSplats& S = wsp[threadIdx.x >> 5];
+    WarpWork& W = ww[threadIdx.x >> 5];
     const int k = find_node(nodes, n_nodes, chunk);
     const NodeDesc& nd = nodes[k];
     if (nd.dtype != DT) return;
     const int c = chunk - nd.chunk0;
-    const int64_t i = (int64_t)c * kChunk + lane;
-    const bool valid = i < nd.n;
     Gauss g;
-    if (valid) load_geometry<DT>(nd, i, g);
-    for (int e = nv_off[k]; e < nv_off[k + 1]; ++e) {
-        const NodeView w = nv[e];
-        if (w.view < v0 || w.view >= v1) continue;
-        count_chunk(c, lane, vnodes[w.view * K + w.slot], views[w.view], P, g, valid, S, counts);
-    }
+    bool valid;
+    stage_geometry<DT>(nd, c, lane, W, g, valid);
+    process_chunk<false>(nd, c, lane, nv + nv_off[k], nv_off[k + 1] - nv_off[k], v0, v1, views, vnodes, K, P, g, valid,
+                         W, nullptr, counts, nullptr, nullptr, 0, 0, nullptr, nullptr, nullptr);
 }
 
 // Plain mode: the chunks of one view.  pmap = [K+1 prefix chunk counts in node-id order, K slots].
 template <int DT>
-__global__ void __launch_bounds__(256) k_count_plain(const NodeDesc* __restrict__ nodes, const ViewDesc* __restrict__ views,
-        const VNode* __restrict__ vnodes, int K, Params P, int v, const int32_t* __restrict__ pmap, int n_view_chunks,
-        uint2* counts) {
-    __shared__ WarpSplats wsp[8];
+__global__ void __launch_bounds__(kCountWarps * 32) k_count_plain(const NodeDesc* __restrict__ nodes,
+        const ViewDesc* __restrict__ views, const VNode* __restrict__ vnodes, int K, Params P, int v,
+        const int32_t* __restrict__ pmap, int n_view_chunks, uint2* counts) {
+    __shared__ WarpWork ww[kCountWarps];
     const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (w >= n_view_chunks) return;
     const int lane = (int)lane_id();
-    WarpSplats& S = wsp[threadIdx.x >> 5];
+    WarpWork& W = ww[threadIdx.x >> 5];
     int lo = 0, hi = K - 1;
     while (lo < hi) { const int mid = (lo + hi + 1) >> 1; if (pmap[mid] <= w) lo = mid; else hi = mid - 1; }
     const int slot = pmap[K + 1 + lo];
-    const VNode& vn = vnodes[v * K + slot];
-    const NodeDesc& nd = nodes[vn.node];
+    const NodeDesc& nd = nodes[vnodes[v * K + slot].node];
     if (nd.dtype != DT) return;
     const int c = w - pmap[lo];
-    const int64_t i = (int64_t)c * kChunk + lane;
-    const bool valid = i < nd.n;
     Gauss g;
-    if (valid) load_geometry<DT>(nd, i, g);
-    count_chunk(c, lane, vn, views[v], P, g, valid, S, counts);
+    bool valid;
+    stage_geometry<DT>(nd, c, lane, W, g, valid);
+    const NodeView one{v, slot};
+    process_chunk<false>(nd, c, lane, &one, 1, v, v + 1, views, vnodes, K, P, g, valid, W, nullptr, counts, nullptr,
+                         nullptr, 0, 0, nullptr, nullptr, nullptr);
 }
-
-// ------------------------------------------------------------------ emit pass
-__device__ __forceinline__ void emit_chunk(const NodeDesc& nd, int c, int lane, int view, const VNode& vn,
-                                           const ViewDesc& vd, const Params& P, const Gauss& g, bool valid, int64_t i,
-                                           const float* __restrict__ coef, WarpSplats& S,
-                                           const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off,
-                                           uint32_t inst_base, uint64_t pair_base, Record* __restrict__ rec,
-                                           uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-    Splat s;
-    const bool vis = valid && project(g, vn, vd, P, s);
-    const int64_t t = vn.tab + c;
-    const uint32_t vmask = __ballot_sync(0xffffffffu, vis);
-    const uint32_t area = vis ? (uint32_t)((s.tx1 - s.tx0 + 1) * (s.ty1 - s.ty0 + 1)) : 0u;
-    const uint32_t excl = warp_excl_scan(area);
-    const uint32_t total = __shfl_sync(0xffffffffu, excl + area, 31);
-    const uint64_t p0 = pair_off[t] - pair_base, p1 = pair_off[t + 1] - pair_base;
-    const uint32_t i0 = inst_off[t] - inst_base, i1 = inst_off[t + 1] - inst_base;
-    // the count pass must have produced the same number of instances; otherwise write nothing
-    // but dead pairs, which sort past every real tile
-    if ((uint32_t)__popc(vmask) != i1 - i0) {
-        for (uint64_t p = p0 + lane; p < p1; p += 32) { keys[p] = ~0ull; vals[p] = 0; }
-        if (lane == 0) atomicOr(P.err, kErrMismatch);
-        return;
-    }
-    const uint32_t r = i0 + __popc(vmask & ((1u << lane) - 1u));
-    if (vis) {
-        float rgb[3];
-        sh_colour(nd.deg, coef, g, vn, rgb);
-        const float op = 1.f / (1.f + __expf(-__ldg(nd.opac + i)));
-        Record R;
-        R.r0 = make_float4(s.u, s.v, op, s.z);
-        R.r1 = make_float4(s.qa, s.qb, s.qc, __uint_as_float((uint32_t)(nd.gbase + i)));
-        R.r2 = make_float4(rgb[0], rgb[1], rgb[2], __int_as_float(view));
-        rec[r] = R;
-        stash_splat(S, lane, s, excl);
-        S.zk[lane] = min(__float_as_uint(s.z) - P.zbase, (1u << kZBits) - 1u);
-        S.rec[lane] = r;
-    } else {
-        S.excl[lane] = excl;
-    }
-    __syncwarp();
-    const uint32_t written = walk_tiles<true>(S, lane, total, vd, P, keys, vals, p0, p1);
-    if ((uint64_t)written != p1 - p0) {
-        if (lane == 0) atomicOr(P.err, kErrMismatch);
-        for (uint64_t p = p0 + written + lane; p < p1; p += 32) { keys[p] = ~0ull; vals[p] = 0; }
-    }
-    __syncwarp();
-}
-
-constexpr int kEmitWarps = 4;
 
 template <int DT>
 __global__ void __launch_bounds__(kEmitWarps * 32) k_emit_batched(const NodeDesc* __restrict__ nodes, int n_nodes,
         const ViewDesc* __restrict__ views, const VNode* __restrict__ vnodes, int K, const NodeView* __restrict__ nv,
-        const int32_t* __restrict__ nv_off, int n_chunks, Params P, int v0, int v1,
+        const int32_t* __restrict__ nv_off, int n_chunks, Params P, int v0, int v1, const uint2* __restrict__ counts,
         const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off, uint32_t inst_base,
         uint64_t pair_base, Record* __restrict__ rec, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-    __shared__ WarpSplats wsp[kEmitWarps];
+    __shared__ WarpWork ww[kEmitWarps];
     __shared__ float shc[kEmitWarps][kChunk * kShStride];
     const int chunk = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (chunk >= n_chunks) return;
     const int lane = (int)lane_id(), wib = threadIdx.x >> 5;
+    WarpWork& W = ww[wib];
     const int k = find_node(nodes, n_nodes, chunk);
     const NodeDesc& nd = nodes[k];
     if (nd.dtype != DT) return;
     const int c = chunk - nd.chunk0;
-    const int64_t i = (int64_t)c * kChunk + lane;
-    const bool valid = i < nd.n;
     Gauss g;
-    if (valid) load_geometry<DT>(nd, i, g);
+    bool valid;
+    stage_geometry<DT>(nd, c, lane, W, g, valid);
     stage_sh<DT>(nd, c, lane, shc[wib]);
-    const float* coef = shc[wib] + lane * kShStride;
-    for (int e = nv_off[k]; e < nv_off[k + 1]; ++e) {
-        const NodeView w = nv[e];
-        if (w.view < v0 || w.view >= v1) continue;
-        emit_chunk(nd, c, lane, w.view, vnodes[w.view * K + w.slot], views[w.view], P, g, valid, i, coef, wsp[wib],
-                   inst_off, pair_off, inst_base, pair_base, rec, keys, vals);
-    }
+    process_chunk<true>(nd, c, lane, nv + nv_off[k], nv_off[k + 1] - nv_off[k], v0, v1, views, vnodes, K, P, g, valid,
+                        W, shc[wib], const_cast<uint2*>(counts), inst_off, pair_off, inst_base, pair_base, rec, keys,
+                        vals);
 }
 
 template <int DT>
 __global__ void __launch_bounds__(kEmitWarps * 32) k_emit_plain(const NodeDesc* __restrict__ nodes,
         const ViewDesc* __restrict__ views, const VNode* __restrict__ vnodes, int K, Params P, int v,
-        const int32_t* __restrict__ pmap, int n_view_chunks, const uint32_t* __restrict__ inst_off,
-        const uint64_t* __restrict__ pair_off, uint32_t inst_base, uint64_t pair_base, Record* __restrict__ rec,
-        uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-    __shared__ WarpSplats wsp[kEmitWarps];
+        const int32_t* __restrict__ pmap, int n_view_chunks, const uint2* __restrict__ counts,
+        const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off, uint32_t inst_base,
+        uint64_t pair_base, Record* __restrict__ rec, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    __shared__ WarpWork ww[kEmitWarps];
     __shared__ float shc[kEmitWarps][kChunk * kShStride];
     const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (w >= n_view_chunks) return;
     const int lane = (int)lane_id(), wib = threadIdx.x >> 5;
+    WarpWork& W = ww[wib];
     int lo = 0, hi = K - 1;
     while (lo < hi) { const int mid = (lo + hi + 1) >> 1; if (pmap[mid] <= w) lo = mid; else hi = mid - 1; }
     const int slot = pmap[K + 1 + lo];
-    const VNode& vn = vnodes[v * K + slot];
-    const NodeDesc& nd = nodes[vn.node];
+    const NodeDesc& nd = nodes[vnodes[v * K + slot].node];
     if (nd.dtype != DT) return;
     const int c = w - pmap[lo];
-    const int64_t i = (int64_t)c * kChunk + lane;
-    const bool valid = i < nd.n;
     Gauss g;
-    if (valid) load_geometry<DT>(nd, i, g);
+    bool valid;
+    stage_geometry<DT>(nd, c, lane, W, g, valid);
     stage_sh<DT>(nd, c, lane, shc[wib]);
-    emit_chunk(nd, c, lane, v, vn, views[v], P, g, valid, i, shc[wib] + lane * kShStride, wsp[wib], inst_off,
-               pair_off, inst_base, pair_base, rec, keys, vals);
+    const NodeView one{v, slot};
+    process_chunk<true>(nd, c, lane, &one, 1, v, v + 1, views, vnodes, K, P, g, valid, W, shc[wib],
+                        const_cast<uint2*>(counts), inst_off, pair_off, inst_base, pair_base, rec, keys, vals);
 }
 
 // ------------------------------------------------------------------ exclusive scan of the count table
@@ -549,7 +695,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_partial(const uint2* __re
     uint64_t a = 0, b = 0;
     for (int j = 0; j < kScanItems; ++j) {
         const int64_t i = base + j;
-        if (i < n) { const uint2 c = counts[i]; a += c.x; b += c.y; }
+        if (i < n) { const uint2 c = counts[i]; a += __popc(c.x); b += c.y; }
     }
     uint64_t ta, tb;
     block_excl_scan2(a, b, ta, tb);
@@ -584,7 +730,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(const uint2* __rest
     for (int j = 0; j < kScanItems; ++j) {
         const int64_t i = base + j;
         c[j] = i < n ? counts[i] : make_uint2(0, 0);
-        a += c[j].x; b += c[j].y;
+        a += __popc(c[j].x); b += c[j].y;
     }
     uint64_t ta, tb;
     block_excl_scan2(a, b, ta, tb);
@@ -594,7 +740,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(const uint2* __rest
         const int64_t i = base + j;
         if (i < n) { inst_off[i] = (uint32_t)a; pair_off[i] = b; }
         if (i == n) { inst_off[i] = (uint32_t)a; pair_off[i] = b; }
-        a += c[j].x; b += c[j].y;
+        a += __popc(c[j].x); b += c[j].y;
     }
     if (n % kScanTile == 0 && blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) {
         inst_off[n] = (uint32_t)a; pair_off[n] = b;
@@ -606,14 +752,14 @@ void count_launch(const Launch& L, const NodeDesc* nodes, int n_nodes, const Vie
                   const NodeView* nv, const int32_t* nv_off, int n_chunks, const Params& P, int v0, int v1,
                   bool batched, const int32_t* pmap, int64_t view_chunks, uint2* counts) {
     if (batched) {
-        const int blocks = (int)(((int64_t)n_chunks * 32 + 255) / 256);
+        const int blocks = (int)(((int64_t)n_chunks + kCountWarps - 1) / kCountWarps);
         if (blocks == 0) return;
-        k_count_batched<DT><<<blocks, 256, 0, L.stream>>>(nodes, n_nodes, views, vnodes, K, nv, nv_off, n_chunks, P,
+        k_count_batched<DT><<<blocks, kCountWarps * 32, 0, L.stream>>>(nodes, n_nodes, views, vnodes, K, nv, nv_off, n_chunks, P,
                                                           v0, v1, counts);
     } else {
-        const int blocks = (int)((view_chunks * 32 + 255) / 256);
+        const int blocks = (int)((view_chunks + kCountWarps - 1) / kCountWarps);
         if (blocks == 0) return;
-        k_count_plain<DT><<<blocks, 256, 0, L.stream>>>(nodes, views, vnodes, K, P, v0, pmap, (int)view_chunks, counts);
+        k_count_plain<DT><<<blocks, kCountWarps * 32, 0, L.stream>>>(nodes, views, vnodes, K, P, v0, pmap, (int)view_chunks, counts);
     }
     ++*L.launches;
 }
@@ -621,18 +767,21 @@ void count_launch(const Launch& L, const NodeDesc* nodes, int n_nodes, const Vie
 template <int DT>
 void emit_launch(const Launch& L, const NodeDesc* nodes, int n_nodes, const ViewDesc* views, const VNode* vnodes, int K,
                  const NodeView* nv, const int32_t* nv_off, int n_chunks, const Params& P, int v0, int v1, bool batched,
-                 const int32_t* pmap, int64_t view_chunks, const uint32_t* inst_off, const uint64_t* pair_off,
-                 uint32_t inst_base, uint64_t pair_base, Record* rec, uint64_t* keys, uint32_t* vals) {
+                 const int32_t* pmap, int64_t view_chunks, const uint2* counts, const uint32_t* inst_off,
+                 const uint64_t* pair_off, uint32_t inst_base, uint64_t pair_base, Record* rec, uint64_t* keys,
+                 uint32_t* vals) {
     if (batched) {
         const int blocks = (int)(((int64_t)n_chunks + kEmitWarps - 1) / kEmitWarps);
         if (blocks == 0) return;
-        k_emit_batched<DT><<<blocks, kEmitWarps * 32, 0, L.stream>>>(nodes, n_nodes, views, vnodes, K, nv, nv_off, n_chunks, P, v0,
-                                                         v1, inst_off, pair_off, inst_base, pair_base, rec, keys, vals);
+        k_emit_batched<DT><<<blocks, kEmitWarps * 32, 0, L.stream>>>(nodes, n_nodes, views, vnodes, K, nv, nv_off, n_chunks,
+                                                                     P, v0, v1, counts, inst_off, pair_off, inst_base,
+                                                                     pair_base, rec, keys, vals);
     } else {
         const int blocks = (int)((view_chunks + kEmitWarps - 1) / kEmitWarps);
         if (blocks == 0) return;
-        k_emit_plain<DT><<<blocks, kEmitWarps * 32, 0, L.stream>>>(nodes, views, vnodes, K, P, v0, pmap, (int)view_chunks, inst_off,
-                                                       pair_off, inst_base, pair_base, rec, keys, vals);
+        k_emit_plain<DT><<<blocks, kEmitWarps * 32, 0, L.stream>>>(nodes, views, vnodes, K, P, v0, pmap, (int)view_chunks,
+                                                                   counts, inst_off, pair_off, inst_base, pair_base,
+                                                                   rec, keys, vals);
     }
     ++*L.launches;
 }
@@ -665,17 +814,18 @@ void launch_count(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_
 void launch_emit(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_nodes, const ViewDesc* views,
                  const VNode* vnodes, int K, const NodeView* node_views, const int32_t* node_view_off,
                  int n_chunks_total, const Params& P, int v0, int v1, bool batched, const int32_t* pmap,
-                 int64_t view_chunks, const uint32_t* inst_off, const uint64_t* pair_off, uint32_t inst_base,
+                 int64_t view_chunks, const uint2* counts, const uint32_t* inst_off, const uint64_t* pair_off,
+                 uint32_t inst_base,
                  uint64_t pair_base, Record* records, uint64_t* keys, uint32_t* vals) {
     if (dtype_mask & (1 << DGS_F32))
         emit_launch<DGS_F32>(L, nodes, n_nodes, views, vnodes, K, node_views, node_view_off, n_chunks_total, P, v0, v1,
-                             batched, pmap, view_chunks, inst_off, pair_off, inst_base, pair_base, records, keys, vals);
+                             batched, pmap, view_chunks, counts, inst_off, pair_off, inst_base, pair_base, records, keys, vals);
     if (dtype_mask & (1 << DGS_BF16))
         emit_launch<DGS_BF16>(L, nodes, n_nodes, views, vnodes, K, node_views, node_view_off, n_chunks_total, P, v0, v1,
-                              batched, pmap, view_chunks, inst_off, pair_off, inst_base, pair_base, records, keys, vals);
+                              batched, pmap, view_chunks, counts, inst_off, pair_off, inst_base, pair_base, records, keys, vals);
     if (dtype_mask & (1 << DGS_F16))
         emit_launch<DGS_F16>(L, nodes, n_nodes, views, vnodes, K, node_views, node_view_off, n_chunks_total, P, v0, v1,
-                             batched, pmap, view_chunks, inst_off, pair_off, inst_base, pair_base, records, keys, vals);
+                             batched, pmap, view_chunks, counts, inst_off, pair_off, inst_base, pair_base, records, keys, vals);
 }
 
 void launch_scan(const Launch& L, const uint2* counts, int64_t n, uint32_t* inst_off, uint64_t* pair_off,
