@@ -86,7 +86,7 @@ typedef struct dgs_camera {
 
 typedef struct dgs_options {
     int32_t mode;               /* dgs_mode, default DGS_MODE_BATCHED */
-    int32_t tile_w, tile_h;     /* tile shape in pixels; w*h in {64,128,256}, default 16x16 */
+    int32_t tile_w, tile_h;     /* tile shape: w a multiple of 8, h of 4, w*h in {64,128,256}; 16x16 */
     int32_t exact_tile_test;    /* 1 = bin a Gaussian only to tiles its ellipse reaches (default) */
     float z_near;               /* default 0.01; must be > 0 */
     float lowpass;              /* screen-space dilation added to the 2D covariance, default 0.3 px^2 */

@@ -114,7 +114,10 @@ bool finite(float x) { return std::isfinite(x); }
 int check_options(const dgs_options* o, std::string& why) {
     if (o->mode != DGS_MODE_PLAIN && o->mode != DGS_MODE_BATCHED) { why = "mode"; return 0; }
     const int area = o->tile_w * o->tile_h;
-    if (o->tile_w < 1 || o->tile_h < 1 || (area != 64 && area != 128 && area != 256)) { why = "tile shape"; return 0; }
+    if (o->tile_w < 8 || o->tile_h < 4 || o->tile_w % 8 || o->tile_h % 4 || (area != 64 && area != 128 && area != 256)) {
+        why = "tile shape";
+        return 0;
+    }
     if (!(o->z_near > 0) || !finite(o->z_near)) { why = "z_near"; return 0; }
     if (!(o->lowpass >= 0) || !finite(o->lowpass)) { why = "lowpass"; return 0; }
     if (!(o->alpha_min >= 0) || !(o->alpha_max > 0) || !(o->alpha_max <= 1)) { why = "alpha limits"; return 0; }

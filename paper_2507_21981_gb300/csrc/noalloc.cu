@@ -86,7 +86,8 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
     if (opt) o = *opt; else dgs_default_options(&o);
     {
         const int area = o.tile_w * o.tile_h;
-        if (o.tile_w < 1 || o.tile_h < 1 || (area != 64 && area != 128 && area != 256)) return DGS_ERR_INVALID_ARG;
+        if (o.tile_w < 8 || o.tile_h < 4 || o.tile_w % 8 || o.tile_h % 4 || (area != 64 && area != 128 && area != 256))
+            return DGS_ERR_INVALID_ARG;
         if (!(o.z_near > 0) || !(o.q_max > 0) || !(o.guard > 0) || !(o.lowpass >= 0)) return DGS_ERR_INVALID_ARG;
     }
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
