@@ -381,6 +381,9 @@ struct PixelResult {
     double tol_rgb = 0, tol_d = 0;
     bool ambiguous = false;
     int64_t amb_kind[4] = {0, 0, 0, 0};   // near, ellipse, alpha, transmittance
+    int64_t contrib = 0;                  // Gaussians composited (primary branch)
+    int64_t reached = 0;                  // in-ellipse Gaussians reached before termination (primary)
+    bool terminated = false;
     uint64_t hash = 1469598103934665603ull;
 };
 
@@ -445,8 +448,10 @@ struct Compositor {
                                          32 * (G.raw[1] <= 0) + 64 * (G.raw[2] <= 0);
                 R->hash = mix(R->hash, (uint64_t)cd.gid * 128 + code);
             }
+            if (primary && d[0] && d[1]) R->reached++;
             if (act == SKIP) continue;
-            if (act == STOP) break;
+            if (act == STOP) { if (primary) R->terminated = true; break; }
+            if (primary) R->contrib++;
             const double w = alpha * T;
             C0 += w * G.rgb[0]; C1 += w * G.rgb[1]; C2 += w * G.rgb[2]; D += w * G.z;
             T = Tn;
@@ -534,7 +539,9 @@ int64_t oracle_project_view(const oracle_scene* s, const oracle_opts* o, int e, 
 // of alternative branches of each pixel; alt [alt_cap*5] receives them (r,g,b,d,a) in pixel
 // order.  stats[0] = alternatives needed, stats[1] = ambiguous pixels, stats[2] = decision
 // hash (as bits), stats[3] = instances projected, stats[4..7] = ambiguous decisions on the
-// primary branch by kind (near plane, ellipse, alpha_min, t_min); stats needs 8 entries.  Returns 0, or -1 on bad arguments, or 1 if
+// primary branch by kind (near plane, ellipse, alpha_min, t_min), stats[8] = Gaussians
+// composited, stats[9] = in-ellipse Gaussians reached before termination, stats[10] = pixels
+// that terminated (all on the primary branch); stats needs 11 entries.  Returns 0, or -1 on bad arguments, or 1 if
 // alt_cap was too small (outputs other than alt are still complete).
 int oracle_render_view(const oracle_scene* s, const oracle_opts* o, int e, int c,
                        double* rgb, double* depth, double* alpha, double* tol_rgb, double* tol_d,
@@ -547,7 +554,7 @@ int oracle_render_view(const oracle_scene* s, const oracle_opts* o, int e, int c
     std::vector<std::vector<Leaf>> row_alts(H);
     std::vector<int64_t> row_amb(H, 0);
     std::vector<uint64_t> row_hash(H, 0);
-    std::vector<int64_t> row_kind((size_t)H * 4, 0);
+    std::vector<int64_t> row_kind((size_t)H * 4, 0), row_work((size_t)H * 3, 0);
     parallel_for(H, n_threads(o), [&](int64_t y, int) {
         std::vector<std::vector<int>> cols(W);
         cols_pool(V, o, rows[y], cols);
@@ -573,6 +580,9 @@ int oracle_render_view(const oracle_scene* s, const oracle_opts* o, int e, int c
             for (auto& L : R.alts) row_alts[y].push_back(L);
             row_amb[y] += R.ambiguous;
             for (int k = 0; k < 4; ++k) row_kind[(size_t)y * 4 + k] += R.amb_kind[k];
+            row_work[(size_t)y * 3 + 0] += R.contrib;
+            row_work[(size_t)y * 3 + 1] += R.reached;
+            row_work[(size_t)y * 3 + 2] += R.terminated;
             hsum += mix(R.hash, (uint64_t)p);
         }
         row_hash[y] = hsum;
@@ -582,6 +592,7 @@ int oracle_render_view(const oracle_scene* s, const oracle_opts* o, int e, int c
     if (stats) {
         stats[0] = need; stats[1] = amb; std::memcpy(&stats[2], &h, 8); stats[3] = (int64_t)V.geo.size();
         for (int k = 0; k < 4; ++k) { int64_t s = 0; for (int y = 0; y < H; ++y) s += row_kind[(size_t)y * 4 + k]; stats[4 + k] = s; }
+        for (int k = 0; k < 3; ++k) { int64_t s = 0; for (int y = 0; y < H; ++y) s += row_work[(size_t)y * 3 + k]; stats[8 + k] = s; }
     }
     if (alt && need <= alt_cap) {
         int64_t k = 0;

@@ -167,6 +167,7 @@ class ViewResult:
     decision_hash: int
     instances: int
     ambiguous_by_kind: dict = field(default=None)
+    work: dict = field(default=None)
     alt_offsets: np.ndarray = field(default=None)
 
     def alternatives(self, p: int) -> np.ndarray:
@@ -182,7 +183,7 @@ def render_view(scene, e: int, c: int, opts: OracleOptions | None = None, packed
     W, H = (int(x) for x in scene.cam_res[e, c])
     rgb = np.zeros((H, W, 3)); depth = np.zeros((H, W)); alpha = np.zeros((H, W))
     tr = np.zeros((H, W)); td = np.zeros((H, W)); na = np.zeros((H, W), np.int32)
-    stats = np.zeros(8, np.int64)
+    stats = np.zeros(11, np.int64)
     cap = max(1024, W * H // 8)
     alt = np.zeros((cap, 5))
     rc = lib.oracle_render_view(C.byref(pk.c), C.byref(o), e, c, _p(rgb), _p(depth), _p(alpha), _p(tr), _p(td),
@@ -195,8 +196,9 @@ def render_view(scene, e: int, c: int, opts: OracleOptions | None = None, packed
     if rc != 0:
         raise ValueError(f"oracle_render_view failed ({rc})")
     kinds = dict(zip(("near", "ellipse", "alpha", "transmittance"), (int(x) for x in stats[4:8])))
+    work = dict(contributions=int(stats[8]), reached=int(stats[9]), terminated_pixels=int(stats[10]))
     return ViewResult(rgb, depth, alpha, tr, td, na, alt[: int(stats[0])], int(stats[1]),
-                      int(np.uint64(stats[2].view(np.uint64))), int(stats[3]), kinds)
+                      int(np.uint64(stats[2].view(np.uint64))), int(stats[3]), kinds, work)
 
 
 def _grad_buffers(pk, scene):

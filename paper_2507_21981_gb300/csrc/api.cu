@@ -39,8 +39,8 @@ struct dgs_ctx {
     dgs_options opt{};
     std::string err;
     int device = 0;
-    DevBuf meta, counts, inst_off, pair_off, parts, records, keys0, vals0, keys1, vals1, hist, status, counters, ranges,
-        errword, readback;
+    DevBuf meta, counts, inst_off, pair_off, parts, records, info, keys0, vals0, keys1, vals1, hist, status, counters,
+        ranges, errword, readback;
     void* h_meta = nullptr;
     size_t h_meta_bytes = 0;
     void* h_read = nullptr;
@@ -212,7 +212,7 @@ int dgs_context_create(dgs_ctx** out, const dgs_options* opt) {
 int dgs_context_destroy(dgs_ctx* ctx) {
     if (!ctx) return DGS_OK;
     cudaDeviceSynchronize();
-    DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->records,
+    DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->records, &ctx->info,
                       &ctx->keys0, &ctx->vals0, &ctx->keys1, &ctx->vals1, &ctx->hist, &ctx->status, &ctx->counters,
                       &ctx->ranges, &ctx->errword, &ctx->readback};
     for (DevBuf* b : bufs) free_buf(*b);
@@ -228,7 +228,7 @@ const char* dgs_last_error(const dgs_ctx* ctx) { return ctx ? ctx->err.c_str() :
 int dgs_workspace_query(const dgs_ctx* ctx, size_t* bytes) {
     if (!ctx || !bytes) return DGS_ERR_INVALID_ARG;
     const DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->records,
-                            &ctx->keys0, &ctx->vals0, &ctx->keys1, &ctx->vals1, &ctx->hist, &ctx->status,
+                            &ctx->info, &ctx->keys0, &ctx->vals0, &ctx->keys1, &ctx->vals1, &ctx->hist, &ctx->status,
                             &ctx->counters, &ctx->ranges, &ctx->errword, &ctx->readback};
     size_t s = 0;
     for (const DevBuf* b : bufs) s += b->bytes;
@@ -534,6 +534,7 @@ int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32
     ctx->stats.n_groups = (int32_t)groups.size();
     ctx->stats.key_bits = max_bits;
     if ((rc = ensure(ctx, ctx->records, sizeof(Record) * max_inst))) return rc;
+    if ((rc = ensure(ctx, ctx->info, sizeof(InstInfo) * max_inst))) return rc;
     if ((rc = ensure(ctx, ctx->keys0, sizeof(uint64_t) * max_pairs))) return rc;
     if ((rc = ensure(ctx, ctx->keys1, sizeof(uint64_t) * max_pairs))) return rc;
     if ((rc = ensure(ctx, ctx->vals0, sizeof(uint32_t) * max_pairs))) return rc;
@@ -555,7 +556,8 @@ int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32
         launch_emit(L, dtype_mask, d_nodes, n_nodes, d_views, d_vnodes, K, d_nv, d_nvoff, (int)chunk_total, Pg, v0, v1,
                     batched, d_pmap + (size_t)v0 * (2 * K + 1), view_tab[v0 + 1] - view_tab[v0], d_counts, d_inst_off,
                     d_pair_off,
-                    (uint32_t)inst_at[v0], pair_at[v0], d_rec, static_cast<uint64_t*>(ctx->keys0.p),
+                    (uint32_t)inst_at[v0], pair_at[v0], d_rec, static_cast<InstInfo*>(ctx->info.p),
+                    static_cast<uint64_t*>(ctx->keys0.p),
                     static_cast<uint32_t*>(ctx->vals0.p));
         tm.end();
         tm.begin(DGS_K_SORT);

@@ -4,10 +4,9 @@
 // Gaussians and each pixel alpha-blends them front to back.  Sec. III-C: the depth image is
 // produced the same way, by alpha-compositing the camera-space z of the Gaussians.
 //
-// One block per tile, one thread per pixel, one warp per 8x4 sub-tile.  The block walks its run
-// in batches of blockDim records staged in shared memory; a pixel stops at the first Gaussian
-// that would drive its transmittance below t_min (that Gaussian is not composited) and the
-// block leaves the loop once all of its pixels have stopped (__syncthreads_count).
+// One block per tile, one warp per 8x4 sub-tile, one thread per pixel.  A pixel stops at the
+// first Gaussian that would drive its transmittance below t_min (that Gaussian is not
+// composited); a warp stops once all of its pixels have.
 #include "dgs_internal.cuh"
 
 namespace dgs {
@@ -22,36 +21,40 @@ __global__ void k_ranges(const uint64_t* __restrict__ keys, uint32_t n, uint2* _
     if (i + 1 == n || (keys[i + 1] >> kZBits) != t) ranges[t].y = i + 1;
 }
 
-// Does the ellipse {d^T Q d <= qlim}, Q = [[a, b], [b, c]], reach the rectangle of pixel
+// Does the ellipse {q <= qlim}, q = qa (dx + qb dy)^2 + qc dy^2, reach the rectangle of pixel
 // centres [X0, X1] x [Y0, Y1] (relative to the mean)?  Minimum of q over the rectangle: 0 if
-// the mean is inside, else the smallest of the four edge minima.
-__device__ __forceinline__ bool ellipse_meets(float a, float b, float c, float ia, float ic, float qlim, float X0,
-                                              float X1, float Y0, float Y1) {
+// the mean is inside; else the least of the edge minima -- on a horizontal edge dy = Y the
+// minimiser is dx = -qb Y, on a vertical edge dx = X it is dy = -qa qb X / (qa qb^2 + qc) --
+// each clamped to its edge.
+__device__ __forceinline__ bool ellipse_meets(float qa, float qb, float qc, float qlim, float X0, float X1, float Y0,
+                                              float Y1) {
     if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return true;
+    const float k = -qa * qb / fmaf(qa * qb, qb, qc);
     float m = INFINITY;
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-        const float X = e ? X1 : X0;
-        const float Y = fminf(Y1, fmaxf(Y0, -b * X * ic));
-        m = fminf(m, fmaf(a * X, X, fmaf(2.f * b * X, Y, c * Y * Y)));
-        const float Yh = e ? Y1 : Y0;
-        const float Xh = fminf(X1, fmaxf(X0, -b * Yh * ia));
-        m = fminf(m, fmaf(a * Xh, Xh, fmaf(2.f * b * Xh, Yh, c * Yh * Yh)));
+        const float Y = e ? Y1 : Y0;
+        const float X = fminf(X1, fmaxf(X0, -qb * Y));
+        const float t = fmaf(qb, Y, X);
+        m = fminf(m, fmaf(qa * t, t, qc * Y * Y));
+        const float Xv = e ? X1 : X0;
+        const float Yv = fminf(Y1, fmaxf(Y0, k * Xv));
+        const float tv = fmaf(qb, Yv, Xv);
+        m = fminf(m, fmaf(qa * tv, tv, qc * Yv * Yv));
     }
     return m <= qlim;
 }
 
-// Block = one tile, warp = one 8x4 sub-tile of it, lane = one pixel.  Per batch of staged
-// records the loader thread of each record computes the set of sub-tiles its ellipse can reach
-// (box overlap, then the exact ellipse-rectangle test with the binning margin), and every warp
-// evaluates only the records whose bit it holds, in list order.
+// Block = one tile, warp = one 8x4 sub-tile, lane = one pixel.  Warps are independent (no
+// block barrier): each walks the tile's list 32 entries at a time, keeps the entries whose
+// pixel box overlaps its sub-tile and whose ellipse reaches one of its pixel centres (exact
+// test with the binning margin), stages them in list order in its own shared memory and
+// composites them; it stops once its 32 pixels have terminated.
 __global__ void __launch_bounds__(256) k_composite(const ViewDesc* __restrict__ views, int v0, int nv,
                                                    const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                                                    const Record* __restrict__ rec, Params P, float* __restrict__ out_rgb,
                                                    float* __restrict__ out_depth, float* __restrict__ out_alpha) {
-    __shared__ float4 s0[256], s1[256], s2[256];
-    __shared__ uint32_t s_mask[256];
-    __shared__ uint8_t s_list[8][256];
+    __shared__ float4 s_rec[8][3][32];
     const int gt = blockIdx.x;                 // tile within the group
     const int ga = gt + P.tile0;               // tile within the call
     // view of this tile: last view of the group whose tile_base <= ga
@@ -64,73 +67,61 @@ __global__ void __launch_bounds__(256) k_composite(const ViewDesc* __restrict__ 
     const int tile = ga - vd.tile_base;
     const int tx = tile % vd.tiles_x, ty = tile / vd.tiles_x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
     const int sub_cols = P.tile_w >> 3;        // 8-pixel-wide sub-tiles per tile row
-    const int tile_x0 = tx * P.tile_w, tile_y0 = ty * P.tile_h;
-    const int wx0 = tile_x0 + (w % sub_cols) * 8, wy0 = tile_y0 + (w / sub_cols) * 4;
+    const int wx0 = tx * P.tile_w + (w % sub_cols) * 8, wy0 = ty * P.tile_h + (w / sub_cols) * 4;
+    const int wx1 = min(wx0 + 7, vd.W - 1), wy1 = min(wy0 + 3, vd.H - 1);
+    if (wx0 > wx1 || wy0 > wy1) return;        // sub-tile outside the image
     const int px = wx0 + (lane & 7), py = wy0 + (lane >> 3);
     const bool inside = px < vd.W && py < vd.H;
     const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
     const uint2 range = ranges[gt];
-    const int nthreads = blockDim.x;
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
     bool done = !inside;
     const uint32_t lt = (1u << lane) - 1u;
-    for (uint32_t b = range.x; b < range.y; b += nthreads) {
-        if (__syncthreads_count(done) == nthreads) break;
-        const uint32_t i = b + threadIdx.x;
+    float4* const sr0 = s_rec[w][0];
+    float4* const sr1 = s_rec[w][1];
+    float4* const sr2 = s_rec[w][2];
+    for (uint32_t base = range.x; base < range.y; base += 32) {
+        if (__all_sync(0xffffffffu, done)) break;
+        const uint32_t i = base + lane;
+        bool rel = false;
+        float4 a, q, col;
         if (i < range.y) {
-            const Record& r = rec[vals[i]];
-            const float4 a = r.r0, q = r.r1;
-            s0[threadIdx.x] = a;
-            s1[threadIdx.x] = q;
-            s2[threadIdx.x] = r.r2;
-            // conic of the factored form q = qa (dx + qb dy)^2 + qc dy^2 and its pixel box
-            const float ca = q.x, cb = q.x * q.y, cc = fmaf(q.x * q.y, q.y, q.z);
-            const float hx = sqrtf(P.qbin * (q.y * q.y / q.z + 1.f / q.x)), hy = sqrtf(P.qbin / q.z);
-            const float ia = 1.f / ca, ic = 1.f / cc;
-            uint32_t m = 0;
-            for (int k = 0; k < nwarps; ++k) {
-                const int X0 = tile_x0 + (k % sub_cols) * 8, Y0 = tile_y0 + (k / sub_cols) * 4;
-                const int X1 = min(X0 + 7, vd.W - 1), Y1 = min(Y0 + 3, vd.H - 1);
-                if (X0 > X1 || Y0 > Y1) continue;
-                const float dx0 = (float)X0 + 0.5f - a.x, dx1 = (float)X1 + 0.5f - a.x;
-                const float dy0 = (float)Y0 + 0.5f - a.y, dy1 = (float)Y1 + 0.5f - a.y;
-                if (dx0 > hx || dx1 < -hx || dy0 > hy || dy1 < -hy) continue;
-                if (ellipse_meets(ca, cb, cc, ia, ic, P.qbin, dx0, dx1, dy0, dy1)) m |= 1u << k;
+            const Record* r = rec + vals[i];
+            q = r->r1;
+            const uint32_t bx = __float_as_uint(q.w), by = __float_as_uint(r->r2.w);
+            if ((int)(bx & 0xFFFFu) <= wx1 && (int)(bx >> 16) >= wx0 && (int)(by & 0xFFFFu) <= wy1 && (int)(by >> 16) >= wy0) {
+                a = r->r0;
+                col = r->r2;
+                rel = ellipse_meets(q.x, q.y, q.z, P.qbin, (float)wx0 + 0.5f - a.x, (float)wx1 + 0.5f - a.x,
+                                    (float)wy0 + 0.5f - a.y, (float)wy1 + 0.5f - a.y);
             }
-            s_mask[threadIdx.x] = m;
         }
-        __syncthreads();
-        // this warp's records of the batch, in list order
-        const int cnt = (int)umin((uint32_t)nthreads, range.y - b);
-        int n_mine = 0;
-        for (int base = 0; base < cnt; base += 32) {
-            const int j = base + lane;
-            const bool rel = j < cnt && ((s_mask[j] >> w) & 1u);
-            const uint32_t bal = __ballot_sync(0xffffffffu, rel);
-            if (rel) s_list[w][n_mine + __popc(bal & lt)] = (uint8_t)j;
-            n_mine += __popc(bal);
+        const uint32_t m = __ballot_sync(0xffffffffu, rel);
+        if (m == 0) continue;
+        if (rel) {
+            const int pos = __popc(m & lt);
+            sr0[pos] = a; sr1[pos] = q; sr2[pos] = col;
         }
         __syncwarp();
-        for (int k = 0; k < n_mine && !done; ++k) {
-            const int j = s_list[w][k];
-            const float4 a = s0[j], c = s1[j];
-            const float dx = fx - a.x, dy = fy - a.y;
-            const float t = fmaf(c.y, dy, dx);
-            const float q = fmaf(c.x * t, t, c.z * dy * dy);
-            if (q > P.q_max) continue;
-            const float alpha = fminf(P.alpha_max, a.z * __expf(-0.5f * q));
+        const int n = __popc(m);
+        for (int k = 0; k < n && !done; ++k) {
+            const float4 g0 = sr0[k], g1 = sr1[k];
+            const float dx = fx - g0.x, dy = fy - g0.y;
+            const float t = fmaf(g1.y, dy, dx);
+            const float qq = fmaf(g1.x * t, t, g1.z * dy * dy);
+            if (qq > P.q_max) continue;
+            const float alpha = fminf(P.alpha_max, g0.z * __expf(-0.5f * qq));
             if (alpha < P.alpha_min) continue;
             const float Tn = T * (1.f - alpha);
             if (Tn < P.t_min) { done = true; break; }
             const float wgt = alpha * T;
-            const float4 col = s2[j];
-            C0 = fmaf(wgt, col.x, C0); C1 = fmaf(wgt, col.y, C1); C2 = fmaf(wgt, col.z, C2);
-            D = fmaf(wgt, a.w, D);
+            const float4 g2 = sr2[k];
+            C0 = fmaf(wgt, g2.x, C0); C1 = fmaf(wgt, g2.y, C1); C2 = fmaf(wgt, g2.z, C2);
+            D = fmaf(wgt, g0.w, D);
             T = Tn;
         }
-        __syncthreads();
+        __syncwarp();
     }
     if (inside) {
         const int64_t p = vd.pix_off + (int64_t)py * vd.W + px;

@@ -66,10 +66,17 @@ struct Params {
 };
 
 // Projected instance as stored for compositing: 48 bytes.
-//   r0 = (u, v, opacity, z), r1 = (qa, qb, qc, gid bits), r2 = (r, g, b, view bits), with
-//   d^T conic d = qa (dx + qb dy)^2 + qc dy^2
+//   r0 = (u, v, opacity, z), r1 = (qa, qb, qc, box x), r2 = (r, g, b, box y), with
+//   d^T conic d = qa (dx + qb dy)^2 + qc dy^2 and box x/y = pixel index range of the ellipse's
+//   bounding box packed as lo | hi << 16.
 struct Record {
     float4 r0, r1, r2;
+};
+
+// Identity of a projected instance (read by the adjoint): global Gaussian id and view.
+struct InstInfo {
+    uint32_t gid;
+    uint32_t view;
 };
 
 // (view, slot) entries of node k: node_views[node_view_off[k] .. node_view_off[k+1])
@@ -116,7 +123,7 @@ void launch_emit(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_n
                  int n_chunks_total, const Params& P, int v0, int v1, bool batched, const int32_t* view_chunk_nodes,
                  int64_t view_chunks, const uint2* counts, const uint32_t* inst_off, const uint64_t* pair_off,
                  uint32_t inst_base,
-                 uint64_t pair_base, Record* records, uint64_t* keys, uint32_t* vals);
+                 uint64_t pair_base, Record* records, InstInfo* info, uint64_t* keys, uint32_t* vals);
 
 void launch_sort(const Launch& L, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                  uint32_t n, int key_bits, uint32_t* hist, uint32_t* status, uint32_t* counters, uint32_t* err,

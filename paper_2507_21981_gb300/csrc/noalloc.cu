@@ -243,6 +243,7 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
 
     // ---------------------------------------------------------------- phase 2 scratch
     Record* d_rec = cv.take<Record>(n_vis);
+    InstInfo* d_info = cv.take<InstInfo>(n_vis);
     uint64_t* d_k0 = cv.take<uint64_t>(n_pairs);
     uint64_t* d_k1 = cv.take<uint64_t>(n_pairs);
     uint32_t* d_v0 = cv.take<uint32_t>(n_pairs);
@@ -253,7 +254,7 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
     uint2* d_ranges = cv.take<uint2>((size_t)tiles_total);
     if (!cv.ok) return DGS_ERR_CAPACITY;
     launch_emit(L, dtype_mask, d_nodes, n_nodes, d_views, d_vnodes, K, d_nv, d_nvoff, (int)chunk_total, P, 0, V, true,
-                nullptr, 0, d_counts, d_inst_off, d_pair_off, 0u, 0ull, d_rec, d_k0, d_v0);
+                nullptr, 0, d_counts, d_inst_off, d_pair_off, 0u, 0ull, d_rec, d_info, d_k0, d_v0);
     uint64_t* skeys;
     uint32_t* svals;
     const int bits = kZBits + std::max(1, bits_for_tiles((uint64_t)tiles_total));

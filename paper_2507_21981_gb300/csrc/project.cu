@@ -260,6 +260,7 @@ struct WarpViews {
     int32_t vv[kViewBlock];       // (view, slot) index of view j, -1 = none
     uint32_t vis[kViewBlock];     // count pass: lanes whose projection succeeded
     uint32_t hits[kViewBlock];    // count pass: pairs of view j
+    uint32_t ibase[kViewBlock];   // emit: first record of (view j, chunk) relative to the group
 };
 
 __device__ __forceinline__ void stash_splat(WarpSplats& S, int lane, const Splat& s, uint32_t excl) {
@@ -457,35 +458,40 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
                                               bool valid, WarpWork& W, const float* __restrict__ shc,
                                               uint2* __restrict__ counts, const uint32_t* __restrict__ inst_off,
                                               const uint64_t* __restrict__ pair_off, uint32_t inst_base,
-                                              uint64_t pair_base, Record* __restrict__ rec,
+                                              uint64_t pair_base, Record* __restrict__ rec, InstInfo* __restrict__ info,
                                               uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
     WarpViews& WV = W.WV;
     for (int eb = 0; eb < n_entries; eb += kViewBlock) {
         const int nvb = min(kViewBlock, n_entries - eb);
-        // 1. survivors of each view of the block
-        for (int j = 0; j < nvb; ++j) {
+        // 1. survivors of each view of the block: lane j fetches the table entries of view j
+        //    (one round of loads for the whole block), then one ballot per view (count pass)
+        if (lane < nvb) {
+            const int j = lane;
             const NodeView w = entries[eb + j];
             const bool in = w.view >= v0 && w.view < v1;
-            const int vvj = in ? w.view * K + w.slot : -1;
-            uint32_t m = 0;
-            int64_t t = 0;
+            WV.vv[j] = in ? w.view * K + w.slot : -1;
+            WV.vis[j] = 0; WV.hits[j] = 0; WV.run[j] = 0; WV.mask[j] = 0;
             if (in) {
-                const VNode& vn = vnodes[vvj];
-                t = vn.tab + c;
-                if constexpr (!EMIT) m = __ballot_sync(0xffffffffu, valid && may_be_visible(gme, vn, views[w.view], P));
-                else m = counts[t].x;
-            }
-            if (lane == j) {
-                WV.mask[j] = m; WV.vv[j] = vvj; WV.tab[j] = t; WV.vis[j] = 0; WV.hits[j] = 0; WV.run[j] = 0;
+                const int64_t t = vnodes[w.view * K + w.slot].tab + c;
+                WV.tab[j] = t;
                 if constexpr (EMIT) {
-                    if (in) {
-                        const ViewDesc& vd = views[w.view];
-                        WV.pbase[j] = pair_off[t] - pair_base;
-                        WV.pend[j] = pair_off[t + 1] - pair_base;
-                        WV.tile_base[j] = vd.tile_base;
-                        WV.tiles_x[j] = vd.tiles_x;
-                    }
+                    WV.mask[j] = counts[t].x;
+                    const ViewDesc& vd = views[w.view];
+                    WV.pbase[j] = pair_off[t] - pair_base;
+                    WV.pend[j] = pair_off[t + 1] - pair_base;
+                    WV.ibase[j] = inst_off[t] - inst_base;
+                    WV.tile_base[j] = vd.tile_base;
+                    WV.tiles_x[j] = vd.tiles_x;
                 }
+            }
+        }
+        __syncwarp();
+        if constexpr (!EMIT) {
+            for (int j = 0; j < nvb; ++j) {
+                const int vvj = WV.vv[j];
+                if (vvj < 0) continue;
+                const uint32_t m = __ballot_sync(0xffffffffu, valid && may_be_visible(gme, vnodes[vvj], views[vvj / K], P));
+                if (lane == 0) WV.mask[j] = m;
             }
         }
         __syncwarp();
@@ -514,16 +520,17 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
             if constexpr (EMIT) {
                 if (act && !vis) atomicOr(P.err, kErrMismatch);
                 if (vis) {
-                    const uint32_t r = inst_off[WV.tab[j]] - inst_base + __popc(WV.mask[j] & ((1u << g) - 1u));
+                    const uint32_t r = WV.ibase[j] + __popc(WV.mask[j] & ((1u << g) - 1u));
                     float rgb[3];
                     sh_colour(nd.deg, shc + g * kShStride, gg, vnodes[vvj], rgb);
                     const int64_t i = (int64_t)c * kChunk + g;
                     const float op = 1.f / (1.f + __expf(-__ldg(nd.opac + i)));
                     Record R;
                     R.r0 = make_float4(s.u, s.v, op, s.z);
-                    R.r1 = make_float4(s.qa, s.qb, s.qc, __uint_as_float((uint32_t)(nd.gbase + i)));
-                    R.r2 = make_float4(rgb[0], rgb[1], rgb[2], __int_as_float(vvj / K));
+                    R.r1 = make_float4(s.qa, s.qb, s.qc, __uint_as_float((uint32_t)s.x0 | ((uint32_t)s.x1 << 16)));
+                    R.r2 = make_float4(rgb[0], rgb[1], rgb[2], __uint_as_float((uint32_t)s.y0 | ((uint32_t)s.y1 << 16)));
                     rec[r] = R;
+                    info[r] = InstInfo{(uint32_t)(nd.gbase + i), (uint32_t)(vvj / K)};
                     W.S.zk[lane] = min(__float_as_uint(s.z) - P.zbase, (1u << kZBits) - 1u);
                     W.S.rec[lane] = r;
                 }
@@ -586,7 +593,7 @@ __global__ void __launch_bounds__(kCountWarps * 32) k_count_batched(const NodeDe
     bool valid;
     stage_geometry<DT>(nd, c, lane, W, g, valid);
     process_chunk<false>(nd, c, lane, nv + nv_off[k], nv_off[k + 1] - nv_off[k], v0, v1, views, vnodes, K, P, g, valid,
-                         W, nullptr, counts, nullptr, nullptr, 0, 0, nullptr, nullptr, nullptr);
+                         W, nullptr, counts, nullptr, nullptr, 0, 0, nullptr, nullptr, nullptr, nullptr);
 }
 
 // Plain mode: the chunks of one view.  pmap = [K+1 prefix chunk counts in node-id order, K slots].
@@ -610,7 +617,7 @@ __global__ void __launch_bounds__(kCountWarps * 32) k_count_plain(const NodeDesc
     stage_geometry<DT>(nd, c, lane, W, g, valid);
     const NodeView one{v, slot};
     process_chunk<false>(nd, c, lane, &one, 1, v, v + 1, views, vnodes, K, P, g, valid, W, nullptr, counts, nullptr,
-                         nullptr, 0, 0, nullptr, nullptr, nullptr);
+                         nullptr, 0, 0, nullptr, nullptr, nullptr, nullptr);
 }
 
 template <int DT>
@@ -618,7 +625,8 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_emit_batched(const NodeDesc
         const ViewDesc* __restrict__ views, const VNode* __restrict__ vnodes, int K, const NodeView* __restrict__ nv,
         const int32_t* __restrict__ nv_off, int n_chunks, Params P, int v0, int v1, const uint2* __restrict__ counts,
         const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off, uint32_t inst_base,
-        uint64_t pair_base, Record* __restrict__ rec, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+        uint64_t pair_base, Record* __restrict__ rec, InstInfo* __restrict__ info, uint64_t* __restrict__ keys,
+        uint32_t* __restrict__ vals) {
     __shared__ WarpWork ww[kEmitWarps];
     __shared__ float shc[kEmitWarps][kChunk * kShStride];
     const int chunk = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
@@ -634,8 +642,8 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_emit_batched(const NodeDesc
     stage_geometry<DT>(nd, c, lane, W, g, valid);
     stage_sh<DT>(nd, c, lane, shc[wib]);
     process_chunk<true>(nd, c, lane, nv + nv_off[k], nv_off[k + 1] - nv_off[k], v0, v1, views, vnodes, K, P, g, valid,
-                        W, shc[wib], const_cast<uint2*>(counts), inst_off, pair_off, inst_base, pair_base, rec, keys,
-                        vals);
+                        W, shc[wib], const_cast<uint2*>(counts), inst_off, pair_off, inst_base, pair_base, rec, info,
+                        keys, vals);
 }
 
 template <int DT>
@@ -643,7 +651,8 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_emit_plain(const NodeDesc* 
         const ViewDesc* __restrict__ views, const VNode* __restrict__ vnodes, int K, Params P, int v,
         const int32_t* __restrict__ pmap, int n_view_chunks, const uint2* __restrict__ counts,
         const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off, uint32_t inst_base,
-        uint64_t pair_base, Record* __restrict__ rec, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+        uint64_t pair_base, Record* __restrict__ rec, InstInfo* __restrict__ info, uint64_t* __restrict__ keys,
+        uint32_t* __restrict__ vals) {
     __shared__ WarpWork ww[kEmitWarps];
     __shared__ float shc[kEmitWarps][kChunk * kShStride];
     const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
@@ -662,7 +671,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_emit_plain(const NodeDesc* 
     stage_sh<DT>(nd, c, lane, shc[wib]);
     const NodeView one{v, slot};
     process_chunk<true>(nd, c, lane, &one, 1, v, v + 1, views, vnodes, K, P, g, valid, W, shc[wib],
-                        const_cast<uint2*>(counts), inst_off, pair_off, inst_base, pair_base, rec, keys, vals);
+                        const_cast<uint2*>(counts), inst_off, pair_off, inst_base, pair_base, rec, info, keys, vals);
 }
 
 // ------------------------------------------------------------------ exclusive scan of the count table
@@ -768,20 +777,20 @@ template <int DT>
 void emit_launch(const Launch& L, const NodeDesc* nodes, int n_nodes, const ViewDesc* views, const VNode* vnodes, int K,
                  const NodeView* nv, const int32_t* nv_off, int n_chunks, const Params& P, int v0, int v1, bool batched,
                  const int32_t* pmap, int64_t view_chunks, const uint2* counts, const uint32_t* inst_off,
-                 const uint64_t* pair_off, uint32_t inst_base, uint64_t pair_base, Record* rec, uint64_t* keys,
-                 uint32_t* vals) {
+                 const uint64_t* pair_off, uint32_t inst_base, uint64_t pair_base, Record* rec, InstInfo* info,
+                 uint64_t* keys, uint32_t* vals) {
     if (batched) {
         const int blocks = (int)(((int64_t)n_chunks + kEmitWarps - 1) / kEmitWarps);
         if (blocks == 0) return;
         k_emit_batched<DT><<<blocks, kEmitWarps * 32, 0, L.stream>>>(nodes, n_nodes, views, vnodes, K, nv, nv_off, n_chunks,
                                                                      P, v0, v1, counts, inst_off, pair_off, inst_base,
-                                                                     pair_base, rec, keys, vals);
+                                                                     pair_base, rec, info, keys, vals);
     } else {
         const int blocks = (int)((view_chunks + kEmitWarps - 1) / kEmitWarps);
         if (blocks == 0) return;
         k_emit_plain<DT><<<blocks, kEmitWarps * 32, 0, L.stream>>>(nodes, views, vnodes, K, P, v0, pmap, (int)view_chunks,
                                                                    counts, inst_off, pair_off, inst_base, pair_base,
-                                                                   rec, keys, vals);
+                                                                   rec, info, keys, vals);
     }
     ++*L.launches;
 }
@@ -816,16 +825,16 @@ void launch_emit(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_n
                  int n_chunks_total, const Params& P, int v0, int v1, bool batched, const int32_t* pmap,
                  int64_t view_chunks, const uint2* counts, const uint32_t* inst_off, const uint64_t* pair_off,
                  uint32_t inst_base,
-                 uint64_t pair_base, Record* records, uint64_t* keys, uint32_t* vals) {
+                 uint64_t pair_base, Record* records, InstInfo* info, uint64_t* keys, uint32_t* vals) {
     if (dtype_mask & (1 << DGS_F32))
         emit_launch<DGS_F32>(L, nodes, n_nodes, views, vnodes, K, node_views, node_view_off, n_chunks_total, P, v0, v1,
-                             batched, pmap, view_chunks, counts, inst_off, pair_off, inst_base, pair_base, records, keys, vals);
+                             batched, pmap, view_chunks, counts, inst_off, pair_off, inst_base, pair_base, records, info, keys, vals);
     if (dtype_mask & (1 << DGS_BF16))
         emit_launch<DGS_BF16>(L, nodes, n_nodes, views, vnodes, K, node_views, node_view_off, n_chunks_total, P, v0, v1,
-                              batched, pmap, view_chunks, counts, inst_off, pair_off, inst_base, pair_base, records, keys, vals);
+                              batched, pmap, view_chunks, counts, inst_off, pair_off, inst_base, pair_base, records, info, keys, vals);
     if (dtype_mask & (1 << DGS_F16))
         emit_launch<DGS_F16>(L, nodes, n_nodes, views, vnodes, K, node_views, node_view_off, n_chunks_total, P, v0, v1,
-                             batched, pmap, view_chunks, counts, inst_off, pair_off, inst_base, pair_base, records, keys, vals);
+                             batched, pmap, view_chunks, counts, inst_off, pair_off, inst_base, pair_base, records, info, keys, vals);
 }
 
 void launch_scan(const Launch& L, const uint2* counts, int64_t n, uint32_t* inst_off, uint64_t* pair_off,
