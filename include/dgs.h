@@ -163,6 +163,42 @@ int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes,
                float* out_rgb, float* out_depth, float* out_alpha,
                const int64_t* view_pixel_offset, void* stream);
 
+/* Gradient buffers of one node (all DEVICE FP32, laid out like the node's attributes).  The
+ * backward pass ADDS into them; a null pointer skips that attribute. */
+typedef struct dgs_node_grads {
+    float* mean;                /* [n,3] */
+    float* log_scale;           /* [n,3] */
+    float* quat;                /* [n,4] */
+    float* opacity_logit;       /* [n]   */
+    float* sh;                  /* [n,(sh_degree+1)^2,3] */
+} dgs_node_grads;
+
+/*
+ * Adjoint of dgs_render (Sec. IV: the 3DGS assets are fitted by gradient descent on rendered
+ * images and depth).  For L = sum grad_rgb . RGB + sum grad_depth . D, adds dL/d(attribute)
+ * to the node gradient buffers and dL/d(world_from_node) (3x4, row-major) to grad_poses.
+ *
+ *   The scene arguments (nodes ... view_pixel_offset) must be those of the forward call.
+ *   out_rgb, out_depth   DEVICE, the forward's outputs (used instead of stored per-pixel state).
+ *   grad_rgb             DEVICE [total_pixels,3]; grad_depth DEVICE [total_pixels] or NULL.
+ *   grads                HOST [n_nodes] of buffers (entries' pointers may be NULL), or NULL.
+ *   grad_poses           DEVICE [n_envs*max_nodes*12] or NULL.
+ *
+ * The per-tile sorted lists are recomputed (same kernels and decisions as the forward), every
+ * pixel is replayed front to back, and per-instance partials are chained through projection,
+ * colour and pose.  Decisions are taken exactly as in the forward pass; gradients of clamped
+ * quantities (alpha at alpha_max, colour at 0, the Jacobian guard) are zero.  Accumulation
+ * uses FP32 atomics, so results may differ in the last bits between calls.
+ */
+int dgs_render_backward(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes,
+                        const int32_t* env_node_ids, int32_t n_envs, int32_t max_nodes,
+                        const float* node_poses,
+                        const dgs_camera* cams, const int32_t* cams_per_env, int32_t max_cams,
+                        const float* out_rgb, const float* out_depth,
+                        const float* grad_rgb, const float* grad_depth,
+                        const dgs_node_grads* grads, float* grad_poses,
+                        const int64_t* view_pixel_offset, void* stream);
+
 /* Statistics of the most recent successful dgs_render on ctx. */
 int dgs_last_stats(const dgs_ctx* ctx, dgs_stats* out);
 

@@ -10,6 +10,7 @@
 // Plain mode makes every view its own group and launches its count/emit per view; batched
 // mode counts all views in one launch (each Gaussian's attributes read once) and emits,
 // sorts and composites as few groups as the 2^30-pair limit of the sort allows.
+// dgs_render_backward rebuilds the same lists and runs the adjoint kernels instead of K5.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -40,7 +41,7 @@ struct dgs_ctx {
     std::string err;
     int device = 0;
     DevBuf meta, counts, inst_off, pair_off, parts, records, info, keys0, vals0, keys1, vals1, hist, status, counters,
-        ranges, errword, readback;
+        ranges, errword, readback, inst_grad;
     void* h_meta = nullptr;
     size_t h_meta_bytes = 0;
     void* h_read = nullptr;
@@ -175,95 +176,46 @@ int bits_for(uint64_t n) {   // smallest b with 2^b >= n (n >= 1)
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-void dgs_default_options(dgs_options* o) {
-    if (!o) return;
-    std::memset(o, 0, sizeof(*o));
-    o->mode = DGS_MODE_BATCHED;
-    o->tile_w = 16;
-    o->tile_h = 16;
-    o->exact_tile_test = 1;
-    o->z_near = 0.01f;
-    o->lowpass = 0.3f;
-    o->alpha_min = 1.0f / 255.0f;
-    o->alpha_max = 0.99f;
-    o->t_min = 1e-4f;
-    o->q_max = 9.0f;
-    o->guard = 1.3f;
-    o->profile = 0;
-    o->views_per_group = 0;
-}
+// Everything one call needs after validation and the count pass.
+struct Batch {
+    int V = 0, K = 0, n_nodes = 0;
+    int dtype_mask = 0;
+    int64_t chunk_total = 0, tiles_total = 0, T = 0;
+    bool batched = true;
+    std::vector<ViewDesc> views;
+    std::vector<int64_t> view_tab;
+    std::vector<std::pair<int, int>> groups;
+    const uint64_t* inst_at = nullptr;     // per-view exclusive instance offsets (host, V+1)
+    const uint64_t* pair_at = nullptr;     // per-view exclusive pair offsets (host, V+1)
+    const NodeDesc* d_nodes = nullptr;
+    const ViewDesc* d_views = nullptr;
+    const NodeView* d_nv = nullptr;
+    const int32_t* d_nvoff = nullptr;
+    const int32_t* d_pmap = nullptr;
+    VNode* d_vnodes = nullptr;
+    uint2* d_counts = nullptr;
+    uint32_t* d_inst_off = nullptr;
+    uint64_t* d_pair_off = nullptr;
+    uint32_t* d_err = nullptr;
+    const dgs_node_grads* d_grads = nullptr;
+    Params P{};
+};
 
-int dgs_context_create(dgs_ctx** out, const dgs_options* opt) {
-    if (!out) return DGS_ERR_INVALID_ARG;
-    *out = nullptr;
-    dgs_options o;
-    if (opt) o = *opt; else dgs_default_options(&o);
-    std::string why;
-    if (!check_options(&o, why)) return DGS_ERR_INVALID_ARG;
-    dgs_ctx* ctx = new dgs_ctx();
-    ctx->opt = o;
-    cudaGetDevice(&ctx->device);
-    *out = ctx;
-    return DGS_OK;
-}
-
-int dgs_context_destroy(dgs_ctx* ctx) {
-    if (!ctx) return DGS_OK;
-    cudaDeviceSynchronize();
-    DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->records, &ctx->info,
-                      &ctx->keys0, &ctx->vals0, &ctx->keys1, &ctx->vals1, &ctx->hist, &ctx->status, &ctx->counters,
-                      &ctx->ranges, &ctx->errword, &ctx->readback};
-    for (DevBuf* b : bufs) free_buf(*b);
-    if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
-    if (ctx->h_read) cudaFreeHost(ctx->h_read);
-    for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
-    delete ctx;
-    return DGS_OK;
-}
-
-const char* dgs_last_error(const dgs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
-
-int dgs_workspace_query(const dgs_ctx* ctx, size_t* bytes) {
-    if (!ctx || !bytes) return DGS_ERR_INVALID_ARG;
-    const DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->records,
-                            &ctx->info, &ctx->keys0, &ctx->vals0, &ctx->keys1, &ctx->vals1, &ctx->hist, &ctx->status,
-                            &ctx->counters, &ctx->ranges, &ctx->errword, &ctx->readback};
-    size_t s = 0;
-    for (const DevBuf* b : bufs) s += b->bytes;
-    *bytes = s;
-    return DGS_OK;
-}
-
-int dgs_last_stats(const dgs_ctx* ctx, dgs_stats* out) {
-    if (!ctx || !out) return DGS_ERR_INVALID_ARG;
-    *out = ctx->stats;
-    return DGS_OK;
-}
-
-int dgs_kernel_times(const dgs_ctx* ctx, float* ms) {
-    if (!ctx || !ms) return DGS_ERR_INVALID_ARG;
-    for (int i = 0; i < DGS_K_COUNT_CLASSES; ++i) ms[i] = ctx->ktimes[i];
-    return DGS_OK;
-}
-
-int64_t dgs_last_launches(const dgs_ctx* ctx) { return ctx ? ctx->launches : -1; }
-
-int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids, int32_t n_envs,
-               int32_t max_nodes, const float* node_poses, const dgs_camera* cams, const int32_t* cams_per_env,
-               int32_t max_cams, float* out_rgb, float* out_depth, float* out_alpha,
-               const int64_t* view_pixel_offset, void* stream_) {
-    if (!ctx) return DGS_ERR_INVALID_ARG;
-    ctx->err.clear();
-    ctx->launches = 0;
-    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+// Validation, host tables, upload, setup, count, scan, per-view totals read back once, view
+// groups and workspace sizing.  Returns DGS_OK with B filled (B.V == 0: nothing to render).
+int prepare(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids, int32_t n_envs,
+            int32_t max_nodes, const float* node_poses, const dgs_camera* cams, const int32_t* cams_per_env,
+            int32_t max_cams, const float* out_rgb, const float* out_depth, const int64_t* view_pixel_offset,
+            const dgs_node_grads* grads, cudaStream_t stream, Timer& tm, Batch& B) {
     const dgs_options& o = ctx->opt;
     // ---------------------------------------------------------------- validation (synchronous)
     if (n_nodes < 1 || !nodes) return fail(ctx, DGS_ERR_INVALID_ARG, "nodes: need n_nodes >= 1 and a node array");
     if (n_envs < 1 || max_nodes < 1 || max_cams < 1) return fail(ctx, DGS_ERR_INVALID_ARG, "n_envs, max_nodes, max_cams must be >= 1");
     if (!env_node_ids || !cams || !cams_per_env || !node_poses) return fail(ctx, DGS_ERR_INVALID_ARG, "null table pointer");
     if (!out_rgb || !out_depth) return fail(ctx, DGS_ERR_INVALID_ARG, "out_rgb and out_depth are required");
+    (void)grads;
     int64_t total_gauss = 0;
     for (int k = 0; k < n_nodes; ++k) {
         const dgs_node& nd = nodes[k];
@@ -331,8 +283,7 @@ int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32
     ctx->stats.n_views = V;
     ctx->stats.n_pixels = pix_total;
     for (float& t : ctx->ktimes) t = 0.f;
-    ctx->ranges_timed.clear();
-    ctx->next_event = 0;
+    B.V = V;
     if (V == 0) return DGS_OK;
 
     // ---------------------------------------------------------------- host tables
@@ -403,6 +354,7 @@ int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32
     const size_t o_nvoff = place(sizeof(int32_t) * (n_nodes + 1));
     const size_t o_pmap = place(sizeof(int32_t) * pmap.size());
     const size_t o_viewtab = place(sizeof(int64_t) * (V + 1));
+    const size_t o_grads = place(sizeof(dgs_node_grads) * n_nodes);
     const size_t upload_bytes = off;
     const size_t o_vnodes = place(sizeof(VNode) * V * K);
     const size_t meta_bytes = off;
@@ -420,6 +372,8 @@ int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32
     std::memcpy(hm + o_nvoff, nv_off.data(), sizeof(int32_t) * (n_nodes + 1));
     std::memcpy(hm + o_pmap, pmap.data(), sizeof(int32_t) * pmap.size());
     std::memcpy(hm + o_viewtab, view_tab.data(), sizeof(int64_t) * (V + 1));
+    if (grads) std::memcpy(hm + o_grads, grads, sizeof(dgs_node_grads) * n_nodes);
+    else std::memset(hm + o_grads, 0, sizeof(dgs_node_grads) * n_nodes);
     char* dm = static_cast<char*>(ctx->meta.p);
     const NodeDesc* d_nodes = reinterpret_cast<const NodeDesc*>(dm + o_nodes);
     const ViewDesc* d_views = reinterpret_cast<const ViewDesc*>(dm + o_views);
@@ -461,7 +415,6 @@ int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32
     P.err = d_err;
     const bool batched = o.mode == DGS_MODE_BATCHED;
     Launch L{stream, &ctx->launches};
-    Timer tm{ctx, stream, o.profile != 0};
 
     tm.begin(DGS_K_SETUP);
     launch_setup_views(L, d_views, V, node_poses, d_slot, K, d_vnodes, d_vtab, d_err);
@@ -543,46 +496,64 @@ int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32
     if ((rc = ensure(ctx, ctx->counters, sizeof(uint32_t) * 8))) return rc;
     if ((rc = ensure(ctx, ctx->status, sizeof(uint32_t) * sort_status_words((uint32_t)max_pairs)))) return rc;
     if ((rc = ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)max_tiles))) return rc;
-    Record* d_rec = static_cast<Record*>(ctx->records.p);
+    B.K = K; B.n_nodes = n_nodes; B.dtype_mask = dtype_mask; B.chunk_total = chunk_total;
+    B.tiles_total = tiles_total; B.T = T; B.batched = batched;
+    B.views = std::move(views); B.view_tab = std::move(view_tab); B.groups = std::move(groups);
+    B.inst_at = inst_at; B.pair_at = pair_at;
+    B.d_nodes = d_nodes; B.d_views = d_views; B.d_nv = d_nv; B.d_nvoff = d_nvoff; B.d_pmap = d_pmap;
+    B.d_vnodes = d_vnodes; B.d_counts = d_counts; B.d_inst_off = d_inst_off; B.d_pair_off = d_pair_off;
+    B.d_err = d_err; B.P = P;
+    B.d_grads = reinterpret_cast<const dgs_node_grads*>(dm + o_grads);
+    return DGS_OK;
+}
 
-    for (auto& g : groups) {
-        const int v0 = g.first, v1 = g.second;
-        const uint32_t n_pairs = (uint32_t)(pair_at[v1] - pair_at[v0]);
-        const int32_t tile0 = views[v0].tile_base;
-        const int n_tiles = (int)((v1 < V ? views[v1].tile_base : tiles_total) - tile0);
-        Params Pg = P;
-        Pg.tile0 = tile0;
-        tm.begin(DGS_K_EMIT);
-        launch_emit(L, dtype_mask, d_nodes, n_nodes, d_views, d_vnodes, K, d_nv, d_nvoff, (int)chunk_total, Pg, v0, v1,
-                    batched, d_pmap + (size_t)v0 * (2 * K + 1), view_tab[v0 + 1] - view_tab[v0], d_counts, d_inst_off,
-                    d_pair_off,
-                    (uint32_t)inst_at[v0], pair_at[v0], d_rec, static_cast<InstInfo*>(ctx->info.p),
-                    static_cast<uint64_t*>(ctx->keys0.p),
-                    static_cast<uint32_t*>(ctx->vals0.p));
-        tm.end();
-        tm.begin(DGS_K_SORT);
-        uint64_t* skeys;
-        uint32_t* svals;
-        const int bits = kZBits + std::max(1, bits_for((uint64_t)n_tiles));
-        launch_sort(L, static_cast<uint64_t*>(ctx->keys0.p), static_cast<uint32_t*>(ctx->vals0.p),
-                    static_cast<uint64_t*>(ctx->keys1.p), static_cast<uint32_t*>(ctx->vals1.p), n_pairs, bits,
-                    static_cast<uint32_t*>(ctx->hist.p), static_cast<uint32_t*>(ctx->status.p),
-                    static_cast<uint32_t*>(ctx->counters.p), d_err, &skeys, &svals, nullptr, nullptr);
-        tm.end();
-        tm.begin(DGS_K_RANGES);
-        launch_ranges(L, skeys, n_pairs, static_cast<uint2*>(ctx->ranges.p), n_tiles);
-        tm.end();
-        tm.begin(DGS_K_COMPOSITE);
-        launch_composite(L, d_views, v0, v1 - v0, n_tiles, static_cast<uint2*>(ctx->ranges.p), svals, d_rec, Pg,
-                         out_rgb, out_depth, out_alpha);
-        tm.end();
-        DGS_CUDA(ctx, cudaGetLastError());
-    }
-    uint32_t* h_err = reinterpret_cast<uint32_t*>(static_cast<char*>(ctx->h_read) + sizeof(uint64_t) * 2 * (V + 1));
-    DGS_CUDA(ctx, cudaMemcpyAsync(h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+// Emit, sort and tile ranges of view group g.
+struct GroupLists {
+    int v0 = 0, v1 = 0, n_tiles = 0;
+    uint32_t n_pairs = 0, n_inst = 0;
+    uint32_t* vals = nullptr;
+    Params P{};
+};
+
+void build_group_lists(dgs_ctx* ctx, const Batch& B, int g, cudaStream_t stream, Timer& tm, GroupLists& G) {
+    Launch L{stream, &ctx->launches};
+    const int V = B.V, K = B.K;
+    const int v0 = B.groups[g].first, v1 = B.groups[g].second;
+    G.v0 = v0; G.v1 = v1;
+    G.n_pairs = (uint32_t)(B.pair_at[v1] - B.pair_at[v0]);
+    G.n_inst = (uint32_t)(B.inst_at[v1] - B.inst_at[v0]);
+    const int32_t tile0 = B.views[v0].tile_base;
+    G.n_tiles = (int)((v1 < V ? B.views[v1].tile_base : B.tiles_total) - tile0);
+    G.P = B.P;
+    G.P.tile0 = tile0;
+    tm.begin(DGS_K_EMIT);
+    launch_emit(L, B.dtype_mask, B.d_nodes, B.n_nodes, B.d_views, B.d_vnodes, K, B.d_nv, B.d_nvoff, (int)B.chunk_total,
+                G.P, v0, v1, B.batched, B.d_pmap + (size_t)v0 * (2 * K + 1), B.view_tab[v0 + 1] - B.view_tab[v0],
+                B.d_counts, B.d_inst_off, B.d_pair_off, (uint32_t)B.inst_at[v0], B.pair_at[v0],
+                static_cast<Record*>(ctx->records.p), static_cast<InstInfo*>(ctx->info.p),
+                static_cast<uint64_t*>(ctx->keys0.p), static_cast<uint32_t*>(ctx->vals0.p));
+    tm.end();
+    tm.begin(DGS_K_SORT);
+    uint64_t* skeys = nullptr;
+    const int bits = kZBits + std::max(1, bits_for((uint64_t)G.n_tiles));
+    launch_sort(L, static_cast<uint64_t*>(ctx->keys0.p), static_cast<uint32_t*>(ctx->vals0.p),
+                static_cast<uint64_t*>(ctx->keys1.p), static_cast<uint32_t*>(ctx->vals1.p), G.n_pairs, bits,
+                static_cast<uint32_t*>(ctx->hist.p), static_cast<uint32_t*>(ctx->status.p),
+                static_cast<uint32_t*>(ctx->counters.p), B.d_err, &skeys, &G.vals, nullptr, nullptr);
+    tm.end();
+    tm.begin(DGS_K_RANGES);
+    launch_ranges(L, skeys, G.n_pairs, static_cast<uint2*>(ctx->ranges.p), G.n_tiles);
+    tm.end();
+}
+
+// Final synchronisation, device error word and kernel times.
+int finish(dgs_ctx* ctx, const Batch& B, cudaStream_t stream) {
+    uint32_t* h_err = reinterpret_cast<uint32_t*>(static_cast<char*>(ctx->h_read) + sizeof(uint64_t) * 2 * (B.V + 1));
+    DGS_CUDA(ctx, cudaGetLastError());
+    DGS_CUDA(ctx, cudaMemcpyAsync(h_err, B.d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
     DGS_CUDA(ctx, cudaStreamSynchronize(stream));
-    errw = *h_err;
-    if (o.profile) {
+    const uint32_t errw = *h_err;
+    if (ctx->opt.profile) {
         for (const TimedRange& r : ctx->ranges_timed) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) ctx->ktimes[r.cls] += ms;
@@ -592,6 +563,152 @@ int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32
     if (errw & kErrMismatch) return fail(ctx, DGS_ERR_CUDA, "internal: count and emit passes disagree");
     if (errw & kErrPose) return fail(ctx, DGS_ERR_INVALID_ARG, "a node pose is not finite or not rigid");
     return DGS_OK;
+}
+
+void begin_call(dgs_ctx* ctx) {
+    ctx->err.clear();
+    ctx->launches = 0;
+    ctx->ranges_timed.clear();
+    ctx->next_event = 0;
+    for (float& t : ctx->ktimes) t = 0.f;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dgs_default_options(dgs_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->mode = DGS_MODE_BATCHED;
+    o->tile_w = 16;
+    o->tile_h = 16;
+    o->exact_tile_test = 1;
+    o->z_near = 0.01f;
+    o->lowpass = 0.3f;
+    o->alpha_min = 1.0f / 255.0f;
+    o->alpha_max = 0.99f;
+    o->t_min = 1e-4f;
+    o->q_max = 9.0f;
+    o->guard = 1.3f;
+    o->profile = 0;
+    o->views_per_group = 0;
+}
+
+int dgs_context_create(dgs_ctx** out, const dgs_options* opt) {
+    if (!out) return DGS_ERR_INVALID_ARG;
+    *out = nullptr;
+    dgs_options o;
+    if (opt) o = *opt; else dgs_default_options(&o);
+    std::string why;
+    if (!check_options(&o, why)) return DGS_ERR_INVALID_ARG;
+    dgs_ctx* ctx = new dgs_ctx();
+    ctx->opt = o;
+    cudaGetDevice(&ctx->device);
+    *out = ctx;
+    return DGS_OK;
+}
+
+int dgs_context_destroy(dgs_ctx* ctx) {
+    if (!ctx) return DGS_OK;
+    cudaDeviceSynchronize();
+    DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->records, &ctx->info,
+                      &ctx->keys0, &ctx->vals0, &ctx->keys1, &ctx->vals1, &ctx->hist, &ctx->status, &ctx->counters,
+                      &ctx->ranges, &ctx->errword, &ctx->readback, &ctx->inst_grad};
+    for (DevBuf* b : bufs) free_buf(*b);
+    if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
+    if (ctx->h_read) cudaFreeHost(ctx->h_read);
+    for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+    delete ctx;
+    return DGS_OK;
+}
+
+const char* dgs_last_error(const dgs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int dgs_workspace_query(const dgs_ctx* ctx, size_t* bytes) {
+    if (!ctx || !bytes) return DGS_ERR_INVALID_ARG;
+    const DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->records,
+                            &ctx->info, &ctx->keys0, &ctx->vals0, &ctx->keys1, &ctx->vals1, &ctx->hist, &ctx->status,
+                            &ctx->counters, &ctx->ranges, &ctx->errword, &ctx->readback, &ctx->inst_grad};
+    size_t s = 0;
+    for (const DevBuf* b : bufs) s += b->bytes;
+    *bytes = s;
+    return DGS_OK;
+}
+
+int dgs_last_stats(const dgs_ctx* ctx, dgs_stats* out) {
+    if (!ctx || !out) return DGS_ERR_INVALID_ARG;
+    *out = ctx->stats;
+    return DGS_OK;
+}
+
+int dgs_kernel_times(const dgs_ctx* ctx, float* ms) {
+    if (!ctx || !ms) return DGS_ERR_INVALID_ARG;
+    for (int i = 0; i < DGS_K_COUNT_CLASSES; ++i) ms[i] = ctx->ktimes[i];
+    return DGS_OK;
+}
+
+int64_t dgs_last_launches(const dgs_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+
+int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids, int32_t n_envs,
+               int32_t max_nodes, const float* node_poses, const dgs_camera* cams, const int32_t* cams_per_env,
+               int32_t max_cams, float* out_rgb, float* out_depth, float* out_alpha,
+               const int64_t* view_pixel_offset, void* stream_) {
+    if (!ctx) return DGS_ERR_INVALID_ARG;
+    begin_call(ctx);
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    Timer tm{ctx, stream, ctx->opt.profile != 0};
+    Batch B;
+    int rc = prepare(ctx, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env, max_cams,
+                     out_rgb, out_depth, view_pixel_offset, nullptr, stream, tm, B);
+    if (rc != DGS_OK || B.V == 0) return rc;
+    Launch L{stream, &ctx->launches};
+    for (int g = 0; g < (int)B.groups.size(); ++g) {
+        GroupLists G;
+        build_group_lists(ctx, B, g, stream, tm, G);
+        tm.begin(DGS_K_COMPOSITE);
+        launch_composite(L, B.d_views, G.v0, G.v1 - G.v0, G.n_tiles, static_cast<uint2*>(ctx->ranges.p), G.vals,
+                         static_cast<Record*>(ctx->records.p), G.P, out_rgb, out_depth, out_alpha);
+        tm.end();
+        DGS_CUDA(ctx, cudaGetLastError());
+    }
+    return finish(ctx, B, stream);
+}
+
+int dgs_render_backward(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids,
+                        int32_t n_envs, int32_t max_nodes, const float* node_poses, const dgs_camera* cams,
+                        const int32_t* cams_per_env, int32_t max_cams, const float* out_rgb, const float* out_depth,
+                        const float* grad_rgb, const float* grad_depth, const dgs_node_grads* grads,
+                        float* grad_poses, const int64_t* view_pixel_offset, void* stream_) {
+    if (!ctx) return DGS_ERR_INVALID_ARG;
+    begin_call(ctx);
+    if (!grad_rgb) return fail(ctx, DGS_ERR_INVALID_ARG, "grad_rgb is required");
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    Timer tm{ctx, stream, ctx->opt.profile != 0};
+    Batch B;
+    int rc = prepare(ctx, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env, max_cams,
+                     out_rgb, out_depth, view_pixel_offset, grads, stream, tm, B);
+    if (rc != DGS_OK || B.V == 0) return rc;
+    Launch L{stream, &ctx->launches};
+    uint64_t max_inst = 1;
+    for (auto& g : B.groups) max_inst = std::max<uint64_t>(max_inst, B.inst_at[g.second] - B.inst_at[g.first]);
+    if ((rc = ensure(ctx, ctx->inst_grad, sizeof(float) * 10 * max_inst))) return rc;
+    for (int g = 0; g < (int)B.groups.size(); ++g) {
+        GroupLists G;
+        build_group_lists(ctx, B, g, stream, tm, G);
+        tm.begin(DGS_K_BACKWARD);
+        DGS_CUDA(ctx, cudaMemsetAsync(ctx->inst_grad.p, 0, sizeof(float) * 10 * std::max<uint32_t>(G.n_inst, 1), stream));
+        launch_composite_bwd(L, B.d_views, G.v0, G.v1 - G.v0, G.n_tiles, static_cast<uint2*>(ctx->ranges.p), G.vals,
+                             static_cast<Record*>(ctx->records.p), G.P, out_rgb, out_depth, grad_rgb, grad_depth,
+                             static_cast<float*>(ctx->inst_grad.p));
+        launch_project_bwd(L, B.dtype_mask, B.d_nodes, B.n_nodes, B.d_views, B.d_vnodes, B.K, node_poses,
+                           static_cast<InstInfo*>(ctx->info.p), static_cast<float*>(ctx->inst_grad.p), G.n_inst, G.P,
+                           B.d_grads, grad_poses);
+        tm.end();
+        DGS_CUDA(ctx, cudaGetLastError());
+    }
+    return finish(ctx, B, stream);
 }
 
 }  // extern "C"

@@ -1,0 +1,491 @@
+// Adjoint of the renderer: compositing (K7) and projection + colour + node pose (K8).
+//
+// Sec. IV: the 3DGS assets are optimised against rendered images and depth, which needs the
+// gradient of the renderer with respect to every Gaussian attribute; the rigid node poses of
+// Sec. III-B are differentiated the same way.  L = sum g_C . RGB + sum g_D . D.
+//
+// K7 replays every pixel front to back with exactly the forward's FP32 decisions, keeping only
+// the forward outputs: with prefix P_i = sum_{j<=i} w_j c_j, the colour behind Gaussian i
+// (normalised, background included) is S_i = (C_out - P_i) / T_{i+1}, and
+//   dL/dalpha_i = T_i [ g_C . (c_i - S_i) + g_D (z_i - SD_i) ],
+//   dL/dc_i = w_i g_C,  dL/dz_i = w_i g_D,
+// because T_{i+1} / (1 - alpha_i) = T_i.  alpha = min(alpha_max, o e^{-q/2}) then gives the
+// partials of o and of q = qa (dx + qb dy)^2 + qc dy^2 (zero where alpha is clamped).  Each warp
+// reduces its 32 pixels' partials of a record and adds them to the record's 10 accumulators.
+//
+// K8 recomputes one instance's projection and applies the chain rule through the factored
+// quadratic form, the 2D covariance A diag(s^2) A^T + lowpass I (A = J M_R R), the guarded
+// Jacobian, the camera_from_node transform, the quaternion normalisation, the sigmoid and the
+// real SH basis; the node pose receives the partials of M = Wc [Rn | tn] and of the camera
+// centre expressed in the node frame (the SH direction).
+#include "dgs_internal.cuh"
+
+namespace dgs {
+namespace {
+
+// per-instance partials, in this order
+enum { G_U = 0, G_V, G_QA, G_QB, G_QC, G_OP, G_R, G_G, G_B, G_Z, G_N };
+
+__device__ __forceinline__ bool ellipse_meets_b(float qa, float qb, float qc, float qlim, float X0, float X1, float Y0,
+                                                float Y1) {
+    if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return true;
+    const float k = -qa * qb / fmaf(qa * qb, qb, qc);
+    float m = INFINITY;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float Y = e ? Y1 : Y0;
+        const float X = fminf(X1, fmaxf(X0, -qb * Y));
+        const float t = fmaf(qb, Y, X);
+        m = fminf(m, fmaf(qa * t, t, qc * Y * Y));
+        const float Xv = e ? X1 : X0;
+        const float Yv = fminf(Y1, fmaxf(Y0, k * Xv));
+        const float tv = fmaf(qb, Yv, Xv);
+        m = fminf(m, fmaf(qa * tv, tv, qc * Yv * Yv));
+    }
+    return m <= qlim;
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// ------------------------------------------------------------------ K7
+__global__ void __launch_bounds__(256) k_composite_bwd(const ViewDesc* __restrict__ views, int v0, int nv,
+                                                       const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
+                                                       const Record* __restrict__ rec, Params P,
+                                                       const float* __restrict__ out_rgb,
+                                                       const float* __restrict__ out_depth,
+                                                       const float* __restrict__ g_rgb,
+                                                       const float* __restrict__ g_depth, float* __restrict__ ig) {
+    __shared__ float4 s_rec[8][3][32];
+    __shared__ uint32_t s_idx[8][32];
+    const int gt = blockIdx.x;
+    const int ga = gt + P.tile0;
+    int lo = v0, hi = v0 + nv - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (views[mid].tile_base <= ga) lo = mid; else hi = mid - 1;
+    }
+    const ViewDesc& vd = views[lo];
+    const int tile = ga - vd.tile_base;
+    const int tx = tile % vd.tiles_x, ty = tile / vd.tiles_x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int sub_cols = P.tile_w >> 3;
+    const int wx0 = tx * P.tile_w + (w % sub_cols) * 8, wy0 = ty * P.tile_h + (w / sub_cols) * 4;
+    const int wx1 = min(wx0 + 7, vd.W - 1), wy1 = min(wy0 + 3, vd.H - 1);
+    if (wx0 > wx1 || wy0 > wy1) return;
+    const int px = wx0 + (lane & 7), py = wy0 + (lane >> 3);
+    const bool inside = px < vd.W && py < vd.H;
+    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, Co0 = 0.f, Co1 = 0.f, Co2 = 0.f, Do = 0.f;
+    if (inside) {
+        const int64_t p = vd.pix_off + (int64_t)py * vd.W + px;
+        gC0 = g_rgb[p * 3 + 0]; gC1 = g_rgb[p * 3 + 1]; gC2 = g_rgb[p * 3 + 2];
+        gD = g_depth ? g_depth[p] : 0.f;
+        Co0 = out_rgb[p * 3 + 0]; Co1 = out_rgb[p * 3 + 1]; Co2 = out_rgb[p * 3 + 2];
+        Do = out_depth[p];
+    }
+    if (__all_sync(0xffffffffu, gC0 == 0.f && gC1 == 0.f && gC2 == 0.f && gD == 0.f)) return;
+    const uint2 range = ranges[gt];
+    float T = 1.f, P0 = 0.f, P1 = 0.f, P2 = 0.f, PD = 0.f;
+    bool done = !inside;
+    const uint32_t lt = (1u << lane) - 1u;
+    float4* const sr0 = s_rec[w][0];
+    float4* const sr1 = s_rec[w][1];
+    float4* const sr2 = s_rec[w][2];
+    for (uint32_t base = range.x; base < range.y; base += 32) {
+        if (__all_sync(0xffffffffu, done)) break;
+        const uint32_t i = base + lane;
+        bool rel = false;
+        float4 a, q, col;
+        uint32_t idx = 0;
+        if (i < range.y) {
+            idx = vals[i];
+            const Record* r = rec + idx;
+            q = r->r1;
+            const uint32_t bx = __float_as_uint(q.w), by = __float_as_uint(r->r2.w);
+            if ((int)(bx & 0xFFFFu) <= wx1 && (int)(bx >> 16) >= wx0 && (int)(by & 0xFFFFu) <= wy1 && (int)(by >> 16) >= wy0) {
+                a = r->r0;
+                col = r->r2;
+                rel = ellipse_meets_b(q.x, q.y, q.z, P.qbin, (float)wx0 + 0.5f - a.x, (float)wx1 + 0.5f - a.x,
+                                      (float)wy0 + 0.5f - a.y, (float)wy1 + 0.5f - a.y);
+            }
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, rel);
+        if (m == 0) continue;
+        if (rel) {
+            const int pos = __popc(m & lt);
+            sr0[pos] = a; sr1[pos] = q; sr2[pos] = col;
+            s_idx[w][pos] = idx;
+        }
+        __syncwarp();
+        const int n = __popc(m);
+        for (int k = 0; k < n; ++k) {
+            float g[G_N];
+#pragma unroll
+            for (int e = 0; e < G_N; ++e) g[e] = 0.f;
+            bool contrib = false;
+            if (!done) {
+                const float4 g0 = sr0[k], g1 = sr1[k];
+                const float dx = fx - g0.x, dy = fy - g0.y;
+                const float t = fmaf(g1.y, dy, dx);
+                const float qq = fmaf(g1.x * t, t, g1.z * dy * dy);
+                if (qq <= P.q_max) {
+                    const float ex = __expf(-0.5f * qq);
+                    const float a_raw = g0.z * ex;
+                    const float alpha = fminf(P.alpha_max, a_raw);
+                    if (alpha >= P.alpha_min) {
+                        const float Tn = T * (1.f - alpha);
+                        if (Tn < P.t_min) {
+                            done = true;
+                        } else {
+                            contrib = true;
+                            const float wgt = alpha * T;
+                            const float4 g2 = sr2[k];
+                            P0 = fmaf(wgt, g2.x, P0); P1 = fmaf(wgt, g2.y, P1); P2 = fmaf(wgt, g2.z, P2);
+                            PD = fmaf(wgt, g0.w, PD);
+                            const float iTn = 1.f / Tn;
+                            const float S0 = (Co0 - P0) * iTn, S1 = (Co1 - P1) * iTn, S2 = (Co2 - P2) * iTn;
+                            const float SD = (Do - PD) * iTn;
+                            const float dal = T * (gC0 * (g2.x - S0) + gC1 * (g2.y - S1) + gC2 * (g2.z - S2) + gD * (g0.w - SD));
+                            g[G_R] = wgt * gC0; g[G_G] = wgt * gC1; g[G_B] = wgt * gC2; g[G_Z] = wgt * gD;
+                            if (!(a_raw > P.alpha_max)) {
+                                g[G_OP] = dal * ex;
+                                const float dq = -0.5f * alpha * dal;
+                                g[G_QA] = dq * t * t;
+                                g[G_QB] = dq * 2.f * g1.x * t * dy;
+                                g[G_QC] = dq * dy * dy;
+                                g[G_U] = dq * (-2.f * g1.x * t);
+                                g[G_V] = dq * (-2.f * fmaf(g1.x * t, g1.y, g1.z * dy));
+                            }
+                            T = Tn;
+                        }
+                    }
+                }
+            }
+            if (__ballot_sync(0xffffffffu, contrib) == 0) continue;
+            const uint32_t r = s_idx[w][k];
+#pragma unroll
+            for (int e = 0; e < G_N; ++e) {
+                const float s = warp_sum(g[e]);
+                if (lane == 0 && s != 0.f) atomicAdd(ig + (size_t)r * G_N + e, s);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ K8
+__device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z, float Y[16], float dY[16][3]) {
+    constexpr float kY00 = 0.28209479177387814f, kC1 = 0.4886025119029199f;
+    constexpr float kC2a = 1.0925484305920792f, kC2b = 0.31539156525252005f, kC2c = 0.5462742152960396f;
+    constexpr float kC3a = 0.5900435899266435f, kC3b = 2.890611442640554f, kC3c = 0.4570457994644658f;
+    constexpr float kC3d = 0.3731763325901154f, kC3e = 1.445305721320277f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) { Y[k] = 0.f; dY[k][0] = dY[k][1] = dY[k][2] = 0.f; }
+    Y[0] = kY00;
+    if (deg < 1) return;
+    Y[1] = -kC1 * y; dY[1][1] = -kC1;
+    Y[2] = kC1 * z;  dY[2][2] = kC1;
+    Y[3] = -kC1 * x; dY[3][0] = -kC1;
+    if (deg < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = kC2a * x * y;        dY[4][0] = kC2a * y; dY[4][1] = kC2a * x;
+    Y[5] = -kC2a * y * z;       dY[5][1] = -kC2a * z; dY[5][2] = -kC2a * y;
+    Y[6] = kC2b * (3.f * zz - 1.f); dY[6][2] = 6.f * kC2b * z;
+    Y[7] = -kC2a * x * z;       dY[7][0] = -kC2a * z; dY[7][2] = -kC2a * x;
+    Y[8] = kC2c * (xx - yy);    dY[8][0] = 2.f * kC2c * x; dY[8][1] = -2.f * kC2c * y;
+    if (deg < 3) return;
+    Y[9] = -kC3a * y * (3.f * xx - yy);  dY[9][0] = -6.f * kC3a * x * y; dY[9][1] = -3.f * kC3a * (xx - yy);
+    Y[10] = kC3b * x * y * z;            dY[10][0] = kC3b * y * z; dY[10][1] = kC3b * x * z; dY[10][2] = kC3b * x * y;
+    Y[11] = -kC3c * y * (5.f * zz - 1.f); dY[11][1] = -kC3c * (5.f * zz - 1.f); dY[11][2] = -10.f * kC3c * y * z;
+    Y[12] = kC3d * z * (5.f * zz - 3.f);  dY[12][2] = kC3d * (15.f * zz - 3.f);
+    Y[13] = -kC3c * x * (5.f * zz - 1.f); dY[13][0] = -kC3c * (5.f * zz - 1.f); dY[13][2] = -10.f * kC3c * x * z;
+    Y[14] = kC3e * z * (xx - yy);        dY[14][0] = 2.f * kC3e * x * z; dY[14][1] = -2.f * kC3e * y * z; dY[14][2] = kC3e * (xx - yy);
+    Y[15] = -kC3a * x * (xx - 3.f * yy); dY[15][0] = -3.f * kC3a * (xx - yy); dY[15][1] = 6.f * kC3a * x * y;
+}
+
+__device__ __forceinline__ int node_of_gid(const NodeDesc* nodes, int n_nodes, uint32_t gid) {
+    int lo = 0, hi = n_nodes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((uint64_t)nodes[mid].gbase <= gid) lo = mid; else hi = mid - 1;
+    }
+    // nodes with no Gaussians share gbase with the next node: step back to a non-empty one
+    while (lo > 0 && nodes[lo].n == 0) --lo;
+    return lo;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(128) k_project_bwd(const NodeDesc* __restrict__ nodes, int n_nodes,
+                                                     const ViewDesc* __restrict__ views,
+                                                     const VNode* __restrict__ vnodes, int K,
+                                                     const float* __restrict__ node_poses,
+                                                     const InstInfo* __restrict__ info, const float* __restrict__ ig,
+                                                     uint32_t n_inst, Params P, const dgs_node_grads* __restrict__ grads,
+                                                     float* __restrict__ grad_poses) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    bool act = r < n_inst;
+    int k = 0, vv = -1;
+    int64_t i = 0;
+    if (act) {
+        const InstInfo inf = info[r];
+        vv = (int)inf.view;
+        k = node_of_gid(nodes, n_nodes, inf.gid);
+        i = (int64_t)inf.gid - nodes[k].gbase;
+        act = nodes[k].dtype == DT;
+    }
+    float gRn[9], gtn[3];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) gRn[e] = 0.f;
+    gtn[0] = gtn[1] = gtn[2] = 0.f;
+    if (act) {
+        const NodeDesc& nd = nodes[k];
+        const VNode& vn = vnodes[vv];
+        const ViewDesc& vd = views[vv / K];
+        const float* M = vn.M;
+        const float* pg = ig + (size_t)r * G_N;
+        const float gu = pg[G_U], gv = pg[G_V], gqa = pg[G_QA], gqb = pg[G_QB], gqc = pg[G_QC];
+        const float gop = pg[G_OP], gcr = pg[G_R], gcg = pg[G_G], gcb = pg[G_B], gz = pg[G_Z];
+        // ---------------------------------------------------------------- recompute the forward
+        const float mx = __ldg(nd.mean + i * 3 + 0), my = __ldg(nd.mean + i * 3 + 1), mz = __ldg(nd.mean + i * 3 + 2);
+        const float s0 = __expf(2.f * ld_attr<DT>(nd.log_scale, i * 3 + 0));
+        const float s1 = __expf(2.f * ld_attr<DT>(nd.log_scale, i * 3 + 1));
+        const float s2 = __expf(2.f * ld_attr<DT>(nd.log_scale, i * 3 + 2));
+        const float q0 = ld_attr<DT>(nd.quat, i * 4 + 0), q1 = ld_attr<DT>(nd.quat, i * 4 + 1);
+        const float q2 = ld_attr<DT>(nd.quat, i * 4 + 2), q3 = ld_attr<DT>(nd.quat, i * 4 + 3);
+        const float qinv = rsqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+        const float w_ = q0 * qinv, x_ = q1 * qinv, y_ = q2 * qinv, z_ = q3 * qinv;
+        float R[3][3];
+        R[0][0] = 1.f - 2.f * (y_ * y_ + z_ * z_); R[0][1] = 2.f * (x_ * y_ - w_ * z_); R[0][2] = 2.f * (x_ * z_ + w_ * y_);
+        R[1][0] = 2.f * (x_ * y_ + w_ * z_); R[1][1] = 1.f - 2.f * (x_ * x_ + z_ * z_); R[1][2] = 2.f * (y_ * z_ - w_ * x_);
+        R[2][0] = 2.f * (x_ * z_ - w_ * y_); R[2][1] = 2.f * (y_ * z_ + w_ * x_); R[2][2] = 1.f - 2.f * (x_ * x_ + y_ * y_);
+        const float s[3] = {s0, s1, s2};
+        const float z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[8], mx), __fmul_rn(M[9], my)), __fmul_rn(M[10], mz)), M[11]);
+        const float tx = fmaf(M[0], mx, fmaf(M[1], my, fmaf(M[2], mz, M[3])));
+        const float ty = fmaf(M[4], mx, fmaf(M[5], my, fmaf(M[6], mz, M[7])));
+        const float iz = 1.f / z;
+        const float xr = tx * iz, yr = ty * iz;
+        const bool clx = xr > vd.limx || xr < -vd.limx, cly = yr > vd.limy || yr < -vd.limy;
+        const float xc = fminf(vd.limx, fmaxf(-vd.limx, xr)), yc = fminf(vd.limy, fmaxf(-vd.limy, yr));
+        const float fxz = vd.fx * iz, fyz = vd.fy * iz;
+        float Tm[2][3];
+        Tm[0][0] = fxz * fmaf(-xc, M[8], M[0]); Tm[0][1] = fxz * fmaf(-xc, M[9], M[1]); Tm[0][2] = fxz * fmaf(-xc, M[10], M[2]);
+        Tm[1][0] = fyz * fmaf(-yc, M[8], M[4]); Tm[1][1] = fyz * fmaf(-yc, M[9], M[5]); Tm[1][2] = fyz * fmaf(-yc, M[10], M[6]);
+        float A[2][3];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) A[a][c] = Tm[a][0] * R[0][c] + Tm[a][1] * R[1][c] + Tm[a][2] * R[2][c];
+        const float cxx = s0 * A[0][0] * A[0][0] + s1 * A[0][1] * A[0][1] + s2 * A[0][2] * A[0][2] + P.lowpass;
+        const float cxy = s0 * A[0][0] * A[1][0] + s1 * A[0][1] * A[1][1] + s2 * A[0][2] * A[1][2];
+        const float cyy = s0 * A[1][0] * A[1][0] + s1 * A[1][1] * A[1][1] + s2 * A[1][2] * A[1][2] + P.lowpass;
+        const float m01 = A[0][0] * A[1][1] - A[0][1] * A[1][0], m02 = A[0][0] * A[1][2] - A[0][2] * A[1][0];
+        const float m12 = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+        const float det = s0 * s1 * m01 * m01 + s0 * s2 * m02 * m02 + s1 * s2 * m12 * m12 +
+                          P.lowpass * (cxx + cyy - P.lowpass);
+        const float idet = 1.f / det, icyy = 1.f / cyy;
+        const float op = 1.f / (1.f + __expf(-__ldg(nd.opac + i)));
+        // ---------------------------------------------------------------- opacity
+        const float glogit = gop * op * (1.f - op);
+        // ---------------------------------------------------------------- colour (SH in the node frame)
+        float gmu[3] = {0.f, 0.f, 0.f};
+        float go[3] = {0.f, 0.f, 0.f};
+        {
+            float dx = mx - vn.o[0], dy = my - vn.o[1], dz = mz - vn.o[2];
+            const float dlen_inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+            dx *= dlen_inv; dy *= dlen_inv; dz *= dlen_inv;
+            float Y[16], dY[16][3];
+            sh_basis_grad(nd.deg, dx, dy, dz, Y, dY);
+            const int nc = (nd.deg + 1) * (nd.deg + 1);
+            const int64_t sb = i * nc * 3;
+            const float gcol[3] = {gcr, gcg, gcb};
+            float raw[3] = {0.5f, 0.5f, 0.5f};
+            for (int c = 0; c < nc; ++c)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) raw[ch] = fmaf(Y[c], ld_attr<DT>(nd.sh, sb + c * 3 + ch), raw[ch]);
+            float gd[3] = {0.f, 0.f, 0.f};
+            float* gsh = grads[k].sh;
+            for (int c = 0; c < nc; ++c) {
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    if (!(raw[ch] > 0.f) || gcol[ch] == 0.f) continue;
+                    if (gsh) atomicAdd(gsh + sb + c * 3 + ch, gcol[ch] * Y[c]);
+                    const float cf = gcol[ch] * ld_attr<DT>(nd.sh, sb + c * 3 + ch);
+                    gd[0] = fmaf(cf, dY[c][0], gd[0]); gd[1] = fmaf(cf, dY[c][1], gd[1]); gd[2] = fmaf(cf, dY[c][2], gd[2]);
+                }
+            }
+            const float dd = gd[0] * dx + gd[1] * dy + gd[2] * dz;
+            const float gdir[3] = {(gd[0] - dx * dd) * dlen_inv, (gd[1] - dy * dd) * dlen_inv, (gd[2] - dz * dd) * dlen_inv};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) { gmu[a] += gdir[a]; go[a] = -gdir[a]; }
+        }
+        // ---------------------------------------------------------------- factored form -> 2D covariance
+        const float idet2 = idet * idet;
+        const float gcxx = gqa * (-cyy * cyy * idet2);
+        const float gcxy = gqa * (2.f * cxy * cyy * idet2) - gqb * icyy;
+        const float gcyy = gqa * (-cxy * cxy * idet2) + gqb * cxy * icyy * icyy - gqc * icyy * icyy;
+        // Sigma2D = A S A^T + lp I, G = [[gcxx, gcxy/2], [gcxy/2, gcyy]]
+        float gA[2][3];
+        float gls[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float a0 = A[0][c], a1 = A[1][c];
+            gA[0][c] = 2.f * s[c] * (gcxx * a0 + 0.5f * gcxy * a1);
+            gA[1][c] = 2.f * s[c] * (0.5f * gcxy * a0 + gcyy * a1);
+            gls[c] = 2.f * s[c] * (gcxx * a0 * a0 + gcxy * a0 * a1 + gcyy * a1 * a1);
+        }
+        // A = T R
+        float gT[2][3], gR[3][3];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) gT[a][j] = gA[a][0] * R[j][0] + gA[a][1] * R[j][1] + gA[a][2] * R[j][2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gR[j][c] = Tm[0][j] * gA[0][c] + Tm[1][j] * gA[1][c];
+        // R(q) -> normalised q -> q
+        float gqn[4];
+        gqn[0] = 2.f * (-z_ * gR[0][1] + y_ * gR[0][2] + z_ * gR[1][0] - x_ * gR[1][2] - y_ * gR[2][0] + x_ * gR[2][1]);
+        gqn[1] = 2.f * (y_ * gR[0][1] + z_ * gR[0][2] + y_ * gR[1][0] - 2.f * x_ * gR[1][1] - w_ * gR[1][2] + z_ * gR[2][0] +
+                        w_ * gR[2][1] - 2.f * x_ * gR[2][2]);
+        gqn[2] = 2.f * (-2.f * y_ * gR[0][0] + x_ * gR[0][1] + w_ * gR[0][2] + x_ * gR[1][0] + z_ * gR[1][2] - w_ * gR[2][0] +
+                        z_ * gR[2][1] - 2.f * y_ * gR[2][2]);
+        gqn[3] = 2.f * (-2.f * z_ * gR[0][0] - w_ * gR[0][1] + x_ * gR[0][2] + w_ * gR[1][0] - 2.f * z_ * gR[1][1] +
+                        y_ * gR[1][2] + x_ * gR[2][0] + y_ * gR[2][1]);
+        const float qd = gqn[0] * w_ + gqn[1] * x_ + gqn[2] * y_ + gqn[3] * z_;
+        const float gq[4] = {(gqn[0] - w_ * qd) * qinv, (gqn[1] - x_ * qd) * qinv, (gqn[2] - y_ * qd) * qinv,
+                             (gqn[3] - z_ * qd) * qinv};
+        // T = J M_R with J = [[fx/z, 0, -fx xc/z], [0, fy/z, -fy yc/z]]
+        const float J[2][3] = {{fxz, 0.f, -fxz * xc}, {0.f, fyz, -fyz * yc}};
+        float gMR[3][3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gMR[b][c] = J[0][b] * gT[0][c] + J[1][b] * gT[1][c];
+        float gJ[2][3];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) gJ[a][b] = gT[a][0] * M[b * 4 + 0] + gT[a][1] * M[b * 4 + 1] + gT[a][2] * M[b * 4 + 2];
+        float gt[3] = {0.f, 0.f, 0.f};
+        const float iz2 = iz * iz;
+        gt[2] += gJ[0][0] * (-vd.fx * iz2) + gJ[1][1] * (-vd.fy * iz2);
+        if (!clx) { gt[2] += gJ[0][2] * (2.f * vd.fx * tx * iz2 * iz); gt[0] += gJ[0][2] * (-vd.fx * iz2); }
+        else { gt[2] += gJ[0][2] * (vd.fx * xc * iz2); }
+        if (!cly) { gt[2] += gJ[1][2] * (2.f * vd.fy * ty * iz2 * iz); gt[1] += gJ[1][2] * (-vd.fy * iz2); }
+        else { gt[2] += gJ[1][2] * (vd.fy * yc * iz2); }
+        // u = fx tx/z + cx, v = fy ty/z + cy, depth = z
+        gt[0] += gu * vd.fx * iz; gt[2] += -gu * vd.fx * tx * iz2;
+        gt[1] += gv * vd.fy * iz; gt[2] += -gv * vd.fy * ty * iz2;
+        gt[2] += gz;
+        // t = M_R mu + M_t
+        const float mu[3] = {mx, my, mz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            gmu[a] += M[0 * 4 + a] * gt[0] + M[1 * 4 + a] * gt[1] + M[2 * 4 + a] * gt[2];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) gMR[a][b] += gt[a] * mu[b];
+        }
+        // ---------------------------------------------------------------- node pose: M = Wc [Rn | tn] + [0 | tc]
+        const float* Wc = vd.cam;
+        const float* Pn = node_poses + ((int64_t)vd.env * K + (vv % K)) * 12;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+            for (int b = 0; b < 3; ++b) gRn[a * 3 + b] = Wc[0 * 4 + a] * gMR[0][b] + Wc[1 * 4 + a] * gMR[1][b] + Wc[2 * 4 + a] * gMR[2][b];
+            gtn[a] = Wc[0 * 4 + a] * gt[0] + Wc[1 * 4 + a] * gt[1] + Wc[2 * 4 + a] * gt[2];
+        }
+        // camera centre in the node frame: o = Rn^T (o_cam - tn), o_cam = -Wc^T tc
+        float oc[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) oc[a] = -(Wc[0 * 4 + a] * Wc[3] + Wc[1 * 4 + a] * Wc[7] + Wc[2 * 4 + a] * Wc[11]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float rel = oc[a] - Pn[a * 4 + 3];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) gRn[a * 3 + b] += rel * go[b];
+            gtn[a] -= Pn[a * 4 + 0] * go[0] + Pn[a * 4 + 1] * go[1] + Pn[a * 4 + 2] * go[2];
+        }
+        // ---------------------------------------------------------------- Gaussian parameters
+        const dgs_node_grads& G = grads[k];
+        if (G.mean) { atomicAdd(G.mean + i * 3 + 0, gmu[0]); atomicAdd(G.mean + i * 3 + 1, gmu[1]); atomicAdd(G.mean + i * 3 + 2, gmu[2]); }
+        if (G.log_scale) {
+            atomicAdd(G.log_scale + i * 3 + 0, gls[0]); atomicAdd(G.log_scale + i * 3 + 1, gls[1]);
+            atomicAdd(G.log_scale + i * 3 + 2, gls[2]);
+        }
+        if (G.quat) {
+            atomicAdd(G.quat + i * 4 + 0, gq[0]); atomicAdd(G.quat + i * 4 + 1, gq[1]);
+            atomicAdd(G.quat + i * 4 + 2, gq[2]); atomicAdd(G.quat + i * 4 + 3, gq[3]);
+        }
+        if (G.opacity_logit) atomicAdd(G.opacity_logit + i, glogit);
+    }
+    // ---------------------------------------------------------------- pose gradient, reduced per warp
+    if (!grad_poses) return;
+    const int lead = __shfl_sync(0xffffffffu, act ? vv : -1, 0);
+    const bool same = __all_sync(0xffffffffu, !act || vv == lead);
+    if (same && lead >= 0) {
+        const ViewDesc& vd0 = views[lead / K];
+        float* gp = grad_poses + ((int64_t)vd0.env * K + (lead % K)) * 12;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const float v = warp_sum(gRn[a * 3 + b]);
+                if (lane == 0) atomicAdd(gp + a * 4 + b, v);
+            }
+            const float v = warp_sum(gtn[a]);
+            if (lane == 0) atomicAdd(gp + a * 4 + 3, v);
+        }
+    } else if (act) {
+        const ViewDesc& vdl = views[vv / K];
+        float* gp = grad_poses + ((int64_t)vdl.env * K + (vv % K)) * 12;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+            for (int b = 0; b < 3; ++b) atomicAdd(gp + a * 4 + b, gRn[a * 3 + b]);
+            atomicAdd(gp + a * 4 + 3, gtn[a]);
+        }
+    }
+}
+
+}  // namespace
+
+void launch_composite_bwd(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
+                          const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,
+                          const float* out_rgb, const float* out_depth, const float* g_rgb, const float* g_depth,
+                          float* inst_grad) {
+    if (n_tiles == 0) return;
+    k_composite_bwd<<<n_tiles, P.tile_w * P.tile_h, 0, L.stream>>>(views, v0, n_group_views, ranges, vals, records, P,
+                                                                   out_rgb, out_depth, g_rgb, g_depth, inst_grad);
+    ++*L.launches;
+}
+
+void launch_project_bwd(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_nodes, const ViewDesc* views,
+                        const VNode* vnodes, int K, const float* node_poses, const InstInfo* info,
+                        const float* inst_grad, uint32_t n_inst, const Params& P, const dgs_node_grads* grads,
+                        float* grad_poses) {
+    if (n_inst == 0) return;
+    const unsigned blocks = (n_inst + 127) / 128;
+    if (dtype_mask & (1 << DGS_F32)) {
+        k_project_bwd<DGS_F32><<<blocks, 128, 0, L.stream>>>(nodes, n_nodes, views, vnodes, K, node_poses, info, inst_grad,
+                                                             n_inst, P, grads, grad_poses);
+        ++*L.launches;
+    }
+    if (dtype_mask & (1 << DGS_BF16)) {
+        k_project_bwd<DGS_BF16><<<blocks, 128, 0, L.stream>>>(nodes, n_nodes, views, vnodes, K, node_poses, info, inst_grad,
+                                                              n_inst, P, grads, grad_poses);
+        ++*L.launches;
+    }
+    if (dtype_mask & (1 << DGS_F16)) {
+        k_project_bwd<DGS_F16><<<blocks, 128, 0, L.stream>>>(nodes, n_nodes, views, vnodes, K, node_poses, info, inst_grad,
+                                                             n_inst, P, grads, grad_poses);
+        ++*L.launches;
+    }
+}
+
+}  // namespace dgs

@@ -73,7 +73,8 @@ struct Record {
     float4 r0, r1, r2;
 };
 
-// Identity of a projected instance (read by the adjoint): global Gaussian id and view.
+// Identity of a projected instance (read by the adjoint): global Gaussian id and the
+// (view * K + slot) index of its VNode.
 struct InstInfo {
     uint32_t gid;
     uint32_t view;
@@ -134,6 +135,16 @@ void launch_ranges(const Launch& L, const uint64_t* keys, uint32_t n, uint2* ran
 void launch_composite(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
                       const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,
                       float* out_rgb, float* out_depth, float* out_alpha);
+
+void launch_composite_bwd(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
+                          const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,
+                          const float* out_rgb, const float* out_depth, const float* g_rgb, const float* g_depth,
+                          float* inst_grad);
+
+void launch_project_bwd(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_nodes, const ViewDesc* views,
+                        const VNode* vnodes, int K, const float* node_poses, const InstInfo* info,
+                        const float* inst_grad, uint32_t n_inst, const Params& P, const dgs_node_grads* grads,
+                        float* grad_poses);
 
 size_t sort_status_words(uint32_t n);
 int sort_passes(int key_bits);

@@ -530,7 +530,7 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
                     R.r1 = make_float4(s.qa, s.qb, s.qc, __uint_as_float((uint32_t)s.x0 | ((uint32_t)s.x1 << 16)));
                     R.r2 = make_float4(rgb[0], rgb[1], rgb[2], __uint_as_float((uint32_t)s.y0 | ((uint32_t)s.y1 << 16)));
                     rec[r] = R;
-                    info[r] = InstInfo{(uint32_t)(nd.gbase + i), (uint32_t)(vvj / K)};
+                    info[r] = InstInfo{(uint32_t)(nd.gbase + i), (uint32_t)vvj};
                     W.S.zk[lane] = min(__float_as_uint(s.z) - P.zbase, (1u << kZBits) - 1u);
                     W.S.rec[lane] = r;
                 }

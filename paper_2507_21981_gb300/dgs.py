@@ -41,6 +41,11 @@ class dgs_options(C.Structure):
                 ("profile", C.c_int32), ("views_per_group", C.c_int32)]
 
 
+class dgs_node_grads(C.Structure):
+    _fields_ = [("mean", C.c_void_p), ("log_scale", C.c_void_p), ("quat", C.c_void_p),
+                ("opacity_logit", C.c_void_p), ("sh", C.c_void_p)]
+
+
 class dgs_stats(C.Structure):
     _fields_ = [("n_views", C.c_int64), ("n_pixels", C.c_int64), ("n_instances", C.c_int64),
                 ("n_visible", C.c_int64), ("n_pairs", C.c_int64), ("n_groups", C.c_int32), ("key_bits", C.c_int32)]
@@ -48,7 +53,7 @@ class dgs_stats(C.Structure):
 
 EXPORTED = ("dgs_default_options", "dgs_context_create", "dgs_context_destroy", "dgs_last_error",
             "dgs_workspace_query", "dgs_render", "dgs_last_stats", "dgs_kernel_times", "dgs_last_launches",
-            "dgs_render_noalloc")
+            "dgs_render_noalloc", "dgs_render_backward")
 
 _lib = None
 _lock = threading.Lock()
@@ -90,6 +95,9 @@ def load(path: str | None = None) -> C.CDLL:
         lib.dgs_kernel_times.argtypes = [vp, C.POINTER(C.c_float)]
         lib.dgs_last_launches.restype = C.c_int64
         lib.dgs_last_launches.argtypes = [vp]
+        lib.dgs_render_backward.restype = C.c_int
+        lib.dgs_render_backward.argtypes = [vp, C.POINTER(dgs_node), i32, vp, i32, i32, vp, C.POINTER(dgs_camera), vp,
+                                            i32, vp, vp, vp, vp, C.POINTER(dgs_node_grads), vp, vp, vp]
         lib.dgs_render_noalloc.restype = C.c_int
         lib.dgs_render_noalloc.argtypes = [C.POINTER(dgs_options), C.POINTER(dgs_node), i32, vp, i32, i32, vp,
                                            C.POINTER(dgs_camera), vp, i32, vp, vp, vp, vp, vp]
@@ -145,6 +153,16 @@ def dgs_render(ctx, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses,
     return load().dgs_render(ctx, nodes, int(n_nodes), _ptr(env_node_ids), int(n_envs), int(max_nodes),
                              _ptr(node_poses), cams, _ptr(cams_per_env), int(max_cams), _ptr(out_rgb),
                              _ptr(out_depth), _ptr(out_alpha), _ptr(view_pixel_offset), stream)
+
+
+def dgs_render_backward(ctx, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env,
+                        max_cams, out_rgb, out_depth, grad_rgb, grad_depth, grads, grad_poses, view_pixel_offset,
+                        stream) -> int:
+    """Direct call of dgs_render_backward; `grads` is a ctypes array of dgs_node_grads (or None)."""
+    return load().dgs_render_backward(ctx, nodes, int(n_nodes), _ptr(env_node_ids), int(n_envs), int(max_nodes),
+                                      _ptr(node_poses), cams, _ptr(cams_per_env), int(max_cams), _ptr(out_rgb),
+                                      _ptr(out_depth), _ptr(grad_rgb), _ptr(grad_depth), grads, _ptr(grad_poses),
+                                      _ptr(view_pixel_offset), stream)
 
 
 def dgs_last_stats(ctx) -> dict:

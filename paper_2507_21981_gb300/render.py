@@ -61,6 +61,12 @@ class DeviceScene:
         self.node_poses = torch.as_tensor(np.ascontiguousarray(scene.node_poses, np.float32).reshape(E, self.max_nodes, 12),
                                           device=self.device)
 
+    PARAM_NAMES = ("mean", "log_scale", "quat", "opacity_logit", "sh")
+
+    def param_list(self):
+        """The attribute tensors, node by node, in PARAM_NAMES order."""
+        return [t[name] for t in self.tensors for name in self.PARAM_NAMES]
+
     def set_poses(self, node_poses):
         """Replace the per-env node poses ([E,K,3,4] or [E,K,12]) with a device copy."""
         self.node_poses = torch.as_tensor(node_poses, dtype=torch.float32, device=self.device).reshape(
@@ -112,6 +118,31 @@ class Renderer:
             raise D.DgsError(rc, D.dgs_last_error(self.ctx))
         return rgb, depth, alpha
 
+    def backward(self, ds: DeviceScene, out_rgb, out_depth, grad_rgb, grad_depth=None, want_poses: bool = True,
+                 stream=None):
+        """Gradients of L = sum(grad_rgb * rgb) + sum(grad_depth * depth) for the render of `ds`.
+
+        Returns (list of per-node dicts of FP32 tensors mean/log_scale/quat/opacity_logit/sh,
+        pose gradient [E,K,3,4] or None)."""
+        node_grads = []
+        arr = (D.dgs_node_grads * ds.n_nodes)()
+        for k, t in enumerate(ds.tensors):
+            g = {name: torch.zeros(t[name].shape, dtype=torch.float32, device=ds.device) for name in
+                 ("mean", "log_scale", "quat", "opacity_logit", "sh")}
+            node_grads.append(g)
+            arr[k].mean, arr[k].log_scale, arr[k].quat = g["mean"].data_ptr(), g["log_scale"].data_ptr(), g["quat"].data_ptr()
+            arr[k].opacity_logit, arr[k].sh = g["opacity_logit"].data_ptr(), g["sh"].data_ptr()
+        gposes = torch.zeros((ds.n_envs, ds.max_nodes, 12), dtype=torch.float32, device=ds.device) if want_poses else None
+        s = stream if stream is not None else torch.cuda.current_stream(ds.device)
+        grad_rgb = grad_rgb.contiguous().float()
+        grad_depth = None if grad_depth is None else grad_depth.contiguous().float()
+        rc = D.dgs_render_backward(self.ctx, ds.nodes, ds.n_nodes, ds.env_node_ids, ds.n_envs, ds.max_nodes,
+                                   ds.node_poses, ds.cams, ds.cams_per_env, ds.max_cams, out_rgb, out_depth, grad_rgb,
+                                   grad_depth, arr, gposes, None, s.cuda_stream)
+        if rc != D.DGS_OK:
+            raise D.DgsError(rc, D.dgs_last_error(self.ctx))
+        return node_grads, (None if gposes is None else gposes.view(ds.n_envs, ds.max_nodes, 3, 4))
+
     def stats(self) -> dict:
         return D.dgs_last_stats(self.ctx)
 
@@ -123,3 +154,43 @@ class Renderer:
 
     def workspace_bytes(self) -> int:
         return D.dgs_workspace_query(self.ctx)
+
+
+class DGSRenderFn(torch.autograd.Function):
+    """Differentiable render of a DeviceScene.
+
+    apply(renderer, ds, node_poses, *params) -> (rgb [P,3], depth [P], alpha [P]), where params
+    are the scene's own attribute tensors in DeviceScene.param_list() order (the C ABI reads them
+    in place) and node_poses is [E,K,3,4] or [E,K,12] FP32 on the device.  Gradients flow to
+    every param and to node_poses through dgs_render_backward; alpha carries no gradient.
+    """
+
+    @staticmethod
+    def forward(ctx, renderer, ds, node_poses, *params):
+        ds.set_poses(node_poses.detach())
+        rgb, depth, alpha = renderer.render(ds)
+        ctx.renderer, ctx.ds = renderer, ds
+        ctx.save_for_backward(rgb, depth)
+        ctx.pose_shape = node_poses.shape
+        ctx.mark_non_differentiable(alpha)
+        return rgb, depth, alpha
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_depth, g_alpha):
+        rgb, depth = ctx.saved_tensors
+        ds = ctx.ds
+        if g_rgb is None:
+            g_rgb = torch.zeros_like(rgb)
+        node_grads, gposes = ctx.renderer.backward(ds, rgb, depth, g_rgb, g_depth)
+        flat = []
+        for k, t in enumerate(ds.tensors):
+            for name in DeviceScene.PARAM_NAMES:
+                flat.append(node_grads[k][name].to(t[name].dtype))
+        return (None, None, gposes.reshape(ctx.pose_shape)) + tuple(flat)
+
+
+def render_differentiable(renderer: Renderer, ds: DeviceScene, node_poses=None):
+    """Convenience wrapper: renders with gradients to the scene tensors (which should have
+    requires_grad set) and to node_poses (defaults to the scene's current poses)."""
+    poses = ds.node_poses if node_poses is None else node_poses
+    return DGSRenderFn.apply(renderer, ds, poses, *ds.param_list())
