@@ -96,6 +96,37 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def fwd_bwd_500k(dev, warmup, steps):
+    """Forward + backward of one 800x800 view of 500k SH-3 Gaussians (300k room + 8 x 25k posed
+    objects): render, then dL/d(all attributes, poses) for a fixed upstream gradient."""
+    import torch
+    from paper_2507_21981_gb300 import scenes
+    from paper_2507_21981_gb300.render import DeviceScene, Renderer
+    sc = scenes.config4(seed=1)
+    ds = DeviceScene(sc, device=dev)
+    r = Renderer(mode="batched", profile=True)
+    gen = torch.Generator(device=dev).manual_seed(0)
+    g_rgb = torch.randn((ds.n_pixels, 3), device=dev, generator=gen)
+    g_d = torch.randn((ds.n_pixels,), device=dev, generator=gen)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        rgb, depth, _ = r.render(ds)
+        r.backward(ds, rgb, depth, g_rgb, g_d)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    return {"ms": ms, "views": 1, "gaussians": sc.n_gaussians, "resolution": "800x800", "steps": steps,
+            "backward_kernels_ms": r.kernel_times()["backward"]}
+
+
 def cpu_baseline(views=1, seed=1):
     """Times the FP64 oracle on `views` sampled views of the workload (host cores)."""
     import oracle
@@ -244,6 +275,9 @@ def main():
     ms_plain = ev0.elapsed_time(ev1) / args.plain_steps
     plain_value = px_per_step * world / (ms_plain / 1e3) / 1e6
 
+    # ---------------------------------------------------------------- fwd+bwd at 500k Gaussians (one 800x800 view)
+    fb = fwd_bwd_500k(dev, args.warmup, max(3, args.steps // 4))
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -279,7 +313,8 @@ def main():
                    "l2": "inputs larger than L2 (255 MB attributes, 629 MB outputs per step)", "mode": "batched",
                    "tile": "16x16"},
         "plain_mpix_s": plain_value, "batched_over_plain": value / plain_value,
-        "fwd_bwd_ms_per_view_500k": None,
+        "fwd_bwd_ms_per_view_500k": fb["ms"],
+        "fwd_bwd_detail": fb,
         "kernel_ms_per_step": per_step, "render_stats": stats,
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -186,6 +186,7 @@ struct Geo {
     bool present, near_amb, valid;
     double hx, hy;               // half extents of the ellipse's axis-aligned box (with band margin)
     double du, dv;               // FP32 error bound of the projected centre (pixels)
+    bool grad_amb;               // a gradient switch (Jacobian guard, colour clamp) is within its FP32 band
     double dqb;                  // FP32 error bound of the factored form's cross coefficient
 };
 
@@ -257,6 +258,7 @@ void project(const oracle_scene* s, const oracle_opts* o, int e, int c, int slot
     G.present = o->order64 ? G.z > o->z_near : G.z32 > (float)o->z_near;
     G.near_amb = false;
     G.valid = true;
+    G.grad_amb = false;
     if (!G.present) { G.valid = false; return; }
     // EWA: Jacobian of the pinhole projection at t (guarded), Sigma2D = J Wc Sigma_w Wc^T J^T + lp I.
     G.xr = G.t[0] / G.t[2]; G.yr = G.t[1] / G.t[2];
@@ -292,6 +294,9 @@ void project(const oracle_scene* s, const oracle_opts* o, int e, int c, int slot
         const double dyr = (dty + std::fabs(G.yr) * dtz) / G.t[2] + 2 * g32 * std::fabs(G.yr);
         G.du = G.fx * dxr + 2 * g32 * (std::fabs(G.fx * G.xr) + std::fabs(G.cx));
         G.dv = G.fy * dyr + 2 * g32 * (std::fabs(G.fy * G.yr) + std::fabs(G.cy));
+        // the guard clamps xr at +-limx: its gradient switches there
+        G.grad_amb = std::fabs(std::fabs(G.xr) - G.limx) <= 2 * dxr + 4 * g32 * G.limx ||
+                     std::fabs(std::fabs(G.yr) - G.limy) <= 2 * dyr + 4 * g32 * G.limy;
         G.dqb = 8 * g32 * std::sqrt(G.cov[0][0] / G.cov[1][1]);
     }
     // Bounding box of {d : d^T Q d <= qb}, a superset of every candidate whose band reaches q_max.
@@ -311,9 +316,11 @@ void project(const oracle_scene* s, const oracle_opts* o, int e, int c, int slot
     sh_basis(deg, G.d, G.Y, G.dY);
     const double* sh = s->sh + g * 48;
     for (int ch = 0; ch < 3; ++ch) {
-        double a = 0.5;
-        for (int k = 0; k < (deg + 1) * (deg + 1); ++k) a += sh[k * 3 + ch] * G.Y[k];
+        double a = 0.5, mag = 0.5;
+        for (int k = 0; k < (deg + 1) * (deg + 1); ++k) { a += sh[k * 3 + ch] * G.Y[k]; mag += std::fabs(sh[k * 3 + ch] * G.Y[k]); }
         G.raw[ch] = a; G.rgb[ch] = a > 0 ? a : 0.0;
+        // the colour clamp at 0 switches the colour gradient: FP32 band of the sum
+        if (std::fabs(a) <= 64 * 5.9604644775390625e-08 * mag) G.grad_amb = true;
     }
 }
 
@@ -381,6 +388,7 @@ struct PixelResult {
     double tol_rgb = 0, tol_d = 0;
     bool ambiguous = false;
     int64_t amb_kind[4] = {0, 0, 0, 0};   // near, ellipse, alpha, transmittance
+    bool grad_amb = false;                // a gradient switch of a contributor lies within its FP32 band
     int64_t contrib = 0;                  // Gaussians composited (primary branch)
     int64_t reached = 0;                  // in-ellipse Gaussians reached before termination (primary)
     bool terminated = false;
@@ -451,7 +459,11 @@ struct Compositor {
             if (primary && d[0] && d[1]) R->reached++;
             if (act == SKIP) continue;
             if (act == STOP) { if (primary) R->terminated = true; break; }
-            if (primary) R->contrib++;
+            if (primary) {
+                R->contrib++;
+                // alpha clamp at alpha_max: continuous value, switched gradient
+                if (G.grad_amb || std::fabs(a_raw - o->alpha_max) <= 2 * a_raw * da + eps * o->alpha_max) R->grad_amb = true;
+            }
             const double w = alpha * T;
             C0 += w * G.rgb[0]; C1 += w * G.rgb[1]; C2 += w * G.rgb[2]; D += w * G.z;
             T = Tn;
@@ -537,7 +549,8 @@ int64_t oracle_project_view(const oracle_scene* s, const oracle_opts* o, int e, 
 // Renders view (e, c).  rgb [H*W*3], depth/alpha [H*W]: the primary branch.
 // tol_rgb/tol_d [H*W]: extra tolerance from flips beyond max_flips.  n_alt [H*W]: number
 // of alternative branches of each pixel; alt [alt_cap*5] receives them (r,g,b,d,a) in pixel
-// order.  stats[0] = alternatives needed, stats[1] = ambiguous pixels, stats[2] = decision
+// order.  grad_amb [H*W] (nullable) marks pixels where a contributor's gradient switch (alpha
+// clamp, Jacobian guard, colour clamp) lies within its FP32 band.  stats[0] = alternatives needed, stats[1] = ambiguous pixels, stats[2] = decision
 // hash (as bits), stats[3] = instances projected, stats[4..7] = ambiguous decisions on the
 // primary branch by kind (near plane, ellipse, alpha_min, t_min), stats[8] = Gaussians
 // composited, stats[9] = in-ellipse Gaussians reached before termination, stats[10] = pixels
@@ -545,7 +558,7 @@ int64_t oracle_project_view(const oracle_scene* s, const oracle_opts* o, int e, 
 // alt_cap was too small (outputs other than alt are still complete).
 int oracle_render_view(const oracle_scene* s, const oracle_opts* o, int e, int c,
                        double* rgb, double* depth, double* alpha, double* tol_rgb, double* tol_d,
-                       int32_t* n_alt, double* alt, int64_t alt_cap, int64_t* stats) {
+                       int32_t* n_alt, double* alt, int64_t alt_cap, int64_t* stats, int32_t* grad_amb) {
     ViewData V;
     if (!build_view(s, o, e, c, V)) return -1;
     std::vector<std::vector<int>> rows;
@@ -577,6 +590,7 @@ int oracle_render_view(const oracle_scene* s, const oracle_opts* o, int e, int c
             if (tol_rgb) tol_rgb[p] = R.tol_rgb;
             if (tol_d) tol_d[p] = R.tol_d;
             if (n_alt) n_alt[p] = (int32_t)R.alts.size();
+            if (grad_amb) grad_amb[p] = R.grad_amb ? 1 : 0;
             for (auto& L : R.alts) row_alts[y].push_back(L);
             row_amb[y] += R.ambiguous;
             for (int k = 0; k < 4; ++k) row_kind[(size_t)y * 4 + k] += R.amb_kind[k];

@@ -84,7 +84,7 @@ def _load():
             lib.oracle_project_view.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64]
             lib.oracle_render_view.restype = C.c_int
             lib.oracle_render_view.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 7 + \
-                [C.c_int64, C.c_void_p]
+                [C.c_int64, C.c_void_p, C.c_void_p]
             lib.oracle_backward_view.restype = C.c_int
             lib.oracle_backward_view.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 8
             lib.oracle_sh_basis.restype = None
@@ -168,6 +168,7 @@ class ViewResult:
     instances: int
     ambiguous_by_kind: dict = field(default=None)
     work: dict = field(default=None)
+    grad_amb: np.ndarray = field(default=None)   # pixels with a gradient switch inside its FP32 band
     alt_offsets: np.ndarray = field(default=None)
 
     def alternatives(self, p: int) -> np.ndarray:
@@ -183,22 +184,23 @@ def render_view(scene, e: int, c: int, opts: OracleOptions | None = None, packed
     W, H = (int(x) for x in scene.cam_res[e, c])
     rgb = np.zeros((H, W, 3)); depth = np.zeros((H, W)); alpha = np.zeros((H, W))
     tr = np.zeros((H, W)); td = np.zeros((H, W)); na = np.zeros((H, W), np.int32)
+    ga = np.zeros((H, W), np.int32)
     stats = np.zeros(11, np.int64)
     cap = max(1024, W * H // 8)
     alt = np.zeros((cap, 5))
     rc = lib.oracle_render_view(C.byref(pk.c), C.byref(o), e, c, _p(rgb), _p(depth), _p(alpha), _p(tr), _p(td),
-                                _p(na), _p(alt), cap, _p(stats))
+                                _p(na), _p(alt), cap, _p(stats), _p(ga))
     if rc == 1:
         cap = int(stats[0])
         alt = np.zeros((cap, 5))
         rc = lib.oracle_render_view(C.byref(pk.c), C.byref(o), e, c, _p(rgb), _p(depth), _p(alpha), _p(tr), _p(td),
-                                    _p(na), _p(alt), cap, _p(stats))
+                                    _p(na), _p(alt), cap, _p(stats), _p(ga))
     if rc != 0:
         raise ValueError(f"oracle_render_view failed ({rc})")
     kinds = dict(zip(("near", "ellipse", "alpha", "transmittance"), (int(x) for x in stats[4:8])))
     work = dict(contributions=int(stats[8]), reached=int(stats[9]), terminated_pixels=int(stats[10]))
     return ViewResult(rgb, depth, alpha, tr, td, na, alt[: int(stats[0])], int(stats[1]),
-                      int(np.uint64(stats[2].view(np.uint64))), int(stats[3]), kinds, work)
+                      int(np.uint64(stats[2].view(np.uint64))), int(stats[3]), kinds, work, ga.astype(bool))
 
 
 def _grad_buffers(pk, scene):
