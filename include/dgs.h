@@ -96,7 +96,8 @@ typedef struct dgs_options {
     float q_max;                /* default 9 */
     float guard;                /* Jacobian clamp: |tx/tz| <= guard * (W/2)/fx, default 1.3 */
     float bg[3];                /* background colour, default 0 */
-    int32_t profile;            /* 1 = time each kernel class with CUDA events (dgs_kernel_times) */
+    int32_t profile;            /* 1 = time each kernel class with CUDA events (dgs_kernel_times);
+                                   2 = also count compositor work (dgs_stats), slower */
     int32_t views_per_group;    /* batched mode: max views per group, 0 = automatic */
 } dgs_options;
 
@@ -111,6 +112,10 @@ typedef struct dgs_stats {
     int64_t n_pairs;            /* (instance, tile) pairs sorted */
     int32_t n_groups;           /* view groups (batched) or views (plain) */
     int32_t key_bits;           /* significant sort-key bits of the largest group */
+    /* compositor work, counted only when dgs_options.profile = 2: */
+    int64_t px_evaluated;       /* (pixel, Gaussian) evaluations performed (warp lanes x records) */
+    int64_t px_reached;         /* pairs inside the 3-sigma ellipse reached before termination */
+    int64_t px_composited;      /* pairs composited */
 } dgs_stats;
 
 /* Kernel classes timed when dgs_options.profile = 1 (milliseconds, summed over the call). */

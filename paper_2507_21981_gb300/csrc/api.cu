@@ -664,16 +664,29 @@ int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32
                      out_rgb, out_depth, view_pixel_offset, nullptr, stream, tm, B);
     if (rc != DGS_OK || B.V == 0) return rc;
     Launch L{stream, &ctx->launches};
+    unsigned long long* work = nullptr;
+    if (ctx->opt.profile >= 2) {
+        work = reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->errword.p) + 32);
+        DGS_CUDA(ctx, cudaMemsetAsync(work, 0, 24, stream));
+    }
     for (int g = 0; g < (int)B.groups.size(); ++g) {
         GroupLists G;
         build_group_lists(ctx, B, g, stream, tm, G);
         tm.begin(DGS_K_COMPOSITE);
         launch_composite(L, B.d_views, G.v0, G.v1 - G.v0, G.n_tiles, static_cast<uint2*>(ctx->ranges.p), G.vals,
-                         static_cast<Record*>(ctx->records.p), G.P, out_rgb, out_depth, out_alpha);
+                         static_cast<Record*>(ctx->records.p), G.P, out_rgb, out_depth, out_alpha, work);
         tm.end();
         DGS_CUDA(ctx, cudaGetLastError());
     }
-    return finish(ctx, B, stream);
+    rc = finish(ctx, B, stream);
+    if (rc == DGS_OK && work) {
+        unsigned long long h[3] = {0, 0, 0};
+        DGS_CUDA(ctx, cudaMemcpy(h, work, sizeof(h), cudaMemcpyDeviceToHost));
+        ctx->stats.px_evaluated = (int64_t)h[0];
+        ctx->stats.px_reached = (int64_t)h[1];
+        ctx->stats.px_composited = (int64_t)h[2];
+    }
+    return rc;
 }
 
 int dgs_render_backward(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids,

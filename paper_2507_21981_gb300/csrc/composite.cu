@@ -50,10 +50,12 @@ __device__ __forceinline__ bool ellipse_meets(float qa, float qb, float qc, floa
 // pixel box overlaps its sub-tile and whose ellipse reaches one of its pixel centres (exact
 // test with the binning margin), stages them in list order in its own shared memory and
 // composites them; it stops once its 32 pixels have terminated.
+template <bool COUNT>
 __global__ void __launch_bounds__(256) k_composite(const ViewDesc* __restrict__ views, int v0, int nv,
                                                    const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                                                    const Record* __restrict__ rec, Params P, float* __restrict__ out_rgb,
-                                                   float* __restrict__ out_depth, float* __restrict__ out_alpha) {
+                                                   float* __restrict__ out_depth, float* __restrict__ out_alpha,
+                                                   unsigned long long* __restrict__ work) {
     __shared__ float4 s_rec[8][3][32];
     const int gt = blockIdx.x;                 // tile within the group
     const int ga = gt + P.tile0;               // tile within the call
@@ -81,6 +83,7 @@ __global__ void __launch_bounds__(256) k_composite(const ViewDesc* __restrict__ 
     float4* const sr0 = s_rec[w][0];
     float4* const sr1 = s_rec[w][1];
     float4* const sr2 = s_rec[w][2];
+    uint32_t n_eval = 0, n_reach = 0, n_comp = 0;
     for (uint32_t base = range.x; base < range.y; base += 32) {
         if (__all_sync(0xffffffffu, done)) break;
         const uint32_t i = base + lane;
@@ -105,16 +108,19 @@ __global__ void __launch_bounds__(256) k_composite(const ViewDesc* __restrict__ 
         }
         __syncwarp();
         const int n = __popc(m);
+        if (COUNT) n_eval += done ? 0u : (uint32_t)n;
         for (int k = 0; k < n && !done; ++k) {
             const float4 g0 = sr0[k], g1 = sr1[k];
             const float dx = fx - g0.x, dy = fy - g0.y;
             const float t = fmaf(g1.y, dy, dx);
             const float qq = fmaf(g1.x * t, t, g1.z * dy * dy);
             if (qq > P.q_max) continue;
+            if (COUNT) ++n_reach;
             const float alpha = fminf(P.alpha_max, g0.z * __expf(-0.5f * qq));
             if (alpha < P.alpha_min) continue;
             const float Tn = T * (1.f - alpha);
             if (Tn < P.t_min) { done = true; break; }
+            if (COUNT) ++n_comp;
             const float wgt = alpha * T;
             const float4 g2 = sr2[k];
             C0 = fmaf(wgt, g2.x, C0); C1 = fmaf(wgt, g2.y, C1); C2 = fmaf(wgt, g2.z, C2);
@@ -122,6 +128,11 @@ __global__ void __launch_bounds__(256) k_composite(const ViewDesc* __restrict__ 
             T = Tn;
         }
         __syncwarp();
+    }
+    if (COUNT) {
+        const uint32_t a = __reduce_add_sync(0xffffffffu, n_eval), b = __reduce_add_sync(0xffffffffu, n_reach),
+                       cc = __reduce_add_sync(0xffffffffu, n_comp);
+        if (lane == 0) { atomicAdd(work + 0, a); atomicAdd(work + 1, b); atomicAdd(work + 2, cc); }
     }
     if (inside) {
         const int64_t p = vd.pix_off + (int64_t)py * vd.W + px;
@@ -144,10 +155,15 @@ void launch_ranges(const Launch& L, const uint64_t* keys, uint32_t n, uint2* ran
 
 void launch_composite(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
                       const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,
-                      float* out_rgb, float* out_depth, float* out_alpha) {
+                      float* out_rgb, float* out_depth, float* out_alpha, unsigned long long* work) {
     if (n_tiles == 0) return;
-    k_composite<<<n_tiles, P.tile_w * P.tile_h, 0, L.stream>>>(views, v0, n_group_views, ranges, vals, records, P,
-                                                               out_rgb, out_depth, out_alpha);
+    if (work)
+        k_composite<true><<<n_tiles, P.tile_w * P.tile_h, 0, L.stream>>>(views, v0, n_group_views, ranges, vals, records,
+                                                                          P, out_rgb, out_depth, out_alpha, work);
+    else
+        k_composite<false><<<n_tiles, P.tile_w * P.tile_h, 0, L.stream>>>(views, v0, n_group_views, ranges, vals,
+                                                                           records, P, out_rgb, out_depth, out_alpha,
+                                                                           nullptr);
     ++*L.launches;
 }
 

@@ -134,7 +134,7 @@ void launch_ranges(const Launch& L, const uint64_t* keys, uint32_t n, uint2* ran
 
 void launch_composite(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
                       const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,
-                      float* out_rgb, float* out_depth, float* out_alpha);
+                      float* out_rgb, float* out_depth, float* out_alpha, unsigned long long* work);
 
 void launch_composite_bwd(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
                           const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,

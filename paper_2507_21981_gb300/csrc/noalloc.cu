@@ -262,7 +262,8 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
     launch_sort(L, d_k0, d_v0, d_k1, d_v1, (uint32_t)n_pairs, bits, d_hist, d_status, d_cnt, d_err, &skeys, &svals,
                 nullptr, nullptr);
     launch_ranges(L, skeys, (uint32_t)n_pairs, d_ranges, (int)tiles_total);
-    launch_composite(L, d_views, 0, V, (int)tiles_total, d_ranges, svals, d_rec, P, out_rgb, out_depth, out_alpha);
+    launch_composite(L, d_views, 0, V, (int)tiles_total, d_ranges, svals, d_rec, P, out_rgb, out_depth, out_alpha,
+                     nullptr);
     uint32_t h_err = 0;
     NA_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
     NA_CUDA(cudaGetLastError());

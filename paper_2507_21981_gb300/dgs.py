@@ -48,7 +48,8 @@ class dgs_node_grads(C.Structure):
 
 class dgs_stats(C.Structure):
     _fields_ = [("n_views", C.c_int64), ("n_pixels", C.c_int64), ("n_instances", C.c_int64),
-                ("n_visible", C.c_int64), ("n_pairs", C.c_int64), ("n_groups", C.c_int32), ("key_bits", C.c_int32)]
+                ("n_visible", C.c_int64), ("n_pairs", C.c_int64), ("n_groups", C.c_int32), ("key_bits", C.c_int32),
+                ("px_evaluated", C.c_int64), ("px_reached", C.c_int64), ("px_composited", C.c_int64)]
 
 
 EXPORTED = ("dgs_default_options", "dgs_context_create", "dgs_context_destroy", "dgs_last_error",

@@ -79,11 +79,11 @@ class DeviceScene:
 class Renderer:
     """A libdgs context.  Options are the fields of dgs_options (see include/dgs.h)."""
 
-    def __init__(self, mode: str = "batched", tile=(16, 16), profile: bool = False, **opts):
+    def __init__(self, mode: str = "batched", tile=(16, 16), profile: int = 0, **opts):
         o = D.dgs_default_options()
         o.mode = D.DGS_MODE_BATCHED if mode == "batched" else D.DGS_MODE_PLAIN
         o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
-        o.profile = int(bool(profile))
+        o.profile = int(profile)
         for k, v in opts.items():
             if k == "bg":
                 o.bg = (C.c_float * 3)(*[float(x) for x in v])

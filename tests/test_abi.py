@@ -56,7 +56,7 @@ def test_struct_sizes_match_header(lib):
     assert C.sizeof(D.dgs_node) == 56
     assert C.sizeof(D.dgs_camera) == 72
     assert C.sizeof(D.dgs_options) == 64
-    assert C.sizeof(D.dgs_stats) == 48
+    assert C.sizeof(D.dgs_stats) == 72
 
 
 def test_invalid_options_rejected(lib):
