@@ -134,6 +134,69 @@ def fwd_bwd_500k(dev, warmup, steps):
             "backward_kernels_ms": r.kernel_times()["backward"]}
 
 
+def _time_renders(r, ds, out, steps, stream):
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        r.render(ds, out=out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / steps
+
+
+def ragged_graph(dev, warmup, steps):
+    """The uneven batch (256 envs, 1-12 of 64 assets of 5k-200k Gaussians each, 1-3 cameras at
+    320x240 / 640x480 / 1280x720, 500k-Gaussian room): tile shape picked by dgs_autotune, then
+    timed as graph replays."""
+    import torch
+    from paper_2507_21981_gb300 import scenes
+    from paper_2507_21981_gb300.render import DeviceScene, Renderer
+    sc = scenes.config3(seed=1)
+    ds = DeviceScene(sc, device=dev)
+    out = (torch.empty((ds.n_pixels, 3), device=dev), torch.empty((ds.n_pixels,), device=dev), None)
+    r = Renderer(mode="graph")
+    best, times, _ = r.autotune(ds, reps=2, out=out)
+    for _ in range(warmup):
+        r.render(ds, out=out)
+    ms = _time_renders(r, ds, out, steps, torch.cuda.current_stream(dev))
+    st = r.stats()
+    res = {"workload": "256 envs, 1-12 assets (5k-200k) + 500k room, 1-3 cams of 320x240/640x480/1280x720 (config 3)",
+           "views": ds.n_views, "pixels_per_step": ds.n_pixels, "gaussians": sc.n_gaussians,
+           "instances": st["n_instances"], "pairs": st["n_pairs"], "mode": "graph",
+           "path": {0: "eager", 1: "graph", 2: "captured", 3: "regrown"}[st["path"]],
+           "tile": f"{best[0]}x{best[1]}", "autotune_ms": {f"{w}x{h}": t for (w, h), t in times.items()},
+           "ms_per_step": ms, "mpix_s": ds.n_pixels / (ms / 1e3) / 1e6, "steps": steps}
+    r.close()
+    return res
+
+
+def precision_scale(dev, warmup, steps):
+    """3M-Gaussian room + 6 objects x 50k, 128 envs x 3 cameras 640x480, with log-scales,
+    quaternions and SH stored in FP32, BF16 and FP16 (means, opacities and all arithmetic FP32)."""
+    import torch
+    from paper_2507_21981_gb300 import scenes
+    from paper_2507_21981_gb300.render import DeviceScene, Renderer
+    sc = scenes.config5(seed=1)
+    res = {"workload": "128 envs x 3 cams 640x480, 3M-Gaussian SH3 room + 6 objects x 50k (config 5)",
+           "views": sc.n_views, "pixels_per_step": sc.n_pixels, "gaussians": sc.n_gaussians, "steps": steps}
+    for dt in ("bf16", "f16", "f32"):
+        ds = DeviceScene(sc, device=dev, dtype=dt)
+        out = (torch.empty((ds.n_pixels, 3), device=dev), torch.empty((ds.n_pixels,), device=dev), None)
+        r = Renderer(mode="graph")
+        for _ in range(warmup):
+            r.render(ds, out=out)
+        ms = _time_renders(r, ds, out, steps, torch.cuda.current_stream(dev))
+        res[dt] = {"ms_per_step": ms, "mpix_s": ds.n_pixels / (ms / 1e3) / 1e6,
+                   "attribute_bytes": int(sum(t.numel() * t.element_size() for d in ds.tensors for t in d.values()))}
+        res["pairs"] = r.stats()["n_pairs"]
+        r.close()
+        del ds, out
+        torch.cuda.empty_cache()
+    return res
+
+
 def cpu_baseline(views=1, seed=1):
     """Times the FP64 oracle on `views` sampled views of the workload (host cores)."""
     import oracle
@@ -145,7 +208,7 @@ def cpu_baseline(views=1, seed=1):
     t0 = time.perf_counter()
     px = 0
     for v in range(views):
-        e, c = sc.views[(v * 37) % sc.n_views]
+        e, c = sc.views[(v * 37) % sc.n_views]     # spread over envs and both camera kinds
         r = oracle.render_view(sc, e, c, opts, pk)
         px += r.depth.size
     dt = time.perf_counter() - t0
@@ -183,6 +246,7 @@ def main():
     ap.add_argument("--envs", type=int, default=64, help="envs per rank (64 = the benchmark workload)")
     ap.add_argument("--only-batched", action="store_true",
                     help="time the batched render only (no e2e, plain or CPU legs): small profiling runs")
+    ap.add_argument("--no-extra", action="store_true", help="skip the ragged and precision workloads")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -243,6 +307,16 @@ def main():
         ms = float(t.item())
     value = px_per_step * world / (ms / 1e3) / 1e6
 
+    # ---------------------------------------------------------------- the same batch as graph replays
+    rg = Renderer(mode="graph")
+    for _ in range(args.warmup):
+        rg.render(ds, out=out)
+    barrier()
+    ms_graph = _time_renders(rg, ds, out, args.steps, stream)
+    graph_path = rg.stats()["path"]
+    graph_value = px_per_step * world / (ms_graph / 1e3) / 1e6
+    rg.close()
+
     # ---------------------------------------------------------------- e2e through the C ABI with host buffers
     poses_host = torch.from_numpy(np.ascontiguousarray(sc.node_poses, np.float32).reshape(ds.n_envs, ds.max_nodes, 12)).pin_memory()
     host_rgb = torch.empty((px_per_step, 3), dtype=torch.float32).pin_memory()
@@ -284,6 +358,10 @@ def main():
 
     # ---------------------------------------------------------------- fwd+bwd at 500k Gaussians (one 800x800 view)
     fb = fwd_bwd_500k(dev, args.warmup, max(3, args.steps // 4))
+    extra = {}
+    if not args.no_extra:
+        extra["ragged"] = ragged_graph(dev, args.warmup, max(3, args.steps // 4))
+        extra["precision_scale"] = precision_scale(dev, args.warmup, max(3, args.steps // 4))
 
     if rank != 0:
         if world > 1:
@@ -334,6 +412,7 @@ def main():
                    "l2": "inputs larger than L2 (255 MB attributes, 629 MB outputs per step)", "mode": "batched",
                    "tile": "16x16"},
         "plain_mpix_s": plain_value, "batched_over_plain": value / plain_value,
+        "graph_mpix_s": graph_value, "graph_path": graph_path,
         "fwd_bwd_ms_per_view_500k": fb["ms"],
         "fwd_bwd_detail": fb,
         "kernel_ms_per_step": per_step, "render_stats": stats,
@@ -342,8 +421,9 @@ def main():
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
+    line.update(extra)
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(views=1)
+        line["cpu_baseline"] = cpu_baseline(views=16)
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -62,7 +62,8 @@ typedef enum dgs_dtype { DGS_F32 = 0, DGS_BF16 = 1, DGS_F16 = 2 } dgs_dtype;
 
 typedef enum dgs_mode {
     DGS_MODE_PLAIN = 0,   /* every view runs its own projection/binning/sort/composite sequence */
-    DGS_MODE_BATCHED = 1  /* all views of a call share one sequence; attributes read once per group */
+    DGS_MODE_BATCHED = 1, /* all views of a call share one sequence; attributes read once per group */
+    DGS_MODE_GRAPH = 2    /* batched, replayed as one captured CUDA graph (see dgs_render) */
 } dgs_mode;
 
 /* One scene node: structure-of-arrays Gaussians in the node's own frame. */
@@ -116,12 +117,24 @@ typedef struct dgs_stats {
     int64_t px_evaluated;       /* (pixel, Gaussian) evaluations performed (warp lanes x records) */
     int64_t px_reached;         /* pairs inside the 3-sigma ellipse reached before termination */
     int64_t px_composited;      /* pairs composited */
+    int32_t path;               /* dgs_path: how the call ran */
+    int32_t graph_captures;     /* graphs captured by this context so far */
 } dgs_stats;
+
+/* dgs_stats.path */
+typedef enum dgs_path {
+    DGS_PATH_EAGER = 0,         /* launched kernel by kernel (with one mid-call readback) */
+    DGS_PATH_GRAPH = 1,         /* replayed the captured graph */
+    DGS_PATH_CAPTURED = 2,      /* ran eagerly, then captured a graph for the next calls */
+    DGS_PATH_REGROWN = 3        /* a replay overflowed its capacity: ran eagerly and recaptured */
+} dgs_path;
 
 /* Kernel classes timed when dgs_options.profile = 1 (milliseconds, summed over the call). */
 typedef enum dgs_kernel_class {
     DGS_K_SETUP = 0, DGS_K_COUNT = 1, DGS_K_SCAN = 2, DGS_K_EMIT = 3, DGS_K_SORT = 4,
-    DGS_K_RANGES = 5, DGS_K_COMPOSITE = 6, DGS_K_BACKWARD = 7, DGS_K_COUNT_CLASSES = 8
+    DGS_K_RANGES = 5, DGS_K_COMPOSITE = 6, DGS_K_BACKWARD = 7,
+    DGS_K_GRAPH = 8,            /* a whole graph replay (DGS_MODE_GRAPH) */
+    DGS_K_COUNT_CLASSES = 9
 } dgs_kernel_class;
 
 /* Fills *opt with the defaults listed above. */
@@ -160,6 +173,19 @@ int dgs_workspace_query(const dgs_ctx* ctx, size_t* bytes);
  * Work is queued on `stream`.  The call reads per-view counts back once (one stream
  * synchronisation) to size the workspace, and synchronises again before returning so that
  * device-side error flags (invalid pose, timeout, capacity) are reported in the return code.
+ *
+ * DGS_MODE_GRAPH: the first call renders as above and then captures the whole sequence
+ * (setup ... composite) as a CUDA graph sized for 1.25x the instance and tile-pair totals it
+ * saw; its kernels read the live totals on the device, so a replay needs no readback until
+ * the final synchronisation.  Later calls whose batch has the same structure -- the same
+ * views, resolutions, node sizes, storage types and env node tables, the same node_poses and
+ * output pointers, and a workspace that has not moved -- upload the host tables (camera
+ * poses, intrinsics and node attribute pointers may change) and replay the graph.  Node poses
+ * are read from node_poses at replay time.  If a replay finds more instances or pairs than its
+ * capacity, its kernels skip their work, the call renders again eagerly (correct outputs) and
+ * recaptures with larger capacities; dgs_stats.path says which happened.  A batch of more
+ * than 2^30 pairs is never captured (it needs several view groups) and runs eagerly.
+ * views_per_group is ignored by the replayed graph.
  */
 int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes,
                const int32_t* env_node_ids, int32_t n_envs, int32_t max_nodes,
@@ -211,8 +237,43 @@ int dgs_last_stats(const dgs_ctx* ctx, dgs_stats* out);
  * ms[DGS_K_COUNT_CLASSES]. */
 int dgs_kernel_times(const dgs_ctx* ctx, float* ms);
 
-/* Launches of library kernels queued by the most recent call. */
+/* Launches of library kernels queued by the most recent call (a graph replay counts the
+ * kernel nodes it runs). */
 int64_t dgs_last_launches(const dgs_ctx* ctx);
+
+/* Result of dgs_autotune: the candidates timed and the one chosen. */
+#define DGS_TUNE_MAX 16
+typedef struct dgs_tune_result {
+    int32_t n;                        /* candidates timed */
+    int32_t best;                     /* index of the fastest */
+    int32_t tile_w[DGS_TUNE_MAX];
+    int32_t tile_h[DGS_TUNE_MAX];
+    float ms[DGS_TUNE_MAX];           /* mean milliseconds per dgs_render call */
+} dgs_tune_result;
+
+/*
+ * Picks the compositing tile shape for a batch by timing it.  Renders the batch (arguments as
+ * for dgs_render) with each candidate tile shape: one untimed call (in DGS_MODE_GRAPH that
+ * call captures), then `reps` timed calls (CUDA events on `stream` around the calls, host
+ * staging included).  Sets the context's tile shape to the fastest, renders once more with it
+ * (so the outputs, and in graph mode the captured graph, belong to the chosen shape) and
+ * fills *out.  All candidates produce the same image; only the binning granularity changes.
+ *
+ *   candidates  HOST [n_candidates][2] (tile_w, tile_h) pairs, each valid for dgs_options;
+ *               NULL = 16x16, 32x8, 8x32, 16x8, 8x8.
+ *   reps        timed calls per candidate, 1..1000.
+ *
+ * Returns DGS_ERR_INVALID_ARG for a bad candidate list (nothing rendered) and the first
+ * failing render's status otherwise (the context keeps its previous tile shape).
+ */
+int dgs_autotune(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes,
+                 const int32_t* env_node_ids, int32_t n_envs, int32_t max_nodes,
+                 const float* node_poses,
+                 const dgs_camera* cams, const int32_t* cams_per_env, int32_t max_cams,
+                 float* out_rgb, float* out_depth, float* out_alpha,
+                 const int64_t* view_pixel_offset,
+                 const int32_t* candidates, int32_t n_candidates, int32_t reps,
+                 dgs_tune_result* out, void* stream);
 
 /*
  * dgs_render_noalloc -- dgs_render for callers that must not allocate GPU memory.  The paper

@@ -36,12 +36,31 @@ struct TimedRange {
 
 }  // namespace
 
+// What a captured launch sequence depends on: every size that shapes a grid or a table
+// layout, and every pointer baked into a kernel argument (workspace pointers through `gen`).
+struct GraphKey {
+    int64_t V, K, n_nodes, dtype_mask, chunk_total, T, tiles_total, n_nv, upload_bytes, meta_bytes;
+    const void *poses, *rgb, *depth, *alpha;
+    uint64_t gen;
+    int64_t tile_w, tile_h, exact_tile_test;
+};
+
 struct dgs_ctx {
     dgs_options opt{};
     std::string err;
     int device = 0;
     DevBuf meta, counts, inst_off, pair_off, parts, records, info, keys0, vals0, keys1, vals1, hist, status, counters,
-        ranges, errword, readback, inst_grad;
+        ranges, errword, readback, inst_grad, gsizes;
+    uint64_t gen = 0;                     // bumped whenever a workspace buffer is reallocated
+    // graph replay (DGS_MODE_GRAPH)
+    cudaStream_t cap_stream = nullptr;    // capture stream (the caller's may be the legacy stream)
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey{};
+    uint64_t cap_inst = 0, cap_pairs = 0; // capacities the captured sequence was sized for
+    int gbits = 0;
+    int64_t glaunches = 0;
+    int32_t captures = 0;
+    void* h_graph = nullptr;              // pinned: error word + live totals after a replay
     void* h_meta = nullptr;
     size_t h_meta_bytes = 0;
     void* h_read = nullptr;
@@ -80,6 +99,7 @@ int ensure(dgs_ctx* ctx, DevBuf& b, size_t bytes) {
         b.bytes = 0;
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFree");
     }
+    ++ctx->gen;
     size_t want = std::max<size_t>(bytes + bytes / 4, 256);
     cudaError_t e = cudaMalloc(&b.p, want);
     if (e != cudaSuccess) {
@@ -113,7 +133,10 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 bool finite(float x) { return std::isfinite(x); }
 
 int check_options(const dgs_options* o, std::string& why) {
-    if (o->mode != DGS_MODE_PLAIN && o->mode != DGS_MODE_BATCHED) { why = "mode"; return 0; }
+    if (o->mode != DGS_MODE_PLAIN && o->mode != DGS_MODE_BATCHED && o->mode != DGS_MODE_GRAPH) {
+        why = "mode";
+        return 0;
+    }
     const int area = o->tile_w * o->tile_h;
     if (o->tile_w < 8 || o->tile_h < 4 || o->tile_w % 8 || o->tile_h % 4 || (area != 64 && area != 128 && area != 256)) {
         why = "tile shape";
@@ -200,12 +223,18 @@ struct Batch {
     uint64_t* d_pair_off = nullptr;
     uint32_t* d_err = nullptr;
     const dgs_node_grads* d_grads = nullptr;
+    const int32_t* d_slot = nullptr;
+    const int64_t* d_vtab = nullptr;
+    const int64_t* d_viewtab = nullptr;
+    const float* node_poses = nullptr;
+    int64_t n_parts = 0, n_nv = 0;
+    size_t upload_bytes = 0, meta_bytes = 0;
     Params P{};
 };
 
-// Validation, host tables, upload, setup, count, scan, per-view totals read back once, view
-// groups and workspace sizing.  Returns DGS_OK with B filled (B.V == 0: nothing to render).
-int prepare(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids, int32_t n_envs,
+// Validation, host tables and their upload (one copy from pinned memory), workspace for the
+// count table.  Returns DGS_OK with B filled (B.V == 0: nothing to render).
+int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids, int32_t n_envs,
             int32_t max_nodes, const float* node_poses, const dgs_camera* cams, const int32_t* cams_per_env,
             int32_t max_cams, const float* out_rgb, const float* out_depth, const int64_t* view_pixel_offset,
             const dgs_node_grads* grads, cudaStream_t stream, Timer& tm, Batch& B) {
@@ -396,7 +425,6 @@ int prepare(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t*
     uint32_t* d_err = static_cast<uint32_t*>(ctx->errword.p);
 
     DGS_CUDA(ctx, cudaMemcpyAsync(dm, hm, upload_bytes, cudaMemcpyHostToDevice, stream));
-    DGS_CUDA(ctx, cudaMemsetAsync(d_err, 0, 64, stream));
 
     Params P{};
     P.z_near = o.z_near; P.lowpass = o.lowpass; P.alpha_min = o.alpha_min; P.alpha_max = o.alpha_max;
@@ -406,39 +434,65 @@ int prepare(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t*
     P.tile_w = o.tile_w; P.tile_h = o.tile_h;
     P.exact_tile_test = o.exact_tile_test;
     P.tile0 = 0;
-    P.err = nullptr;
     {
         uint32_t b;
         std::memcpy(&b, &o.z_near, 4);
         P.zbase = b & 0x7F800000u;   // 2^floor(log2 z_near)
     }
     P.err = d_err;
-    const bool batched = o.mode == DGS_MODE_BATCHED;
-    Launch L{stream, &ctx->launches};
+    P.gate = nullptr;
+    B.K = K; B.n_nodes = n_nodes; B.dtype_mask = dtype_mask; B.chunk_total = chunk_total;
+    B.tiles_total = tiles_total; B.T = T; B.batched = o.mode != DGS_MODE_PLAIN;
+    B.views = std::move(views); B.view_tab = std::move(view_tab);
+    B.d_nodes = d_nodes; B.d_views = d_views; B.d_nv = d_nv; B.d_nvoff = d_nvoff; B.d_pmap = d_pmap;
+    B.d_vnodes = d_vnodes; B.d_slot = d_slot; B.d_vtab = d_vtab; B.d_viewtab = d_viewtab;
+    B.d_counts = static_cast<uint2*>(ctx->counts.p);
+    B.d_inst_off = static_cast<uint32_t*>(ctx->inst_off.p);
+    B.d_pair_off = static_cast<uint64_t*>(ctx->pair_off.p);
+    B.d_err = d_err; B.P = P;
+    B.d_grads = reinterpret_cast<const dgs_node_grads*>(dm + o_grads);
+    B.node_poses = node_poses;
+    B.n_parts = n_parts;
+    B.n_nv = (int64_t)nv.size();
+    B.upload_bytes = upload_bytes;
+    B.meta_bytes = meta_bytes;
+    return DGS_OK;
+}
 
+// Clears the error word, then setup (K0), count (K1) and the exclusive scan of the count table.
+void launch_front(dgs_ctx* ctx, const Batch& B, const Launch& L, Timer& tm) {
+    cudaMemsetAsync(B.d_err, 0, 64, L.stream);
     tm.begin(DGS_K_SETUP);
-    launch_setup_views(L, d_views, V, node_poses, d_slot, K, d_vnodes, d_vtab, d_err);
+    launch_setup_views(L, B.d_views, B.V, B.node_poses, B.d_slot, B.K, B.d_vnodes, B.d_vtab, B.d_err);
     tm.end();
-    uint2* d_counts = static_cast<uint2*>(ctx->counts.p);
-    uint32_t* d_inst_off = static_cast<uint32_t*>(ctx->inst_off.p);
-    uint64_t* d_pair_off = static_cast<uint64_t*>(ctx->pair_off.p);
     tm.begin(DGS_K_COUNT);
-    if (batched) {
-        launch_count(L, dtype_mask, d_nodes, n_nodes, d_views, d_vnodes, K, d_nv, d_nvoff, (int)chunk_total, P, 0, V,
-                     true, nullptr, 0, d_counts);
+    if (B.batched) {
+        launch_count(L, B.dtype_mask, B.d_nodes, B.n_nodes, B.d_views, B.d_vnodes, B.K, B.d_nv, B.d_nvoff,
+                     (int)B.chunk_total, B.P, 0, B.V, true, nullptr, 0, B.d_counts);
     } else {
-        for (int v = 0; v < V; ++v)
-            launch_count(L, dtype_mask, d_nodes, n_nodes, d_views, d_vnodes, K, d_nv, d_nvoff, (int)chunk_total, P, v,
-                         v + 1, false, d_pmap + (size_t)v * (2 * K + 1), view_tab[v + 1] - view_tab[v], d_counts);
+        for (int v = 0; v < B.V; ++v)
+            launch_count(L, B.dtype_mask, B.d_nodes, B.n_nodes, B.d_views, B.d_vnodes, B.K, B.d_nv, B.d_nvoff,
+                         (int)B.chunk_total, B.P, v, v + 1, false, B.d_pmap + (size_t)v * (2 * B.K + 1),
+                         B.view_tab[v + 1] - B.view_tab[v], B.d_counts);
     }
     tm.end();
     tm.begin(DGS_K_SCAN);
-    launch_scan(L, d_counts, T, d_inst_off, d_pair_off, static_cast<ulonglong2*>(ctx->parts.p), n_parts + 1);
+    launch_scan(L, B.d_counts, B.T, B.d_inst_off, B.d_pair_off, static_cast<ulonglong2*>(ctx->parts.p), B.n_parts + 1);
+    tm.end();
+}
+
+// Per-view totals read back once (one stream synchronisation), view groups and workspace
+// sizing for the eager sequence.
+int readback_groups(dgs_ctx* ctx, Batch& B, cudaStream_t stream, Timer& tm) {
+    const dgs_options& o = ctx->opt;
+    const int V = B.V;
+    int rc;
+    tm.begin(DGS_K_SCAN);
     {
         uint64_t* d_rb = static_cast<uint64_t*>(ctx->readback.p);
-        k_view_totals<<<(V + 1 + 127) / 128, 128, 0, stream>>>(d_inst_off, d_pair_off, d_viewtab, V + 1, d_rb);
+        k_view_totals<<<(V + 1 + 127) / 128, 128, 0, stream>>>(B.d_inst_off, B.d_pair_off, B.d_viewtab, V + 1, d_rb);
         ++ctx->launches;
-        DGS_CUDA(ctx, cudaMemcpyAsync(d_rb + 2 * (V + 1), d_err, sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream));
+        DGS_CUDA(ctx, cudaMemcpyAsync(d_rb + 2 * (V + 1), B.d_err, sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream));
         DGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_read, d_rb, sizeof(uint64_t) * 2 * (V + 1) + 8, cudaMemcpyDeviceToHost, stream));
     }
     tm.end();
@@ -455,7 +509,7 @@ int prepare(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t*
 
     // ---------------------------------------------------------------- groups
     std::vector<std::pair<int, int>> groups;
-    if (!batched) {
+    if (!B.batched) {
         for (int v = 0; v < V; ++v) groups.push_back({v, v + 1});
     } else {
         int v0 = 0;
@@ -476,8 +530,8 @@ int prepare(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t*
     for (auto& g : groups) {
         max_inst = std::max<uint64_t>(max_inst, inst_at[g.second] - inst_at[g.first]);
         max_pairs = std::max<uint64_t>(max_pairs, pair_at[g.second] - pair_at[g.first]);
-        const int64_t t0 = views[g.first].tile_base;
-        const int64_t t1 = g.second < V ? views[g.second].tile_base : tiles_total;
+        const int64_t t0 = B.views[g.first].tile_base;
+        const int64_t t1 = g.second < V ? B.views[g.second].tile_base : B.tiles_total;
         max_tiles = std::max<int64_t>(max_tiles, t1 - t0);
         if (pair_at[g.second] - pair_at[g.first] > kMaxPairs)
             return fail(ctx, DGS_ERR_CAPACITY, "view group exceeds 2^30 tile pairs");
@@ -496,15 +550,22 @@ int prepare(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t*
     if ((rc = ensure(ctx, ctx->counters, sizeof(uint32_t) * 8))) return rc;
     if ((rc = ensure(ctx, ctx->status, sizeof(uint32_t) * sort_status_words((uint32_t)max_pairs)))) return rc;
     if ((rc = ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)max_tiles))) return rc;
-    B.K = K; B.n_nodes = n_nodes; B.dtype_mask = dtype_mask; B.chunk_total = chunk_total;
-    B.tiles_total = tiles_total; B.T = T; B.batched = batched;
-    B.views = std::move(views); B.view_tab = std::move(view_tab); B.groups = std::move(groups);
+    B.groups = std::move(groups);
     B.inst_at = inst_at; B.pair_at = pair_at;
-    B.d_nodes = d_nodes; B.d_views = d_views; B.d_nv = d_nv; B.d_nvoff = d_nvoff; B.d_pmap = d_pmap;
-    B.d_vnodes = d_vnodes; B.d_counts = d_counts; B.d_inst_off = d_inst_off; B.d_pair_off = d_pair_off;
-    B.d_err = d_err; B.P = P;
-    B.d_grads = reinterpret_cast<const dgs_node_grads*>(dm + o_grads);
     return DGS_OK;
+}
+
+// The eager sequence's front half: staging, setup/count/scan and the readback.
+int prepare(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids, int32_t n_envs,
+            int32_t max_nodes, const float* node_poses, const dgs_camera* cams, const int32_t* cams_per_env,
+            int32_t max_cams, const float* out_rgb, const float* out_depth, const int64_t* view_pixel_offset,
+            const dgs_node_grads* grads, cudaStream_t stream, Timer& tm, Batch& B) {
+    int rc = stage(ctx, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env, max_cams,
+                   out_rgb, out_depth, view_pixel_offset, grads, stream, tm, B);
+    if (rc != DGS_OK || B.V == 0) return rc;
+    Launch L{stream, &ctx->launches};
+    launch_front(ctx, B, L, tm);
+    return readback_groups(ctx, B, stream, tm);
 }
 
 // Emit, sort and tile ranges of view group g.
@@ -565,6 +626,216 @@ int finish(dgs_ctx* ctx, const Batch& B, cudaStream_t stream) {
     return DGS_OK;
 }
 
+// ------------------------------------------------------------------ eager sequence
+// Setup/count/scan, the readback, then per view group emit/sort/ranges/composite, and the
+// final synchronisation.  B must have been staged.
+int run_eager(dgs_ctx* ctx, Batch& B, float* out_rgb, float* out_depth, float* out_alpha, cudaStream_t stream,
+              Timer& tm) {
+    Launch L{stream, &ctx->launches};
+    launch_front(ctx, B, L, tm);
+    int rc = readback_groups(ctx, B, stream, tm);
+    if (rc != DGS_OK) return rc;
+    unsigned long long* work = nullptr;
+    if (ctx->opt.profile >= 2) {
+        work = reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->errword.p) + 32);
+        DGS_CUDA(ctx, cudaMemsetAsync(work, 0, 24, stream));
+    }
+    for (int g = 0; g < (int)B.groups.size(); ++g) {
+        GroupLists G;
+        build_group_lists(ctx, B, g, stream, tm, G);
+        tm.begin(DGS_K_COMPOSITE);
+        launch_composite(L, B.d_views, G.v0, G.v1 - G.v0, G.n_tiles, static_cast<uint2*>(ctx->ranges.p), G.vals,
+                         static_cast<Record*>(ctx->records.p), G.P, out_rgb, out_depth, out_alpha, work);
+        tm.end();
+        DGS_CUDA(ctx, cudaGetLastError());
+    }
+    rc = finish(ctx, B, stream);
+    if (rc == DGS_OK && work) {
+        unsigned long long h[3] = {0, 0, 0};
+        DGS_CUDA(ctx, cudaMemcpy(h, work, sizeof(h), cudaMemcpyDeviceToHost));
+        ctx->stats.px_evaluated = (int64_t)h[0];
+        ctx->stats.px_reached = (int64_t)h[1];
+        ctx->stats.px_composited = (int64_t)h[2];
+    }
+    return rc;
+}
+
+// ------------------------------------------------------------------ graph replay
+// gsizes layout: u32 [0] live instances, [1] live pairs, [2] overflow flag; u64 at byte 16:
+// the totals the scan produced (valid even on overflow).
+__global__ void k_graph_sizes(const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off, int64_t T,
+                              uint64_t cap_inst, uint64_t cap_pairs, uint32_t* sizes, uint32_t* err) {
+    const uint64_t ni = inst_off[T], np = pair_off[T];
+    uint64_t* raw = reinterpret_cast<uint64_t*>(sizes + 4);
+    raw[0] = ni;
+    raw[1] = np;
+    const bool over = ni > cap_inst || np > cap_pairs;
+    sizes[0] = over ? 0u : (uint32_t)ni;
+    sizes[1] = over ? 0u : (uint32_t)np;
+    sizes[2] = over ? 1u : 0u;
+    if (over) atomicOr(err, kErrCapacity);
+}
+
+GraphKey make_key(const dgs_ctx* ctx, const Batch& B, const float* rgb, const float* depth, const float* alpha) {
+    GraphKey k;
+    std::memset(&k, 0, sizeof(k));
+    k.V = B.V; k.K = B.K; k.n_nodes = B.n_nodes; k.dtype_mask = B.dtype_mask; k.chunk_total = B.chunk_total;
+    k.T = B.T; k.tiles_total = B.tiles_total; k.n_nv = B.n_nv; k.upload_bytes = (int64_t)B.upload_bytes;
+    k.meta_bytes = (int64_t)B.meta_bytes;
+    k.poses = B.node_poses; k.rgb = rgb; k.depth = depth; k.alpha = alpha;
+    k.gen = ctx->gen;
+    k.tile_w = ctx->opt.tile_w; k.tile_h = ctx->opt.tile_h; k.exact_tile_test = ctx->opt.exact_tile_test;
+    return k;
+}
+
+bool same_key(const GraphKey& a, const GraphKey& b) { return std::memcmp(&a, &b, sizeof(a)) == 0; }
+
+void drop_graph(dgs_ctx* ctx) {
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+}
+
+// The whole render as one sequence sized for the context's capacities; every kernel after the
+// scan reads the live counts on the device, so nothing is read back between count and
+// composite.  On overflow the size check raises kErrCapacity and the later kernels do no work.
+void enqueue_graph_body(dgs_ctx* ctx, const Batch& B, const Launch& L, float* out_rgb, float* out_depth,
+                        float* out_alpha) {
+    Timer off{ctx, L.stream, false};
+    launch_front(ctx, B, L, off);
+    uint32_t* sizes = static_cast<uint32_t*>(ctx->gsizes.p);
+    k_graph_sizes<<<1, 1, 0, L.stream>>>(B.d_inst_off, B.d_pair_off, B.T, ctx->cap_inst, ctx->cap_pairs, sizes,
+                                         B.d_err);
+    ++*L.launches;
+    Params P = B.P;
+    P.gate = sizes + 2;
+    launch_emit(L, B.dtype_mask, B.d_nodes, B.n_nodes, B.d_views, B.d_vnodes, B.K, B.d_nv, B.d_nvoff,
+                (int)B.chunk_total, P, 0, B.V, true, B.d_pmap, B.view_tab[1] - B.view_tab[0], B.d_counts,
+                B.d_inst_off, B.d_pair_off, 0u, 0ull, static_cast<Record*>(ctx->records.p),
+                static_cast<InstInfo*>(ctx->info.p), static_cast<uint64_t*>(ctx->keys0.p),
+                static_cast<uint32_t*>(ctx->vals0.p));
+    uint64_t* skeys = nullptr;
+    uint32_t* svals = nullptr;
+    launch_sort(L, static_cast<uint64_t*>(ctx->keys0.p), static_cast<uint32_t*>(ctx->vals0.p),
+                static_cast<uint64_t*>(ctx->keys1.p), static_cast<uint32_t*>(ctx->vals1.p), (uint32_t)ctx->cap_pairs,
+                ctx->gbits, static_cast<uint32_t*>(ctx->hist.p), static_cast<uint32_t*>(ctx->status.p),
+                static_cast<uint32_t*>(ctx->counters.p), B.d_err, &skeys, &svals, nullptr, nullptr, sizes + 1);
+    launch_ranges(L, skeys, (uint32_t)ctx->cap_pairs, static_cast<uint2*>(ctx->ranges.p), (int)B.tiles_total,
+                  sizes + 1);
+    launch_composite(L, B.d_views, 0, B.V, (int)B.tiles_total, static_cast<uint2*>(ctx->ranges.p), svals,
+                     static_cast<Record*>(ctx->records.p), P, out_rgb, out_depth, out_alpha, nullptr);
+}
+
+// Sizes the capacities from the totals of the render just done (need_inst, need_pairs) with
+// 25 % headroom, and captures the sequence.  Returns DGS_OK without a graph when the batch
+// cannot run as one view group (more than 2^30 pairs or a key wider than 64 bits).
+int capture_graph(dgs_ctx* ctx, const Batch& B, uint64_t need_inst, uint64_t need_pairs, float* out_rgb,
+                  float* out_depth, float* out_alpha) {
+    drop_graph(ctx);
+    const int bits = kZBits + std::max(1, bits_for((uint64_t)std::max<int64_t>(B.tiles_total, 1)));
+    if (need_pairs > kMaxPairs || bits > 64 || need_inst >= (1ull << 31)) return DGS_OK;
+    ctx->cap_inst = std::max(ctx->cap_inst, need_inst + need_inst / 4 + 1024);
+    ctx->cap_pairs = std::min<uint64_t>(kMaxPairs, std::max(ctx->cap_pairs, need_pairs + need_pairs / 4 + 4096));
+    ctx->gbits = bits;
+    int rc;
+    if ((rc = ensure(ctx, ctx->records, sizeof(Record) * ctx->cap_inst))) return rc;
+    if ((rc = ensure(ctx, ctx->info, sizeof(InstInfo) * ctx->cap_inst))) return rc;
+    if ((rc = ensure(ctx, ctx->keys0, sizeof(uint64_t) * ctx->cap_pairs))) return rc;
+    if ((rc = ensure(ctx, ctx->keys1, sizeof(uint64_t) * ctx->cap_pairs))) return rc;
+    if ((rc = ensure(ctx, ctx->vals0, sizeof(uint32_t) * ctx->cap_pairs))) return rc;
+    if ((rc = ensure(ctx, ctx->vals1, sizeof(uint32_t) * ctx->cap_pairs))) return rc;
+    if ((rc = ensure(ctx, ctx->hist, sizeof(uint32_t) * 256 * 8))) return rc;
+    if ((rc = ensure(ctx, ctx->counters, sizeof(uint32_t) * 8))) return rc;
+    if ((rc = ensure(ctx, ctx->status, sizeof(uint32_t) * sort_status_words((uint32_t)ctx->cap_pairs)))) return rc;
+    if ((rc = ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)std::max<int64_t>(B.tiles_total, 1)))) return rc;
+    if ((rc = ensure(ctx, ctx->gsizes, 64))) return rc;
+    if (!ctx->h_graph) DGS_CUDA(ctx, cudaHostAlloc(&ctx->h_graph, 64, cudaHostAllocDefault));
+    if (!ctx->cap_stream) DGS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    sort_prepare();
+    int64_t n_launch = 0;
+    Launch L{ctx->cap_stream, &n_launch};
+    DGS_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_graph_body(ctx, B, L, out_rgb, out_depth, out_alpha);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    if (e != cudaSuccess || !g) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(ctx, e != cudaSuccess ? e : cudaErrorUnknown, "stream capture of the render sequence");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&ctx->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        ctx->gexec = nullptr;
+        cudaGetLastError();
+        return cuda_fail(ctx, ei, "cudaGraphInstantiate");
+    }
+    ctx->gkey = make_key(ctx, B, out_rgb, out_depth, out_alpha);
+    ctx->glaunches = n_launch;
+    ++ctx->captures;
+    return DGS_OK;
+}
+
+// DGS_MODE_GRAPH: replay the captured sequence when the staged batch has the captured
+// structure; otherwise (or after an overflow) render eagerly and capture for the next call.
+int render_graph(dgs_ctx* ctx, Batch& B, float* out_rgb, float* out_depth, float* out_alpha, cudaStream_t stream,
+                 Timer& tm) {
+    int rc;
+    if (ctx->gexec && same_key(make_key(ctx, B, out_rgb, out_depth, out_alpha), ctx->gkey)) {
+        cudaEvent_t a = nullptr;
+        if (ctx->opt.profile) {
+            a = take_event(ctx);
+            cudaEventRecord(a, stream);
+        }
+        DGS_CUDA(ctx, cudaGraphLaunch(ctx->gexec, stream));
+        if (ctx->opt.profile) {
+            cudaEvent_t b = take_event(ctx);
+            cudaEventRecord(b, stream);
+            ctx->ranges_timed.push_back({DGS_K_GRAPH, a, b});
+        }
+        ctx->launches = ctx->glaunches;
+        char* hg = static_cast<char*>(ctx->h_graph);
+        DGS_CUDA(ctx, cudaMemcpyAsync(hg, B.d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+        DGS_CUDA(ctx, cudaMemcpyAsync(hg + 16, static_cast<char*>(ctx->gsizes.p) + 16, 16, cudaMemcpyDeviceToHost,
+                                      stream));
+        DGS_CUDA(ctx, cudaStreamSynchronize(stream));
+        uint32_t errw;
+        uint64_t raw[2];
+        std::memcpy(&errw, hg, 4);
+        std::memcpy(raw, hg + 16, 16);
+        if (ctx->opt.profile)
+            for (const TimedRange& r : ctx->ranges_timed) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) ctx->ktimes[r.cls] += ms;
+            }
+        ctx->stats.n_visible = (int64_t)raw[0];
+        ctx->stats.n_pairs = (int64_t)raw[1];
+        ctx->stats.n_groups = 1;
+        ctx->stats.key_bits = ctx->gbits;
+        if (errw & kErrPose) return fail(ctx, DGS_ERR_INVALID_ARG, "a node pose is not finite or not rigid");
+        if (errw & kErrTimeout) return fail(ctx, DGS_ERR_TIMEOUT, "a bounded device wait timed out (sort look-back)");
+        if (errw & kErrMismatch) return fail(ctx, DGS_ERR_CUDA, "internal: count and emit passes disagree");
+        if (!(errw & kErrCapacity)) {
+            ctx->stats.path = DGS_PATH_GRAPH;
+            ctx->stats.graph_captures = ctx->captures;
+            return DGS_OK;
+        }
+        // the replay's outputs are invalid: render again eagerly (the staged tables are still
+        // in place) and capture with capacities sized for these totals
+        ctx->ranges_timed.clear();
+        ctx->launches = 0;
+        if ((rc = run_eager(ctx, B, out_rgb, out_depth, out_alpha, stream, tm))) return rc;
+        if ((rc = capture_graph(ctx, B, raw[0], raw[1], out_rgb, out_depth, out_alpha))) return rc;
+        ctx->stats.path = DGS_PATH_REGROWN;
+        return DGS_OK;
+    }
+    if ((rc = run_eager(ctx, B, out_rgb, out_depth, out_alpha, stream, tm))) return rc;
+    if ((rc = capture_graph(ctx, B, (uint64_t)ctx->stats.n_visible, (uint64_t)ctx->stats.n_pairs, out_rgb, out_depth,
+                            out_alpha)))
+        return rc;
+    ctx->stats.path = ctx->gexec ? DGS_PATH_CAPTURED : DGS_PATH_EAGER;
+    return DGS_OK;
+}
+
 void begin_call(dgs_ctx* ctx) {
     ctx->err.clear();
     ctx->launches = 0;
@@ -614,8 +885,11 @@ int dgs_context_destroy(dgs_ctx* ctx) {
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->records, &ctx->info,
                       &ctx->keys0, &ctx->vals0, &ctx->keys1, &ctx->vals1, &ctx->hist, &ctx->status, &ctx->counters,
-                      &ctx->ranges, &ctx->errword, &ctx->readback, &ctx->inst_grad};
+                      &ctx->ranges, &ctx->errword, &ctx->readback, &ctx->inst_grad, &ctx->gsizes};
     for (DevBuf* b : bufs) free_buf(*b);
+    drop_graph(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->h_graph) cudaFreeHost(ctx->h_graph);
     if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
     if (ctx->h_read) cudaFreeHost(ctx->h_read);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
@@ -629,7 +903,8 @@ int dgs_workspace_query(const dgs_ctx* ctx, size_t* bytes) {
     if (!ctx || !bytes) return DGS_ERR_INVALID_ARG;
     const DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->records,
                             &ctx->info, &ctx->keys0, &ctx->vals0, &ctx->keys1, &ctx->vals1, &ctx->hist, &ctx->status,
-                            &ctx->counters, &ctx->ranges, &ctx->errword, &ctx->readback, &ctx->inst_grad};
+                            &ctx->counters, &ctx->ranges, &ctx->errword, &ctx->readback, &ctx->inst_grad,
+                            &ctx->gsizes};
     size_t s = 0;
     for (const DevBuf* b : bufs) s += b->bytes;
     *bytes = s;
@@ -660,33 +935,78 @@ int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     Timer tm{ctx, stream, ctx->opt.profile != 0};
     Batch B;
-    int rc = prepare(ctx, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env, max_cams,
-                     out_rgb, out_depth, view_pixel_offset, nullptr, stream, tm, B);
+    int rc = stage(ctx, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env, max_cams,
+                   out_rgb, out_depth, view_pixel_offset, nullptr, stream, tm, B);
     if (rc != DGS_OK || B.V == 0) return rc;
-    Launch L{stream, &ctx->launches};
-    unsigned long long* work = nullptr;
-    if (ctx->opt.profile >= 2) {
-        work = reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->errword.p) + 32);
-        DGS_CUDA(ctx, cudaMemsetAsync(work, 0, 24, stream));
-    }
-    for (int g = 0; g < (int)B.groups.size(); ++g) {
-        GroupLists G;
-        build_group_lists(ctx, B, g, stream, tm, G);
-        tm.begin(DGS_K_COMPOSITE);
-        launch_composite(L, B.d_views, G.v0, G.v1 - G.v0, G.n_tiles, static_cast<uint2*>(ctx->ranges.p), G.vals,
-                         static_cast<Record*>(ctx->records.p), G.P, out_rgb, out_depth, out_alpha, work);
-        tm.end();
-        DGS_CUDA(ctx, cudaGetLastError());
-    }
-    rc = finish(ctx, B, stream);
-    if (rc == DGS_OK && work) {
-        unsigned long long h[3] = {0, 0, 0};
-        DGS_CUDA(ctx, cudaMemcpy(h, work, sizeof(h), cudaMemcpyDeviceToHost));
-        ctx->stats.px_evaluated = (int64_t)h[0];
-        ctx->stats.px_reached = (int64_t)h[1];
-        ctx->stats.px_composited = (int64_t)h[2];
-    }
+    if (ctx->opt.mode == DGS_MODE_GRAPH && B.T > 0)
+        rc = render_graph(ctx, B, out_rgb, out_depth, out_alpha, stream, tm);
+    else
+        rc = run_eager(ctx, B, out_rgb, out_depth, out_alpha, stream, tm);
+    ctx->stats.graph_captures = ctx->captures;
     return rc;
+}
+
+int dgs_autotune(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids, int32_t n_envs,
+                 int32_t max_nodes, const float* node_poses, const dgs_camera* cams, const int32_t* cams_per_env,
+                 int32_t max_cams, float* out_rgb, float* out_depth, float* out_alpha,
+                 const int64_t* view_pixel_offset, const int32_t* candidates, int32_t n_candidates, int32_t reps,
+                 dgs_tune_result* out, void* stream_) {
+    if (!ctx) return DGS_ERR_INVALID_ARG;
+    static const int32_t kDefault[5][2] = {{16, 16}, {32, 8}, {8, 32}, {16, 8}, {8, 8}};
+    const int32_t* cand = candidates ? candidates : &kDefault[0][0];
+    const int nc = candidates ? n_candidates : 5;
+    if (!out) return fail(ctx, DGS_ERR_INVALID_ARG, "out is required");
+    if (nc < 1 || nc > DGS_TUNE_MAX) return fail(ctx, DGS_ERR_INVALID_ARG, "n_candidates must be 1..16");
+    if (reps < 1 || reps > 1000) return fail(ctx, DGS_ERR_INVALID_ARG, "reps must be 1..1000");
+    for (int i = 0; i < nc; ++i) {
+        dgs_options o = ctx->opt;
+        o.tile_w = cand[2 * i];
+        o.tile_h = cand[2 * i + 1];
+        std::string why;
+        if (!check_options(&o, why)) return fail(ctx, DGS_ERR_INVALID_ARG, "candidate " + std::to_string(i) + ": " + why);
+    }
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    const dgs_options saved = ctx->opt;
+    cudaEvent_t a = nullptr, b = nullptr;
+    DGS_CUDA(ctx, cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return fail(ctx, DGS_ERR_CUDA, "cudaEventCreate");
+    }
+    std::memset(out, 0, sizeof(*out));
+    out->n = nc;
+    ctx->opt.profile = 0;
+    int rc = DGS_OK, best = 0;
+    auto render = [&]() {
+        return dgs_render(ctx, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env,
+                          max_cams, out_rgb, out_depth, out_alpha, view_pixel_offset, stream_);
+    };
+    for (int i = 0; i < nc && rc == DGS_OK; ++i) {
+        ctx->opt.tile_w = out->tile_w[i] = cand[2 * i];
+        ctx->opt.tile_h = out->tile_h[i] = cand[2 * i + 1];
+        if ((rc = render())) break;
+        cudaEventRecord(a, stream);
+        for (int r = 0; r < reps && rc == DGS_OK; ++r) rc = render();
+        cudaEventRecord(b, stream);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        out->ms[i] = ms / (float)reps;
+        if (out->ms[i] < out->ms[best]) best = i;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc != DGS_OK) {
+        const std::string why = ctx->err;
+        ctx->opt = saved;
+        ctx->err = why;
+        return rc;
+    }
+    out->best = best;
+    ctx->opt = saved;
+    ctx->opt.tile_w = out->tile_w[best];
+    ctx->opt.tile_h = out->tile_h[best];
+    return render();
 }
 
 int dgs_render_backward(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids,

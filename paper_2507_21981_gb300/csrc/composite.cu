@@ -12,8 +12,10 @@
 namespace dgs {
 namespace {
 
-__global__ void k_ranges(const uint64_t* __restrict__ keys, uint32_t n, uint2* __restrict__ ranges, int n_tiles) {
+__global__ void k_ranges(const uint64_t* __restrict__ keys, uint32_t n, const uint32_t* __restrict__ d_n,
+                         uint2* __restrict__ ranges, int n_tiles) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d_n) n = min(n, *d_n);
     if (i >= n) return;
     const uint64_t t = keys[i] >> kZBits;
     if (t >= (uint64_t)n_tiles) return;   // dead pairs sort past every real tile
@@ -146,10 +148,11 @@ __global__ void __launch_bounds__(256) k_composite(const ViewDesc* __restrict__ 
 
 }  // namespace
 
-void launch_ranges(const Launch& L, const uint64_t* keys, uint32_t n, uint2* ranges, int n_tiles) {
+void launch_ranges(const Launch& L, const uint64_t* keys, uint32_t n, uint2* ranges, int n_tiles,
+                   const uint32_t* d_n) {
     cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, L.stream);
     if (n == 0) return;
-    k_ranges<<<(n + 255) / 256, 256, 0, L.stream>>>(keys, n, ranges, n_tiles);
+    k_ranges<<<(n + 255) / 256, 256, 0, L.stream>>>(keys, n, d_n, ranges, n_tiles);
     ++*L.launches;
 }
 

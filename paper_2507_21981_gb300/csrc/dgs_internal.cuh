@@ -63,6 +63,7 @@ struct Params {
     uint32_t zbase;       // float bits of 2^floor(log2 z_near)
     int32_t tile0;        // first global tile of the current view group
     uint32_t* err;        // device error word
+    const uint32_t* gate; // emission is skipped when non-null and *gate != 0 (capacity overflow)
 };
 
 // Projected instance as stored for compositing: 48 bytes.
@@ -126,11 +127,18 @@ void launch_emit(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_n
                  uint32_t inst_base,
                  uint64_t pair_base, Record* records, InstInfo* info, uint64_t* keys, uint32_t* vals);
 
+// launch_sort / launch_ranges: with d_n non-null the number of pairs is read on the device as
+// min(*d_n, n), and n is the capacity the launches are sized for (graph replay).
 void launch_sort(const Launch& L, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                  uint32_t n, int key_bits, uint32_t* hist, uint32_t* status, uint32_t* counters, uint32_t* err,
-                 uint64_t** keys_out, uint32_t** vals_out, float* sort_ms_slot, cudaEvent_t* evs);
+                 uint64_t** keys_out, uint32_t** vals_out, float* sort_ms_slot, cudaEvent_t* evs,
+                 const uint32_t* d_n = nullptr);
 
-void launch_ranges(const Launch& L, const uint64_t* keys, uint32_t n, uint2* ranges, int n_tiles);
+// Sets the sort kernels' launch attributes; call before a stream capture that contains a sort.
+void sort_prepare();
+
+void launch_ranges(const Launch& L, const uint64_t* keys, uint32_t n, uint2* ranges, int n_tiles,
+                   const uint32_t* d_n = nullptr);
 
 void launch_composite(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
                       const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,

@@ -631,6 +631,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_emit_batched(const NodeDesc
     __shared__ float shc[kEmitWarps][kChunk * kShStride];
     const int chunk = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (chunk >= n_chunks) return;
+    if (P.gate && *P.gate) return;       // capacity overflow: write nothing
     const int lane = (int)lane_id(), wib = threadIdx.x >> 5;
     WarpWork& W = ww[wib];
     const int k = find_node(nodes, n_nodes, chunk);

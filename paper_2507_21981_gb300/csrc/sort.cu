@@ -34,8 +34,12 @@ __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__global__ void __launch_bounds__(kThreads) k_hist(const uint64_t* __restrict__ keys, uint32_t n, int passes, uint32_t* hist) {
+__device__ __forceinline__ uint32_t live_count(uint32_t n, const uint32_t* d_n) { return d_n ? min(*d_n, n) : n; }
+
+__global__ void __launch_bounds__(kThreads) k_hist(const uint64_t* __restrict__ keys, uint32_t n,
+                                                   const uint32_t* __restrict__ d_n, int passes, uint32_t* hist) {
     __shared__ uint32_t sh[8 * 256];
+    n = live_count(n, d_n);
     for (int i = threadIdx.x; i < passes * 256; i += kThreads) sh[i] = 0;
     __syncthreads();
     for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
@@ -67,8 +71,9 @@ __global__ void __launch_bounds__(256) k_hist_scan(uint32_t* hist, int passes) {
 
 __global__ void __launch_bounds__(kThreads) k_onesweep(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                       uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t n,
-                                                      int shift, const uint32_t* __restrict__ digit_off,
-                                                      uint32_t* status, uint32_t* counter, uint32_t* err) {
+                                                      const uint32_t* __restrict__ d_n, int shift,
+                                                      const uint32_t* __restrict__ digit_off, uint32_t* status,
+                                                      uint32_t* counter, uint32_t* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);                          // kTile
     uint32_t* s_vals = reinterpret_cast<uint32_t*>(smem + kTile * 8);               // kTile
@@ -83,6 +88,10 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(const uint64_t* __restric
     for (int i = tid; i < kWarps * 256; i += kThreads) s_whist[i] = 0;
     __syncthreads();
     const uint32_t part = s_part;
+    n = live_count(n, d_n);
+    // a capacity-sized grid: partitions past the live count have no keys (and no later
+    // partition looks back at them)
+    if (part * (uint64_t)kTile >= n && part > 0) return;
     const uint32_t base = part * (uint32_t)kTile;
 
     uint64_t k[kItems];
@@ -182,24 +191,32 @@ int sort_passes(int key_bits) { return (key_bits + 7) / 8; }
 
 size_t sort_status_words(uint32_t n) { return ((size_t)n + kTile - 1) / kTile * 256; }
 
-// hist: [8*256] words, counters: [8] words, status: sort_status_words(n) words.
-void launch_sort(const Launch& L, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, uint32_t n,
-                 int key_bits, uint32_t* hist, uint32_t* status, uint32_t* counters, uint32_t* err,
-                 uint64_t** keys_out, uint32_t** vals_out, float* sort_ms_slot, cudaEvent_t* evs) {
-    (void)sort_ms_slot; (void)evs;
-    *keys_out = keys;
-    *vals_out = vals;
-    if (n <= 1) return;
-    const int passes = sort_passes(key_bits);
+void sort_prepare() {
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, kTile * 12 + kWarps * 256 * 4);
         attr_set = true;
     }
+}
+
+// hist: [8*256] words, counters: [8] words, status: sort_status_words(n) words.
+void launch_sort(const Launch& L, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, uint32_t n,
+                 int key_bits, uint32_t* hist, uint32_t* status, uint32_t* counters, uint32_t* err,
+                 uint64_t** keys_out, uint32_t** vals_out, float* sort_ms_slot, cudaEvent_t* evs,
+                 const uint32_t* d_n) {
+    (void)sort_ms_slot; (void)evs;
+    *keys_out = keys;
+    *vals_out = vals;
+    // with a device-side count every pass runs (the output lands in the same buffer whatever
+    // the count); a host-known count of 0 or 1 is already sorted
+    if (n <= 1 && !d_n) return;
+    if (n == 0) return;
+    const int passes = sort_passes(key_bits);
+    sort_prepare();
     cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 256 * passes, L.stream);
     cudaMemsetAsync(counters, 0, sizeof(uint32_t) * 8, L.stream);
     const int hist_blocks = (int)std::min<uint32_t>(4 * 152, (n + kThreads * 8 - 1) / (kThreads * 8));
-    k_hist<<<hist_blocks, kThreads, 0, L.stream>>>(keys, n, passes, hist);
+    k_hist<<<hist_blocks, kThreads, 0, L.stream>>>(keys, n, d_n, passes, hist);
     k_hist_scan<<<1, 256, 0, L.stream>>>(hist, passes);
     *L.launches += 2;
     const uint32_t parts = (n + kTile - 1) / kTile;
@@ -207,8 +224,9 @@ void launch_sort(const Launch& L, uint64_t* keys, uint32_t* vals, uint64_t* keys
     uint32_t *vi = vals, *vo = vals_alt;
     for (int p = 0; p < passes; ++p) {
         cudaMemsetAsync(status, 0, sizeof(uint32_t) * 256 * (size_t)parts, L.stream);
-        k_onesweep<<<parts, kThreads, kTile * 12 + kWarps * 256 * 4, L.stream>>>(ki, vi, ko, vo, n, 8 * p, hist + p * 256,
-                                                                                 status, counters + p, err);
+        k_onesweep<<<parts, kThreads, kTile * 12 + kWarps * 256 * 4, L.stream>>>(ki, vi, ko, vo, n, d_n, 8 * p,
+                                                                                 hist + p * 256, status, counters + p,
+                                                                                 err);
         ++*L.launches;
         uint64_t* tk = ki; ki = ko; ko = tk;
         uint32_t* tv = vi; vi = vo; vo = tv;

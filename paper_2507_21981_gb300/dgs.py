@@ -17,8 +17,10 @@ LIB_PATH = os.path.join(HERE, "libdgs.so")
 
 DGS_OK, DGS_ERR_INVALID_ARG, DGS_ERR_CUDA, DGS_ERR_OOM, DGS_ERR_CAPACITY, DGS_ERR_TIMEOUT, DGS_ERR_UNSUPPORTED = range(7)
 DGS_F32, DGS_BF16, DGS_F16 = 0, 1, 2
-DGS_MODE_PLAIN, DGS_MODE_BATCHED = 0, 1
-KERNEL_CLASSES = ("setup", "count", "scan", "emit", "sort", "ranges", "composite", "backward")
+DGS_MODE_PLAIN, DGS_MODE_BATCHED, DGS_MODE_GRAPH = 0, 1, 2
+DGS_PATH_EAGER, DGS_PATH_GRAPH, DGS_PATH_CAPTURED, DGS_PATH_REGROWN = 0, 1, 2, 3
+DGS_TUNE_MAX = 16
+KERNEL_CLASSES = ("setup", "count", "scan", "emit", "sort", "ranges", "composite", "backward", "graph")
 STATUS_NAMES = {0: "DGS_OK", 1: "DGS_ERR_INVALID_ARG", 2: "DGS_ERR_CUDA", 3: "DGS_ERR_OOM", 4: "DGS_ERR_CAPACITY",
                 5: "DGS_ERR_TIMEOUT", 6: "DGS_ERR_UNSUPPORTED"}
 
@@ -49,12 +51,18 @@ class dgs_node_grads(C.Structure):
 class dgs_stats(C.Structure):
     _fields_ = [("n_views", C.c_int64), ("n_pixels", C.c_int64), ("n_instances", C.c_int64),
                 ("n_visible", C.c_int64), ("n_pairs", C.c_int64), ("n_groups", C.c_int32), ("key_bits", C.c_int32),
-                ("px_evaluated", C.c_int64), ("px_reached", C.c_int64), ("px_composited", C.c_int64)]
+                ("px_evaluated", C.c_int64), ("px_reached", C.c_int64), ("px_composited", C.c_int64),
+                ("path", C.c_int32), ("graph_captures", C.c_int32)]
+
+
+class dgs_tune_result(C.Structure):
+    _fields_ = [("n", C.c_int32), ("best", C.c_int32), ("tile_w", C.c_int32 * DGS_TUNE_MAX),
+                ("tile_h", C.c_int32 * DGS_TUNE_MAX), ("ms", C.c_float * DGS_TUNE_MAX)]
 
 
 EXPORTED = ("dgs_default_options", "dgs_context_create", "dgs_context_destroy", "dgs_last_error",
             "dgs_workspace_query", "dgs_render", "dgs_last_stats", "dgs_kernel_times", "dgs_last_launches",
-            "dgs_render_noalloc", "dgs_render_backward")
+            "dgs_render_noalloc", "dgs_render_backward", "dgs_autotune")
 
 _lib = None
 _lock = threading.Lock()
@@ -99,6 +107,9 @@ def load(path: str | None = None) -> C.CDLL:
         lib.dgs_render_backward.restype = C.c_int
         lib.dgs_render_backward.argtypes = [vp, C.POINTER(dgs_node), i32, vp, i32, i32, vp, C.POINTER(dgs_camera), vp,
                                             i32, vp, vp, vp, vp, C.POINTER(dgs_node_grads), vp, vp, vp]
+        lib.dgs_autotune.restype = C.c_int
+        lib.dgs_autotune.argtypes = [vp, C.POINTER(dgs_node), i32, vp, i32, i32, vp, C.POINTER(dgs_camera), vp, i32,
+                                     vp, vp, vp, vp, vp, i32, i32, C.POINTER(dgs_tune_result), vp]
         lib.dgs_render_noalloc.restype = C.c_int
         lib.dgs_render_noalloc.argtypes = [C.POINTER(dgs_options), C.POINTER(dgs_node), i32, vp, i32, i32, vp,
                                            C.POINTER(dgs_camera), vp, i32, vp, vp, vp, vp, vp]
@@ -173,7 +184,7 @@ def dgs_last_stats(ctx) -> dict:
 
 
 def dgs_kernel_times(ctx) -> dict:
-    a = (C.c_float * 8)()
+    a = (C.c_float * len(KERNEL_CLASSES))()
     load().dgs_kernel_times(ctx, a)
     return dict(zip(KERNEL_CLASSES, [float(x) for x in a]))
 
@@ -191,3 +202,20 @@ def dgs_render_noalloc(opt, nodes, n_nodes, env_node_ids, n_envs, max_nodes, nod
                                      _ptr(env_node_ids), int(n_envs), int(max_nodes), _ptr(node_poses), cams,
                                      _ptr(cams_per_env), int(max_cams), _ptr(out_rgb), _ptr(out_depth),
                                      _ptr(out_alpha), _ptr(view_pixel_offset), stream)
+
+
+def dgs_autotune(ctx, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env, max_cams,
+                 out_rgb, out_depth, out_alpha, view_pixel_offset, candidates, reps, stream):
+    """Direct call of dgs_autotune.  `candidates` is a sequence of (tile_w, tile_h) or None for
+    the library's default list.  Returns (status, dgs_tune_result)."""
+    res = dgs_tune_result()
+    if candidates is None:
+        cand, nc = None, 0
+    else:
+        flat = np.ascontiguousarray(np.asarray(candidates, np.int32).reshape(-1, 2))
+        cand, nc = flat, len(flat)
+    rc = load().dgs_autotune(ctx, nodes, int(n_nodes), _ptr(env_node_ids), int(n_envs), int(max_nodes),
+                             _ptr(node_poses), cams, _ptr(cams_per_env), int(max_cams), _ptr(out_rgb),
+                             _ptr(out_depth), _ptr(out_alpha), _ptr(view_pixel_offset), _ptr(cand), int(nc),
+                             int(reps), C.byref(res), stream)
+    return rc, res

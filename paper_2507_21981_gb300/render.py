@@ -68,20 +68,31 @@ class DeviceScene:
         return [t[name] for t in self.tensors for name in self.PARAM_NAMES]
 
     def set_poses(self, node_poses):
-        """Replace the per-env node poses ([E,K,3,4] or [E,K,12]) with a device copy."""
-        self.node_poses = torch.as_tensor(node_poses, dtype=torch.float32, device=self.device).reshape(
-            self.n_envs, self.max_nodes, 12).contiguous()
+        """Copy new per-env node poses ([E,K,3,4] or [E,K,12]) into the scene's pose buffer (in
+        place, so a captured render graph keeps reading the same device array)."""
+        src = torch.as_tensor(node_poses, dtype=torch.float32).reshape(self.n_envs, self.max_nodes, 12)
+        if src.data_ptr() != self.node_poses.data_ptr():
+            self.node_poses.copy_(src, non_blocking=False)
 
     def view_slice(self, v: int):
         return slice(int(self.view_offsets[v]), int(self.view_offsets[v + 1]))
 
 
+_MODES = {"plain": D.DGS_MODE_PLAIN, "batched": D.DGS_MODE_BATCHED, "graph": D.DGS_MODE_GRAPH}
+
+
 class Renderer:
-    """A libdgs context.  Options are the fields of dgs_options (see include/dgs.h)."""
+    """A libdgs context.  Options are the fields of dgs_options (see include/dgs.h).
+
+    mode "graph" replays a captured CUDA graph of the whole render when the batch keeps its
+    structure and buffers; render() then returns output tensors owned by the Renderer (the
+    same storage every call, overwritten by the next render) unless `out` is given."""
 
     def __init__(self, mode: str = "batched", tile=(16, 16), profile: int = 0, **opts):
         o = D.dgs_default_options()
-        o.mode = D.DGS_MODE_BATCHED if mode == "batched" else D.DGS_MODE_PLAIN
+        o.mode = _MODES[mode]
+        self.mode = mode
+        self._outs = None
         o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
         o.profile = int(profile)
         for k, v in opts.items():
@@ -105,18 +116,42 @@ class Renderer:
 
     def render(self, ds: DeviceScene, out=None, with_alpha: bool = True, stream=None):
         """Renders every view of `ds`; returns (rgb [P,3], depth [P], alpha [P] or None), flat over views."""
-        if out is None:
-            rgb = torch.empty((ds.n_pixels, 3), dtype=torch.float32, device=ds.device)
-            depth = torch.empty((ds.n_pixels,), dtype=torch.float32, device=ds.device)
-            alpha = torch.empty((ds.n_pixels,), dtype=torch.float32, device=ds.device) if with_alpha else None
-        else:
-            rgb, depth, alpha = out
+        rgb, depth, alpha = out if out is not None else self._outputs(ds, with_alpha)
         s = stream if stream is not None else torch.cuda.current_stream(ds.device)
         rc = D.dgs_render(self.ctx, ds.nodes, ds.n_nodes, ds.env_node_ids, ds.n_envs, ds.max_nodes, ds.node_poses,
                           ds.cams, ds.cams_per_env, ds.max_cams, rgb, depth, alpha, None, s.cuda_stream)
         if rc != D.DGS_OK:
             raise D.DgsError(rc, D.dgs_last_error(self.ctx))
         return rgb, depth, alpha
+
+    def _outputs(self, ds: DeviceScene, with_alpha: bool):
+        def fresh():
+            return (torch.empty((ds.n_pixels, 3), dtype=torch.float32, device=ds.device),
+                    torch.empty((ds.n_pixels,), dtype=torch.float32, device=ds.device),
+                    torch.empty((ds.n_pixels,), dtype=torch.float32, device=ds.device) if with_alpha else None)
+        if self.mode != "graph":
+            return fresh()
+        o = self._outs
+        if o is None or o[1].numel() != ds.n_pixels or o[1].device != ds.device or (o[2] is not None) != with_alpha:
+            self._outs = o = fresh()
+        return o
+
+    def autotune(self, ds: DeviceScene, candidates=None, reps: int = 3, out=None, with_alpha: bool = True,
+                 stream=None):
+        """Times dgs_render of `ds` with each candidate tile shape ((w, h) pairs; None = the
+        library's list), keeps the fastest on this context and renders once with it.
+        Returns (best (w, h), {(w, h): ms per render}, (rgb, depth, alpha))."""
+        rgb, depth, alpha = out if out is not None else self._outputs(ds, with_alpha)
+        s = stream if stream is not None else torch.cuda.current_stream(ds.device)
+        rc, res = D.dgs_autotune(self.ctx, ds.nodes, ds.n_nodes, ds.env_node_ids, ds.n_envs, ds.max_nodes,
+                                 ds.node_poses, ds.cams, ds.cams_per_env, ds.max_cams, rgb, depth, alpha, None,
+                                 candidates, reps, s.cuda_stream)
+        if rc != D.DGS_OK:
+            raise D.DgsError(rc, D.dgs_last_error(self.ctx))
+        times = {(res.tile_w[i], res.tile_h[i]): float(res.ms[i]) for i in range(res.n)}
+        best = (res.tile_w[res.best], res.tile_h[res.best])
+        self.options.tile_w, self.options.tile_h = best
+        return best, times, (rgb, depth, alpha)
 
     def backward(self, ds: DeviceScene, out_rgb, out_depth, grad_rgb, grad_depth=None, want_poses: bool = True,
                  stream=None):

@@ -56,7 +56,8 @@ def test_struct_sizes_match_header(lib):
     assert C.sizeof(D.dgs_node) == 56
     assert C.sizeof(D.dgs_camera) == 72
     assert C.sizeof(D.dgs_options) == 64
-    assert C.sizeof(D.dgs_stats) == 72
+    assert C.sizeof(D.dgs_stats) == 80
+    assert C.sizeof(D.dgs_tune_result) == 8 + 3 * 4 * D.DGS_TUNE_MAX
 
 
 def test_invalid_options_rejected(lib):
@@ -138,6 +139,36 @@ def test_render_validates_arguments_on_host(lib):
         cpe[0] = 1
         cams[0].cam_from_world[3] = float("nan")
         assert _render(lib, ctx, nodes, 1, ids, 1, 1, cams, cpe, 1) == D.DGS_ERR_INVALID_ARG
+    finally:
+        lib.dgs_context_destroy(ctx)
+
+
+def test_graph_mode_is_accepted_and_bad_modes_rejected(lib):
+    o = D.dgs_default_options()
+    o.mode = D.DGS_MODE_GRAPH
+    h = C.c_void_p()
+    assert lib.dgs_context_create(C.byref(h), C.byref(o)) == D.DGS_OK
+    lib.dgs_context_destroy(h)
+    o.mode = 3
+    assert lib.dgs_context_create(C.byref(h), C.byref(o)) == D.DGS_ERR_INVALID_ARG
+
+
+def test_autotune_validates_arguments_on_host(lib):
+    ctx = _ctx(lib)
+    try:
+        nodes, ids, cams, cpe = _args()
+        res = D.dgs_tune_result()
+
+        def tune(cand, nc, reps, out=True):
+            cp = None if cand is None else np.ascontiguousarray(np.asarray(cand, np.int32)).ctypes.data
+            return lib.dgs_autotune(ctx, nodes, 1, ids.ctypes.data, 1, 1, FAKE_DEV, cams, cpe.ctypes.data, 1,
+                                    FAKE_DEV, FAKE_DEV, None, None, cp, nc, reps, C.byref(res) if out else None, None)
+        assert tune(None, 0, 3, out=False) == D.DGS_ERR_INVALID_ARG
+        assert tune(None, 0, 0) == D.DGS_ERR_INVALID_ARG                  # reps
+        assert tune([[16, 16]] * 17, 17, 1) == D.DGS_ERR_INVALID_ARG      # too many candidates
+        assert tune([[16, 16], [12, 8]], 2, 1) == D.DGS_ERR_INVALID_ARG   # 12 is not a multiple of 8
+        assert "candidate 1" in D.dgs_last_error(ctx)
+        assert tune([[16, 32]], 1, 1) == D.DGS_ERR_INVALID_ARG            # area 512
     finally:
         lib.dgs_context_destroy(ctx)
 
