@@ -110,7 +110,7 @@ def fwd_bwd_500k(dev, warmup, steps):
     from paper_2507_21981_gb300 import scenes
     from paper_2507_21981_gb300.render import DeviceScene, Renderer
     sc = scenes.config4(seed=1)
-    ds = DeviceScene(sc, device=dev)
+    ds = DeviceScene(sc, device=dev, spatial_order=True)
     r = Renderer(mode="batched", profile=True)
     gen = torch.Generator(device=dev).manual_seed(0)
     g_rgb = torch.randn((ds.n_pixels, 3), device=dev, generator=gen)
@@ -154,7 +154,7 @@ def ragged_graph(dev, warmup, steps):
     from paper_2507_21981_gb300 import scenes
     from paper_2507_21981_gb300.render import DeviceScene, Renderer
     sc = scenes.config3(seed=1)
-    ds = DeviceScene(sc, device=dev)
+    ds = DeviceScene(sc, device=dev, spatial_order=True)
     out = (torch.empty((ds.n_pixels, 3), device=dev), torch.empty((ds.n_pixels,), device=dev), None)
     r = Renderer(mode="graph")
     best, times, _ = r.autotune(ds, reps=2, out=out)
@@ -182,7 +182,7 @@ def precision_scale(dev, warmup, steps):
     res = {"workload": "128 envs x 3 cams 640x480, 3M-Gaussian SH3 room + 6 objects x 50k (config 5)",
            "views": sc.n_views, "pixels_per_step": sc.n_pixels, "gaussians": sc.n_gaussians, "steps": steps}
     for dt in ("bf16", "f16", "f32"):
-        ds = DeviceScene(sc, device=dev, dtype=dt)
+        ds = DeviceScene(sc, device=dev, dtype=dt, spatial_order=True)
         out = (torch.empty((ds.n_pixels, 3), device=dev), torch.empty((ds.n_pixels,), device=dev), None)
         r = Renderer(mode="graph")
         for _ in range(warmup):
@@ -264,7 +264,7 @@ def main():
     from paper_2507_21981_gb300.render import DeviceScene, Renderer
 
     sc = scenes.config2(seed=1 + rank, n_envs=args.envs)
-    ds = DeviceScene(sc, device=dev)
+    ds = DeviceScene(sc, device=dev, spatial_order=True)
     stream = torch.cuda.current_stream(dev)
     px_per_step = ds.n_pixels
 
@@ -410,7 +410,7 @@ def main():
         "data": "synthetic (seeded room + objects; the paper's scanned scenes are not available)",
         "config": {"workload": WORKLOAD, "views": ds.n_views, "pixels_per_step": px_per_step, "gaussians": sc.n_gaussians,
                    "l2": "inputs larger than L2 (255 MB attributes, 629 MB outputs per step)", "mode": "batched",
-                   "tile": "16x16"},
+                   "tile": "16x16", "layout": "nodes stored in Z-order of their means (dgs_spatial_order, once at load)"},
         "plain_mpix_s": plain_value, "batched_over_plain": value / plain_value,
         "graph_mpix_s": graph_value, "graph_path": graph_path,
         "fwd_bwd_ms_per_view_500k": fb["ms"],

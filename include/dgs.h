@@ -241,6 +241,20 @@ int dgs_kernel_times(const dgs_ctx* ctx, float* ms);
  * kernel nodes it runs). */
 int64_t dgs_last_launches(const dgs_ctx* ctx);
 
+/*
+ * Storage order for a node (asset formatting, Sec. III-B: assets are converted once into the
+ * renderer's format).  Writes to perm[n] (HOST) the permutation that lists the node's
+ * Gaussians along a Z-order (Morton) curve of their means, mean[n,3] (HOST, FP32): 21 bits
+ * per axis over the node's bounding box, one cell size for all axes, ties and non-finite means
+ * (placed last) in index order.  The caller stores every attribute array permuted by it,
+ * a'[i] = a[perm[i]], once at load time; global ids then follow the new order.  The renderer
+ * culls each run of 32 consecutive Gaussians per view with one bounding-sphere test, which
+ * rejects work only for spatially compact runs: the order changes speed, not the image
+ * (except the id tie-break between Gaussians with bit-equal depth keys in one pixel).
+ * Returns DGS_ERR_INVALID_ARG for n < 0 or null pointers with n > 0.  No GPU is used.
+ */
+int dgs_spatial_order(const float* mean, int64_t n, int64_t* perm);
+
 /* Result of dgs_autotune: the candidates timed and the one chosen. */
 #define DGS_TUNE_MAX 16
 typedef struct dgs_tune_result {

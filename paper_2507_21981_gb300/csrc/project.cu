@@ -213,6 +213,67 @@ __device__ __forceinline__ bool may_be_visible(const Gauss& g, const VNode& vn, 
            v - hy - 0.5f <= (float)(vd.H - 1);
 }
 
+// Bound of a 32-Gaussian chunk in the node frame: a ball of radius r around c holding every
+// mean, and the largest standard deviation sigma.
+struct ChunkBound {
+    float x, y, z, r, sigma;
+};
+
+// Warp-wide: all lanes get the same bound (butterfly sums are bitwise equal on every lane).
+// Non-finite values make the bound non-finite, and chunk_may_be_visible then keeps the chunk.
+__device__ __forceinline__ ChunkBound chunk_bound(const Gauss& g, bool valid) {
+    const uint32_t full = 0xffffffffu;
+    const float nv = (float)__popc(__ballot_sync(full, valid));
+    float sx = valid ? g.mx : 0.f, sy = valid ? g.my : 0.f, sz = valid ? g.mz : 0.f;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        sx += __shfl_xor_sync(full, sx, o);
+        sy += __shfl_xor_sync(full, sy, o);
+        sz += __shfl_xor_sync(full, sz, o);
+    }
+    ChunkBound b;
+    b.x = sx / nv; b.y = sy / nv; b.z = sz / nv;
+    const float dx = g.mx - b.x, dy = g.my - b.y, dz = g.mz - b.z;
+    const float d = valid ? sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) : 0.f;
+    const float sg = valid ? sqrtf(g.smax) : 0.f;
+    // non-negative floats order like their bit patterns (NaN above +inf)
+    b.r = __uint_as_float(__reduce_max_sync(full, __float_as_uint(d)));
+    b.sigma = __uint_as_float(__reduce_max_sync(full, __float_as_uint(sg)));
+    return b;
+}
+
+// Conservative per-view cull of a whole chunk: false only if may_be_visible() is false for
+// every Gaussian of the chunk.  may_be_visible() keeps a Gaussian only if z > z_near and its
+// box reaches the image, e.g. u + hx - 1/2 >= 0 on the left, with
+//   hx <= k_x (fx / z) sigma + m,   k_x = sqrt(1.02 qbin (1 + limx^2)),  m = sqrt(qbin lowpass) + 1e-3
+// (sqrt(a + b) <= sqrt(a) + sqrt(b)).  Multiplied by z > 0 the left condition becomes the
+// half-space  fx x + (cx - 1/2 + m) z + k_x fx sigma >= 0  of the camera-space mean, whose
+// largest value over the chunk's ball is n.c + |n| r + k_x fx sigma; likewise for the other
+// three image edges, and z <= c_z + r for the near plane.  Slack covers the rigid transform's
+// orthonormality tolerance (1e-4) and FP32 rounding.
+__device__ __forceinline__ bool chunk_may_be_visible(const ChunkBound& b, const VNode& vn, const ViewDesc& vd,
+                                                     const Params& P) {
+    const float* M = vn.M;
+    const float x = fmaf(M[0], b.x, fmaf(M[1], b.y, fmaf(M[2], b.z, M[3])));
+    const float y = fmaf(M[4], b.x, fmaf(M[5], b.y, fmaf(M[6], b.z, M[7])));
+    const float z = fmaf(M[8], b.x, fmaf(M[9], b.y, fmaf(M[10], b.z, M[11])));
+    const float R = fmaf(b.r, 1.001f, 1e-5f * (fabsf(x) + fabsf(y) + fabsf(z)) + 1e-6f);
+    if (z + R <= P.z_near) return false;
+    const float m = sqrtf(P.qbin * P.lowpass) + 2e-3f;
+    const float kx = 1.01f * sqrtf(1.02f * P.qbin * fmaf(vd.limx, vd.limx, 1.f)) * vd.fx * b.sigma;
+    const float ky = 1.01f * sqrtf(1.02f * P.qbin * fmaf(vd.limy, vd.limy, 1.f)) * vd.fy * b.sigma;
+    const float nzl = vd.cx - 0.5f + m, nzr = (float)vd.W - 0.5f - vd.cx + m;
+    const float nzt = vd.cy - 0.5f + m, nzb = (float)vd.H - 0.5f - vd.cy + m;
+    // largest value of n.p over the ball, p = (x, y, z) + d, |d| <= R, with a relative slack
+    const float fl = fmaf(vd.fx, x, nzl * z) + sqrtf(fmaf(vd.fx, vd.fx, nzl * nzl)) * R + kx;
+    const float fr = fmaf(-vd.fx, x, nzr * z) + sqrtf(fmaf(vd.fx, vd.fx, nzr * nzr)) * R + kx;
+    const float ft = fmaf(vd.fy, y, nzt * z) + sqrtf(fmaf(vd.fy, vd.fy, nzt * nzt)) * R + ky;
+    const float fb = fmaf(-vd.fy, y, nzb * z) + sqrtf(fmaf(vd.fy, vd.fy, nzb * nzb)) * R + ky;
+    const float ex = 1e-4f * (vd.fx * fabsf(x) + fmaxf(fabsf(nzl), fabsf(nzr)) * fabsf(z));
+    const float ey = 1e-4f * (vd.fy * fabsf(y) + fmaxf(fabsf(nzt), fabsf(nzb)) * fabsf(z));
+    return !(fl + ex < 0.f || fr + ex < 0.f || ft + ey < 0.f || fb + ey < 0.f);
+}
+
 // Does the ellipse {d^T conic d <= qlim} reach a pixel centre of the rectangle
 // [X0,X1] x [Y0,Y1] (coordinates relative to the mean)?  Minimum of the convex quadratic over
 // the rectangle: 0 if the mean is inside, else the smallest of the four edge minima.
@@ -455,7 +516,7 @@ template <bool EMIT>
 __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lane, const NodeView* __restrict__ entries,
                                               int n_entries, int v0, int v1, const ViewDesc* __restrict__ views,
                                               const VNode* __restrict__ vnodes, int K, const Params& P, const Gauss& gme,
-                                              bool valid, WarpWork& W, const float* __restrict__ shc,
+                                              bool valid, const ChunkBound& cb, WarpWork& W, const float* __restrict__ shc,
                                               uint2* __restrict__ counts, const uint32_t* __restrict__ inst_off,
                                               const uint64_t* __restrict__ pair_off, uint32_t inst_base,
                                               uint64_t pair_base, Record* __restrict__ rec, InstInfo* __restrict__ info,
@@ -465,6 +526,7 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
         const int nvb = min(kViewBlock, n_entries - eb);
         // 1. survivors of each view of the block: lane j fetches the table entries of view j
         //    (one round of loads for the whole block), then one ballot per view (count pass)
+        bool sees = false;
         if (lane < nvb) {
             const int j = lane;
             const NodeView w = entries[eb + j];
@@ -474,6 +536,7 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
             if (in) {
                 const int64_t t = vnodes[w.view * K + w.slot].tab + c;
                 WV.tab[j] = t;
+                if constexpr (!EMIT) sees = chunk_may_be_visible(cb, vnodes[w.view * K + w.slot], views[w.view], P);
                 if constexpr (EMIT) {
                     WV.mask[j] = counts[t].x;
                     const ViewDesc& vd = views[w.view];
@@ -487,9 +550,10 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
         }
         __syncwarp();
         if constexpr (!EMIT) {
+            const uint32_t seen = __ballot_sync(0xffffffffu, sees);   // views the chunk's ball may reach
             for (int j = 0; j < nvb; ++j) {
                 const int vvj = WV.vv[j];
-                if (vvj < 0) continue;
+                if (vvj < 0 || !((seen >> j) & 1u)) continue;
                 const uint32_t m = __ballot_sync(0xffffffffu, valid && may_be_visible(gme, vnodes[vvj], views[vvj / K], P));
                 if (lane == 0) WV.mask[j] = m;
             }
@@ -592,8 +656,9 @@ __global__ void __launch_bounds__(kCountWarps * 32) k_count_batched(const NodeDe
     Gauss g;
     bool valid;
     stage_geometry<DT>(nd, c, lane, W, g, valid);
+    const ChunkBound cb = chunk_bound(g, valid);
     process_chunk<false>(nd, c, lane, nv + nv_off[k], nv_off[k + 1] - nv_off[k], v0, v1, views, vnodes, K, P, g, valid,
-                         W, nullptr, counts, nullptr, nullptr, 0, 0, nullptr, nullptr, nullptr, nullptr);
+                         cb, W, nullptr, counts, nullptr, nullptr, 0, 0, nullptr, nullptr, nullptr, nullptr);
 }
 
 // Plain mode: the chunks of one view.  pmap = [K+1 prefix chunk counts in node-id order, K slots].
@@ -615,8 +680,9 @@ __global__ void __launch_bounds__(kCountWarps * 32) k_count_plain(const NodeDesc
     Gauss g;
     bool valid;
     stage_geometry<DT>(nd, c, lane, W, g, valid);
+    const ChunkBound cb = chunk_bound(g, valid);
     const NodeView one{v, slot};
-    process_chunk<false>(nd, c, lane, &one, 1, v, v + 1, views, vnodes, K, P, g, valid, W, nullptr, counts, nullptr,
+    process_chunk<false>(nd, c, lane, &one, 1, v, v + 1, views, vnodes, K, P, g, valid, cb, W, nullptr, counts, nullptr,
                          nullptr, 0, 0, nullptr, nullptr, nullptr, nullptr);
 }
 
@@ -643,7 +709,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_emit_batched(const NodeDesc
     stage_geometry<DT>(nd, c, lane, W, g, valid);
     stage_sh<DT>(nd, c, lane, shc[wib]);
     process_chunk<true>(nd, c, lane, nv + nv_off[k], nv_off[k + 1] - nv_off[k], v0, v1, views, vnodes, K, P, g, valid,
-                        W, shc[wib], const_cast<uint2*>(counts), inst_off, pair_off, inst_base, pair_base, rec, info,
+                        ChunkBound{}, W, shc[wib], const_cast<uint2*>(counts), inst_off, pair_off, inst_base, pair_base, rec, info,
                         keys, vals);
 }
 
@@ -671,7 +737,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_emit_plain(const NodeDesc* 
     stage_geometry<DT>(nd, c, lane, W, g, valid);
     stage_sh<DT>(nd, c, lane, shc[wib]);
     const NodeView one{v, slot};
-    process_chunk<true>(nd, c, lane, &one, 1, v, v + 1, views, vnodes, K, P, g, valid, W, shc[wib],
+    process_chunk<true>(nd, c, lane, &one, 1, v, v + 1, views, vnodes, K, P, g, valid, ChunkBound{}, W, shc[wib],
                         const_cast<uint2*>(counts), inst_off, pair_off, inst_base, pair_base, rec, info, keys, vals);
 }
 

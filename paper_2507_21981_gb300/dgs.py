@@ -62,7 +62,7 @@ class dgs_tune_result(C.Structure):
 
 EXPORTED = ("dgs_default_options", "dgs_context_create", "dgs_context_destroy", "dgs_last_error",
             "dgs_workspace_query", "dgs_render", "dgs_last_stats", "dgs_kernel_times", "dgs_last_launches",
-            "dgs_render_noalloc", "dgs_render_backward", "dgs_autotune")
+            "dgs_render_noalloc", "dgs_render_backward", "dgs_autotune", "dgs_spatial_order")
 
 _lib = None
 _lock = threading.Lock()
@@ -107,6 +107,8 @@ def load(path: str | None = None) -> C.CDLL:
         lib.dgs_render_backward.restype = C.c_int
         lib.dgs_render_backward.argtypes = [vp, C.POINTER(dgs_node), i32, vp, i32, i32, vp, C.POINTER(dgs_camera), vp,
                                             i32, vp, vp, vp, vp, C.POINTER(dgs_node_grads), vp, vp, vp]
+        lib.dgs_spatial_order.restype = C.c_int
+        lib.dgs_spatial_order.argtypes = [vp, i64, vp]
         lib.dgs_autotune.restype = C.c_int
         lib.dgs_autotune.argtypes = [vp, C.POINTER(dgs_node), i32, vp, i32, i32, vp, C.POINTER(dgs_camera), vp, i32,
                                      vp, vp, vp, vp, vp, i32, i32, C.POINTER(dgs_tune_result), vp]
@@ -219,3 +221,13 @@ def dgs_autotune(ctx, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_pose
                              _ptr(out_depth), _ptr(out_alpha), _ptr(view_pixel_offset), _ptr(cand), int(nc),
                              int(reps), C.byref(res), stream)
     return rc, res
+
+
+def dgs_spatial_order(mean) -> np.ndarray:
+    """Direct call of dgs_spatial_order on a host [n,3] FP32 array; returns the int64 permutation."""
+    m = np.ascontiguousarray(mean, np.float32).reshape(-1, 3)
+    perm = np.empty(len(m), np.int64)
+    rc = load().dgs_spatial_order(m.ctypes.data if len(m) else None, len(m), perm.ctypes.data if len(m) else None)
+    if rc != DGS_OK:
+        raise DgsError(rc, "dgs_spatial_order")
+    return perm

@@ -2,6 +2,7 @@
 step runs in the CUDA library (dgs.py marshals the arguments)."""
 from __future__ import annotations
 
+import copy
 import ctypes as C
 
 import numpy as np
@@ -18,10 +19,20 @@ class DeviceScene:
 
     Attribute storage: `dtype` in {"f32", "bf16", "f16"} applies to log-scales, quaternions
     and SH coefficients; means and opacity logits stay FP32.
+
+    spatial_order: store every node's Gaussians in the order dgs_spatial_order gives (Z-order of
+    the means), applied once here; `perms[k]` maps stored index -> index in `scene`, and
+    `scene` is the permuted scene the device arrays hold (gradients come back in that order).
     """
 
-    def __init__(self, scene, device="cuda", dtype: str = "f32"):
+    def __init__(self, scene, device="cuda", dtype: str = "f32", spatial_order: bool = False):
         tdt, code = _TORCH_DTYPES[dtype]
+        self.perms = None
+        if spatial_order:
+            self.perms = [D.dgs_spatial_order(nd.mean) for nd in scene.nodes]
+            scene = copy.copy(scene)
+            scene.nodes = [nd.subset(p) for nd, p in zip(scene.nodes, self.perms)]
+        self.scene = scene
         self.dtype = dtype
         self.device = torch.device(device)
         self.tensors = []

@@ -12,9 +12,9 @@ pytestmark = pytest.mark.gpu
 OPTS = O.OracleOptions()
 
 
-def _render(sc, mode="batched", dtype="f32", **kw):
+def _render(sc, mode="batched", dtype="f32", spatial_order=False, **kw):
     from paper_2507_21981_gb300.render import DeviceScene, Renderer
-    ds = DeviceScene(sc, device="cuda:0", dtype=dtype)
+    ds = DeviceScene(sc, device="cuda:0", dtype=dtype, spatial_order=spatial_order)
     r = Renderer(mode=mode, **kw)
     rgb, depth, alpha = r.render(ds)
     torch.cuda.synchronize()
@@ -71,11 +71,12 @@ def test_batched_equals_plain_bitwise():
         assert np.array_equal(x, y)
 
 
-def test_config3_reduced_ragged_views():
+@pytest.mark.parametrize("spatial_order", [False, True])
+def test_config3_reduced_ragged_views(spatial_order):
     sc = S.config3(seed=1, n_envs=6, n_bg=30_000, n_assets=8, asset_lo=500, asset_hi=4_000, max_nodes=4,
                    resolutions=((80, 60), (160, 120), (200, 110)))
-    ds, out, st, _ = _render(sc, "batched")
-    _check_views(sc, ds, out, range(sc.n_views))
+    ds, out, st, _ = _render(sc, "batched", spatial_order=spatial_order)
+    _check_views(ds.scene, ds, out, range(sc.n_views))
 
 
 def test_ragged_tiles_and_tile_shapes():
@@ -112,14 +113,69 @@ def test_all_transparent_scene_gives_background():
     assert np.allclose(rgb, [0.1, 0.2, 0.3], atol=1e-7) and np.all(depth == 0) and np.all(alpha == 0)
 
 
-def test_config2_full_size_sampled_views():
-    """Full workload of the benchmark (64 envs x 2 cams 640x480, 1.08M Gaussians); the oracle
-    checks two seeded sampled views pixel by pixel."""
+@pytest.mark.parametrize("mode", ["batched", "graph"])
+def test_config2_full_size_sampled_views(mode):
+    """Full workload of the benchmark (64 envs x 2 cams 640x480, 1.08M Gaussians, nodes in
+    Z-order as the benchmark stores them); the oracle checks two seeded sampled views pixel by
+    pixel of the permuted scene."""
     sc = S.config2(seed=1)
-    ds, out, st, _ = _render(sc, "batched")
-    assert st["n_views"] == 128 and st["n_groups"] >= 1
+    from paper_2507_21981_gb300.render import DeviceScene, Renderer
+    ds = DeviceScene(sc, device="cuda:0", spatial_order=True)
+    r = Renderer(mode=mode)
+    for _ in range(2 if mode == "graph" else 1):     # graph: the second call replays
+        out = [t.cpu().numpy() for t in r.render(ds)]
+    st = r.stats()
+    r.close()
+    assert st["n_views"] == 128 and st["n_groups"] >= 1 and st["path"] == (1 if mode == "graph" else 0)
     views = sorted(int(v) for v in np.random.default_rng(7).choice(sc.n_views, 2, replace=False))
-    _check_views(sc, ds, out, views, packed=O.oracle._Packed(sc))
+    _check_views(ds.scene, ds, out, views, packed=O.oracle._Packed(ds.scene))
+
+
+def test_spatial_order_reduced_all_views_and_nearly_equal_image():
+    """Z-ordered storage: every view against the oracle of the permuted scene.  Against the
+    original order the image changes only where two Gaussians reaching a pixel share a depth
+    key bit for bit (their id order follows the permutation): a few pixels in 1e5."""
+    sc = S.config2(seed=1, n_envs=4, n_bg=60_000, n_obj=2_000, width=160, height=120, f=125.0)
+    ds, out, st, _ = _render(sc, "batched", spatial_order=True)
+    _check_views(ds.scene, ds, out, range(8))
+    _, ref, st0, _ = _render(sc, "batched")
+    assert st["n_visible"] == st0["n_visible"] and st["n_pairs"] == st0["n_pairs"]
+    differ = np.any(out[0] != ref[0], axis=1) | (out[1] != ref[1])
+    assert differ.mean() < 1e-3, int(differ.sum())
+
+
+def _cluster(rng, n, centre, spread, log_sigma, opacity_logit):
+    mean = (np.asarray(centre) + rng.uniform(-spread, spread, (n, 3))).astype(np.float32)
+    q = rng.normal(size=(n, 4)).astype(np.float32)
+    sh = rng.uniform(-1.0, 1.0, (n, 1, 3)).astype(np.float32)
+    return S.GaussianNode(mean, np.full((n, 3), log_sigma, np.float32), q,
+                          np.full(n, opacity_logit, np.float32), sh, 0, "cluster")
+
+
+def test_chunk_cull_keeps_gaussians_that_bleed_into_the_image():
+    """Camera at (0,0,-5) looking along +z, 128x128, f = 110: at depth 5 the image edges lie at
+    |x|, |y| = 2.909.  Four 32-Gaussian clusters sit just outside the four edges (centres about
+    2 px beyond them, sigma 2.2 px) and reach back into the image; one straddles the near plane;
+    one lies far outside (its chunk is culled); a cloud fills the middle.  The per-chunk cull
+    must keep every Gaussian whose ellipse reaches a pixel."""
+    rng = np.random.default_rng(0)
+    e = 5.0 * 64.0 / 110.0
+    parts = [_cluster(rng, 32, c, 0.04, np.log(0.1), 3.0)
+             for c in [(-e - 0.1, 0, 0), (e + 0.1, 0.5, 0), (0.4, -e - 0.1, 0), (-0.3, e + 0.1, 0)]]
+    parts.append(_cluster(rng, 32, (0.0005, 0.0003, -4.99), 0.004, np.log(0.0005), -1.0))
+    parts.append(_cluster(rng, 32, (-e - 3.0, 0, 0), 0.04, np.log(0.1), 3.0))
+    parts.append(_cluster(rng, 256, (0, 0, 0), 1.5, np.log(0.05), 0.0))
+    node = S.GaussianNode(*(np.concatenate([getattr(p, f) for p in parts]) for f in
+                            ("mean", "log_scale", "quat", "opacity_logit", "sh")), 0, "edges")
+    I = np.concatenate([np.eye(3), np.zeros((3, 1))], axis=1)
+    cam = np.concatenate([np.eye(3), np.array([[0.0], [0.0], [5.0]])], axis=1)
+    sc = S.scene_from_lists("edges", [node], [[0]], [[I]], [[(110.0, 110.0, 64.0, 64.0, 128, 128, cam)]])
+    for mode in ("batched", "plain"):
+        ds, out, _, _ = _render(sc, mode, spatial_order=True)
+        _check_views(ds.scene, ds, out, [0])
+    ref = O.render_view(sc, 0, 0, OPTS)
+    a = ref.alpha                                      # the border coverage comes from the edge clusters
+    assert a[:, 0].max() > 0.2 and a[:, -1].max() > 0.2 and a[0, :].max() > 0.2 and a[-1, :].max() > 0.2
 
 
 def test_config4_full_view():
