@@ -371,8 +371,12 @@ def main():
     peaks, peak_kind = _peaks()
     per_step = {k: v / args.steps for k, v in ktimes.items()}
     dom = max(per_step, key=per_step.get)
-    P = stats["n_pairs"]
-    passes = (stats["key_bits"] + 7) // 8
+    P, NV = stats["n_pairs"], stats["n_visible"]
+    passes = (stats["key_bits"] + 7) // 8          # tile-sort passes (key_bits = tile key bits)
+    # algorithmic bytes of the binning class: depth sort of the instances (28-bit keys, 4
+    # passes of 16 B plus the histogram read), tile-count scan (16 B), pair emission (record
+    # 48 + identity 8 + order/offsets 12 read; 8 B written per pair) and the tile sort
+    sort_bytes = NV * (4 + 4 * 16 + 16 + 68) + P * (8 + 4 + passes * 16)
     # compositor work of one step, counted by the instrumented compositor outside the timed region
     rc_ = Renderer(mode="batched", profile=2)
     rc_.render(ds, out=out)
@@ -387,11 +391,12 @@ def main():
                       "units": {"pairs_reached": work["px_reached"], "pairs_composited": work["px_composited"],
                                 "pairs_evaluated": work["px_evaluated"], "ops_per_pair": OPS_PER_PAIR}},
         "sort": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
-                 "achieved": P * (8 + passes * 24) / (per_step["sort"] / 1e3) / 1e9,
-                 "units": {"pairs": P, "passes": passes, "bytes_per_pair": 8 + passes * 24}},
+                 "achieved": sort_bytes / (per_step["sort"] / 1e3) / 1e9,
+                 "units": {"instances": NV, "pairs": P, "depth_passes": 4, "tile_passes": passes,
+                           "bytes_per_instance": 4 + 4 * 16 + 16 + 68, "bytes_per_pair": 8 + 4 + passes * 16}},
         "emit": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
-                 "achieved": (sc.n_gaussians * 236 + stats["n_visible"] * 56 + P * 12) / (per_step["emit"] / 1e3) / 1e9,
-                 "units": {"gaussians": sc.n_gaussians, "visible": stats["n_visible"], "pairs": P}},
+                 "achieved": (sc.n_gaussians * 236 + NV * (48 + 8 + 12)) / (per_step["emit"] / 1e3) / 1e9,
+                 "units": {"gaussians": sc.n_gaussians, "visible": NV, "bytes_per_visible": 68}},
         "count": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
                   "achieved": sc.n_gaussians * 40 / (per_step["count"] / 1e3) / 1e9,
                   "units": {"gaussians": sc.n_gaussians, "bytes_per_gaussian": 40}},

@@ -49,8 +49,11 @@ struct dgs_ctx {
     dgs_options opt{};
     std::string err;
     int device = 0;
-    DevBuf meta, counts, inst_off, pair_off, parts, records, info, keys0, vals0, keys1, vals1, hist, status, counters,
-        ranges, errword, readback, inst_grad, gsizes;
+    // dkey/ival: depth keys and instance numbers (depth sort, ping-pong); ntile: pairs per
+    // instance; poff/tparts: pair offsets in depth order; tkeys/tvals: (tile, instance) pairs
+    // (tile sort, ping-pong); totals: exact pairs per view group
+    DevBuf meta, counts, inst_off, pair_off, parts, records, info, dkey0, ival0, dkey1, ival1, ntile, poff, tparts,
+        tkeys0, tvals0, tkeys1, tvals1, hist, status, counters, ranges, errword, readback, inst_grad, gsizes, totals;
     uint64_t gen = 0;                     // bumped whenever a workspace buffer is reallocated
     // graph replay (DGS_MODE_GRAPH)
     cudaStream_t cap_stream = nullptr;    // capture stream (the caller's may be the legacy stream)
@@ -58,6 +61,7 @@ struct dgs_ctx {
     GraphKey gkey{};
     uint64_t cap_inst = 0, cap_pairs = 0; // capacities the captured sequence was sized for
     int gbits = 0;
+    uint64_t last_bound = 0;              // pair bound (summed tile rectangles) of the last eager call
     int64_t glaunches = 0;
     int32_t captures = 0;
     void* h_graph = nullptr;              // pinned: error word + live totals after a replay
@@ -421,7 +425,10 @@ int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* e
     const int64_t n_parts = (T + 4095) / 4096;
     if ((rc = ensure(ctx, ctx->parts, sizeof(ulonglong2) * (n_parts + 1)))) return rc;
     if ((rc = ensure(ctx, ctx->readback, sizeof(uint64_t) * 2 * (V + 1) + 64))) return rc;
-    if ((rc = ensure_host(ctx, ctx->h_read, ctx->h_read_bytes, sizeof(uint64_t) * 2 * (V + 1) + 64))) return rc;
+    // pinned: per-view totals, the error word, then the exact pairs of every view group (<= V)
+    if ((rc = ensure_host(ctx, ctx->h_read, ctx->h_read_bytes, sizeof(uint64_t) * 2 * (V + 1) + 64 + 4 * (V + 1))))
+        return rc;
+    if ((rc = ensure(ctx, ctx->totals, sizeof(uint32_t) * (V + 1)))) return rc;
     uint32_t* d_err = static_cast<uint32_t*>(ctx->errword.p);
 
     DGS_CUDA(ctx, cudaMemcpyAsync(dm, hm, upload_bytes, cudaMemcpyHostToDevice, stream));
@@ -481,6 +488,29 @@ void launch_front(dgs_ctx* ctx, const Batch& B, const Launch& L, Timer& tm) {
     tm.end();
 }
 
+// Workspace of the per-group lists: n_inst instances, n_pairs tile pairs, n_tiles tiles.
+int ensure_lists(dgs_ctx* ctx, uint64_t n_inst, uint64_t n_pairs, int64_t n_tiles) {
+    int rc;
+    n_inst = std::max<uint64_t>(n_inst, 1);
+    n_pairs = std::max<uint64_t>(n_pairs, 1);
+    if ((rc = ensure(ctx, ctx->records, sizeof(Record) * n_inst))) return rc;
+    if ((rc = ensure(ctx, ctx->info, sizeof(InstInfo) * n_inst))) return rc;
+    DevBuf* inst_bufs[] = {&ctx->dkey0, &ctx->ival0, &ctx->dkey1, &ctx->ival1, &ctx->ntile};
+    for (DevBuf* b : inst_bufs)
+        if ((rc = ensure(ctx, *b, sizeof(uint32_t) * n_inst))) return rc;
+    if ((rc = ensure(ctx, ctx->poff, sizeof(uint32_t) * (n_inst + 1)))) return rc;
+    if ((rc = ensure(ctx, ctx->tparts, sizeof(uint32_t) * tile_scan_parts((uint32_t)n_inst)))) return rc;
+    DevBuf* pair_bufs[] = {&ctx->tkeys0, &ctx->tvals0, &ctx->tkeys1, &ctx->tvals1};
+    for (DevBuf* b : pair_bufs)
+        if ((rc = ensure(ctx, *b, sizeof(uint32_t) * n_pairs))) return rc;
+    if ((rc = ensure(ctx, ctx->hist, sizeof(uint32_t) * 4 * 1024))) return rc;
+    if ((rc = ensure(ctx, ctx->counters, sizeof(uint32_t) * 8))) return rc;
+    const uint64_t most = std::max(n_inst, n_pairs);
+    if ((rc = ensure(ctx, ctx->status, sizeof(uint32_t) * sort_status_words((uint32_t)most)))) return rc;
+    if ((rc = ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)std::max<int64_t>(n_tiles, 1)))) return rc;
+    return DGS_OK;
+}
+
 // Per-view totals read back once (one stream synchronisation), view groups and workspace
 // sizing for the eager sequence.
 int readback_groups(dgs_ctx* ctx, Batch& B, cudaStream_t stream, Timer& tm) {
@@ -504,7 +534,7 @@ int readback_groups(dgs_ctx* ctx, Batch& B, cudaStream_t stream, Timer& tm) {
     uint32_t errw = (uint32_t)(h_rb[2 * (V + 1)] & 0xFFFFFFFFu);
     if (errw & kErrPose) return fail(ctx, DGS_ERR_INVALID_ARG, "a node pose is not finite or not rigid");
     ctx->stats.n_visible = (int64_t)inst_at[V];
-    ctx->stats.n_pairs = (int64_t)pair_at[V];
+    ctx->last_bound = pair_at[V];
     if (inst_at[V] >= (1ull << 32)) return fail(ctx, DGS_ERR_CAPACITY, "more than 2^32 visible instances");
 
     // ---------------------------------------------------------------- groups
@@ -536,20 +566,11 @@ int readback_groups(dgs_ctx* ctx, Batch& B, cudaStream_t stream, Timer& tm) {
         if (pair_at[g.second] - pair_at[g.first] > kMaxPairs)
             return fail(ctx, DGS_ERR_CAPACITY, "view group exceeds 2^30 tile pairs");
     }
-    max_bits = kZBits + std::max(1, bits_for((uint64_t)max_tiles));
-    if (max_bits > 64) return fail(ctx, DGS_ERR_CAPACITY, "sort key wider than 64 bits");
+    max_bits = bits_for((uint64_t)max_tiles + 1);
+    if (max_bits > 31) return fail(ctx, DGS_ERR_CAPACITY, "more than 2^31 tiles in a view group");
     ctx->stats.n_groups = (int32_t)groups.size();
     ctx->stats.key_bits = max_bits;
-    if ((rc = ensure(ctx, ctx->records, sizeof(Record) * max_inst))) return rc;
-    if ((rc = ensure(ctx, ctx->info, sizeof(InstInfo) * max_inst))) return rc;
-    if ((rc = ensure(ctx, ctx->keys0, sizeof(uint64_t) * max_pairs))) return rc;
-    if ((rc = ensure(ctx, ctx->keys1, sizeof(uint64_t) * max_pairs))) return rc;
-    if ((rc = ensure(ctx, ctx->vals0, sizeof(uint32_t) * max_pairs))) return rc;
-    if ((rc = ensure(ctx, ctx->vals1, sizeof(uint32_t) * max_pairs))) return rc;
-    if ((rc = ensure(ctx, ctx->hist, sizeof(uint32_t) * 256 * 8))) return rc;
-    if ((rc = ensure(ctx, ctx->counters, sizeof(uint32_t) * 8))) return rc;
-    if ((rc = ensure(ctx, ctx->status, sizeof(uint32_t) * sort_status_words((uint32_t)max_pairs)))) return rc;
-    if ((rc = ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)max_tiles))) return rc;
+    if ((rc = ensure_lists(ctx, max_inst, max_pairs, max_tiles))) return rc;
     B.groups = std::move(groups);
     B.inst_at = inst_at; B.pair_at = pair_at;
     return DGS_OK;
@@ -568,52 +589,79 @@ int prepare(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t*
     return readback_groups(ctx, B, stream, tm);
 }
 
-// Emit, sort and tile ranges of view group g.
+// The depth-ordered tile lists of views [v0, v1): emission (K2), depth sort of the instances,
+// pair offsets in depth order, pair emission, stable tile sort (K3) and tile ranges (K4).
+//   n_inst   instances of the group (host count; the capacity when d_inst is set)
+//   n_bound  bound on its pairs (host; the capacity the pair buffers hold)
+//   d_inst   device count of instances (graph replay) or null
+//   d_pairs  device word receiving the group's exact pair count (at most n_bound)
+// Returns the tile-sorted instance numbers in *vals.
+void enqueue_lists(dgs_ctx* ctx, const Batch& B, const Launch& L, Timer& tm, int v0, int v1, int n_tiles,
+                   uint32_t inst_base, uint32_t n_inst, uint32_t n_bound, const uint32_t* d_inst, uint32_t* d_pairs,
+                   const Params& P, const uint32_t** vals) {
+    const int K = B.K;
+    auto u32 = [](DevBuf& b) { return static_cast<uint32_t*>(b.p); };
+    Record* rec = static_cast<Record*>(ctx->records.p);
+    InstInfo* info = static_cast<InstInfo*>(ctx->info.p);
+    tm.begin(DGS_K_EMIT);
+    launch_emit(L, B.dtype_mask, B.d_nodes, B.n_nodes, B.d_views, B.d_vnodes, K, B.d_nv, B.d_nvoff, (int)B.chunk_total,
+                P, v0, v1, B.batched, B.d_pmap + (size_t)v0 * (2 * K + 1), B.view_tab[v0 + 1] - B.view_tab[v0],
+                B.d_counts, B.d_inst_off, inst_base, rec, info, u32(ctx->dkey0), u32(ctx->ival0), u32(ctx->ntile));
+    tm.end();
+    tm.begin(DGS_K_SORT);
+    uint32_t *dk = nullptr, *order = nullptr;
+    launch_sort(L, u32(ctx->dkey0), u32(ctx->ival0), u32(ctx->dkey1), u32(ctx->ival1), n_inst, kZBits, u32(ctx->hist),
+                u32(ctx->status), u32(ctx->counters), B.d_err, &dk, &order, d_inst);
+    launch_tile_scan(L, order, u32(ctx->ntile), n_inst, d_inst, u32(ctx->poff), u32(ctx->tparts), n_bound, d_pairs);
+    launch_pairs(L, B.d_views, K, order, u32(ctx->poff), rec, info, n_inst, d_inst, P, u32(ctx->tkeys0),
+                 u32(ctx->tvals0), n_bound);
+    uint32_t *tk = nullptr, *tv = nullptr;
+    launch_sort(L, u32(ctx->tkeys0), u32(ctx->tvals0), u32(ctx->tkeys1), u32(ctx->tvals1), n_bound,
+                bits_for((uint64_t)n_tiles + 1), u32(ctx->hist), u32(ctx->status), u32(ctx->counters), B.d_err, &tk,
+                &tv, d_pairs);
+    tm.end();
+    tm.begin(DGS_K_RANGES);
+    launch_ranges(L, tk, n_bound, static_cast<uint2*>(ctx->ranges.p), n_tiles, d_pairs);
+    tm.end();
+    *vals = tv;
+}
+
+// The lists of view group g (eager sequence, host-known sizes).
 struct GroupLists {
     int v0 = 0, v1 = 0, n_tiles = 0;
-    uint32_t n_pairs = 0, n_inst = 0;
-    uint32_t* vals = nullptr;
+    uint32_t n_bound = 0, n_inst = 0;
+    const uint32_t* vals = nullptr;
     Params P{};
 };
 
 void build_group_lists(dgs_ctx* ctx, const Batch& B, int g, cudaStream_t stream, Timer& tm, GroupLists& G) {
     Launch L{stream, &ctx->launches};
-    const int V = B.V, K = B.K;
+    const int V = B.V;
     const int v0 = B.groups[g].first, v1 = B.groups[g].second;
     G.v0 = v0; G.v1 = v1;
-    G.n_pairs = (uint32_t)(B.pair_at[v1] - B.pair_at[v0]);
+    G.n_bound = (uint32_t)(B.pair_at[v1] - B.pair_at[v0]);
     G.n_inst = (uint32_t)(B.inst_at[v1] - B.inst_at[v0]);
     const int32_t tile0 = B.views[v0].tile_base;
     G.n_tiles = (int)((v1 < V ? B.views[v1].tile_base : B.tiles_total) - tile0);
     G.P = B.P;
     G.P.tile0 = tile0;
-    tm.begin(DGS_K_EMIT);
-    launch_emit(L, B.dtype_mask, B.d_nodes, B.n_nodes, B.d_views, B.d_vnodes, K, B.d_nv, B.d_nvoff, (int)B.chunk_total,
-                G.P, v0, v1, B.batched, B.d_pmap + (size_t)v0 * (2 * K + 1), B.view_tab[v0 + 1] - B.view_tab[v0],
-                B.d_counts, B.d_inst_off, B.d_pair_off, (uint32_t)B.inst_at[v0], B.pair_at[v0],
-                static_cast<Record*>(ctx->records.p), static_cast<InstInfo*>(ctx->info.p),
-                static_cast<uint64_t*>(ctx->keys0.p), static_cast<uint32_t*>(ctx->vals0.p));
-    tm.end();
-    tm.begin(DGS_K_SORT);
-    uint64_t* skeys = nullptr;
-    const int bits = kZBits + std::max(1, bits_for((uint64_t)G.n_tiles));
-    launch_sort(L, static_cast<uint64_t*>(ctx->keys0.p), static_cast<uint32_t*>(ctx->vals0.p),
-                static_cast<uint64_t*>(ctx->keys1.p), static_cast<uint32_t*>(ctx->vals1.p), G.n_pairs, bits,
-                static_cast<uint32_t*>(ctx->hist.p), static_cast<uint32_t*>(ctx->status.p),
-                static_cast<uint32_t*>(ctx->counters.p), B.d_err, &skeys, &G.vals, nullptr, nullptr);
-    tm.end();
-    tm.begin(DGS_K_RANGES);
-    launch_ranges(L, skeys, G.n_pairs, static_cast<uint2*>(ctx->ranges.p), G.n_tiles);
-    tm.end();
+    enqueue_lists(ctx, B, L, tm, v0, v1, G.n_tiles, (uint32_t)B.inst_at[v0], G.n_inst, G.n_bound, nullptr,
+                  static_cast<uint32_t*>(ctx->totals.p) + g, G.P, &G.vals);
 }
 
 // Final synchronisation, device error word and kernel times.
 int finish(dgs_ctx* ctx, const Batch& B, cudaStream_t stream) {
     uint32_t* h_err = reinterpret_cast<uint32_t*>(static_cast<char*>(ctx->h_read) + sizeof(uint64_t) * 2 * (B.V + 1));
+    uint32_t* h_tot = reinterpret_cast<uint32_t*>(static_cast<char*>(ctx->h_read) + sizeof(uint64_t) * 2 * (B.V + 1) + 64);
+    const size_t ng = B.groups.size();
     DGS_CUDA(ctx, cudaGetLastError());
     DGS_CUDA(ctx, cudaMemcpyAsync(h_err, B.d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+    if (ng) DGS_CUDA(ctx, cudaMemcpyAsync(h_tot, ctx->totals.p, sizeof(uint32_t) * ng, cudaMemcpyDeviceToHost, stream));
     DGS_CUDA(ctx, cudaStreamSynchronize(stream));
     const uint32_t errw = *h_err;
+    int64_t pairs = 0;
+    for (size_t g = 0; g < ng; ++g) pairs += h_tot[g];
+    ctx->stats.n_pairs = pairs;
     if (ctx->opt.profile) {
         for (const TimedRange& r : ctx->ranges_timed) {
             float ms = 0.f;
@@ -622,6 +670,7 @@ int finish(dgs_ctx* ctx, const Batch& B, cudaStream_t stream) {
     }
     if (errw & kErrTimeout) return fail(ctx, DGS_ERR_TIMEOUT, "a bounded device wait timed out (sort look-back)");
     if (errw & kErrMismatch) return fail(ctx, DGS_ERR_CUDA, "internal: count and emit passes disagree");
+    if (errw & kErrCapacity) return fail(ctx, DGS_ERR_CUDA, "internal: tile pairs beyond their bound");
     if (errw & kErrPose) return fail(ctx, DGS_ERR_INVALID_ARG, "a node pose is not finite or not rigid");
     return DGS_OK;
 }
@@ -661,8 +710,9 @@ int run_eager(dgs_ctx* ctx, Batch& B, float* out_rgb, float* out_depth, float* o
 }
 
 // ------------------------------------------------------------------ graph replay
-// gsizes layout: u32 [0] live instances, [1] live pairs, [2] overflow flag; u64 at byte 16:
-// the totals the scan produced (valid even on overflow).
+// gsizes layout: u32 [0] live instances, [1] live pair bound, [2] overflow flag, [3] exact
+// pairs (written by the tile-count scan); u64 at byte 16: the instance and pair-bound totals
+// the scan produced (valid even on overflow).
 __global__ void k_graph_sizes(const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off, int64_t T,
                               uint64_t cap_inst, uint64_t cap_pairs, uint32_t* sizes, uint32_t* err) {
     const uint64_t ni = inst_off[T], np = pair_off[T];
@@ -673,6 +723,7 @@ __global__ void k_graph_sizes(const uint32_t* __restrict__ inst_off, const uint6
     sizes[0] = over ? 0u : (uint32_t)ni;
     sizes[1] = over ? 0u : (uint32_t)np;
     sizes[2] = over ? 1u : 0u;
+    sizes[3] = 0u;
     if (over) atomicOr(err, kErrCapacity);
 }
 
@@ -708,45 +759,27 @@ void enqueue_graph_body(dgs_ctx* ctx, const Batch& B, const Launch& L, float* ou
     ++*L.launches;
     Params P = B.P;
     P.gate = sizes + 2;
-    launch_emit(L, B.dtype_mask, B.d_nodes, B.n_nodes, B.d_views, B.d_vnodes, B.K, B.d_nv, B.d_nvoff,
-                (int)B.chunk_total, P, 0, B.V, true, B.d_pmap, B.view_tab[1] - B.view_tab[0], B.d_counts,
-                B.d_inst_off, B.d_pair_off, 0u, 0ull, static_cast<Record*>(ctx->records.p),
-                static_cast<InstInfo*>(ctx->info.p), static_cast<uint64_t*>(ctx->keys0.p),
-                static_cast<uint32_t*>(ctx->vals0.p));
-    uint64_t* skeys = nullptr;
-    uint32_t* svals = nullptr;
-    launch_sort(L, static_cast<uint64_t*>(ctx->keys0.p), static_cast<uint32_t*>(ctx->vals0.p),
-                static_cast<uint64_t*>(ctx->keys1.p), static_cast<uint32_t*>(ctx->vals1.p), (uint32_t)ctx->cap_pairs,
-                ctx->gbits, static_cast<uint32_t*>(ctx->hist.p), static_cast<uint32_t*>(ctx->status.p),
-                static_cast<uint32_t*>(ctx->counters.p), B.d_err, &skeys, &svals, nullptr, nullptr, sizes + 1);
-    launch_ranges(L, skeys, (uint32_t)ctx->cap_pairs, static_cast<uint2*>(ctx->ranges.p), (int)B.tiles_total,
-                  sizes + 1);
-    launch_composite(L, B.d_views, 0, B.V, (int)B.tiles_total, static_cast<uint2*>(ctx->ranges.p), svals,
+    Timer off2{ctx, L.stream, false};
+    const uint32_t* vals = nullptr;
+    enqueue_lists(ctx, B, L, off2, 0, B.V, (int)B.tiles_total, 0u, (uint32_t)ctx->cap_inst, (uint32_t)ctx->cap_pairs,
+                  sizes + 0, sizes + 3, P, &vals);
+    launch_composite(L, B.d_views, 0, B.V, (int)B.tiles_total, static_cast<uint2*>(ctx->ranges.p), vals,
                      static_cast<Record*>(ctx->records.p), P, out_rgb, out_depth, out_alpha, nullptr);
 }
 
-// Sizes the capacities from the totals of the render just done (need_inst, need_pairs) with
-// 25 % headroom, and captures the sequence.  Returns DGS_OK without a graph when the batch
-// cannot run as one view group (more than 2^30 pairs or a key wider than 64 bits).
+// Sizes the capacities from the totals of the render just done (instances and pair bound)
+// with 25 % headroom, and captures the sequence.  Returns DGS_OK without a graph when the
+// batch cannot run as one view group (a pair bound above 2^30 or more than 2^31 tiles).
 int capture_graph(dgs_ctx* ctx, const Batch& B, uint64_t need_inst, uint64_t need_pairs, float* out_rgb,
                   float* out_depth, float* out_alpha) {
     drop_graph(ctx);
-    const int bits = kZBits + std::max(1, bits_for((uint64_t)std::max<int64_t>(B.tiles_total, 1)));
-    if (need_pairs > kMaxPairs || bits > 64 || need_inst >= (1ull << 31)) return DGS_OK;
+    const int bits = bits_for((uint64_t)std::max<int64_t>(B.tiles_total, 1) + 1);
+    if (need_pairs > kMaxPairs || bits > 31 || need_inst >= (1ull << 31)) return DGS_OK;
     ctx->cap_inst = std::max(ctx->cap_inst, need_inst + need_inst / 4 + 1024);
     ctx->cap_pairs = std::min<uint64_t>(kMaxPairs, std::max(ctx->cap_pairs, need_pairs + need_pairs / 4 + 4096));
     ctx->gbits = bits;
     int rc;
-    if ((rc = ensure(ctx, ctx->records, sizeof(Record) * ctx->cap_inst))) return rc;
-    if ((rc = ensure(ctx, ctx->info, sizeof(InstInfo) * ctx->cap_inst))) return rc;
-    if ((rc = ensure(ctx, ctx->keys0, sizeof(uint64_t) * ctx->cap_pairs))) return rc;
-    if ((rc = ensure(ctx, ctx->keys1, sizeof(uint64_t) * ctx->cap_pairs))) return rc;
-    if ((rc = ensure(ctx, ctx->vals0, sizeof(uint32_t) * ctx->cap_pairs))) return rc;
-    if ((rc = ensure(ctx, ctx->vals1, sizeof(uint32_t) * ctx->cap_pairs))) return rc;
-    if ((rc = ensure(ctx, ctx->hist, sizeof(uint32_t) * 256 * 8))) return rc;
-    if ((rc = ensure(ctx, ctx->counters, sizeof(uint32_t) * 8))) return rc;
-    if ((rc = ensure(ctx, ctx->status, sizeof(uint32_t) * sort_status_words((uint32_t)ctx->cap_pairs)))) return rc;
-    if ((rc = ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)std::max<int64_t>(B.tiles_total, 1)))) return rc;
+    if ((rc = ensure_lists(ctx, ctx->cap_inst, ctx->cap_pairs, B.tiles_total))) return rc;
     if ((rc = ensure(ctx, ctx->gsizes, 64))) return rc;
     if (!ctx->h_graph) DGS_CUDA(ctx, cudaHostAlloc(&ctx->h_graph, 64, cudaHostAllocDefault));
     if (!ctx->cap_stream) DGS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
@@ -795,26 +828,27 @@ int render_graph(dgs_ctx* ctx, Batch& B, float* out_rgb, float* out_depth, float
         ctx->launches = ctx->glaunches;
         char* hg = static_cast<char*>(ctx->h_graph);
         DGS_CUDA(ctx, cudaMemcpyAsync(hg, B.d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
-        DGS_CUDA(ctx, cudaMemcpyAsync(hg + 16, static_cast<char*>(ctx->gsizes.p) + 16, 16, cudaMemcpyDeviceToHost,
-                                      stream));
+        DGS_CUDA(ctx, cudaMemcpyAsync(hg + 4, ctx->gsizes.p, 32, cudaMemcpyDeviceToHost, stream));
         DGS_CUDA(ctx, cudaStreamSynchronize(stream));
-        uint32_t errw;
+        uint32_t errw, sizes[4];
         uint64_t raw[2];
         std::memcpy(&errw, hg, 4);
-        std::memcpy(raw, hg + 16, 16);
+        std::memcpy(sizes, hg + 4, 16);
+        std::memcpy(raw, hg + 20, 16);
         if (ctx->opt.profile)
             for (const TimedRange& r : ctx->ranges_timed) {
                 float ms = 0.f;
                 if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) ctx->ktimes[r.cls] += ms;
             }
         ctx->stats.n_visible = (int64_t)raw[0];
-        ctx->stats.n_pairs = (int64_t)raw[1];
+        ctx->stats.n_pairs = (int64_t)sizes[3];
         ctx->stats.n_groups = 1;
         ctx->stats.key_bits = ctx->gbits;
         if (errw & kErrPose) return fail(ctx, DGS_ERR_INVALID_ARG, "a node pose is not finite or not rigid");
         if (errw & kErrTimeout) return fail(ctx, DGS_ERR_TIMEOUT, "a bounded device wait timed out (sort look-back)");
         if (errw & kErrMismatch) return fail(ctx, DGS_ERR_CUDA, "internal: count and emit passes disagree");
-        if (!(errw & kErrCapacity)) {
+        if (!(errw & kErrCapacity) || !sizes[2]) {
+            if (errw & kErrCapacity) return fail(ctx, DGS_ERR_CUDA, "internal: tile pairs beyond their bound");
             ctx->stats.path = DGS_PATH_GRAPH;
             ctx->stats.graph_captures = ctx->captures;
             return DGS_OK;
@@ -829,8 +863,7 @@ int render_graph(dgs_ctx* ctx, Batch& B, float* out_rgb, float* out_depth, float
         return DGS_OK;
     }
     if ((rc = run_eager(ctx, B, out_rgb, out_depth, out_alpha, stream, tm))) return rc;
-    if ((rc = capture_graph(ctx, B, (uint64_t)ctx->stats.n_visible, (uint64_t)ctx->stats.n_pairs, out_rgb, out_depth,
-                            out_alpha)))
+    if ((rc = capture_graph(ctx, B, (uint64_t)ctx->stats.n_visible, ctx->last_bound, out_rgb, out_depth, out_alpha)))
         return rc;
     ctx->stats.path = ctx->gexec ? DGS_PATH_CAPTURED : DGS_PATH_EAGER;
     return DGS_OK;
@@ -884,8 +917,9 @@ int dgs_context_destroy(dgs_ctx* ctx) {
     if (!ctx) return DGS_OK;
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->records, &ctx->info,
-                      &ctx->keys0, &ctx->vals0, &ctx->keys1, &ctx->vals1, &ctx->hist, &ctx->status, &ctx->counters,
-                      &ctx->ranges, &ctx->errword, &ctx->readback, &ctx->inst_grad, &ctx->gsizes};
+                      &ctx->dkey0, &ctx->ival0, &ctx->dkey1, &ctx->ival1, &ctx->ntile, &ctx->poff, &ctx->tparts,
+                      &ctx->tkeys0, &ctx->tvals0, &ctx->tkeys1, &ctx->tvals1, &ctx->hist, &ctx->status, &ctx->counters,
+                      &ctx->ranges, &ctx->errword, &ctx->readback, &ctx->inst_grad, &ctx->gsizes, &ctx->totals};
     for (DevBuf* b : bufs) free_buf(*b);
     drop_graph(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -902,9 +936,10 @@ const char* dgs_last_error(const dgs_ctx* ctx) { return ctx ? ctx->err.c_str() :
 int dgs_workspace_query(const dgs_ctx* ctx, size_t* bytes) {
     if (!ctx || !bytes) return DGS_ERR_INVALID_ARG;
     const DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->records,
-                            &ctx->info, &ctx->keys0, &ctx->vals0, &ctx->keys1, &ctx->vals1, &ctx->hist, &ctx->status,
-                            &ctx->counters, &ctx->ranges, &ctx->errword, &ctx->readback, &ctx->inst_grad,
-                            &ctx->gsizes};
+                            &ctx->info, &ctx->dkey0, &ctx->ival0, &ctx->dkey1, &ctx->ival1, &ctx->ntile,
+                            &ctx->poff, &ctx->tparts, &ctx->tkeys0, &ctx->tvals0, &ctx->tkeys1, &ctx->tvals1,
+                            &ctx->hist, &ctx->status, &ctx->counters, &ctx->ranges, &ctx->errword, &ctx->readback,
+                            &ctx->inst_grad, &ctx->gsizes, &ctx->totals};
     size_t s = 0;
     for (const DevBuf* b : bufs) s += b->bytes;
     *bytes = s;

@@ -1,0 +1,231 @@
+// Depth-ordered (tile, instance) pairs: tile-count scan (K3b) and pair emission (K3c).
+//
+// Sec. III-A: after projection every screen tile must receive the Gaussians that reach it in
+// front-to-back order.  The projected instances are first sorted by depth key; here each
+// instance's tile pairs are laid out in that order (an exclusive scan of the instances' pair
+// counts taken in sorted order) and written by walking the instance's tile rectangle with the
+// same exact test that counted them.  A stable sort by tile then leaves every tile's run in
+// depth order, equal depths in emission (id) order.
+#include "dgs_internal.cuh"
+
+namespace dgs {
+namespace {
+
+constexpr int kScanThreads = 256, kScanItems = 16, kScanTile = kScanThreads * kScanItems;
+constexpr int kPairWarps = 4;
+
+__device__ __forceinline__ uint32_t live(uint32_t n, const uint32_t* d_n) { return d_n ? min(n, *d_n) : n; }
+
+__device__ __forceinline__ uint32_t block_sum(uint32_t x) {
+    __shared__ uint32_t s[kScanThreads / 32];
+    x = __reduce_add_sync(0xffffffffu, x);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = x;
+    __syncthreads();
+    uint32_t t = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) t += s[w];
+    return t;
+}
+
+// parts[b] = sum of ntile[order[i]] over partition b
+__global__ void __launch_bounds__(kScanThreads) k_tscan_partial(const uint32_t* __restrict__ order,
+                                                               const uint32_t* __restrict__ ntile, uint32_t n,
+                                                               const uint32_t* __restrict__ d_n, uint32_t* parts) {
+    n = live(n, d_n);
+    const uint32_t base = blockIdx.x * (uint32_t)kScanTile;
+    if (base >= n) return;
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const uint32_t i = base + j * kScanThreads + threadIdx.x;
+        if (i < n) s += ntile[order[i]];
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0) parts[blockIdx.x] = s;
+}
+
+// one block: exclusive scan of the live partitions' sums in place; poff[n] = the grand total
+// and *total = min(grand total, cap)
+__global__ void __launch_bounds__(kScanThreads) k_tscan_parts(uint32_t* parts, uint32_t n, const uint32_t* __restrict__ d_n,
+                                                              uint32_t* poff, uint32_t cap, uint32_t* total) {
+    __shared__ uint32_t s_w[kScanThreads / 32];
+    n = live(n, d_n);
+    const uint32_t np = (n + kScanTile - 1) / kScanTile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t carry = 0;
+    for (uint32_t b0 = 0; b0 < np; b0 += kScanThreads) {
+        const uint32_t i = b0 + threadIdx.x;
+        const uint32_t x = i < np ? parts[i] : 0u;
+        uint32_t y = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += t;
+        }
+        if (lane == 31) s_w[warp] = y;
+        __syncthreads();
+        uint32_t wpre = 0, all = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) {
+            if (w < warp) wpre += s_w[w];
+            all += s_w[w];
+        }
+        if (i < np) parts[i] = carry + wpre + y - x;
+        carry += all;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        poff[n] = carry;
+        *total = min(carry, cap);
+    }
+}
+
+// poff[i] for i < n: thread t of block b scans 16 consecutive entries
+__global__ void __launch_bounds__(kScanThreads) k_tscan_final(const uint32_t* __restrict__ order,
+                                                             const uint32_t* __restrict__ ntile, uint32_t n,
+                                                             const uint32_t* __restrict__ d_n,
+                                                             const uint32_t* __restrict__ parts, uint32_t* poff) {
+    __shared__ uint32_t s_w[kScanThreads / 32];
+    n = live(n, d_n);
+    const uint32_t base = blockIdx.x * (uint32_t)kScanTile;
+    if (base >= n) return;
+    const uint32_t i0 = base + threadIdx.x * kScanItems;
+    uint32_t v[kScanItems], sum = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        v[j] = i0 + j < n ? ntile[order[i0 + j]] : 0u;
+        sum += v[j];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t y = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += t;
+    }
+    if (lane == 31) s_w[warp] = y;
+    __syncthreads();
+    uint32_t run = parts[blockIdx.x] + y - sum;
+    for (int w = 0; w < warp; ++w) run += s_w[w];
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (i0 + j < n) poff[i0 + j] = run;
+        run += v[j];
+    }
+}
+
+// Per-warp state of the pair walk: lane l holds depth-ordered instance i0 + l.
+struct PairWarp {
+    float u[32], v[32], qa[32], qb[32], qc[32];
+    int32_t tx0[32], ty0[32], tw[32], x0[32], x1[32], y0[32], y1[32], tbase[32], tiles_x[32];
+    uint32_t excl[32], off[32], end[32], run[32], rec[32];
+};
+
+__global__ void __launch_bounds__(kPairWarps * 32) k_pairs(const ViewDesc* __restrict__ views, int K,
+                                                          const uint32_t* __restrict__ order,
+                                                          const uint32_t* __restrict__ poff,
+                                                          const Record* __restrict__ rec,
+                                                          const InstInfo* __restrict__ info, uint32_t n,
+                                                          const uint32_t* __restrict__ d_n, Params P,
+                                                          uint32_t* __restrict__ tkeys, uint32_t* __restrict__ tvals,
+                                                          uint32_t cap) {
+    __shared__ PairWarp pw[kPairWarps];
+    n = live(n, d_n);
+    const uint32_t w = (blockIdx.x * (uint32_t)blockDim.x + threadIdx.x) >> 5;
+    if (w * 32u >= n) return;
+    const int lane = (int)lane_id();
+    PairWarp& S = pw[threadIdx.x >> 5];
+    const uint32_t item = w * 32u + (uint32_t)lane;
+    const bool act = item < n;
+    uint32_t area = 0;
+    if (act) {
+        const uint32_t r = order[item];
+        const Record& R = rec[r];
+        const float4 r0 = R.r0, r1 = R.r1;
+        const uint32_t bx = __float_as_uint(r1.w), by = __float_as_uint(R.r2.w);
+        const int x0 = (int)(bx & 0xFFFFu), x1 = (int)(bx >> 16), y0 = (int)(by & 0xFFFFu), y1 = (int)(by >> 16);
+        const int tx0 = x0 / P.tile_w, tx1 = x1 / P.tile_w, ty0 = y0 / P.tile_h, ty1 = y1 / P.tile_h;
+        const ViewDesc& vd = views[info[r].view / (uint32_t)K];
+        S.u[lane] = r0.x; S.v[lane] = r0.y; S.qa[lane] = r1.x; S.qb[lane] = r1.y; S.qc[lane] = r1.z;
+        S.x0[lane] = x0; S.x1[lane] = x1; S.y0[lane] = y0; S.y1[lane] = y1;
+        S.tx0[lane] = tx0; S.ty0[lane] = ty0; S.tw[lane] = tx1 - tx0 + 1;
+        S.tbase[lane] = vd.tile_base - P.tile0; S.tiles_x[lane] = vd.tiles_x;
+        S.off[lane] = poff[item]; S.end[lane] = poff[item + 1]; S.run[lane] = 0; S.rec[lane] = r;
+        area = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+    }
+    uint32_t excl = area;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, excl, o);
+        if (lane >= o) excl += t;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, excl, 31);
+    S.excl[lane] = excl - area;
+    __syncwarp();
+    const uint32_t lt = (1u << lane) - 1u;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t f = base + (uint32_t)lane;
+        bool hit = false;
+        int o = -1, tx = 0, ty = 0;
+        if (f < total) {
+            int lo = 0, hi = 31;
+#pragma unroll
+            for (int it = 0; it < 5; ++it) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (S.excl[mid] <= f) lo = mid; else hi = mid - 1;
+            }
+            o = lo;
+            const uint32_t r = f - S.excl[o];
+            const uint32_t wd = (uint32_t)S.tw[o];
+            const uint32_t row = r / wd;
+            tx = S.tx0[o] + (int)(r - row * wd);
+            ty = S.ty0[o] + (int)row;
+            hit = tile_hit(S.u[o], S.v[o], S.qa[o], S.qb[o], S.qc[o], S.x0[o], S.x1[o], S.y0[o], S.y1[o], tx, ty,
+                           P.tile_w, P.tile_h, P.qbin, P.exact_tile_test);
+        }
+        const uint32_t peers = __match_any_sync(0xffffffffu, hit ? o : -1);
+        if (hit) {
+            const uint32_t pos = S.off[o] + S.run[o] + __popc(peers & lt);
+            if (pos < S.end[o] && pos < cap) {
+                tkeys[pos] = (uint32_t)(S.tbase[o] + ty * S.tiles_x[o] + tx);
+                tvals[pos] = S.rec[o];
+            } else {
+                atomicOr(P.err, pos < cap ? kErrMismatch : kErrCapacity);
+            }
+        }
+        __syncwarp();
+        if (hit && (peers & lt) == 0) S.run[o] += __popc(peers);
+        __syncwarp();
+    }
+    // the emission count and this walk take the same decisions; pad a shortfall with dead keys
+    if (act) {
+        const uint32_t have = S.off[lane] + S.run[lane];
+        if (have != S.end[lane]) {
+            atomicOr(P.err, kErrMismatch);
+            for (uint32_t q = have; q < S.end[lane] && q < cap; ++q) { tkeys[q] = ~0u; tvals[q] = 0; }
+        }
+    }
+}
+
+}  // namespace
+
+size_t tile_scan_parts(uint32_t n) { return ((size_t)n + kScanTile - 1) / kScanTile + 1; }
+
+void launch_tile_scan(const Launch& L, const uint32_t* order, const uint32_t* ntile, uint32_t n, const uint32_t* d_n,
+                      uint32_t* poff, uint32_t* parts, uint32_t cap, uint32_t* total) {
+    const uint32_t blocks = (n + kScanTile - 1) / kScanTile;
+    if (blocks) k_tscan_partial<<<blocks, kScanThreads, 0, L.stream>>>(order, ntile, n, d_n, parts);
+    k_tscan_parts<<<1, kScanThreads, 0, L.stream>>>(parts, n, d_n, poff, cap, total);
+    if (blocks) k_tscan_final<<<blocks, kScanThreads, 0, L.stream>>>(order, ntile, n, d_n, parts, poff);
+    *L.launches += blocks ? 3 : 1;
+}
+
+void launch_pairs(const Launch& L, const ViewDesc* views, int K, const uint32_t* order, const uint32_t* poff,
+                  const Record* records, const InstInfo* info, uint32_t n, const uint32_t* d_n, const Params& P,
+                  uint32_t* tkeys, uint32_t* tvals, uint32_t cap) {
+    if (n == 0) return;
+    const uint32_t warps = (n + 31) / 32;
+    const uint32_t blocks = (warps + kPairWarps - 1) / kPairWarps;
+    k_pairs<<<blocks, kPairWarps * 32, 0, L.stream>>>(views, K, order, poff, records, info, n, d_n, P, tkeys, tvals, cap);
+    ++*L.launches;
+}
+
+}  // namespace dgs

@@ -12,39 +12,15 @@
 namespace dgs {
 namespace {
 
-__global__ void k_ranges(const uint64_t* __restrict__ keys, uint32_t n, const uint32_t* __restrict__ d_n,
+__global__ void k_ranges(const uint32_t* __restrict__ keys, uint32_t n, const uint32_t* __restrict__ d_n,
                          uint2* __restrict__ ranges, int n_tiles) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (d_n) n = min(n, *d_n);
     if (i >= n) return;
-    const uint64_t t = keys[i] >> kZBits;
-    if (t >= (uint64_t)n_tiles) return;   // dead pairs sort past every real tile
-    if (i == 0 || (keys[i - 1] >> kZBits) != t) ranges[t].x = i;
-    if (i + 1 == n || (keys[i + 1] >> kZBits) != t) ranges[t].y = i + 1;
-}
-
-// Does the ellipse {q <= qlim}, q = qa (dx + qb dy)^2 + qc dy^2, reach the rectangle of pixel
-// centres [X0, X1] x [Y0, Y1] (relative to the mean)?  Minimum of q over the rectangle: 0 if
-// the mean is inside; else the least of the edge minima -- on a horizontal edge dy = Y the
-// minimiser is dx = -qb Y, on a vertical edge dx = X it is dy = -qa qb X / (qa qb^2 + qc) --
-// each clamped to its edge.
-__device__ __forceinline__ bool ellipse_meets(float qa, float qb, float qc, float qlim, float X0, float X1, float Y0,
-                                              float Y1) {
-    if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return true;
-    const float k = -qa * qb / fmaf(qa * qb, qb, qc);
-    float m = INFINITY;
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const float Y = e ? Y1 : Y0;
-        const float X = fminf(X1, fmaxf(X0, -qb * Y));
-        const float t = fmaf(qb, Y, X);
-        m = fminf(m, fmaf(qa * t, t, qc * Y * Y));
-        const float Xv = e ? X1 : X0;
-        const float Yv = fminf(Y1, fmaxf(Y0, k * Xv));
-        const float tv = fmaf(qb, Yv, Xv);
-        m = fminf(m, fmaf(qa * tv, tv, qc * Yv * Yv));
-    }
-    return m <= qlim;
+    const uint32_t t = keys[i];
+    if (t >= (uint32_t)n_tiles) return;   // dead pairs sort past every real tile
+    if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
+    if (i + 1 == n || keys[i + 1] != t) ranges[t].y = i + 1;
 }
 
 // Block = one tile, warp = one 8x4 sub-tile, lane = one pixel.  Warps are independent (no
@@ -148,7 +124,7 @@ __global__ void __launch_bounds__(256) k_composite(const ViewDesc* __restrict__ 
 
 }  // namespace
 
-void launch_ranges(const Launch& L, const uint64_t* keys, uint32_t n, uint2* ranges, int n_tiles,
+void launch_ranges(const Launch& L, const uint32_t* keys, uint32_t n, uint2* ranges, int n_tiles,
                    const uint32_t* d_n) {
     cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, L.stream);
     if (n == 0) return;

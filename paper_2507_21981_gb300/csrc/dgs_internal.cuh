@@ -96,6 +96,43 @@ __device__ __forceinline__ float ld_attr(const void* p, int64_t i) {
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
+// Does the ellipse {q <= qlim}, q = qa (dx + qb dy)^2 + qc dy^2, reach the rectangle of pixel
+// centres [X0, X1] x [Y0, Y1] (relative to the mean)?  Minimum of q over the rectangle: 0 if
+// the mean is inside; else the least of the edge minima -- on a horizontal edge dy = Y the
+// minimiser is dx = -qb Y, on a vertical edge dx = X it is dy = -qa qb X / (qa qb^2 + qc) --
+// each clamped to its edge.
+__device__ __forceinline__ bool ellipse_meets(float qa, float qb, float qc, float qlim, float X0, float X1, float Y0,
+                                              float Y1) {
+    if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return true;
+    const float k = -qa * qb / fmaf(qa * qb, qb, qc);
+    float m = INFINITY;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float Y = e ? Y1 : Y0;
+        const float X = fminf(X1, fmaxf(X0, -qb * Y));
+        const float t = fmaf(qb, Y, X);
+        m = fminf(m, fmaf(qa * t, t, qc * Y * Y));
+        const float Xv = e ? X1 : X0;
+        const float Yv = fminf(Y1, fmaxf(Y0, k * Xv));
+        const float tv = fmaf(qb, Yv, Xv);
+        m = fminf(m, fmaf(qa * tv, tv, qc * Yv * Yv));
+    }
+    return m <= qlim;
+}
+
+// Binning decision for tile (tx, ty) of an instance with centre (u, v), factored form
+// (qa, qb, qc) and ellipse pixel box [x0, x1] x [y0, y1]: the tile's part of the box holds a
+// pixel centre of the ellipse {q <= qbin}.  Emission counts and pair writing both call this
+// on the same stored record values, so they agree exactly.
+__device__ __forceinline__ bool tile_hit(float u, float v, float qa, float qb, float qc, int x0, int x1, int y0, int y1,
+                                         int tx, int ty, int tile_w, int tile_h, float qbin, int exact) {
+    if (!exact) return true;
+    const int px0 = max(tx * tile_w, x0), px1 = min(tx * tile_w + tile_w - 1, x1);
+    const int py0 = max(ty * tile_h, y0), py1 = min(ty * tile_h + tile_h - 1, y1);
+    return ellipse_meets(qa, qb, qc, qbin, (float)px0 + 0.5f - u, (float)px1 + 0.5f - u, (float)py0 + 0.5f - v,
+                         (float)py1 + 0.5f - v);
+}
+
 __device__ __forceinline__ uint64_t global_timer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -120,24 +157,41 @@ void launch_count(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_
 void launch_scan(const Launch& L, const uint2* counts, int64_t n, uint32_t* inst_off, uint64_t* pair_off,
                  ulonglong2* parts, int64_t n_parts_cap);
 
+// K2: for every visible instance of views [v0, v1): its record, identity, depth key
+// (bits(z32) - zbase saturated to 28 bits), its own index (the value the depth sort carries)
+// and its number of tile pairs, at the scanned instance offsets minus inst_base.
 void launch_emit(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_nodes, const ViewDesc* views,
                  const VNode* vnodes, int K, const NodeView* node_views, const int32_t* node_view_off,
                  int n_chunks_total, const Params& P, int v0, int v1, bool batched, const int32_t* view_chunk_nodes,
-                 int64_t view_chunks, const uint2* counts, const uint32_t* inst_off, const uint64_t* pair_off,
-                 uint32_t inst_base,
-                 uint64_t pair_base, Record* records, InstInfo* info, uint64_t* keys, uint32_t* vals);
+                 int64_t view_chunks, const uint2* counts, const uint32_t* inst_off, uint32_t inst_base,
+                 Record* records, InstInfo* info, uint32_t* dkey, uint32_t* ival, uint32_t* ntile);
 
-// launch_sort / launch_ranges: with d_n non-null the number of pairs is read on the device as
-// min(*d_n, n), and n is the capacity the launches are sized for (graph replay).
-void launch_sort(const Launch& L, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+// Stable LSD radix sort of (key, value) on the low key_bits bits.  With d_n non-null the
+// number of pairs is read on the device as min(*d_n, n), and n is the capacity the launches
+// are sized for.  *keys_out / *vals_out receive the buffers holding the result.
+void launch_sort(const Launch& L, uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                  uint32_t n, int key_bits, uint32_t* hist, uint32_t* status, uint32_t* counters, uint32_t* err,
-                 uint64_t** keys_out, uint32_t** vals_out, float* sort_ms_slot, cudaEvent_t* evs,
-                 const uint32_t* d_n = nullptr);
+                 uint32_t** keys_out, uint32_t** vals_out, const uint32_t* d_n = nullptr);
 
 // Sets the sort kernels' launch attributes; call before a stream capture that contains a sort.
 void sort_prepare();
 
-void launch_ranges(const Launch& L, const uint64_t* keys, uint32_t n, uint2* ranges, int n_tiles,
+// K3b: pair offsets in depth order, poff[i] = sum_{j<i} ntile[order[j]] for i <= n (n =
+// min(*d_n, n) if d_n), and *total = min(poff[n], cap).  parts: scratch of
+// tile_scan_parts(n) words.
+void launch_tile_scan(const Launch& L, const uint32_t* order, const uint32_t* ntile, uint32_t n, const uint32_t* d_n,
+                      uint32_t* poff, uint32_t* parts, uint32_t cap, uint32_t* total);
+size_t tile_scan_parts(uint32_t n);
+
+// K3c: the (tile, instance) pairs of the depth-ordered instances, instance by instance in
+// that order and each instance's tiles in row-major order: keys = tile within the group,
+// values = instance index.  Pairs at or beyond cap are not written (kErrCapacity).
+void launch_pairs(const Launch& L, const ViewDesc* views, int K, const uint32_t* order, const uint32_t* poff,
+                  const Record* records, const InstInfo* info, uint32_t n, const uint32_t* d_n, const Params& P,
+                  uint32_t* tkeys, uint32_t* tvals, uint32_t cap);
+
+// K4: [start, end) of every tile's run in the tile-sorted keys (d_n: device pair count).
+void launch_ranges(const Launch& L, const uint32_t* keys, uint32_t n, uint2* ranges, int n_tiles,
                    const uint32_t* d_n = nullptr);
 
 void launch_composite(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,

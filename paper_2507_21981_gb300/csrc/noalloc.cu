@@ -242,34 +242,45 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
     if (n_pairs > kMaxPairs) return DGS_ERR_CAPACITY;
 
     // ---------------------------------------------------------------- phase 2 scratch
-    Record* d_rec = cv.take<Record>(n_vis);
-    InstInfo* d_info = cv.take<InstInfo>(n_vis);
-    uint64_t* d_k0 = cv.take<uint64_t>(n_pairs);
-    uint64_t* d_k1 = cv.take<uint64_t>(n_pairs);
-    uint32_t* d_v0 = cv.take<uint32_t>(n_pairs);
-    uint32_t* d_v1 = cv.take<uint32_t>(n_pairs);
-    uint32_t* d_hist = cv.take<uint32_t>(256 * 8);
+    const uint64_t ni = std::max<uint64_t>(n_vis, 1), np = std::max<uint64_t>(n_pairs, 1);
+    Record* d_rec = cv.take<Record>(ni);
+    InstInfo* d_info = cv.take<InstInfo>(ni);
+    uint32_t* d_dk0 = cv.take<uint32_t>(ni);
+    uint32_t* d_iv0 = cv.take<uint32_t>(ni);
+    uint32_t* d_dk1 = cv.take<uint32_t>(ni);
+    uint32_t* d_iv1 = cv.take<uint32_t>(ni);
+    uint32_t* d_ntile = cv.take<uint32_t>(ni);
+    uint32_t* d_poff = cv.take<uint32_t>(ni + 1);
+    uint32_t* d_tparts = cv.take<uint32_t>(tile_scan_parts((uint32_t)ni));
+    uint32_t* d_k0 = cv.take<uint32_t>(np);
+    uint32_t* d_v0 = cv.take<uint32_t>(np);
+    uint32_t* d_k1 = cv.take<uint32_t>(np);
+    uint32_t* d_v1 = cv.take<uint32_t>(np);
+    uint32_t* d_hist = cv.take<uint32_t>(4 * 1024);
     uint32_t* d_cnt = cv.take<uint32_t>(8);
-    uint32_t* d_status = cv.take<uint32_t>(sort_status_words((uint32_t)std::max<uint64_t>(n_pairs, 1)));
+    uint32_t* d_total = cv.take<uint32_t>(1);
+    uint32_t* d_status = cv.take<uint32_t>(sort_status_words((uint32_t)std::max(ni, np)));
     uint2* d_ranges = cv.take<uint2>((size_t)tiles_total);
     if (!cv.ok) return DGS_ERR_CAPACITY;
+    const int tbits = bits_for_tiles((uint64_t)tiles_total + 1);
+    if (tbits > 31) return DGS_ERR_CAPACITY;
+    // depth-ordered tile lists, as in dgs_render with one view group
     launch_emit(L, dtype_mask, d_nodes, n_nodes, d_views, d_vnodes, K, d_nv, d_nvoff, (int)chunk_total, P, 0, V, true,
-                nullptr, 0, d_counts, d_inst_off, d_pair_off, 0u, 0ull, d_rec, d_info, d_k0, d_v0);
-    uint64_t* skeys;
-    uint32_t* svals;
-    const int bits = kZBits + std::max(1, bits_for_tiles((uint64_t)tiles_total));
-    if (bits > 64) return DGS_ERR_CAPACITY;
-    launch_sort(L, d_k0, d_v0, d_k1, d_v1, (uint32_t)n_pairs, bits, d_hist, d_status, d_cnt, d_err, &skeys, &svals,
-                nullptr, nullptr);
-    launch_ranges(L, skeys, (uint32_t)n_pairs, d_ranges, (int)tiles_total);
-    launch_composite(L, d_views, 0, V, (int)tiles_total, d_ranges, svals, d_rec, P, out_rgb, out_depth, out_alpha,
+                nullptr, 0, d_counts, d_inst_off, 0u, d_rec, d_info, d_dk0, d_iv0, d_ntile);
+    uint32_t *dk, *order, *tk, *tv;
+    launch_sort(L, d_dk0, d_iv0, d_dk1, d_iv1, (uint32_t)n_vis, kZBits, d_hist, d_status, d_cnt, d_err, &dk, &order);
+    launch_tile_scan(L, order, d_ntile, (uint32_t)n_vis, nullptr, d_poff, d_tparts, (uint32_t)n_pairs, d_total);
+    launch_pairs(L, d_views, K, order, d_poff, d_rec, d_info, (uint32_t)n_vis, nullptr, P, d_k0, d_v0, (uint32_t)n_pairs);
+    launch_sort(L, d_k0, d_v0, d_k1, d_v1, (uint32_t)n_pairs, tbits, d_hist, d_status, d_cnt, d_err, &tk, &tv, d_total);
+    launch_ranges(L, tk, (uint32_t)n_pairs, d_ranges, (int)tiles_total, d_total);
+    launch_composite(L, d_views, 0, V, (int)tiles_total, d_ranges, tv, d_rec, P, out_rgb, out_depth, out_alpha,
                      nullptr);
     uint32_t h_err = 0;
     NA_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
     NA_CUDA(cudaGetLastError());
     NA_CUDA(cudaStreamSynchronize(stream));
     if (h_err & kErrTimeout) return DGS_ERR_TIMEOUT;
-    if (h_err & kErrMismatch) return DGS_ERR_CUDA;
+    if (h_err & (kErrMismatch | kErrCapacity)) return DGS_ERR_CUDA;
     if (h_err & kErrPose) return DGS_ERR_INVALID_ARG;
     return DGS_OK;
 #undef NA_CUDA

@@ -274,112 +274,63 @@ __device__ __forceinline__ bool chunk_may_be_visible(const ChunkBound& b, const 
     return !(fl + ex < 0.f || fr + ex < 0.f || ft + ey < 0.f || fb + ey < 0.f);
 }
 
-// Does the ellipse {d^T conic d <= qlim} reach a pixel centre of the rectangle
-// [X0,X1] x [Y0,Y1] (coordinates relative to the mean)?  Minimum of the convex quadratic over
-// the rectangle: 0 if the mean is inside, else the smallest of the four edge minima.
-__device__ __forceinline__ bool ellipse_meets_rect(float a, float b, float c, float qlim, float X0, float X1, float Y0, float Y1) {
-    if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return true;
-    float m = INFINITY;
-    const float ia = 1.f / a, ic = 1.f / c;
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const float X = e ? X1 : X0;
-        const float Y = fminf(Y1, fmaxf(Y0, -b * X * ic));
-        m = fminf(m, fmaf(a * X, X, fmaf(2.f * b * X, Y, c * Y * Y)));
-        const float Yh = e ? Y1 : Y0;
-        const float Xh = fminf(X1, fmaxf(X0, -b * Yh * ia));
-        m = fminf(m, fmaf(a * Xh, Xh, fmaf(2.f * b * Xh, Yh, c * Yh * Yh)));
-    }
-    return m <= qlim;
-}
-
-// Walks the union of the warp's tile rectangles, flattened in (lane, row-major tile) order,
-// 32 candidates at a time.  Lane l of the flush holds one (Gaussian, view) item; items are in
-// view-major, Gaussian order.  COUNT: adds each item's hit count to S.hits[l].  EMIT: writes
-// the hits of view j at S.pbase[j] + S.run[j] + rank, in walk order, and advances S.run[j].
-// The count and emit passes walk the same items in the same order.
+// Emission walk: the union of the warp's tile rectangles, flattened in (lane, row-major tile)
+// order, is tested 32 candidates at a time; lane l of a flush holds one visible instance and
+// S.hits[l] receives its number of tile pairs.  The pair kernel walks the same rectangles with
+// the same test on the same stored values.
 struct WarpSplats {
-    float u[32], v[32], a[32], b[32], c[32];
+    float u[32], v[32], qa[32], qb[32], qc[32];
     int32_t tx0[32], ty0[32], tw[32], x0[32], x1[32], y0[32], y1[32];
     uint32_t excl[32];     // exclusive prefix of the items' tile-rectangle areas
-    uint32_t zk[32];       // depth key of the item (emit)
-    uint32_t rec[32];      // record index of the item (emit)
-    int32_t vj[32];        // view slot (0..kViewBlock-1) of the item
-    uint32_t hits[32];     // hit count of the item (count)
+    uint32_t hits[32];     // tile pairs of the item
 };
 
 constexpr int kViewBlock = 8;
 
 struct WarpViews {
-    uint64_t pbase[kViewBlock];   // first pair of (view j, chunk) relative to the group (emit)
-    uint64_t pend[kViewBlock];
     int64_t tab[kViewBlock];      // count-table entry of (view j, chunk)
-    uint32_t run[kViewBlock];     // pairs written so far for view j (emit)
-    int32_t tile_base[kViewBlock];
-    int32_t tiles_x[kViewBlock];
     uint32_t mask[kViewBlock];    // survivor lanes of view j
     int32_t vv[kViewBlock];       // (view, slot) index of view j, -1 = none
     uint32_t vis[kViewBlock];     // count pass: lanes whose projection succeeded
-    uint32_t hits[kViewBlock];    // count pass: pairs of view j
+    uint32_t hits[kViewBlock];    // count pass: tile-rectangle area of view j's visible lanes
     uint32_t ibase[kViewBlock];   // emit: first record of (view j, chunk) relative to the group
 };
 
 __device__ __forceinline__ void stash_splat(WarpSplats& S, int lane, const Splat& s, uint32_t excl) {
-    S.u[lane] = s.u; S.v[lane] = s.v; S.a[lane] = s.a; S.b[lane] = s.b; S.c[lane] = s.c;
+    S.u[lane] = s.u; S.v[lane] = s.v; S.qa[lane] = s.qa; S.qb[lane] = s.qb; S.qc[lane] = s.qc;
     S.tx0[lane] = s.tx0; S.ty0[lane] = s.ty0; S.tw[lane] = s.tx1 - s.tx0 + 1;
     S.x0[lane] = s.x0; S.x1[lane] = s.x1; S.y0[lane] = s.y0; S.y1[lane] = s.y1;
     S.excl[lane] = excl;
 }
 
-template <bool EMIT>
-__device__ __forceinline__ void walk_tiles(WarpSplats& S, WarpViews& WV, int lane, uint32_t total, const Params& P,
-                                           uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+// Owner of flattened candidate f: the last item whose rectangle starts at or before f.
+__device__ __forceinline__ int walk_owner(const uint32_t* excl, uint32_t f) {
+    int lo = 0, hi = 31;
+#pragma unroll
+    for (int it = 0; it < 5; ++it) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (excl[mid] <= f) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void walk_count(WarpSplats& S, int lane, uint32_t total, const Params& P) {
     const uint32_t lt = (1u << lane) - 1u;
     for (uint32_t base = 0; base < total; base += 32) {
         const uint32_t f = base + (uint32_t)lane;
         bool hit = false;
-        int o = -1, tx = 0, ty = 0;
+        int o = -1;
         if (f < total) {
-            // owner: last item whose rectangle starts at or before f
-            int lo = 0, hi = 31;
-#pragma unroll
-            for (int it = 0; it < 5; ++it) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (S.excl[mid] <= f) lo = mid; else hi = mid - 1;
-            }
-            o = lo;
+            o = walk_owner(S.excl, f);
             const uint32_t r = f - S.excl[o];
             const uint32_t w = (uint32_t)S.tw[o];
             const uint32_t row = r / w;
-            tx = S.tx0[o] + (int)(r - row * w);
-            ty = S.ty0[o] + (int)row;
-            if (P.exact_tile_test) {
-                const int px0 = max(tx * P.tile_w, S.x0[o]), px1 = min(tx * P.tile_w + P.tile_w - 1, S.x1[o]);
-                const int py0 = max(ty * P.tile_h, S.y0[o]), py1 = min(ty * P.tile_h + P.tile_h - 1, S.y1[o]);
-                const float u = S.u[o], v = S.v[o];
-                hit = ellipse_meets_rect(S.a[o], S.b[o], S.c[o], P.qbin, (float)px0 + 0.5f - u, (float)px1 + 0.5f - u,
-                                         (float)py0 + 0.5f - v, (float)py1 + 0.5f - v);
-            } else {
-                hit = true;
-            }
+            hit = tile_hit(S.u[o], S.v[o], S.qa[o], S.qb[o], S.qc[o], S.x0[o], S.x1[o], S.y0[o], S.y1[o],
+                           S.tx0[o] + (int)(r - row * w), S.ty0[o] + (int)row, P.tile_w, P.tile_h, P.qbin,
+                           P.exact_tile_test);
         }
-        if constexpr (!EMIT) {
-            const uint32_t peers = __match_any_sync(0xffffffffu, hit ? o : -1);
-            if (hit && (peers & lt) == 0) S.hits[o] += __popc(peers);
-        } else {
-            const int j = hit ? S.vj[o] : -1;
-            const uint32_t peers = __match_any_sync(0xffffffffu, j);
-            if (hit) {
-                const uint64_t pos = WV.pbase[j] + WV.run[j] + __popc(peers & lt);
-                if (pos < WV.pend[j]) {
-                    const uint64_t gt = (uint64_t)(WV.tile_base[j] - P.tile0 + ty * WV.tiles_x[j] + tx);
-                    keys[pos] = (gt << kZBits) | S.zk[o];
-                    vals[pos] = S.rec[o];
-                }
-            }
-            __syncwarp();
-            if (hit && (peers & lt) == 0) WV.run[j] += __popc(peers);
-        }
+        const uint32_t peers = __match_any_sync(0xffffffffu, hit ? o : -1);
+        if (hit && (peers & lt) == 0) S.hits[o] += __popc(peers);
         __syncwarp();
     }
 }
@@ -475,13 +426,15 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x) {
 // ------------------------------------------------------------------ count and emit passes
 // A warp owns a chunk of 32 consecutive Gaussians of one node and walks the (view, slot)
 // entries of that node in blocks of kViewBlock views:
-//   1. survivors: count pass -- a conservative cull of every (lane, view) pair, one ballot per
-//      view; emit pass -- the exact visible-lane masks the count pass stored;
+//   1. survivors: count pass -- a cull of the whole chunk per view (bounding ball), then a
+//      conservative cull of every (lane, view) pair, one ballot per view; emit pass -- the
+//      exact visible-lane masks the count pass stored;
 //   2. the survivors, queued view-major in Gaussian order, are projected 32 at a time (one
-//      per lane) and their tiles walked cooperatively;
-//   3. count pass -- per view, the mask of lanes whose projection succeeded and the number of
-//      (instance, tile) pairs go to the count table; emit pass -- records and pairs were
-//      written at the scanned offsets of each (view, chunk) entry.
+//      per lane);
+//   3. count pass -- per view, the mask of lanes whose projection succeeded and the summed
+//      area of their tile rectangles (a bound on their tile pairs) go to the count table;
+//      emit pass -- record, identity, depth key and exact tile-pair count of each instance at
+//      the scanned offset of its (view, chunk) entry.
 struct WarpWork {
     WarpSplats S;
     WarpViews WV;
@@ -512,15 +465,22 @@ __device__ __forceinline__ void decode_item(uint32_t idx, const WarpViews& WV, i
     g = nth_set_bit(WV.mask[j], idx - before);
 }
 
+// Outputs of the emit pass, indexed by record (instance) number.
+struct EmitOut {
+    Record* rec;
+    InstInfo* info;
+    uint32_t* dkey;       // depth key
+    uint32_t* ival;       // the record number itself (value carried by the depth sort)
+    uint32_t* ntile;      // tile pairs of the instance
+};
+
 template <bool EMIT>
 __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lane, const NodeView* __restrict__ entries,
                                               int n_entries, int v0, int v1, const ViewDesc* __restrict__ views,
                                               const VNode* __restrict__ vnodes, int K, const Params& P, const Gauss& gme,
                                               bool valid, const ChunkBound& cb, WarpWork& W, const float* __restrict__ shc,
                                               uint2* __restrict__ counts, const uint32_t* __restrict__ inst_off,
-                                              const uint64_t* __restrict__ pair_off, uint32_t inst_base,
-                                              uint64_t pair_base, Record* __restrict__ rec, InstInfo* __restrict__ info,
-                                              uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                                              uint32_t inst_base, const EmitOut& out) {
     WarpViews& WV = W.WV;
     for (int eb = 0; eb < n_entries; eb += kViewBlock) {
         const int nvb = min(kViewBlock, n_entries - eb);
@@ -532,19 +492,14 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
             const NodeView w = entries[eb + j];
             const bool in = w.view >= v0 && w.view < v1;
             WV.vv[j] = in ? w.view * K + w.slot : -1;
-            WV.vis[j] = 0; WV.hits[j] = 0; WV.run[j] = 0; WV.mask[j] = 0;
+            WV.vis[j] = 0; WV.hits[j] = 0; WV.mask[j] = 0;
             if (in) {
                 const int64_t t = vnodes[w.view * K + w.slot].tab + c;
                 WV.tab[j] = t;
                 if constexpr (!EMIT) sees = chunk_may_be_visible(cb, vnodes[w.view * K + w.slot], views[w.view], P);
                 if constexpr (EMIT) {
                     WV.mask[j] = counts[t].x;
-                    const ViewDesc& vd = views[w.view];
-                    WV.pbase[j] = pair_off[t] - pair_base;
-                    WV.pend[j] = pair_off[t + 1] - pair_base;
                     WV.ibase[j] = inst_off[t] - inst_base;
-                    WV.tile_base[j] = vd.tile_base;
-                    WV.tiles_x[j] = vd.tiles_x;
                 }
             }
         }
@@ -561,7 +516,7 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
         __syncwarp();
         uint32_t n_items = 0;
         for (int j = 0; j < nvb; ++j) n_items += __popc(WV.mask[j]);
-        // 2. project the survivors 32 at a time and walk their tiles
+        // 2. project the survivors 32 at a time
         for (uint32_t it = 0; it < n_items; it += 32) {
             const uint32_t idx = it + (uint32_t)lane;
             const bool act = idx < n_items;
@@ -576,15 +531,21 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
                 vis = project(gg, vnodes[vvj], views[vvj / K], P, s);
             }
             const uint32_t area = vis ? (uint32_t)((s.tx1 - s.tx0 + 1) * (s.ty1 - s.ty0 + 1)) : 0u;
-            const uint32_t excl = warp_excl_scan(area);
-            const uint32_t total = __shfl_sync(0xffffffffu, excl + area, 31);
-            if (vis) stash_splat(W.S, lane, s, excl); else W.S.excl[lane] = excl;
-            W.S.vj[lane] = j;
-            W.S.hits[lane] = 0;
-            if constexpr (EMIT) {
+            if constexpr (!EMIT) {
+                // per-view totals of this flush: items are view-sorted, reduce each view's run
+                const uint32_t peers = __match_any_sync(0xffffffffu, act ? j : -1);
+                const uint32_t h = __reduce_add_sync(peers, area);
+                const uint32_t bits = __reduce_or_sync(peers, vis ? (1u << g) : 0u);
+                if (act && (peers & ((1u << lane) - 1u)) == 0) { WV.hits[j] += h; WV.vis[j] |= bits; }
+            } else {
+                const uint32_t excl = warp_excl_scan(area);
+                const uint32_t total = __shfl_sync(0xffffffffu, excl + area, 31);
+                if (vis) stash_splat(W.S, lane, s, excl); else W.S.excl[lane] = excl;
+                W.S.hits[lane] = 0;
+                uint32_t r = 0;
                 if (act && !vis) atomicOr(P.err, kErrMismatch);
                 if (vis) {
-                    const uint32_t r = WV.ibase[j] + __popc(WV.mask[j] & ((1u << g) - 1u));
+                    r = WV.ibase[j] + __popc(WV.mask[j] & ((1u << g) - 1u));
                     float rgb[3];
                     sh_colour(nd.deg, shc + g * kShStride, gg, vnodes[vvj], rgb);
                     const int64_t i = (int64_t)c * kChunk + g;
@@ -593,35 +554,20 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
                     R.r0 = make_float4(s.u, s.v, op, s.z);
                     R.r1 = make_float4(s.qa, s.qb, s.qc, __uint_as_float((uint32_t)s.x0 | ((uint32_t)s.x1 << 16)));
                     R.r2 = make_float4(rgb[0], rgb[1], rgb[2], __uint_as_float((uint32_t)s.y0 | ((uint32_t)s.y1 << 16)));
-                    rec[r] = R;
-                    info[r] = InstInfo{(uint32_t)(nd.gbase + i), (uint32_t)vvj};
-                    W.S.zk[lane] = min(__float_as_uint(s.z) - P.zbase, (1u << kZBits) - 1u);
-                    W.S.rec[lane] = r;
+                    out.rec[r] = R;
+                    out.info[r] = InstInfo{(uint32_t)(nd.gbase + i), (uint32_t)vvj};
+                    out.dkey[r] = min(__float_as_uint(s.z) - P.zbase, (1u << kZBits) - 1u);
+                    out.ival[r] = r;
                 }
-            }
-            __syncwarp();
-            walk_tiles<EMIT>(W.S, WV, lane, total, P, keys, vals);
-            if constexpr (!EMIT) {
-                // per-view totals of this flush: items are view-sorted, reduce each view's run
-                const uint32_t peers = __match_any_sync(0xffffffffu, act ? j : -1);
-                const uint32_t h = __reduce_add_sync(peers, act ? W.S.hits[lane] : 0u);
-                const uint32_t bits = __reduce_or_sync(peers, vis ? (1u << g) : 0u);
-                if (act && (peers & ((1u << lane) - 1u)) == 0) { WV.hits[j] += h; WV.vis[j] |= bits; }
+                __syncwarp();
+                walk_count(W.S, lane, total, P);
+                if (vis) out.ntile[r] = W.S.hits[lane];
             }
             __syncwarp();
         }
-        // 3. results of the block
-        if (lane < nvb && WV.vv[lane] >= 0) {
-            const int j = lane;
-            if constexpr (!EMIT) {
-                counts[WV.tab[j]] = make_uint2(WV.vis[j], WV.hits[j]);
-            } else {
-                const uint64_t want = WV.pend[j] - WV.pbase[j];
-                if ((uint64_t)WV.run[j] != want) {
-                    atomicOr(P.err, kErrMismatch);
-                    for (uint64_t q = WV.pbase[j] + WV.run[j]; q < WV.pend[j]; ++q) { keys[q] = ~0ull; vals[q] = 0; }
-                }
-            }
+        // 3. count-table entries of the block
+        if constexpr (!EMIT) {
+            if (lane < nvb && WV.vv[lane] >= 0) counts[WV.tab[lane]] = make_uint2(WV.vis[lane], WV.hits[lane]);
         }
         __syncwarp();
     }
@@ -658,7 +604,7 @@ __global__ void __launch_bounds__(kCountWarps * 32) k_count_batched(const NodeDe
     stage_geometry<DT>(nd, c, lane, W, g, valid);
     const ChunkBound cb = chunk_bound(g, valid);
     process_chunk<false>(nd, c, lane, nv + nv_off[k], nv_off[k + 1] - nv_off[k], v0, v1, views, vnodes, K, P, g, valid,
-                         cb, W, nullptr, counts, nullptr, nullptr, 0, 0, nullptr, nullptr, nullptr, nullptr);
+                         cb, W, nullptr, counts, nullptr, 0, EmitOut{});
 }
 
 // Plain mode: the chunks of one view.  pmap = [K+1 prefix chunk counts in node-id order, K slots].
@@ -683,16 +629,14 @@ __global__ void __launch_bounds__(kCountWarps * 32) k_count_plain(const NodeDesc
     const ChunkBound cb = chunk_bound(g, valid);
     const NodeView one{v, slot};
     process_chunk<false>(nd, c, lane, &one, 1, v, v + 1, views, vnodes, K, P, g, valid, cb, W, nullptr, counts, nullptr,
-                         nullptr, 0, 0, nullptr, nullptr, nullptr, nullptr);
+                         0, EmitOut{});
 }
 
 template <int DT>
 __global__ void __launch_bounds__(kEmitWarps * 32) k_emit_batched(const NodeDesc* __restrict__ nodes, int n_nodes,
         const ViewDesc* __restrict__ views, const VNode* __restrict__ vnodes, int K, const NodeView* __restrict__ nv,
         const int32_t* __restrict__ nv_off, int n_chunks, Params P, int v0, int v1, const uint2* __restrict__ counts,
-        const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off, uint32_t inst_base,
-        uint64_t pair_base, Record* __restrict__ rec, InstInfo* __restrict__ info, uint64_t* __restrict__ keys,
-        uint32_t* __restrict__ vals) {
+        const uint32_t* __restrict__ inst_off, uint32_t inst_base, EmitOut out) {
     __shared__ WarpWork ww[kEmitWarps];
     __shared__ float shc[kEmitWarps][kChunk * kShStride];
     const int chunk = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
@@ -709,17 +653,14 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_emit_batched(const NodeDesc
     stage_geometry<DT>(nd, c, lane, W, g, valid);
     stage_sh<DT>(nd, c, lane, shc[wib]);
     process_chunk<true>(nd, c, lane, nv + nv_off[k], nv_off[k + 1] - nv_off[k], v0, v1, views, vnodes, K, P, g, valid,
-                        ChunkBound{}, W, shc[wib], const_cast<uint2*>(counts), inst_off, pair_off, inst_base, pair_base, rec, info,
-                        keys, vals);
+                        ChunkBound{}, W, shc[wib], const_cast<uint2*>(counts), inst_off, inst_base, out);
 }
 
 template <int DT>
 __global__ void __launch_bounds__(kEmitWarps * 32) k_emit_plain(const NodeDesc* __restrict__ nodes,
         const ViewDesc* __restrict__ views, const VNode* __restrict__ vnodes, int K, Params P, int v,
         const int32_t* __restrict__ pmap, int n_view_chunks, const uint2* __restrict__ counts,
-        const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off, uint32_t inst_base,
-        uint64_t pair_base, Record* __restrict__ rec, InstInfo* __restrict__ info, uint64_t* __restrict__ keys,
-        uint32_t* __restrict__ vals) {
+        const uint32_t* __restrict__ inst_off, uint32_t inst_base, EmitOut out) {
     __shared__ WarpWork ww[kEmitWarps];
     __shared__ float shc[kEmitWarps][kChunk * kShStride];
     const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
@@ -738,7 +679,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_emit_plain(const NodeDesc* 
     stage_sh<DT>(nd, c, lane, shc[wib]);
     const NodeView one{v, slot};
     process_chunk<true>(nd, c, lane, &one, 1, v, v + 1, views, vnodes, K, P, g, valid, ChunkBound{}, W, shc[wib],
-                        const_cast<uint2*>(counts), inst_off, pair_off, inst_base, pair_base, rec, info, keys, vals);
+                        const_cast<uint2*>(counts), inst_off, inst_base, out);
 }
 
 // ------------------------------------------------------------------ exclusive scan of the count table
@@ -844,20 +785,17 @@ template <int DT>
 void emit_launch(const Launch& L, const NodeDesc* nodes, int n_nodes, const ViewDesc* views, const VNode* vnodes, int K,
                  const NodeView* nv, const int32_t* nv_off, int n_chunks, const Params& P, int v0, int v1, bool batched,
                  const int32_t* pmap, int64_t view_chunks, const uint2* counts, const uint32_t* inst_off,
-                 const uint64_t* pair_off, uint32_t inst_base, uint64_t pair_base, Record* rec, InstInfo* info,
-                 uint64_t* keys, uint32_t* vals) {
+                 uint32_t inst_base, const EmitOut& out) {
     if (batched) {
         const int blocks = (int)(((int64_t)n_chunks + kEmitWarps - 1) / kEmitWarps);
         if (blocks == 0) return;
         k_emit_batched<DT><<<blocks, kEmitWarps * 32, 0, L.stream>>>(nodes, n_nodes, views, vnodes, K, nv, nv_off, n_chunks,
-                                                                     P, v0, v1, counts, inst_off, pair_off, inst_base,
-                                                                     pair_base, rec, info, keys, vals);
+                                                                     P, v0, v1, counts, inst_off, inst_base, out);
     } else {
         const int blocks = (int)((view_chunks + kEmitWarps - 1) / kEmitWarps);
         if (blocks == 0) return;
         k_emit_plain<DT><<<blocks, kEmitWarps * 32, 0, L.stream>>>(nodes, views, vnodes, K, P, v0, pmap, (int)view_chunks,
-                                                                   counts, inst_off, pair_off, inst_base, pair_base,
-                                                                   rec, info, keys, vals);
+                                                                   counts, inst_off, inst_base, out);
     }
     ++*L.launches;
 }
@@ -890,18 +828,18 @@ void launch_count(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_
 void launch_emit(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_nodes, const ViewDesc* views,
                  const VNode* vnodes, int K, const NodeView* node_views, const int32_t* node_view_off,
                  int n_chunks_total, const Params& P, int v0, int v1, bool batched, const int32_t* pmap,
-                 int64_t view_chunks, const uint2* counts, const uint32_t* inst_off, const uint64_t* pair_off,
-                 uint32_t inst_base,
-                 uint64_t pair_base, Record* records, InstInfo* info, uint64_t* keys, uint32_t* vals) {
+                 int64_t view_chunks, const uint2* counts, const uint32_t* inst_off, uint32_t inst_base,
+                 Record* records, InstInfo* info, uint32_t* dkey, uint32_t* ival, uint32_t* ntile) {
+    const EmitOut out{records, info, dkey, ival, ntile};
     if (dtype_mask & (1 << DGS_F32))
         emit_launch<DGS_F32>(L, nodes, n_nodes, views, vnodes, K, node_views, node_view_off, n_chunks_total, P, v0, v1,
-                             batched, pmap, view_chunks, counts, inst_off, pair_off, inst_base, pair_base, records, info, keys, vals);
+                             batched, pmap, view_chunks, counts, inst_off, inst_base, out);
     if (dtype_mask & (1 << DGS_BF16))
         emit_launch<DGS_BF16>(L, nodes, n_nodes, views, vnodes, K, node_views, node_view_off, n_chunks_total, P, v0, v1,
-                              batched, pmap, view_chunks, counts, inst_off, pair_off, inst_base, pair_base, records, info, keys, vals);
+                              batched, pmap, view_chunks, counts, inst_off, inst_base, out);
     if (dtype_mask & (1 << DGS_F16))
         emit_launch<DGS_F16>(L, nodes, n_nodes, views, vnodes, K, node_views, node_view_off, n_chunks_total, P, v0, v1,
-                             batched, pmap, view_chunks, counts, inst_off, pair_off, inst_base, pair_base, records, info, keys, vals);
+                             batched, pmap, view_chunks, counts, inst_off, inst_base, out);
 }
 
 void launch_scan(const Launch& L, const uint2* counts, int64_t n, uint32_t* inst_off, uint64_t* pair_off,

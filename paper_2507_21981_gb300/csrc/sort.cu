@@ -1,16 +1,20 @@
-// Stable LSD radix sort of (64-bit key, 32-bit value) pairs in the onesweep style (kernel K3).
+// Stable LSD radix sort of (32-bit key, 32-bit value) pairs in the onesweep style (kernel K3).
 //
 // Sec. III-A: the 3DGS rasterizer orders the (tile, depth) pairs of every view with a fast
-// GPU sort before blending.  Keys are (global tile << 28) | depth-key, values the instance
-// index; emission in global-id order plus stability breaks equal depths by id.
+// GPU sort before blending.  Here the order is built in two stable sorts of 32-bit keys: the
+// projected instances by depth key (28 bits), then the (tile, instance) pairs -- emitted in
+// that depth order -- by tile.  Stability carries the depth order, and the id order of equal
+// depths, into every tile's run.
 //
-// Structure: one upfront pass builds the 256-bin histograms of every digit at once; then
-// each digit is one kernel in which a block takes the next 4096-key partition from an atomic
-// counter, ranks its keys by digit inside the block (warp match + per-warp counters), and
-// finds its global offset per digit by decoupled look-back over the partitions before it
-// (status word = 2-bit flag | 30-bit count).  Only digits inside the significant key bits
-// are sorted.  Look-back spins are bounded by a wall-clock limit; on expiry the kernel sets
-// kErrTimeout and finishes (the output is then invalid and the host reports it).
+// Structure: one upfront pass builds the histograms of every digit at once; then each digit is
+// one kernel in which a block takes the next 4096-key partition from an atomic counter, ranks
+// its keys by digit inside the block (warp match + per-warp counters), and finds its global
+// offset per digit by decoupled look-back over the partitions before it (status word = 2-bit
+// flag | 30-bit count).  Digits are D = ceil(bits / passes) bits wide with passes =
+// ceil(bits / 8): measured on this path, wider digits (fewer passes) lose what they save to
+// the scatter, whose runs per partition shrink to a few keys.  Look-back spins are bounded by
+// a wall-clock limit; on expiry the kernel sets kErrTimeout and finishes (the output is then
+// invalid and the host reports it).
 #include <algorithm>
 
 #include "dgs_internal.cuh"
@@ -22,8 +26,12 @@ constexpr int kThreads = 256;
 constexpr int kItems = 16;
 constexpr int kTile = kThreads * kItems;          // 4096 keys per partition
 constexpr int kWarps = kThreads / 32;
+constexpr int kMaxD = 8;                          // widest digit: 256 bins
+constexpr int kMaxR = 1 << kMaxD;
+constexpr int kWindow = 4;                        // predecessors read per digit and look-back round
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kCountMask = (1u << 30) - 1u;
 constexpr uint64_t kSpinLimitNs = 1000000000ull;  // 1 s
+constexpr int kSmem = kTile * 8 + kWarps * kMaxR * 4;
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
     uint32_t v;
@@ -36,56 +44,80 @@ __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
 
 __device__ __forceinline__ uint32_t live_count(uint32_t n, const uint32_t* d_n) { return d_n ? min(*d_n, n) : n; }
 
-__global__ void __launch_bounds__(kThreads) k_hist(const uint64_t* __restrict__ keys, uint32_t n,
-                                                   const uint32_t* __restrict__ d_n, int passes, uint32_t* hist) {
-    __shared__ uint32_t sh[8 * 256];
+// Histograms of every pass's digit (digit width D) in one read of the keys; hist[p * kMaxR + b].
+__global__ void __launch_bounds__(kThreads) k_hist(const uint32_t* __restrict__ keys, uint32_t n,
+                                                   const uint32_t* __restrict__ d_n, int passes, int D,
+                                                   uint32_t* hist) {
+    __shared__ uint32_t sh[4 * kMaxR];
     n = live_count(n, d_n);
-    for (int i = threadIdx.x; i < passes * 256; i += kThreads) sh[i] = 0;
+    const uint32_t R = 1u << D, mask = R - 1u;
+    for (int i = threadIdx.x; i < passes * (int)R; i += kThreads) sh[i] = 0;
     __syncthreads();
     for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
-        const uint64_t k = keys[i];
-        for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * 256 + (uint32_t)((k >> (8 * p)) & 255u)], 1u);
+        const uint32_t k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * R + ((k >> (D * p)) & mask)], 1u);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * 256; i += kThreads)
-        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+    for (int i = threadIdx.x; i < passes * (int)R; i += kThreads)
+        if (sh[i]) atomicAdd(&hist[(i / R) * kMaxR + (i % R)], sh[i]);
 }
 
-// one block, 256 threads: exclusive scan of each pass's 256 bins, in place
-__global__ void __launch_bounds__(256) k_hist_scan(uint32_t* hist, int passes) {
-    __shared__ uint32_t s[256];
+// one block, 256 threads: exclusive scan of each pass's R bins, in place (4 bins per thread)
+__global__ void __launch_bounds__(256) k_hist_scan(uint32_t* hist, int passes, int R) {
+    __shared__ uint32_t s_w[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int p = 0; p < passes; ++p) {
-        const uint32_t x = hist[p * 256 + threadIdx.x];
-        s[threadIdx.x] = x;
-        __syncthreads();
-        for (int o = 1; o < 256; o <<= 1) {
-            const uint32_t y = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0u;
-            __syncthreads();
-            s[threadIdx.x] += y;
-            __syncthreads();
+        uint32_t* h = hist + p * kMaxR;
+        uint32_t v[4], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int b = threadIdx.x * 4 + j;
+            v[j] = b < R ? h[b] : 0u;
+            sum += v[j];
         }
-        hist[p * 256 + threadIdx.x] = s[threadIdx.x] - x;
+        uint32_t y = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += t;
+        }
+        if (lane == 31) s_w[warp] = y;
+        __syncthreads();
+        uint32_t run = y - sum;
+        for (int w = 0; w < warp; ++w) run += s_w[w];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int b = threadIdx.x * 4 + j;
+            if (b < R) h[b] = run;
+            run += v[j];
+        }
         __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_onesweep(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                                                      uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t n,
+// One digit pass.  Thread t owns digits t, t + 256, ... (< 2^D) in the per-digit phases
+// (prefix over warps, look-back, block scan); digits are (key >> shift) & (2^D - 1).
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                      uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t n,
                                                       const uint32_t* __restrict__ d_n, int shift,
                                                       const uint32_t* __restrict__ digit_off, uint32_t* status,
                                                       uint32_t* counter, uint32_t* err) {
+    constexpr int R = 1 << D;
+    constexpr uint32_t M = R - 1;
+    constexpr int DPT = (R + kThreads - 1) / kThreads;   // digits per thread
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);                          // kTile
-    uint32_t* s_vals = reinterpret_cast<uint32_t*>(smem + kTile * 8);               // kTile
-    uint32_t* s_whist = reinterpret_cast<uint32_t*>(smem + kTile * 12);             // kWarps x 256
-    __shared__ uint32_t s_dexcl[256];
-    __shared__ uint32_t s_gbase[256];
+    uint32_t* s_keys = reinterpret_cast<uint32_t*>(smem);                          // kTile
+    uint32_t* s_vals = reinterpret_cast<uint32_t*>(smem + kTile * 4);               // kTile
+    uint32_t* s_whist = reinterpret_cast<uint32_t*>(smem + kTile * 8);              // kWarps x R
+    __shared__ uint32_t s_dexcl[R];
+    __shared__ uint32_t s_gbase[R];
     __shared__ uint32_t s_wsum[kWarps];
     __shared__ uint32_t s_part;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_part = atomicAdd(counter, 1u);
-    for (int i = tid; i < kWarps * 256; i += kThreads) s_whist[i] = 0;
+    for (int i = tid; i < kWarps * R; i += kThreads) s_whist[i] = 0;
     __syncthreads();
     const uint32_t part = s_part;
     n = live_count(n, d_n);
@@ -94,67 +126,109 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(const uint64_t* __restric
     if (part * (uint64_t)kTile >= n && part > 0) return;
     const uint32_t base = part * (uint32_t)kTile;
 
-    uint64_t k[kItems];
-    uint32_t v[kItems], rank[kItems];
+    uint32_t k[kItems], v[kItems], rank[kItems];
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
         const uint32_t idx = base + warp * (kItems * 32) + j * 32 + lane;
         if (idx < n) { k[j] = kin[idx]; v[j] = vin[idx]; }
-        else { k[j] = ~0ull; v[j] = 0; }
+        else { k[j] = ~0u; v[j] = 0; }
     }
     // rank within the warp, in original order (round j covers 32 consecutive keys)
     const uint32_t lt = (1u << lane) - 1u;
-    uint32_t* wh = s_whist + warp * 256;
+    uint32_t* wh = s_whist + warp * R;
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
-        const uint32_t d = (uint32_t)(k[j] >> shift) & 255u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t pre = wh[d];
+        const uint32_t dg = (k[j] >> shift) & M;
+        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        const uint32_t pre = wh[dg];
         rank[j] = pre + __popc(peers & lt);
         __syncwarp();
-        if ((peers & lt) == 0) wh[d] = pre + __popc(peers);
+        if ((peers & lt) == 0) wh[dg] = pre + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    // thread d: exclusive prefix over warps and the partition total of digit d
-    const uint32_t d = tid;
-    uint32_t total = 0;
+    // per owned digit: exclusive prefix over warps and the partition total
+    uint32_t total[DPT], excl[DPT];
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-        const uint32_t c = s_whist[w * 256 + d];
-        s_whist[w * 256 + d] = total;
-        total += c;
+    for (int q = 0; q < DPT; ++q) {
+        const int d = tid + q * kThreads;
+        total[q] = 0;
+        excl[q] = 0;
+        if (d < R) {
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const uint32_t c = s_whist[w * R + d];
+                s_whist[w * R + d] = total[q];
+                total[q] += c;
+            }
+        }
     }
-    // decoupled look-back over earlier partitions for digit d
-    uint32_t excl = 0;
+    // decoupled look-back over earlier partitions, all owned digits at once
     if (part == 0) {
-        st_relaxed(&status[d], kFlagInc | total);
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+            const int d = tid + q * kThreads;
+            if (d < R) st_relaxed(&status[d], kFlagInc | total[q]);
+        }
     } else {
-        st_relaxed(&status[(size_t)part * 256 + d], kFlagAgg | total);
-        int64_t p = (int64_t)part - 1;
+        int64_t p[DPT];
+        bool done[DPT];
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+            const int d = tid + q * kThreads;
+            done[q] = d >= R;
+            p[q] = (int64_t)part - 1;
+            if (d < R) st_relaxed(&status[(size_t)part * R + d], kFlagAgg | total[q]);
+        }
         uint64_t t0 = 0;
         uint32_t spins = 0;
-        while (p >= 0) {
-            const uint32_t s = ld_relaxed(&status[(size_t)p * 256 + d]);
-            const uint32_t f = s & ~kCountMask;
-            if (f == 0) {
-                if ((++spins & 1023u) == 0) {
-                    const uint64_t now = global_timer_ns();
-                    if (t0 == 0) t0 = now;
-                    else if (now - t0 > kSpinLimitNs) { atomicOr(err, kErrTimeout); break; }
+        while (true) {
+            uint32_t sv[DPT][kWindow];
+#pragma unroll
+            for (int q = 0; q < DPT; ++q)
+#pragma unroll
+                for (int w = 0; w < kWindow; ++w)
+                    sv[q][w] = (!done[q] && p[q] - w >= 0)
+                                   ? ld_relaxed(&status[(size_t)(p[q] - w) * R + tid + q * kThreads]) : kFlagInc;
+            bool all = true, stall = false;
+#pragma unroll
+            for (int q = 0; q < DPT; ++q) {
+                if (done[q]) continue;
+                bool stop = false;
+#pragma unroll
+                for (int w = 0; w < kWindow; ++w) {
+                    if (stop || done[q]) continue;
+                    const uint32_t f = sv[q][w] & ~kCountMask;
+                    if (f == 0) { stop = true; continue; }
+                    excl[q] += sv[q][w] & kCountMask;
+                    if (f == kFlagInc) done[q] = true; else --p[q];
                 }
-                continue;
+                if (!done[q]) { all = false; stall |= stop; }
             }
-            excl += s & kCountMask;
-            if (f == kFlagInc) break;
-            --p;
+            if (all) break;
+            if (stall && (++spins & 1023u) == 0) {
+                const uint64_t now = global_timer_ns();
+                if (t0 == 0) t0 = now;
+                else if (now - t0 > kSpinLimitNs) { atomicOr(err, kErrTimeout); break; }
+            }
         }
-        st_relaxed(&status[(size_t)part * 256 + d], kFlagInc | (excl + total));
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+            const int d = tid + q * kThreads;
+            if (d < R) st_relaxed(&status[(size_t)part * R + d], kFlagInc | (excl[q] + total[q]));
+        }
     }
-    s_gbase[d] = digit_off[d] + excl;
-    // block exclusive scan of the digit totals -> local digit offsets
-    {
-        uint32_t x = total;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+        const int d = tid + q * kThreads;
+        if (d < R) s_gbase[d] = digit_off[d] + excl[q];
+    }
+    // block exclusive scan of the digit totals in digit order -> local digit offsets; slab q
+    // holds digits [q * 256, q * 256 + 256)
+    uint32_t carry = 0;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+        uint32_t x = total[q];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -162,49 +236,69 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(const uint64_t* __restric
         }
         if (lane == 31) s_wsum[warp] = x;
         __syncthreads();
-        uint32_t wpre = 0;
-        for (int w = 0; w < warp; ++w) wpre += s_wsum[w];
-        s_dexcl[d] = wpre + x - total;
+        uint32_t wpre = 0, slab = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            if (w < warp) wpre += s_wsum[w];
+            slab += s_wsum[w];
+        }
+        const int d = tid + q * kThreads;
+        if (d < R) s_dexcl[d] = carry + wpre + x - total[q];
+        carry += slab;
+        __syncthreads();
     }
-    __syncthreads();
     // local scatter: digit-major order inside the partition
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
-        const uint32_t dj = (uint32_t)(k[j] >> shift) & 255u;
-        const uint32_t pos = s_dexcl[dj] + s_whist[warp * 256 + dj] + rank[j];
+        const uint32_t dj = (k[j] >> shift) & M;
+        const uint32_t pos = s_dexcl[dj] + s_whist[warp * R + dj] + rank[j];
         s_keys[pos] = k[j];
         s_vals[pos] = v[j];
     }
     __syncthreads();
 #pragma unroll 4
     for (int i = tid; i < kTile; i += kThreads) {
-        const uint64_t key = s_keys[i];
-        const uint32_t dj = (uint32_t)(key >> shift) & 255u;
+        const uint32_t key = s_keys[i];
+        const uint32_t dj = (key >> shift) & M;
         const uint32_t g = s_gbase[dj] + (uint32_t)i - s_dexcl[dj];
         if (g < n) { kout[g] = key; vout[g] = s_vals[i]; }
     }
 }
 
+using OnesweepFn = void (*)(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t, const uint32_t*, int,
+                            const uint32_t*, uint32_t*, uint32_t*, uint32_t*);
+
+OnesweepFn onesweep_for(int D) {
+    switch (D) {
+        case 1: return k_onesweep<1>;
+        case 2: return k_onesweep<2>;
+        case 3: return k_onesweep<3>;
+        case 4: return k_onesweep<4>;
+        case 5: return k_onesweep<5>;
+        case 6: return k_onesweep<6>;
+        case 7: return k_onesweep<7>;
+        default: return k_onesweep<8>;
+    }
+}
+
 }  // namespace
 
-int sort_passes(int key_bits) { return (key_bits + 7) / 8; }
+int sort_passes(int key_bits) { return std::max(1, (key_bits + kMaxD - 1) / kMaxD); }
 
-size_t sort_status_words(uint32_t n) { return ((size_t)n + kTile - 1) / kTile * 256; }
+size_t sort_status_words(uint32_t n) { return ((size_t)n + kTile - 1) / kTile * kMaxR; }
 
 void sort_prepare() {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, kTile * 12 + kWarps * 256 * 4);
+        for (int D = 1; D <= kMaxD; ++D)
+            cudaFuncSetAttribute(onesweep_for(D), cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
         attr_set = true;
     }
 }
 
-// hist: [8*256] words, counters: [8] words, status: sort_status_words(n) words.
-void launch_sort(const Launch& L, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, uint32_t n,
+// hist: [4 * 256] words, counters: [8] words, status: sort_status_words(n) words.
+void launch_sort(const Launch& L, uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, uint32_t n,
                  int key_bits, uint32_t* hist, uint32_t* status, uint32_t* counters, uint32_t* err,
-                 uint64_t** keys_out, uint32_t** vals_out, float* sort_ms_slot, cudaEvent_t* evs,
-                 const uint32_t* d_n) {
-    (void)sort_ms_slot; (void)evs;
+                 uint32_t** keys_out, uint32_t** vals_out, const uint32_t* d_n) {
     *keys_out = keys;
     *vals_out = vals;
     // with a device-side count every pass runs (the output lands in the same buffer whatever
@@ -212,23 +306,24 @@ void launch_sort(const Launch& L, uint64_t* keys, uint32_t* vals, uint64_t* keys
     if (n <= 1 && !d_n) return;
     if (n == 0) return;
     const int passes = sort_passes(key_bits);
+    const int D = (std::max(1, key_bits) + passes - 1) / passes;
     sort_prepare();
-    cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 256 * passes, L.stream);
+    cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kMaxR * passes, L.stream);
     cudaMemsetAsync(counters, 0, sizeof(uint32_t) * 8, L.stream);
     const int hist_blocks = (int)std::min<uint32_t>(4 * 152, (n + kThreads * 8 - 1) / (kThreads * 8));
-    k_hist<<<hist_blocks, kThreads, 0, L.stream>>>(keys, n, d_n, passes, hist);
-    k_hist_scan<<<1, 256, 0, L.stream>>>(hist, passes);
+    k_hist<<<hist_blocks, kThreads, 0, L.stream>>>(keys, n, d_n, passes, D, hist);
+    k_hist_scan<<<1, 256, 0, L.stream>>>(hist, passes, 1 << D);
     *L.launches += 2;
     const uint32_t parts = (n + kTile - 1) / kTile;
-    uint64_t *ki = keys, *ko = keys_alt;
+    const OnesweepFn fn = onesweep_for(D);
+    uint32_t *ki = keys, *ko = keys_alt;
     uint32_t *vi = vals, *vo = vals_alt;
     for (int p = 0; p < passes; ++p) {
-        cudaMemsetAsync(status, 0, sizeof(uint32_t) * 256 * (size_t)parts, L.stream);
-        k_onesweep<<<parts, kThreads, kTile * 12 + kWarps * 256 * 4, L.stream>>>(ki, vi, ko, vo, n, d_n, 8 * p,
-                                                                                 hist + p * 256, status, counters + p,
-                                                                                 err);
+        cudaMemsetAsync(status, 0, sizeof(uint32_t) * (size_t)(1 << D) * parts, L.stream);
+        fn<<<parts, kThreads, kSmem, L.stream>>>(ki, vi, ko, vo, n, d_n, D * p, hist + p * kMaxR, status, counters + p,
+                                                 err);
         ++*L.launches;
-        uint64_t* tk = ki; ki = ko; ko = tk;
+        uint32_t* tk = ki; ki = ko; ko = tk;
         uint32_t* tv = vi; vi = vo; vo = tv;
     }
     *keys_out = ki;
