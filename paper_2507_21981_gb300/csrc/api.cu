@@ -438,6 +438,7 @@ int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* e
     P.t_min = o.t_min; P.q_max = o.q_max; P.guard = o.guard;
     P.bg0 = o.bg[0]; P.bg1 = o.bg[1]; P.bg2 = o.bg[2];
     P.qbin = o.q_max * 1.001f + 1e-3f;
+    P.p_min = kHalfLog2e * o.q_max;
     P.tile_w = o.tile_w; P.tile_h = o.tile_h;
     P.exact_tile_test = o.exact_tile_test;
     P.tile0 = 0;

@@ -26,25 +26,6 @@ namespace {
 // per-instance partials, in this order
 enum { G_U = 0, G_V, G_QA, G_QB, G_QC, G_OP, G_R, G_G, G_B, G_Z, G_N };
 
-__device__ __forceinline__ bool ellipse_meets_b(float qa, float qb, float qc, float qlim, float X0, float X1, float Y0,
-                                                float Y1) {
-    if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return true;
-    const float k = -qa * qb / fmaf(qa * qb, qb, qc);
-    float m = INFINITY;
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const float Y = e ? Y1 : Y0;
-        const float X = fminf(X1, fmaxf(X0, -qb * Y));
-        const float t = fmaf(qb, Y, X);
-        m = fminf(m, fmaf(qa * t, t, qc * Y * Y));
-        const float Xv = e ? X1 : X0;
-        const float Yv = fminf(Y1, fmaxf(Y0, k * Xv));
-        const float tv = fmaf(qb, Yv, Xv);
-        m = fminf(m, fmaf(qa * tv, tv, qc * Yv * Yv));
-    }
-    return m <= qlim;
-}
-
 __device__ __forceinline__ float warp_sum(float x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -109,7 +90,7 @@ __global__ void __launch_bounds__(256) k_composite_bwd(const ViewDesc* __restric
             if ((int)(bx & 0xFFFFu) <= wx1 && (int)(bx >> 16) >= wx0 && (int)(by & 0xFFFFu) <= wy1 && (int)(by >> 16) >= wy0) {
                 a = r->r0;
                 col = r->r2;
-                rel = ellipse_meets_b(q.x, q.y, q.z, P.qbin, (float)wx0 + 0.5f - a.x, (float)wx1 + 0.5f - a.x,
+                rel = ellipse_meets(q.x, q.y, q.z, P.qbin, (float)wx0 + 0.5f - a.x, (float)wx1 + 0.5f - a.x,
                                       (float)wy0 + 0.5f - a.y, (float)wy1 + 0.5f - a.y);
             }
         }
@@ -130,10 +111,11 @@ __global__ void __launch_bounds__(256) k_composite_bwd(const ViewDesc* __restric
             if (!done) {
                 const float4 g0 = sr0[k], g1 = sr1[k];
                 const float dx = fx - g0.x, dy = fy - g0.y;
-                const float t = fmaf(g1.y, dy, dx);
-                const float qq = fmaf(g1.x * t, t, g1.z * dy * dy);
-                if (qq <= P.q_max) {
-                    const float ex = __expf(-0.5f * qq);
+                float t;
+                // the forward pass's decisions: same staged products, same exponent
+                const float pe = pixel_exponent(kHalfLog2e * g1.x, g1.y, kHalfLog2e * g1.z, dx, dy, t);
+                if (pe >= P.p_min) {
+                    const float ex = fast_exp2(pe);
                     const float a_raw = g0.z * ex;
                     const float alpha = fminf(P.alpha_max, a_raw);
                     if (alpha >= P.alpha_min) {

@@ -82,19 +82,19 @@ __global__ void __launch_bounds__(256) k_composite(const ViewDesc* __restrict__ 
         if (m == 0) continue;
         if (rel) {
             const int pos = __popc(m & lt);
-            sr0[pos] = a; sr1[pos] = q; sr2[pos] = col;
+            sr0[pos] = a; sr2[pos] = col;
+            sr1[pos] = make_float4(kHalfLog2e * q.x, q.y, kHalfLog2e * q.z, 0.f);
         }
         __syncwarp();
         const int n = __popc(m);
         if (COUNT) n_eval += done ? 0u : (uint32_t)n;
         for (int k = 0; k < n && !done; ++k) {
             const float4 g0 = sr0[k], g1 = sr1[k];
-            const float dx = fx - g0.x, dy = fy - g0.y;
-            const float t = fmaf(g1.y, dy, dx);
-            const float qq = fmaf(g1.x * t, t, g1.z * dy * dy);
-            if (qq > P.q_max) continue;
+            float t;
+            const float pe = pixel_exponent(g1.x, g1.y, g1.z, fx - g0.x, fy - g0.y, t);
+            if (pe < P.p_min) continue;
             if (COUNT) ++n_reach;
-            const float alpha = fminf(P.alpha_max, g0.z * __expf(-0.5f * qq));
+            const float alpha = fminf(P.alpha_max, g0.z * fast_exp2(pe));
             if (alpha < P.alpha_min) continue;
             const float Tn = T * (1.f - alpha);
             if (Tn < P.t_min) { done = true; break; }

@@ -64,6 +64,7 @@ struct Params {
     int32_t tile0;        // first global tile of the current view group
     uint32_t* err;        // device error word
     const uint32_t* gate; // emission is skipped when non-null and *gate != 0 (capacity overflow)
+    float p_min;          // kHalfLog2e * q_max: exponents below it are outside the 3-sigma ellipse
 };
 
 // Projected instance as stored for compositing: 48 bytes.
@@ -104,7 +105,9 @@ __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 __device__ __forceinline__ bool ellipse_meets(float qa, float qb, float qc, float qlim, float X0, float X1, float Y0,
                                               float Y1) {
     if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return true;
-    const float k = -qa * qb / fmaf(qa * qb, qb, qc);
+    // the slope of the vertical-edge minimiser needs no correct rounding: any point of the
+    // edge bounds the minimum from above, and the binning limit carries a 0.1 % + 1e-3 margin
+    const float k = __fdividef(-qa * qb, fmaf(qa * qb, qb, qc));
     float m = INFINITY;
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
@@ -118,6 +121,25 @@ __device__ __forceinline__ bool ellipse_meets(float qa, float qb, float qc, floa
         m = fminf(m, fmaf(qa * tv, tv, qc * Yv * Yv));
     }
     return m <= qlim;
+}
+
+// Compositing arithmetic shared by the forward pass and its adjoint, so both take the same
+// FP32 decisions.  exp(-q/2) = 2^(c q) with c = -log2(e)/2: a staged record carries
+// (c qa, qb, c qc), each coefficient one FP32 product, and the pixel's exponent is
+// p = (c qa) (dx + qb dy)^2 + (c qc) dy^2; the 3-sigma test q <= q_max reads p >= c q_max.
+constexpr float kHalfLog2e = -0.72134752044448170f;   // -log2(e) / 2
+
+__device__ __forceinline__ float fast_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Exponent p of a staged record (scaled coefficients ca, qb, cc) at pixel offset (dx, dy);
+// also returns t = dx + qb dy.
+__device__ __forceinline__ float pixel_exponent(float ca, float qb, float cc, float dx, float dy, float& t) {
+    t = fmaf(qb, dy, dx);
+    return fmaf(ca * t, t, cc * dy * dy);
 }
 
 // Binning decision for tile (tx, ty) of an instance with centre (u, v), factored form
