@@ -360,7 +360,7 @@ int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* e
             pre += nd[k].nchunks;
             tab += nd[k].nchunks;
             n_instances += nd[k].n;
-            per_node[k].push_back({v, j});
+            per_node[k].push_back({v, j, vnode_tab[(size_t)v * K + j]});
         }
         for (int i = (int)present.size(); i <= K; ++i) pm[i] = pre;
         for (int i = (int)present.size(); i < K; ++i) pm[K + 1 + i] = present.empty() ? 0 : present[0].second;

@@ -86,6 +86,7 @@ struct InstInfo {
 struct NodeView {
     int32_t view;
     int32_t slot;
+    int64_t tab;          // count-table index of the node's first chunk in this view
 };
 
 template <int DT>

@@ -167,7 +167,7 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
         for (auto& pk : present) {
             vnode_tab[(size_t)v * K + pk.second] = tab;
             tab += nd[pk.first].nchunks;
-            per_node[pk.first].push_back({v, pk.second});
+            per_node[pk.first].push_back({v, pk.second, vnode_tab[(size_t)v * K + pk.second]});
         }
     }
     view_tab[V] = tab;

@@ -474,102 +474,139 @@ struct EmitOut {
     uint32_t* ntile;      // tile pairs of the instance
 };
 
-template <bool EMIT>
+template <int DT>
+__device__ __forceinline__ void stage_geometry(const NodeDesc& nd, int c, int lane, WarpWork& W, Gauss& g, bool& valid);
+template <int DT>
+__device__ __forceinline__ void stage_sh(const NodeDesc& nd, int c, int lane, float* __restrict__ sh_smem);
+
+// The emit pass stages the chunk's geometry and SH coefficients at its first visible view
+// (lazily: chunks no view sees read nothing but their count-table entries).
+template <bool EMIT, int DT>
 __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lane, const NodeView* __restrict__ entries,
                                               int n_entries, int v0, int v1, const ViewDesc* __restrict__ views,
                                               const VNode* __restrict__ vnodes, int K, const Params& P, const Gauss& gme,
-                                              bool valid, const ChunkBound& cb, WarpWork& W, const float* __restrict__ shc,
+                                              bool valid, const ChunkBound& cb, WarpWork& W, float* __restrict__ shc,
                                               uint2* __restrict__ counts, const uint32_t* __restrict__ inst_off,
                                               uint32_t inst_base, const EmitOut& out) {
     WarpViews& WV = W.WV;
-    for (int eb = 0; eb < n_entries; eb += kViewBlock) {
-        const int nvb = min(kViewBlock, n_entries - eb);
-        // 1. survivors of each view of the block: lane j fetches the table entries of view j
-        //    (one round of loads for the whole block), then one ballot per view (count pass)
-        bool sees = false;
-        if (lane < nvb) {
-            const int j = lane;
-            const NodeView w = entries[eb + j];
-            const bool in = w.view >= v0 && w.view < v1;
-            WV.vv[j] = in ? w.view * K + w.slot : -1;
-            WV.vis[j] = 0; WV.hits[j] = 0; WV.mask[j] = 0;
-            if (in) {
-                const int64_t t = vnodes[w.view * K + w.slot].tab + c;
-                WV.tab[j] = t;
-                if constexpr (!EMIT) sees = chunk_may_be_visible(cb, vnodes[w.view * K + w.slot], views[w.view], P);
-                if constexpr (EMIT) {
-                    WV.mask[j] = counts[t].x;
-                    WV.ibase[j] = inst_off[t] - inst_base;
+    const uint32_t full = 0xffffffffu;
+    bool staged = false;
+    for (int rb = 0; rb < n_entries; rb += 32) {
+        // 1a. a round of 32 views, one per lane.  Count pass: the chunk's bounding ball against
+        //     the view (an entry it cannot reach gets its empty count right away); emit pass:
+        //     the view's visible-lane mask and record offset from the count table.
+        const int e = rb + lane;
+        bool keep = false;
+        int vv_l = -1;
+        int64_t t_l = 0;
+        uint32_t m_l = 0, ib_l = 0;
+        if (e < n_entries) {
+            const NodeView w = entries[e];
+            if (w.view >= v0 && w.view < v1) {
+                vv_l = w.view * K + w.slot;
+                t_l = w.tab + c;
+                if constexpr (!EMIT) {
+                    keep = chunk_may_be_visible(cb, vnodes[vv_l], views[w.view], P);
+                    if (!keep) counts[t_l] = make_uint2(0u, 0u);
+                } else {
+                    m_l = counts[t_l].x;
+                    keep = m_l != 0u;
+                    if (keep) ib_l = inst_off[t_l] - inst_base;
                 }
             }
         }
-        __syncwarp();
-        if constexpr (!EMIT) {
-            const uint32_t seen = __ballot_sync(0xffffffffu, sees);   // views the chunk's ball may reach
-            for (int j = 0; j < nvb; ++j) {
-                const int vvj = WV.vv[j];
-                if (vvj < 0 || !((seen >> j) & 1u)) continue;
-                const uint32_t m = __ballot_sync(0xffffffffu, valid && may_be_visible(gme, vnodes[vvj], views[vvj / K], P));
-                if (lane == 0) WV.mask[j] = m;
+        uint32_t surv = __ballot_sync(full, keep);
+        if constexpr (EMIT) {
+            if (surv && !staged) {
+                Gauss gs;
+                bool vs;
+                stage_geometry<DT>(nd, c, lane, W, gs, vs);
+                stage_sh<DT>(nd, c, lane, shc);
+                staged = true;
             }
         }
-        __syncwarp();
-        uint32_t n_items = 0;
-        for (int j = 0; j < nvb; ++j) n_items += __popc(WV.mask[j]);
-        // 2. project the survivors 32 at a time
-        for (uint32_t it = 0; it < n_items; it += 32) {
-            const uint32_t idx = it + (uint32_t)lane;
-            const bool act = idx < n_items;
-            int j = 0, g = 0;
-            if (act) decode_item(idx, WV, nvb, j, g);
-            Splat s;
-            bool vis = false;
-            Gauss gg;
-            const int vvj = act ? WV.vv[j] : 0;
-            if (act) {
-                get_geo(W.geo + g * kGeoStride, gg);
-                vis = project(gg, vnodes[vvj], views[vvj / K], P, s);
+        // 1b. the surviving views, kViewBlock at a time
+        while (surv) {
+            const int nvb = min(kViewBlock, __popc(surv));
+            const int src = nth_set_bit(surv, (uint32_t)min(lane, nvb - 1));
+            const int vv_j = __shfl_sync(full, vv_l, src);
+            const int64_t t_j = __shfl_sync(full, t_l, src);
+            const uint32_t m_j = __shfl_sync(full, m_l, src), ib_j = __shfl_sync(full, ib_l, src);
+            if (lane < nvb) {
+                WV.vv[lane] = vv_j;
+                WV.tab[lane] = t_j;
+                WV.vis[lane] = 0;
+                WV.hits[lane] = 0;
+                WV.mask[lane] = m_j;
+                WV.ibase[lane] = ib_j;
             }
-            const uint32_t area = vis ? (uint32_t)((s.tx1 - s.tx0 + 1) * (s.ty1 - s.ty0 + 1)) : 0u;
+            for (int q = 0; q < nvb; ++q) surv &= surv - 1u;   // drop the views taken
+            __syncwarp();
             if constexpr (!EMIT) {
-                // per-view totals of this flush: items are view-sorted, reduce each view's run
-                const uint32_t peers = __match_any_sync(0xffffffffu, act ? j : -1);
-                const uint32_t h = __reduce_add_sync(peers, area);
-                const uint32_t bits = __reduce_or_sync(peers, vis ? (1u << g) : 0u);
-                if (act && (peers & ((1u << lane) - 1u)) == 0) { WV.hits[j] += h; WV.vis[j] |= bits; }
-            } else {
-                const uint32_t excl = warp_excl_scan(area);
-                const uint32_t total = __shfl_sync(0xffffffffu, excl + area, 31);
-                if (vis) stash_splat(W.S, lane, s, excl); else W.S.excl[lane] = excl;
-                W.S.hits[lane] = 0;
-                uint32_t r = 0;
-                if (act && !vis) atomicOr(P.err, kErrMismatch);
-                if (vis) {
-                    r = WV.ibase[j] + __popc(WV.mask[j] & ((1u << g) - 1u));
-                    float rgb[3];
-                    sh_colour(nd.deg, shc + g * kShStride, gg, vnodes[vvj], rgb);
-                    const int64_t i = (int64_t)c * kChunk + g;
-                    const float op = 1.f / (1.f + __expf(-__ldg(nd.opac + i)));
-                    Record R;
-                    R.r0 = make_float4(s.u, s.v, op, s.z);
-                    R.r1 = make_float4(s.qa, s.qb, s.qc, __uint_as_float((uint32_t)s.x0 | ((uint32_t)s.x1 << 16)));
-                    R.r2 = make_float4(rgb[0], rgb[1], rgb[2], __uint_as_float((uint32_t)s.y0 | ((uint32_t)s.y1 << 16)));
-                    out.rec[r] = R;
-                    out.info[r] = InstInfo{(uint32_t)(nd.gbase + i), (uint32_t)vvj};
-                    out.dkey[r] = min(__float_as_uint(s.z) - P.zbase, (1u << kZBits) - 1u);
-                    out.ival[r] = r;
+                for (int j = 0; j < nvb; ++j) {
+                    const int vvj = WV.vv[j];
+                    const uint32_t m = __ballot_sync(full, valid && may_be_visible(gme, vnodes[vvj], views[vvj / K], P));
+                    if (lane == 0) WV.mask[j] = m;
+                }
+            }
+            __syncwarp();
+            uint32_t n_items = 0;
+            for (int j = 0; j < nvb; ++j) n_items += __popc(WV.mask[j]);
+            // 2. project the survivors 32 at a time
+            for (uint32_t it = 0; it < n_items; it += 32) {
+                const uint32_t idx = it + (uint32_t)lane;
+                const bool act = idx < n_items;
+                int j = 0, g = 0;
+                if (act) decode_item(idx, WV, nvb, j, g);
+                Splat s;
+                bool vis = false;
+                Gauss gg;
+                const int vvj = act ? WV.vv[j] : 0;
+                if (act) {
+                    get_geo(W.geo + g * kGeoStride, gg);
+                    vis = project(gg, vnodes[vvj], views[vvj / K], P, s);
+                }
+                const uint32_t area = vis ? (uint32_t)((s.tx1 - s.tx0 + 1) * (s.ty1 - s.ty0 + 1)) : 0u;
+                if constexpr (!EMIT) {
+                    // per-view totals of this flush: items are view-sorted, reduce each view's run
+                    const uint32_t peers = __match_any_sync(0xffffffffu, act ? j : -1);
+                    const uint32_t h = __reduce_add_sync(peers, area);
+                    const uint32_t bits = __reduce_or_sync(peers, vis ? (1u << g) : 0u);
+                    if (act && (peers & ((1u << lane) - 1u)) == 0) { WV.hits[j] += h; WV.vis[j] |= bits; }
+                } else {
+                    const uint32_t excl = warp_excl_scan(area);
+                    const uint32_t total = __shfl_sync(0xffffffffu, excl + area, 31);
+                    if (vis) stash_splat(W.S, lane, s, excl); else W.S.excl[lane] = excl;
+                    W.S.hits[lane] = 0;
+                    uint32_t r = 0;
+                    if (act && !vis) atomicOr(P.err, kErrMismatch);
+                    if (vis) {
+                        r = WV.ibase[j] + __popc(WV.mask[j] & ((1u << g) - 1u));
+                        float rgb[3];
+                        sh_colour(nd.deg, shc + g * kShStride, gg, vnodes[vvj], rgb);
+                        const int64_t i = (int64_t)c * kChunk + g;
+                        const float op = 1.f / (1.f + __expf(-__ldg(nd.opac + i)));
+                        Record R;
+                        R.r0 = make_float4(s.u, s.v, op, s.z);
+                        R.r1 = make_float4(s.qa, s.qb, s.qc, __uint_as_float((uint32_t)s.x0 | ((uint32_t)s.x1 << 16)));
+                        R.r2 = make_float4(rgb[0], rgb[1], rgb[2], __uint_as_float((uint32_t)s.y0 | ((uint32_t)s.y1 << 16)));
+                        out.rec[r] = R;
+                        out.info[r] = InstInfo{(uint32_t)(nd.gbase + i), (uint32_t)vvj};
+                        out.dkey[r] = min(__float_as_uint(s.z) - P.zbase, (1u << kZBits) - 1u);
+                        out.ival[r] = r;
+                    }
+                    __syncwarp();
+                    walk_count(W.S, lane, total, P);
+                    if (vis) out.ntile[r] = W.S.hits[lane];
                 }
                 __syncwarp();
-                walk_count(W.S, lane, total, P);
-                if (vis) out.ntile[r] = W.S.hits[lane];
+            }
+            // 3. count-table entries of the block
+            if constexpr (!EMIT) {
+                if (lane < nvb) counts[WV.tab[lane]] = make_uint2(WV.vis[lane], WV.hits[lane]);
             }
             __syncwarp();
         }
-        // 3. count-table entries of the block
-        if constexpr (!EMIT) {
-            if (lane < nvb && WV.vv[lane] >= 0) counts[WV.tab[lane]] = make_uint2(WV.vis[lane], WV.hits[lane]);
-        }
-        __syncwarp();
     }
 }
 
@@ -603,8 +640,8 @@ __global__ void __launch_bounds__(kCountWarps * 32) k_count_batched(const NodeDe
     bool valid;
     stage_geometry<DT>(nd, c, lane, W, g, valid);
     const ChunkBound cb = chunk_bound(g, valid);
-    process_chunk<false>(nd, c, lane, nv + nv_off[k], nv_off[k + 1] - nv_off[k], v0, v1, views, vnodes, K, P, g, valid,
-                         cb, W, nullptr, counts, nullptr, 0, EmitOut{});
+    process_chunk<false, DT>(nd, c, lane, nv + nv_off[k], nv_off[k + 1] - nv_off[k], v0, v1, views, vnodes, K, P, g,
+                             valid, cb, W, nullptr, counts, nullptr, 0, EmitOut{});
 }
 
 // Plain mode: the chunks of one view.  pmap = [K+1 prefix chunk counts in node-id order, K slots].
@@ -627,9 +664,9 @@ __global__ void __launch_bounds__(kCountWarps * 32) k_count_plain(const NodeDesc
     bool valid;
     stage_geometry<DT>(nd, c, lane, W, g, valid);
     const ChunkBound cb = chunk_bound(g, valid);
-    const NodeView one{v, slot};
-    process_chunk<false>(nd, c, lane, &one, 1, v, v + 1, views, vnodes, K, P, g, valid, cb, W, nullptr, counts, nullptr,
-                         0, EmitOut{});
+    const NodeView one{v, slot, vnodes[v * K + slot].tab};
+    process_chunk<false, DT>(nd, c, lane, &one, 1, v, v + 1, views, vnodes, K, P, g, valid, cb, W, nullptr, counts,
+                             nullptr, 0, EmitOut{});
 }
 
 template <int DT>
@@ -648,12 +685,9 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_emit_batched(const NodeDesc
     const NodeDesc& nd = nodes[k];
     if (nd.dtype != DT) return;
     const int c = chunk - nd.chunk0;
-    Gauss g;
-    bool valid;
-    stage_geometry<DT>(nd, c, lane, W, g, valid);
-    stage_sh<DT>(nd, c, lane, shc[wib]);
-    process_chunk<true>(nd, c, lane, nv + nv_off[k], nv_off[k + 1] - nv_off[k], v0, v1, views, vnodes, K, P, g, valid,
-                        ChunkBound{}, W, shc[wib], const_cast<uint2*>(counts), inst_off, inst_base, out);
+    process_chunk<true, DT>(nd, c, lane, nv + nv_off[k], nv_off[k + 1] - nv_off[k], v0, v1, views, vnodes, K, P,
+                            Gauss{}, false, ChunkBound{}, W, shc[wib], const_cast<uint2*>(counts), inst_off, inst_base,
+                            out);
 }
 
 template <int DT>
@@ -673,13 +707,9 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_emit_plain(const NodeDesc* 
     const NodeDesc& nd = nodes[vnodes[v * K + slot].node];
     if (nd.dtype != DT) return;
     const int c = w - pmap[lo];
-    Gauss g;
-    bool valid;
-    stage_geometry<DT>(nd, c, lane, W, g, valid);
-    stage_sh<DT>(nd, c, lane, shc[wib]);
-    const NodeView one{v, slot};
-    process_chunk<true>(nd, c, lane, &one, 1, v, v + 1, views, vnodes, K, P, g, valid, ChunkBound{}, W, shc[wib],
-                        const_cast<uint2*>(counts), inst_off, inst_base, out);
+    const NodeView one{v, slot, vnodes[v * K + slot].tab};
+    process_chunk<true, DT>(nd, c, lane, &one, 1, v, v + 1, views, vnodes, K, P, Gauss{}, false, ChunkBound{}, W,
+                            shc[wib], const_cast<uint2*>(counts), inst_off, inst_base, out);
 }
 
 // ------------------------------------------------------------------ exclusive scan of the count table
