@@ -112,11 +112,12 @@ __global__ void __launch_bounds__(kScanThreads) k_tscan_final(const uint32_t* __
     }
 }
 
-// Per-warp state of the pair walk: lane l holds depth-ordered instance i0 + l.
+// Per-warp state of the pair walk: item l is depth-ordered instance i0 + l.
 struct PairWarp {
-    float u[32], v[32], qa[32], qb[32], qc[32];
-    int32_t tx0[32], ty0[32], tw[32], x0[32], x1[32], y0[32], y1[32], tbase[32], tiles_x[32];
-    uint32_t excl[32], off[32], end[32], run[32], rec[32];
+    float4 a[32];          // (u, v, qa, qb)
+    float4 b[32];          // (qc, x-box, y-box, tile origin)
+    int4 c[32];            // (rectangle width in tiles, first tile of the view in the group, view tiles_x, record)
+    uint32_t excl[32], off[32], end[32], run[32];
 };
 
 __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(const ViewDesc* __restrict__ views, int K,
@@ -140,53 +141,46 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(const ViewDesc* __res
         const uint32_t r = order[item];
         const Record& R = rec[r];
         const float4 r0 = R.r0, r1 = R.r1;
-        const uint32_t bx = __float_as_uint(r1.w), by = __float_as_uint(R.r2.w);
-        const int x0 = (int)(bx & 0xFFFFu), x1 = (int)(bx >> 16), y0 = (int)(by & 0xFFFFu), y1 = (int)(by >> 16);
-        const int tx0 = x0 / P.tile_w, tx1 = x1 / P.tile_w, ty0 = y0 / P.tile_h, ty1 = y1 / P.tile_h;
+        const float byf = R.r2.w;
+        const uint32_t bx = __float_as_uint(r1.w), by = __float_as_uint(byf);
+        const int tx0 = (int)(bx & 0xFFFFu) / P.tile_w, tx1 = (int)(bx >> 16) / P.tile_w;
+        const int ty0 = (int)(by & 0xFFFFu) / P.tile_h, ty1 = (int)(by >> 16) / P.tile_h;
         const ViewDesc& vd = views[info[r].view / (uint32_t)K];
-        S.u[lane] = r0.x; S.v[lane] = r0.y; S.qa[lane] = r1.x; S.qb[lane] = r1.y; S.qc[lane] = r1.z;
-        S.x0[lane] = x0; S.x1[lane] = x1; S.y0[lane] = y0; S.y1[lane] = y1;
-        S.tx0[lane] = tx0; S.ty0[lane] = ty0; S.tw[lane] = tx1 - tx0 + 1;
-        S.tbase[lane] = vd.tile_base - P.tile0; S.tiles_x[lane] = vd.tiles_x;
-        S.off[lane] = poff[item]; S.end[lane] = poff[item + 1]; S.run[lane] = 0; S.rec[lane] = r;
+        S.a[lane] = make_float4(r0.x, r0.y, r1.x, r1.y);
+        S.b[lane] = make_float4(r1.z, r1.w, byf, pack_u16x2((uint32_t)tx0, (uint32_t)ty0));
+        S.c[lane] = make_int4(tx1 - tx0 + 1, vd.tile_base - P.tile0, vd.tiles_x, (int)r);
+        S.off[lane] = poff[item];
+        S.end[lane] = poff[item + 1];
+        S.run[lane] = 0;
         area = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
     }
-    uint32_t excl = area;
+    uint32_t incl = area;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, excl, o);
-        if (lane >= o) excl += t;
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
     }
-    const uint32_t total = __shfl_sync(0xffffffffu, excl, 31);
-    S.excl[lane] = excl - area;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t my = incl - area;
+    S.excl[lane] = my;
     __syncwarp();
     const uint32_t lt = (1u << lane) - 1u;
     for (uint32_t base = 0; base < total; base += 32) {
+        const int o = walk_owner_of(lane, act, act ? my : total, base);
         const uint32_t f = base + (uint32_t)lane;
         bool hit = false;
-        int o = -1, tx = 0, ty = 0;
+        int tx = 0, ty = 0;
+        int4 cc = make_int4(0, 0, 0, 0);
         if (f < total) {
-            int lo = 0, hi = 31;
-#pragma unroll
-            for (int it = 0; it < 5; ++it) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (S.excl[mid] <= f) lo = mid; else hi = mid - 1;
-            }
-            o = lo;
-            const uint32_t r = f - S.excl[o];
-            const uint32_t wd = (uint32_t)S.tw[o];
-            const uint32_t row = r / wd;
-            tx = S.tx0[o] + (int)(r - row * wd);
-            ty = S.ty0[o] + (int)row;
-            hit = tile_hit(S.u[o], S.v[o], S.qa[o], S.qb[o], S.qc[o], S.x0[o], S.x1[o], S.y0[o], S.y1[o], tx, ty,
-                           P.tile_w, P.tile_h, P.qbin, P.exact_tile_test);
+            cc = S.c[o];
+            hit = walk_tile(S.a[o], S.b[o], cc.x, f - S.excl[o], P, tx, ty);
         }
         const uint32_t peers = __match_any_sync(0xffffffffu, hit ? o : -1);
         if (hit) {
             const uint32_t pos = S.off[o] + S.run[o] + __popc(peers & lt);
             if (pos < S.end[o] && pos < cap) {
-                tkeys[pos] = (uint32_t)(S.tbase[o] + ty * S.tiles_x[o] + tx);
-                tvals[pos] = S.rec[o];
+                tkeys[pos] = (uint32_t)(cc.y + ty * cc.z + tx);
+                tvals[pos] = (uint32_t)cc.w;
             } else {
                 atomicOr(P.err, pos < cap ? kErrMismatch : kErrCapacity);
             }

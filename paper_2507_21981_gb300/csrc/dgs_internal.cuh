@@ -124,6 +124,27 @@ __device__ __forceinline__ bool ellipse_meets(float qa, float qb, float qc, floa
     return m <= qlim;
 }
 
+// Flattened tile-rectangle walk shared by the emission count and the pair writer.  An item is
+// one instance with a = (u, v, qa, qb) and b = (qc, x-box, y-box, tile origin), boxes packed
+// lo | hi << 16 and the origin tx0 | ty0 << 16; its rectangle is tw tiles wide.  Candidate r of
+// an item is tile (tx0 + r % tw, ty0 + r / tw).
+__device__ __forceinline__ float pack_u16x2(uint32_t lo, uint32_t hi) { return __uint_as_float(lo | (hi << 16)); }
+
+__device__ __forceinline__ bool walk_tile(const float4& a, const float4& b, int tw, uint32_t r, const Params& P,
+                                          int& tx, int& ty);
+
+// Items are dense (lane k of the warp holds item k for k < n_items) and my_excl is item
+// lane's exclusive prefix of rectangle areas (>= 1 each).  For the 32 candidates of a flush
+// starting at `base`, the owner of candidate base + lane is the last item whose prefix is
+// <= base + lane: the items at or before `base` (one ballot) plus those starting inside the
+// flush up to the candidate (one OR-reduction of start bits).
+__device__ __forceinline__ int walk_owner_of(int lane, bool item, uint32_t my_excl, uint32_t base) {
+    const int first = __popc(__ballot_sync(0xffffffffu, item && my_excl <= base)) - 1;
+    const uint32_t d = my_excl - base;
+    const uint32_t starts = __reduce_or_sync(0xffffffffu, (item && my_excl > base && d < 32u) ? (1u << d) : 0u);
+    return first + __popc(starts & ((2u << lane) - 1u));
+}
+
 // Compositing arithmetic shared by the forward pass and its adjoint, so both take the same
 // FP32 decisions.  exp(-q/2) = 2^(c q) with c = -log2(e)/2: a staged record carries
 // (c qa, qb, c qc), each coefficient one FP32 product, and the pixel's exponent is
@@ -154,6 +175,16 @@ __device__ __forceinline__ bool tile_hit(float u, float v, float qa, float qb, f
     const int py0 = max(ty * tile_h, y0), py1 = min(ty * tile_h + tile_h - 1, y1);
     return ellipse_meets(qa, qb, qc, qbin, (float)px0 + 0.5f - u, (float)px1 + 0.5f - u, (float)py0 + 0.5f - v,
                          (float)py1 + 0.5f - v);
+}
+
+__device__ __forceinline__ bool walk_tile(const float4& a, const float4& b, int tw, uint32_t r, const Params& P,
+                                          int& tx, int& ty) {
+    const uint32_t row = r / (uint32_t)tw;
+    const uint32_t org = __float_as_uint(b.w), bx = __float_as_uint(b.y), by = __float_as_uint(b.z);
+    tx = (int)(org & 0xFFFFu) + (int)(r - row * (uint32_t)tw);
+    ty = (int)(org >> 16) + (int)row;
+    return tile_hit(a.x, a.y, a.z, a.w, b.x, (int)(bx & 0xFFFFu), (int)(bx >> 16), (int)(by & 0xFFFFu),
+                    (int)(by >> 16), tx, ty, P.tile_w, P.tile_h, P.qbin, P.exact_tile_test);
 }
 
 __device__ __forceinline__ uint64_t global_timer_ns() {

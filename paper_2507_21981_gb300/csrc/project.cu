@@ -274,14 +274,15 @@ __device__ __forceinline__ bool chunk_may_be_visible(const ChunkBound& b, const 
     return !(fl + ex < 0.f || fr + ex < 0.f || ft + ey < 0.f || fb + ey < 0.f);
 }
 
-// Emission walk: the union of the warp's tile rectangles, flattened in (lane, row-major tile)
-// order, is tested 32 candidates at a time; lane l of a flush holds one visible instance and
-// S.hits[l] receives its number of tile pairs.  The pair kernel walks the same rectangles with
-// the same test on the same stored values.
+// Emission walk: the union of the tile rectangles of a flush's visible instances (dense items
+// in lane order), flattened in (item, row-major tile) order, is tested 32 candidates at a
+// time; S.hits[k] receives item k's number of tile pairs.  The pair kernel walks the same
+// rectangles with the same test on the same stored values.
 struct WarpSplats {
-    float u[32], v[32], qa[32], qb[32], qc[32];
-    int32_t tx0[32], ty0[32], tw[32], x0[32], x1[32], y0[32], y1[32];
-    uint32_t excl[32];     // exclusive prefix of the items' tile-rectangle areas
+    float4 a[32];          // (u, v, qa, qb)
+    float4 b[32];          // (qc, x-box, y-box, tile origin)
+    int32_t tw[32];        // rectangle width in tiles
+    uint32_t excl[32];     // exclusive prefix of the items' rectangle areas
     uint32_t hits[32];     // tile pairs of the item
 };
 
@@ -296,38 +297,26 @@ struct WarpViews {
     uint32_t ibase[kViewBlock];   // emit: first record of (view j, chunk) relative to the group
 };
 
-__device__ __forceinline__ void stash_splat(WarpSplats& S, int lane, const Splat& s, uint32_t excl) {
-    S.u[lane] = s.u; S.v[lane] = s.v; S.qa[lane] = s.qa; S.qb[lane] = s.qb; S.qc[lane] = s.qc;
-    S.tx0[lane] = s.tx0; S.ty0[lane] = s.ty0; S.tw[lane] = s.tx1 - s.tx0 + 1;
-    S.x0[lane] = s.x0; S.x1[lane] = s.x1; S.y0[lane] = s.y0; S.y1[lane] = s.y1;
-    S.excl[lane] = excl;
+__device__ __forceinline__ void stash_splat(WarpSplats& S, int k, const Splat& s, uint32_t excl) {
+    S.a[k] = make_float4(s.u, s.v, s.qa, s.qb);
+    S.b[k] = make_float4(s.qc, pack_u16x2((uint32_t)s.x0, (uint32_t)s.x1), pack_u16x2((uint32_t)s.y0, (uint32_t)s.y1),
+                         pack_u16x2((uint32_t)s.tx0, (uint32_t)s.ty0));
+    S.tw[k] = s.tx1 - s.tx0 + 1;
+    S.excl[k] = excl;
+    S.hits[k] = 0;
 }
 
-// Owner of flattened candidate f: the last item whose rectangle starts at or before f.
-__device__ __forceinline__ int walk_owner(const uint32_t* excl, uint32_t f) {
-    int lo = 0, hi = 31;
-#pragma unroll
-    for (int it = 0; it < 5; ++it) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (excl[mid] <= f) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ void walk_count(WarpSplats& S, int lane, uint32_t total, const Params& P) {
+__device__ __forceinline__ void walk_count(WarpSplats& S, int lane, int n_items, uint32_t total, const Params& P) {
     const uint32_t lt = (1u << lane) - 1u;
+    const bool item = lane < n_items;
+    const uint32_t my = item ? S.excl[lane] : total;
     for (uint32_t base = 0; base < total; base += 32) {
+        const int o = walk_owner_of(lane, item, my, base);
         const uint32_t f = base + (uint32_t)lane;
         bool hit = false;
-        int o = -1;
         if (f < total) {
-            o = walk_owner(S.excl, f);
-            const uint32_t r = f - S.excl[o];
-            const uint32_t w = (uint32_t)S.tw[o];
-            const uint32_t row = r / w;
-            hit = tile_hit(S.u[o], S.v[o], S.qa[o], S.qb[o], S.qc[o], S.x0[o], S.x1[o], S.y0[o], S.y1[o],
-                           S.tx0[o] + (int)(r - row * w), S.ty0[o] + (int)row, P.tile_w, P.tile_h, P.qbin,
-                           P.exact_tile_test);
+            int tx, ty;
+            hit = walk_tile(S.a[o], S.b[o], S.tw[o], f - S.excl[o], P, tx, ty);
         }
         const uint32_t peers = __match_any_sync(0xffffffffu, hit ? o : -1);
         if (hit && (peers & lt) == 0) S.hits[o] += __popc(peers);
@@ -576,8 +565,9 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
                 } else {
                     const uint32_t excl = warp_excl_scan(area);
                     const uint32_t total = __shfl_sync(0xffffffffu, excl + area, 31);
-                    if (vis) stash_splat(W.S, lane, s, excl); else W.S.excl[lane] = excl;
-                    W.S.hits[lane] = 0;
+                    const uint32_t vmask = __ballot_sync(0xffffffffu, vis);
+                    const int slot = __popc(vmask & ((1u << lane) - 1u));   // dense item number
+                    if (vis) stash_splat(W.S, slot, s, excl);
                     uint32_t r = 0;
                     if (act && !vis) atomicOr(P.err, kErrMismatch);
                     if (vis) {
@@ -596,8 +586,8 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
                         out.ival[r] = r;
                     }
                     __syncwarp();
-                    walk_count(W.S, lane, total, P);
-                    if (vis) out.ntile[r] = W.S.hits[lane];
+                    walk_count(W.S, lane, __popc(vmask), total, P);
+                    if (vis) out.ntile[r] = W.S.hits[slot];
                 }
                 __syncwarp();
             }
