@@ -43,6 +43,24 @@ def _dist():
     return rank, world, local
 
 
+def rank_scene(rank: int, envs: int, **kw):
+    """Weak scaling: rank r renders its own batch of `envs` environments of the benchmark law
+    (seed 1 + r); no data crosses ranks."""
+    from paper_2507_21981_gb300 import scenes
+    return scenes.config2(seed=1 + rank, n_envs=envs, **kw)
+
+
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """The slowest rank's time (the only collective of the benchmark)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """Samples nvidia-smi clocks and throttle reasons in the background during the timed region."""
 
@@ -260,10 +278,9 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    from paper_2507_21981_gb300 import scenes
     from paper_2507_21981_gb300.render import DeviceScene, Renderer
 
-    sc = scenes.config2(seed=1 + rank, n_envs=args.envs)
+    sc = rank_scene(rank, args.envs)
     ds = DeviceScene(sc, device=dev, spatial_order=True)
     stream = torch.cuda.current_stream(dev)
     px_per_step = ds.n_pixels
@@ -301,10 +318,7 @@ def main():
                               "kernel_ms_per_step": {k: v / args.steps for k, v in ktimes.items()},
                               "render_stats": stats}))
         return 0
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     value = px_per_step * world / (ms / 1e3) / 1e6
 
     # ---------------------------------------------------------------- the same batch as graph replays
@@ -312,7 +326,7 @@ def main():
     for _ in range(args.warmup):
         rg.render(ds, out=out)
     barrier()
-    ms_graph = _time_renders(rg, ds, out, args.steps, stream)
+    ms_graph = max_over_ranks(_time_renders(rg, ds, out, args.steps, stream), world, dev)
     graph_path = rg.stats()["path"]
     graph_value = px_per_step * world / (ms_graph / 1e3) / 1e6
     rg.close()
@@ -338,7 +352,7 @@ def main():
         e2e_step()
     ev1.record(stream)
     barrier()
-    ms_e2e = ev0.elapsed_time(ev1) / args.steps
+    ms_e2e = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
     e2e_value = px_per_step * world / (ms_e2e / 1e3) / 1e6
     h2d = poses_host.numel() * 4
     d2h = (host_rgb.numel() + host_depth.numel()) * 4
@@ -353,13 +367,13 @@ def main():
         rp.render(ds, out=out)
     ev1.record(stream)
     barrier()
-    ms_plain = ev0.elapsed_time(ev1) / args.plain_steps
+    ms_plain = max_over_ranks(ev0.elapsed_time(ev1) / args.plain_steps, world, dev)
     plain_value = px_per_step * world / (ms_plain / 1e3) / 1e6
 
     # ---------------------------------------------------------------- fwd+bwd at 500k Gaussians (one 800x800 view)
     fb = fwd_bwd_500k(dev, args.warmup, max(3, args.steps // 4))
     extra = {}
-    if not args.no_extra:
+    if not args.no_extra and world == 1:       # single-GPU workloads, reported at N = 1
         extra["ragged"] = ragged_graph(dev, args.warmup, max(3, args.steps // 4))
         extra["precision_scale"] = precision_scale(dev, args.warmup, max(3, args.steps // 4))
 

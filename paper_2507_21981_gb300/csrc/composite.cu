@@ -29,7 +29,7 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, uint32_t n, const ui
 // test with the binning margin), stages them in list order in its own shared memory and
 // composites them; it stops once its 32 pixels have terminated.
 template <bool COUNT>
-__global__ void __launch_bounds__(256) k_composite(const ViewDesc* __restrict__ views, int v0, int nv,
+__global__ void __launch_bounds__(256, 6) k_composite(const ViewDesc* __restrict__ views, int v0, int nv,
                                                    const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                                                    const Record* __restrict__ rec, Params P, float* __restrict__ out_rgb,
                                                    float* __restrict__ out_depth, float* __restrict__ out_alpha,

@@ -152,3 +152,30 @@ def test_autotune_picks_a_candidate_and_renders_with_it(mode):
     best2, times2, _ = r.autotune(ds, candidates=[(8, 8), (16, 16)], reps=1)
     assert set(times2) == {(8, 8), (16, 16)} and best2 in times2
     r.close()
+
+
+def test_config3_full_size_graph_sampled_views():
+    """The uneven workload at full size (256 envs, 1-12 assets of 5k-200k Gaussians, 1-3
+    cameras at three resolutions, 504 views, Z-ordered nodes) rendered as a graph replay after
+    dgs_autotune; one sampled view of each resolution against the oracle."""
+    from paper_2507_21981_gb300.render import DeviceScene, Renderer
+    sc = S.config3(seed=1)
+    ds = DeviceScene(sc, device="cuda:0", spatial_order=True)
+    r = Renderer(mode="graph")
+    r.autotune(ds, reps=1)
+    rgb, depth, alpha = [t.cpu().numpy() for t in r.render(ds)]
+    assert r.stats()["path"] == 1
+    r.close()
+    rng = np.random.default_rng(5)
+    picked = {}
+    for v in rng.permutation(sc.n_views):
+        w, h = (int(x) for x in sc.view_res(int(v)))
+        picked.setdefault((w, h), int(v))
+    pk = O.oracle._Packed(ds.scene)
+    for (w, h), v in sorted(picked.items()):
+        e, c = sc.views[v]
+        ref = O.render_view(ds.scene, e, c, O.OracleOptions(), pk)
+        sl = ds.view_slice(v)
+        bad, rep = compare_view(rgb[sl].reshape(h, w, 3), depth[sl].reshape(h, w), ref, alpha[sl].reshape(h, w))
+        assert bad == 0, (w, h, rep)
+    assert len(picked) == 3

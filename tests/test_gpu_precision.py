@@ -64,3 +64,39 @@ def test_low_precision_backward_matches_oracle_on_rounded_attributes():
     rs = _rounded(sc, "bf16")
     # the GPU reads BF16 storage of sc; the oracle sees the same rounded values (rs)
     _compare(rs, *_gradients(sc, seed=8, dtype="bf16", oracle_scene=rs))
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_config5_full_size_sampled_views(dtype):
+    """The precision-and-scale workload at full size (3M-Gaussian room + 6 x 50k objects,
+    128 envs x 3 cameras, nodes in Z-order, graph replay): four seeded sampled views against
+    the oracle fed the same rounded attributes (compute error, FP32 tolerance) and against the
+    oracle fed FP32 attributes (storage error: max-abs and PSNR, reported)."""
+    from paper_2507_21981_gb300.render import DeviceScene, Renderer
+    sc = S.config5(seed=1)
+    ds = DeviceScene(sc, device="cuda:0", dtype=dtype, spatial_order=True)
+    r = Renderer(mode="graph")
+    for _ in range(2):
+        out = [t.cpu().numpy() for t in r.render(ds)]
+    assert r.stats()["path"] == 1
+    r.close()
+    rgb, depth, alpha = out
+    osc = ds.scene
+    rs = _rounded(osc, dtype)
+    pk_r, pk_f = O.oracle._Packed(rs), O.oracle._Packed(osc)
+    views = sorted(int(v) for v in np.random.default_rng(11).choice(sc.n_views, 4, replace=False))
+    lines = []
+    for v in views:
+        e, c = sc.views[v]
+        sl = ds.view_slice(v)
+        ref = O.render_view(rs, e, c, O.OracleOptions(), pk_r)
+        H, W = ref.depth.shape
+        img = rgb[sl].reshape(H, W, 3)
+        bad, rep = compare_view(img, depth[sl].reshape(H, W), ref, alpha[sl].reshape(H, W))
+        assert bad == 0, rep
+        full = O.render_view(osc, e, c, O.OracleOptions(), pk_f)
+        err = np.abs(img - full.rgb)
+        psnr = 10 * np.log10(1.0 / max(float(np.mean(err ** 2)), 1e-30))
+        lines.append(f"view {v}: max-abs {err.max():.4f} PSNR {psnr:.1f} dB")
+        assert psnr > 25.0, lines[-1]
+    print(f"config 5 {dtype} storage error vs FP32 attributes: " + "; ".join(lines))
