@@ -142,7 +142,9 @@ int check_options(const dgs_options* o, std::string& why) {
         return 0;
     }
     const int area = o->tile_w * o->tile_h;
-    if (o->tile_w < 8 || o->tile_h < 4 || o->tile_w % 8 || o->tile_h % 4 || (area != 64 && area != 128 && area != 256)) {
+    // w = 8a, h = 4b with 32ab in {64, 128, 256}: both are powers of two
+    if (o->tile_w < 8 || o->tile_h < 4 || o->tile_w % 8 || o->tile_h % 4 || (area != 64 && area != 128 && area != 256) ||
+        (o->tile_w & (o->tile_w - 1)) || (o->tile_h & (o->tile_h - 1))) {
         why = "tile shape";
         return 0;
     }
@@ -440,6 +442,10 @@ int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* e
     P.qbin = o.q_max * 1.001f + 1e-3f;
     P.p_min = kHalfLog2e * o.q_max;
     P.tile_w = o.tile_w; P.tile_h = o.tile_h;
+    P.tile_sx = 0;
+    P.tile_sy = 0;
+    while ((1 << P.tile_sx) < o.tile_w) ++P.tile_sx;
+    while ((1 << P.tile_sy) < o.tile_h) ++P.tile_sy;
     P.exact_tile_test = o.exact_tile_test;
     P.tile0 = 0;
     {

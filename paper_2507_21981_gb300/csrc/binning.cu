@@ -143,8 +143,8 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(const ViewDesc* __res
         const float4 r0 = R.r0, r1 = R.r1;
         const float byf = R.r2.w;
         const uint32_t bx = __float_as_uint(r1.w), by = __float_as_uint(byf);
-        const int tx0 = (int)(bx & 0xFFFFu) / P.tile_w, tx1 = (int)(bx >> 16) / P.tile_w;
-        const int ty0 = (int)(by & 0xFFFFu) / P.tile_h, ty1 = (int)(by >> 16) / P.tile_h;
+        const int tx0 = (int)(bx & 0xFFFFu) >> P.tile_sx, tx1 = (int)(bx >> 16) >> P.tile_sx;
+        const int ty0 = (int)(by & 0xFFFFu) >> P.tile_sy, ty1 = (int)(by >> 16) >> P.tile_sy;
         const ViewDesc& vd = views[info[r].view / (uint32_t)K];
         S.a[lane] = make_float4(r0.x, r0.y, r1.x, r1.y);
         S.b[lane] = make_float4(r1.z, r1.w, byf, pack_u16x2((uint32_t)tx0, (uint32_t)ty0));

@@ -59,6 +59,7 @@ struct Params {
     float bg0, bg1, bg2;
     float qbin;           // binning limit on d^T conic d (q_max with an FP32 safety margin)
     int32_t tile_w, tile_h;
+    int32_t tile_sx, tile_sy; // log2 of tile_w, tile_h (valid tile shapes are powers of two)
     int32_t exact_tile_test;
     uint32_t zbase;       // float bits of 2^floor(log2 z_near)
     int32_t tile0;        // first global tile of the current view group
@@ -177,9 +178,19 @@ __device__ __forceinline__ bool tile_hit(float u, float v, float qa, float qb, f
                          (float)py1 + 0.5f - v);
 }
 
+// floor(r / w), w >= 1: below 2^22 a float estimate (within one of the quotient) and one
+// integer correction each way; larger r (a rectangle of more than 4M tiles) divides exactly.
+__device__ __forceinline__ uint32_t small_div(uint32_t r, uint32_t w) {
+    if (r >= (1u << 22)) return r / w;
+    uint32_t q = __float2uint_rz(__fdividef((float)r + 0.5f, (float)w));
+    if (q * w > r) --q;
+    if ((q + 1u) * w <= r) ++q;
+    return q;
+}
+
 __device__ __forceinline__ bool walk_tile(const float4& a, const float4& b, int tw, uint32_t r, const Params& P,
                                           int& tx, int& ty) {
-    const uint32_t row = r / (uint32_t)tw;
+    const uint32_t row = small_div(r, (uint32_t)tw);
     const uint32_t org = __float_as_uint(b.w), bx = __float_as_uint(b.y), by = __float_as_uint(b.z);
     tx = (int)(org & 0xFFFFu) + (int)(r - row * (uint32_t)tw);
     ty = (int)(org >> 16) + (int)row;

@@ -219,6 +219,10 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
     P.qbin = o.q_max * 1.001f + 1e-3f;
     P.p_min = kHalfLog2e * o.q_max;
     P.tile_w = o.tile_w; P.tile_h = o.tile_h;
+    P.tile_sx = 0;
+    P.tile_sy = 0;
+    while ((1 << P.tile_sx) < o.tile_w) ++P.tile_sx;
+    while ((1 << P.tile_sy) < o.tile_h) ++P.tile_sy;
     P.exact_tile_test = o.exact_tile_test;
     P.tile0 = 0;
     P.err = d_err;

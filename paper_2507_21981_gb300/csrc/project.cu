@@ -184,8 +184,8 @@ __device__ __forceinline__ bool project(const Gauss& g, const VNode& vn, const V
     s.x1 = (int)fminf(fx1, (float)(vd.W - 1));
     s.y0 = (int)fmaxf(fy0, 0.f);
     s.y1 = (int)fminf(fy1, (float)(vd.H - 1));
-    s.tx0 = s.x0 / P.tile_w; s.tx1 = s.x1 / P.tile_w;
-    s.ty0 = s.y0 / P.tile_h; s.ty1 = s.y1 / P.tile_h;
+    s.tx0 = s.x0 >> P.tile_sx; s.tx1 = s.x1 >> P.tile_sx;
+    s.ty0 = s.y0 >> P.tile_sy; s.ty1 = s.y1 >> P.tile_sy;
     return true;
 }
 
