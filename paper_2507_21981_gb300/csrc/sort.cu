@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) k_hist_scan(uint32_t* hist, int passes, i
 // One digit pass.  Thread t owns digits t, t + 256, ... (< 2^D) in the per-digit phases
 // (prefix over warps, look-back, block scan); digits are (key >> shift) & (2^D - 1).
 template <int D>
-__global__ void __launch_bounds__(kThreads) k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+__global__ void __launch_bounds__(kThreads, 3) k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                       uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t n,
                                                       const uint32_t* __restrict__ d_n, int shift,
                                                       const uint32_t* __restrict__ digit_off, uint32_t* status,
