@@ -99,7 +99,10 @@ typedef struct dgs_options {
     float bg[3];                /* background colour, default 0 */
     int32_t profile;            /* 1 = time each kernel class with CUDA events (dgs_kernel_times);
                                    2 = also count compositor work (dgs_stats), slower */
-    int32_t views_per_group;    /* batched mode: max views per group, 0 = automatic */
+    int32_t views_per_group;    /* batched mode: max views per group; 0 = automatic: a batch with at
+                                   least 2^22 tile pairs (bound) runs as two view groups on two
+                                   streams, one group's binning overlapping the other's compositing;
+                                   more groups only where the 2^30-pair limit needs them */
 } dgs_options;
 
 typedef struct dgs_ctx dgs_ctx;

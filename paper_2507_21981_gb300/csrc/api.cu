@@ -45,15 +45,26 @@ struct GraphKey {
     int64_t tile_w, tile_h, exact_tile_test;
 };
 
+// Workspace of one view group's lists.  dkey/ival: depth keys and instance numbers (depth
+// sort, ping-pong); ntile: pairs per instance; poff/tparts: pair offsets in depth order;
+// tkeys/tvals: (tile, instance) pairs (tile sort, ping-pong); ranges: per tile.
+struct ListBufs {
+    DevBuf records, info, dkey0, ival0, dkey1, ival1, ntile, poff, tparts, tkeys0, tvals0, tkeys1, tvals1, hist,
+        status, counters, ranges;
+    DevBuf* all[17] = {&records, &info, &dkey0, &ival0, &dkey1, &ival1, &ntile, &poff, &tparts, &tkeys0, &tvals0,
+                       &tkeys1, &tvals1, &hist, &status, &counters, &ranges};
+    ListBufs() = default;
+    ListBufs(const ListBufs&) = delete;
+    ListBufs& operator=(const ListBufs&) = delete;
+};
+
 struct dgs_ctx {
     dgs_options opt{};
     std::string err;
     int device = 0;
-    // dkey/ival: depth keys and instance numbers (depth sort, ping-pong); ntile: pairs per
-    // instance; poff/tparts: pair offsets in depth order; tkeys/tvals: (tile, instance) pairs
-    // (tile sort, ping-pong); totals: exact pairs per view group
-    DevBuf meta, counts, inst_off, pair_off, parts, records, info, dkey0, ival0, dkey1, ival1, ntile, poff, tparts,
-        tkeys0, tvals0, tkeys1, tvals1, hist, status, counters, ranges, errword, readback, inst_grad, gsizes, totals;
+    DevBuf meta, counts, inst_off, pair_off, parts, errword, readback, inst_grad, gsizes, totals;
+    ListBufs lists[2];                    // view groups alternate between two sets (two streams)
+    cudaStream_t aux_stream = nullptr;    // second stream of the eager sequence
     uint64_t gen = 0;                     // bumped whenever a workspace buffer is reallocated
     // graph replay (DGS_MODE_GRAPH)
     cudaStream_t cap_stream = nullptr;    // capture stream (the caller's may be the legacy stream)
@@ -196,6 +207,8 @@ __global__ void k_view_totals(const uint32_t* __restrict__ inst_off, const uint6
     out[i] = inst_off[view_tab[i]];
     out[n + i] = pair_off[view_tab[i]];
 }
+
+constexpr uint64_t kPipelinePairs = 1ull << 22;   // batches with this many pairs run as two groups
 
 int bits_for(uint64_t n) {   // smallest b with 2^b >= n (n >= 1)
     int b = 0;
@@ -495,26 +508,26 @@ void launch_front(dgs_ctx* ctx, const Batch& B, const Launch& L, Timer& tm) {
     tm.end();
 }
 
-// Workspace of the per-group lists: n_inst instances, n_pairs tile pairs, n_tiles tiles.
-int ensure_lists(dgs_ctx* ctx, uint64_t n_inst, uint64_t n_pairs, int64_t n_tiles) {
+// Workspace of one set of group lists: n_inst instances, n_pairs tile pairs, n_tiles tiles.
+int ensure_lists(dgs_ctx* ctx, ListBufs& lb, uint64_t n_inst, uint64_t n_pairs, int64_t n_tiles) {
     int rc;
     n_inst = std::max<uint64_t>(n_inst, 1);
     n_pairs = std::max<uint64_t>(n_pairs, 1);
-    if ((rc = ensure(ctx, ctx->records, sizeof(Record) * n_inst))) return rc;
-    if ((rc = ensure(ctx, ctx->info, sizeof(InstInfo) * n_inst))) return rc;
-    DevBuf* inst_bufs[] = {&ctx->dkey0, &ctx->ival0, &ctx->dkey1, &ctx->ival1, &ctx->ntile};
+    if ((rc = ensure(ctx, lb.records, sizeof(Record) * n_inst))) return rc;
+    if ((rc = ensure(ctx, lb.info, sizeof(InstInfo) * n_inst))) return rc;
+    DevBuf* inst_bufs[] = {&lb.dkey0, &lb.ival0, &lb.dkey1, &lb.ival1, &lb.ntile};
     for (DevBuf* b : inst_bufs)
         if ((rc = ensure(ctx, *b, sizeof(uint32_t) * n_inst))) return rc;
-    if ((rc = ensure(ctx, ctx->poff, sizeof(uint32_t) * (n_inst + 1)))) return rc;
-    if ((rc = ensure(ctx, ctx->tparts, sizeof(uint32_t) * tile_scan_parts((uint32_t)n_inst)))) return rc;
-    DevBuf* pair_bufs[] = {&ctx->tkeys0, &ctx->tvals0, &ctx->tkeys1, &ctx->tvals1};
+    if ((rc = ensure(ctx, lb.poff, sizeof(uint32_t) * (n_inst + 1)))) return rc;
+    if ((rc = ensure(ctx, lb.tparts, sizeof(uint32_t) * tile_scan_parts((uint32_t)n_inst)))) return rc;
+    DevBuf* pair_bufs[] = {&lb.tkeys0, &lb.tvals0, &lb.tkeys1, &lb.tvals1};
     for (DevBuf* b : pair_bufs)
         if ((rc = ensure(ctx, *b, sizeof(uint32_t) * n_pairs))) return rc;
-    if ((rc = ensure(ctx, ctx->hist, sizeof(uint32_t) * 4 * 1024))) return rc;
-    if ((rc = ensure(ctx, ctx->counters, sizeof(uint32_t) * 8))) return rc;
+    if ((rc = ensure(ctx, lb.hist, sizeof(uint32_t) * 4 * 1024))) return rc;
+    if ((rc = ensure(ctx, lb.counters, sizeof(uint32_t) * 8))) return rc;
     const uint64_t most = std::max(n_inst, n_pairs);
-    if ((rc = ensure(ctx, ctx->status, sizeof(uint32_t) * sort_status_words((uint32_t)most)))) return rc;
-    if ((rc = ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)std::max<int64_t>(n_tiles, 1)))) return rc;
+    if ((rc = ensure(ctx, lb.status, sizeof(uint32_t) * sort_status_words((uint32_t)most)))) return rc;
+    if ((rc = ensure(ctx, lb.ranges, sizeof(uint2) * (size_t)std::max<int64_t>(n_tiles, 1)))) return rc;
     return DGS_OK;
 }
 
@@ -551,10 +564,17 @@ int readback_groups(dgs_ctx* ctx, Batch& B, cudaStream_t stream, Timer& tm) {
     } else {
         int v0 = 0;
         const int cap_views = o.views_per_group > 0 ? o.views_per_group : V;
+        // automatic grouping of a large batch: two groups of about half the tile pairs each, so
+        // that the second group's binning overlaps the first group's compositing
+        int split_at = -1;
+        if (o.views_per_group == 0 && V >= 2 && pair_at[V] >= kPipelinePairs) {
+            split_at = 1;
+            while (split_at < V - 1 && pair_at[split_at] < pair_at[V] / 2) ++split_at;
+        }
         for (int v = 0; v < V; ++v) {
             if (pair_at[v + 1] - pair_at[v] > kMaxPairs)
                 return fail(ctx, DGS_ERR_CAPACITY, "one view has more than 2^30 tile pairs");
-            if (v > v0 && (pair_at[v + 1] - pair_at[v0] > kMaxPairs || v - v0 >= cap_views)) {
+            if (v > v0 && (pair_at[v + 1] - pair_at[v0] > kMaxPairs || v - v0 >= cap_views || v == split_at)) {
                 groups.push_back({v0, v});
                 v0 = v;
             }
@@ -577,7 +597,8 @@ int readback_groups(dgs_ctx* ctx, Batch& B, cudaStream_t stream, Timer& tm) {
     if (max_bits > 31) return fail(ctx, DGS_ERR_CAPACITY, "more than 2^31 tiles in a view group");
     ctx->stats.n_groups = (int32_t)groups.size();
     ctx->stats.key_bits = max_bits;
-    if ((rc = ensure_lists(ctx, max_inst, max_pairs, max_tiles))) return rc;
+    if ((rc = ensure_lists(ctx, ctx->lists[0], max_inst, max_pairs, max_tiles))) return rc;
+    if (groups.size() > 1 && (rc = ensure_lists(ctx, ctx->lists[1], max_inst, max_pairs, max_tiles))) return rc;
     B.groups = std::move(groups);
     B.inst_at = inst_at; B.pair_at = pair_at;
     return DGS_OK;
@@ -603,32 +624,33 @@ int prepare(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t*
 //   d_inst   device count of instances (graph replay) or null
 //   d_pairs  device word receiving the group's exact pair count (at most n_bound)
 // Returns the tile-sorted instance numbers in *vals.
-void enqueue_lists(dgs_ctx* ctx, const Batch& B, const Launch& L, Timer& tm, int v0, int v1, int n_tiles,
+void enqueue_lists(dgs_ctx* ctx, ListBufs& lb, const Batch& B, const Launch& L, Timer& tm, int v0, int v1, int n_tiles,
                    uint32_t inst_base, uint32_t n_inst, uint32_t n_bound, const uint32_t* d_inst, uint32_t* d_pairs,
                    const Params& P, const uint32_t** vals) {
+    (void)ctx;
     const int K = B.K;
     auto u32 = [](DevBuf& b) { return static_cast<uint32_t*>(b.p); };
-    Record* rec = static_cast<Record*>(ctx->records.p);
-    InstInfo* info = static_cast<InstInfo*>(ctx->info.p);
+    Record* rec = static_cast<Record*>(lb.records.p);
+    InstInfo* info = static_cast<InstInfo*>(lb.info.p);
     tm.begin(DGS_K_EMIT);
     launch_emit(L, B.dtype_mask, B.d_nodes, B.n_nodes, B.d_views, B.d_vnodes, K, B.d_nv, B.d_nvoff, (int)B.chunk_total,
                 P, v0, v1, B.batched, B.d_pmap + (size_t)v0 * (2 * K + 1), B.view_tab[v0 + 1] - B.view_tab[v0],
-                B.d_counts, B.d_inst_off, inst_base, rec, info, u32(ctx->dkey0), u32(ctx->ival0), u32(ctx->ntile));
+                B.d_counts, B.d_inst_off, inst_base, rec, info, u32(lb.dkey0), u32(lb.ival0), u32(lb.ntile));
     tm.end();
     tm.begin(DGS_K_SORT);
     uint32_t *dk = nullptr, *order = nullptr;
-    launch_sort(L, u32(ctx->dkey0), u32(ctx->ival0), u32(ctx->dkey1), u32(ctx->ival1), n_inst, kZBits, u32(ctx->hist),
-                u32(ctx->status), u32(ctx->counters), B.d_err, &dk, &order, d_inst);
-    launch_tile_scan(L, order, u32(ctx->ntile), n_inst, d_inst, u32(ctx->poff), u32(ctx->tparts), n_bound, d_pairs);
-    launch_pairs(L, B.d_views, K, order, u32(ctx->poff), rec, info, n_inst, d_inst, P, u32(ctx->tkeys0),
-                 u32(ctx->tvals0), n_bound);
+    launch_sort(L, u32(lb.dkey0), u32(lb.ival0), u32(lb.dkey1), u32(lb.ival1), n_inst, kZBits, u32(lb.hist),
+                u32(lb.status), u32(lb.counters), B.d_err, &dk, &order, d_inst);
+    launch_tile_scan(L, order, u32(lb.ntile), n_inst, d_inst, u32(lb.poff), u32(lb.tparts), n_bound, d_pairs);
+    launch_pairs(L, B.d_views, K, order, u32(lb.poff), rec, info, n_inst, d_inst, P, u32(lb.tkeys0),
+                 u32(lb.tvals0), n_bound);
     uint32_t *tk = nullptr, *tv = nullptr;
-    launch_sort(L, u32(ctx->tkeys0), u32(ctx->tvals0), u32(ctx->tkeys1), u32(ctx->tvals1), n_bound,
-                bits_for((uint64_t)n_tiles + 1), u32(ctx->hist), u32(ctx->status), u32(ctx->counters), B.d_err, &tk,
+    launch_sort(L, u32(lb.tkeys0), u32(lb.tvals0), u32(lb.tkeys1), u32(lb.tvals1), n_bound,
+                bits_for((uint64_t)n_tiles + 1), u32(lb.hist), u32(lb.status), u32(lb.counters), B.d_err, &tk,
                 &tv, d_pairs);
     tm.end();
     tm.begin(DGS_K_RANGES);
-    launch_ranges(L, tk, n_bound, static_cast<uint2*>(ctx->ranges.p), n_tiles, d_pairs);
+    launch_ranges(L, tk, n_bound, static_cast<uint2*>(lb.ranges.p), n_tiles, d_pairs);
     tm.end();
     *vals = tv;
 }
@@ -638,10 +660,12 @@ struct GroupLists {
     int v0 = 0, v1 = 0, n_tiles = 0;
     uint32_t n_bound = 0, n_inst = 0;
     const uint32_t* vals = nullptr;
+    ListBufs* lb = nullptr;
     Params P{};
 };
 
-void build_group_lists(dgs_ctx* ctx, const Batch& B, int g, cudaStream_t stream, Timer& tm, GroupLists& G) {
+void build_group_lists(dgs_ctx* ctx, const Batch& B, int g, ListBufs& lb, cudaStream_t stream, Timer& tm,
+                       GroupLists& G) {
     Launch L{stream, &ctx->launches};
     const int V = B.V;
     const int v0 = B.groups[g].first, v1 = B.groups[g].second;
@@ -652,7 +676,8 @@ void build_group_lists(dgs_ctx* ctx, const Batch& B, int g, cudaStream_t stream,
     G.n_tiles = (int)((v1 < V ? B.views[v1].tile_base : B.tiles_total) - tile0);
     G.P = B.P;
     G.P.tile0 = tile0;
-    enqueue_lists(ctx, B, L, tm, v0, v1, G.n_tiles, (uint32_t)B.inst_at[v0], G.n_inst, G.n_bound, nullptr,
+    G.lb = &lb;
+    enqueue_lists(ctx, lb, B, L, tm, v0, v1, G.n_tiles, (uint32_t)B.inst_at[v0], G.n_inst, G.n_bound, nullptr,
                   static_cast<uint32_t*>(ctx->totals.p) + g, G.P, &G.vals);
 }
 
@@ -696,14 +721,33 @@ int run_eager(dgs_ctx* ctx, Batch& B, float* out_rgb, float* out_depth, float* o
         work = reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->errword.p) + 32);
         DGS_CUDA(ctx, cudaMemsetAsync(work, 0, 24, stream));
     }
-    for (int g = 0; g < (int)B.groups.size(); ++g) {
+    // view groups alternate between the caller's stream and a second one, each with its own
+    // list workspace, so one group's binning overlaps the previous group's compositing
+    const int ng = (int)B.groups.size();
+    cudaStream_t streams[2] = {stream, stream};
+    if (ng > 1) {
+        if (!ctx->aux_stream) DGS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
+        streams[1] = ctx->aux_stream;
+        cudaEvent_t front = take_event(ctx);
+        DGS_CUDA(ctx, cudaEventRecord(front, stream));
+        DGS_CUDA(ctx, cudaStreamWaitEvent(streams[1], front, 0));
+    }
+    Timer tms[2] = {tm, Timer{ctx, streams[1], tm.on}};
+    for (int g = 0; g < ng; ++g) {
+        const int b = g & 1;
         GroupLists G;
-        build_group_lists(ctx, B, g, stream, tm, G);
-        tm.begin(DGS_K_COMPOSITE);
-        launch_composite(L, B.d_views, G.v0, G.v1 - G.v0, G.n_tiles, static_cast<uint2*>(ctx->ranges.p), G.vals,
-                         static_cast<Record*>(ctx->records.p), G.P, out_rgb, out_depth, out_alpha, work);
-        tm.end();
+        build_group_lists(ctx, B, g, ctx->lists[b], streams[b], tms[b], G);
+        Launch Lg{streams[b], &ctx->launches};
+        tms[b].begin(DGS_K_COMPOSITE);
+        launch_composite(Lg, B.d_views, G.v0, G.v1 - G.v0, G.n_tiles, static_cast<uint2*>(G.lb->ranges.p), G.vals,
+                         static_cast<Record*>(G.lb->records.p), G.P, out_rgb, out_depth, out_alpha, work);
+        tms[b].end();
         DGS_CUDA(ctx, cudaGetLastError());
+    }
+    if (ng > 1) {
+        cudaEvent_t join = take_event(ctx);
+        DGS_CUDA(ctx, cudaEventRecord(join, streams[1]));
+        DGS_CUDA(ctx, cudaStreamWaitEvent(stream, join, 0));
     }
     rc = finish(ctx, B, stream);
     if (rc == DGS_OK && work) {
@@ -768,10 +812,11 @@ void enqueue_graph_body(dgs_ctx* ctx, const Batch& B, const Launch& L, float* ou
     P.gate = sizes + 2;
     Timer off2{ctx, L.stream, false};
     const uint32_t* vals = nullptr;
-    enqueue_lists(ctx, B, L, off2, 0, B.V, (int)B.tiles_total, 0u, (uint32_t)ctx->cap_inst, (uint32_t)ctx->cap_pairs,
-                  sizes + 0, sizes + 3, P, &vals);
-    launch_composite(L, B.d_views, 0, B.V, (int)B.tiles_total, static_cast<uint2*>(ctx->ranges.p), vals,
-                     static_cast<Record*>(ctx->records.p), P, out_rgb, out_depth, out_alpha, nullptr);
+    ListBufs& lb = ctx->lists[0];
+    enqueue_lists(ctx, lb, B, L, off2, 0, B.V, (int)B.tiles_total, 0u, (uint32_t)ctx->cap_inst,
+                  (uint32_t)ctx->cap_pairs, sizes + 0, sizes + 3, P, &vals);
+    launch_composite(L, B.d_views, 0, B.V, (int)B.tiles_total, static_cast<uint2*>(lb.ranges.p), vals,
+                     static_cast<Record*>(lb.records.p), P, out_rgb, out_depth, out_alpha, nullptr);
 }
 
 // Sizes the capacities from the totals of the render just done (instances and pair bound)
@@ -786,7 +831,7 @@ int capture_graph(dgs_ctx* ctx, const Batch& B, uint64_t need_inst, uint64_t nee
     ctx->cap_pairs = std::min<uint64_t>(kMaxPairs, std::max(ctx->cap_pairs, need_pairs + need_pairs / 4 + 4096));
     ctx->gbits = bits;
     int rc;
-    if ((rc = ensure_lists(ctx, ctx->cap_inst, ctx->cap_pairs, B.tiles_total))) return rc;
+    if ((rc = ensure_lists(ctx, ctx->lists[0], ctx->cap_inst, ctx->cap_pairs, B.tiles_total))) return rc;
     if ((rc = ensure(ctx, ctx->gsizes, 64))) return rc;
     if (!ctx->h_graph) DGS_CUDA(ctx, cudaHostAlloc(&ctx->h_graph, 64, cudaHostAllocDefault));
     if (!ctx->cap_stream) DGS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
@@ -923,11 +968,12 @@ int dgs_context_create(dgs_ctx** out, const dgs_options* opt) {
 int dgs_context_destroy(dgs_ctx* ctx) {
     if (!ctx) return DGS_OK;
     cudaDeviceSynchronize();
-    DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->records, &ctx->info,
-                      &ctx->dkey0, &ctx->ival0, &ctx->dkey1, &ctx->ival1, &ctx->ntile, &ctx->poff, &ctx->tparts,
-                      &ctx->tkeys0, &ctx->tvals0, &ctx->tkeys1, &ctx->tvals1, &ctx->hist, &ctx->status, &ctx->counters,
-                      &ctx->ranges, &ctx->errword, &ctx->readback, &ctx->inst_grad, &ctx->gsizes, &ctx->totals};
+    DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->errword,
+                      &ctx->readback, &ctx->inst_grad, &ctx->gsizes, &ctx->totals};
     for (DevBuf* b : bufs) free_buf(*b);
+    for (ListBufs& lb : ctx->lists)
+        for (DevBuf* b : lb.all) free_buf(*b);
+    if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
     drop_graph(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->h_graph) cudaFreeHost(ctx->h_graph);
@@ -942,13 +988,12 @@ const char* dgs_last_error(const dgs_ctx* ctx) { return ctx ? ctx->err.c_str() :
 
 int dgs_workspace_query(const dgs_ctx* ctx, size_t* bytes) {
     if (!ctx || !bytes) return DGS_ERR_INVALID_ARG;
-    const DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->records,
-                            &ctx->info, &ctx->dkey0, &ctx->ival0, &ctx->dkey1, &ctx->ival1, &ctx->ntile,
-                            &ctx->poff, &ctx->tparts, &ctx->tkeys0, &ctx->tvals0, &ctx->tkeys1, &ctx->tvals1,
-                            &ctx->hist, &ctx->status, &ctx->counters, &ctx->ranges, &ctx->errword, &ctx->readback,
-                            &ctx->inst_grad, &ctx->gsizes, &ctx->totals};
+    const DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->errword,
+                            &ctx->readback, &ctx->inst_grad, &ctx->gsizes, &ctx->totals};
     size_t s = 0;
     for (const DevBuf* b : bufs) s += b->bytes;
+    for (const ListBufs& lb : ctx->lists)
+        for (const DevBuf* b : lb.all) s += b->bytes;
     *bytes = s;
     return DGS_OK;
 }
@@ -1071,14 +1116,14 @@ int dgs_render_backward(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, co
     if ((rc = ensure(ctx, ctx->inst_grad, sizeof(float) * 10 * max_inst))) return rc;
     for (int g = 0; g < (int)B.groups.size(); ++g) {
         GroupLists G;
-        build_group_lists(ctx, B, g, stream, tm, G);
+        build_group_lists(ctx, B, g, ctx->lists[0], stream, tm, G);
         tm.begin(DGS_K_BACKWARD);
         DGS_CUDA(ctx, cudaMemsetAsync(ctx->inst_grad.p, 0, sizeof(float) * 10 * std::max<uint32_t>(G.n_inst, 1), stream));
-        launch_composite_bwd(L, B.d_views, G.v0, G.v1 - G.v0, G.n_tiles, static_cast<uint2*>(ctx->ranges.p), G.vals,
-                             static_cast<Record*>(ctx->records.p), G.P, out_rgb, out_depth, grad_rgb, grad_depth,
+        launch_composite_bwd(L, B.d_views, G.v0, G.v1 - G.v0, G.n_tiles, static_cast<uint2*>(G.lb->ranges.p), G.vals,
+                             static_cast<Record*>(G.lb->records.p), G.P, out_rgb, out_depth, grad_rgb, grad_depth,
                              static_cast<float*>(ctx->inst_grad.p));
         launch_project_bwd(L, B.dtype_mask, B.d_nodes, B.n_nodes, B.d_views, B.d_vnodes, B.K, node_poses,
-                           static_cast<InstInfo*>(ctx->info.p), static_cast<float*>(ctx->inst_grad.p), G.n_inst, G.P,
+                           static_cast<InstInfo*>(G.lb->info.p), static_cast<float*>(ctx->inst_grad.p), G.n_inst, G.P,
                            B.d_grads, grad_poses);
         tm.end();
         DGS_CUDA(ctx, cudaGetLastError());
