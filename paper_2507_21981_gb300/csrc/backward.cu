@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) k_composite_bwd(const ViewDesc* __restric
                     const float a_raw = g0.z * ex;
                     const float alpha = fminf(P.alpha_max, a_raw);
                     if (alpha >= P.alpha_min) {
-                        const float Tn = T * (1.f - alpha);
+                        const float Tn = fmaf(-alpha, T, T);   // T (1 - alpha), one rounding
                         if (Tn < P.t_min) {
                             done = true;
                         } else {

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256, 6) k_composite(const ViewDesc* __restrict
             if (COUNT) ++n_reach;
             const float alpha = fminf(P.alpha_max, g0.z * fast_exp2(pe));
             if (alpha < P.alpha_min) continue;
-            const float Tn = T * (1.f - alpha);
+            const float Tn = fmaf(-alpha, T, T);   // T (1 - alpha), one rounding
             if (Tn < P.t_min) { done = true; break; }
             if (COUNT) ++n_comp;
             const float wgt = alpha * T;
