@@ -26,6 +26,34 @@ namespace {
 // per-instance partials, in this order
 enum { G_U = 0, G_V, G_QA, G_QB, G_QC, G_OP, G_R, G_G, G_B, G_Z, G_N };
 
+// Warp sums of 16 values by recursive halving: at the step with offset o each lane keeps the
+// half of its values that its side of the butterfly owns and adds the partner's copy of them
+// (8 + 4 + 2 + 1 + 1 shuffles instead of 16 x 5).  Lanes 2j and 2j + 1 end with the total of
+// value j.
+__device__ __forceinline__ float warp_transpose_sum16(const float (&v)[16], int lane) {
+    const uint32_t full = 0xffffffffu;
+    float a[8], b[4], c[2];
+    const bool h16 = (lane >> 4) & 1, h8 = (lane >> 3) & 1, h4 = (lane >> 2) & 1, h2 = (lane >> 1) & 1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float mine = h16 ? v[8 + j] : v[j], give = h16 ? v[j] : v[8 + j];
+        a[j] = mine + __shfl_xor_sync(full, give, 16);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float mine = h8 ? a[4 + j] : a[j], give = h8 ? a[j] : a[4 + j];
+        b[j] = mine + __shfl_xor_sync(full, give, 8);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float mine = h4 ? b[2 + j] : b[j], give = h4 ? b[j] : b[2 + j];
+        c[j] = mine + __shfl_xor_sync(full, give, 4);
+    }
+    const float mine = h2 ? c[1] : c[0], give = h2 ? c[0] : c[1];
+    const float d = mine + __shfl_xor_sync(full, give, 2);
+    return d + __shfl_xor_sync(full, d, 1);
+}
+
 __device__ __forceinline__ float warp_sum(float x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -128,7 +156,7 @@ __global__ void __launch_bounds__(256) k_composite_bwd(const ViewDesc* __restric
                             const float4 g2 = sr2[k];
                             P0 = fmaf(wgt, g2.x, P0); P1 = fmaf(wgt, g2.y, P1); P2 = fmaf(wgt, g2.z, P2);
                             PD = fmaf(wgt, g0.w, PD);
-                            const float iTn = 1.f / Tn;
+                            const float iTn = __fdividef(1.f, Tn);   // Tn >= t_min > 0
                             const float S0 = (Co0 - P0) * iTn, S1 = (Co1 - P1) * iTn, S2 = (Co2 - P2) * iTn;
                             const float SD = (Do - PD) * iTn;
                             const float dal = T * (gC0 * (g2.x - S0) + gC1 * (g2.y - S1) + gC2 * (g2.z - S2) + gD * (g0.w - SD));
@@ -149,11 +177,12 @@ __global__ void __launch_bounds__(256) k_composite_bwd(const ViewDesc* __restric
             }
             if (__ballot_sync(0xffffffffu, contrib) == 0) continue;
             const uint32_t r = s_idx[w][k];
+            float v16[16];
 #pragma unroll
-            for (int e = 0; e < G_N; ++e) {
-                const float s = warp_sum(g[e]);
-                if (lane == 0 && s != 0.f) atomicAdd(ig + (size_t)r * G_N + e, s);
-            }
+            for (int e = 0; e < 16; ++e) v16[e] = e < G_N ? g[e] : 0.f;
+            const float tot = warp_transpose_sum16(v16, lane);
+            const int e = lane >> 1;
+            if ((lane & 1) == 0 && e < G_N && tot != 0.f) atomicAdd(ig + (size_t)r * G_N + e, tot);
         }
         __syncwarp();
     }
@@ -413,16 +442,18 @@ __global__ void __launch_bounds__(128) k_project_bwd(const NodeDesc* __restrict_
     if (same && lead >= 0) {
         const ViewDesc& vd0 = views[lead / K];
         float* gp = grad_poses + ((int64_t)vd0.env * K + (lead % K)) * 12;
+        // the 3x4 pose partials in row-major [R | t] order, summed over the warp
+        float v16[16];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
 #pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                const float v = warp_sum(gRn[a * 3 + b]);
-                if (lane == 0) atomicAdd(gp + a * 4 + b, v);
-            }
-            const float v = warp_sum(gtn[a]);
-            if (lane == 0) atomicAdd(gp + a * 4 + 3, v);
+            for (int b = 0; b < 3; ++b) v16[a * 4 + b] = gRn[a * 3 + b];
+            v16[a * 4 + 3] = gtn[a];
         }
+#pragma unroll
+        for (int e = 12; e < 16; ++e) v16[e] = 0.f;
+        const float tot = warp_transpose_sum16(v16, lane);
+        if ((lane & 1) == 0 && (lane >> 1) < 12) atomicAdd(gp + (lane >> 1), tot);
     } else if (act) {
         const ViewDesc& vdl = views[vv / K];
         float* gp = grad_poses + ((int64_t)vdl.env * K + (vv % K)) * 12;
