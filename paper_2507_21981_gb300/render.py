@@ -172,13 +172,22 @@ class Renderer:
         pose gradient [E,K,3,4] or None)."""
         node_grads = []
         arr = (D.dgs_node_grads * ds.n_nodes)()
+        # every gradient is a view of one zeroed buffer (one fill instead of one per tensor)
+        names = ("mean", "log_scale", "quat", "opacity_logit", "sh")
+        sizes = [t[name].numel() for t in ds.tensors for name in names]
+        flat = torch.zeros(sum(sizes) + (ds.n_envs * ds.max_nodes * 12 if want_poses else 0), dtype=torch.float32,
+                           device=ds.device)
+        off = 0
         for k, t in enumerate(ds.tensors):
-            g = {name: torch.zeros(t[name].shape, dtype=torch.float32, device=ds.device) for name in
-                 ("mean", "log_scale", "quat", "opacity_logit", "sh")}
+            g = {}
+            for name in names:
+                n = t[name].numel()
+                g[name] = flat[off:off + n].view(t[name].shape)
+                off += n
             node_grads.append(g)
             arr[k].mean, arr[k].log_scale, arr[k].quat = g["mean"].data_ptr(), g["log_scale"].data_ptr(), g["quat"].data_ptr()
             arr[k].opacity_logit, arr[k].sh = g["opacity_logit"].data_ptr(), g["sh"].data_ptr()
-        gposes = torch.zeros((ds.n_envs, ds.max_nodes, 12), dtype=torch.float32, device=ds.device) if want_poses else None
+        gposes = flat[off:].view(ds.n_envs, ds.max_nodes, 12) if want_poses else None
         s = stream if stream is not None else torch.cuda.current_stream(ds.device)
         grad_rgb = grad_rgb.contiguous().float()
         grad_depth = None if grad_depth is None else grad_depth.contiguous().float()
