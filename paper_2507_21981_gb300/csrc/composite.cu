@@ -12,15 +12,32 @@
 namespace dgs {
 namespace {
 
+// Thread = 4 consecutive sorted keys (one 16-byte load); a run starts where the key differs
+// from the one before and ends where it differs from the one after.
 __global__ void k_ranges(const uint32_t* __restrict__ keys, uint32_t n, const uint32_t* __restrict__ d_n,
                          uint2* __restrict__ ranges, int n_tiles) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t i4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4u;
     if (d_n) n = min(n, *d_n);
-    if (i >= n) return;
-    const uint32_t t = keys[i];
-    if (t >= (uint32_t)n_tiles) return;   // dead pairs sort past every real tile
-    if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
-    if (i + 1 == n || keys[i + 1] != t) ranges[t].y = i + 1;
+    if (i4 >= n) return;
+    uint32_t k[6];                                  // k[0] = key before, k[5] = key after
+    if (i4 + 4 <= n) {
+        const uint4 q = *reinterpret_cast<const uint4*>(keys + i4);
+        k[1] = q.x; k[2] = q.y; k[3] = q.z; k[4] = q.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) k[1 + j] = i4 + j < n ? keys[i4 + j] : 0u;
+    }
+    k[0] = i4 > 0 ? keys[i4 - 1] : 0u;
+    k[5] = i4 + 4 < n ? keys[i4 + 4] : 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t i = i4 + j;
+        if (i >= n) break;
+        const uint32_t t = k[1 + j];
+        if (t >= (uint32_t)n_tiles) continue;       // dead pairs sort past every real tile
+        if (i == 0 || k[j] != t) ranges[t].x = i;
+        if (i + 1 == n || k[2 + j] != t) ranges[t].y = i + 1;
+    }
 }
 
 // Block = one tile, warp = one 8x4 sub-tile, lane = one pixel.  Warps are independent (no
@@ -128,7 +145,8 @@ void launch_ranges(const Launch& L, const uint32_t* keys, uint32_t n, uint2* ran
                    const uint32_t* d_n) {
     cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, L.stream);
     if (n == 0) return;
-    k_ranges<<<(n + 255) / 256, 256, 0, L.stream>>>(keys, n, d_n, ranges, n_tiles);
+    const uint32_t threads = (n + 3) / 4;
+    k_ranges<<<(threads + 255) / 256, 256, 0, L.stream>>>(keys, n, d_n, ranges, n_tiles);
     ++*L.launches;
 }
 
