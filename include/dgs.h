@@ -186,9 +186,9 @@ int dgs_workspace_query(const dgs_ctx* ctx, size_t* bytes);
  * poses, intrinsics and node attribute pointers may change) and replay the graph.  Node poses
  * are read from node_poses at replay time.  If a replay finds more instances or pairs than its
  * capacity, its kernels skip their work, the call renders again eagerly (correct outputs) and
- * recaptures with larger capacities; dgs_stats.path says which happened.  A batch of more
- * than 2^30 pairs is never captured (it needs several view groups) and runs eagerly.
- * views_per_group is ignored by the replayed graph.
+ * recaptures with larger capacities; dgs_stats.path says which happened.  The graph keeps the
+ * one or two view groups of the render it was captured from (two groups run on two streams,
+ * see views_per_group); a batch that needs more groups is not captured and runs eagerly.
  */
 int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes,
                const int32_t* env_node_ids, int32_t n_envs, int32_t max_nodes,

@@ -43,6 +43,7 @@ struct GraphKey {
     const void *poses, *rgb, *depth, *alpha;
     uint64_t gen;
     int64_t tile_w, tile_h, exact_tile_test;
+    int64_t ng, split;
 };
 
 // Workspace of one view group's lists.  dkey/ival: depth keys and instance numbers (depth
@@ -68,11 +69,12 @@ struct dgs_ctx {
     uint64_t gen = 0;                     // bumped whenever a workspace buffer is reallocated
     // graph replay (DGS_MODE_GRAPH)
     cudaStream_t cap_stream = nullptr;    // capture stream (the caller's may be the legacy stream)
+    cudaStream_t cap_stream2 = nullptr;   // second capture stream (the second view group)
     cudaGraphExec_t gexec = nullptr;
     GraphKey gkey{};
-    uint64_t cap_inst = 0, cap_pairs = 0; // capacities the captured sequence was sized for
+    int gng = 1, gsplit = 0;              // captured view groups: [0, gsplit) and [gsplit, V)
+    uint64_t cap_inst[2] = {0, 0}, cap_pairs[2] = {0, 0};  // capacities of each captured group
     int gbits = 0;
-    uint64_t last_bound = 0;              // pair bound (summed tile rectangles) of the last eager call
     int64_t glaunches = 0;
     int32_t captures = 0;
     void* h_graph = nullptr;              // pinned: error word + live totals after a replay
@@ -554,7 +556,6 @@ int readback_groups(dgs_ctx* ctx, Batch& B, cudaStream_t stream, Timer& tm) {
     uint32_t errw = (uint32_t)(h_rb[2 * (V + 1)] & 0xFFFFFFFFu);
     if (errw & kErrPose) return fail(ctx, DGS_ERR_INVALID_ARG, "a node pose is not finite or not rigid");
     ctx->stats.n_visible = (int64_t)inst_at[V];
-    ctx->last_bound = pair_at[V];
     if (inst_at[V] >= (1ull << 32)) return fail(ctx, DGS_ERR_CAPACITY, "more than 2^32 visible instances");
 
     // ---------------------------------------------------------------- groups
@@ -761,20 +762,38 @@ int run_eager(dgs_ctx* ctx, Batch& B, float* out_rgb, float* out_depth, float* o
 }
 
 // ------------------------------------------------------------------ graph replay
-// gsizes layout: u32 [0] live instances, [1] live pair bound, [2] overflow flag, [3] exact
-// pairs (written by the tile-count scan); u64 at byte 16: the instance and pair-bound totals
-// the scan produced (valid even on overflow).
-__global__ void k_graph_sizes(const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off, int64_t T,
-                              uint64_t cap_inst, uint64_t cap_pairs, uint32_t* sizes, uint32_t* err) {
-    const uint64_t ni = inst_off[T], np = pair_off[T];
-    uint64_t* raw = reinterpret_cast<uint64_t*>(sizes + 4);
-    raw[0] = ni;
-    raw[1] = np;
-    const bool over = ni > cap_inst || np > cap_pairs;
-    sizes[0] = over ? 0u : (uint32_t)ni;
-    sizes[1] = over ? 0u : (uint32_t)np;
+// The captured sequence runs one or two view groups; group g covers views [v0, v1) whose
+// count-table entries are [t0, t1).
+struct GraphGroups {
+    int64_t t0[2], t1[2];
+    uint64_t cap_inst[2], cap_pairs[2];
+    int32_t ng;
+};
+
+// gsizes layout (u32 words): group g at [8g]: [8g] live instances, [8g+1] live pair bound,
+// [8g+3] exact pairs (written by the tile-count scan), [8g+4] the group's first record; [2]
+// the overflow flag of the whole replay; u64 at word 16: the instance and pair-bound totals of
+// each group (valid even on overflow).
+__global__ void k_graph_sizes(const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off,
+                              GraphGroups G, uint32_t* sizes, uint32_t* err) {
+    uint64_t ni[2] = {0, 0}, np[2] = {0, 0};
+    bool over = false;
+    for (int g = 0; g < G.ng; ++g) {
+        ni[g] = (uint64_t)inst_off[G.t1[g]] - inst_off[G.t0[g]];
+        np[g] = pair_off[G.t1[g]] - pair_off[G.t0[g]];
+        over |= ni[g] > G.cap_inst[g] || np[g] > G.cap_pairs[g];
+    }
+    uint64_t* raw = reinterpret_cast<uint64_t*>(sizes + 16);
+    for (int g = 0; g < 2; ++g) {
+        uint32_t* s = sizes + 8 * g;
+        s[0] = over ? 0u : (uint32_t)ni[g];
+        s[1] = over ? 0u : (uint32_t)np[g];
+        s[3] = 0u;
+        s[4] = g < G.ng ? inst_off[G.t0[g]] : 0u;
+        raw[2 * g] = ni[g];
+        raw[2 * g + 1] = np[g];
+    }
     sizes[2] = over ? 1u : 0u;
-    sizes[3] = 0u;
     if (over) atomicOr(err, kErrCapacity);
 }
 
@@ -787,6 +806,7 @@ GraphKey make_key(const dgs_ctx* ctx, const Batch& B, const float* rgb, const fl
     k.poses = B.node_poses; k.rgb = rgb; k.depth = depth; k.alpha = alpha;
     k.gen = ctx->gen;
     k.tile_w = ctx->opt.tile_w; k.tile_h = ctx->opt.tile_h; k.exact_tile_test = ctx->opt.exact_tile_test;
+    k.ng = ctx->gng; k.split = ctx->gsplit;
     return k;
 }
 
@@ -799,52 +819,99 @@ void drop_graph(dgs_ctx* ctx) {
 
 // The whole render as one sequence sized for the context's capacities; every kernel after the
 // scan reads the live counts on the device, so nothing is read back between count and
-// composite.  On overflow the size check raises kErrCapacity and the later kernels do no work.
-void enqueue_graph_body(dgs_ctx* ctx, const Batch& B, const Launch& L, float* out_rgb, float* out_depth,
-                        float* out_alpha) {
+// composite.  With two view groups the second runs on a forked stream (its binning overlaps
+// the first group's compositing) and joins before the end.  On overflow the size check raises
+// kErrCapacity and the later kernels do no work.
+int enqueue_graph_body(dgs_ctx* ctx, const Batch& B, const Launch& L, float* out_rgb, float* out_depth,
+                       float* out_alpha) {
     Timer off{ctx, L.stream, false};
     launch_front(ctx, B, L, off);
     uint32_t* sizes = static_cast<uint32_t*>(ctx->gsizes.p);
-    k_graph_sizes<<<1, 1, 0, L.stream>>>(B.d_inst_off, B.d_pair_off, B.T, ctx->cap_inst, ctx->cap_pairs, sizes,
-                                         B.d_err);
+    const int ng = ctx->gng;
+    const int vb[3] = {0, ng == 2 ? ctx->gsplit : B.V, B.V};
+    GraphGroups G{};
+    G.ng = ng;
+    for (int g = 0; g < ng; ++g) {
+        G.t0[g] = B.view_tab[vb[g]];
+        G.t1[g] = B.view_tab[vb[g + 1]];
+        G.cap_inst[g] = ctx->cap_inst[g];
+        G.cap_pairs[g] = ctx->cap_pairs[g];
+    }
+    k_graph_sizes<<<1, 1, 0, L.stream>>>(B.d_inst_off, B.d_pair_off, G, sizes, B.d_err);
     ++*L.launches;
-    Params P = B.P;
-    P.gate = sizes + 2;
-    Timer off2{ctx, L.stream, false};
-    const uint32_t* vals = nullptr;
-    ListBufs& lb = ctx->lists[0];
-    enqueue_lists(ctx, lb, B, L, off2, 0, B.V, (int)B.tiles_total, 0u, (uint32_t)ctx->cap_inst,
-                  (uint32_t)ctx->cap_pairs, sizes + 0, sizes + 3, P, &vals);
-    launch_composite(L, B.d_views, 0, B.V, (int)B.tiles_total, static_cast<uint2*>(lb.ranges.p), vals,
-                     static_cast<Record*>(lb.records.p), P, out_rgb, out_depth, out_alpha, nullptr);
+    cudaStream_t st[2] = {L.stream, ctx->cap_stream2};
+    if (ng == 2) {
+        cudaEvent_t fork = take_event(ctx);
+        DGS_CUDA(ctx, cudaEventRecord(fork, L.stream));
+        DGS_CUDA(ctx, cudaStreamWaitEvent(st[1], fork, 0));
+    }
+    for (int g = 0; g < ng; ++g) {
+        const int v0 = vb[g], v1 = vb[g + 1];
+        const int32_t tile0 = B.views[v0].tile_base;
+        const int n_tiles = (int)((v1 < B.V ? B.views[v1].tile_base : B.tiles_total) - tile0);
+        Launch Lg{st[g], L.launches};
+        Timer tg{ctx, st[g], false};
+        Params P = B.P;
+        P.tile0 = tile0;
+        P.gate = sizes + 2;
+        P.inst_base_dev = sizes + 8 * g + 4;
+        ListBufs& lb = ctx->lists[g];
+        const uint32_t* vals = nullptr;
+        enqueue_lists(ctx, lb, B, Lg, tg, v0, v1, n_tiles, 0u, (uint32_t)ctx->cap_inst[g],
+                      (uint32_t)ctx->cap_pairs[g], sizes + 8 * g, sizes + 8 * g + 3, P, &vals);
+        launch_composite(Lg, B.d_views, v0, v1 - v0, n_tiles, static_cast<uint2*>(lb.ranges.p), vals,
+                         static_cast<Record*>(lb.records.p), P, out_rgb, out_depth, out_alpha, nullptr);
+    }
+    if (ng == 2) {
+        cudaEvent_t join = take_event(ctx);
+        DGS_CUDA(ctx, cudaEventRecord(join, st[1]));
+        DGS_CUDA(ctx, cudaStreamWaitEvent(L.stream, join, 0));
+    }
+    return DGS_OK;
 }
 
-// Sizes the capacities from the totals of the render just done (instances and pair bound)
-// with 25 % headroom, and captures the sequence.  Returns DGS_OK without a graph when the
-// batch cannot run as one view group (a pair bound above 2^30 or more than 2^31 tiles).
-int capture_graph(dgs_ctx* ctx, const Batch& B, uint64_t need_inst, uint64_t need_pairs, float* out_rgb,
-                  float* out_depth, float* out_alpha) {
+// Captures the sequence with the view groups of the eager render just done (B: one or two
+// groups) and capacities of 1.25x its per-group instance and pair-bound totals.  Returns
+// DGS_OK without a graph when the batch needs more than two groups or a group more than 2^31
+// tiles.
+int capture_graph(dgs_ctx* ctx, const Batch& B, float* out_rgb, float* out_depth, float* out_alpha) {
     drop_graph(ctx);
-    const int bits = bits_for((uint64_t)std::max<int64_t>(B.tiles_total, 1) + 1);
-    if (need_pairs > kMaxPairs || bits > 31 || need_inst >= (1ull << 31)) return DGS_OK;
-    ctx->cap_inst = std::max(ctx->cap_inst, need_inst + need_inst / 4 + 1024);
-    ctx->cap_pairs = std::min<uint64_t>(kMaxPairs, std::max(ctx->cap_pairs, need_pairs + need_pairs / 4 + 4096));
-    ctx->gbits = bits;
+    const int ng = (int)B.groups.size();
+    if (ng < 1 || ng > 2) return DGS_OK;
+    const int split = ng == 2 ? B.groups[0].second : B.V;
+    const bool same_split = ng == ctx->gng && split == ctx->gsplit;
+    ctx->gng = ng;
+    ctx->gsplit = split;
     int rc;
-    if ((rc = ensure_lists(ctx, ctx->lists[0], ctx->cap_inst, ctx->cap_pairs, B.tiles_total))) return rc;
-    if ((rc = ensure(ctx, ctx->gsizes, 64))) return rc;
-    if (!ctx->h_graph) DGS_CUDA(ctx, cudaHostAlloc(&ctx->h_graph, 64, cudaHostAllocDefault));
+    int bits = 0;
+    for (int g = 0; g < ng; ++g) {
+        const int v0 = B.groups[g].first, v1 = B.groups[g].second;
+        const uint64_t need_inst = B.inst_at[v1] - B.inst_at[v0], need_pairs = B.pair_at[v1] - B.pair_at[v0];
+        const int64_t n_tiles = (v1 < B.V ? B.views[v1].tile_base : B.tiles_total) - B.views[v0].tile_base;
+        bits = std::max(bits, bits_for((uint64_t)std::max<int64_t>(n_tiles, 1) + 1));
+        if (need_pairs > kMaxPairs || bits > 31 || need_inst >= (1ull << 31)) return DGS_OK;
+        const uint64_t ci = need_inst + need_inst / 4 + 1024;
+        const uint64_t cp = std::min<uint64_t>(kMaxPairs, need_pairs + need_pairs / 4 + 4096);
+        ctx->cap_inst[g] = same_split ? std::max(ctx->cap_inst[g], ci) : ci;
+        ctx->cap_pairs[g] = same_split ? std::max(ctx->cap_pairs[g], cp) : cp;
+        if ((rc = ensure_lists(ctx, ctx->lists[g], ctx->cap_inst[g], ctx->cap_pairs[g], n_tiles))) return rc;
+    }
+    ctx->gbits = bits;
+    if ((rc = ensure(ctx, ctx->gsizes, 128))) return rc;
+    if (!ctx->h_graph) DGS_CUDA(ctx, cudaHostAlloc(&ctx->h_graph, 128, cudaHostAllocDefault));
     if (!ctx->cap_stream) DGS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    if (!ctx->cap_stream2) DGS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking));
     sort_prepare();
     int64_t n_launch = 0;
     Launch L{ctx->cap_stream, &n_launch};
     DGS_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_graph_body(ctx, B, L, out_rgb, out_depth, out_alpha);
+    const int rb = enqueue_graph_body(ctx, B, L, out_rgb, out_depth, out_alpha);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
-    if (e != cudaSuccess || !g) {
+    if (rb != DGS_OK || e != cudaSuccess || !g) {
         cudaGetLastError();
         if (g) cudaGraphDestroy(g);
+        if (rb != DGS_OK) return rb;
         return cuda_fail(ctx, e != cudaSuccess ? e : cudaErrorUnknown, "stream capture of the render sequence");
     }
     const cudaError_t ei = cudaGraphInstantiate(&ctx->gexec, g, 0);
@@ -879,22 +946,22 @@ int render_graph(dgs_ctx* ctx, Batch& B, float* out_rgb, float* out_depth, float
         }
         ctx->launches = ctx->glaunches;
         char* hg = static_cast<char*>(ctx->h_graph);
-        DGS_CUDA(ctx, cudaMemcpyAsync(hg, B.d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
-        DGS_CUDA(ctx, cudaMemcpyAsync(hg + 4, ctx->gsizes.p, 32, cudaMemcpyDeviceToHost, stream));
+        DGS_CUDA(ctx, cudaMemcpyAsync(hg, ctx->gsizes.p, 96, cudaMemcpyDeviceToHost, stream));
+        DGS_CUDA(ctx, cudaMemcpyAsync(hg + 96, B.d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
         DGS_CUDA(ctx, cudaStreamSynchronize(stream));
-        uint32_t errw, sizes[4];
-        uint64_t raw[2];
-        std::memcpy(&errw, hg, 4);
-        std::memcpy(sizes, hg + 4, 16);
-        std::memcpy(raw, hg + 20, 16);
+        uint32_t errw, sizes[16];
+        uint64_t raw[4];
+        std::memcpy(sizes, hg, 64);
+        std::memcpy(raw, hg + 64, 32);
+        std::memcpy(&errw, hg + 96, 4);
         if (ctx->opt.profile)
             for (const TimedRange& r : ctx->ranges_timed) {
                 float ms = 0.f;
                 if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) ctx->ktimes[r.cls] += ms;
             }
-        ctx->stats.n_visible = (int64_t)raw[0];
-        ctx->stats.n_pairs = (int64_t)sizes[3];
-        ctx->stats.n_groups = 1;
+        ctx->stats.n_visible = (int64_t)(raw[0] + raw[2]);
+        ctx->stats.n_pairs = (int64_t)sizes[3] + (ctx->gng == 2 ? (int64_t)sizes[11] : 0);
+        ctx->stats.n_groups = ctx->gng;
         ctx->stats.key_bits = ctx->gbits;
         if (errw & kErrPose) return fail(ctx, DGS_ERR_INVALID_ARG, "a node pose is not finite or not rigid");
         if (errw & kErrTimeout) return fail(ctx, DGS_ERR_TIMEOUT, "a bounded device wait timed out (sort look-back)");
@@ -910,13 +977,12 @@ int render_graph(dgs_ctx* ctx, Batch& B, float* out_rgb, float* out_depth, float
         ctx->ranges_timed.clear();
         ctx->launches = 0;
         if ((rc = run_eager(ctx, B, out_rgb, out_depth, out_alpha, stream, tm))) return rc;
-        if ((rc = capture_graph(ctx, B, raw[0], raw[1], out_rgb, out_depth, out_alpha))) return rc;
+        if ((rc = capture_graph(ctx, B, out_rgb, out_depth, out_alpha))) return rc;
         ctx->stats.path = DGS_PATH_REGROWN;
         return DGS_OK;
     }
     if ((rc = run_eager(ctx, B, out_rgb, out_depth, out_alpha, stream, tm))) return rc;
-    if ((rc = capture_graph(ctx, B, (uint64_t)ctx->stats.n_visible, ctx->last_bound, out_rgb, out_depth, out_alpha)))
-        return rc;
+    if ((rc = capture_graph(ctx, B, out_rgb, out_depth, out_alpha))) return rc;
     ctx->stats.path = ctx->gexec ? DGS_PATH_CAPTURED : DGS_PATH_EAGER;
     return DGS_OK;
 }
@@ -976,6 +1042,7 @@ int dgs_context_destroy(dgs_ctx* ctx) {
     if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
     drop_graph(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->cap_stream2) cudaStreamDestroy(ctx->cap_stream2);
     if (ctx->h_graph) cudaFreeHost(ctx->h_graph);
     if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
     if (ctx->h_read) cudaFreeHost(ctx->h_read);

@@ -66,6 +66,7 @@ struct Params {
     uint32_t* err;        // device error word
     const uint32_t* gate; // emission is skipped when non-null and *gate != 0 (capacity overflow)
     float p_min;          // kHalfLog2e * q_max: exponents below it are outside the 3-sigma ellipse
+    const uint32_t* inst_base_dev;  // emission: first record of the group read on the device (graph replay)
 };
 
 // Projected instance as stored for compositing: 48 bytes.

@@ -669,6 +669,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 6) k_emit_batched(const NodeD
     const int chunk = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (chunk >= n_chunks) return;
     if (P.gate && *P.gate) return;       // capacity overflow: write nothing
+    if (P.inst_base_dev) inst_base = *P.inst_base_dev;
     const int lane = (int)lane_id(), wib = threadIdx.x >> 5;
     WarpWork& W = ww[wib];
     const int k = find_node(nodes, n_nodes, chunk);
