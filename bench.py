@@ -364,26 +364,44 @@ def main():
     rg.close()
 
     # ---------------------------------------------------------------- e2e through the C ABI with host buffers
+    # every step uploads its poses from pinned host memory and reads its RGB + depth back into
+    # pinned host memory; the read-back of step i runs on a copy stream while step i + 1
+    # renders (two output buffers), and the timed region ends after the last read-back
     poses_host = torch.from_numpy(np.ascontiguousarray(sc.node_poses, np.float32).reshape(ds.n_envs, ds.max_nodes, 12)).pin_memory()
-    host_rgb = torch.empty((px_per_step, 3), dtype=torch.float32).pin_memory()
-    host_depth = torch.empty((px_per_step,), dtype=torch.float32).pin_memory()
+    host_out = [(torch.empty((px_per_step, 3), dtype=torch.float32).pin_memory(),
+                 torch.empty((px_per_step,), dtype=torch.float32).pin_memory()) for _ in range(2)]
+    dev_out = [(out[0], out[1]), (torch.empty_like(out[0]), torch.empty_like(out[1]))]
+    copy_stream = torch.cuda.Stream(dev)
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    for e in copied:
+        e.record(copy_stream)
     re2e = Renderer(mode="batched", tile=tile, views_per_group=vpg)
     dposes = torch.empty_like(ds.node_poses)
 
-    def e2e_step():
+    def e2e_step(i):
+        b = i & 1
         dposes.copy_(poses_host, non_blocking=True)
         ds.node_poses = dposes
-        rgb, depth, _ = re2e.render(ds, out=(out[0], out[1], None))
-        host_rgb.copy_(rgb, non_blocking=True)
-        host_depth.copy_(depth, non_blocking=True)
-    for _ in range(args.warmup):
-        e2e_step()
+        stream.wait_event(copied[b])               # buffer b's previous read-back is done
+        rgb, depth, _ = re2e.render(ds, out=(dev_out[b][0], dev_out[b][1], None))
+        ready = torch.cuda.Event()
+        ready.record(stream)
+        copy_stream.wait_event(ready)
+        with torch.cuda.stream(copy_stream):
+            host_out[b][0].copy_(rgb, non_blocking=True)
+            host_out[b][1].copy_(depth, non_blocking=True)
+        copied[b].record(copy_stream)
+    for i in range(args.warmup):
+        e2e_step(i)
     barrier()
     ev0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
+    for i in range(args.steps):
+        e2e_step(i)
+    for e in copied:
+        stream.wait_event(e)
     ev1.record(stream)
     barrier()
+    host_rgb, host_depth = host_out[0]
     ms_e2e = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
     e2e_value = px_per_step * world / (ms_e2e / 1e3) / 1e6
     h2d = poses_host.numel() * 4
