@@ -54,12 +54,6 @@ __device__ __forceinline__ float warp_transpose_sum16(const float (&v)[16], int 
     return d + __shfl_xor_sync(full, d, 1);
 }
 
-__device__ __forceinline__ float warp_sum(float x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
 // ------------------------------------------------------------------ K7
 __global__ void __launch_bounds__(256) k_composite_bwd(const ViewDesc* __restrict__ views, int v0, int nv,
                                                        const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
