@@ -6,11 +6,13 @@ and this package imports nothing from the product: scenes are read by duck typin
 object with the attributes of a `Scene` (nodes with SoA arrays, env_node_ids, node_poses,
 cams_per_env, cam_intr, cam_res, cam_pose).
 
-The arithmetic lives in oracle.cpp (plain FP64 C++, std::thread over pixel rows); see its
-header for the definition it implements and the readings it fixes.
+The rendering arithmetic lives in oracle.cpp (plain FP64 C++, std::thread over pixel rows);
+see its header for the definition it implements and the readings it fixes.  The image
+randomisation applied to rendered frames is augment.py (numpy, FP64).
 """
+from . import augment
 from .oracle import (OracleOptions, build, lib_path, project_view, render_view, backward_view,
                      backward_scene, pose_twist_grad, sh_basis, depth_key32)
 
-__all__ = ["OracleOptions", "build", "lib_path", "project_view", "render_view", "backward_view",
+__all__ = ["OracleOptions", "augment", "build", "lib_path", "project_view", "render_view", "backward_view",
            "backward_scene", "pose_twist_grad", "sh_basis", "depth_key32"]

@@ -461,3 +461,69 @@ def select_views(scene: Scene, views) -> Scene:
         w, h = (int(x) for x in scene.cam_res[e, c])
         env_cams.append([(fx, fy, cx, cy, w, h, scene.cam_pose[e, c])])
     return scene_from_lists(scene.name + "-views", scene.nodes, env_nodes, env_poses, env_cams, dict(scene.meta))
+
+
+# ------------------------------------------------------------------------ image randomisation
+# Per-view parameters of the randomisation applied to rendered frames (Sec. IV: overlay blend,
+# HSV jitter, random gamma); the record layout of the C struct dgs_augment.
+AUGMENT_DTYPE = np.dtype([("hue_shift", "<f4"), ("sat_scale", "<f4"), ("val_scale", "<f4"), ("gamma", "<f4"),
+                          ("overlay_beta", "<f4"), ("overlay_frame", "<i4"), ("overlay_x", "<i4"),
+                          ("overlay_y", "<i4")])
+
+
+def overlay_frames(seed: int = 1, n_frames: int = 8, width: int = 1280, height: int = 720) -> np.ndarray:
+    """A seeded synthetic stand-in for the Internet video clips whose crops the paper blends
+    into rendered frames: uint8 [n_frames, height, width, 3].  Each frame is a smooth colour
+    field (a few drifting plane waves per channel) with a dozen flat-coloured discs and boxes
+    moving at constant velocity across the clip, plus mild per-pixel noise, so that crops hold
+    edges, flat regions and gradients as video does."""
+    rng = _rng(seed, 101)
+    y, x = np.mgrid[0:height, 0:width].astype(np.float64)
+    waves = rng.uniform(-1.0, 1.0, size=(3, 4, 2)) * (2 * math.pi / np.array([width, height]) * 3.0)
+    phase0 = rng.uniform(0, 2 * math.pi, size=(3, 4))
+    drift = rng.uniform(-0.3, 0.3, size=(3, 4))
+    n_shapes = 12
+    kind = rng.integers(0, 2, size=n_shapes)
+    c0 = rng.uniform([0, 0], [width, height], size=(n_shapes, 2))
+    vel = rng.uniform(-12.0, 12.0, size=(n_shapes, 2))
+    size = rng.uniform(0.03, 0.15, size=n_shapes) * min(width, height)
+    colour = rng.uniform(0.0, 1.0, size=(n_shapes, 3))
+    frames = np.empty((n_frames, height, width, 3), dtype=np.uint8)
+    for f in range(n_frames):
+        img = np.empty((height, width, 3))
+        for ch in range(3):
+            acc = np.zeros((height, width))
+            for k in range(4):
+                acc += np.cos(waves[ch, k, 0] * x + waves[ch, k, 1] * y + phase0[ch, k] + drift[ch, k] * f)
+            img[..., ch] = 0.5 + 0.12 * acc
+        for s in range(n_shapes):
+            cx, cy = c0[s] + vel[s] * f
+            if kind[s] == 0:
+                m = (x - cx) ** 2 + (y - cy) ** 2 <= size[s] ** 2
+            else:
+                m = (np.abs(x - cx) <= size[s]) & (np.abs(y - cy) <= 0.6 * size[s])
+            img[m] = colour[s]
+        img += rng.normal(0.0, 0.02, size=img.shape)
+        frames[f] = np.clip(np.rint(img * 255.0), 0, 255).astype(np.uint8)
+    return frames
+
+
+def augment_params(seed: int, n_views: int, n_frames: int, overlay_w: int, overlay_h: int,
+                   hue: float = 0.05, sat=(0.7, 1.3), val=(0.7, 1.3), gamma=(0.7, 1.5), beta=(0.1, 0.4),
+                   p_overlay: float = 0.5) -> np.ndarray:
+    """Seeded per-view randomisation parameters (AUGMENT_DTYPE [n_views]): hue shift uniform in
+    [-hue, hue] turns, saturation and value scales and gamma uniform in their ranges, and with
+    probability p_overlay an overlay weight uniform in `beta` (else 0) with a uniformly drawn
+    frame and crop origin."""
+    rng = _rng(seed, 102)
+    p = np.zeros(n_views, dtype=AUGMENT_DTYPE)
+    p["hue_shift"] = rng.uniform(-hue, hue, n_views)
+    p["sat_scale"] = rng.uniform(*sat, n_views)
+    p["val_scale"] = rng.uniform(*val, n_views)
+    p["gamma"] = rng.uniform(*gamma, n_views)
+    on = rng.uniform(size=n_views) < p_overlay
+    p["overlay_beta"] = np.where(on, rng.uniform(*beta, n_views), 0.0)
+    p["overlay_frame"] = rng.integers(0, n_frames, n_views)
+    p["overlay_x"] = rng.integers(0, overlay_w, n_views)
+    p["overlay_y"] = rng.integers(0, overlay_h, n_views)
+    return p
