@@ -223,6 +223,65 @@ def precision_scale(dev, warmup, steps):
     return res
 
 
+def augment_leg(dev, ds, tile, out, warmup, steps, ms_plain_render):
+    """Image randomisation on the benchmark batch (overlay crops of a seeded 8-frame 1280x720
+    clip blended into half of the views, HSV jitter and gamma on all): the render with the
+    randomisation fused into the compositor, and the separate in-place pass over the same
+    RGB (HBM-bound: 24 B of RGB per pixel plus 3 B of overlay where the weight is non-zero)."""
+    import numpy as np
+    import torch
+    from paper_2507_21981_gb300 import dgs as D
+    from paper_2507_21981_gb300 import scenes
+    from paper_2507_21981_gb300.render import Renderer
+    n_f, ow, oh = 8, 1280, 720
+    ov = torch.as_tensor(scenes.overlay_frames(1, n_frames=n_f, width=ow, height=oh)).to(dev)
+    prm = scenes.augment_params(1, ds.n_views, n_f, ow, oh)
+    stream = torch.cuda.current_stream(dev)
+    r = Renderer(mode="batched", tile=tile)
+    r.set_augment(prm, ov)
+    for _ in range(warmup):
+        r.render(ds, out=out)
+    ms_fused = _time_renders(r, ds, out, steps, stream)
+    sizes = np.asarray(ds.view_res, np.int32)
+    rgb = out[0]
+    for _ in range(warmup):
+        r.augment_rgb(ds, rgb)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(steps):
+        rc = D.dgs_augment_rgb(r.ctx, rgb, sizes, None, ds.n_views, stream.cuda_stream)
+        assert rc == D.DGS_OK
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_sep = ev0.elapsed_time(ev1) / steps
+    r.close()
+    px = np.asarray([w * h for w, h in ds.view_res], np.int64)
+    px_ov = int(px[prm["overlay_beta"] > 0].sum())
+    sep_bytes = ds.n_pixels * 24 + px_ov * 3
+    peaks, kind = _peaks()
+    gbs = sep_bytes / (ms_sep / 1e3) / 1e9
+    # the oracle's randomisation of one view (numpy FP64, one host thread)
+    import oracle
+    x = np.random.default_rng(0).uniform(0, 1, size=(480, 640, 3))
+    ovh = ov[:1].cpu().numpy()
+    q = dict(zip(oracle.augment.FIELDS, [prm[0][f] for f in oracle.augment.FIELDS]))
+    q["overlay_beta"], q["overlay_frame"] = 0.3, 0
+    t0 = time.perf_counter()
+    oracle.augment.augment_view(x, q, ovh)
+    t_or = time.perf_counter() - t0
+    return {"workload": "benchmark batch + per-view randomisation, overlay clip 8 x 1280x720 uint8, "
+                        f"{int((prm['overlay_beta'] > 0).sum())} of {ds.n_views} views blended",
+            "fused_ms_per_step": ms_fused, "fused_mpix_s": ds.n_pixels / (ms_fused / 1e3) / 1e6,
+            "render_ms_per_step_without": ms_plain_render,
+            "fused_overhead_pct": 100.0 * (ms_fused - ms_plain_render) / ms_plain_render,
+            "separate_pass": {"ms": ms_sep, "bytes": sep_bytes, "gb_s": gbs, "peak_gb_s": peaks["hbm_gbs"],
+                              "frac": gbs / peaks["hbm_gbs"], "peak_source": f"{kind} MEASURED_PEAKS.json hbm_gbs",
+                              "bytes_per_pixel": "24 (+3 with overlay)"},
+            "oracle_mpix_s": 640 * 480 / t_or / 1e6, "oracle_sample": "one 640x480 view, numpy FP64, 1 thread",
+            "steps": steps}
+
+
 def cpu_baseline(views=1, seed=1):
     """Times the FP64 oracle on `views` sampled views of the workload (host cores)."""
     import oracle
@@ -426,6 +485,7 @@ def main():
     if not args.no_extra and world == 1:       # single-GPU workloads, reported at N = 1
         extra["ragged"] = ragged_graph(dev, args.warmup, max(3, args.steps // 4))
         extra["precision_scale"] = precision_scale(dev, args.warmup, max(3, args.steps // 4))
+        extra["augment"] = augment_leg(dev, ds, tile, out, args.warmup, max(3, args.steps // 4), ms)
 
     if rank != 0:
         if world > 1:

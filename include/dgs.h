@@ -293,6 +293,73 @@ int dgs_autotune(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes,
                  dgs_tune_result* out, void* stream);
 
 /*
+ * Image randomisation of rendered frames (Sec. IV: policies are trained on rendered images
+ * that are blended with crops of Internet videos, jittered in HSV space and given a random
+ * gamma).  One parameter set per view, drawn by the caller.  Per pixel (x, y) of a view, with
+ * c its composited RGB (background included):
+ *   c0 = clamp(c, 0, 1)
+ *   c1 = (1 - overlay_beta) c0 + overlay_beta o,   o = overlay[overlay_frame,
+ *        (overlay_y + y) mod overlay_h, (overlay_x + x) mod overlay_w] / 255  (crop with wrap-around;
+ *        not read when overlay_beta = 0)
+ *   (H, S, V) = hexcone HSV of c1 (H in turns; H = 0 for a grey, S = 0 for black)
+ *   c2 = RGB of (frac(H + hue_shift), min(1, S sat_scale), min(1, V val_scale))
+ *   out = c2 ^ gamma  (0 ^ gamma = 0; gamma = 1 leaves c2 unchanged)
+ * Depth and alpha are not randomised.  FP32 arithmetic: the two divisions of the HSV conversion
+ * are approximate (2 ulp), a chroma max - min <= 1e-30 counts as grey, and the power is
+ * 2^(gamma log2 c2) with the hardware's approximate base-2 logarithm and exponential.
+ */
+typedef struct dgs_augment {
+    float hue_shift;            /* turns added to the hue, any finite value (1 = 360 degrees) */
+    float sat_scale;            /* >= 0, finite */
+    float val_scale;            /* >= 0, finite */
+    float gamma;                /* > 0, finite */
+    float overlay_beta;         /* weight of the overlay in the blend, in [0, 1] */
+    int32_t overlay_frame;      /* 0 .. n_frames-1 */
+    int32_t overlay_x;          /* crop origin in the frame: 0 .. overlay_w-1 */
+    int32_t overlay_y;          /* 0 .. overlay_h-1 */
+} dgs_augment;                  /* 32 bytes */
+
+/*
+ * Sets (or clears) the randomisation that every later dgs_render / dgs_autotune call on ctx
+ * applies to its RGB output, fused into the compositing kernel (the un-randomised colour is
+ * never written).
+ *
+ *   aug[n_views]   HOST, one record per view in dgs_render's view order; copied (the caller may
+ *                  free it on return).  aug = NULL or n_views = 0 clears the randomisation.
+ *   overlay        DEVICE uint8 [n_frames, overlay_h, overlay_w, 3] (row-major, interleaved RGB),
+ *                  the clip whose crops are blended in; it must stay valid and unchanged while
+ *                  calls that read it run.  May be NULL only if every overlay_beta is 0.
+ *   n_frames, overlay_w, overlay_h  >= 1 and <= 32768 each when overlay is set.
+ *
+ * A render whose batch does not have exactly n_views views fails with DGS_ERR_INVALID_ARG.
+ * dgs_render_backward fails with DGS_ERR_UNSUPPORTED while a randomisation is set (its
+ * out_rgb must be the un-randomised forward output).  In DGS_MODE_GRAPH the records are
+ * uploaded with the other host tables on every call; a new overlay pointer or shape, or
+ * turning the randomisation on or off, recaptures.  Returns DGS_ERR_INVALID_ARG (and keeps the
+ * previous setting) for a parameter outside the ranges above.  dgs_render_noalloc never
+ * randomises.
+ */
+int dgs_set_augment(dgs_ctx* ctx, const dgs_augment* aug, int32_t n_views, const uint8_t* overlay,
+                    int32_t n_frames, int32_t overlay_w, int32_t overlay_h);
+
+/*
+ * Applies the randomisation set on ctx to an existing RGB image batch, in place, as a
+ * separate kernel (the same per-pixel arithmetic as the fused path, so the result is bitwise
+ * that of dgs_render with the randomisation set).
+ *
+ *   rgb                  DEVICE FP32 [total_pixels,3], read and overwritten.
+ *   view_size[n_views*2] HOST (width, height) of each view, 1..32768.
+ *   view_pixel_offset    HOST [n_views] first pixel of each view, or NULL (views packed in order).
+ *   n_views              must equal the n_views of dgs_set_augment (>= 1).
+ *
+ * Work is queued on `stream` and the call returns without synchronising; the host tables are
+ * staged in the context (the caller's arrays may be freed on return).  Returns
+ * DGS_ERR_INVALID_ARG when no randomisation is set or an argument is out of range.
+ */
+int dgs_augment_rgb(dgs_ctx* ctx, float* rgb, const int32_t* view_size, const int64_t* view_pixel_offset,
+                    int32_t n_views, void* stream);
+
+/*
  * dgs_render_noalloc -- dgs_render for callers that must not allocate GPU memory.  The paper
  * has no counterpart: this is a deployment variant of the same batched render.
  *

@@ -44,6 +44,8 @@ struct GraphKey {
     uint64_t gen;
     int64_t tile_w, tile_h, exact_tile_test;
     int64_t ng, split;
+    const void* overlay;
+    int64_t aug_on, ov_n, ov_w, ov_h;
 };
 
 // Workspace of one view group's lists.  dkey/ival: depth keys and instance numbers (depth
@@ -88,6 +90,14 @@ struct dgs_ctx {
     std::vector<cudaEvent_t> events;
     std::vector<TimedRange> ranges_timed;
     size_t next_event = 0;
+    // image randomisation (dgs_set_augment): per-view records, overlay clip
+    std::vector<dgs_augment> aug;
+    const uint8_t* overlay = nullptr;
+    int32_t ov_n = 0, ov_w = 0, ov_h = 0;
+    DevBuf aug_dev;                       // dgs_augment_rgb: spans + records
+    void* h_aug = nullptr;                // its pinned staging
+    size_t h_aug_bytes = 0;
+    cudaEvent_t aug_copied = nullptr;     // the staging's last upload has been read
 };
 
 namespace {
@@ -329,6 +339,10 @@ int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* e
             view_cam.push_back(c);
         }
     const int V = (int)views.size();
+    const bool aug_on = !ctx->aug.empty();
+    if (aug_on && (int64_t)ctx->aug.size() != V)
+        return fail(ctx, DGS_ERR_INVALID_ARG, "the randomisation is set for " + std::to_string(ctx->aug.size()) +
+                                                  " views, the batch has " + std::to_string(V));
     ctx->stats = dgs_stats{};
     ctx->stats.n_views = V;
     ctx->stats.n_pixels = pix_total;
@@ -405,6 +419,7 @@ int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* e
     const size_t o_pmap = place(sizeof(int32_t) * pmap.size());
     const size_t o_viewtab = place(sizeof(int64_t) * (V + 1));
     const size_t o_grads = place(sizeof(dgs_node_grads) * n_nodes);
+    const size_t o_aug = aug_on ? place(sizeof(dgs_augment) * V) : 0;
     const size_t upload_bytes = off;
     const size_t o_vnodes = place(sizeof(VNode) * V * K);
     const size_t meta_bytes = off;
@@ -424,6 +439,7 @@ int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* e
     std::memcpy(hm + o_viewtab, view_tab.data(), sizeof(int64_t) * (V + 1));
     if (grads) std::memcpy(hm + o_grads, grads, sizeof(dgs_node_grads) * n_nodes);
     else std::memset(hm + o_grads, 0, sizeof(dgs_node_grads) * n_nodes);
+    if (aug_on) std::memcpy(hm + o_aug, ctx->aug.data(), sizeof(dgs_augment) * V);
     char* dm = static_cast<char*>(ctx->meta.p);
     const NodeDesc* d_nodes = reinterpret_cast<const NodeDesc*>(dm + o_nodes);
     const ViewDesc* d_views = reinterpret_cast<const ViewDesc*>(dm + o_views);
@@ -470,6 +486,12 @@ int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* e
     }
     P.err = d_err;
     P.gate = nullptr;
+    if (aug_on) {
+        P.aug = reinterpret_cast<const dgs_augment*>(dm + o_aug);
+        P.overlay = ctx->overlay;
+        P.ov_w = ctx->ov_w;
+        P.ov_h = ctx->ov_h;
+    }
     B.K = K; B.n_nodes = n_nodes; B.dtype_mask = dtype_mask; B.chunk_total = chunk_total;
     B.tiles_total = tiles_total; B.T = T; B.batched = o.mode != DGS_MODE_PLAIN;
     B.views = std::move(views); B.view_tab = std::move(view_tab);
@@ -807,6 +829,8 @@ GraphKey make_key(const dgs_ctx* ctx, const Batch& B, const float* rgb, const fl
     k.gen = ctx->gen;
     k.tile_w = ctx->opt.tile_w; k.tile_h = ctx->opt.tile_h; k.exact_tile_test = ctx->opt.exact_tile_test;
     k.ng = ctx->gng; k.split = ctx->gsplit;
+    k.overlay = ctx->overlay;
+    k.aug_on = !ctx->aug.empty(); k.ov_n = ctx->ov_n; k.ov_w = ctx->ov_w; k.ov_h = ctx->ov_h;
     return k;
 }
 
@@ -1046,6 +1070,9 @@ int dgs_context_destroy(dgs_ctx* ctx) {
     if (ctx->h_graph) cudaFreeHost(ctx->h_graph);
     if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
     if (ctx->h_read) cudaFreeHost(ctx->h_read);
+    free_buf(ctx->aug_dev);
+    if (ctx->h_aug) cudaFreeHost(ctx->h_aug);
+    if (ctx->aug_copied) cudaEventDestroy(ctx->aug_copied);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     delete ctx;
     return DGS_OK;
@@ -1056,7 +1083,7 @@ const char* dgs_last_error(const dgs_ctx* ctx) { return ctx ? ctx->err.c_str() :
 int dgs_workspace_query(const dgs_ctx* ctx, size_t* bytes) {
     if (!ctx || !bytes) return DGS_ERR_INVALID_ARG;
     const DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->errword,
-                            &ctx->readback, &ctx->inst_grad, &ctx->gsizes, &ctx->totals};
+                            &ctx->readback, &ctx->inst_grad, &ctx->gsizes, &ctx->totals, &ctx->aug_dev};
     size_t s = 0;
     for (const DevBuf* b : bufs) s += b->bytes;
     for (const ListBufs& lb : ctx->lists)
@@ -1171,6 +1198,9 @@ int dgs_render_backward(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, co
     if (!ctx) return DGS_ERR_INVALID_ARG;
     begin_call(ctx);
     if (!grad_rgb) return fail(ctx, DGS_ERR_INVALID_ARG, "grad_rgb is required");
+    if (!ctx->aug.empty())
+        return fail(ctx, DGS_ERR_UNSUPPORTED, "a randomisation is set: the adjoint needs the un-randomised forward "
+                                              "outputs (clear it with dgs_set_augment(ctx, NULL, 0, ...))");
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     Timer tm{ctx, stream, ctx->opt.profile != 0};
     Batch B;
@@ -1196,6 +1226,91 @@ int dgs_render_backward(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, co
         DGS_CUDA(ctx, cudaGetLastError());
     }
     return finish(ctx, B, stream);
+}
+
+int dgs_set_augment(dgs_ctx* ctx, const dgs_augment* aug, int32_t n_views, const uint8_t* overlay,
+                    int32_t n_frames, int32_t overlay_w, int32_t overlay_h) {
+    if (!ctx) return DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (n_views < 0) return fail(ctx, DGS_ERR_INVALID_ARG, "n_views must be >= 0");
+    if (!aug || n_views == 0) {
+        ctx->aug.clear();
+        ctx->overlay = nullptr;
+        ctx->ov_n = ctx->ov_w = ctx->ov_h = 0;
+        return DGS_OK;
+    }
+    if (overlay && (n_frames < 1 || n_frames > 32768 || overlay_w < 1 || overlay_w > 32768 || overlay_h < 1 ||
+                    overlay_h > 32768))
+        return fail(ctx, DGS_ERR_INVALID_ARG, "overlay: n_frames, overlay_w and overlay_h must be 1..32768");
+    for (int v = 0; v < n_views; ++v) {
+        const dgs_augment& a = aug[v];
+        const std::string at = "view " + std::to_string(v) + ": ";
+        if (!finite(a.hue_shift)) return fail(ctx, DGS_ERR_INVALID_ARG, at + "hue_shift must be finite");
+        if (!(a.sat_scale >= 0.f) || !finite(a.sat_scale) || !(a.val_scale >= 0.f) || !finite(a.val_scale))
+            return fail(ctx, DGS_ERR_INVALID_ARG, at + "sat_scale and val_scale must be finite and >= 0");
+        if (!(a.gamma > 0.f) || !finite(a.gamma)) return fail(ctx, DGS_ERR_INVALID_ARG, at + "gamma must be finite and > 0");
+        if (!(a.overlay_beta >= 0.f && a.overlay_beta <= 1.f))
+            return fail(ctx, DGS_ERR_INVALID_ARG, at + "overlay_beta must be in [0, 1]");
+        if (a.overlay_beta > 0.f) {
+            if (!overlay) return fail(ctx, DGS_ERR_INVALID_ARG, at + "overlay_beta > 0 needs an overlay");
+            if (a.overlay_frame < 0 || a.overlay_frame >= n_frames || a.overlay_x < 0 || a.overlay_x >= overlay_w ||
+                a.overlay_y < 0 || a.overlay_y >= overlay_h)
+                return fail(ctx, DGS_ERR_INVALID_ARG, at + "overlay frame or crop origin out of range");
+        }
+    }
+    ctx->aug.assign(aug, aug + n_views);
+    ctx->overlay = overlay;
+    ctx->ov_n = overlay ? n_frames : 0;
+    ctx->ov_w = overlay ? overlay_w : 0;
+    ctx->ov_h = overlay ? overlay_h : 0;
+    return DGS_OK;
+}
+
+int dgs_augment_rgb(dgs_ctx* ctx, float* rgb, const int32_t* view_size, const int64_t* view_pixel_offset,
+                    int32_t n_views, void* stream_) {
+    if (!ctx) return DGS_ERR_INVALID_ARG;
+    begin_call(ctx);
+    if (ctx->aug.empty()) return fail(ctx, DGS_ERR_INVALID_ARG, "no randomisation is set (dgs_set_augment)");
+    if (n_views != (int64_t)ctx->aug.size())
+        return fail(ctx, DGS_ERR_INVALID_ARG, "the randomisation is set for " + std::to_string(ctx->aug.size()) +
+                                                  " views, n_views is " + std::to_string(n_views));
+    if (!rgb || !view_size) return fail(ctx, DGS_ERR_INVALID_ARG, "rgb and view_size are required");
+    const int V = n_views;
+    std::vector<AugSpan> spans(V);
+    int64_t q = 0, packed = 0;            // quads so far, pixels so far
+    for (int v = 0; v < V; ++v) {
+        const int32_t w = view_size[2 * v], h = view_size[2 * v + 1];
+        if (w < 1 || h < 1 || w > 32768 || h > 32768) return fail(ctx, DGS_ERR_INVALID_ARG, "view size must be 1..32768");
+        const int64_t off = view_pixel_offset ? view_pixel_offset[v] : packed;
+        if (off < 0) return fail(ctx, DGS_ERR_INVALID_ARG, "negative view_pixel_offset");
+        const int64_t n = (int64_t)w * h;
+        spans[v] = AugSpan{off, q, w, h};
+        q += (off + n - 1) / 4 - off / 4 + 1;    // quads of 4 output pixels holding the view
+        packed += n;
+    }
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    const size_t o_aug = align_up(sizeof(AugSpan) * V, 256);
+    const size_t bytes = o_aug + sizeof(dgs_augment) * V;
+    // the buffer is read by this pass only, never by a captured graph: its reallocation does
+    // not invalidate one
+    const uint64_t gen = ctx->gen;
+    int rc = ensure(ctx, ctx->aug_dev, bytes);
+    ctx->gen = gen;
+    if (rc) return rc;
+    if ((rc = ensure_host(ctx, ctx->h_aug, ctx->h_aug_bytes, bytes))) return rc;
+    if (!ctx->aug_copied) DGS_CUDA(ctx, cudaEventCreateWithFlags(&ctx->aug_copied, cudaEventDisableTiming));
+    else DGS_CUDA(ctx, cudaEventSynchronize(ctx->aug_copied));   // the previous upload from the staging is done
+    char* hs = static_cast<char*>(ctx->h_aug);
+    std::memcpy(hs, spans.data(), sizeof(AugSpan) * V);
+    std::memcpy(hs + o_aug, ctx->aug.data(), sizeof(dgs_augment) * V);
+    char* ds = static_cast<char*>(ctx->aug_dev.p);
+    DGS_CUDA(ctx, cudaMemcpyAsync(ds, hs, bytes, cudaMemcpyHostToDevice, stream));
+    DGS_CUDA(ctx, cudaEventRecord(ctx->aug_copied, stream));
+    Launch L{stream, &ctx->launches};
+    launch_augment(L, reinterpret_cast<const AugSpan*>(ds), V, q, reinterpret_cast<const dgs_augment*>(ds + o_aug),
+                   ctx->overlay, ctx->ov_w, ctx->ov_h, rgb);
+    DGS_CUDA(ctx, cudaGetLastError());
+    return DGS_OK;
 }
 
 }  // extern "C"

@@ -44,8 +44,9 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, uint32_t n, const ui
 // block barrier): each walks the tile's list 32 entries at a time, keeps the entries whose
 // pixel box overlaps its sub-tile and whose ellipse reaches one of its pixel centres (exact
 // test with the binning margin), stages them in list order in its own shared memory and
-// composites them; it stops once its 32 pixels have terminated.
-template <bool COUNT>
+// composites them; it stops once its 32 pixels have terminated.  AUG: the view's image
+// randomisation is applied to the RGB before it is stored.
+template <bool COUNT, bool AUG>
 __global__ void __launch_bounds__(256, 6) k_composite(const ViewDesc* __restrict__ views, int v0, int nv,
                                                    const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                                                    const Record* __restrict__ rec, Params P, float* __restrict__ out_rgb,
@@ -131,9 +132,15 @@ __global__ void __launch_bounds__(256, 6) k_composite(const ViewDesc* __restrict
     }
     if (inside) {
         const int64_t p = vd.pix_off + (int64_t)py * vd.W + px;
-        out_rgb[p * 3 + 0] = fmaf(P.bg0, T, C0);
-        out_rgb[p * 3 + 1] = fmaf(P.bg1, T, C1);
-        out_rgb[p * 3 + 2] = fmaf(P.bg2, T, C2);
+        float r = fmaf(P.bg0, T, C0), g = fmaf(P.bg1, T, C1), b = fmaf(P.bg2, T, C2);
+        if (AUG) {
+            const dgs_augment& a = P.aug[lo];
+            augment_pixel(a, a.overlay_beta != 0.f ? overlay_pixel(P.overlay, P.ov_w, P.ov_h, a, px, py) : nullptr,
+                          r, g, b);
+        }
+        out_rgb[p * 3 + 0] = r;
+        out_rgb[p * 3 + 1] = g;
+        out_rgb[p * 3 + 2] = b;
         out_depth[p] = D;
         if (out_alpha) out_alpha[p] = 1.f - T;
     }
@@ -154,13 +161,10 @@ void launch_composite(const Launch& L, const ViewDesc* views, int v0, int n_grou
                       const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,
                       float* out_rgb, float* out_depth, float* out_alpha, unsigned long long* work) {
     if (n_tiles == 0) return;
-    if (work)
-        k_composite<true><<<n_tiles, P.tile_w * P.tile_h, 0, L.stream>>>(views, v0, n_group_views, ranges, vals, records,
-                                                                          P, out_rgb, out_depth, out_alpha, work);
-    else
-        k_composite<false><<<n_tiles, P.tile_w * P.tile_h, 0, L.stream>>>(views, v0, n_group_views, ranges, vals,
-                                                                           records, P, out_rgb, out_depth, out_alpha,
-                                                                           nullptr);
+    auto* kern = work ? (P.aug ? k_composite<true, true> : k_composite<true, false>)
+                      : (P.aug ? k_composite<false, true> : k_composite<false, false>);
+    kern<<<n_tiles, P.tile_w * P.tile_h, 0, L.stream>>>(views, v0, n_group_views, ranges, vals, records, P, out_rgb,
+                                                        out_depth, out_alpha, work);
     ++*L.launches;
 }
 

@@ -67,6 +67,10 @@ struct Params {
     const uint32_t* gate; // emission is skipped when non-null and *gate != 0 (capacity overflow)
     float p_min;          // kHalfLog2e * q_max: exponents below it are outside the 3-sigma ellipse
     const uint32_t* inst_base_dev;  // emission: first record of the group read on the device (graph replay)
+    // image randomisation of the RGB output (null aug = none): per-view records, overlay clip
+    const dgs_augment* aug;
+    const uint8_t* overlay;
+    int32_t ov_w, ov_h;
 };
 
 // Projected instance as stored for compositing: 48 bytes.
@@ -157,6 +161,66 @@ __device__ __forceinline__ float fast_exp2(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+__device__ __forceinline__ float fast_log2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Image randomisation of one pixel (Sec. IV): clamp to [0, 1], linear blend with the overlay
+// pixel o (3 bytes; read only when overlay_beta != 0), hue shift and saturation/value scaling
+// in the hexcone HSV model, then the power curve c^gamma evaluated as 2^(gamma log2 c).
+// Every multiply-add is an explicit fmaf, so the fused and the separate kernel round
+// identically.  The hue's sector is chosen with selects, not branches.  HSV -> RGB uses the
+// per-channel form c_n = V - V S clamp(min(k, 4 - k), 0, 1), k = (n + 6H) mod 6, n = 5, 3, 1
+// for red, green, blue, which equals the six-sector table of the model.
+__device__ __forceinline__ void augment_pixel(const dgs_augment& a, const uint8_t* __restrict__ o, float& r,
+                                              float& g, float& b) {
+    r = fminf(fmaxf(r, 0.f), 1.f);
+    g = fminf(fmaxf(g, 0.f), 1.f);
+    b = fminf(fmaxf(b, 0.f), 1.f);
+    const float beta = a.overlay_beta;
+    if (beta != 0.f) {
+        constexpr float k255 = 1.f / 255.f;
+        r = fmaf(beta, fmaf((float)o[0], k255, -r), r);
+        g = fmaf(beta, fmaf((float)o[1], k255, -g), g);
+        b = fmaf(beta, fmaf((float)o[2], k255, -b), b);
+    }
+    const float v = fmaxf(fmaxf(r, g), b), m = fminf(fminf(r, g), b), c = v - m;
+    // hue in sixths of a turn from the sector of the largest channel (red first, then green);
+    // a chroma <= 1e-30 counts as grey (H = S = 0), which keeps 1/c finite
+    const bool grey = !(c > 1e-30f), is_r = v == r, is_g = v == g;
+    const float num = is_r ? g - b : (is_g ? b - r : r - g);
+    const float off = is_r ? 0.f : (is_g ? 2.f : 4.f);
+    float h = grey ? 0.f : __fdividef(num, c) + off;
+    if (h < 0.f) h += 6.f;
+    const float s = grey ? 0.f : __fdividef(c, v);
+    h = fmaf(6.f, a.hue_shift, h);
+    h = fmaf(-6.f, floorf(h * (1.f / 6.f)), h);      // [0, 6) up to one rounding
+    const float vv = fminf(1.f, v * a.val_scale);
+    const float vs = vv * fminf(1.f, s * a.sat_scale);
+    float k;
+    k = 5.f + h; if (k >= 6.f) k -= 6.f;
+    r = fmaf(-vs, fminf(fmaxf(fminf(k, 4.f - k), 0.f), 1.f), vv);
+    k = 3.f + h; if (k >= 6.f) k -= 6.f;
+    g = fmaf(-vs, fminf(fmaxf(fminf(k, 4.f - k), 0.f), 1.f), vv);
+    k = 1.f + h; if (k >= 6.f) k -= 6.f;
+    b = fmaf(-vs, fminf(fmaxf(fminf(k, 4.f - k), 0.f), 1.f), vv);
+    if (a.gamma != 1.f) {
+        r = fast_exp2(a.gamma * fast_log2(r));
+        g = fast_exp2(a.gamma * fast_log2(g));
+        b = fast_exp2(a.gamma * fast_log2(b));
+    }
+}
+
+// The overlay pixel a view's pixel (x, y) blends with: frame overlay_frame, row
+// (overlay_y + y) mod oh, column (overlay_x + x) mod ow of the [frames, oh, ow, 3] clip.
+__device__ __forceinline__ const uint8_t* overlay_pixel(const uint8_t* overlay, int ow, int oh, const dgs_augment& a,
+                                                        int x, int y) {
+    const int ox = (a.overlay_x + x) % ow, oy = (a.overlay_y + y) % oh;
+    return overlay + (((int64_t)a.overlay_frame * oh + oy) * ow + ox) * 3;
 }
 
 // Exponent p of a staged record (scaled coefficients ca, qb, cc) at pixel offset (dx, dy);
@@ -263,6 +327,18 @@ void launch_ranges(const Launch& L, const uint32_t* keys, uint32_t n, uint2* ran
 void launch_composite(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
                       const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,
                       float* out_rgb, float* out_depth, float* out_alpha, unsigned long long* work);
+
+// Image randomisation of an RGB batch in place (the separate form of the compositor's
+// epilogue).  spans[V]: per view its first output pixel, its first quad in the view-by-view
+// enumeration of the 4-pixel quads (of the global pixel index) that hold its pixels, and its
+// size; n_quads = total quads.
+struct AugSpan {
+    int64_t pix_off;
+    int64_t q0;
+    int32_t W, H;
+};
+void launch_augment(const Launch& L, const AugSpan* spans, int V, int64_t n_quads, const dgs_augment* aug,
+                    const uint8_t* overlay, int ow, int oh, float* rgb);
 
 void launch_composite_bwd(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
                           const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,

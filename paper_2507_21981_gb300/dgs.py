@@ -60,9 +60,16 @@ class dgs_tune_result(C.Structure):
                 ("tile_h", C.c_int32 * DGS_TUNE_MAX), ("ms", C.c_float * DGS_TUNE_MAX)]
 
 
+class dgs_augment(C.Structure):
+    _fields_ = [("hue_shift", C.c_float), ("sat_scale", C.c_float), ("val_scale", C.c_float), ("gamma", C.c_float),
+                ("overlay_beta", C.c_float), ("overlay_frame", C.c_int32), ("overlay_x", C.c_int32),
+                ("overlay_y", C.c_int32)]
+
+
 EXPORTED = ("dgs_default_options", "dgs_context_create", "dgs_context_destroy", "dgs_last_error",
             "dgs_workspace_query", "dgs_render", "dgs_last_stats", "dgs_kernel_times", "dgs_last_launches",
-            "dgs_render_noalloc", "dgs_render_backward", "dgs_autotune", "dgs_spatial_order")
+            "dgs_render_noalloc", "dgs_render_backward", "dgs_autotune", "dgs_spatial_order",
+            "dgs_set_augment", "dgs_augment_rgb")
 
 _lib = None
 _lock = threading.Lock()
@@ -115,6 +122,10 @@ def load(path: str | None = None) -> C.CDLL:
         lib.dgs_render_noalloc.restype = C.c_int
         lib.dgs_render_noalloc.argtypes = [C.POINTER(dgs_options), C.POINTER(dgs_node), i32, vp, i32, i32, vp,
                                            C.POINTER(dgs_camera), vp, i32, vp, vp, vp, vp, vp]
+        lib.dgs_set_augment.restype = C.c_int
+        lib.dgs_set_augment.argtypes = [vp, vp, i32, vp, i32, i32, i32]
+        lib.dgs_augment_rgb.restype = C.c_int
+        lib.dgs_augment_rgb.argtypes = [vp, vp, vp, vp, i32, vp]
         if path is None:
             _lib = lib
         return lib
@@ -231,3 +242,19 @@ def dgs_spatial_order(mean) -> np.ndarray:
     if rc != DGS_OK:
         raise DgsError(rc, "dgs_spatial_order")
     return perm
+
+
+def dgs_set_augment(ctx, aug, n_views, overlay, n_frames, overlay_w, overlay_h) -> int:
+    """Direct call of dgs_set_augment.  `aug` is a numpy record array with dgs_augment's layout
+    (scenes.AUGMENT_DTYPE) or a ctypes array of dgs_augment, or None to clear; `overlay` a uint8
+    device tensor [n_frames, overlay_h, overlay_w, 3], an integer device address, or None."""
+    if isinstance(aug, np.ndarray):
+        assert aug.dtype.itemsize == C.sizeof(dgs_augment) and aug.flags.c_contiguous
+    return load().dgs_set_augment(ctx, _ptr(aug) if not isinstance(aug, C.Array) else C.addressof(aug),
+                                  int(n_views), _ptr(overlay), int(n_frames), int(overlay_w), int(overlay_h))
+
+
+def dgs_augment_rgb(ctx, rgb, view_size, view_pixel_offset, n_views, stream) -> int:
+    """Direct call of dgs_augment_rgb; view_size is a host int32 [n_views, 2] array of (width, height)."""
+    vs = np.ascontiguousarray(view_size, np.int32)
+    return load().dgs_augment_rgb(ctx, _ptr(rgb), vs.ctypes.data, _ptr(view_pixel_offset), int(n_views), stream)

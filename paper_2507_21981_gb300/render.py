@@ -112,6 +112,7 @@ class Renderer:
             else:
                 setattr(o, k, v)
         self.options = o
+        self._aug = None
         self.ctx = D.dgs_context_create(o)
 
     def close(self):
@@ -134,6 +135,38 @@ class Renderer:
         if rc != D.DGS_OK:
             raise D.DgsError(rc, D.dgs_last_error(self.ctx))
         return rgb, depth, alpha
+
+    def set_augment(self, params=None, overlay=None):
+        """Sets the per-view image randomisation that every later render applies to its RGB
+        (dgs_set_augment): `params` a record array with dgs_augment's fields (one per view), or
+        None to clear; `overlay` a uint8 CUDA tensor [frames, height, width, 3] (kept alive
+        here while the randomisation is set)."""
+        if params is None:
+            rc = D.dgs_set_augment(self.ctx, None, 0, None, 0, 0, 0)
+            self._aug = None
+        else:
+            prm = np.ascontiguousarray(params)
+            if overlay is not None:
+                assert overlay.dtype == torch.uint8 and overlay.is_cuda and overlay.dim() == 4 and overlay.shape[3] == 3
+                overlay = overlay.contiguous()
+                nf, oh, ow = (int(x) for x in overlay.shape[:3])
+            else:
+                nf = oh = ow = 0
+            rc = D.dgs_set_augment(self.ctx, prm, len(prm), overlay, nf, ow, oh)
+            if rc == D.DGS_OK:
+                self._aug = (prm, overlay)
+        if rc != D.DGS_OK:
+            raise D.DgsError(rc, D.dgs_last_error(self.ctx))
+
+    def augment_rgb(self, ds: DeviceScene, rgb, stream=None):
+        """Applies the randomisation set by set_augment to `rgb` ([P,3] FP32 CUDA, flat over the
+        views of `ds`) in place, as a separate kernel (dgs_augment_rgb)."""
+        s = stream if stream is not None else torch.cuda.current_stream(ds.device)
+        sizes = np.asarray(ds.view_res, np.int32).reshape(-1, 2)
+        rc = D.dgs_augment_rgb(self.ctx, rgb, sizes, None, ds.n_views, s.cuda_stream)
+        if rc != D.DGS_OK:
+            raise D.DgsError(rc, D.dgs_last_error(self.ctx))
+        return rgb
 
     def _outputs(self, ds: DeviceScene, with_alpha: bool):
         def fresh():

@@ -58,6 +58,14 @@ def test_struct_sizes_match_header(lib):
     assert C.sizeof(D.dgs_options) == 64
     assert C.sizeof(D.dgs_stats) == 80
     assert C.sizeof(D.dgs_tune_result) == 8 + 3 * 4 * D.DGS_TUNE_MAX
+    assert C.sizeof(D.dgs_augment) == 32
+
+
+def test_augment_record_layout_matches_the_numpy_generator():
+    from paper_2507_21981_gb300 import scenes as S
+    assert S.AUGMENT_DTYPE.itemsize == C.sizeof(D.dgs_augment)
+    for name, _ in D.dgs_augment._fields_:
+        assert S.AUGMENT_DTYPE.fields[name][1] == getattr(D.dgs_augment, name).offset, name
 
 
 def test_invalid_options_rejected(lib):
@@ -175,3 +183,57 @@ def test_autotune_validates_arguments_on_host(lib):
 
 def test_build_flags_target_sm103a():
     assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _aug(n, **kw):
+    from paper_2507_21981_gb300 import scenes as S
+    a = np.zeros(n, S.AUGMENT_DTYPE)
+    a["sat_scale"] = 1.0
+    a["val_scale"] = 1.0
+    a["gamma"] = 1.0
+    for k, v in kw.items():
+        a[k] = v
+    return a
+
+
+def test_set_augment_validates_on_host(lib):
+    ctx = _ctx(lib)
+    try:
+        def setp(a, ov=None, nf=0, w=0, h=0):
+            return lib.dgs_set_augment(ctx, None if a is None else a.ctypes.data, 0 if a is None else len(a), ov,
+                                       nf, w, h)
+        assert lib.dgs_set_augment(None, None, 0, None, 0, 0, 0) == D.DGS_ERR_INVALID_ARG
+        assert setp(_aug(2)) == D.DGS_OK                                   # no overlay needed at weight 0
+        assert setp(None) == D.DGS_OK                                      # clears
+        assert lib.dgs_set_augment(ctx, _aug(1).ctypes.data, -1, None, 0, 0, 0) == D.DGS_ERR_INVALID_ARG
+        for bad in (dict(gamma=0.0), dict(gamma=float("inf")), dict(sat_scale=-0.1), dict(val_scale=float("nan")),
+                    dict(hue_shift=float("inf")), dict(overlay_beta=1.5), dict(overlay_beta=float("nan"))):
+            assert setp(_aug(2, **bad)) == D.DGS_ERR_INVALID_ARG, bad
+        assert setp(_aug(2, overlay_beta=0.5)) == D.DGS_ERR_INVALID_ARG  # weight > 0 without an overlay
+        assert "overlay" in D.dgs_last_error(ctx)
+        assert setp(_aug(2, overlay_beta=0.5), FAKE_DEV, 2, 64, 48) == D.DGS_OK
+        assert setp(_aug(2, overlay_beta=0.5, overlay_frame=2), FAKE_DEV, 2, 64, 48) == D.DGS_ERR_INVALID_ARG
+        assert setp(_aug(2, overlay_beta=0.5, overlay_x=64), FAKE_DEV, 2, 64, 48) == D.DGS_ERR_INVALID_ARG
+        assert setp(_aug(2, overlay_beta=0.5, overlay_y=-1), FAKE_DEV, 2, 64, 48) == D.DGS_ERR_INVALID_ARG
+        assert setp(_aug(2), FAKE_DEV, 0, 64, 48) == D.DGS_ERR_INVALID_ARG   # bad overlay shape
+        # the last valid setting (2 views) stands: a one-view render is refused before any device work
+        nodes, ids, cams, cpe = _args()
+        assert _render(lib, ctx, nodes, 1, ids, 1, 1, cams, cpe, 1) == D.DGS_ERR_INVALID_ARG
+        assert "2 views" in D.dgs_last_error(ctx)
+        # the adjoint refuses while a randomisation is set
+        assert lib.dgs_render_backward(ctx, nodes, 1, ids.ctypes.data, 1, 1, FAKE_DEV, cams, cpe.ctypes.data, 1,
+                                       FAKE_DEV, FAKE_DEV, FAKE_DEV, None, None, None, None, None) \
+            == D.DGS_ERR_UNSUPPORTED
+        # the separate pass: view count and sizes are checked on the host
+        sizes = np.array([[8, 8], [8, 8]], np.int32)
+        assert lib.dgs_augment_rgb(ctx, FAKE_DEV, sizes.ctypes.data, None, 1, None) == D.DGS_ERR_INVALID_ARG
+        assert lib.dgs_augment_rgb(ctx, None, sizes.ctypes.data, None, 2, None) == D.DGS_ERR_INVALID_ARG
+        bad = np.array([[8, 8], [0, 8]], np.int32)
+        assert lib.dgs_augment_rgb(ctx, FAKE_DEV, bad.ctypes.data, None, 2, None) == D.DGS_ERR_INVALID_ARG
+        neg = np.array([0, -5], np.int64)
+        assert lib.dgs_augment_rgb(ctx, FAKE_DEV, sizes.ctypes.data, neg.ctypes.data, 2, None) == D.DGS_ERR_INVALID_ARG
+        assert setp(None) == D.DGS_OK
+        assert lib.dgs_augment_rgb(ctx, FAKE_DEV, sizes.ctypes.data, None, 2, None) == D.DGS_ERR_INVALID_ARG
+        assert "no randomisation" in D.dgs_last_error(ctx)
+    finally:
+        lib.dgs_context_destroy(ctx)
