@@ -33,7 +33,7 @@ OPS_PER_PAIR = 21
 # DRAM bytes (read + write) per launch on the full workload, from the ncu capture of the same
 # kernel on the 8-env case (profiles/kernels_config2_8envs_640x480.md: 120.7 + 70.4 MB) scaled
 # by the 8x views of the full launch; absent for a kernel that changed since its capture.
-TRAFFIC = {"composite": (120.7e6 + 70.4e6) * 8}
+TRAFFIC = {"composite": (116.2e6 + 68.6e6) * 8}
 WORKLOAD = "64 envs x 2 cams 640x480, 1M-Gaussian SH3 room + 4 objects x 20k at per-env poses (config 2)"
 
 
