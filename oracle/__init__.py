@@ -8,11 +8,12 @@ cams_per_env, cam_intr, cam_res, cam_pose).
 
 The rendering arithmetic lives in oracle.cpp (plain FP64 C++, std::thread over pixel rows);
 see its header for the definition it implements and the readings it fixes.  The image
-randomisation applied to rendered frames is augment.py (numpy, FP64).
+randomisation applied to rendered frames is augment.py (numpy, FP64); LiDAR ray tracing of the
+same Gaussians is lidar.cpp / lidar.py (FP64 C++, brute force over the env's Gaussians).
 """
-from . import augment
+from . import augment, lidar
 from .oracle import (OracleOptions, build, lib_path, project_view, render_view, backward_view,
                      backward_scene, pose_twist_grad, sh_basis, depth_key32)
 
-__all__ = ["OracleOptions", "augment", "build", "lib_path", "project_view", "render_view", "backward_view",
+__all__ = ["OracleOptions", "augment", "lidar", "build", "lib_path", "project_view", "render_view", "backward_view",
            "backward_scene", "pose_twist_grad", "sh_basis", "depth_key32"]

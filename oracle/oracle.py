@@ -11,6 +11,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.cpp")
+_SRCS = [_SRC, os.path.join(_HERE, "lidar.cpp")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -21,11 +22,11 @@ def lib_path() -> str:
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.cpp into liboracle.so next to it (g++, -O2, portable flags only)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile oracle.cpp and lidar.cpp into liboracle.so next to them (g++, -O2, portable flags only)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(p) for p in _SRCS):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", "-pthread",
-                               "-o", tmp, _SRC])
+                               "-o", tmp, *_SRCS])
         os.replace(tmp, _LIB)
     return _LIB
 

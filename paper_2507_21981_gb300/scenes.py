@@ -527,3 +527,37 @@ def augment_params(seed: int, n_views: int, n_frames: int, overlay_w: int, overl
     p["overlay_x"] = rng.integers(0, overlay_w, n_views)
     p["overlay_y"] = rng.integers(0, overlay_h, n_views)
     return p
+
+
+# ------------------------------------------------------------------------------------- LiDAR
+def lidar_pattern(channels: int = 32, azimuths: int = 1024, el_min_deg: float = -30.67,
+                  el_max_deg: float = 10.67, az0_deg: float = 0.0, az_span_deg: float = 360.0) -> np.ndarray:
+    """Beam directions of a spinning multi-channel LiDAR in its own frame (x forward, y left,
+    z up): `channels` elevations spaced evenly over [el_min, el_max] (the defaults are those
+    of a 32-beam automotive unit) times `azimuths` evenly spaced azimuths; float32 [channels *
+    azimuths, 3] unit vectors, channel-major."""
+    el = np.deg2rad(np.linspace(el_min_deg, el_max_deg, channels))
+    az = np.deg2rad(az0_deg + az_span_deg * np.arange(azimuths) / azimuths)
+    ce, se = np.cos(el)[:, None], np.sin(el)[:, None]
+    d = np.stack([ce * np.cos(az)[None, :], ce * np.sin(az)[None, :], np.broadcast_to(se, (channels, azimuths))],
+                 axis=-1)
+    return np.ascontiguousarray(d.reshape(-1, 3).astype(np.float32))
+
+
+def lidar_sensors(seed: int, n_envs: int, radius=(1.0, 2.0), height=(0.8, 1.6), tilt_deg: float = 2.0):
+    """One LiDAR per env, mounted as on a mobile robot near the workspace: at a distance in
+    `radius` from the workspace centre (horizontally), at a height in `height`, facing the
+    workspace within 30 degrees of yaw, tilted by N(0, tilt_deg).  Returns (sensor_env int32
+    [n_envs], world_from_sensor float32 [n_envs, 3, 4])."""
+    rng = _rng(seed, 103)
+    poses = np.zeros((n_envs, 3, 4), np.float64)
+    for e in range(n_envs):
+        phi = rng.uniform(-np.pi, np.pi)
+        r = rng.uniform(*radius)
+        p = np.array([WORKSPACE_CENTRE[0] + r * math.cos(phi), WORKSPACE_CENTRE[1] + r * math.sin(phi),
+                      rng.uniform(*height)])
+        yaw = phi + np.pi + rng.uniform(-np.pi / 6, np.pi / 6)      # x axis towards the workspace
+        ax = rng.normal(size=2)
+        R = _rot_axis([ax[0], ax[1], 0.0], np.deg2rad(rng.normal(0.0, tilt_deg))) @ _rot_axis([0, 0, 1], yaw)
+        poses[e] = np.concatenate([_orthonormalise(R), p[:, None]], axis=1)
+    return np.arange(n_envs, dtype=np.int32), poses.astype(np.float32)
