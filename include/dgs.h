@@ -360,6 +360,52 @@ int dgs_augment_rgb(dgs_ctx* ctx, float* rgb, const int32_t* view_size, const in
                     int32_t n_views, void* stream);
 
 /*
+ * LiDAR by Gaussian ray tracing (Sec. III-C: LiDAR is simulated by native ray tracing of the
+ * scene's Gaussians, accelerated by a BVH).  For a ray o + t d (|d| = 1, t in metres) and a
+ * Gaussian with mean mu and whitening M = diag(1/s) R^T in its node's frame (o, d moved there
+ * with the node's pose): o' = M (o - mu), d' = M d; the response peaks at
+ * t* = -(o'.d') / (d'.d') with Mahalanobis distance q* = |o' x d'|^2 / (d'.d').  A Gaussian is
+ * hit iff q* <= q_max and r_min <= t* <= r_max; alpha = min(alpha_max, opacity exp(-q* / 2)),
+ * skipped when < alpha_min.  Hits composite front to back in (t*, global id) order, stopping
+ * (without the current hit) once T (1 - alpha) < t_min: D = sum T alpha t* (not normalised),
+ * A = 1 - T_final.  The return's range is D / A.  q_max, alpha_min, alpha_max and t_min are the
+ * context's options.  FP32 arithmetic.
+ */
+typedef struct dgs_lidar {
+    int32_t env;                /* the env whose nodes the sensor sees */
+    float world_from_sensor[12]; /* row-major [R|t], R orthonormal within 1e-4 */
+} dgs_lidar;                    /* 52 bytes */
+
+/*
+ * Builds the ray-tracing structures of the nodes on the context: per Gaussian a 64-byte record
+ * (mean, opacity, whitening matrix) and per node an implicit binary BVH over leaves of 8
+ * consecutive Gaussians in storage order (store nodes in dgs_spatial_order for compact
+ * leaves), boxes of the q_max ellipsoids in the node's frame.  Reads the nodes' mean,
+ * log_scale, quat and opacity_logit (DEVICE, any dgs_dtype); replaces any earlier build.  Call
+ * it again whenever those attributes change.  Synchronises `stream`.  Returns
+ * DGS_ERR_INVALID_ARG for the node errors dgs_render reports.
+ */
+int dgs_lidar_build(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, void* stream);
+
+/*
+ * Traces n_sensors x n_dirs rays: ray (s, j) starts at sensor s's origin along
+ * R_s dirs[j] (normalised).
+ *   nodes, n_nodes                the nodes of the last dgs_lidar_build (same sizes and attribute
+ *                                 pointers; else DGS_ERR_INVALID_ARG)
+ *   env_node_ids, n_envs, max_nodes, node_poses   as for dgs_render (node_poses DEVICE)
+ *   sensors[n_sensors]            HOST
+ *   dirs[n_dirs*3]                DEVICE FP32 sensor-frame directions (non-zero)
+ *   r_min, r_max                  range window, 0 <= r_min < r_max, finite
+ *   out_d, out_a                  DEVICE FP32 [n_sensors*n_dirs], sensor-major
+ * Work is queued on `stream`; the call synchronises it before returning (device-side pose
+ * validation is reported as DGS_ERR_INVALID_ARG).
+ */
+int dgs_lidar_trace(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes,
+                    const int32_t* env_node_ids, int32_t n_envs, int32_t max_nodes, const float* node_poses,
+                    const dgs_lidar* sensors, int32_t n_sensors, const float* dirs, int32_t n_dirs,
+                    float r_min, float r_max, float* out_d, float* out_a, void* stream);
+
+/*
  * dgs_render_noalloc -- dgs_render for callers that must not allocate GPU memory.  The paper
  * has no counterpart: this is a deployment variant of the same batched render.
  *

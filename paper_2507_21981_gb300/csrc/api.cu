@@ -98,6 +98,11 @@ struct dgs_ctx {
     void* h_aug = nullptr;                // its pinned staging
     size_t h_aug_bytes = 0;
     cudaEvent_t aug_copied = nullptr;     // the staging's last upload has been read
+    // LiDAR (dgs_lidar_build / dgs_lidar_trace)
+    DevBuf lid_rec, lid_box, lid_tab, lid_meta, lid_slots;
+    std::vector<dgs_node> lid_nodes;      // the nodes the structures were built from
+    void* h_lid = nullptr;                // pinned staging of the per-call tables
+    size_t h_lid_bytes = 0;
 };
 
 namespace {
@@ -1071,6 +1076,8 @@ int dgs_context_destroy(dgs_ctx* ctx) {
     if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
     if (ctx->h_read) cudaFreeHost(ctx->h_read);
     free_buf(ctx->aug_dev);
+    for (DevBuf* b : {&ctx->lid_rec, &ctx->lid_box, &ctx->lid_tab, &ctx->lid_meta, &ctx->lid_slots}) free_buf(*b);
+    if (ctx->h_lid) cudaFreeHost(ctx->h_lid);
     if (ctx->h_aug) cudaFreeHost(ctx->h_aug);
     if (ctx->aug_copied) cudaEventDestroy(ctx->aug_copied);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
@@ -1083,7 +1090,8 @@ const char* dgs_last_error(const dgs_ctx* ctx) { return ctx ? ctx->err.c_str() :
 int dgs_workspace_query(const dgs_ctx* ctx, size_t* bytes) {
     if (!ctx || !bytes) return DGS_ERR_INVALID_ARG;
     const DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->errword,
-                            &ctx->readback, &ctx->inst_grad, &ctx->gsizes, &ctx->totals, &ctx->aug_dev};
+                            &ctx->readback, &ctx->inst_grad, &ctx->gsizes, &ctx->totals, &ctx->aug_dev,
+                            &ctx->lid_rec, &ctx->lid_box, &ctx->lid_tab, &ctx->lid_meta, &ctx->lid_slots};
     size_t s = 0;
     for (const DevBuf* b : bufs) s += b->bytes;
     for (const ListBufs& lb : ctx->lists)
@@ -1310,6 +1318,182 @@ int dgs_augment_rgb(dgs_ctx* ctx, float* rgb, const int32_t* view_size, const in
     launch_augment(L, reinterpret_cast<const AugSpan*>(ds), V, q, reinterpret_cast<const dgs_augment*>(ds + o_aug),
                    ctx->overlay, ctx->ov_w, ctx->ov_h, rgb);
     DGS_CUDA(ctx, cudaGetLastError());
+    return DGS_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------- LiDAR
+namespace {
+
+int check_nodes(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes) {
+    if (n_nodes < 1 || !nodes) return fail(ctx, DGS_ERR_INVALID_ARG, "nodes: need n_nodes >= 1 and a node array");
+    int64_t total = 0;
+    for (int k = 0; k < n_nodes; ++k) {
+        const dgs_node& nd = nodes[k];
+        if (nd.n < 0 || nd.sh_degree < 0 || nd.sh_degree > 3 || nd.dtype < 0 || nd.dtype > 2)
+            return fail(ctx, DGS_ERR_INVALID_ARG, "node " + std::to_string(k) + ": bad n, sh_degree or dtype");
+        if (nd.n > 0 && (!nd.mean || !nd.log_scale || !nd.quat || !nd.opacity_logit))
+            return fail(ctx, DGS_ERR_INVALID_ARG, "node " + std::to_string(k) + ": null attribute pointer");
+        total += nd.n;
+    }
+    if (total >= (1ll << 32)) return fail(ctx, DGS_ERR_INVALID_ARG, "more than 2^32 Gaussians");
+    return DGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dgs_lidar_build(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, void* stream_) {
+    if (!ctx) return DGS_ERR_INVALID_ARG;
+    begin_call(ctx);
+    int rc = check_nodes(ctx, nodes, n_nodes);
+    if (rc) return rc;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    ctx->lid_nodes.clear();
+    std::vector<int64_t> P(n_nodes), rec_off(n_nodes), box_off(n_nodes);
+    int64_t n_rec = 0, n_box = 0, maxP = 0;
+    for (int k = 0; k < n_nodes; ++k) {
+        const int64_t nodes2 = (int64_t)lidar_tree_nodes(nodes[k].n);
+        P[k] = nodes2 / 2;
+        rec_off[k] = n_rec;
+        box_off[k] = n_box;
+        n_rec += nodes[k].n;
+        n_box += nodes2;
+        maxP = std::max(maxP, P[k]);
+    }
+    // level jobs: for h = maxP/2 .. 1, every tree with P >= 2h
+    std::vector<std::pair<int64_t, std::vector<std::pair<int, int64_t>>>> levels;
+    size_t n_jobs = 0;
+    for (int64_t h = maxP / 2; h >= 1; h /= 2) {
+        std::vector<std::pair<int, int64_t>> jobs;
+        int64_t first = 0;
+        for (int k = 0; k < n_nodes; ++k)
+            if (P[k] >= 2 * h) { jobs.push_back({k, first}); first += h; }
+        n_jobs += jobs.size();
+        levels.push_back({h, std::move(jobs)});
+    }
+    const size_t jb = lidar_level_job_bytes();
+    const size_t o_jobs = align_up(sizeof(LidarTreeDev) * n_nodes, 256);
+    const size_t tab_bytes = o_jobs + jb * std::max<size_t>(n_jobs, 1);
+    if ((rc = ensure(ctx, ctx->lid_rec, sizeof(float4) * 4 * std::max<int64_t>(n_rec, 1)))) return rc;
+    if ((rc = ensure(ctx, ctx->lid_box, sizeof(float4) * 2 * std::max<int64_t>(n_box, 1)))) return rc;
+    if ((rc = ensure(ctx, ctx->lid_tab, tab_bytes))) return rc;
+    float4* rec = static_cast<float4*>(ctx->lid_rec.p);
+    float4* box = static_cast<float4*>(ctx->lid_box.p);
+    std::vector<char> host(tab_bytes, 0);
+    int64_t gbase = 0;
+    for (int k = 0; k < n_nodes; ++k) {
+        LidarTreeDev t{box + 2 * box_off[k], rec + 4 * rec_off[k], nodes[k].n, P[k], (uint32_t)gbase};
+        std::memcpy(host.data() + sizeof(LidarTreeDev) * k, &t, sizeof(t));
+        gbase += nodes[k].n;
+    }
+    size_t ji = 0;
+    for (auto& lv : levels)
+        for (auto& j : lv.second) lidar_level_job(host.data() + o_jobs, (int)ji++, box + 2 * box_off[j.first], j.second);
+    DGS_CUDA(ctx, cudaMemcpyAsync(ctx->lid_tab.p, host.data(), tab_bytes, cudaMemcpyHostToDevice, stream));
+    Launch L{stream, &ctx->launches};
+    gbase = 0;
+    for (int k = 0; k < n_nodes; ++k) {
+        NodeDesc nd{};
+        nd.mean = nodes[k].mean; nd.log_scale = nodes[k].log_scale; nd.quat = nodes[k].quat;
+        nd.opac = nodes[k].opacity_logit; nd.sh = nodes[k].sh; nd.n = nodes[k].n; nd.gbase = gbase;
+        nd.deg = nodes[k].sh_degree; nd.dtype = nodes[k].dtype;
+        launch_lidar_records(L, nd, ctx->opt.q_max, rec + 4 * rec_off[k], box + 2 * box_off[k], P[k]);
+        gbase += nodes[k].n;
+    }
+    ji = 0;
+    for (auto& lv : levels) {
+        const int64_t total = lv.first * (int64_t)lv.second.size();
+        launch_lidar_level(L, static_cast<char*>(ctx->lid_tab.p) + o_jobs + jb * ji, (int)lv.second.size(), lv.first,
+                           total);
+        ji += lv.second.size();
+    }
+    DGS_CUDA(ctx, cudaGetLastError());
+    DGS_CUDA(ctx, cudaStreamSynchronize(stream));   // the host table above must outlive its copy
+    ctx->lid_nodes.assign(nodes, nodes + n_nodes);
+    return DGS_OK;
+}
+
+int dgs_lidar_trace(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids, int32_t n_envs,
+                    int32_t max_nodes, const float* node_poses, const dgs_lidar* sensors, int32_t n_sensors,
+                    const float* dirs, int32_t n_dirs, float r_min, float r_max, float* out_d, float* out_a,
+                    void* stream_) {
+    if (!ctx) return DGS_ERR_INVALID_ARG;
+    begin_call(ctx);
+    int rc = check_nodes(ctx, nodes, n_nodes);
+    if (rc) return rc;
+    if ((int)ctx->lid_nodes.size() != n_nodes)
+        return fail(ctx, DGS_ERR_INVALID_ARG, "no LiDAR structures for these nodes (call dgs_lidar_build)");
+    for (int k = 0; k < n_nodes; ++k) {
+        const dgs_node &a = nodes[k], &b = ctx->lid_nodes[k];
+        if (a.n != b.n || a.mean != b.mean || a.log_scale != b.log_scale || a.quat != b.quat ||
+            a.opacity_logit != b.opacity_logit || a.dtype != b.dtype)
+            return fail(ctx, DGS_ERR_INVALID_ARG, "node " + std::to_string(k) + " differs from the one built (call dgs_lidar_build)");
+    }
+    if (n_envs < 1 || max_nodes < 1) return fail(ctx, DGS_ERR_INVALID_ARG, "n_envs and max_nodes must be >= 1");
+    if (!env_node_ids || !node_poses || !sensors || !dirs || !out_d || !out_a)
+        return fail(ctx, DGS_ERR_INVALID_ARG, "null pointer argument");
+    if (n_sensors < 0 || n_dirs < 1) return fail(ctx, DGS_ERR_INVALID_ARG, "n_sensors >= 0 and n_dirs >= 1 required");
+    if (!(r_min >= 0.f) || !(r_max > r_min) || !finite(r_max))
+        return fail(ctx, DGS_ERR_INVALID_ARG, "range window: need 0 <= r_min < r_max, finite");
+    const int E = n_envs, K = max_nodes;
+    std::vector<int> seen(n_nodes, -1);
+    for (int e = 0; e < E; ++e)
+        for (int j = 0; j < K; ++j) {
+            const int k = env_node_ids[(int64_t)e * K + j];
+            if (k < -1 || k >= n_nodes) return fail(ctx, DGS_ERR_INVALID_ARG, "env_node_ids out of range");
+            if (k >= 0) {
+                if (seen[k] == e) return fail(ctx, DGS_ERR_INVALID_ARG, "a node appears twice in one env");
+                seen[k] = e;
+            }
+        }
+    std::vector<LidarSensorDev> sd(n_sensors);
+    for (int s = 0; s < n_sensors; ++s) {
+        const dgs_lidar& L = sensors[s];
+        if (L.env < 0 || L.env >= E) return fail(ctx, DGS_ERR_INVALID_ARG, "sensor env out of range");
+        for (int a = 0; a < 12; ++a)
+            if (!finite(L.world_from_sensor[a])) return fail(ctx, DGS_ERR_INVALID_ARG, "sensor pose not finite");
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double d = 0;
+                for (int r = 0; r < 3; ++r) d += (double)L.world_from_sensor[r * 4 + a] * L.world_from_sensor[r * 4 + b];
+                if (std::fabs(d - (a == b ? 1.0 : 0.0)) > 1e-4)
+                    return fail(ctx, DGS_ERR_INVALID_ARG, "sensor rotation not orthonormal");
+            }
+        sd[s].env = L.env;
+        std::memcpy(sd[s].pose, L.world_from_sensor, sizeof(sd[s].pose));
+    }
+    if (n_sensors == 0) return DGS_OK;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    const size_t o_slot = align_up(sizeof(LidarSensorDev) * n_sensors, 256);
+    const size_t bytes = o_slot + sizeof(int32_t) * (size_t)E * K;
+    if ((rc = ensure(ctx, ctx->lid_meta, bytes))) return rc;
+    if ((rc = ensure(ctx, ctx->lid_slots, sizeof(LidarSlot) * (size_t)n_sensors * K))) return rc;
+    if ((rc = ensure(ctx, ctx->errword, 64))) return rc;
+    if ((rc = ensure_host(ctx, ctx->h_lid, ctx->h_lid_bytes, bytes))) return rc;
+    DGS_CUDA(ctx, cudaStreamSynchronize(stream));   // the previous call's upload from the staging
+    char* h = static_cast<char*>(ctx->h_lid);
+    std::memcpy(h, sd.data(), sizeof(LidarSensorDev) * n_sensors);
+    std::memcpy(h + o_slot, env_node_ids, sizeof(int32_t) * (size_t)E * K);
+    char* d = static_cast<char*>(ctx->lid_meta.p);
+    uint32_t* err = static_cast<uint32_t*>(ctx->errword.p);
+    DGS_CUDA(ctx, cudaMemsetAsync(err, 0, 64, stream));
+    DGS_CUDA(ctx, cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, stream));
+    Launch L{stream, &ctx->launches};
+    LidarSlot* slots = static_cast<LidarSlot*>(ctx->lid_slots.p);
+    launch_lidar_setup(L, reinterpret_cast<const LidarSensorDev*>(d), n_sensors,
+                       reinterpret_cast<const int32_t*>(d + o_slot), K, node_poses, slots, err);
+    LidarParams LP{r_min, r_max, ctx->opt.alpha_min, ctx->opt.alpha_max, ctx->opt.t_min, ctx->opt.q_max};
+    launch_lidar_trace(L, static_cast<const LidarTreeDev*>(ctx->lid_tab.p), slots, K, dirs, n_dirs,
+                       (int64_t)n_sensors * n_dirs, LP, out_d, out_a, err);
+    DGS_CUDA(ctx, cudaGetLastError());
+    uint32_t errw = 0;
+    DGS_CUDA(ctx, cudaMemcpyAsync(&errw, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+    DGS_CUDA(ctx, cudaStreamSynchronize(stream));
+    if (errw & kErrPose) return fail(ctx, DGS_ERR_INVALID_ARG, "a node pose is not finite or not rigid");
+    if (errw & kErrCapacity) return fail(ctx, DGS_ERR_CUDA, "internal: BVH traversal stack overflow");
     return DGS_OK;
 }
 

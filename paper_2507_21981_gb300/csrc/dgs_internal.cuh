@@ -340,6 +340,38 @@ struct AugSpan {
 void launch_augment(const Launch& L, const AugSpan* spans, int V, int64_t n_quads, const dgs_augment* aug,
                     const uint8_t* overlay, int ow, int oh, float* rgb);
 
+// LiDAR (csrc/lidar.cu).  Per node: records (4 float4 per Gaussian: mean + opacity, whitening
+// matrix) and an implicit BVH of 2P boxes (2 float4 each, heap numbering from 1).
+struct LidarTreeDev {
+    const float4* box;
+    const float4* rec;
+    int64_t n;
+    int64_t P;               // leaves (a power of two; leaf k covers Gaussians 8(k-P) .. +8)
+    uint32_t gbase;          // global id of the node's first Gaussian
+};
+struct LidarSensorDev {
+    int32_t env;
+    float pose[12];          // world_from_sensor
+};
+struct LidarSlot {           // per (sensor, slot): sensor in the node's frame
+    float R[9];              // node_from_sensor rotation
+    float o[3];              // sensor origin in the node frame
+    int32_t node;            // -1 = empty slot or invalid pose
+    int32_t pad;
+};
+struct LidarParams {
+    float r_min, r_max, alpha_min, alpha_max, t_min, q_max;
+};
+size_t lidar_tree_nodes(int64_t n);
+void launch_lidar_records(const Launch& L, const NodeDesc& nd, float q_max, float4* rec, float4* box, int64_t P);
+size_t lidar_level_job_bytes();
+void lidar_level_job(void* jobs, int i, float4* box, int64_t first);
+void launch_lidar_level(const Launch& L, const void* jobs, int n_jobs, int64_t h, int64_t total);
+void launch_lidar_setup(const Launch& L, const LidarSensorDev* sensors, int S, const int32_t* slot_node, int K,
+                        const float* node_poses, LidarSlot* out, uint32_t* err);
+void launch_lidar_trace(const Launch& L, const LidarTreeDev* trees, const LidarSlot* slots, int K, const float* dirs,
+                        int n_dirs, int64_t n_rays, const LidarParams& LP, float* out_d, float* out_a, uint32_t* err);
+
 void launch_composite_bwd(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
                           const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,
                           const float* out_rgb, const float* out_depth, const float* g_rgb, const float* g_depth,

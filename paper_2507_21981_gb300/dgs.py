@@ -66,10 +66,14 @@ class dgs_augment(C.Structure):
                 ("overlay_y", C.c_int32)]
 
 
+class dgs_lidar(C.Structure):
+    _fields_ = [("env", C.c_int32), ("world_from_sensor", C.c_float * 12)]
+
+
 EXPORTED = ("dgs_default_options", "dgs_context_create", "dgs_context_destroy", "dgs_last_error",
             "dgs_workspace_query", "dgs_render", "dgs_last_stats", "dgs_kernel_times", "dgs_last_launches",
             "dgs_render_noalloc", "dgs_render_backward", "dgs_autotune", "dgs_spatial_order",
-            "dgs_set_augment", "dgs_augment_rgb")
+            "dgs_set_augment", "dgs_augment_rgb", "dgs_lidar_build", "dgs_lidar_trace")
 
 _lib = None
 _lock = threading.Lock()
@@ -126,6 +130,11 @@ def load(path: str | None = None) -> C.CDLL:
         lib.dgs_set_augment.argtypes = [vp, vp, i32, vp, i32, i32, i32]
         lib.dgs_augment_rgb.restype = C.c_int
         lib.dgs_augment_rgb.argtypes = [vp, vp, vp, vp, i32, vp]
+        lib.dgs_lidar_build.restype = C.c_int
+        lib.dgs_lidar_build.argtypes = [vp, C.POINTER(dgs_node), i32, vp]
+        lib.dgs_lidar_trace.restype = C.c_int
+        lib.dgs_lidar_trace.argtypes = [vp, C.POINTER(dgs_node), i32, vp, i32, i32, vp, C.POINTER(dgs_lidar), i32, vp,
+                                        i32, C.c_float, C.c_float, vp, vp, vp]
         if path is None:
             _lib = lib
         return lib
@@ -258,3 +267,28 @@ def dgs_augment_rgb(ctx, rgb, view_size, view_pixel_offset, n_views, stream) -> 
     """Direct call of dgs_augment_rgb; view_size is a host int32 [n_views, 2] array of (width, height)."""
     vs = np.ascontiguousarray(view_size, np.int32)
     return load().dgs_augment_rgb(ctx, _ptr(rgb), vs.ctypes.data, _ptr(view_pixel_offset), int(n_views), stream)
+
+
+def dgs_lidar_build(ctx, nodes, n_nodes, stream) -> int:
+    """Direct call of dgs_lidar_build (nodes: ctypes array of dgs_node)."""
+    return load().dgs_lidar_build(ctx, nodes, int(n_nodes), stream)
+
+
+def dgs_lidar_trace(ctx, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, sensors, n_sensors, dirs,
+                    n_dirs, r_min, r_max, out_d, out_a, stream) -> int:
+    """Direct call of dgs_lidar_trace; `sensors` is a ctypes array of dgs_lidar, `dirs` a device
+    tensor [n_dirs, 3] (or address), outputs device tensors [n_sensors * n_dirs]."""
+    return load().dgs_lidar_trace(ctx, nodes, int(n_nodes), _ptr(env_node_ids), int(n_envs), int(max_nodes),
+                                  _ptr(node_poses), sensors, int(n_sensors), _ptr(dirs), int(n_dirs), float(r_min),
+                                  float(r_max), _ptr(out_d), _ptr(out_a), stream)
+
+
+def lidar_sensors(sensor_env, sensor_pose):
+    """ctypes array of dgs_lidar from env indices [S] and world_from_sensor poses [S,3,4]."""
+    env = np.asarray(sensor_env, np.int32).reshape(-1)
+    pose = np.asarray(sensor_pose, np.float32).reshape(len(env), 12)
+    arr = (dgs_lidar * max(len(env), 1))()
+    for i in range(len(env)):
+        arr[i].env = int(env[i])
+        arr[i].world_from_sensor[:] = [float(x) for x in pose[i]]
+    return arr

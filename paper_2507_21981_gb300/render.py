@@ -168,6 +168,31 @@ class Renderer:
             raise D.DgsError(rc, D.dgs_last_error(self.ctx))
         return rgb
 
+    def lidar_build(self, ds: DeviceScene, stream=None):
+        """Builds the LiDAR ray-tracing structures of the scene's nodes (dgs_lidar_build)."""
+        s = stream if stream is not None else torch.cuda.current_stream(ds.device)
+        rc = D.dgs_lidar_build(self.ctx, ds.nodes, ds.n_nodes, s.cuda_stream)
+        if rc != D.DGS_OK:
+            raise D.DgsError(rc, D.dgs_last_error(self.ctx))
+
+    def lidar_trace(self, ds: DeviceScene, sensor_env, sensor_pose, dirs, r_min: float = 0.05, r_max: float = 30.0,
+                    out=None, stream=None):
+        """Traces every (sensor, direction) ray (dgs_lidar_trace): sensor_env [S], sensor_pose
+        [S,3,4] world_from_sensor, dirs a CUDA tensor [J,3] of sensor-frame directions.  Returns
+        (D, A) CUDA tensors [S, J]: D = sum w t* (range = D / A), A = 1 - T."""
+        sensors = sensor_env if isinstance(sensor_env, C.Array) else D.lidar_sensors(sensor_env, sensor_pose)
+        S = len(sensors) if isinstance(sensor_env, C.Array) else len(np.asarray(sensor_env).reshape(-1))
+        J = int(dirs.shape[0])
+        if out is None:
+            out = (torch.empty((S, J), dtype=torch.float32, device=ds.device),
+                   torch.empty((S, J), dtype=torch.float32, device=ds.device))
+        s = stream if stream is not None else torch.cuda.current_stream(ds.device)
+        rc = D.dgs_lidar_trace(self.ctx, ds.nodes, ds.n_nodes, ds.env_node_ids, ds.n_envs, ds.max_nodes,
+                               ds.node_poses, sensors, S, dirs, J, r_min, r_max, out[0], out[1], s.cuda_stream)
+        if rc != D.DGS_OK:
+            raise D.DgsError(rc, D.dgs_last_error(self.ctx))
+        return out
+
     def _outputs(self, ds: DeviceScene, with_alpha: bool):
         def fresh():
             return (torch.empty((ds.n_pixels, 3), dtype=torch.float32, device=ds.device),

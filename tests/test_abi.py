@@ -59,6 +59,7 @@ def test_struct_sizes_match_header(lib):
     assert C.sizeof(D.dgs_stats) == 80
     assert C.sizeof(D.dgs_tune_result) == 8 + 3 * 4 * D.DGS_TUNE_MAX
     assert C.sizeof(D.dgs_augment) == 32
+    assert C.sizeof(D.dgs_lidar) == 52
 
 
 def test_augment_record_layout_matches_the_numpy_generator():
@@ -235,5 +236,24 @@ def test_set_augment_validates_on_host(lib):
         assert setp(None) == D.DGS_OK
         assert lib.dgs_augment_rgb(ctx, FAKE_DEV, sizes.ctypes.data, None, 2, None) == D.DGS_ERR_INVALID_ARG
         assert "no randomisation" in D.dgs_last_error(ctx)
+    finally:
+        lib.dgs_context_destroy(ctx)
+
+
+def test_lidar_validates_on_host(lib):
+    ctx = _ctx(lib)
+    try:
+        nodes, ids, _, _ = _args()
+        sens = D.lidar_sensors([0], np.eye(3, 4)[None])
+
+        def trace(nodes=nodes, n=1, sensors=sens, ns=1, dirs=FAKE_DEV, nd=4, r0=0.05, r1=30.0, env=1):
+            return lib.dgs_lidar_trace(ctx, nodes, n, ids.ctypes.data, env, 1, FAKE_DEV, sensors, ns, dirs, nd, r0, r1,
+                                       FAKE_DEV, FAKE_DEV, None)
+        assert trace() == D.DGS_ERR_INVALID_ARG                        # nothing built yet
+        assert "dgs_lidar_build" in D.dgs_last_error(ctx)
+        assert lib.dgs_lidar_build(ctx, nodes, 0, None) == D.DGS_ERR_INVALID_ARG
+        bad = (D.dgs_node * 1)()
+        bad[0].n, bad[0].sh_degree, bad[0].dtype = 5, 0, 0            # null attribute pointers
+        assert lib.dgs_lidar_build(ctx, bad, 1, None) == D.DGS_ERR_INVALID_ARG
     finally:
         lib.dgs_context_destroy(ctx)
