@@ -1487,7 +1487,8 @@ int dgs_lidar_trace(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const 
                        reinterpret_cast<const int32_t*>(d + o_slot), K, node_poses, slots, err);
     LidarParams LP{r_min, r_max, ctx->opt.alpha_min, ctx->opt.alpha_max, ctx->opt.t_min, ctx->opt.q_max};
     launch_lidar_trace(L, static_cast<const LidarTreeDev*>(ctx->lid_tab.p), slots, K, dirs, n_dirs,
-                       (int64_t)n_sensors * n_dirs, LP, out_d, out_a, err);
+                       (int64_t)n_sensors * n_dirs, LP, out_d, out_a, err,
+                       reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->errword.p) + 8));
     DGS_CUDA(ctx, cudaGetLastError());
     uint32_t errw = 0;
     DGS_CUDA(ctx, cudaMemcpyAsync(&errw, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));

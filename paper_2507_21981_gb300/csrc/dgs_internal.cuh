@@ -370,7 +370,8 @@ void launch_lidar_level(const Launch& L, const void* jobs, int n_jobs, int64_t h
 void launch_lidar_setup(const Launch& L, const LidarSensorDev* sensors, int S, const int32_t* slot_node, int K,
                         const float* node_poses, LidarSlot* out, uint32_t* err);
 void launch_lidar_trace(const Launch& L, const LidarTreeDev* trees, const LidarSlot* slots, int K, const float* dirs,
-                        int n_dirs, int64_t n_rays, const LidarParams& LP, float* out_d, float* out_a, uint32_t* err);
+                        int n_dirs, int64_t n_rays, const LidarParams& LP, float* out_d, float* out_a, uint32_t* err,
+                        unsigned long long* next_ray);
 
 void launch_composite_bwd(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
                           const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,

@@ -15,11 +15,14 @@
 // tree's quality follows the storage order: Z-ordered nodes (dgs_spatial_order) give compact
 // leaves.  Trees are never refitted per env: rays are moved into each node's frame instead.
 //
-// Tracing: one thread per ray.  A round collects, over every node of the ray's env, the K
-// nearest hits whose (t*, id) key follows the last key composited, in a sorted register buffer;
-// the traversal is front to back and skips boxes outside [t_last, t of the K-th hit].  The
-// round's hits are composited; the next round resumes after the last of them, until the
-// transmittance drops below t_min or fewer than K hits were left.
+// Tracing: one thread per ray, one warp per packet of 32 rays.  A round collects, over every
+// node of the ray's env, the K nearest hits whose (t*, id) key follows the last key
+// composited, in a sorted register buffer; the packet's traversal is front to back and skips
+// boxes outside every lane's [t_last, t of its K-th hit].  The round's hits are composited;
+// the next round resumes after the last of them, until the transmittance drops below t_min or
+// fewer than K hits were left.
+#include <algorithm>
+
 #include "dgs_internal.cuh"
 
 namespace dgs {
@@ -61,7 +64,10 @@ __global__ void k_lidar_records(NodeDesc nd, float sq, float4* __restrict__ rec,
         rec[4 * i + 0] = make_float4(mx, my, mz, op);
         rec[4 * i + 1] = make_float4(M[0][0], M[0][1], M[0][2], M[1][0]);
         rec[4 * i + 2] = make_float4(M[1][1], M[1][2], M[2][0], M[2][1]);
-        rec[4 * i + 3] = make_float4(M[2][2], 0.f, 0.f, 0.f);
+        // squared radius of the sphere holding the q_max ellipsoid: a ray farther from the mean
+        // than that cannot hit (cheap test before the exact one)
+        const float smax = fmaxf(fmaxf(s[0], s[1]), s[2]);
+        rec[4 * i + 3] = make_float4(M[2][2], sq * sq * smax * smax * 1.002f, 0.f, 0.f);
         const float m[3] = {mx, my, mz};
         for (int a = 0; a < 3; ++a) {
             // half extent of the ellipsoid q <= q_max along axis a, widened slightly so that
@@ -171,120 +177,183 @@ struct Kbuf {
     float alpha[kKbuf];
 };
 
+// Warp = a packet of up to 32 rays (consecutive ray numbers: make them neighbours in the beam
+// pattern).  The packet walks each tree together on a warp-uniform stack: a box is descended
+// if it holds the interval of any lane's ray, the children in the order of the first such
+// lane's entry distances; records and boxes are read once per warp.  Each lane keeps its own
+// hit buffer, interval and compositing state, and rounds repeat while any lane is unfinished.
+// Lanes whose sensor differs in a slot's node take the tree in turns.  Warps are persistent:
+// each takes the next 32 rays from a counter until none are left, so that packets of very
+// different cost (rays grazing a surface, many rounds) do not leave SMs idle at the end.
 __global__ void __launch_bounds__(kTraceThreads) k_lidar_trace(const LidarTreeDev* __restrict__ trees,
                                                                const LidarSlot* __restrict__ slots, int K,
                                                                const float* __restrict__ dirs, int n_dirs,
                                                                int64_t n_rays, LidarParams LP,
                                                                float* __restrict__ out_d, float* __restrict__ out_a,
-                                                               uint32_t* __restrict__ err) {
-    const int64_t ray = (int64_t)blockIdx.x * kTraceThreads + threadIdx.x;
-    if (ray >= n_rays) return;
-    const int s = (int)(ray / n_dirs), j = (int)(ray - (int64_t)s * n_dirs);
-    float ds[3] = {dirs[3 * j], dirs[3 * j + 1], dirs[3 * j + 2]};
-    {
-        const float r = rsqrtf(ds[0] * ds[0] + ds[1] * ds[1] + ds[2] * ds[2]);
-        ds[0] *= r; ds[1] *= r; ds[2] *= r;
-    }
-    const LidarSlot* sl = slots + (int64_t)s * K;
-    float T = 1.f, D = 0.f;
-    uint64_t last = 0;                                 // keys <= last are composited
-    bool first = true, done = false;
-    int stack[kStack];
-    while (!done) {
-        Kbuf kb;
-#pragma unroll
-        for (int i = 0; i < kKbuf; ++i) { kb.key[i] = ~0ull; kb.alpha[i] = 0.f; }
-        int cnt = 0;
-        const float t_lo = first ? LP.r_min : __uint_as_float((uint32_t)(last >> 32));
-        float t_hi = LP.r_max;
-        for (int slot = 0; slot < K; ++slot) {
-            const LidarSlot& S = sl[slot];
-            if (S.node < 0) continue;
-            const LidarTreeDev tr = trees[S.node];
-            if (tr.n == 0) continue;
-            float o[3] = {S.o[0], S.o[1], S.o[2]}, d[3], id[3];
-            for (int a = 0; a < 3; ++a) {
-                d[a] = S.R[3 * a] * ds[0] + S.R[3 * a + 1] * ds[1] + S.R[3 * a + 2] * ds[2];
-                id[a] = 1.f / d[a];
-            }
-            int sp = 0;
-            if (slab(tr.box[2], tr.box[3], o, id, t_lo, t_hi)) stack[sp++] = 1;
-            while (sp > 0) {
-                const int64_t k = stack[--sp];
-                if (k >= tr.P) {
-                    const int64_t g0 = (k - tr.P) * kLeaf;
-                    const int64_t g1 = min(g0 + kLeaf, tr.n);
-                    for (int64_t g = g0; g < g1; ++g) {
-                        const float4 r0 = __ldg(tr.rec + 4 * g), r1 = __ldg(tr.rec + 4 * g + 1),
-                                     r2 = __ldg(tr.rec + 4 * g + 2), r3 = __ldg(tr.rec + 4 * g + 3);
-                        const float v0 = o[0] - r0.x, v1 = o[1] - r0.y, v2 = o[2] - r0.z;
-                        const float op0 = fmaf(r1.x, v0, fmaf(r1.y, v1, r1.z * v2));
-                        const float op1 = fmaf(r1.w, v0, fmaf(r2.x, v1, r2.y * v2));
-                        const float op2 = fmaf(r2.z, v0, fmaf(r2.w, v1, r3.x * v2));
-                        const float dp0 = fmaf(r1.x, d[0], fmaf(r1.y, d[1], r1.z * d[2]));
-                        const float dp1 = fmaf(r1.w, d[0], fmaf(r2.x, d[1], r2.y * d[2]));
-                        const float dp2 = fmaf(r2.z, d[0], fmaf(r2.w, d[1], r3.x * d[2]));
-                        const float dd = fmaf(dp0, dp0, fmaf(dp1, dp1, dp2 * dp2));
-                        const float od = fmaf(op0, dp0, fmaf(op1, dp1, op2 * dp2));
-                        const float c0 = fmaf(op1, dp2, -op2 * dp1), c1 = fmaf(op2, dp0, -op0 * dp2),
-                                    c2 = fmaf(op0, dp1, -op1 * dp0);
-                        const float idd = 1.f / dd;
-                        const float t = -od * idd;
-                        const float q = fmaf(c0, c0, fmaf(c1, c1, c2 * c2)) * idd;
-                        if (!(q <= LP.q_max) || !(t >= LP.r_min) || !(t <= LP.r_max)) continue;
-                        const uint64_t key = ((uint64_t)__float_as_uint(t) << 32) | (uint32_t)(tr.gbase + g);
-                        if ((!first && key <= last) || key >= kb.key[kKbuf - 1]) continue;
-                        const float alpha = fminf(LP.alpha_max, r0.w * fast_exp2(kHalfLog2e * q));
-                        if (alpha < LP.alpha_min) continue;
-                        uint64_t ck = key;
-                        float ca = alpha;
-#pragma unroll
-                        for (int i = 0; i < kKbuf; ++i) {
-                            if (ck < kb.key[i]) {
-                                const uint64_t tk = kb.key[i]; kb.key[i] = ck; ck = tk;
-                                const float ta = kb.alpha[i]; kb.alpha[i] = ca; ca = ta;
-                            }
+                                                               uint32_t* __restrict__ err,
+                                                               unsigned long long* __restrict__ next_ray) {
+    __shared__ int s_stack[kTraceThreads / 32][kStack];
+    const int lane = threadIdx.x & 31;
+    int* stk = s_stack[threadIdx.x >> 5];
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(next_ray, 32ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= (unsigned long long)n_rays) break;
+        const int64_t ray = (int64_t)base + lane;
+        const bool valid = ray < n_rays;
+        int s = 0, j = 0;
+        float ds[3] = {1.f, 0.f, 0.f};
+        if (valid) {
+            s = (int)(ray / n_dirs);
+            j = (int)(ray - (int64_t)s * n_dirs);
+            ds[0] = dirs[3 * j]; ds[1] = dirs[3 * j + 1]; ds[2] = dirs[3 * j + 2];
+            const float r = rsqrtf(ds[0] * ds[0] + ds[1] * ds[1] + ds[2] * ds[2]);
+            ds[0] *= r; ds[1] *= r; ds[2] *= r;
+        }
+        const LidarSlot* sl = slots + (int64_t)s * K;
+        float T = 1.f, D = 0.f;
+        uint64_t last = 0;                                 // keys <= last are composited
+        bool first = true, done = !valid;
+        while (__any_sync(0xffffffffu, !done)) {
+            Kbuf kb;
+    #pragma unroll
+            for (int i = 0; i < kKbuf; ++i) { kb.key[i] = ~0ull; kb.alpha[i] = 0.f; }
+            int cnt = 0;
+            const float t_lo = first ? LP.r_min : __uint_as_float((uint32_t)(last >> 32));
+            float t_hi = LP.r_max;
+            for (int slot = 0; slot < K; ++slot) {
+                int my_node = -1;
+                float o[3] = {0.f, 0.f, 0.f}, d[3] = {1.f, 1.f, 1.f}, id[3] = {1.f, 1.f, 1.f};
+                if (!done) {
+                    const LidarSlot& S = sl[slot];
+                    my_node = S.node;
+                    if (my_node >= 0 && trees[my_node].n == 0) my_node = -1;
+                    if (my_node >= 0) {
+                        for (int a = 0; a < 3; ++a) {
+                            o[a] = S.o[a];
+                            d[a] = S.R[3 * a] * ds[0] + S.R[3 * a + 1] * ds[1] + S.R[3 * a + 2] * ds[2];
+                            id[a] = 1.f / d[a];
                         }
-                        if (cnt < kKbuf) ++cnt;
-                        if (cnt == kKbuf) t_hi = __uint_as_float((uint32_t)(kb.key[kKbuf - 1] >> 32));
-                    }
-                } else {
-                    const int64_t c = 2 * k;
-                    const float4 l0 = tr.box[2 * c], h0 = tr.box[2 * c + 1], l1 = tr.box[2 * c + 2],
-                                 h1 = tr.box[2 * c + 3];
-                    const bool in0 = slab(l0, h0, o, id, t_lo, t_hi), in1 = slab(l1, h1, o, id, t_lo, t_hi);
-                    if (in0 && in1) {
-                        const bool near0 = slab_enter(l0, h0, o, id) <= slab_enter(l1, h1, o, id);
-                        if (sp + 2 > kStack) { atomicOr(err, kErrCapacity); sp = 0; break; }
-                        stack[sp++] = (int)(near0 ? c + 1 : c);   // far child below, near on top
-                        stack[sp++] = (int)(near0 ? c : c + 1);
-                    } else if (in0 || in1) {
-                        if (sp + 1 > kStack) { atomicOr(err, kErrCapacity); sp = 0; break; }
-                        stack[sp++] = (int)(in0 ? c : c + 1);
                     }
                 }
-            }
-        }
-        // composite this round's hits in order
-#pragma unroll
-        for (int i = 0; i < kKbuf; ++i) {
-            if (i < cnt && !done) {
-                const float a = kb.alpha[i];
-                const float Tn = fmaf(-a, T, T);
-                if (Tn < LP.t_min) {
-                    done = true;
-                } else {
-                    D = fmaf(a * T, __uint_as_float((uint32_t)(kb.key[i] >> 32)), D);
-                    T = Tn;
+                unsigned pending = __ballot_sync(0xffffffffu, my_node >= 0);
+                while (pending) {
+                    const int node = __shfl_sync(0xffffffffu, my_node, __ffs(pending) - 1);
+                    const unsigned mine_mask = __ballot_sync(0xffffffffu, my_node == node) & pending;
+                    pending &= ~mine_mask;
+                    const bool mine = (mine_mask >> lane) & 1u;
+                    const LidarTreeDev tr = trees[node];
+                    int sp = 0;
+                    if (__any_sync(0xffffffffu, mine && slab(tr.box[2], tr.box[3], o, id, t_lo, t_hi))) {
+                        if (lane == 0) stk[0] = 1;
+                        sp = 1;
+                    }
+                    __syncwarp();
+                    while (sp > 0) {
+                        const int64_t k = stk[--sp];
+                        __syncwarp();                        // every lane has read before lane 0 writes
+                        if (k >= tr.P) {
+                            const int64_t g0 = (k - tr.P) * kLeaf;
+                            const int64_t g1 = min(g0 + kLeaf, tr.n);
+                            for (int64_t g = g0; g < g1; ++g) {
+                                const float4 r0 = __ldg(tr.rec + 4 * g), r1 = __ldg(tr.rec + 4 * g + 1),
+                                             r2 = __ldg(tr.rec + 4 * g + 2), r3 = __ldg(tr.rec + 4 * g + 3);
+                                if (!mine) continue;
+                                const float v0 = o[0] - r0.x, v1 = o[1] - r0.y, v2 = o[2] - r0.z;
+                                {
+                                    const float x0 = fmaf(v1, d[2], -v2 * d[1]), x1 = fmaf(v2, d[0], -v0 * d[2]),
+                                                x2 = fmaf(v0, d[1], -v1 * d[0]);
+                                    if (fmaf(x0, x0, fmaf(x1, x1, x2 * x2)) > r3.y) continue;   // |d| = 1 up to rounding
+                                }
+                                const float op0 = fmaf(r1.x, v0, fmaf(r1.y, v1, r1.z * v2));
+                                const float op1 = fmaf(r1.w, v0, fmaf(r2.x, v1, r2.y * v2));
+                                const float op2 = fmaf(r2.z, v0, fmaf(r2.w, v1, r3.x * v2));
+                                const float dp0 = fmaf(r1.x, d[0], fmaf(r1.y, d[1], r1.z * d[2]));
+                                const float dp1 = fmaf(r1.w, d[0], fmaf(r2.x, d[1], r2.y * d[2]));
+                                const float dp2 = fmaf(r2.z, d[0], fmaf(r2.w, d[1], r3.x * d[2]));
+                                const float dd = fmaf(dp0, dp0, fmaf(dp1, dp1, dp2 * dp2));
+                                const float od = fmaf(op0, dp0, fmaf(op1, dp1, op2 * dp2));
+                                const float c0 = fmaf(op1, dp2, -op2 * dp1), c1 = fmaf(op2, dp0, -op0 * dp2),
+                                            c2 = fmaf(op0, dp1, -op1 * dp0);
+                                const float idd = 1.f / dd;
+                                const float t = -od * idd;
+                                const float q = fmaf(c0, c0, fmaf(c1, c1, c2 * c2)) * idd;
+                                if (!(q <= LP.q_max) || !(t >= LP.r_min) || !(t <= LP.r_max)) continue;
+                                const uint64_t key = ((uint64_t)__float_as_uint(t) << 32) | (uint32_t)(tr.gbase + g);
+                                if ((!first && key <= last) || key >= kb.key[kKbuf - 1]) continue;
+                                const float alpha = fminf(LP.alpha_max, r0.w * fast_exp2(kHalfLog2e * q));
+                                if (alpha < LP.alpha_min) continue;
+                                uint64_t ck = key;
+                                float ca = alpha;
+    #pragma unroll
+                                for (int i = 0; i < kKbuf; ++i) {
+                                    if (ck < kb.key[i]) {
+                                        const uint64_t tk = kb.key[i]; kb.key[i] = ck; ck = tk;
+                                        const float ta = kb.alpha[i]; kb.alpha[i] = ca; ca = ta;
+                                    }
+                                }
+                                if (cnt < kKbuf) ++cnt;
+                                if (cnt == kKbuf) t_hi = __uint_as_float((uint32_t)(kb.key[kKbuf - 1] >> 32));
+                            }
+                        } else {
+                            const int64_t c = 2 * k;
+                            const float4 l0 = __ldg(tr.box + 2 * c), h0 = __ldg(tr.box + 2 * c + 1),
+                                         l1 = __ldg(tr.box + 2 * c + 2), h1 = __ldg(tr.box + 2 * c + 3);
+                            const bool in0 = mine && slab(l0, h0, o, id, t_lo, t_hi);
+                            const bool in1 = mine && slab(l1, h1, o, id, t_lo, t_hi);
+                            const unsigned b0 = __ballot_sync(0xffffffffu, in0), b1 = __ballot_sync(0xffffffffu, in1);
+                            if (b0 && b1) {
+                                const bool near0 = slab_enter(l0, h0, o, id) <= slab_enter(l1, h1, o, id);
+                                const bool n0 = __shfl_sync(0xffffffffu, near0, __ffs(b0 | b1) - 1);
+                                if (sp + 2 > kStack) {
+                                    if (lane == 0) atomicOr(err, kErrCapacity);
+                                    break;
+                                }
+                                if (lane == 0) {
+                                    stk[sp] = (int)(n0 ? c + 1 : c);     // far child below, near on top
+                                    stk[sp + 1] = (int)(n0 ? c : c + 1);
+                                }
+                                sp += 2;
+                            } else if (b0 || b1) {
+                                if (sp + 1 > kStack) {
+                                    if (lane == 0) atomicOr(err, kErrCapacity);
+                                    break;
+                                }
+                                if (lane == 0) stk[sp] = (int)(b0 ? c : c + 1);
+                                sp += 1;
+                            }
+                            __syncwarp();
+                        }
+                    }
+                    __syncwarp();
                 }
             }
+            if (!done) {
+                // composite this round's hits in order
+    #pragma unroll
+                for (int i = 0; i < kKbuf; ++i) {
+                    if (i < cnt && !done) {
+                        const float a = kb.alpha[i];
+                        const float Tn = fmaf(-a, T, T);
+                        if (Tn < LP.t_min) {
+                            done = true;
+                        } else {
+                            D = fmaf(a * T, __uint_as_float((uint32_t)(kb.key[i] >> 32)), D);
+                            T = Tn;
+                        }
+                    }
+                }
+                if (cnt < kKbuf) done = true;
+                last = kb.key[kKbuf - 1];
+                first = false;
+            }
         }
-        if (cnt < kKbuf) done = true;
-        last = kb.key[kKbuf - 1];
-        first = false;
+        if (valid) {
+            out_d[ray] = D;
+            out_a[ray] = 1.f - T;
+        }
     }
-    out_d[ray] = D;
-    out_a[ray] = 1.f - T;
 }
 
 }  // namespace
@@ -332,10 +401,21 @@ void launch_lidar_setup(const Launch& L, const LidarSensorDev* sensors, int S, c
 }
 
 void launch_lidar_trace(const Launch& L, const LidarTreeDev* trees, const LidarSlot* slots, int K, const float* dirs,
-                        int n_dirs, int64_t n_rays, const LidarParams& LP, float* out_d, float* out_a, uint32_t* err) {
+                        int n_dirs, int64_t n_rays, const LidarParams& LP, float* out_d, float* out_a, uint32_t* err,
+                        unsigned long long* next_ray) {
     if (n_rays <= 0) return;
-    k_lidar_trace<<<(unsigned)((n_rays + kTraceThreads - 1) / kTraceThreads), kTraceThreads, 0, L.stream>>>(
-        trees, slots, K, dirs, n_dirs, n_rays, LP, out_d, out_a, err);
+    static int resident = 0, sms = 0;           // blocks per SM at this kernel's resources
+    if (!resident) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_lidar_trace, kTraceThreads, 0);
+        resident = std::max(resident, 1);
+    }
+    const int64_t need = (n_rays + kTraceThreads - 1) / kTraceThreads;
+    const unsigned blocks = (unsigned)std::min<int64_t>(need, (int64_t)resident * sms);
+    k_lidar_trace<<<blocks, kTraceThreads, 0, L.stream>>>(trees, slots, K, dirs, n_dirs, n_rays, LP, out_d, out_a, err,
+                                                          next_ray);
     ++*L.launches;
 }
 

@@ -531,16 +531,24 @@ def augment_params(seed: int, n_views: int, n_frames: int, overlay_w: int, overl
 
 # ------------------------------------------------------------------------------------- LiDAR
 def lidar_pattern(channels: int = 32, azimuths: int = 1024, el_min_deg: float = -30.67,
-                  el_max_deg: float = 10.67, az0_deg: float = 0.0, az_span_deg: float = 360.0) -> np.ndarray:
+                  el_max_deg: float = 10.67, az0_deg: float = 0.0, az_span_deg: float = 360.0,
+                  tile=(4, 8)) -> np.ndarray:
     """Beam directions of a spinning multi-channel LiDAR in its own frame (x forward, y left,
     z up): `channels` elevations spaced evenly over [el_min, el_max] (the defaults are those
     of a 32-beam automotive unit) times `azimuths` evenly spaced azimuths; float32 [channels *
-    azimuths, 3] unit vectors, channel-major."""
+    azimuths, 3] unit vectors.  Order: tiles of tile[0] channels x tile[1] azimuths (each tile
+    channel-major, tiles channel-block-major), so that every 32 consecutive beams are
+    neighbours; tile=None gives plain channel-major order."""
     el = np.deg2rad(np.linspace(el_min_deg, el_max_deg, channels))
     az = np.deg2rad(az0_deg + az_span_deg * np.arange(azimuths) / azimuths)
     ce, se = np.cos(el)[:, None], np.sin(el)[:, None]
     d = np.stack([ce * np.cos(az)[None, :], ce * np.sin(az)[None, :], np.broadcast_to(se, (channels, azimuths))],
                  axis=-1)
+    if tile is not None:
+        c, a = np.meshgrid(np.arange(channels), np.arange(azimuths), indexing="ij")
+        tc, ta = tile
+        order = np.lexsort(((a % ta).ravel(), (c % tc).ravel(), (a // ta).ravel(), (c // tc).ravel()))
+        return np.ascontiguousarray(d.reshape(-1, 3)[order].astype(np.float32))
     return np.ascontiguousarray(d.reshape(-1, 3).astype(np.float32))
 
 
