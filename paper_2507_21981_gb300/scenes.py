@@ -569,3 +569,53 @@ def lidar_sensors(seed: int, n_envs: int, radius=(1.0, 2.0), height=(0.8, 1.6), 
         R = _rot_axis([ax[0], ax[1], 0.0], np.deg2rad(rng.normal(0.0, tilt_deg))) @ _rot_axis([0, 0, 1], yaw)
         poses[e] = np.concatenate([_orthonormalise(R), p[:, None]], axis=1)
     return np.arange(n_envs, dtype=np.int32), poses.astype(np.float32)
+
+
+# ------------------------------------------------------------------------------------ meshes
+def mesh_icosphere(subdiv: int = 3, radius: float = 0.05):
+    """A closed triangle mesh of a sphere (icosahedron subdivided `subdiv` times, vertices pushed
+    to the sphere), outward winding: (vertices float32 [V,3], faces int32 [F,3]), F = 20 * 4^subdiv."""
+    t = (1.0 + 5 ** 0.5) / 2.0
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+         (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2), (10, 7, 6),
+         (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10),
+         (8, 6, 7), (9, 8, 1)]
+    verts = [np.array(p, np.float64) / np.linalg.norm(p) for p in v]
+    faces = list(f)
+    for _ in range(subdiv):
+        cache = {}
+
+        def mid(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in cache:
+                m = verts[a] + verts[b]
+                verts.append(m / np.linalg.norm(m))
+                cache[key] = len(verts) - 1
+            return cache[key]
+        nf = []
+        for a, b, c in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    return (np.asarray(verts) * radius).astype(np.float32), np.asarray(faces, np.int32)
+
+
+def mesh_heightfield(seed: int, nx: int, ny: int, size: float = 1.0, amp: float = 0.05):
+    """A noisy terrain-like sheet: an nx x ny vertex grid over [0, size]^2 with heights from a few
+    random plane waves, two triangles per cell (upward normals), and per-vertex colours from
+    another smooth field: (vertices float32 [V,3], faces int32 [F,3], colours float32 [V,3]),
+    F = 2 (nx - 1)(ny - 1)."""
+    rng = _rng(seed, 104)
+    xs, ys = np.meshgrid(np.linspace(0, size, nx), np.linspace(0, size, ny), indexing="xy")
+    k = rng.uniform(-12, 12, (5, 2)) / size
+    ph = rng.uniform(0, 2 * np.pi, 5)
+    z = amp * sum(np.sin(k[i, 0] * xs + k[i, 1] * ys + ph[i]) for i in range(5)) / 5.0
+    z += rng.normal(0.0, amp * 0.05, z.shape)
+    verts = np.stack([xs, ys, z], axis=-1).reshape(-1, 3)
+    idx = np.arange(nx * ny).reshape(ny, nx)
+    a, b, c, d = idx[:-1, :-1].ravel(), idx[:-1, 1:].ravel(), idx[1:, :-1].ravel(), idx[1:, 1:].ravel()
+    faces = np.concatenate([np.stack([a, b, d], 1), np.stack([a, d, c], 1)], axis=0)
+    col = 0.5 + 0.4 * np.stack([np.sin(3 * xs + ph[0]), np.sin(4 * ys + ph[1]), np.cos(2 * (xs + ys) + ph[2])],
+                               axis=-1).reshape(-1, 3)
+    return verts.astype(np.float32), faces.astype(np.int32), col.astype(np.float32)
