@@ -282,6 +282,100 @@ def augment_leg(dev, ds, tile, out, warmup, steps, ms_plain_render):
             "steps": steps}
 
 
+def lidar_leg(dev, ds, warmup, steps):
+    """LiDAR by Gaussian ray tracing on the benchmark scene: one 32-beam spinning sensor per env
+    (32 x 1024 rays over 360 degrees, -30.7 to +10.7 degrees elevation, 0.05-30 m), mounted near
+    the workspace; one dgs_lidar_trace call traces all 64 sensors (2.1M rays)."""
+    import numpy as np
+    import torch
+    from paper_2507_21981_gb300 import scenes
+    from paper_2507_21981_gb300.render import Renderer
+    se, sp = scenes.lidar_sensors(1, ds.n_envs)
+    dirs_h = scenes.lidar_pattern(32, 1024)
+    dirs = torch.as_tensor(dirs_h).to(dev)
+    r = Renderer()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    r.lidar_build(ds)
+    build_ms = (time.perf_counter() - t0) * 1e3
+    out = (torch.empty((len(se), len(dirs_h)), device=dev), torch.empty((len(se), len(dirs_h)), device=dev))
+    for _ in range(warmup):
+        r.lidar_trace(ds, se, sp, dirs, out=out)
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(steps):
+        r.lidar_trace(ds, se, sp, dirs, out=out)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / steps
+    a = out[1]
+    rays = len(se) * len(dirs_h)
+    res = {"workload": f"{len(se)} sensors x 32 x 1024 rays (one per env), benchmark scene (1.08M Gaussians per env)",
+           "rays_per_step": rays, "ms_per_step": ms, "mrays_s": rays / ms / 1e3,
+           "sensor_frames_s": len(se) * 1e3 / ms, "build_ms": build_ms,
+           "returns_frac": float((a > 0.5).float().mean()), "steps": steps}
+    r.close()
+    # the oracle on a sample of one sensor's rays (host cores)
+    import oracle
+    from oracle import lidar as OL
+    js = np.random.default_rng(0).choice(len(dirs_h), 256, replace=False)
+    pk = oracle.oracle._Packed(ds.scene)
+    t0 = time.perf_counter()
+    OL.trace(ds.scene, se[:1], sp[:1], dirs_h[js], packed=pk)
+    dt = time.perf_counter() - t0
+    res["oracle_mrays_s"] = 256 / dt / 1e6
+    res["oracle_sample"] = f"256 rays of one sensor, brute force over 1.08M Gaussians, FP64, {os.cpu_count()} cores"
+    return res
+
+
+def mesh_leg(dev, warmup, steps):
+    """Mesh -> Gaussian transfer of a 1M-facet coloured heightfield into SH-degree-3 node
+    arrays.  HBM-bound: algorithmic bytes = 12 B of indices per facet, every vertex position
+    and colour read once (24 B per vertex), 236 B written per facet."""
+    import numpy as np
+    import torch
+    from paper_2507_21981_gb300 import dgs as D
+    from paper_2507_21981_gb300 import scenes
+    from paper_2507_21981_gb300.render import Renderer
+    v, f, col = scenes.mesh_heightfield(5, 708, 708, size=4.0, amp=0.2)
+    dv, df, dc = (torch.as_tensor(a).to(dev) for a in (v, f, col))
+    F = len(f)
+    out = [torch.empty((F, 3), device=dev), torch.empty((F, 3), device=dev), torch.empty((F, 4), device=dev),
+           torch.empty((F,), device=dev), torch.empty((F, 16, 3), device=dev)]
+    r = Renderer()
+    stream = torch.cuda.current_stream(dev)
+
+    def call():
+        rc = D.dgs_mesh_to_gaussians(r.ctx, dv, len(v), df, F, dc, 0.01, 2.0, 3, *out, stream.cuda_stream)
+        assert rc == D.DGS_OK
+    for _ in range(warmup):
+        call()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(steps):
+        call()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / steps
+    r.close()
+    byt = F * (12 + 236) + len(v) * 24
+    peaks, kind = _peaks()
+    # the oracle on a sample of the facets (numpy FP64)
+    import oracle
+    idx = np.arange(20_000)
+    t0 = time.perf_counter()
+    oracle.mesh.mesh_to_gaussians(v, f[idx], vertex_colors=col, sh_degree=3)
+    t_or = time.perf_counter() - t0
+    return {"workload": "1M-facet coloured heightfield (708 x 708 vertices) -> SH3 Gaussian node", "facets": F,
+            "ms_per_call": ms, "mfacets_s": F / ms / 1e3, "bytes": byt, "gb_s": byt / ms / 1e6,
+            "frac_of_hbm": byt / ms / 1e6 / peaks["hbm_gbs"], "peak_source": f"{kind} MEASURED_PEAKS.json hbm_gbs",
+            "note": "each call synchronises its stream (host round trip included)",
+            "oracle_mfacets_s": 20_000 / t_or / 1e6, "oracle_sample": "20k facets, numpy FP64, 1 thread", "steps": steps}
+
+
 def cpu_baseline(views=1, seed=1):
     """Times the FP64 oracle on `views` sampled views of the workload (host cores)."""
     import oracle
@@ -486,6 +580,8 @@ def main():
         extra["ragged"] = ragged_graph(dev, args.warmup, max(3, args.steps // 4))
         extra["precision_scale"] = precision_scale(dev, args.warmup, max(3, args.steps // 4))
         extra["augment"] = augment_leg(dev, ds, tile, out, args.warmup, max(3, args.steps // 4), ms)
+        extra["lidar"] = lidar_leg(dev, ds, args.warmup, max(3, args.steps // 8))
+        extra["mesh"] = mesh_leg(dev, args.warmup, max(3, args.steps // 4))
 
     if rank != 0:
         if world > 1:

@@ -406,6 +406,31 @@ int dgs_lidar_trace(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes,
                     float r_min, float r_max, float* out_d, float* out_a, void* stream);
 
 /*
+ * Mesh -> Gaussian transfer (Sec. III-B, Mesh-Gaussian Transfer: interactive nodes reconstructed
+ * as textured meshes become Gaussian nodes).  Writes one Gaussian per facet, in the node layout
+ * of dgs_node (FP32): mean = the facet's barycentre; rotation with columns (t1, t2, n),
+ * n = normalised (v1 - v0) x (v2 - v0), t1 = normalised v1 - v0, t2 = n x t1 (identity for a
+ * facet of zero area); log_scale = (log s, log s, log(flatten s)) with s the mean
+ * barycentre-to-vertex distance (at least 1e-12); opacity_logit as given; SH degree-0
+ * coefficient (c - 1/2) / Y_00 with c the mean of the facet's vertex colours (zero without
+ * colours) and higher-degree coefficients zero.
+ *
+ *   vertices[n_vertices*3]       DEVICE FP32
+ *   faces[n_faces*3]             DEVICE int32 vertex indices
+ *   vertex_colors                DEVICE FP32 [n_vertices*3] in [0,1], or NULL
+ *   flatten                      normal-to-tangent scale ratio, (0, 1]
+ *   sh_degree                    0..3: out_sh holds (sh_degree+1)^2 coefficients per facet
+ *   out_mean [F*3], out_log_scale [F*3], out_quat [F*4] (16-byte aligned), out_opacity_logit [F],
+ *   out_sh [F*(sh_degree+1)^2*3]  DEVICE FP32
+ * Synchronises `stream`; a face index outside [0, n_vertices) gives DGS_ERR_INVALID_ARG (that
+ * facet's outputs are the identity-frame defaults).
+ */
+int dgs_mesh_to_gaussians(dgs_ctx* ctx, const float* vertices, int64_t n_vertices, const int32_t* faces,
+                          int64_t n_faces, const float* vertex_colors, float flatten, float opacity_logit,
+                          int32_t sh_degree, float* out_mean, float* out_log_scale, float* out_quat,
+                          float* out_opacity_logit, float* out_sh, void* stream);
+
+/*
  * dgs_render_noalloc -- dgs_render for callers that must not allocate GPU memory.  The paper
  * has no counterpart: this is a deployment variant of the same batched render.
  *

@@ -1499,3 +1499,39 @@ int dgs_lidar_trace(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const 
 }
 
 }  // extern "C"
+
+extern "C" {
+
+int dgs_mesh_to_gaussians(dgs_ctx* ctx, const float* vertices, int64_t n_vertices, const int32_t* faces,
+                          int64_t n_faces, const float* vertex_colors, float flatten, float opacity_logit,
+                          int32_t sh_degree, float* out_mean, float* out_log_scale, float* out_quat,
+                          float* out_opacity_logit, float* out_sh, void* stream_) {
+    if (!ctx) return DGS_ERR_INVALID_ARG;
+    begin_call(ctx);
+    if (n_faces < 0 || n_vertices < 0 || n_vertices >= (1ll << 31))
+        return fail(ctx, DGS_ERR_INVALID_ARG, "need n_faces >= 0 and 0 <= n_vertices < 2^31");
+    if (!(flatten > 0.f && flatten <= 1.f)) return fail(ctx, DGS_ERR_INVALID_ARG, "flatten must be in (0, 1]");
+    if (!finite(opacity_logit)) return fail(ctx, DGS_ERR_INVALID_ARG, "opacity_logit must be finite");
+    if (sh_degree < 0 || sh_degree > 3) return fail(ctx, DGS_ERR_INVALID_ARG, "sh_degree must be 0..3");
+    if (n_faces == 0) return DGS_OK;
+    if (!vertices || !faces || !out_mean || !out_log_scale || !out_quat || !out_opacity_logit || !out_sh)
+        return fail(ctx, DGS_ERR_INVALID_ARG, "null pointer argument");
+    if (reinterpret_cast<uintptr_t>(out_quat) % 16) return fail(ctx, DGS_ERR_INVALID_ARG, "out_quat must be 16-byte aligned");
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    int rc;
+    if ((rc = ensure(ctx, ctx->errword, 64))) return rc;
+    uint32_t* err = static_cast<uint32_t*>(ctx->errword.p);
+    DGS_CUDA(ctx, cudaMemsetAsync(err, 0, 64, stream));
+    Launch L{stream, &ctx->launches};
+    launch_mesh_gaussians(L, vertices, n_vertices, faces, n_faces, vertex_colors, flatten, opacity_logit,
+                          (sh_degree + 1) * (sh_degree + 1), out_mean, out_log_scale, out_quat, out_opacity_logit, out_sh,
+                          err);
+    DGS_CUDA(ctx, cudaGetLastError());
+    uint32_t errw = 0;
+    DGS_CUDA(ctx, cudaMemcpyAsync(&errw, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+    DGS_CUDA(ctx, cudaStreamSynchronize(stream));
+    if (errw & kErrIndex) return fail(ctx, DGS_ERR_INVALID_ARG, "a face index is outside [0, n_vertices)");
+    return DGS_OK;
+}
+
+}  // extern "C"

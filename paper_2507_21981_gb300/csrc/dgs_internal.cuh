@@ -20,6 +20,7 @@ constexpr uint32_t kErrPose = 1u;       // non-finite or non-rigid node pose
 constexpr uint32_t kErrTimeout = 2u;    // a bounded spin gave up
 constexpr uint32_t kErrCapacity = 4u;   // a count exceeded its buffer
 constexpr uint32_t kErrMismatch = 8u;   // count and emit passes disagreed on a chunk
+constexpr uint32_t kErrIndex = 16u;     // an input index out of range (mesh faces)
 
 struct NodeDesc {
     const float* mean;
@@ -372,6 +373,12 @@ void launch_lidar_setup(const Launch& L, const LidarSensorDev* sensors, int S, c
 void launch_lidar_trace(const Launch& L, const LidarTreeDev* trees, const LidarSlot* slots, int K, const float* dirs,
                         int n_dirs, int64_t n_rays, const LidarParams& LP, float* out_d, float* out_a, uint32_t* err,
                         unsigned long long* next_ray);
+
+// Mesh -> Gaussian transfer (csrc/mesh.cu): one Gaussian per facet into node-layout arrays
+// (quat must be 16-byte aligned).
+void launch_mesh_gaussians(const Launch& L, const float* v, int64_t n_v, const int32_t* f, int64_t n_f,
+                           const float* col, float flatten, float opacity_logit, int n_coef, float* mean,
+                           float* log_scale, float* quat, float* opac, float* sh, uint32_t* err);
 
 void launch_composite_bwd(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
                           const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,

@@ -73,7 +73,7 @@ class dgs_lidar(C.Structure):
 EXPORTED = ("dgs_default_options", "dgs_context_create", "dgs_context_destroy", "dgs_last_error",
             "dgs_workspace_query", "dgs_render", "dgs_last_stats", "dgs_kernel_times", "dgs_last_launches",
             "dgs_render_noalloc", "dgs_render_backward", "dgs_autotune", "dgs_spatial_order",
-            "dgs_set_augment", "dgs_augment_rgb", "dgs_lidar_build", "dgs_lidar_trace")
+            "dgs_set_augment", "dgs_augment_rgb", "dgs_lidar_build", "dgs_lidar_trace", "dgs_mesh_to_gaussians")
 
 _lib = None
 _lock = threading.Lock()
@@ -135,6 +135,9 @@ def load(path: str | None = None) -> C.CDLL:
         lib.dgs_lidar_trace.restype = C.c_int
         lib.dgs_lidar_trace.argtypes = [vp, C.POINTER(dgs_node), i32, vp, i32, i32, vp, C.POINTER(dgs_lidar), i32, vp,
                                         i32, C.c_float, C.c_float, vp, vp, vp]
+        lib.dgs_mesh_to_gaussians.restype = C.c_int
+        lib.dgs_mesh_to_gaussians.argtypes = [vp, vp, i64, vp, i64, vp, C.c_float, C.c_float, i32, vp, vp, vp, vp, vp,
+                                              vp]
         if path is None:
             _lib = lib
         return lib
@@ -292,3 +295,12 @@ def lidar_sensors(sensor_env, sensor_pose):
         arr[i].env = int(env[i])
         arr[i].world_from_sensor[:] = [float(x) for x in pose[i]]
     return arr
+
+
+def dgs_mesh_to_gaussians(ctx, vertices, n_vertices, faces, n_faces, vertex_colors, flatten, opacity_logit, sh_degree,
+                          out_mean, out_log_scale, out_quat, out_opacity_logit, out_sh, stream) -> int:
+    """Direct call of dgs_mesh_to_gaussians (device buffers as torch tensors or addresses)."""
+    return load().dgs_mesh_to_gaussians(ctx, _ptr(vertices), int(n_vertices), _ptr(faces), int(n_faces),
+                                        _ptr(vertex_colors), float(flatten), float(opacity_logit), int(sh_degree),
+                                        _ptr(out_mean), _ptr(out_log_scale), _ptr(out_quat), _ptr(out_opacity_logit),
+                                        _ptr(out_sh), stream)

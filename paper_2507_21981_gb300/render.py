@@ -193,6 +193,25 @@ class Renderer:
             raise D.DgsError(rc, D.dgs_last_error(self.ctx))
         return out
 
+    def mesh_to_gaussians(self, vertices, faces, vertex_colors=None, flatten: float = 0.01,
+                          opacity_logit: float = 2.0, sh_degree: int = 0, stream=None) -> dict:
+        """One flat Gaussian per facet (dgs_mesh_to_gaussians): vertices [V,3] FP32 and faces
+        [F,3] int32 CUDA tensors (colours [V,3] or None).  Returns CUDA tensors in the node
+        layout: mean, log_scale, quat, opacity_logit, sh [F, (deg+1)^2, 3]."""
+        F = int(faces.shape[0])
+        dev = vertices.device
+        nc = (sh_degree + 1) ** 2
+        out = dict(mean=torch.empty((F, 3), device=dev), log_scale=torch.empty((F, 3), device=dev),
+                   quat=torch.empty((F, 4), device=dev), opacity_logit=torch.empty((F,), device=dev),
+                   sh=torch.empty((F, nc, 3), device=dev))
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        rc = D.dgs_mesh_to_gaussians(self.ctx, vertices, int(vertices.shape[0]), faces, F, vertex_colors, flatten,
+                                     opacity_logit, sh_degree, out["mean"], out["log_scale"], out["quat"],
+                                     out["opacity_logit"], out["sh"], s.cuda_stream)
+        if rc != D.DGS_OK:
+            raise D.DgsError(rc, D.dgs_last_error(self.ctx))
+        return out
+
     def _outputs(self, ds: DeviceScene, with_alpha: bool):
         def fresh():
             return (torch.empty((ds.n_pixels, 3), dtype=torch.float32, device=ds.device),

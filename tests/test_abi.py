@@ -257,3 +257,19 @@ def test_lidar_validates_on_host(lib):
         assert lib.dgs_lidar_build(ctx, bad, 1, None) == D.DGS_ERR_INVALID_ARG
     finally:
         lib.dgs_context_destroy(ctx)
+
+
+def test_mesh_to_gaussians_validates_on_host(lib):
+    ctx = _ctx(lib)
+    try:
+        def call(nv=3, nf=1, flatten=0.01, op=2.0, deg=0, quat=FAKE_DEV, v=FAKE_DEV):
+            return lib.dgs_mesh_to_gaussians(ctx, v, nv, FAKE_DEV, nf, None, flatten, op, deg, FAKE_DEV, FAKE_DEV,
+                                             quat, FAKE_DEV, FAKE_DEV, None)
+        assert lib.dgs_mesh_to_gaussians(None, FAKE_DEV, 3, FAKE_DEV, 1, None, 0.01, 2.0, 0, FAKE_DEV, FAKE_DEV,
+                                         FAKE_DEV, FAKE_DEV, FAKE_DEV, None) == D.DGS_ERR_INVALID_ARG
+        assert call(nf=0) == D.DGS_OK                                       # nothing to do
+        for bad in (dict(nf=-1), dict(nv=-1), dict(flatten=0.0), dict(flatten=1.5), dict(op=float("nan")),
+                    dict(deg=4), dict(quat=FAKE_DEV + 4), dict(v=None)):
+            assert call(**bad) == D.DGS_ERR_INVALID_ARG, bad
+    finally:
+        lib.dgs_context_destroy(ctx)
