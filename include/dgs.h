@@ -137,7 +137,10 @@ typedef enum dgs_kernel_class {
     DGS_K_SETUP = 0, DGS_K_COUNT = 1, DGS_K_SCAN = 2, DGS_K_EMIT = 3, DGS_K_SORT = 4,
     DGS_K_RANGES = 5, DGS_K_COMPOSITE = 6, DGS_K_BACKWARD = 7,
     DGS_K_GRAPH = 8,            /* a whole graph replay (DGS_MODE_GRAPH) */
-    DGS_K_COUNT_CLASSES = 9
+    DGS_K_AUGMENT = 9,          /* dgs_augment_rgb's pass */
+    DGS_K_LIDAR = 10,           /* dgs_lidar_trace (setup + trace) */
+    DGS_K_MESH = 11,            /* dgs_mesh_to_gaussians */
+    DGS_K_COUNT_CLASSES = 12
 } dgs_kernel_class;
 
 /* Fills *opt with the defaults listed above. */
@@ -236,7 +239,8 @@ int dgs_render_backward(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes,
 /* Statistics of the most recent successful dgs_render on ctx. */
 int dgs_last_stats(const dgs_ctx* ctx, dgs_stats* out);
 
-/* Per-kernel-class device time (ms) of the most recent call with profile = 1;
+/* Per-kernel-class device time (ms) of the most recent call with profile = 1 (dgs_render,
+ * dgs_render_backward, dgs_augment_rgb, dgs_lidar_trace or dgs_mesh_to_gaussians);
  * ms[DGS_K_COUNT_CLASSES]. */
 int dgs_kernel_times(const dgs_ctx* ctx, float* ms);
 
@@ -352,8 +356,9 @@ int dgs_set_augment(dgs_ctx* ctx, const dgs_augment* aug, int32_t n_views, const
  *   view_pixel_offset    HOST [n_views] first pixel of each view, or NULL (views packed in order).
  *   n_views              must equal the n_views of dgs_set_augment (>= 1).
  *
- * Work is queued on `stream` and the call returns without synchronising; the host tables are
- * staged in the context (the caller's arrays may be freed on return).  Returns
+ * Work is queued on `stream` and the call returns without synchronising (with dgs_options.profile
+ * set it synchronises to read its kernel time); the host tables are staged in the context (the
+ * caller's arrays may be freed on return).  Returns
  * DGS_ERR_INVALID_ARG when no randomisation is set or an argument is out of range.
  */
 int dgs_augment_rgb(dgs_ctx* ctx, float* rgb, const int32_t* view_size, const int64_t* view_pixel_offset,

@@ -201,6 +201,7 @@ struct Timer {
     cudaStream_t s;
     bool on;
     cudaEvent_t a{};
+
     int cls = -1;
     void begin(int c) {
         if (!on) return;
@@ -216,6 +217,15 @@ struct Timer {
         cls = -1;
     }
 };
+
+// After the stream has been synchronised: the profiled ranges' times into ctx->ktimes.
+void collect_times(dgs_ctx* ctx) {
+    if (!ctx->opt.profile) return;
+    for (const TimedRange& r : ctx->ranges_timed) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) ctx->ktimes[r.cls] += ms;
+    }
+}
 
 __global__ void k_view_totals(const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off,
                               const int64_t* __restrict__ view_tab, int n, uint64_t* out) {
@@ -1315,9 +1325,16 @@ int dgs_augment_rgb(dgs_ctx* ctx, float* rgb, const int32_t* view_size, const in
     DGS_CUDA(ctx, cudaMemcpyAsync(ds, hs, bytes, cudaMemcpyHostToDevice, stream));
     DGS_CUDA(ctx, cudaEventRecord(ctx->aug_copied, stream));
     Launch L{stream, &ctx->launches};
+    Timer tm{ctx, stream, ctx->opt.profile != 0};
+    tm.begin(DGS_K_AUGMENT);
     launch_augment(L, reinterpret_cast<const AugSpan*>(ds), V, q, reinterpret_cast<const dgs_augment*>(ds + o_aug),
                    ctx->overlay, ctx->ov_w, ctx->ov_h, rgb);
+    tm.end();
     DGS_CUDA(ctx, cudaGetLastError());
+    if (ctx->opt.profile) {
+        DGS_CUDA(ctx, cudaStreamSynchronize(stream));
+        collect_times(ctx);
+    }
     return DGS_OK;
 }
 
@@ -1325,6 +1342,7 @@ int dgs_augment_rgb(dgs_ctx* ctx, float* rgb, const int32_t* view_size, const in
 
 // ------------------------------------------------------------------------------------- LiDAR
 namespace {
+
 
 int check_nodes(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes) {
     if (n_nodes < 1 || !nodes) return fail(ctx, DGS_ERR_INVALID_ARG, "nodes: need n_nodes >= 1 and a node array");
@@ -1482,6 +1500,8 @@ int dgs_lidar_trace(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const 
     DGS_CUDA(ctx, cudaMemsetAsync(err, 0, 64, stream));
     DGS_CUDA(ctx, cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, stream));
     Launch L{stream, &ctx->launches};
+    Timer tm{ctx, stream, ctx->opt.profile != 0};
+    tm.begin(DGS_K_LIDAR);
     LidarSlot* slots = static_cast<LidarSlot*>(ctx->lid_slots.p);
     launch_lidar_setup(L, reinterpret_cast<const LidarSensorDev*>(d), n_sensors,
                        reinterpret_cast<const int32_t*>(d + o_slot), K, node_poses, slots, err);
@@ -1489,10 +1509,12 @@ int dgs_lidar_trace(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const 
     launch_lidar_trace(L, static_cast<const LidarTreeDev*>(ctx->lid_tab.p), slots, K, dirs, n_dirs,
                        (int64_t)n_sensors * n_dirs, LP, out_d, out_a, err,
                        reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->errword.p) + 8));
+    tm.end();
     DGS_CUDA(ctx, cudaGetLastError());
     uint32_t errw = 0;
     DGS_CUDA(ctx, cudaMemcpyAsync(&errw, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
     DGS_CUDA(ctx, cudaStreamSynchronize(stream));
+    collect_times(ctx);
     if (errw & kErrPose) return fail(ctx, DGS_ERR_INVALID_ARG, "a node pose is not finite or not rigid");
     if (errw & kErrCapacity) return fail(ctx, DGS_ERR_CUDA, "internal: BVH traversal stack overflow");
     return DGS_OK;
@@ -1523,13 +1545,17 @@ int dgs_mesh_to_gaussians(dgs_ctx* ctx, const float* vertices, int64_t n_vertice
     uint32_t* err = static_cast<uint32_t*>(ctx->errword.p);
     DGS_CUDA(ctx, cudaMemsetAsync(err, 0, 64, stream));
     Launch L{stream, &ctx->launches};
+    Timer tm{ctx, stream, ctx->opt.profile != 0};
+    tm.begin(DGS_K_MESH);
     launch_mesh_gaussians(L, vertices, n_vertices, faces, n_faces, vertex_colors, flatten, opacity_logit,
                           (sh_degree + 1) * (sh_degree + 1), out_mean, out_log_scale, out_quat, out_opacity_logit, out_sh,
                           err);
+    tm.end();
     DGS_CUDA(ctx, cudaGetLastError());
     uint32_t errw = 0;
     DGS_CUDA(ctx, cudaMemcpyAsync(&errw, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
     DGS_CUDA(ctx, cudaStreamSynchronize(stream));
+    collect_times(ctx);
     if (errw & kErrIndex) return fail(ctx, DGS_ERR_INVALID_ARG, "a face index is outside [0, n_vertices)");
     return DGS_OK;
 }

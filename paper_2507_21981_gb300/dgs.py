@@ -20,7 +20,8 @@ DGS_F32, DGS_BF16, DGS_F16 = 0, 1, 2
 DGS_MODE_PLAIN, DGS_MODE_BATCHED, DGS_MODE_GRAPH = 0, 1, 2
 DGS_PATH_EAGER, DGS_PATH_GRAPH, DGS_PATH_CAPTURED, DGS_PATH_REGROWN = 0, 1, 2, 3
 DGS_TUNE_MAX = 16
-KERNEL_CLASSES = ("setup", "count", "scan", "emit", "sort", "ranges", "composite", "backward", "graph")
+KERNEL_CLASSES = ("setup", "count", "scan", "emit", "sort", "ranges", "composite", "backward", "graph", "augment",
+                  "lidar", "mesh")
 STATUS_NAMES = {0: "DGS_OK", 1: "DGS_ERR_INVALID_ARG", 2: "DGS_ERR_CUDA", 3: "DGS_ERR_OOM", 4: "DGS_ERR_CAPACITY",
                 5: "DGS_ERR_TIMEOUT", 6: "DGS_ERR_UNSUPPORTED"}
 
