@@ -10,11 +10,11 @@ The rendering arithmetic lives in oracle.cpp (plain FP64 C++, std::thread over p
 see its header for the definition it implements and the readings it fixes.  The image
 randomisation applied to rendered frames is augment.py (numpy, FP64); LiDAR ray tracing of the
 same Gaussians is lidar.cpp / lidar.py (FP64 C++, brute force over the env's Gaussians); the
-mesh -> Gaussian transfer is mesh.py (numpy, FP64).
+mesh -> Gaussian transfer is mesh.py and depth -> TSDF fusion tsdf.py (numpy, FP64).
 """
-from . import augment, lidar, mesh
+from . import augment, lidar, mesh, tsdf
 from .oracle import (OracleOptions, build, lib_path, project_view, render_view, backward_view,
                      backward_scene, pose_twist_grad, sh_basis, depth_key32)
 
-__all__ = ["OracleOptions", "augment", "lidar", "mesh", "build", "lib_path", "project_view", "render_view", "backward_view",
+__all__ = ["OracleOptions", "augment", "lidar", "mesh", "tsdf", "build", "lib_path", "project_view", "render_view", "backward_view",
            "backward_scene", "pose_twist_grad", "sh_basis", "depth_key32"]

@@ -619,3 +619,37 @@ def mesh_heightfield(seed: int, nx: int, ny: int, size: float = 1.0, amp: float 
     col = 0.5 + 0.4 * np.stack([np.sin(3 * xs + ph[0]), np.sin(4 * ys + ph[1]), np.cos(2 * (xs + ys) + ph[2])],
                                axis=-1).reshape(-1, 3)
     return verts.astype(np.float32), faces.astype(np.int32), col.astype(np.float32)
+
+
+# ------------------------------------------------------------------------------- depth views
+def sphere_depth_views(centre, radius: float, n_views: int = 8, width: int = 96, height: int = 72,
+                       f: float = 80.0, dist: float = 1.0, seed: int = 0):
+    """Synthetic depth maps of a sphere for fusion tests: n_views pinhole cameras on a ring at
+    `dist` from the centre (random elevation in +-30 degrees) looking at it; per view the
+    camera-space z of the first ray-sphere intersection through each pixel centre (0 where the
+    ray misses) and coverage 1 / 0.  Returns (cams [(fx, fy, cx, cy, W, H, cam_from_world)],
+    depth float32 [V, H, W], alpha float32 [V, H, W])."""
+    rng = _rng(seed, 105)
+    c = np.asarray(centre, np.float64)
+    cams, depth, alpha = [], [], []
+    for k in range(n_views):
+        az = 2 * np.pi * k / n_views + rng.uniform(-0.2, 0.2)
+        el = rng.uniform(-np.pi / 6, np.pi / 6)
+        eye = c + dist * np.array([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)])
+        P = look_at(eye, c)
+        R, t = P[:, :3], P[:, 3]
+        ys, xs = np.mgrid[0:height, 0:width].astype(np.float64)
+        dc = np.stack([(xs + 0.5 - width / 2) / f, (ys + 0.5 - height / 2) / f, np.ones_like(xs)], axis=-1)
+        dw = dc @ R                                  # world direction (unnormalised, camera z = 1)
+        oc = eye - c
+        a = np.sum(dw * dw, axis=-1)
+        b = 2 * dw @ oc
+        cc = oc @ oc - radius * radius
+        disc = b * b - 4 * a * cc
+        hit = disc >= 0
+        s = np.where(hit, (-b - np.sqrt(np.maximum(disc, 0))) / (2 * a), 0.0)   # s = camera-space z
+        hit &= s > 0
+        depth.append(np.where(hit, s, 0.0).astype(np.float32))
+        alpha.append(hit.astype(np.float32))
+        cams.append((f, f, width / 2.0, height / 2.0, width, height, P.astype(np.float32)))
+    return cams, np.stack(depth), np.stack(alpha)
