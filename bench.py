@@ -34,6 +34,10 @@ OPS_PER_PAIR = 21
 # kernel on the 8-env case (profiles/kernels_config2_8envs_640x480.md: 120.7 + 70.4 MB) scaled
 # by the 8x views of the full launch; absent for a kernel that changed since its capture.
 TRAFFIC = {"composite": (116.2e6 + 68.6e6) * 8}
+# FP32 operations per (voxel, view) of the TSDF fusion: camera-space point (9 FMA), reciprocal,
+# projection (4), bounds (4 compares), coverage test, normalised depth (2), sdf, truncation,
+# clamp (2), running average (3), weight update (2)
+TSDF_OPS = 30
 WORKLOAD = "64 envs x 2 cams 640x480, 1M-Gaussian SH3 room + 4 objects x 20k at per-env poses (config 2)"
 
 
@@ -392,6 +396,69 @@ def mesh_leg(dev, warmup, steps):
             "oracle_mfacets_s": 20_000 / t_or / 1e6, "oracle_sample": "20k facets, numpy FP64, 1 thread", "steps": steps}
 
 
+def tsdf_leg(dev, sc, warmup, steps):
+    """Gaussian node -> mesh, first half (Sec. III-B): 64 depth views of env 0 of the benchmark
+    scene (room + objects) from a ring of cameras around the workspace, rendered by the library,
+    then fused into a 256^3 TSDF over a 1.2 m cube around the workspace (4.7 mm voxels).  The
+    fusion kernel is timed with the library's CUDA events; its work is 16.8M voxels x 64 views."""
+    import numpy as np
+    import torch
+    from paper_2507_21981_gb300 import dgs as D
+    from paper_2507_21981_gb300 import scenes
+    from paper_2507_21981_gb300.render import DeviceScene, Renderer
+    c = scenes.WORKSPACE_CENTRE
+    cams = []
+    for k in range(64):
+        az = 2 * np.pi * k / 64
+        el = np.deg2rad(20 + 25 * (k % 2))
+        eye = c + 1.1 * np.array([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)])
+        cams.append((500.0, 500.0, 320.0, 240.0, 640, 480, scenes.look_at(eye, c)))
+    ks = [int(x) for x in sc.env_node_ids[0] if x >= 0]
+    one = scenes.scene_from_lists("tsdf", sc.nodes, [ks], [[sc.node_poses[0, j] for j in range(len(ks))]], [cams])
+    ds = DeviceScene(one, device=dev, spatial_order=True)
+    r = Renderer(mode="batched")
+    rgb, depth, alpha = r.render(ds)
+    n, side = 256, 1.2
+    origin = (c - side / 2).astype(np.float32)
+    F = torch.zeros((n, n, n), device=dev)
+    W = torch.zeros((n, n, n), device=dev)
+    cam_arr = D.cameras(cams)
+    rp = Renderer(profile=1)
+    stream = torch.cuda.current_stream(dev)
+    kms = []
+    for it in range(warmup + steps):
+        F.zero_(); W.zero_()
+        rc = D.dgs_tsdf_integrate(rp.ctx, F, W, n, n, n, origin, side / n, 0.02, 100.0, 0.5, cam_arr, 64, depth, alpha,
+                                  None, stream.cuda_stream)
+        assert rc == D.DGS_OK
+        if it >= warmup:
+            kms.append(rp.kernel_times()["tsdf"])
+    rp.close()
+    r.close()
+    k_ms = float(np.median(kms))
+    upd = n ** 3 * 64
+    seen = float((W > 0).float().mean())
+    mhz = _peaks()[0].get("sm_max_mhz", 2070.0)
+    peak = 152 * 128 * mhz * 1e6 / 1e12
+    ops = upd * TSDF_OPS
+    res = {"workload": "64 rendered depth views (640x480) of env 0 -> 256^3 TSDF over a 1.2 m cube", "voxels": n ** 3,
+           "views": 64, "kernel_ms": k_ms, "gupdates_s": upd / k_ms / 1e6, "observed_frac": seen,
+           "roofline": {"bound": "alu", "achieved": ops / k_ms / 1e9, "peak": peak, "unit": "Tops/s FP32",
+                        "frac": ops / k_ms / 1e9 / peak, "ops_per_voxel_view": TSDF_OPS,
+                        "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"}, "steps": steps}
+    # the oracle on a 24^3 block of the grid (numpy FP64, one thread)
+    import oracle
+    Dh = depth.cpu().numpy().reshape(64, 480, 640)
+    Ah = alpha.cpu().numpy().reshape(64, 480, 640)
+    t0 = time.perf_counter()
+    oracle.tsdf.integrate(np.zeros((24, 24, 24)), np.zeros((24, 24, 24)), origin.astype(np.float64) + 0.5, side / n,
+                          0.02, 100.0, 0.5, cams, Dh, Ah)
+    dt = time.perf_counter() - t0
+    res["oracle_gupdates_s"] = 24 ** 3 * 64 / dt / 1e9
+    res["oracle_sample"] = "24^3 voxels x 64 views, numpy FP64, 1 thread"
+    return res
+
+
 def cpu_baseline(views=1, seed=1):
     """Times the FP64 oracle on `views` sampled views of the workload (host cores)."""
     import oracle
@@ -598,6 +665,7 @@ def main():
         extra["augment"] = augment_leg(dev, ds, tile, out, args.warmup, max(3, args.steps // 4), ms)
         extra["lidar"] = lidar_leg(dev, ds, args.warmup, max(3, args.steps // 8))
         extra["mesh"] = mesh_leg(dev, args.warmup, max(3, args.steps // 4))
+        extra["tsdf"] = tsdf_leg(dev, sc, args.warmup, max(3, args.steps // 8))
 
     if rank != 0:
         if world > 1:

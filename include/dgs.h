@@ -140,7 +140,8 @@ typedef enum dgs_kernel_class {
     DGS_K_AUGMENT = 9,          /* dgs_augment_rgb's pass */
     DGS_K_LIDAR = 10,           /* dgs_lidar_trace (setup + trace) */
     DGS_K_MESH = 11,            /* dgs_mesh_to_gaussians */
-    DGS_K_COUNT_CLASSES = 12
+    DGS_K_TSDF = 12,            /* dgs_tsdf_integrate */
+    DGS_K_COUNT_CLASSES = 13
 } dgs_kernel_class;
 
 /* Fills *opt with the defaults listed above. */
@@ -240,7 +241,8 @@ int dgs_render_backward(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes,
 int dgs_last_stats(const dgs_ctx* ctx, dgs_stats* out);
 
 /* Per-kernel-class device time (ms) of the most recent call with profile = 1 (dgs_render,
- * dgs_render_backward, dgs_augment_rgb, dgs_lidar_trace or dgs_mesh_to_gaussians);
+ * dgs_render_backward, dgs_augment_rgb, dgs_lidar_trace, dgs_mesh_to_gaussians or
+ * dgs_tsdf_integrate);
  * ms[DGS_K_COUNT_CLASSES]. */
 int dgs_kernel_times(const dgs_ctx* ctx, float* ms);
 
@@ -434,6 +436,32 @@ int dgs_mesh_to_gaussians(dgs_ctx* ctx, const float* vertices, int64_t n_vertice
                           int64_t n_faces, const float* vertex_colors, float flatten, float opacity_logit,
                           int32_t sh_degree, float* out_mean, float* out_log_scale, float* out_quat,
                           float* out_opacity_logit, float* out_sh, void* stream);
+
+/*
+ * Depth -> TSDF fusion (Sec. III-B: a Gaussian node is converted back to a mesh by rendering
+ * multi-view depth maps and fusing them into a truncated signed distance field; decimation is
+ * not part of the library).  Updates a voxel field in place, view by view in the given order.
+ * Voxel (i, j, k) (x fastest) has centre origin + (i + 1/2, j + 1/2, k + 1/2) * voxel.  Per view:
+ * x_c = cam_from_world p; skip if z_c <= 0; (u, v) = (fx x_c / z_c + cx, fy y_c / z_c + cy), the
+ * pixel (floor u, floor v), skipped outside the image; the depth is D / A (the renderer's
+ * unnormalised depth over its coverage), valid where A >= min_alpha; sdf = D / A - z_c, skipped
+ * when sdf < -trunc; f = min(1, sdf / trunc); F <- (W F + f) / (W + 1); W <- min(W + 1, max_weight).
+ * FP32 (approximate reciprocal in the projection and the normalisation).
+ *
+ *   tsdf, weight             DEVICE FP32 [nz*ny*nx] (start from F = 0, W = 0)
+ *   nx, ny, nz               >= 1, nx*ny*nz < 2^31
+ *   origin[3]                HOST, world coordinates of the grid's corner
+ *   voxel, trunc, max_weight > 0, finite; min_alpha in (0, 1]
+ *   cams[n_views]            HOST (intrinsics, resolution and cam_from_world of each view)
+ *   depth, alpha             DEVICE FP32, flat over views like dgs_render's out_depth/out_alpha
+ *   view_pixel_offset        HOST [n_views] or NULL (views packed in order)
+ * Work is queued on `stream` without synchronising (with dgs_options.profile set the call
+ * synchronises to read its kernel time); the host tables are staged in the context.
+ */
+int dgs_tsdf_integrate(dgs_ctx* ctx, float* tsdf, float* weight, int32_t nx, int32_t ny, int32_t nz,
+                       const float* origin, float voxel, float trunc, float max_weight, float min_alpha,
+                       const dgs_camera* cams, int32_t n_views, const float* depth, const float* alpha,
+                       const int64_t* view_pixel_offset, void* stream);
 
 /*
  * dgs_render_noalloc -- dgs_render for callers that must not allocate GPU memory.  The paper

@@ -13,7 +13,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgs.so")
 SOURCES = ["api.cu", "project.cu", "sort.cu", "binning.cu", "composite.cu", "backward.cu", "noalloc.cu", "layout.cu",
-           "augment.cu", "lidar.cu", "mesh.cu"]
+           "augment.cu", "lidar.cu", "mesh.cu", "tsdf.cu"]
 HEADERS = [os.path.join(CSRC, "dgs_internal.cuh"), os.path.join(INCLUDE, "dgs.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]

@@ -98,6 +98,11 @@ struct dgs_ctx {
     void* h_aug = nullptr;                // its pinned staging
     size_t h_aug_bytes = 0;
     cudaEvent_t aug_copied = nullptr;     // the staging's last upload has been read
+    // TSDF fusion: view table (device), its pinned staging and the event guarding the staging
+    DevBuf tsdf_meta, tsdf_depth;
+    void* h_tsdf = nullptr;
+    size_t h_tsdf_bytes = 0;
+    cudaEvent_t tsdf_copied = nullptr;
     // LiDAR (dgs_lidar_build / dgs_lidar_trace)
     DevBuf lid_rec, lid_box, lid_tab, lid_meta, lid_slots;
     std::vector<dgs_node> lid_nodes;      // the nodes the structures were built from
@@ -1086,6 +1091,10 @@ int dgs_context_destroy(dgs_ctx* ctx) {
     if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
     if (ctx->h_read) cudaFreeHost(ctx->h_read);
     free_buf(ctx->aug_dev);
+    free_buf(ctx->tsdf_meta);
+    free_buf(ctx->tsdf_depth);
+    if (ctx->h_tsdf) cudaFreeHost(ctx->h_tsdf);
+    if (ctx->tsdf_copied) cudaEventDestroy(ctx->tsdf_copied);
     for (DevBuf* b : {&ctx->lid_rec, &ctx->lid_box, &ctx->lid_tab, &ctx->lid_meta, &ctx->lid_slots}) free_buf(*b);
     if (ctx->h_lid) cudaFreeHost(ctx->h_lid);
     if (ctx->h_aug) cudaFreeHost(ctx->h_aug);
@@ -1101,7 +1110,8 @@ int dgs_workspace_query(const dgs_ctx* ctx, size_t* bytes) {
     if (!ctx || !bytes) return DGS_ERR_INVALID_ARG;
     const DevBuf* bufs[] = {&ctx->meta, &ctx->counts, &ctx->inst_off, &ctx->pair_off, &ctx->parts, &ctx->errword,
                             &ctx->readback, &ctx->inst_grad, &ctx->gsizes, &ctx->totals, &ctx->aug_dev,
-                            &ctx->lid_rec, &ctx->lid_box, &ctx->lid_tab, &ctx->lid_meta, &ctx->lid_slots};
+                            &ctx->lid_rec, &ctx->lid_box, &ctx->lid_tab, &ctx->lid_meta, &ctx->lid_slots,
+                            &ctx->tsdf_meta, &ctx->tsdf_depth};
     size_t s = 0;
     for (const DevBuf* b : bufs) s += b->bytes;
     for (const ListBufs& lb : ctx->lists)
@@ -1557,6 +1567,76 @@ int dgs_mesh_to_gaussians(dgs_ctx* ctx, const float* vertices, int64_t n_vertice
     DGS_CUDA(ctx, cudaStreamSynchronize(stream));
     collect_times(ctx);
     if (errw & kErrIndex) return fail(ctx, DGS_ERR_INVALID_ARG, "a face index is outside [0, n_vertices)");
+    return DGS_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int dgs_tsdf_integrate(dgs_ctx* ctx, float* tsdf, float* weight, int32_t nx, int32_t ny, int32_t nz,
+                       const float* origin, float voxel, float trunc, float max_weight, float min_alpha,
+                       const dgs_camera* cams, int32_t n_views, const float* depth, const float* alpha,
+                       const int64_t* view_pixel_offset, void* stream_) {
+    if (!ctx) return DGS_ERR_INVALID_ARG;
+    begin_call(ctx);
+    if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz >= (1ll << 31))
+        return fail(ctx, DGS_ERR_INVALID_ARG, "grid: need nx, ny, nz >= 1 and nx*ny*nz < 2^31");
+    if (!origin || !finite(origin[0]) || !finite(origin[1]) || !finite(origin[2]))
+        return fail(ctx, DGS_ERR_INVALID_ARG, "origin must be 3 finite values");
+    if (!(voxel > 0.f) || !finite(voxel) || !(trunc > 0.f) || !finite(trunc) || !(max_weight > 0.f) ||
+        !finite(max_weight) || !(min_alpha > 0.f && min_alpha <= 1.f))
+        return fail(ctx, DGS_ERR_INVALID_ARG, "need voxel, trunc, max_weight > 0 (finite) and min_alpha in (0, 1]");
+    if (n_views < 0) return fail(ctx, DGS_ERR_INVALID_ARG, "n_views must be >= 0");
+    if (!tsdf || !weight || (n_views > 0 && (!cams || !depth || !alpha)))
+        return fail(ctx, DGS_ERR_INVALID_ARG, "null pointer argument");
+    if (n_views == 0) return DGS_OK;
+    std::vector<TsdfView> views(n_views);
+    int64_t packed = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const dgs_camera& c = cams[v];
+        if (c.width < 1 || c.height < 1 || c.width > 32768 || c.height > 32768)
+            return fail(ctx, DGS_ERR_INVALID_ARG, "camera resolution");
+        if (!(c.fx > 0) || !(c.fy > 0) || !finite(c.fx) || !finite(c.fy) || !finite(c.cx) || !finite(c.cy))
+            return fail(ctx, DGS_ERR_INVALID_ARG, "camera intrinsics");
+        for (int a = 0; a < 12; ++a)
+            if (!finite(c.cam_from_world[a])) return fail(ctx, DGS_ERR_INVALID_ARG, "camera pose not finite");
+        TsdfView& tv = views[v];
+        for (int a = 0; a < 3; ++a) {
+            for (int b = 0; b < 3; ++b) tv.R[3 * a + b] = c.cam_from_world[4 * a + b];
+            tv.t[a] = c.cam_from_world[4 * a + 3];
+        }
+        tv.fx = c.fx; tv.fy = c.fy; tv.cx = c.cx; tv.cy = c.cy; tv.W = c.width; tv.H = c.height;
+        tv.pix_off = view_pixel_offset ? view_pixel_offset[v] : packed;
+        if (tv.pix_off < 0) return fail(ctx, DGS_ERR_INVALID_ARG, "negative view_pixel_offset");
+        tv.q0 = packed;
+        packed += (int64_t)c.width * c.height;
+    }
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    const size_t bytes = sizeof(TsdfView) * n_views;
+    const uint64_t gen = ctx->gen;               // read by this call only, never by a captured graph
+    int rc = ensure(ctx, ctx->tsdf_meta, bytes);
+    if (!rc) rc = ensure(ctx, ctx->tsdf_depth, sizeof(float) * packed);
+    ctx->gen = gen;
+    if (rc) return rc;
+    if ((rc = ensure_host(ctx, ctx->h_tsdf, ctx->h_tsdf_bytes, bytes))) return rc;
+    if (!ctx->tsdf_copied) DGS_CUDA(ctx, cudaEventCreateWithFlags(&ctx->tsdf_copied, cudaEventDisableTiming));
+    else DGS_CUDA(ctx, cudaEventSynchronize(ctx->tsdf_copied));
+    std::memcpy(ctx->h_tsdf, views.data(), bytes);
+    DGS_CUDA(ctx, cudaMemcpyAsync(ctx->tsdf_meta.p, ctx->h_tsdf, bytes, cudaMemcpyHostToDevice, stream));
+    DGS_CUDA(ctx, cudaEventRecord(ctx->tsdf_copied, stream));
+    TsdfParams TP{origin[0], origin[1], origin[2], voxel, trunc, 1.f / trunc, max_weight, min_alpha};
+    Launch L{stream, &ctx->launches};
+    Timer tm{ctx, stream, ctx->opt.profile != 0};
+    tm.begin(DGS_K_TSDF);
+    launch_tsdf(L, tsdf, weight, nx, ny, (int64_t)nx * ny * nz, TP, static_cast<const TsdfView*>(ctx->tsdf_meta.p),
+                n_views, depth, alpha, static_cast<float*>(ctx->tsdf_depth.p), packed);
+    tm.end();
+    DGS_CUDA(ctx, cudaGetLastError());
+    if (ctx->opt.profile) {
+        DGS_CUDA(ctx, cudaStreamSynchronize(stream));
+        collect_times(ctx);
+    }
     return DGS_OK;
 }
 

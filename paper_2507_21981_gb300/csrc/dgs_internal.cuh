@@ -380,6 +380,20 @@ void launch_mesh_gaussians(const Launch& L, const float* v, int64_t n_v, const i
                            const float* col, float flatten, float opacity_logit, int n_coef, float* mean,
                            float* log_scale, float* quat, float* opac, float* sh, uint32_t* err);
 
+// Depth -> TSDF fusion (csrc/tsdf.cu).
+struct TsdfView {
+    float R[9], t[3];        // cam_from_world
+    float fx, fy, cx, cy;
+    int32_t W, H;
+    int64_t pix_off;         // first pixel of the view in the depth / coverage arrays
+    int64_t q0;              // first pixel of the view in the packed normalised-depth scratch
+};
+struct TsdfParams {
+    float ox, oy, oz, voxel, trunc, inv_trunc, max_weight, min_alpha;
+};
+void launch_tsdf(const Launch& L, float* F, float* W, int nx, int ny, int64_t n_vox, const TsdfParams& TP,
+                 const TsdfView* views, int V, const float* depth, const float* alpha, float* dn, int64_t n_pix);
+
 void launch_composite_bwd(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
                           const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,
                           const float* out_rgb, const float* out_depth, const float* g_rgb, const float* g_depth,

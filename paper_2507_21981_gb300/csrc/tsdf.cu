@@ -1,0 +1,80 @@
+// Depth -> TSDF fusion (Sec. III-B: a Gaussian node is turned back into a mesh by rendering
+// multi-view depth maps and fusing them into a truncated signed distance field; the decimation
+// that follows is not part of this library).
+//
+// A pre-pass writes every pixel's normalised depth d = D / A (NaN where A < min_alpha) into a
+// packed array.  Then one thread per voxel, x fastest (coalesced field reads and writes); each
+// thread loops over the views in order: project the voxel centre, read d at the pixel holding
+// the projection, sdf = d - z, skip when
+// sdf < -trunc, f = min(1, sdf / trunc), F <- (W F + f) / (W + 1), W <- min(W + 1, max_weight).
+// The field is read and written once per call whatever the number of views, so a call with
+// many views is bound by the per-view arithmetic and the depth gathers (served by L2).
+#include "dgs_internal.cuh"
+
+namespace dgs {
+namespace {
+
+constexpr int kTsdfThreads = 256;
+
+// Pre-pass: the normalised depth D / A of every pixel of every view into a packed array (NaN
+// where A < min_alpha), so that the fusion makes one gather per (voxel, view) and no division.
+// Thread = packed pixel q; views[v].q0 = first packed pixel of view v.
+__global__ void __launch_bounds__(kTsdfThreads) k_tsdf_depth(const TsdfView* __restrict__ views, int V, int64_t n_pix,
+                                                             float min_alpha, const float* __restrict__ depth,
+                                                             const float* __restrict__ alpha, float* __restrict__ dn) {
+    const int64_t q = (int64_t)blockIdx.x * kTsdfThreads + threadIdx.x;
+    if (q >= n_pix) return;
+    int lo = 0, hi = V - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (views[mid].q0 <= q) lo = mid; else hi = mid - 1;
+    }
+    const int64_t p = views[lo].pix_off + (q - views[lo].q0);
+    const float a = alpha[p];
+    dn[q] = a >= min_alpha ? __fdividef(depth[p], a) : __int_as_float(0x7fc00000);
+}
+
+__global__ void __launch_bounds__(kTsdfThreads) k_tsdf(float* __restrict__ F, float* __restrict__ Wt, int nx, int ny,
+                                                       int64_t n_vox, TsdfParams TP, const TsdfView* __restrict__ views,
+                                                       int V, const float* __restrict__ dn) {
+    const int64_t idx = (int64_t)blockIdx.x * kTsdfThreads + threadIdx.x;
+    if (idx >= n_vox) return;
+    const int i = (int)(idx % nx);
+    const int64_t r = idx / nx;
+    const int j = (int)(r % ny), k = (int)(r / ny);
+    const float px = fmaf((float)i + 0.5f, TP.voxel, TP.ox), py = fmaf((float)j + 0.5f, TP.voxel, TP.oy),
+                pz = fmaf((float)k + 0.5f, TP.voxel, TP.oz);
+    float f = F[idx], w = Wt[idx];
+    for (int v = 0; v < V; ++v) {
+        const TsdfView& cv = views[v];
+        const float z = fmaf(cv.R[6], px, fmaf(cv.R[7], py, fmaf(cv.R[8], pz, cv.t[2])));
+        if (!(z > 0.f)) continue;
+        const float x = fmaf(cv.R[0], px, fmaf(cv.R[1], py, fmaf(cv.R[2], pz, cv.t[0])));
+        const float y = fmaf(cv.R[3], px, fmaf(cv.R[4], py, fmaf(cv.R[5], pz, cv.t[1])));
+        const float iz = __fdividef(1.f, z);
+        const float u = fmaf(cv.fx * x, iz, cv.cx), vv = fmaf(cv.fy * y, iz, cv.cy);
+        if (!(u >= 0.f) || !(vv >= 0.f) || !(u < (float)cv.W) || !(vv < (float)cv.H)) continue;
+        const float d = __ldg(dn + cv.q0 + (int64_t)(int)vv * cv.W + (int)u);
+        const float sdf = d - z;
+        if (!(sdf >= -TP.trunc)) continue;              // also a pixel without coverage (NaN)
+        const float fv = fminf(1.f, sdf * TP.inv_trunc);
+        f = __fdividef(fmaf(w, f, fv), w + 1.f);
+        w = fminf(w + 1.f, TP.max_weight);
+    }
+    F[idx] = f;
+    Wt[idx] = w;
+}
+
+}  // namespace
+
+void launch_tsdf(const Launch& L, float* F, float* W, int nx, int ny, int64_t n_vox, const TsdfParams& TP,
+                 const TsdfView* views, int V, const float* depth, const float* alpha, float* dn, int64_t n_pix) {
+    if (n_vox <= 0 || n_pix <= 0) return;
+    k_tsdf_depth<<<(unsigned)((n_pix + kTsdfThreads - 1) / kTsdfThreads), kTsdfThreads, 0, L.stream>>>(
+        views, V, n_pix, TP.min_alpha, depth, alpha, dn);
+    k_tsdf<<<(unsigned)((n_vox + kTsdfThreads - 1) / kTsdfThreads), kTsdfThreads, 0, L.stream>>>(F, W, nx, ny, n_vox, TP,
+                                                                                                 views, V, dn);
+    *L.launches += 2;
+}
+
+}  // namespace dgs

@@ -21,7 +21,7 @@ DGS_MODE_PLAIN, DGS_MODE_BATCHED, DGS_MODE_GRAPH = 0, 1, 2
 DGS_PATH_EAGER, DGS_PATH_GRAPH, DGS_PATH_CAPTURED, DGS_PATH_REGROWN = 0, 1, 2, 3
 DGS_TUNE_MAX = 16
 KERNEL_CLASSES = ("setup", "count", "scan", "emit", "sort", "ranges", "composite", "backward", "graph", "augment",
-                  "lidar", "mesh")
+                  "lidar", "mesh", "tsdf")
 STATUS_NAMES = {0: "DGS_OK", 1: "DGS_ERR_INVALID_ARG", 2: "DGS_ERR_CUDA", 3: "DGS_ERR_OOM", 4: "DGS_ERR_CAPACITY",
                 5: "DGS_ERR_TIMEOUT", 6: "DGS_ERR_UNSUPPORTED"}
 
@@ -74,7 +74,8 @@ class dgs_lidar(C.Structure):
 EXPORTED = ("dgs_default_options", "dgs_context_create", "dgs_context_destroy", "dgs_last_error",
             "dgs_workspace_query", "dgs_render", "dgs_last_stats", "dgs_kernel_times", "dgs_last_launches",
             "dgs_render_noalloc", "dgs_render_backward", "dgs_autotune", "dgs_spatial_order",
-            "dgs_set_augment", "dgs_augment_rgb", "dgs_lidar_build", "dgs_lidar_trace", "dgs_mesh_to_gaussians")
+            "dgs_set_augment", "dgs_augment_rgb", "dgs_lidar_build", "dgs_lidar_trace", "dgs_mesh_to_gaussians",
+            "dgs_tsdf_integrate")
 
 _lib = None
 _lock = threading.Lock()
@@ -139,6 +140,9 @@ def load(path: str | None = None) -> C.CDLL:
         lib.dgs_mesh_to_gaussians.restype = C.c_int
         lib.dgs_mesh_to_gaussians.argtypes = [vp, vp, i64, vp, i64, vp, C.c_float, C.c_float, i32, vp, vp, vp, vp, vp,
                                               vp]
+        lib.dgs_tsdf_integrate.restype = C.c_int
+        lib.dgs_tsdf_integrate.argtypes = [vp, vp, vp, i32, i32, i32, vp, C.c_float, C.c_float, C.c_float, C.c_float,
+                                           C.POINTER(dgs_camera), i32, vp, vp, vp, vp]
         if path is None:
             _lib = lib
         return lib
@@ -305,3 +309,22 @@ def dgs_mesh_to_gaussians(ctx, vertices, n_vertices, faces, n_faces, vertex_colo
                                         _ptr(vertex_colors), float(flatten), float(opacity_logit), int(sh_degree),
                                         _ptr(out_mean), _ptr(out_log_scale), _ptr(out_quat), _ptr(out_opacity_logit),
                                         _ptr(out_sh), stream)
+
+
+def dgs_tsdf_integrate(ctx, tsdf, weight, nx, ny, nz, origin, voxel, trunc, max_weight, min_alpha, cams, n_views,
+                       depth, alpha, view_pixel_offset, stream) -> int:
+    """Direct call of dgs_tsdf_integrate; `cams` is a ctypes array of dgs_camera, `origin` 3 floats."""
+    org = np.ascontiguousarray(np.asarray(origin, np.float32).reshape(3))
+    return load().dgs_tsdf_integrate(ctx, _ptr(tsdf), _ptr(weight), int(nx), int(ny), int(nz), org.ctypes.data,
+                                     float(voxel), float(trunc), float(max_weight), float(min_alpha), cams, int(n_views),
+                                     _ptr(depth), _ptr(alpha), _ptr(view_pixel_offset), stream)
+
+
+def cameras(views) -> "C.Array":
+    """ctypes array of dgs_camera from (fx, fy, cx, cy, W, H, cam_from_world [3,4]) tuples."""
+    arr = (dgs_camera * max(len(views), 1))()
+    for k, (fx, fy, cx, cy, w, h, P) in enumerate(views):
+        c = arr[k]
+        c.fx, c.fy, c.cx, c.cy, c.width, c.height = float(fx), float(fy), float(cx), float(cy), int(w), int(h)
+        c.cam_from_world[:] = [float(x) for x in np.asarray(P, np.float32).reshape(12)]
+    return arr

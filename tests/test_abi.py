@@ -273,3 +273,22 @@ def test_mesh_to_gaussians_validates_on_host(lib):
             assert call(**bad) == D.DGS_ERR_INVALID_ARG, bad
     finally:
         lib.dgs_context_destroy(ctx)
+
+
+def test_tsdf_validates_on_host(lib):
+    ctx = _ctx(lib)
+    try:
+        cams = D.cameras([(50.0, 50.0, 16.0, 16.0, 32, 32, np.eye(3, 4))])
+        org = np.zeros(3, np.float32)
+
+        def call(n=(4, 4, 4), org=org, vox=0.01, tr=0.05, wmax=10.0, amin=0.5, nv=1, cams=cams):
+            return lib.dgs_tsdf_integrate(ctx, FAKE_DEV, FAKE_DEV, n[0], n[1], n[2], org.ctypes.data if org is not None else None,
+                                          vox, tr, wmax, amin, cams, nv, FAKE_DEV, FAKE_DEV, None, None)
+        assert call(nv=0) == D.DGS_OK
+        for bad in (dict(n=(0, 4, 4)), dict(n=(2048, 2048, 1024)), dict(org=None), dict(vox=0.0), dict(tr=-1.0),
+                    dict(wmax=0.0), dict(amin=0.0), dict(amin=1.5), dict(nv=-1)):
+            assert call(**bad) == D.DGS_ERR_INVALID_ARG, bad
+        bad_cam = D.cameras([(50.0, 50.0, 16.0, 16.0, 0, 32, np.eye(3, 4))])
+        assert call(cams=bad_cam) == D.DGS_ERR_INVALID_ARG
+    finally:
+        lib.dgs_context_destroy(ctx)
