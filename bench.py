@@ -509,6 +509,8 @@ def main():
     ap.add_argument("--only-batched", action="store_true",
                     help="time the batched render only (no e2e, plain or CPU legs): small profiling runs")
     ap.add_argument("--no-extra", action="store_true", help="skip the ragged and precision workloads")
+    ap.add_argument("--only-leg", choices=["augment", "lidar", "mesh", "tsdf"], default=None,
+                    help="run one side workload alone on --envs envs and print its JSON (profiling runs)")
     ap.add_argument("--views-per-group", type=int, default=0,
                     help="views per group of the batched sequence (0 = as few groups as the sort allows)")
     args = ap.parse_args()
@@ -528,6 +530,19 @@ def main():
 
     sc = rank_scene(rank, args.envs)
     ds = DeviceScene(sc, device=dev, spatial_order=True)
+    if args.only_leg:
+        if args.only_leg == "augment":
+            o = (torch.empty((ds.n_pixels, 3), device=dev), torch.empty((ds.n_pixels,), device=dev), None)
+            res = augment_leg(dev, ds, (16, 16), o, args.warmup, args.steps, float("nan"))
+        elif args.only_leg == "lidar":
+            res = lidar_leg(dev, ds, args.warmup, args.steps)
+        elif args.only_leg == "mesh":
+            res = mesh_leg(dev, args.warmup, args.steps)
+        else:
+            res = tsdf_leg(dev, sc, args.warmup, args.steps)
+        if rank == 0:
+            print(json.dumps({"leg": args.only_leg, **res}))
+        return 0
     stream = torch.cuda.current_stream(dev)
     px_per_step = ds.n_pixels
 

@@ -14,27 +14,26 @@ constexpr int kThreads = 256;
 
 // Thread = one quad of 4 consecutive output pixels (48 bytes: three 16-byte loads and stores
 // when the quad lies inside one view and the buffer is 16-byte aligned; per-pixel scalar
-// accesses at view edges).  Quads are enumerated view by view (spans[v].q0 = first quad of
+// accesses at view edges).  Lane 0 of each warp finds the view of the warp's first quad.  Quads are enumerated view by view (spans[v].q0 = first quad of
 // view v); a view whose first pixel is not a multiple of 4 shares its edge quads with its
 // neighbours, each thread touching only its own view's pixels.
 __global__ void __launch_bounds__(kThreads) k_augment(const AugSpan* __restrict__ spans, int V, int64_t n_quads,
                                                       const dgs_augment* __restrict__ aug,
                                                       const uint8_t* __restrict__ overlay, int ow, int oh,
                                                       float* __restrict__ rgb, bool vec) {
-    __shared__ int s_v;
-    const int64_t j0 = (int64_t)blockIdx.x * kThreads;
-    if (threadIdx.x == 0) {                      // view of the block's first quad
+    const int64_t j0 = (int64_t)blockIdx.x * kThreads + (threadIdx.x & ~31);   // the warp's first quad
+    int v = 0;
+    if ((threadIdx.x & 31) == 0) {               // view of the warp's first quad
         int lo = 0, hi = V - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (spans[mid].q0 <= j0) lo = mid; else hi = mid - 1;
         }
-        s_v = lo;
+        v = lo;
     }
-    __syncthreads();
-    const int64_t j = j0 + threadIdx.x;
+    v = __shfl_sync(0xffffffffu, v, 0);
+    const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (j >= n_quads) return;
-    int v = s_v;
     while (v + 1 < V && spans[v + 1].q0 <= j) ++v;
     const AugSpan sp = spans[v];
     const int32_t n = sp.W * sp.H;               // <= 2^30

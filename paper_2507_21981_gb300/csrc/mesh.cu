@@ -26,8 +26,9 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
 
 constexpr int kMeshThreads = 256;
 
+template <int NC>        // SH coefficients per facet: (degree + 1)^2
 __global__ void __launch_bounds__(kMeshThreads) k_mesh_gaussians(const float* __restrict__ v, int64_t n_v, const int32_t* __restrict__ f, int64_t n_f,
-                                 const float* __restrict__ col, float flatten, float opacity_logit, int n_coef,
+                                 const float* __restrict__ col, float flatten, float opacity_logit,
                                  float* __restrict__ o_mean, float* __restrict__ o_ls, float* __restrict__ o_q,
                                  float* __restrict__ o_op, float* __restrict__ o_sh, uint32_t* __restrict__ err) {
     __shared__ float s_mean[kMeshThreads * 3], s_ls[kMeshThreads * 3], s_dc[kMeshThreads * 3];
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_gaussians(const float* __
         o_mean[3 * f0 + e] = s_mean[e];
         o_ls[3 * f0 + e] = s_ls[e];
     }
-    const int per = 3 * n_coef;                        // SH words per facet
+    constexpr int per = 3 * NC;                        // SH words per facet
     float* sh = o_sh + f0 * per;
     for (int e = threadIdx.x; e < per * nb; e += kMeshThreads) {
         const int fi = e / per, k = e - fi * per;
@@ -107,8 +108,11 @@ void launch_mesh_gaussians(const Launch& L, const float* v, int64_t n_v, const i
                            const float* col, float flatten, float opacity_logit, int n_coef, float* mean,
                            float* log_scale, float* quat, float* opac, float* sh, uint32_t* err) {
     if (n_f <= 0) return;
-    k_mesh_gaussians<<<(unsigned)((n_f + kMeshThreads - 1) / kMeshThreads), kMeshThreads, 0, L.stream>>>(v, n_v, f, n_f, col, flatten, opacity_logit,
-                                                                          n_coef, mean, log_scale, quat, opac, sh, err);
+    const unsigned blocks = (unsigned)((n_f + kMeshThreads - 1) / kMeshThreads);
+    auto* kern = n_coef == 1 ? k_mesh_gaussians<1> : n_coef == 4 ? k_mesh_gaussians<4>
+               : n_coef == 9 ? k_mesh_gaussians<9> : k_mesh_gaussians<16>;
+    kern<<<blocks, kMeshThreads, 0, L.stream>>>(v, n_v, f, n_f, col, flatten, opacity_logit, mean, log_scale, quat, opac,
+                                                sh, err);
     ++*L.launches;
 }
 
