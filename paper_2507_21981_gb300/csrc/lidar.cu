@@ -17,7 +17,7 @@
 //
 // Tracing: one thread per ray, one warp per packet of 32 rays.  A round collects, over every
 // node of the ray's env, the K nearest hits whose (t*, id) key follows the last key
-// composited, in a sorted register buffer; the packet's traversal is front to back and skips
+// composited, in a sorted buffer in shared memory; the packet's traversal is front to back and skips
 // boxes outside every lane's [t_last, t of its K-th hit].  The round's hits are composited;
 // the next round resumes after the last of them, until the transmittance drops below t_min or
 // fewer than K hits were left.
@@ -29,7 +29,7 @@ namespace dgs {
 namespace {
 
 constexpr int kLeaf = 8;             // Gaussians per leaf
-constexpr int kKbuf = 16;            // hits per round
+constexpr int kKbuf = 32;            // hits per round
 constexpr int kStack = 40;           // traversal stack (depth <= 31 levels + the far children)
 constexpr int kTraceThreads = 128;
 
@@ -172,10 +172,9 @@ __device__ __forceinline__ float slab_enter(const float4 lo, const float4 hi, co
     return fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fminf(z0, z1));
 }
 
-struct Kbuf {
-    uint64_t key[kKbuf];     // (bits of t*) << 32 | global id; ~0 = empty
-    float alpha[kKbuf];
-};
+// Per lane, in dynamic shared memory (lane-interleaved: entry i of thread x at [i][x]): the
+// round's sorted hits as bits of t*, global id and alpha; (t bits, id) is the 64-bit order key.
+constexpr size_t kKbufBytes = (size_t)3 * kKbuf * kTraceThreads * sizeof(uint32_t);
 
 // Warp = a packet of up to 32 rays (consecutive ray numbers: make them neighbours in the beam
 // pattern).  The packet walks each tree together on a warp-uniform stack: a box is descended
@@ -193,6 +192,10 @@ __global__ void __launch_bounds__(kTraceThreads) k_lidar_trace(const LidarTreeDe
                                                                uint32_t* __restrict__ err,
                                                                unsigned long long* __restrict__ next_ray) {
     __shared__ int s_stack[kTraceThreads / 32][kStack];
+    extern __shared__ uint32_t s_kbuf[];
+    uint32_t* const kt = s_kbuf + threadIdx.x;                      // entry i at kt[i * kTraceThreads]
+    uint32_t* const kg = kt + kKbuf * kTraceThreads;
+    float* const ka = reinterpret_cast<float*>(kg + kKbuf * kTraceThreads);
     const int lane = threadIdx.x & 31;
     int* stk = s_stack[threadIdx.x >> 5];
     for (;;) {
@@ -216,10 +219,8 @@ __global__ void __launch_bounds__(kTraceThreads) k_lidar_trace(const LidarTreeDe
         uint64_t last = 0;                                 // keys <= last are composited
         bool first = true, done = !valid;
         while (__any_sync(0xffffffffu, !done)) {
-            Kbuf kb;
-    #pragma unroll
-            for (int i = 0; i < kKbuf; ++i) { kb.key[i] = ~0ull; kb.alpha[i] = 0.f; }
             int cnt = 0;
+            uint64_t maxkey = ~0ull;                   // key of the last entry once the buffer is full
             const float t_lo = first ? LP.r_min : __uint_as_float((uint32_t)(last >> 32));
             float t_hi = LP.r_max;
             for (int slot = 0; slot < K; ++slot) {
@@ -281,20 +282,28 @@ __global__ void __launch_bounds__(kTraceThreads) k_lidar_trace(const LidarTreeDe
                                 const float q = fmaf(c0, c0, fmaf(c1, c1, c2 * c2)) * idd;
                                 if (!(q <= LP.q_max) || !(t >= LP.r_min) || !(t <= LP.r_max)) continue;
                                 const uint64_t key = ((uint64_t)__float_as_uint(t) << 32) | (uint32_t)(tr.gbase + g);
-                                if ((!first && key <= last) || key >= kb.key[kKbuf - 1]) continue;
+                                if ((!first && key <= last) || key >= maxkey) continue;
                                 const float alpha = fminf(LP.alpha_max, r0.w * fast_exp2(kHalfLog2e * q));
                                 if (alpha < LP.alpha_min) continue;
-                                uint64_t ck = key;
-                                float ca = alpha;
-    #pragma unroll
-                                for (int i = 0; i < kKbuf; ++i) {
-                                    if (ck < kb.key[i]) {
-                                        const uint64_t tk = kb.key[i]; kb.key[i] = ck; ck = tk;
-                                        const float ta = kb.alpha[i]; kb.alpha[i] = ca; ca = ta;
-                                    }
+                                // insert in order; a full buffer drops its last entry
+                                int i = cnt < kKbuf ? cnt : kKbuf - 1;
+                                while (i > 0) {
+                                    const uint32_t pt = kt[(i - 1) * kTraceThreads], pg = kg[(i - 1) * kTraceThreads];
+                                    if ((((uint64_t)pt << 32) | pg) < key) break;
+                                    kt[i * kTraceThreads] = pt;
+                                    kg[i * kTraceThreads] = pg;
+                                    ka[i * kTraceThreads] = ka[(i - 1) * kTraceThreads];
+                                    --i;
                                 }
+                                kt[i * kTraceThreads] = (uint32_t)(key >> 32);
+                                kg[i * kTraceThreads] = (uint32_t)key;
+                                ka[i * kTraceThreads] = alpha;
                                 if (cnt < kKbuf) ++cnt;
-                                if (cnt == kKbuf) t_hi = __uint_as_float((uint32_t)(kb.key[kKbuf - 1] >> 32));
+                                if (cnt == kKbuf) {
+                                    const uint32_t lt = kt[(kKbuf - 1) * kTraceThreads];
+                                    maxkey = ((uint64_t)lt << 32) | kg[(kKbuf - 1) * kTraceThreads];
+                                    t_hi = __uint_as_float(lt);
+                                }
                             }
                         } else {
                             const int64_t c = 2 * k;
@@ -331,21 +340,18 @@ __global__ void __launch_bounds__(kTraceThreads) k_lidar_trace(const LidarTreeDe
             }
             if (!done) {
                 // composite this round's hits in order
-    #pragma unroll
-                for (int i = 0; i < kKbuf; ++i) {
-                    if (i < cnt && !done) {
-                        const float a = kb.alpha[i];
-                        const float Tn = fmaf(-a, T, T);
-                        if (Tn < LP.t_min) {
-                            done = true;
-                        } else {
-                            D = fmaf(a * T, __uint_as_float((uint32_t)(kb.key[i] >> 32)), D);
-                            T = Tn;
-                        }
+                for (int i = 0; i < cnt && !done; ++i) {
+                    const float a = ka[i * kTraceThreads];
+                    const float Tn = fmaf(-a, T, T);
+                    if (Tn < LP.t_min) {
+                        done = true;
+                    } else {
+                        D = fmaf(a * T, __uint_as_float(kt[i * kTraceThreads]), D);
+                        T = Tn;
                     }
                 }
                 if (cnt < kKbuf) done = true;
-                last = kb.key[kKbuf - 1];
+                last = maxkey;
                 first = false;
             }
         }
@@ -409,13 +415,14 @@ void launch_lidar_trace(const Launch& L, const LidarTreeDev* trees, const LidarS
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_lidar_trace, kTraceThreads, 0);
+        cudaFuncSetAttribute(k_lidar_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKbufBytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_lidar_trace, kTraceThreads, kKbufBytes);
         resident = std::max(resident, 1);
     }
     const int64_t need = (n_rays + kTraceThreads - 1) / kTraceThreads;
     const unsigned blocks = (unsigned)std::min<int64_t>(need, (int64_t)resident * sms);
-    k_lidar_trace<<<blocks, kTraceThreads, 0, L.stream>>>(trees, slots, K, dirs, n_dirs, n_rays, LP, out_d, out_a, err,
-                                                          next_ray);
+    k_lidar_trace<<<blocks, kTraceThreads, kKbufBytes, L.stream>>>(trees, slots, K, dirs, n_dirs, n_rays, LP, out_d,
+                                                                   out_a, err, next_ray);
     ++*L.launches;
 }
 
