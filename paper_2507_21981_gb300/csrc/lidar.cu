@@ -190,7 +190,8 @@ __global__ void __launch_bounds__(kTraceThreads) k_lidar_trace(const LidarTreeDe
                                                                int64_t n_rays, LidarParams LP,
                                                                float* __restrict__ out_d, float* __restrict__ out_a,
                                                                uint32_t* __restrict__ err,
-                                                               unsigned long long* __restrict__ next_ray) {
+                                                               unsigned long long* __restrict__ next_ray,
+                                                               unsigned long long n_packets, unsigned long long scramble) {
     __shared__ int s_stack[kTraceThreads / 32][kStack];
     extern __shared__ uint32_t s_kbuf[];
     uint32_t* const kt = s_kbuf + threadIdx.x;                      // entry i at kt[i * kTraceThreads]
@@ -199,10 +200,13 @@ __global__ void __launch_bounds__(kTraceThreads) k_lidar_trace(const LidarTreeDe
     const int lane = threadIdx.x & 31;
     int* stk = s_stack[threadIdx.x >> 5];
     for (;;) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(next_ray, 32ull);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= (unsigned long long)n_rays) break;
+        unsigned long long pk = 0;
+        if (lane == 0) pk = atomicAdd(next_ray, 1ull);
+        pk = __shfl_sync(0xffffffffu, pk, 0);
+        if (pk >= n_packets) break;
+        // packets in a scrambled order (p -> p * scramble mod n_packets, a bijection): costly
+        // packets that are neighbours in ray order do not all start last
+        const unsigned long long base = (unsigned long long)((unsigned __int128)pk * scramble % n_packets) * 32ull;
         const int64_t ray = (int64_t)base + lane;
         const bool valid = ray < n_rays;
         int s = 0, j = 0;
@@ -421,8 +425,13 @@ void launch_lidar_trace(const Launch& L, const LidarTreeDev* trees, const LidarS
     }
     const int64_t need = (n_rays + kTraceThreads - 1) / kTraceThreads;
     const unsigned blocks = (unsigned)std::min<int64_t>(need, (int64_t)resident * sms);
+    const unsigned long long n_packets = (unsigned long long)(n_rays + 31) / 32;
+    unsigned long long a = 0x9E3779B97F4A7C15ull % n_packets;          // a multiplier coprime with n_packets
+    auto gcd = [](unsigned long long x, unsigned long long y) { while (y) { const auto t = x % y; x = y; y = t; } return x; };
+    if (a == 0) a = 1;
+    while (gcd(a, n_packets) != 1) ++a;
     k_lidar_trace<<<blocks, kTraceThreads, kKbufBytes, L.stream>>>(trees, slots, K, dirs, n_dirs, n_rays, LP, out_d,
-                                                                   out_a, err, next_ray);
+                                                                   out_a, err, next_ray, n_packets, a);
     ++*L.launches;
 }
 
