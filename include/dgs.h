@@ -403,7 +403,8 @@ int dgs_lidar_build(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, void* 
  *   sensors[n_sensors]            HOST
  *   dirs[n_dirs*3]                DEVICE FP32 sensor-frame directions (non-zero)
  *   r_min, r_max                  range window, 0 <= r_min < r_max, finite
- *   out_d, out_a                  DEVICE FP32 [n_sensors*n_dirs], sensor-major
+ *   out_d, out_a                  DEVICE FP32 [n_sensors*n_dirs], sensor-major (sensors, dirs and the
+ *                                 outputs may be NULL when n_sensors = 0: nothing is traced)
  * Work is queued on `stream`; the call synchronises it before returning (device-side pose
  * validation is reported as DGS_ERR_INVALID_ARG).
  */

@@ -1461,9 +1461,9 @@ int dgs_lidar_trace(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const 
             return fail(ctx, DGS_ERR_INVALID_ARG, "node " + std::to_string(k) + " differs from the one built (call dgs_lidar_build)");
     }
     if (n_envs < 1 || max_nodes < 1) return fail(ctx, DGS_ERR_INVALID_ARG, "n_envs and max_nodes must be >= 1");
-    if (!env_node_ids || !node_poses || !sensors || !dirs || !out_d || !out_a)
-        return fail(ctx, DGS_ERR_INVALID_ARG, "null pointer argument");
     if (n_sensors < 0 || n_dirs < 1) return fail(ctx, DGS_ERR_INVALID_ARG, "n_sensors >= 0 and n_dirs >= 1 required");
+    if (!env_node_ids || !node_poses || (n_sensors > 0 && (!sensors || !dirs || !out_d || !out_a)))
+        return fail(ctx, DGS_ERR_INVALID_ARG, "null pointer argument");
     if (!(r_min >= 0.f) || !(r_max > r_min) || !finite(r_max))
         return fail(ctx, DGS_ERR_INVALID_ARG, "range window: need 0 <= r_min < r_max, finite");
     const int E = n_envs, K = max_nodes;

@@ -223,6 +223,26 @@ def test_fused_render_matches_oracle_render_and_randomisation():
     assert max(x["median_err"] for x in rep) < 1e-4
 
 
+@pytest.mark.gpu
+def test_full_batch_fused_randomisation_sampled_views():
+    """The benchmark batch (64 envs x 2 cameras 640x480, 1.08M Gaussians per env, Z-ordered) as
+    graph replays with the randomisation fused (8-frame 1280x720 overlay clip), as bench.py times
+    it; two sampled views against oracle render + oracle randomisation."""
+    from paper_2507_21981_gb300.render import DeviceScene, Renderer
+    sc = S.config2(seed=1)
+    ds = DeviceScene(sc, device="cuda:0", spatial_order=True)
+    ov = S.overlay_frames(1, n_frames=8, width=1280, height=720)
+    prm = S.augment_params(1, ds.n_views, 8, 1280, 720)
+    prm[[5, 77]]["overlay_beta"] = 0.35                   # both sampled views blend the overlay
+    r = Renderer(mode="graph")
+    r.set_augment(prm, torch.as_tensor(ov).cuda())
+    for _ in range(2):
+        rgb = r.render(ds)[0]
+    rgb = rgb.cpu().numpy()
+    r.close()
+    _compare_to_oracle(ds.scene, ds, rgb, prm, ov, [5, 77])
+
+
 def test_oracle_bound_rejects_a_wrong_crop_and_a_wrong_order():
     """CPU only: the per-pixel bound used above would catch plausible mistakes.  The mistakes
     are planted in copies of the oracle's own steps on a synthetic image, never on the GPU."""

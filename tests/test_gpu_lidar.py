@@ -139,6 +139,8 @@ def test_edge_cases():
     assert (ref.a[2] > 0.1).any()                             # the sensor inside a Gaussian sees it
     d2, a2 = _trace(ds, se, sp, dirs, r_min=50.0, r_max=60.0, build=False, r=r)
     assert np.all(a2 == 0) and np.all(d2 == 0)
+    d3, a3 = _trace(ds, se[:0], sp[:0], dirs, build=False, r=r)          # no sensors: nothing to do
+    assert d3.size == 0 and a3.size == 0
     r.close()
 
 
