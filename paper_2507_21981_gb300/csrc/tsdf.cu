@@ -5,8 +5,8 @@
 // A pre-pass writes every pixel's normalised depth d = D / A (NaN where A < min_alpha) into a
 // packed array.  Then one thread per voxel, x fastest (coalesced field reads and writes); each
 // thread loops over the views in order: project the voxel centre, read d at the pixel holding
-// the projection, sdf = d - z, skip when
-// sdf < -trunc, f = min(1, sdf / trunc), F <- (W F + f) / (W + 1), W <- min(W + 1, max_weight).
+// the projection, sdf = d - z, skip when sdf < -trunc, f = min(1, sdf / trunc),
+// F <- (W F + f) / (W + 1), W <- min(W + 1, max_weight).
 // The field is read and written once per call whatever the number of views, so a call with
 // many views is bound by the per-view arithmetic and the depth gathers (served by L2).
 #include "dgs_internal.cuh"
