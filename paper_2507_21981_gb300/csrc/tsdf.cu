@@ -34,9 +34,23 @@ __global__ void __launch_bounds__(kTsdfThreads) k_tsdf_depth(const TsdfView* __r
     dn[q] = a >= min_alpha ? __fdividef(depth[p], a) : __int_as_float(0x7fc00000);
 }
 
+// The block first copies the view table (up to kSmemViews views) into shared memory, so that
+// the per-view camera fields are shared-memory broadcasts rather than cached global loads.
+constexpr int kSmemViews = 64;
+
 __global__ void __launch_bounds__(kTsdfThreads) k_tsdf(float* __restrict__ F, float* __restrict__ Wt, int nx, int ny,
-                                                       int64_t n_vox, TsdfParams TP, const TsdfView* __restrict__ views,
+                                                       int64_t n_vox, TsdfParams TP, const TsdfView* __restrict__ gviews,
                                                        int V, const float* __restrict__ dn) {
+    __shared__ TsdfView s_views[kSmemViews];
+    const bool in_smem = V <= kSmemViews;
+    if (in_smem) {
+        const int words = V * (int)(sizeof(TsdfView) / 4);
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(gviews);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(s_views);
+        for (int w = threadIdx.x; w < words; w += kTsdfThreads) dst[w] = src[w];
+        __syncthreads();
+    }
+    const TsdfView* __restrict__ views = in_smem ? s_views : gviews;
     const int64_t idx = (int64_t)blockIdx.x * kTsdfThreads + threadIdx.x;
     if (idx >= n_vox) return;
     const int i = (int)(idx % nx);
