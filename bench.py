@@ -478,6 +478,45 @@ def cpu_baseline(views=1, seed=1):
             "sample": f"{views} view(s) of the workload, 640x480, full 1.08M-Gaussian scene, FP64, {dt:.1f} s"}
 
 
+def oracle_timings():
+    """The FP64 oracle timed per configuration on the host cores (all threads unless stated):
+    config 1 every view, configs 3 and 5 on seeded sampled views (2 for config 5: its 3.3M
+    Gaussians per view make each view slow), config 4 forward + backward of its one view, and
+    one config-2 view on a single thread."""
+    import numpy as np
+    import oracle
+    from paper_2507_21981_gb300 import scenes
+    res = {"cores": os.cpu_count()}
+    rng = np.random.default_rng(2)
+
+    def views(sc, idx, opts=None):
+        pk = oracle.oracle._Packed(sc)
+        t0 = time.perf_counter()
+        px = 0
+        for v in idx:
+            e, c = sc.views[int(v)]
+            px += oracle.render_view(sc, e, c, opts or oracle.OracleOptions(), pk).depth.size
+        dt = time.perf_counter() - t0
+        return {"mpix_s": px / dt / 1e6, "views": [int(v) for v in idx], "seconds": dt}
+    sc = scenes.config1(seed=1)
+    res["config1"] = views(sc, range(sc.n_views))
+    sc = scenes.config3(seed=1)
+    res["config3"] = views(sc, rng.choice(sc.n_views, 4, replace=False))
+    sc = scenes.config5(seed=1)
+    res["config5"] = views(sc, rng.choice(sc.n_views, 2, replace=False))
+    sc = scenes.config2(seed=1)
+    res["config2_single_thread"] = views(sc, [0], oracle.OracleOptions(nthreads=1))
+    sc = scenes.config4(seed=1)
+    pk = oracle.oracle._Packed(sc)
+    g = np.random.default_rng(0).normal(size=(800, 800, 3))
+    gd = np.random.default_rng(1).normal(size=(800, 800))
+    t0 = time.perf_counter()
+    oracle.render_view(sc, 0, 0, oracle.OracleOptions(), pk)
+    oracle.backward_view(sc, 0, 0, g, gd, oracle.OracleOptions(), pk)
+    res["config4_fwd_bwd_ms"] = (time.perf_counter() - t0) * 1e3
+    return res
+
+
 def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
@@ -509,7 +548,7 @@ def main():
     ap.add_argument("--only-batched", action="store_true",
                     help="time the batched render only (no e2e, plain or CPU legs): small profiling runs")
     ap.add_argument("--no-extra", action="store_true", help="skip the ragged and precision workloads")
-    ap.add_argument("--only-leg", choices=["augment", "lidar", "mesh", "tsdf"], default=None,
+    ap.add_argument("--only-leg", choices=["augment", "lidar", "mesh", "tsdf", "fwd_bwd"], default=None,
                     help="run one side workload alone on --envs envs and print its JSON (profiling runs)")
     ap.add_argument("--views-per-group", type=int, default=0,
                     help="views per group of the batched sequence (0 = as few groups as the sort allows)")
@@ -538,6 +577,8 @@ def main():
             res = lidar_leg(dev, ds, args.warmup, args.steps)
         elif args.only_leg == "mesh":
             res = mesh_leg(dev, args.warmup, args.steps)
+        elif args.only_leg == "fwd_bwd":
+            res = fwd_bwd_500k(dev, args.warmup, args.steps)
         else:
             res = tsdf_leg(dev, sc, args.warmup, args.steps)
         if rank == 0:
@@ -757,6 +798,8 @@ def main():
     line.update(extra)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(views=16)
+        if world == 1:
+            line["oracle_timing"] = oracle_timings()
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
