@@ -229,3 +229,32 @@ def test_tolerance_is_tight_on_a_room():
     assert hit.mean() > 0.25           # a sparse room (60k Gaussians): many rays pass through
     # thin surface Gaussians (1.8 mm normal axis) make FP32 positions at metres the main error
     assert np.median(r.tol_a[hit]) < 3e-3 and np.median(r.tol_d[hit] / r.d[hit]) < 3e-3
+
+
+def test_tolerance_rejects_plausible_mistakes():
+    """The per-ray tolerance the GPU is held to is tight enough to catch plausible mistakes:
+    ignoring the node poses, Gaussians 5 % too large, and a sensor 1 mm off along its beams each
+    move D or A beyond twice the tolerance on many rays of a posed multi-node scene."""
+    rng = np.random.default_rng(8)
+    nodes = [_rand_node(rng, 400, np.array([2.0, 0, 0]), 0.5), _rand_node(rng, 200, np.zeros(3), 0.2)]
+    P1 = S.random_pose(rng, 0.3)
+    P1[:, 3] += [1.8, 0.3, 0.0]
+    poses = [np.eye(3, 4), P1]
+    dirs = S.lidar_pattern(16, 64, -25, 25, az0_deg=-40, az_span_deg=80).astype(np.float64)
+    sensor = np.eye(3, 4)
+    ref = _trace(_scene(nodes, poses), sensor, dirs)
+    hit = ref.a > 0.05
+    assert hit.sum() > 100
+
+    def frac_beyond(other):
+        bad = (np.abs(other.a - ref.a) > 2 * ref.tol_a + 1e-6) | (np.abs(other.d - ref.d) > 2 * ref.tol_d + 1e-6)
+        return float(bad[hit].mean())
+    no_pose = _trace(_scene(nodes, [np.eye(3, 4), np.eye(3, 4)]), sensor, dirs)
+    big = [_node(nd.mean, nd.log_scale + np.float32(np.log(1.05)), nd.quat, nd.opacity_logit) for nd in nodes]
+    bigger = _trace(_scene(big, poses), sensor, dirs)
+    moved = sensor.copy()
+    moved[:, 3] = [0.001, 0.0, 0.0]
+    shifted = _trace(_scene(nodes, poses), moved, dirs)
+    assert frac_beyond(no_pose) > 0.8           # measured: 100 %, 99.6 % and 99.4 % of hit rays
+    assert frac_beyond(bigger) > 0.8
+    assert frac_beyond(shifted) > 0.8
