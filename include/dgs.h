@@ -406,7 +406,9 @@ int dgs_lidar_build(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, void* 
  *   out_d, out_a                  DEVICE FP32 [n_sensors*n_dirs], sensor-major (sensors, dirs and the
  *                                 outputs may be NULL when n_sensors = 0: nothing is traced)
  * Work is queued on `stream`; the call synchronises it before returning (device-side pose
- * validation is reported as DGS_ERR_INVALID_ARG).
+ * validation is reported as DGS_ERR_INVALID_ARG).  Rays (s, j) .. (s, j + 31) are traced together
+ * as one packet: order dirs so that every 32 consecutive directions are neighbours (e.g. tiles of
+ * 4 channels x 8 azimuths) — the result does not depend on the order, the speed does.
  */
 int dgs_lidar_trace(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes,
                     const int32_t* env_node_ids, int32_t n_envs, int32_t max_nodes, const float* node_poses,
