@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(kCountWarps * 32) k_count_plain(const NodeDesc
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kEmitWarps * 32, 6) k_emit_batched(const NodeDesc* __restrict__ nodes, int n_nodes,
+__global__ void __launch_bounds__(kEmitWarps * 32, 5) k_emit_batched(const NodeDesc* __restrict__ nodes, int n_nodes,
         const ViewDesc* __restrict__ views, const VNode* __restrict__ vnodes, int K, const NodeView* __restrict__ nv,
         const int32_t* __restrict__ nv_off, int n_chunks, Params P, int v0, int v1, const uint2* __restrict__ counts,
         const uint32_t* __restrict__ inst_off, uint32_t inst_base, EmitOut out) {
@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 6) k_emit_batched(const NodeD
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kEmitWarps * 32, 6) k_emit_plain(const NodeDesc* __restrict__ nodes,
+__global__ void __launch_bounds__(kEmitWarps * 32, 5) k_emit_plain(const NodeDesc* __restrict__ nodes,
         const ViewDesc* __restrict__ views, const VNode* __restrict__ vnodes, int K, Params P, int v,
         const int32_t* __restrict__ pmap, int n_view_chunks, const uint2* __restrict__ counts,
         const uint32_t* __restrict__ inst_off, uint32_t inst_base, EmitOut out) {
