@@ -292,3 +292,27 @@ def test_tsdf_validates_on_host(lib):
         assert call(cams=bad_cam) == D.DGS_ERR_INVALID_ARG
     finally:
         lib.dgs_context_destroy(ctx)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No silent fallback: without the built library the binding raises instead of computing."""
+    with pytest.raises(RuntimeError, match="libdgs.so not found"):
+        D.load(str(tmp_path / "libdgs.so"))
+
+
+def test_product_never_reaches_the_oracle():
+    """The library and its binding neither import, link nor compile anything under oracle/, and
+    the oracle imports nothing from the product (the two share only the seeded input
+    generators, which tests pass to both)."""
+    pkg = os.path.join(ROOT, "paper_2507_21981_gb300")
+    use = re.compile(r"^\s*(?:import\s+oracle\b|from\s+oracle\b|#\s*include\s*[<\"][^>\"]*oracle)", re.M)
+    for d, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                src = open(os.path.join(d, f)).read()
+                assert not use.search(src), os.path.join(d, f)
+    assert all("oracle" not in s for s in B.SOURCES)
+    back = re.compile(r"^\s*(?:import\s+paper_2507_21981_gb300|from\s+paper_2507_21981_gb300)", re.M)
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".cpp", ".h")):
+            assert not back.search(open(os.path.join(ROOT, "oracle", f)).read()), f
