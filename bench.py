@@ -67,20 +67,31 @@ def max_over_ranks(x: float, world: int, device="cpu") -> float:
 
 
 class ClockSampler:
-    """Samples nvidia-smi clocks and throttle reasons in the background during the timed region."""
+    """Samples nvidia-smi clocks and throttle reasons every `period_ms` in the background.
 
-    def __init__(self, gpu_index: int):
+    Start it before the warm-up (nvidia-smi needs a moment to start) and bracket each timed
+    region with mark_start() / mark_end(): the summary keeps the samples whose own nvidia-smi
+    timestamps fall inside those windows.  If none can be placed (a timestamp that does not
+    parse), it keeps every sample taken while the sampler ran and says so in `window`."""
+
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 100):
         self.gpu = gpu_index
+        self.period_ms = period_ms
         self.proc = None
         self.lines = []
+        self.windows = []
+        self._t0 = None
 
     def __enter__(self):
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-             "clocks_event_reasons.sw_power_cap")
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.reader = threading.Thread(target=self._read, daemon=True)
             self.reader.start()
         except (OSError, ValueError):
@@ -91,6 +102,14 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def mark_start(self):
+        self._t0 = time.time()
+
+    def mark_end(self):
+        if self._t0 is not None:
+            self.windows.append((self._t0, time.time()))
+            self._t0 = None
+
     def __exit__(self, *a):
         if self.proc:
             self.proc.terminate()
@@ -98,23 +117,34 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+            self.reader.join(timeout=5)
+
+    @staticmethod
+    def _when(stamp: str):
+        import datetime
+        try:
+            return datetime.datetime.strptime(stamp.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1])); mx = float(f[2])
+                sm, mx = float(f[2]), float(f[3])
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+            rows.append((self._when(f[0]), sm, mx, {n for n, v in zip(self.REASONS, f[6:10]) if v.lower() == "active"}))
+        inside = [r for r in rows if r[0] is not None and any(a <= r[0] <= b for a, b in self.windows)]
+        window = "timed region"
+        if not inside:
+            inside, window = rows, "whole sampling (no sample placed in the timed region)"
+        sm = [r[1] for r in inside]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": inside[-1][2] if inside else None,
+                "reasons": sorted(set().union(*(r[3] for r in inside))), "samples": len(sm), "window": window}
 
 
 def _peaks():
@@ -603,19 +633,21 @@ def main():
     # headline: the default sequence (a large batch runs as two pipelined view groups), no
     # per-kernel events
     rb = Renderer(mode="batched", tile=tile, views_per_group=vpg)
-    for _ in range(args.warmup):
-        rb.render(ds, out=out)
-    barrier()
     launches = 0
-    with ClockSampler(local) as clk:
+    with ClockSampler(local) as clk:            # started before the warm-up: nvidia-smi takes a moment
+        for _ in range(args.warmup):
+            rb.render(ds, out=out)
+        barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
+        clk.mark_start()
         ev0.record(stream)
         for _ in range(args.steps):
             rb.render(ds, out=out)
             launches += rb.launches()
         ev1.record(stream)
         barrier()
+        clk.mark_end()
     ms = ev0.elapsed_time(ev1) / args.steps
     groups = rb.stats()["n_groups"]
     # per-kernel breakdown: the same batch as one view group (kernels not overlapped), CUDA
