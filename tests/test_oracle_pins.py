@@ -319,3 +319,78 @@ def test_empty_node_and_empty_env_render_background():
     sc.env_node_ids[0, :] = -1
     r = O.render_view(sc, 0, 0, opts(bg=(0.5, 0.5, 0.5)))
     assert r.instances == 0 and np.all(r.rgb == 0.5) and np.all(r.depth == 0)
+
+
+# --------------------------------------------------------------------------- FP32-ambiguous decisions
+# The method's cutoffs (Sec. III-A compositing: alpha below 1/255 skipped, stop once T < 1e-4,
+# the 3-sigma ellipse) are thresholds an FP32 evaluation may land on either side of.  Each case
+# places one decision exactly on its threshold in a hand-built scene whose two outcomes have
+# closed forms; the oracle must flag that pixel and return both branches.
+def _branches(r, y, x):
+    """Every branch's (r, g, b, d, a) at pixel (y, x): the primary result, then the alternatives."""
+    p = y * r.rgb.shape[1] + x
+    prim = np.r_[r.rgb[y, x], r.depth[y, x], r.alpha[y, x]]
+    return np.vstack([prim[None], r.alternatives(p)])
+
+
+def _same_branches(got, want, tol=1e-12):
+    assert len(got) == len(want), (got, want)
+    for w in want:
+        assert np.abs(got - np.asarray(w)).max(axis=1).min() <= tol, (got, want)
+
+
+C_FG, C_BG = np.array([0.9, 0.3, 0.1]), np.array([0.2, 0.4, 0.6])
+
+
+def _alpha_tie_scene():
+    # opacity exactly alpha_min; the mean projects onto the centre of pixel (8, 8) (q = 0)
+    p = 1 / 255
+    nd = U.node([[0, 0, 4.0]], log_scales=np.full((1, 3), math.log(0.08)), logits=[math.log(p / (1 - p))],
+                sh=U.colour_sh([C_FG]), dtype=np.float64)
+    return U.single_view([nd], f=100.0, W=17, H=17, cx=8.5, cy=8.5), p, 4.0
+
+
+def test_alpha_min_tie_returns_composited_and_skipped_branches():
+    sc, p, z = _alpha_tie_scene()
+    r = O.render_view(sc, 0, 0, opts(bg=tuple(C_BG)))
+    assert r.ambiguous_by_kind["alpha"] == 1 and r.ambiguous_pixels == 1 and r.n_alt[8, 8] == 1
+    _same_branches(_branches(r, 8, 8), [np.r_[p * C_FG + (1 - p) * C_BG, p * z, p], np.r_[C_BG, 0, 0]])
+
+
+def test_unexplored_flip_widens_the_tolerance_over_the_other_branch():
+    sc, p, z = _alpha_tie_scene()
+    r = O.render_view(sc, 0, 0, opts(bg=tuple(C_BG), max_flips=0))
+    assert r.n_alt[8, 8] == 0 and r.ambiguous_pixels == 1
+    comp, skip = np.r_[p * C_FG + (1 - p) * C_BG, p * z], np.r_[C_BG, 0.0]
+    other = skip if abs(r.alpha[8, 8]) < 1e-15 else comp                 # the branch not taken
+    here = np.r_[r.rgb[8, 8], r.depth[8, 8]]
+    assert r.tol_rgb[8, 8] >= np.abs(other[:3] - here[:3]).max() - 1e-15
+    assert r.tol_d[8, 8] >= abs(other[3] - here[3]) - 1e-15
+
+
+def test_transmittance_tie_returns_stop_and_composite_branches():
+    # two Gaussians clamped at alpha 0.99 on the centre pixel: T = 0.01, then 0.01 * 0.01 = t_min
+    c2 = np.array([0.1, 0.8, 0.5])
+    nd = U.node([[0, 0, 3.0], [0, 0, 4.0]], log_scales=np.full((2, 3), math.log(0.3)), logits=[10.0, 10.0],
+                sh=U.colour_sh([C_FG, c2]), dtype=np.float64)
+    sc = U.single_view([nd], W=17, H=17, cx=8.5, cy=8.5)
+    r = O.render_view(sc, 0, 0, opts(bg=tuple(C_BG)))
+    assert r.ambiguous_by_kind["transmittance"] >= 1 and r.n_alt[8, 8] == 1
+    stop = np.r_[0.99 * C_FG + 0.01 * C_BG, 0.99 * 3.0, 0.99]
+    comp = np.r_[0.99 * C_FG + 0.0099 * c2 + 1e-4 * C_BG, 0.99 * 3.0 + 0.0099 * 4.0, 1 - 1e-4]
+    _same_branches(_branches(r, 8, 8), [stop, comp])
+
+
+def test_ellipse_boundary_tie_returns_inside_and_outside_branches():
+    # f sigma / z = 1 px and no low-pass: q = (distance in px)^2, so the four pixels 3 px from
+    # the centre lie on q_max = 9, where alpha = sigmoid(8) exp(-4.5) is well above alpha_min
+    z = 4.0
+    nd = U.node([[0, 0, z]], log_scales=np.full((1, 3), math.log(0.04)), logits=[8.0], sh=U.colour_sh([C_FG]),
+                dtype=np.float64)
+    sc = U.single_view([nd], f=100.0, W=17, H=17, cx=8.5, cy=8.5)
+    r = O.render_view(sc, 0, 0, opts(lowpass=0.0, bg=tuple(C_BG)))
+    assert r.ambiguous_by_kind["ellipse"] == 4 and r.ambiguous_pixels == 4
+    a9 = math.exp(-4.5) / (1 + math.exp(-8.0))
+    for y, x in [(8, 11), (8, 5), (11, 8), (5, 8)]:
+        assert r.n_alt[y, x] == 1
+        _same_branches(_branches(r, y, x), [np.r_[a9 * C_FG + (1 - a9) * C_BG, a9 * z, a9], np.r_[C_BG, 0, 0]])
