@@ -258,3 +258,63 @@ def test_tolerance_rejects_plausible_mistakes():
     assert frac_beyond(no_pose) > 0.8           # measured: 100 %, 99.6 % and 99.4 % of hit rays
     assert frac_beyond(bigger) > 0.8
     assert frac_beyond(shifted) > 0.8
+
+
+# The FP32 tracer may take either side of a decision that lies on its threshold.  Each case
+# puts one decision exactly there, on a ray along +x from the origin through isotropic
+# Gaussians (s = 0.1, identity rotation), and checks that the oracle flags it and that both
+# closed-form outcomes lie within the tolerance it returns around its primary result.
+def _tie(mus, logits, opts=LO):
+    n = len(mus)
+    sc = _scene([_node(mus, [[math.log(0.1)] * 3] * n, [[1, 0, 0, 0]] * n, logits)])
+    return _trace(sc, np.eye(3, 4), [[1.0, 0, 0]], opts)
+
+
+def _covers(r, outcomes):
+    assert r.n_amb[0, 0] >= 1
+    for a, d in outcomes:
+        assert abs(a - r.a[0, 0]) <= r.tol_a[0, 0] + 1e-12, (a, r.a[0, 0], r.tol_a[0, 0])
+        assert abs(d - r.d[0, 0]) <= r.tol_d[0, 0] + 1e-12, (d, r.d[0, 0], r.tol_d[0, 0])
+
+
+def _f32(x):
+    return float(np.float32(x))
+
+
+def _alpha(y, logit):
+    """Closed form on the stored FP32 inputs: opacity sigmoid(logit) times exp(-q*/2), q* the
+    squared perpendicular distance y over s."""
+    s = math.exp(_f32(math.log(0.1)))
+    return math.exp(-0.5 * (_f32(y) / s) ** 2) / (1 + math.exp(-_f32(logit)))
+
+
+def test_tie_on_the_three_sigma_ellipsoid():
+    a9 = _alpha(0.3, _logit(0.9))             # perpendicular distance 3 s: q* = 9
+    _covers(_tie([[2.0, 0.3, 0.0]], [_logit(0.9)]), [(0.0, 0.0), (a9, a9 * 2.0)])
+
+
+def test_tie_on_the_far_end_of_the_range_window():
+    a = _alpha(0.0, _logit(0.9))
+    _covers(_tie([[30.0, 0.0, 0.0]], [_logit(0.9)]), [(0.0, 0.0), (a, a * 30.0)])
+
+
+def test_tie_on_alpha_min():
+    a = _alpha(0.0, _logit(1 / 255))           # 1/255 up to the FP32 rounding of the logit
+    assert a == pytest.approx(1 / 255, rel=1e-6)
+    _covers(_tie([[2.0, 0.0, 0.0]], [_logit(1 / 255)]), [(0.0, 0.0), (a, a * 2.0)])
+
+
+def test_tie_on_the_termination_threshold():
+    # two hits clamped at alpha 0.99: T = 0.01, then 0.01 * 0.01 = t_min
+    r = _tie([[2.0, 0.0, 0.0], [3.0, 0.0, 0.0]], [10.0, 10.0])
+    _covers(r, [(0.99, 0.99 * 2.0), (1 - 1e-4, 0.99 * 2.0 + 0.0099 * 3.0)])
+
+
+def test_decisions_away_from_thresholds_are_not_flagged():
+    """Control for the ties above: 2.5 s off the ray, alpha well above alpha_min, well inside
+    the window and far from t_min, nothing is flagged and the tolerance is far below the hit's
+    own weight."""
+    a = 0.9 * math.exp(-0.5 * 2.5 ** 2)
+    r = _tie([[2.0, 0.25, 0.0]], [_logit(0.9)])
+    assert r.n_amb[0, 0] == 0
+    assert r.a[0, 0] == pytest.approx(a, rel=1e-5) and r.tol_a[0, 0] < 1e-3 * a and r.tol_d[0, 0] < 1e-3 * a * 2.0
