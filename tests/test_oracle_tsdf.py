@@ -1,8 +1,9 @@
 """Pins of the TSDF fusion oracle (oracle/tsdf.py) against facts that do not come from it: a
 head-on plane in closed form (projective distance, truncation, frustum), the normalisation of
 the renderer's unnormalised depth by its coverage, the running average over views and the
-weight cap, and a sphere seen from many views whose fused field changes sign at the sphere's
-radius.  No GPU is needed.
+weight cap, a sphere seen from many views whose fused field changes sign at the sphere's
+radius, and single voxels placed exactly on the thresholds of the fusion's integer decisions.
+No GPU is needed.
 """
 import numpy as np
 
@@ -69,3 +70,24 @@ def test_sphere_zero_crossing():
     inside = seen & (r < R - 1.5 * vox) & (r > R - 0.03)
     assert (F[outside] > 0).mean() > 0.99 and (F[inside] < 0).mean() > 0.99
     assert not seen[r < R - 0.05].any()                  # deep inside: behind every surface by > trunc
+
+
+def _one_voxel(centre, depth=1.0, trunc=0.25, vox=0.02):
+    origin = np.asarray(centre, np.float64) - vox / 2
+    return T.integrate(np.zeros((1, 1, 1)), np.zeros((1, 1, 1)), origin, vox, trunc, 100.0, 0.5, [CAM],
+                       [np.full((32, 32), depth)], [np.ones((32, 32))])
+
+
+def test_decisions_on_their_thresholds_are_flagged():
+    """One voxel per case puts one integer decision of the fusion exactly on its threshold (the
+    camera has f = 40, c = 16, so u = 40 x / z + 16): the oracle must flag it, since an FP32
+    evaluation may take either side; an off-threshold control is not flagged and is updated in
+    closed form (sdf = 1 - 1.2 = -0.2, f = -0.8, weight 1)."""
+    for what, centre in [("pixel edge, u = 20", [0.1, 0.0125, 1.0]),
+                         ("image border, u = 0", [-0.4, 0.0125, 1.0]),
+                         ("sdf = -trunc", [0.015625, 0.015625, 1.25]),
+                         ("camera plane, z = 0", [0.1, 0.0, 0.0])]:
+        assert _one_voxel(centre)[2].all(), what
+    F, W, amb = _one_voxel([0.015, 0.015, 1.2])
+    assert not amb.any()
+    assert W[0, 0, 0] == 1.0 and abs(F[0, 0, 0] + 0.8) < 1e-12
