@@ -2,8 +2,9 @@
 closed form of an isotropic Gaussian on a ray, the peak of an anisotropic one found by
 numerical minimisation (covariance from scipy's rotations), compositing closed forms with
 termination, the 3-sigma and range windows, the node pose against pre-transformed Gaussians,
-rigid-motion invariance, and a brute force on a small random scene that locates each peak by
-sampling q(t) along the ray.  No GPU is needed.
+rigid-motion invariance, a brute force on a small random scene that locates each peak by
+sampling q(t) along the ray, and exact ties on the decision thresholds whose two closed-form
+outcomes must both lie inside the tolerance the oracle returns.  No GPU is needed.
 """
 import math
 

@@ -3,7 +3,8 @@
 Each test states what fixes the expected value: a library routine (scipy's complex spherical
 harmonics, scipy's rotation matrices), a closed form of the EWA projection of an isotropic
 Gaussian, compositing invariants (weights + transmittance = 1), rigid-motion invariance,
-brute force, or finite differences.  No GPU is needed.
+brute force, finite differences, or the two closed-form outcomes of a decision placed exactly
+on its threshold.  No GPU is needed.
 """
 import math
 
