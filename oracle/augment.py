@@ -29,9 +29,9 @@ FIELDS = ("hue_shift", "sat_scale", "val_scale", "gamma", "overlay_beta", "overl
 
 
 def rgb_to_hsv(c: np.ndarray) -> np.ndarray:
-    """Hexcone model: V = max, C = max - min, S = C / V (0 for V = 0), H from the sector of
-    the largest channel (red checked first, then green), in turns in [0, 1); H = 0 for C = 0.
-    c: [..., 3] -> [..., 3] (H, S, V)."""
+    """Sec. IV (HSV colour jitter), RGB -> HSV.  Hexcone model: V = max, C = max - min, S = C / V (0
+    for V = 0), H from the sector of the largest channel (red checked first, then green), in turns
+    in [0, 1); H = 0 for C = 0. c: [..., 3] -> [..., 3] (H, S, V)."""
     c = np.asarray(c, dtype=np.float64)
     r, g, b = c[..., 0], c[..., 1], c[..., 2]
     v = np.maximum(np.maximum(r, g), b)
@@ -49,8 +49,8 @@ def rgb_to_hsv(c: np.ndarray) -> np.ndarray:
 
 
 def hsv_to_rgb(hsv: np.ndarray) -> np.ndarray:
-    """Inverse hexcone map: sector i = floor(6H) mod 6, fraction f = 6H - floor(6H),
-    p = V(1 - S), q = V(1 - S f), t = V(1 - S(1 - f)), and per sector
+    """Sec. IV (HSV colour jitter), HSV -> RGB.  Inverse hexcone map: sector i = floor(6H) mod 6,
+    fraction f = 6H - floor(6H), p = V(1 - S), q = V(1 - S f), t = V(1 - S(1 - f)), and per sector
     (V,t,p) (q,V,p) (p,V,t) (p,q,V) (t,p,V) (V,p,q).  hsv: [..., 3] -> [..., 3]."""
     hsv = np.asarray(hsv, dtype=np.float64)
     h, s, v = hsv[..., 0], hsv[..., 1], hsv[..., 2]
@@ -72,8 +72,9 @@ def hsv_to_rgb(hsv: np.ndarray) -> np.ndarray:
 
 
 def overlay_crop(overlay: np.ndarray, frame: int, ox: int, oy: int, w: int, h: int) -> np.ndarray:
-    """The w x h crop of overlay frame `frame` whose pixel (x, y) is frame pixel
-    ((oy + y) mod OH, (ox + x) mod OW), as FP64 in [0, 1].  overlay: uint8 [F, OH, OW, 3]."""
+    """Sec. IV (blend with crops of video frames).  The w x h crop of overlay frame `frame` whose pixel
+    (x, y) is frame pixel ((oy + y) mod OH, (ox + x) mod OW), as FP64 in [0, 1].  overlay: uint8 [F,
+    OH, OW, 3]."""
     n_f, oh, ow, _ = overlay.shape
     assert 0 <= frame < n_f
     rows = (oy + np.arange(h)) % oh
@@ -82,7 +83,7 @@ def overlay_crop(overlay: np.ndarray, frame: int, ox: int, oy: int, w: int, h: i
 
 
 def augment_view(rgb: np.ndarray, prm, overlay: np.ndarray | None, return_stages: bool = False):
-    """Randomises one rendered view.  rgb: [H, W, 3] (any float type; taken as FP64);
+    """Sec. IV: randomises one rendered view.  rgb: [H, W, 3] (any float type; taken as FP64);
     prm: mapping or record with the FIELDS above; overlay: uint8 [F, OH, OW, 3] (may be None
     when overlay_beta == 0).  Returns out [H, W, 3] FP64 (and, with return_stages, a dict of
     the intermediate images c0, c1, c2)."""
@@ -109,9 +110,9 @@ def augment_view(rgb: np.ndarray, prm, overlay: np.ndarray | None, return_stages
 
 
 def gamma_spread(c2: np.ndarray, gamma: float, delta: float) -> np.ndarray:
-    """Largest change of c ** gamma when c (in [0, 1]) moves by at most delta: the error that
-    an absolute error delta before the gamma curve can leave after it.  Used to state
-    tolerances; c ** gamma is monotone, so the extremes sit at c +- delta."""
+    """Sec. IV (random gamma), tolerance helper.  Largest change of c ** gamma when c (in [0, 1]) moves
+    by at most delta: the error that an absolute error delta before the gamma curve can leave after
+    it.  Used to state tolerances; c ** gamma is monotone, so the extremes sit at c +- delta."""
     c2 = np.asarray(c2, dtype=np.float64)
     hi = np.minimum(c2 + delta, 1.0) ** gamma
     lo = np.maximum(c2 - delta, 0.0) ** gamma

@@ -62,7 +62,8 @@ def _lib():
 
 
 def trace(scene, sensor_env, sensor_pose, dirs, opts: LidarOptions | None = None, packed=None) -> LidarResult:
-    """sensor_env [S] int, sensor_pose [S,3,4] world_from_sensor, dirs [J,3] sensor-frame
+    """Sec. III-C: LiDAR returns by ray tracing the env's Gaussians (definition in lidar.cpp).
+    sensor_env [S] int, sensor_pose [S,3,4] world_from_sensor, dirs [J,3] sensor-frame
     directions (normalised inside)."""
     opts = opts or LidarOptions()
     pk = packed or _o._Packed(scene)

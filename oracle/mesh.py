@@ -28,8 +28,8 @@ Y00 = 0.5 / math.sqrt(math.pi)     # real SH basis, degree 0
 
 
 def facet_frames(v: np.ndarray, f: np.ndarray):
-    """Per facet: barycentre b, tangent scale s_t, rotation R (columns t1, t2, n) and a flag for
-    zero-area facets.  v [V,3], f [F,3] int."""
+    """Sec. III-B (mesh-Gaussian transfer).  Per facet: barycentre b, tangent scale s_t, rotation R
+    (columns t1, t2, n) and a flag for zero-area facets.  v [V,3], f [F,3] int."""
     v = np.asarray(v, np.float64)
     p0, p1, p2 = v[f[:, 0]], v[f[:, 1]], v[f[:, 2]]
     b = (p0 + p1 + p2) / 3.0
@@ -50,8 +50,9 @@ def facet_frames(v: np.ndarray, f: np.ndarray):
 
 
 def quat_from_rot(R: np.ndarray) -> np.ndarray:
-    """(w, x, y, z) of rotation matrices [F,3,3] (Shepperd's method: the largest of the four
-    squared components decides), sign chosen with w >= 0."""
+    """Sec. III-B: the facet frame as the node layout's quaternion.  (w, x, y, z) of rotation matrices
+    [F,3,3] (Shepperd's method: the largest of the four squared components decides), sign chosen
+    with w >= 0."""
     F = len(R)
     q = np.zeros((F, 4))
     tr = R[:, 0, 0] + R[:, 1, 1] + R[:, 2, 2]
@@ -77,7 +78,7 @@ def quat_from_rot(R: np.ndarray) -> np.ndarray:
 
 def mesh_to_gaussians(v, f, vertex_colors=None, flatten: float = 0.01, opacity_logit: float = 2.0,
                       sh_degree: int = 0) -> dict:
-    """The transfer of every facet (see the module header).  Returns a dict of FP64 arrays."""
+    """Sec. III-B: the transfer of every facet (see the module header).  Returns a dict of FP64 arrays."""
     f = np.asarray(f, np.int64)
     b, s_t, R, _ = facet_frames(v, f)
     F = len(f)
@@ -93,7 +94,8 @@ def mesh_to_gaussians(v, f, vertex_colors=None, flatten: float = 0.01, opacity_l
 
 
 def covariance(log_scale: np.ndarray, quat: np.ndarray) -> np.ndarray:
-    """Sigma = R diag(exp(2 log_scale)) R^T for (w, x, y, z) quaternions (normalised here)."""
+    """Sec. III-A (3DGS covariance from scale and rotation): Sigma = R diag(exp(2 log_scale)) R^T for
+    (w, x, y, z) quaternions (normalised here)."""
     q = np.asarray(quat, np.float64)
     q = q / np.linalg.norm(q, axis=1, keepdims=True)
     w, x, y, z = q[:, 0], q[:, 1], q[:, 2], q[:, 3]

@@ -142,8 +142,8 @@ def _p(a):
 
 
 def project_view(scene, e: int, c: int, opts: OracleOptions | None = None, packed=None) -> np.ndarray:
-    """Per-instance projection of view (e, c): columns gid, u, v, z, conic a, b, c, cov xx, xy,
-    yy, opacity, r, g, b, present, near_ambiguous."""
+    """Sec. III-A (EWA splatting, SH colour, depth key).  Per-instance projection of view (e, c):
+    columns gid, u, v, z, conic a, b, c, cov xx, xy, yy, opacity, r, g, b, present, near_ambiguous."""
     lib = _load()
     pk = packed or _Packed(scene)
     o = (opts or OracleOptions())._c()
@@ -179,6 +179,9 @@ class ViewResult:
 
 
 def render_view(scene, e: int, c: int, opts: OracleOptions | None = None, packed=None) -> ViewResult:
+    """Sec. III-A and III-C: RGB, unnormalised depth and coverage of view (e, c) by the plain
+    per-pixel definition in oracle.cpp, with the FP32-ambiguous decisions flagged and their
+    alternative branches (r, g, b, d, a) returned."""
     lib = _load()
     pk = packed or _Packed(scene)
     o = (opts or OracleOptions())._c()
@@ -212,11 +215,11 @@ def _grad_buffers(pk, scene):
 
 def backward_view(scene, e: int, c: int, grad_rgb, grad_depth=None, opts: OracleOptions | None = None,
                   packed=None, out=None) -> dict:
-    """Adjoint of view (e, c) for L = sum(grad_rgb * RGB) + sum(grad_depth * D).
+    """Sec. IV (assets fitted by gradient descent on rendered images).  Adjoint of view (e, c)
+    for L = sum(grad_rgb * RGB) + sum(grad_depth * D).
 
-    Returns (or accumulates into `out`) gradients laid out as concatenated node arrays:
-    mean [G,3], log_scale [G,3], quat [G,4], opacity_logit [G], sh [G,16,3], pose [E,K,3,4].
-    """
+    Returns (or accumulates into `out`) gradients laid out as concatenated node arrays: mean [G,3],
+    log_scale [G,3], quat [G,4], opacity_logit [G], sh [G,16,3], pose [E,K,3,4]."""
     lib = _load()
     pk = packed or _Packed(scene)
     o = (opts or OracleOptions())._c()
@@ -231,7 +234,7 @@ def backward_view(scene, e: int, c: int, grad_rgb, grad_depth=None, opts: Oracle
 
 
 def backward_scene(scene, grad_rgb_views, grad_depth_views, opts=None) -> dict:
-    """Sum of backward_view over all views (lists of per-view gradient images)."""
+    """Sec. IV: sum of backward_view over all views (lists of per-view gradient images)."""
     pk = _Packed(scene)
     g = _grad_buffers(pk, scene)
     for v, (e, c) in enumerate(scene.views):
@@ -241,11 +244,11 @@ def backward_scene(scene, grad_rgb_views, grad_depth_views, opts=None) -> dict:
 
 
 def pose_twist_grad(pose: np.ndarray, grad_pose: np.ndarray) -> np.ndarray:
-    """se(3) gradient (rho, phi) of a left perturbation exp(xi^) [R|t] from the 3x4 gradient.
+    """Sec. III-B (rigid node poses): se(3) gradient (rho, phi) of a left perturbation exp(xi^) [R|t]
+    from the 3x4 gradient.
 
-    With R' = (I + [phi]x) R and t' = (I + [phi]x) t + rho:  dL/drho = G_t and dL/dphi is the
-    axial vector of the skew part of A = G_R R^T + G_t t^T, i.e. (A32-A23, A13-A31, A21-A12).
-    """
+    With R' = (I + [phi]x) R and t' = (I + [phi]x) t + rho:  dL/drho = G_t and dL/dphi is the axial
+    vector of the skew part of A = G_R R^T + G_t t^T, i.e. (A32-A23, A13-A31, A21-A12)."""
     P = np.asarray(pose, np.float64).reshape(3, 4)
     Gm = np.asarray(grad_pose, np.float64).reshape(3, 4)
     A = Gm[:, :3] @ P[:, :3].T + np.outer(Gm[:, 3], P[:, 3])
@@ -254,7 +257,8 @@ def pose_twist_grad(pose: np.ndarray, grad_pose: np.ndarray) -> np.ndarray:
 
 
 def sh_basis(deg: int, d) -> tuple:
-    """(Y[16], dY[16,3]) of the oracle's real SH basis at direction d (entries above deg are 0)."""
+    """Sec. III-A (spherical-harmonics colour): (Y[16], dY[16,3]) of the oracle's real SH basis at
+    direction d (entries above deg are 0)."""
     lib = _load()
     dd = np.ascontiguousarray(d, np.float64)
     Y = np.zeros(16); dY = np.zeros((16, 3))
@@ -263,7 +267,7 @@ def sh_basis(deg: int, d) -> tuple:
 
 
 def depth_key32(cam_from_world, world_from_node, mu) -> np.float32:
-    """The FP32 depth key (order and near cull) of a node-frame point."""
+    """Sec. III-A (depth sorting): the FP32 depth key (order and near cull) of a node-frame point."""
     lib = _load()
     a = np.ascontiguousarray(np.asarray(cam_from_world, np.float64).reshape(12))
     b = np.ascontiguousarray(np.asarray(world_from_node, np.float64).reshape(12))

@@ -24,7 +24,8 @@ import numpy as np
 
 def integrate(tsdf, weight, origin, voxel: float, trunc: float, max_weight: float, min_alpha: float, cams,
               depth_views, alpha_views, band_px: float = 1e-3, band_rel: float = 1e-5):
-    """tsdf, weight: FP64 [nz, ny, nx] (updated copies are returned); cams: list of
+    """Sec. III-B: fuses depth views into the field (definition in the module header).
+    tsdf, weight: FP64 [nz, ny, nx] (updated copies are returned); cams: list of
     (fx, fy, cx, cy, W, H, cam_from_world [3,4]); depth_views / alpha_views: per view [H, W]
     (unnormalised D and coverage A).  Returns (tsdf, weight, ambiguous [nz, ny, nx] bool)."""
     F = np.array(tsdf, np.float64, copy=True)
