@@ -114,7 +114,8 @@ void parallel_for(int64_t n, int nth, F&& f) {
 
 extern "C" {
 
-// Traces rays (sensor s, direction j) for s < n_sensors, j < n_dirs.
+// Sec. III-C (LiDAR by ray tracing the Gaussians): traces rays (sensor s, direction j) for
+// s < n_sensors, j < n_dirs.
 //   sensor_env[S], sensor_pose[S,12] (world_from_sensor), dirs[J,3] (sensor frame, normalised here)
 //   outputs [S,J]: D, A, their tolerances, hits composited, ambiguous decisions seen
 int oracle_lidar_rays(const oracle_lidar_scene* sc, const oracle_lidar_opts* o, int32_t n_sensors,

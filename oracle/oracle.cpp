@@ -121,7 +121,7 @@ void parallel_for(int64_t n, int nth, F&& f) {
 }
 
 // ------------------------------------------------------------------ real spherical harmonics
-// Y_lm for l <= 3 from the associated Legendre functions with the Condon-Shortley phase,
+// Sec. III-A (spherical-harmonics colour).  Y_lm for l <= 3 from the associated Legendre functions with the Condon-Shortley phase,
 // written through Cartesian polynomials on the unit sphere:
 //   P_l^m(cos t) e^{i m phi} = (-1)^m Q_l^m(z) (x + i y)^m,   Q_l^m = d^m P_l / dz^m,
 //   Y_l0 = N_l0 Q_l^0,  Y_lm = sqrt2 N_lm (-1)^m Q_l^m Re[(x+iy)^m],
@@ -190,6 +190,7 @@ struct Geo {
     double dqb;                  // FP32 error bound of the factored form's cross coefficient
 };
 
+// Sec. III-A: the Gaussian's rotation from its quaternion (w, x, y, z), normalised first.
 void rot_from_quat(const double q[4], double R[3][3]) {
     const double w = q[0], x = q[1], y = q[2], z = q[3];
     R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - w * z); R[0][2] = 2 * (x * z + w * y);
@@ -220,8 +221,8 @@ float depth_key32(const double Wc[3][3], const double tc[3], const double Rn[3][
     return ((a + b) + c) + M[3];
 }
 
-// Projects Gaussian g (row in attribute arrays) of the node in `slot` of env e into camera
-// (e, c).  Fills every intermediate.  valid=false if the 2D covariance is not positive.
+// Sec. III-A (EWA splatting) with Sec. III-B's rigid node pose.  Projects Gaussian g (row in
+// attribute arrays) of the node in `slot` of env e into camera (e, c).  Fills every intermediate.  valid=false if the 2D covariance is not positive.
 void project(const oracle_scene* s, const oracle_opts* o, int e, int c, int slot, int64_t g, int deg, Geo& G) {
     G.g = g; G.gid = g; G.slot = slot; G.deg = deg;
     const double* P = s->node_poses + ((int64_t)e * s->K + slot) * 12;
@@ -397,7 +398,8 @@ struct PixelResult {
 
 inline uint64_t mix(uint64_t h, uint64_t v) { h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2); return h * 1099511628211ull; }
 
-// Front-to-back composite of one pixel, branching on ambiguous decisions.
+// Sec. III-A (alpha-blending) and Sec. III-C (depth from the composited z).  Front-to-back
+// composite of one pixel, branching on ambiguous decisions.
 // A candidate's action is SKIP unless it is in front of the near plane, inside the ellipse and
 // has alpha >= alpha_min; then it is STOP if T(1-alpha) < t_min, else COMPOSITE.  Flipping one
 // ambiguous decision that changes the action starts an alternative branch.
@@ -509,14 +511,14 @@ extern "C" {
 
 int oracle_abi_version() { return 1; }
 
-// Real SH basis Y[16] (entries above the degree are 0) and its gradient dY[16][3] at d.
+// Sec. III-A: real SH basis Y[16] (entries above the degree are 0) and its gradient dY[16][3] at d.
 void oracle_sh_basis(int deg, const double* d, double* Y, double* dY) {
     double y[16], dy[16][3];
     sh_basis(deg, d, y, dy);
     for (int k = 0; k < 16; ++k) { Y[k] = y[k]; if (dY) for (int j = 0; j < 3; ++j) dY[k * 3 + j] = dy[k][j]; }
 }
 
-// The FP32 depth key of a node-frame point (poses row-major 3x4 in doubles holding floats).
+// Sec. III-A (depth sorting): the FP32 depth key of a node-frame point (poses row-major 3x4 in doubles holding floats).
 float oracle_depth_key32(const double* cam_from_world, const double* world_from_node, const double* mu) {
     double Wc[3][3], tc[3], Rn[3][3], tn[3];
     for (int i = 0; i < 3; ++i) {
@@ -526,7 +528,7 @@ float oracle_depth_key32(const double* cam_from_world, const double* world_from_
     return depth_key32(Wc, tc, Rn, tn, mu);
 }
 
-// Projection of every Gaussian of view (e, c), for closed-form checks.
+// Sec. III-A: projection of every Gaussian of view (e, c), for closed-form checks.
 // out[n, 16]: gid, u, v, z, conic a, b, c, cov xx, xy, yy, opacity, r, g, b, present, near_amb.
 // Returns the number of valid instances written (<= cap), or -1 on bad arguments.
 int64_t oracle_project_view(const oracle_scene* s, const oracle_opts* o, int e, int c, double* out, int64_t cap) {
@@ -546,7 +548,7 @@ int64_t oracle_project_view(const oracle_scene* s, const oracle_opts* o, int e, 
     return (int64_t)V.geo.size();
 }
 
-// Renders view (e, c).  rgb [H*W*3], depth/alpha [H*W]: the primary branch.
+// Sec. III-A and III-C: renders view (e, c).  rgb [H*W*3], depth/alpha [H*W]: the primary branch.
 // tol_rgb/tol_d [H*W]: extra tolerance from flips beyond max_flips.  n_alt [H*W]: number
 // of alternative branches of each pixel; alt [alt_cap*5] receives them (r,g,b,d,a) in pixel
 // order.  grad_amb [H*W] (nullable) marks pixels where a contributor's gradient switch (alpha
@@ -617,7 +619,8 @@ int oracle_render_view(const oracle_scene* s, const oracle_opts* o, int e, int c
     return need <= alt_cap ? 0 : 1;
 }
 
-// Adjoint of oracle_render_view's primary branch for L = sum grad_rgb . RGB + grad_depth . D.
+// Sec. IV (assets fitted by gradient descent on rendered images): adjoint of
+// oracle_render_view's primary branch for L = sum grad_rgb . RGB + grad_depth . D.
 // Accumulates (+=) into the gradient arrays, which are laid out like the scene arrays
 // (g_sh is [G,16,3]; g_pose is [E,K,12]).  Returns 0, or -1 on bad arguments.
 int oracle_backward_view(const oracle_scene* s, const oracle_opts* o, int e, int c,
