@@ -161,7 +161,8 @@ const char* dgs_last_error(const dgs_ctx* ctx);
 int dgs_workspace_query(const dgs_ctx* ctx, size_t* bytes);
 
 /*
- * Renders every view of a batch of environments.
+ * Renders every view of a batch of environments (Sec. III-A: tile-based splatting of RGB;
+ * Sec. III-C: depth composited the same way; Sec. III-B: nodes at per-env rigid poses).
  *
  *   nodes[n_nodes]                HOST array of node descriptors (attribute arrays DEVICE).
  *   env_node_ids[n_envs*max_nodes] HOST, node drawn in slot j of env e, -1 = empty; a node id
@@ -275,7 +276,8 @@ typedef struct dgs_tune_result {
 } dgs_tune_result;
 
 /*
- * Picks the compositing tile shape for a batch by timing it.  Renders the batch (arguments as
+ * Picks the compositing tile shape for a batch by timing it (Sec. III-A's rasterizer works on
+ * screen tiles; their shape changes speed, never the image).  Renders the batch (arguments as
  * for dgs_render) with each candidate tile shape: one untimed call (in DGS_MODE_GRAPH that
  * call captures), then `reps` timed calls (CUDA events on `stream` around the calls, host
  * staging included).  Sets the context's tile shape to the fastest, renders once more with it
@@ -326,9 +328,9 @@ typedef struct dgs_augment {
 } dgs_augment;                  /* 32 bytes */
 
 /*
- * Sets (or clears) the randomisation that every later dgs_render / dgs_autotune call on ctx
- * applies to its RGB output, fused into the compositing kernel (the un-randomised colour is
- * never written).
+ * Sec. IV randomisation, set per context.  Sets (or clears) the randomisation that every
+ * later dgs_render / dgs_autotune call on ctx applies to its RGB output, fused into the
+ * compositing kernel (the un-randomised colour is never written).
  *
  *   aug[n_views]   HOST, one record per view in dgs_render's view order; copied (the caller may
  *                  free it on return).  aug = NULL or n_views = 0 clears the randomisation.
@@ -349,9 +351,9 @@ int dgs_set_augment(dgs_ctx* ctx, const dgs_augment* aug, int32_t n_views, const
                     int32_t n_frames, int32_t overlay_w, int32_t overlay_h);
 
 /*
- * Applies the randomisation set on ctx to an existing RGB image batch, in place, as a
- * separate kernel (the same per-pixel arithmetic as the fused path, so the result is bitwise
- * that of dgs_render with the randomisation set).
+ * Sec. IV randomisation as a separate pass.  Applies the randomisation set on ctx to an
+ * existing RGB image batch, in place, as a separate kernel (the same per-pixel arithmetic as
+ * the fused path, so the result is bitwise that of dgs_render with the randomisation set).
  *
  *   rgb                  DEVICE FP32 [total_pixels,3], read and overwritten.
  *   view_size[n_views*2] HOST (width, height) of each view, 1..32768.
@@ -384,7 +386,8 @@ typedef struct dgs_lidar {
 } dgs_lidar;                    /* 52 bytes */
 
 /*
- * Builds the ray-tracing structures of the nodes on the context: per Gaussian a 64-byte record
+ * Sec. III-C (BVH-accelerated ray tracing).  Builds the ray-tracing structures of the nodes
+ * on the context: per Gaussian a 64-byte record
  * (mean, opacity, whitening matrix) and per node an implicit binary BVH over leaves of 8
  * consecutive Gaussians in storage order (store nodes in dgs_spatial_order for compact
  * leaves), boxes of the q_max ellipsoids in the node's frame.  Reads the nodes' mean,
@@ -395,7 +398,7 @@ typedef struct dgs_lidar {
 int dgs_lidar_build(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, void* stream);
 
 /*
- * Traces n_sensors x n_dirs rays: ray (s, j) starts at sensor s's origin along
+ * Sec. III-C LiDAR returns.  Traces n_sensors x n_dirs rays: ray (s, j) starts at sensor s's origin along
  * R_s dirs[j] (normalised).
  *   nodes, n_nodes                the nodes of the last dgs_lidar_build (same sizes and attribute
  *                                 pointers; else DGS_ERR_INVALID_ARG)
