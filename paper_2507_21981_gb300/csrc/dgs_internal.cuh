@@ -1,4 +1,5 @@
-// Internal device structures and helpers of libdgs (sm_103a).
+// Internal device structures and helpers of libdgs (sm_103a): the splatting renderer of
+// Sec. III-A / III-C and the side workloads of Sec. III-B, III-C and IV share them.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -105,7 +106,8 @@ __device__ __forceinline__ float ld_attr(const void* p, int64_t i) {
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
-// Does the ellipse {q <= qlim}, q = qa (dx + qb dy)^2 + qc dy^2, reach the rectangle of pixel
+// Sec. III-A (a Gaussian's screen footprint, the 3-sigma ellipse).  Does the ellipse
+// {q <= qlim}, q = qa (dx + qb dy)^2 + qc dy^2, reach the rectangle of pixel
 // centres [X0, X1] x [Y0, Y1] (relative to the mean)?  Minimum of q over the rectangle: 0 if
 // the mean is inside; else the least of the edge minima -- on a horizontal edge dy = Y the
 // minimiser is dx = -qb Y, on a vertical edge dx = X it is dy = -qa qb X / (qa qb^2 + qc) --
@@ -224,14 +226,15 @@ __device__ __forceinline__ const uint8_t* overlay_pixel(const uint8_t* overlay, 
     return overlay + (((int64_t)a.overlay_frame * oh + oy) * ow + ox) * 3;
 }
 
-// Exponent p of a staged record (scaled coefficients ca, qb, cc) at pixel offset (dx, dy);
+// Sec. III-A (the splat's falloff at a pixel).  Exponent p of a staged record (scaled
+// coefficients ca, qb, cc) at pixel offset (dx, dy);
 // also returns t = dx + qb dy.
 __device__ __forceinline__ float pixel_exponent(float ca, float qb, float cc, float dx, float dy, float& t) {
     t = fmaf(qb, dy, dx);
     return fmaf(ca * t, t, cc * dy * dy);
 }
 
-// Binning decision for tile (tx, ty) of an instance with centre (u, v), factored form
+// Sec. III-A (tile binning).  Binning decision for tile (tx, ty) of an instance with centre (u, v), factored form
 // (qa, qb, qc) and ellipse pixel box [x0, x1] x [y0, y1]: the tile's part of the box holds a
 // pixel centre of the ellipse {q <= qbin}.  Emission counts and pair writing both call this
 // on the same stored record values, so they agree exactly.

@@ -1,5 +1,6 @@
-// dgs_render_noalloc: the batched render with all of its scratch in one fixed, statically
-// allocated device array, for callers that must not allocate GPU memory.
+// dgs_render_noalloc: the batched render of Sec. III-A / III-C with all of its scratch in one
+// fixed, statically allocated device array, for callers that must not allocate GPU memory
+// (a deployment variant; the paper has no counterpart).
 //
 // Who needs it: a host program that runs inside another framework's memory manager (a
 // caching allocator that owns the device budget and forbids foreign cudaMalloc calls), a
