@@ -489,17 +489,24 @@ def tsdf_leg(dev, sc, warmup, steps):
     return res
 
 
-def cpu_baseline(views=1, seed=1):
-    """Times the FP64 oracle on `views` sampled views of the workload (host cores)."""
+def _oracle_workload(seed=1):
+    """The benchmark workload (config 2) and its FP64 copy for the oracle, built once."""
     import oracle
     from paper_2507_21981_gb300 import scenes
     sc = scenes.config2(seed=seed)
+    return sc, oracle.oracle._Packed(sc)
+
+
+def cpu_baseline(views=1, seed=1, first=0, workload=None):
+    """Times the FP64 oracle on `views` sampled views of the workload (host cores): views
+    first, first + 1, ... of a fixed spread over envs and both camera kinds."""
+    import oracle
+    sc, pk = workload or _oracle_workload(seed)
     opts = oracle.OracleOptions()
     cores = os.cpu_count() or 1
-    pk = oracle.oracle._Packed(sc)
     t0 = time.perf_counter()
     px = 0
-    for v in range(views):
+    for v in range(first, first + views):
         e, c = sc.views[(v * 37) % sc.n_views]     # spread over envs and both camera kinds
         r = oracle.render_view(sc, e, c, opts, pk)
         px += r.depth.size
@@ -551,16 +558,16 @@ def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
         return 0
-    samples = []
-    for _ in range(args.warmup):
-        pass                                   # the oracle has no warm state worth excluding
-    for _ in range(args.steps):
-        samples.append(cpu_baseline(views=1, seed=1))
+    wl = _oracle_workload(1)                   # built once, outside every step
+    for i in range(args.warmup):               # untimed: first touches of the scene's pages
+        cpu_baseline(views=1, first=i, workload=wl)
+    samples = [cpu_baseline(views=1, first=args.warmup + i, workload=wl) for i in range(args.steps)]
     val = statistics.median(s["value"] for s in samples)
     cb = dict(samples[0]); cb["value"] = val
+    cb["sample"] = f"1 view per step ({args.steps} different views), 640x480, full 1.08M-Gaussian scene, FP64"
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "1 view per step"},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "1 view per step, a different view each step"},
             "cpu_baseline": cb, "e2e": {"value": val, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
