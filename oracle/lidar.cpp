@@ -233,10 +233,10 @@ int oracle_lidar_rays(const oracle_lidar_scene* sc, const oracle_lidar_opts* o, 
         tD += 4 * kU * (double)comp * D;
         // ambiguous inclusions among the composited and among the left-out candidates
         auto behind = [&](double t) {     // primary D of the composited hits behind t
-            double s = 0.0;
+            double sum = 0.0;
             for (size_t i = 0; i < stop; ++i)
-                if (hits[i].t > t) s += w[i] * hits[i].t;
-            return s;
+                if (hits[i].t > t) sum += w[i] * hits[i].t;
+            return sum;
         };
         auto trans_at = [&](double t) {   // primary transmittance in front of t
             double Tt = 1.0;

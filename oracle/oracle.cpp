@@ -607,8 +607,8 @@ int oracle_render_view(const oracle_scene* s, const oracle_opts* o, int e, int c
     for (int y = 0; y < H; ++y) { need += (int64_t)row_alts[y].size(); amb += row_amb[y]; h += row_hash[y]; }
     if (stats) {
         stats[0] = need; stats[1] = amb; std::memcpy(&stats[2], &h, 8); stats[3] = (int64_t)V.geo.size();
-        for (int k = 0; k < 4; ++k) { int64_t s = 0; for (int y = 0; y < H; ++y) s += row_kind[(size_t)y * 4 + k]; stats[4 + k] = s; }
-        for (int k = 0; k < 3; ++k) { int64_t s = 0; for (int y = 0; y < H; ++y) s += row_work[(size_t)y * 3 + k]; stats[8 + k] = s; }
+        for (int k = 0; k < 4; ++k) { int64_t sum = 0; for (int y = 0; y < H; ++y) sum += row_kind[(size_t)y * 4 + k]; stats[4 + k] = sum; }
+        for (int k = 0; k < 3; ++k) { int64_t sum = 0; for (int y = 0; y < H; ++y) sum += row_work[(size_t)y * 3 + k]; stats[8 + k] = sum; }
     }
     if (alt && need <= alt_cap) {
         int64_t k = 0;
