@@ -14,7 +14,7 @@ mesh -> Gaussian transfer is mesh.py and depth -> TSDF fusion tsdf.py (numpy, FP
 """
 from . import augment, lidar, mesh, tsdf
 from .oracle import (OracleOptions, build, lib_path, project_view, render_view, backward_view,
-                     backward_scene, pose_twist_grad, sh_basis, depth_key32)
+                     backward_scene, pose_twist_grad, sh_basis)
 
 __all__ = ["OracleOptions", "augment", "lidar", "mesh", "tsdf", "build", "lib_path", "project_view", "render_view", "backward_view",
-           "backward_scene", "pose_twist_grad", "sh_basis", "depth_key32"]
+           "backward_scene", "pose_twist_grad", "sh_basis"]

@@ -27,29 +27,33 @@
 //   degree 3, colour = max(0, sum c_lm Y_lm(d) + 1/2), d = unit view direction expressed in
 //   the node frame.
 //
-// Depth order and near-plane cull are integer decisions taken on an FP32 key, the same on
-// both sides (the method keeps its sort keys in FP32): z32 = camera-space z of the centre,
-// evaluated in binary32 round-to-nearest, one rounding per multiply and per add, no fused
-// multiply-add, in this order:
-//   M2j = ((W20*R0j + W21*R1j) + W22*R2j)               j = 0,1,2   (camera_from_node row 2)
-//   M23 = (((W20*t0 + W21*t1) + W22*t2) + tc2)
-//   z32 = (((M20*mx + M21*my) + M22*mz) + M23)
-// with [W|tc] = cam_from_world, [R|t] = world_from_node, (mx,my,mz) the node-frame mean.
-// Candidates are sorted by (z32, global id), global id = node_base[node] + local index, and
-// culled when z32 <= float(z_near).  Every other quantity is FP64.
+// Depth order and the near-plane cull are decided on the FP64 camera-space z of the centre:
+// candidates are sorted by (z, global id), global id = node_base[node] + local index, and culled
+// when z <= z_near.  The method keeps its depth keys in FP32, so these two decisions are
+// ambiguous where FP32 may take them the other way: the near cull when |z - z_near| lies within
+// the error band of z, and the order of two candidates when their depths differ by less than the
+// sum of their bands (an FP32 order may then place the later one first).  The method's FP32
+// camera-space centre t (its z is the depth key) is taken to be rounded to binary32 within one
+// unit in the last place per coordinate (faithful rounding, the accuracy of a compensated dot
+// product; a key cannot be more accurate than the rounding of z itself), so the band of t_i is
+// dt_i = 2u |t_i| + 64 u^2 S_i, u = 2^-24 (one ulp of t_i is at most 2u |t_i|; the second term,
+// with S_i = sum_j |(Wc Rn)_ij mu_j| + |t_n| + |t_c,i| the magnitude of the summands, covers the
+// residual error of the compensated sum with a factor 4 to spare).
 //
-// Decisions whose FP64 quantity lies within the FP32 error band of its threshold (ellipse,
-// alpha_min, t_min) are "ambiguous": an FP32 implementation may legitimately take the other
-// branch.  The band is twice an error bound of the FP32 evaluation of that quantity
-// (u = 2^-24): the projected centre carries dU ~ fx (d_tx + |x/z| d_tz)/z + 2u(|u| + |cx|)
-// with d_t ~ 8u (|M_R| |mu| + |t_n| + |t_c|); d_q = 2|dq/du| dU + 2|dq/dv| dV + 32u q (+ the
-// error of the factored form); alpha moves by alpha (d_q/2 + (8 + 1.2|logit| + 0.6 q) u); the
-// transmittance accumulates sum alpha/(1-alpha) d_alpha/alpha + 2u per step.  eps_rel adds a
-// relative floor to every band.  The forward pass enumerates
-// up to max_flips such flips per pixel and returns every branch's result; beyond that it
-// widens the pixel's tolerance by T * max|value| per unexplored flip (the two branches agree
-// on the first 1-T of the composite and both stay inside the convex hull of the rest).
-//
+// Every other decision is FP64 too.  A decision whose FP64 quantity lies within the FP32 error
+// band of its threshold (ellipse, alpha_min, t_min) is likewise ambiguous.  The band is twice an
+// error bound of the FP32 evaluation of that quantity: the projected centre carries
+// dU ~ fx (d_tx + |x/z| d_tz)/z + 2u(|u| + |cx|) with d_t the band of t above;
+// d_q = 2|dq/du| dU + 2|dq/dv| dV + 32u q (+ the error of the factored form); alpha moves by
+// alpha (d_q/2 + (8 + 1.2|logit| + 0.6 q) u); the transmittance accumulates
+// sum alpha/(1-alpha) d_alpha/alpha + 2u per step.  eps_rel adds a relative floor to every band.
+// The forward pass enumerates up to max_flips flipped decisions per pixel along a branch (and at
+// most max_branches branches per pixel) and returns every branch's result, each with the FP32
+// error bound 2 T dT of its coverage A = 1 - T; beyond that it widens the pixel's tolerance by
+// T * max|value| per unexplored flip (the two branches agree on the first 1-T of the composite
+// and both stay inside the convex hull of the rest).  An order flip moves one later candidate,
+// which may precede every acting candidate between, to the current position.
+
 // The backward pass is the analytic adjoint of the primary branch (decisions held fixed).
 // It is pinned by FP64 central finite differences of the forward pass in the tests.
 #include <algorithm>
@@ -87,7 +91,7 @@ typedef struct {
     int32_t max_flips;  // branches enumerated per pixel (<= 6)
     int32_t nthreads;   // 0 = hardware concurrency
     int32_t bruteforce; // 1 = test every Gaussian at every pixel (no AABB candidate lists)
-    int32_t order64;    // 1 = decide depth order and near cull on the FP64 depth instead of z32
+    int32_t max_branches; // alternative branches enumerated per pixel before widening (0 = 64)
 } oracle_opts;
 
 }  // extern "C"
@@ -180,7 +184,7 @@ struct Geo {
     bool clx, cly;
     double J[2][3], T[2][3], cov[2][2], det, Q[2][2];
     double u, v, z, logit, opac;
-    float z32;                   // FP32 depth key (order + near cull)
+    double dz;                   // FP32 error bound of z (order and near-plane decisions)
     double ocam[3], oloc[3], dir[3], dlen, d[3], Y[16], dY[16][3];
     double raw[3], rgb[3];
     bool present, near_amb, valid;
@@ -196,29 +200,6 @@ void rot_from_quat(const double q[4], double R[3][3]) {
     R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - w * z); R[0][2] = 2 * (x * z + w * y);
     R[1][0] = 2 * (x * y + w * z); R[1][1] = 1 - 2 * (x * x + z * z); R[1][2] = 2 * (y * z - w * x);
     R[2][0] = 2 * (x * z - w * y); R[2][1] = 2 * (y * z + w * x); R[2][2] = 1 - 2 * (x * x + y * y);
-}
-
-// The FP32 depth key (see the file header).  Inputs are binary32 values held in doubles, so
-// the conversions are exact; the file is compiled with -ffp-contract=off.
-float depth_key32(const double Wc[3][3], const double tc[3], const double Rn[3][3], const double tn[3],
-                  const double mu[3]) {
-    float M[4];
-    for (int j = 0; j < 3; ++j) {
-        float a = (float)Wc[2][0] * (float)Rn[0][j];
-        float b = (float)Wc[2][1] * (float)Rn[1][j];
-        float c = (float)Wc[2][2] * (float)Rn[2][j];
-        M[j] = (a + b) + c;
-    }
-    {
-        float a = (float)Wc[2][0] * (float)tn[0];
-        float b = (float)Wc[2][1] * (float)tn[1];
-        float c = (float)Wc[2][2] * (float)tn[2];
-        M[3] = ((a + b) + c) + (float)tc[2];
-    }
-    float a = M[0] * (float)mu[0];
-    float b = M[1] * (float)mu[1];
-    float c = M[2] * (float)mu[2];
-    return ((a + b) + c) + M[3];
 }
 
 // Sec. III-A (EWA splatting) with Sec. III-B's rigid node pose.  Projects Gaussian g (row in
@@ -255,12 +236,24 @@ void project(const oracle_scene* s, const oracle_opts* o, int e, int c, int slot
     // Camera space.
     for (int i = 0; i < 3; ++i) G.t[i] = G.Wc[i][0] * G.muw[0] + G.Wc[i][1] * G.muw[1] + G.Wc[i][2] * G.muw[2] + G.tc[i];
     G.z = G.t[2];
-    G.z32 = depth_key32(G.Wc, G.tc, G.Rn, G.tn, G.mu);
-    G.present = o->order64 ? G.z > o->z_near : G.z32 > (float)o->z_near;
-    G.near_amb = false;
+    const double g32 = 5.9604644775390625e-08;
+    double MR[3][3];
+    for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) {
+        double a = 0; for (int k = 0; k < 3; ++k) a += G.Wc[i][k] * G.Rn[k][j]; MR[i][j] = a; }
+    const double tnn = std::sqrt(G.tn[0] * G.tn[0] + G.tn[1] * G.tn[1] + G.tn[2] * G.tn[2]);
+    double S[3];   // magnitude of the terms summed into each camera-space coordinate
+    for (int i = 0; i < 3; ++i)
+        S[i] = std::fabs(MR[i][0] * G.mu[0]) + std::fabs(MR[i][1] * G.mu[1]) + std::fabs(MR[i][2] * G.mu[2]) +
+               tnn + std::fabs(G.tc[i]);
+    double dt[3];   // FP32 error bounds of the camera-space centre (faithful rounding, twice)
+    for (int i = 0; i < 3; ++i) dt[i] = 2 * g32 * std::fabs(G.t[i]) + 64 * g32 * g32 * S[i];
+    G.dz = dt[2];
+    // near plane: FP64 decision, ambiguous within the band of z (and the FP32 rounding of z_near)
+    G.present = G.z > o->z_near;
+    G.near_amb = std::fabs(G.z - o->z_near) <= G.dz + 2 * g32 * o->z_near + o->eps_rel * o->z_near;
     G.valid = true;
     G.grad_amb = false;
-    if (!G.present) { G.valid = false; return; }
+    if (!G.present && !G.near_amb) { G.valid = false; return; }
     // EWA: Jacobian of the pinhole projection at t (guarded), Sigma2D = J Wc Sigma_w Wc^T J^T + lp I.
     G.xr = G.t[0] / G.t[2]; G.yr = G.t[1] / G.t[2];
     G.xc = std::min(G.limx, std::max(-G.limx, G.xr)); G.clx = G.xc != G.xr;
@@ -281,16 +274,7 @@ void project(const oracle_scene* s, const oracle_opts* o, int e, int c, int slot
     G.Q[0][1] = G.Q[1][0] = -G.cov[0][1] / G.det;
     G.u = G.fx * G.xr + G.cx; G.v = G.fy * G.yr + G.cy;
     {   // FP32 error model of the projected centre
-        const double g32 = 5.9604644775390625e-08;
-        double MR[3][3];
-        for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) {
-            double a = 0; for (int k = 0; k < 3; ++k) a += G.Wc[i][k] * G.Rn[k][j]; MR[i][j] = a; }
-        const double tnn = std::sqrt(G.tn[0] * G.tn[0] + G.tn[1] * G.tn[1] + G.tn[2] * G.tn[2]);
-        double S[3];
-        for (int i = 0; i < 3; ++i)
-            S[i] = std::fabs(MR[i][0] * G.mu[0]) + std::fabs(MR[i][1] * G.mu[1]) + std::fabs(MR[i][2] * G.mu[2]) +
-                   tnn + std::fabs(G.tc[i]);
-        const double dtx = 8 * g32 * S[0], dty = 8 * g32 * S[1], dtz = 8 * g32 * S[2];
+        const double dtx = dt[0], dty = dt[1], dtz = dt[2];
         const double dxr = (dtx + std::fabs(G.xr) * dtz) / G.t[2] + 2 * g32 * std::fabs(G.xr);
         const double dyr = (dty + std::fabs(G.yr) * dtz) / G.t[2] + 2 * g32 * std::fabs(G.yr);
         G.du = G.fx * dxr + 2 * g32 * (std::fabs(G.fx * G.xr) + std::fabs(G.cx));
@@ -357,8 +341,18 @@ bool build_view(const oracle_scene* s, const oracle_opts* o, int e, int c, ViewD
     return true;
 }
 
-// Per-pixel candidate: a Gaussian whose band-widened ellipse contains the pixel centre.
-struct Cand { int idx; double key; int64_t gid; double q, dx, dy, dq; };
+// Per-pixel candidate: a Gaussian whose band-widened ellipse contains the pixel centre, with the
+// decisions that do not depend on the transmittance: near plane, ellipse and alpha_min (d) and
+// whether FP32 may take each the other way (amb).
+struct Cand {
+    int idx;
+    double z, dz;                 // FP64 depth and its FP32 error bound
+    int64_t gid;
+    double q, dx, dy, dq;         // quadratic form at the pixel and its FP32 error bound
+    double a_raw, alpha, da;      // opacity * exp(-q/2), its clamp, relative FP32 error bound
+    bool d[3], amb[3];
+    bool may_act;                 // composited or stopping under some admissible decision
+};
 
 void pixel_candidates(const ViewData& V, const oracle_opts* o, const std::vector<int>& pool, int px, int py,
                       std::vector<Cand>& out) {
@@ -366,6 +360,7 @@ void pixel_candidates(const ViewData& V, const oracle_opts* o, const std::vector
     const double X = px + 0.5, Yc = py + 0.5;
     const double qlim = o->q_max * (1.01 + 2.0 * o->eps_rel) + 0.1;
     const double g32 = 5.9604644775390625e-08;
+    const double eps = o->eps_rel;
     for (int idx : pool) {
         const Geo& G = V.geo[idx];
         const double dx = X - G.u, dy = Yc - G.v;
@@ -375,20 +370,37 @@ void pixel_candidates(const ViewData& V, const oracle_opts* o, const std::vector
         const double t = dx - (G.cov[0][1] / G.cov[1][1]) * dy;
         const double dq = 2 * (std::fabs(G.Q[0][0] * dx + G.Q[0][1] * dy) * G.du + std::fabs(G.Q[0][1] * dx + G.Q[1][1] * dy) * G.dv) +
                           2 * G.Q[0][0] * std::fabs(t * dy) * G.dqb + 32 * g32 * q + 1e-9;
-        out.push_back({idx, o->order64 ? G.z : (double)G.z32, G.gid, q, dx, dy, dq});
+        Cand c;
+        c.idx = idx; c.z = G.z; c.dz = G.dz; c.gid = G.gid; c.q = q; c.dx = dx; c.dy = dy; c.dq = dq;
+        c.a_raw = G.opac * std::exp(-0.5 * q);
+        c.alpha = std::min(o->alpha_max, c.a_raw);
+        c.da = (c.a_raw > o->alpha_max) ? 4 * g32 : 0.5 * dq + (8 + 1.2 * std::fabs(G.logit) + 0.6 * q) * g32;
+        c.d[0] = G.present; c.d[1] = q <= o->q_max; c.d[2] = c.alpha >= o->alpha_min;
+        c.amb[0] = G.near_amb;
+        c.amb[1] = std::fabs(q - o->q_max) <= 2 * dq + eps * o->q_max;
+        c.amb[2] = std::fabs(c.alpha - o->alpha_min) <= 2 * c.alpha * c.da + eps * o->alpha_min;
+        c.may_act = (c.d[0] || c.amb[0]) && (c.d[1] || c.amb[1]) && (c.d[2] || c.amb[2]);
+        out.push_back(c);
     }
     std::sort(out.begin(), out.end(), [](const Cand& a, const Cand& b) {
-        return a.key < b.key || (a.key == b.key && a.gid < b.gid); });
+        return a.z < b.z || (a.z == b.z && a.gid < b.gid); });
 }
 
-struct Leaf { double r, g, b, d, a; };
+// May an FP32 evaluation of the two depths place candidate b (after a in FP64 order) first?
+inline bool may_precede(const Cand& a, const Cand& b, double eps) {
+    return b.z - a.z <= a.dz + b.dz + eps * std::fabs(a.z);
+}
+
+// One composite: colour, depth, coverage and the FP32 error bound 2 T dT of the coverage.
+struct Leaf { double r, g, b, d, a, ea; };
 
 struct PixelResult {
     Leaf primary;
     std::vector<Leaf> alts;
     double tol_rgb = 0, tol_d = 0;
     bool ambiguous = false;
-    int64_t amb_kind[4] = {0, 0, 0, 0};   // near, ellipse, alpha, transmittance
+    bool widened = false;                 // a flip beyond the branch budget widened the tolerance
+    int64_t amb_kind[5] = {0, 0, 0, 0, 0};   // near, ellipse, alpha, transmittance, depth order
     bool grad_amb = false;                // a gradient switch of a contributor lies within its FP32 band
     int64_t contrib = 0;                  // Gaussians composited (primary branch)
     int64_t reached = 0;                  // in-ellipse Gaussians reached before termination (primary)
@@ -402,7 +414,9 @@ inline uint64_t mix(uint64_t h, uint64_t v) { h ^= v + 0x9e3779b97f4a7c15ull + (
 // composite of one pixel, branching on ambiguous decisions.
 // A candidate's action is SKIP unless it is in front of the near plane, inside the ellipse and
 // has alpha >= alpha_min; then it is STOP if T(1-alpha) < t_min, else COMPOSITE.  Flipping one
-// ambiguous decision that changes the action starts an alternative branch.
+// ambiguous decision that changes the action starts an alternative branch; so does placing a
+// later candidate first whose depth ties with every acting candidate before it (the order
+// decision).
 enum Act { SKIP = 0, COMP = 1, STOP = 2 };
 
 inline Act action(bool near_ok, bool ell_ok, bool keep, bool stop) {
@@ -412,28 +426,46 @@ inline Act action(bool near_ok, bool ell_ok, bool keep, bool stop) {
 
 struct Compositor {
     const ViewData& V; const oracle_opts* o;
-    double Mc, Mz;
+    double Mc, Mz, dz_max;
+    size_t max_branches;
     PixelResult* R;
 
-    void widen(double T) { R->tol_rgb += T * Mc; R->tol_d += T * Mz; }
+    void widen(double T) { R->tol_rgb += T * Mc; R->tol_d += T * Mz; R->widened = true; }
+    bool budget(int flips) const { return flips < o->max_flips && R->alts.size() < max_branches; }
 
+    // fixed: the candidate at `pos` was placed there by an order flip of this branch (its order
+    // decision is taken)
     void run(const std::vector<Cand>& order, size_t pos, double T, double C0, double C1, double C2, double D,
-             int flips, bool primary, double dT) {
+             int flips, bool primary, double dT, bool fixed) {
         const double eps = o->eps_rel;
         const double g32 = 5.9604644775390625e-08;
-        for (; pos < order.size(); ++pos) {
+        for (; pos < order.size(); ++pos, fixed = false) {
             const Cand& cd = order[pos];
             const Geo& G = V.geo[cd.idx];
-            const double a_raw = G.opac * std::exp(-0.5 * cd.q);
-            const double alpha = std::min(o->alpha_max, a_raw);
+            if (!fixed && cd.may_act) {
+                // order decisions: a later candidate that may act and may precede every acting
+                // candidate from here to it
+                for (size_t j = pos + 1; j < order.size(); ++j) {
+                    const Cand& cj = order[j];
+                    if (cj.z - cd.z > cd.dz + dz_max + eps * std::fabs(cd.z)) break;
+                    if (!cj.may_act) continue;
+                    bool tie = true;
+                    for (size_t i = pos; i < j && tie; ++i) tie = !order[i].may_act || may_precede(order[i], cj, eps);
+                    if (!tie) continue;
+                    R->ambiguous = true;
+                    if (primary) R->amb_kind[4]++;
+                    if (!budget(flips)) { widen(T); continue; }
+                    std::vector<Cand> alt(order);
+                    std::rotate(alt.begin() + pos, alt.begin() + j, alt.begin() + j + 1);
+                    run(alt, pos, T, C0, C1, C2, D, flips + 1, false, dT, true);
+                }
+            }
+            const double alpha = cd.alpha;
             const double Tn = T * (1.0 - alpha);
-            // relative FP32 error bounds of alpha and of T after this Gaussian
-            const double da = (a_raw > o->alpha_max) ? 4 * g32 : 0.5 * cd.dq + (8 + 1.2 * std::fabs(G.logit) + 0.6 * cd.q) * g32;
-            const double dTn = dT + alpha / (1.0 - alpha) * da + 2 * g32;
-            const bool d[4] = {G.present, cd.q <= o->q_max, alpha >= o->alpha_min, Tn < o->t_min};
-            const bool amb[4] = {G.near_amb, std::fabs(cd.q - o->q_max) <= 2 * cd.dq + eps * o->q_max,
-                                 std::fabs(alpha - o->alpha_min) <= 2 * alpha * da + eps * o->alpha_min,
-                                 std::fabs(Tn - o->t_min) <= 2 * Tn * dTn + eps * o->t_min};
+            // relative FP32 error bound of T after this Gaussian
+            const double dTn = dT + alpha / (1.0 - alpha) * cd.da + 2 * g32;
+            const bool d[4] = {cd.d[0], cd.d[1], cd.d[2], Tn < o->t_min};
+            const bool amb[4] = {cd.amb[0], cd.amb[1], cd.amb[2], std::fabs(Tn - o->t_min) <= 2 * Tn * dTn + eps * o->t_min};
             const Act act = action(d[0], d[1], d[2], d[3]);
             for (int k = 0; k < 4; ++k) {
                 if (!amb[k]) continue;
@@ -443,18 +475,18 @@ struct Compositor {
                 if (alt == act) continue;
                 R->ambiguous = true;
                 if (primary) R->amb_kind[k]++;
-                if (flips >= o->max_flips) { widen(T); continue; }
-                if (alt == SKIP) run(order, pos + 1, T, C0, C1, C2, D, flips + 1, false, dT);
-                else if (alt == STOP) emit(T, C0, C1, C2, D, false);
+                if (!budget(flips)) { widen(T); continue; }
+                if (alt == SKIP) run(order, pos + 1, T, C0, C1, C2, D, flips + 1, false, dT, false);
+                else if (alt == STOP) emit(T, C0, C1, C2, D, dT, false);
                 else {
                     const double w = alpha * T;
                     run(order, pos + 1, Tn, C0 + w * G.rgb[0], C1 + w * G.rgb[1], C2 + w * G.rgb[2], D + w * G.z,
-                        flips + 1, false, dTn);
+                        flips + 1, false, dTn, false);
                 }
             }
             if (primary) {
                 uint64_t code = (uint64_t)act;
-                if (act != SKIP) code += 4 * (a_raw > o->alpha_max) + 8 * (G.clx || G.cly) + 16 * (G.raw[0] <= 0) +
+                if (act != SKIP) code += 4 * (cd.a_raw > o->alpha_max) + 8 * (G.clx || G.cly) + 16 * (G.raw[0] <= 0) +
                                          32 * (G.raw[1] <= 0) + 64 * (G.raw[2] <= 0);
                 R->hash = mix(R->hash, (uint64_t)cd.gid * 128 + code);
             }
@@ -464,17 +496,18 @@ struct Compositor {
             if (primary) {
                 R->contrib++;
                 // alpha clamp at alpha_max: continuous value, switched gradient
-                if (G.grad_amb || std::fabs(a_raw - o->alpha_max) <= 2 * a_raw * da + eps * o->alpha_max) R->grad_amb = true;
+                if (G.grad_amb || std::fabs(cd.a_raw - o->alpha_max) <= 2 * cd.a_raw * cd.da + eps * o->alpha_max)
+                    R->grad_amb = true;
             }
             const double w = alpha * T;
             C0 += w * G.rgb[0]; C1 += w * G.rgb[1]; C2 += w * G.rgb[2]; D += w * G.z;
             T = Tn;
             dT = dTn;
         }
-        emit(T, C0, C1, C2, D, primary);
+        emit(T, C0, C1, C2, D, dT, primary);
     }
-    void emit(double T, double C0, double C1, double C2, double D, bool primary) {
-        Leaf L{C0 + o->bg[0] * T, C1 + o->bg[1] * T, C2 + o->bg[2] * T, D, 1.0 - T};
+    void emit(double T, double C0, double C1, double C2, double D, double dT, bool primary) {
+        Leaf L{C0 + o->bg[0] * T, C1 + o->bg[1] * T, C2 + o->bg[2] * T, D, 1.0 - T, 2 * T * dT};
         if (primary) R->primary = L; else R->alts.push_back(L);
     }
 };
@@ -518,16 +551,6 @@ void oracle_sh_basis(int deg, const double* d, double* Y, double* dY) {
     for (int k = 0; k < 16; ++k) { Y[k] = y[k]; if (dY) for (int j = 0; j < 3; ++j) dY[k * 3 + j] = dy[k][j]; }
 }
 
-// Sec. III-A (depth sorting): the FP32 depth key of a node-frame point (poses row-major 3x4 in doubles holding floats).
-float oracle_depth_key32(const double* cam_from_world, const double* world_from_node, const double* mu) {
-    double Wc[3][3], tc[3], Rn[3][3], tn[3];
-    for (int i = 0; i < 3; ++i) {
-        for (int j = 0; j < 3; ++j) { Wc[i][j] = cam_from_world[i * 4 + j]; Rn[i][j] = world_from_node[i * 4 + j]; }
-        tc[i] = cam_from_world[i * 4 + 3]; tn[i] = world_from_node[i * 4 + 3];
-    }
-    return depth_key32(Wc, tc, Rn, tn, mu);
-}
-
 // Sec. III-A: projection of every Gaussian of view (e, c), for closed-form checks.
 // out[n, 16]: gid, u, v, z, conic a, b, c, cov xx, xy, yy, opacity, r, g, b, present, near_amb.
 // Returns the number of valid instances written (<= cap), or -1 on bad arguments.
@@ -549,27 +572,31 @@ int64_t oracle_project_view(const oracle_scene* s, const oracle_opts* o, int e, 
 }
 
 // Sec. III-A and III-C: renders view (e, c).  rgb [H*W*3], depth/alpha [H*W]: the primary branch.
-// tol_rgb/tol_d [H*W]: extra tolerance from flips beyond max_flips.  n_alt [H*W]: number
-// of alternative branches of each pixel; alt [alt_cap*5] receives them (r,g,b,d,a) in pixel
-// order.  grad_amb [H*W] (nullable) marks pixels where a contributor's gradient switch (alpha
-// clamp, Jacobian guard, colour clamp) lies within its FP32 band.  stats[0] = alternatives needed, stats[1] = ambiguous pixels, stats[2] = decision
-// hash (as bits), stats[3] = instances projected, stats[4..7] = ambiguous decisions on the
-// primary branch by kind (near plane, ellipse, alpha_min, t_min), stats[8] = Gaussians
-// composited, stats[9] = in-ellipse Gaussians reached before termination, stats[10] = pixels
-// that terminated (all on the primary branch); stats needs 11 entries.  Returns 0, or -1 on bad arguments, or 1 if
-// alt_cap was too small (outputs other than alt are still complete).
+// err_a [H*W] (nullable): FP32 error bound of the primary branch's coverage.
+// tol_rgb/tol_d [H*W]: extra tolerance from flips beyond the branch budget.  n_alt [H*W]: number
+// of alternative branches of each pixel; alt [alt_cap*6] receives them (r, g, b, d, a, error
+// bound of a) in pixel order.  grad_amb [H*W] (nullable) marks pixels where a contributor's
+// gradient switch (alpha clamp, Jacobian guard, colour clamp) lies within its FP32 band.
+// stats[0] = alternatives needed, stats[1] = ambiguous pixels, stats[2] = decision hash (as
+// bits), stats[3] = instances projected, stats[4..7] = ambiguous decisions on the primary branch
+// by kind (near plane, ellipse, alpha_min, t_min), stats[8] = Gaussians composited, stats[9] =
+// in-ellipse Gaussians reached before termination, stats[10] = pixels that terminated (all on
+// the primary branch), stats[11] = ambiguous depth-order decisions on the primary branch,
+// stats[12] = pixels whose tolerance was widened; stats needs 13 entries.  Returns 0, or -1 on
+// bad arguments, or 1 if alt_cap was too small (outputs other than alt are still complete).
 int oracle_render_view(const oracle_scene* s, const oracle_opts* o, int e, int c,
-                       double* rgb, double* depth, double* alpha, double* tol_rgb, double* tol_d,
+                       double* rgb, double* depth, double* alpha, double* err_a, double* tol_rgb, double* tol_d,
                        int32_t* n_alt, double* alt, int64_t alt_cap, int64_t* stats, int32_t* grad_amb) {
     ViewData V;
     if (!build_view(s, o, e, c, V)) return -1;
     std::vector<std::vector<int>> rows;
     row_pools(V, o, rows);
     const int W = V.W, H = V.H;
+    const size_t max_branches = o->max_branches > 0 ? (size_t)o->max_branches : 64;
     std::vector<std::vector<Leaf>> row_alts(H);
-    std::vector<int64_t> row_amb(H, 0);
+    std::vector<int64_t> row_amb(H, 0), row_wide(H, 0);
     std::vector<uint64_t> row_hash(H, 0);
-    std::vector<int64_t> row_kind((size_t)H * 4, 0), row_work((size_t)H * 3, 0);
+    std::vector<int64_t> row_kind((size_t)H * 5, 0), row_work((size_t)H * 3, 0);
     parallel_for(H, n_threads(o), [&](int64_t y, int) {
         std::vector<std::vector<int>> cols(W);
         cols_pool(V, o, rows[y], cols);
@@ -577,25 +604,28 @@ int oracle_render_view(const oracle_scene* s, const oracle_opts* o, int e, int c
         uint64_t hsum = 0;
         for (int x = 0; x < W; ++x) {
             pixel_candidates(V, o, cols[x], x, (int)y, cand);
-            double Mc = std::max({std::fabs(o->bg[0]), std::fabs(o->bg[1]), std::fabs(o->bg[2])}), Mz = 0;
+            double Mc = std::max({std::fabs(o->bg[0]), std::fabs(o->bg[1]), std::fabs(o->bg[2])}), Mz = 0, dzm = 0;
             for (const Cand& cd : cand) {
                 const Geo& G = V.geo[cd.idx];
                 Mc = std::max({Mc, G.rgb[0], G.rgb[1], G.rgb[2]});
                 Mz = std::max(Mz, std::fabs(G.z));
+                dzm = std::max(dzm, cd.dz);
             }
             PixelResult R;
-            Compositor comp{V, o, Mc, Mz, &R};
-            comp.run(cand, 0, 1.0, 0, 0, 0, 0, 0, true, 0.0);
+            Compositor comp{V, o, Mc, Mz, dzm, max_branches, &R};
+            comp.run(cand, 0, 1.0, 0, 0, 0, 0, 0, true, 0.0, false);
             const int64_t p = y * W + x;
             rgb[p * 3 + 0] = R.primary.r; rgb[p * 3 + 1] = R.primary.g; rgb[p * 3 + 2] = R.primary.b;
             depth[p] = R.primary.d; if (alpha) alpha[p] = R.primary.a;
+            if (err_a) err_a[p] = R.primary.ea;
             if (tol_rgb) tol_rgb[p] = R.tol_rgb;
             if (tol_d) tol_d[p] = R.tol_d;
             if (n_alt) n_alt[p] = (int32_t)R.alts.size();
             if (grad_amb) grad_amb[p] = R.grad_amb ? 1 : 0;
             for (auto& L : R.alts) row_alts[y].push_back(L);
             row_amb[y] += R.ambiguous;
-            for (int k = 0; k < 4; ++k) row_kind[(size_t)y * 4 + k] += R.amb_kind[k];
+            row_wide[y] += R.widened;
+            for (int k = 0; k < 5; ++k) row_kind[(size_t)y * 5 + k] += R.amb_kind[k];
             row_work[(size_t)y * 3 + 0] += R.contrib;
             row_work[(size_t)y * 3 + 1] += R.reached;
             row_work[(size_t)y * 3 + 2] += R.terminated;
@@ -603,17 +633,22 @@ int oracle_render_view(const oracle_scene* s, const oracle_opts* o, int e, int c
         }
         row_hash[y] = hsum;
     });
-    int64_t need = 0, amb = 0; uint64_t h = 0;
-    for (int y = 0; y < H; ++y) { need += (int64_t)row_alts[y].size(); amb += row_amb[y]; h += row_hash[y]; }
+    int64_t need = 0, amb = 0, wide = 0; uint64_t h = 0;
+    for (int y = 0; y < H; ++y) { need += (int64_t)row_alts[y].size(); amb += row_amb[y]; wide += row_wide[y]; h += row_hash[y]; }
     if (stats) {
         stats[0] = need; stats[1] = amb; std::memcpy(&stats[2], &h, 8); stats[3] = (int64_t)V.geo.size();
-        for (int k = 0; k < 4; ++k) { int64_t sum = 0; for (int y = 0; y < H; ++y) sum += row_kind[(size_t)y * 4 + k]; stats[4 + k] = sum; }
+        int64_t kind[5] = {0, 0, 0, 0, 0};
+        for (int y = 0; y < H; ++y) for (int k = 0; k < 5; ++k) kind[k] += row_kind[(size_t)y * 5 + k];
+        for (int k = 0; k < 4; ++k) stats[4 + k] = kind[k];
         for (int k = 0; k < 3; ++k) { int64_t sum = 0; for (int y = 0; y < H; ++y) sum += row_work[(size_t)y * 3 + k]; stats[8 + k] = sum; }
+        stats[11] = kind[4];
+        stats[12] = wide;
     }
     if (alt && need <= alt_cap) {
         int64_t k = 0;
         for (int y = 0; y < H; ++y) for (auto& L : row_alts[y]) {
-            alt[k * 5 + 0] = L.r; alt[k * 5 + 1] = L.g; alt[k * 5 + 2] = L.b; alt[k * 5 + 3] = L.d; alt[k * 5 + 4] = L.a; ++k; }
+            double* q = alt + k * 6;
+            q[0] = L.r; q[1] = L.g; q[2] = L.b; q[3] = L.d; q[4] = L.a; q[5] = L.ea; ++k; }
         return 0;
     }
     return need <= alt_cap ? 0 : 1;

@@ -45,7 +45,7 @@ class _Opts(C.Structure):
                 ("alpha_max", C.c_double), ("t_min", C.c_double), ("q_max", C.c_double),
                 ("guard", C.c_double), ("bg", C.c_double * 3), ("eps_rel", C.c_double),
                 ("max_flips", C.c_int32), ("nthreads", C.c_int32),
-                ("bruteforce", C.c_int32), ("order64", C.c_int32)]
+                ("bruteforce", C.c_int32), ("max_branches", C.c_int32)]
 
 
 @dataclass
@@ -62,7 +62,7 @@ class OracleOptions:
     max_flips: int = 4
     nthreads: int = 0
     bruteforce: int = 0
-    order64: int = 0
+    max_branches: int = 64
 
     def _c(self) -> _Opts:
         o = _Opts()
@@ -71,7 +71,7 @@ class OracleOptions:
             setattr(o, k, float(getattr(self, k)))
         o.bg = (C.c_double * 3)(*[float(b) for b in self.bg])
         o.max_flips, o.nthreads, o.bruteforce = int(self.max_flips), int(self.nthreads), int(self.bruteforce)
-        o.order64 = int(self.order64)
+        o.max_branches = int(self.max_branches)
         return o
 
 
@@ -84,14 +84,12 @@ def _load():
             lib.oracle_project_view.restype = C.c_int64
             lib.oracle_project_view.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64]
             lib.oracle_render_view.restype = C.c_int
-            lib.oracle_render_view.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 7 + \
+            lib.oracle_render_view.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 8 + \
                 [C.c_int64, C.c_void_p, C.c_void_p]
             lib.oracle_backward_view.restype = C.c_int
             lib.oracle_backward_view.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 8
             lib.oracle_sh_basis.restype = None
             lib.oracle_sh_basis.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
-            lib.oracle_depth_key32.restype = C.c_float
-            lib.oracle_depth_key32.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
             _lib = lib
     return _lib
 
@@ -142,8 +140,9 @@ def _p(a):
 
 
 def project_view(scene, e: int, c: int, opts: OracleOptions | None = None, packed=None) -> np.ndarray:
-    """Sec. III-A (EWA splatting, SH colour, depth key).  Per-instance projection of view (e, c):
-    columns gid, u, v, z, conic a, b, c, cov xx, xy, yy, opacity, r, g, b, present, near_ambiguous."""
+    """Sec. III-A (EWA splatting, SH colour, depth).  Per-instance projection of view (e, c):
+    columns gid, u, v, z, conic a, b, c, cov xx, xy, yy, opacity, r, g, b, present, near_ambiguous
+    (instances behind the near plane are listed only when that decision is ambiguous)."""
     lib = _load()
     pk = packed or _Packed(scene)
     o = (opts or OracleOptions())._c()
@@ -163,13 +162,15 @@ class ViewResult:
     tol_rgb: np.ndarray
     tol_d: np.ndarray
     n_alt: np.ndarray
-    alt: np.ndarray           # [n_alt_total, 5] in pixel order
+    alt: np.ndarray           # [n_alt_total, 6] (r, g, b, d, a, FP32 error bound of a) in pixel order
     ambiguous_pixels: int
     decision_hash: int
     instances: int
     ambiguous_by_kind: dict = field(default=None)
     work: dict = field(default=None)
     grad_amb: np.ndarray = field(default=None)   # pixels with a gradient switch inside its FP32 band
+    err_a: np.ndarray = field(default=None)      # FP32 error bound of the primary branch's coverage
+    widened_pixels: int = 0                      # pixels whose tolerance covers unexplored flips
     alt_offsets: np.ndarray = field(default=None)
 
     def alternatives(self, p: int) -> np.ndarray:
@@ -180,31 +181,35 @@ class ViewResult:
 
 def render_view(scene, e: int, c: int, opts: OracleOptions | None = None, packed=None) -> ViewResult:
     """Sec. III-A and III-C: RGB, unnormalised depth and coverage of view (e, c) by the plain
-    per-pixel definition in oracle.cpp, with the FP32-ambiguous decisions flagged and their
-    alternative branches (r, g, b, d, a) returned."""
+    per-pixel definition in oracle.cpp (FP64, depth order by FP64 z), with the FP32-ambiguous
+    decisions -- near plane, ellipse, alpha_min, t_min and depth order -- flagged and their
+    alternative branches (r, g, b, d, a, error bound of a) returned."""
     lib = _load()
     pk = packed or _Packed(scene)
     o = (opts or OracleOptions())._c()
     W, H = (int(x) for x in scene.cam_res[e, c])
     rgb = np.zeros((H, W, 3)); depth = np.zeros((H, W)); alpha = np.zeros((H, W))
+    ea = np.zeros((H, W))
     tr = np.zeros((H, W)); td = np.zeros((H, W)); na = np.zeros((H, W), np.int32)
     ga = np.zeros((H, W), np.int32)
-    stats = np.zeros(11, np.int64)
+    stats = np.zeros(13, np.int64)
     cap = max(1024, W * H // 8)
-    alt = np.zeros((cap, 5))
-    rc = lib.oracle_render_view(C.byref(pk.c), C.byref(o), e, c, _p(rgb), _p(depth), _p(alpha), _p(tr), _p(td),
-                                _p(na), _p(alt), cap, _p(stats), _p(ga))
+    alt = np.zeros((cap, 6))
+    args = lambda: (C.byref(pk.c), C.byref(o), e, c, _p(rgb), _p(depth), _p(alpha), _p(ea), _p(tr), _p(td), _p(na),
+                    _p(alt), cap, _p(stats), _p(ga))
+    rc = lib.oracle_render_view(*args())
     if rc == 1:
         cap = int(stats[0])
-        alt = np.zeros((cap, 5))
-        rc = lib.oracle_render_view(C.byref(pk.c), C.byref(o), e, c, _p(rgb), _p(depth), _p(alpha), _p(tr), _p(td),
-                                    _p(na), _p(alt), cap, _p(stats), _p(ga))
+        alt = np.zeros((cap, 6))
+        rc = lib.oracle_render_view(*args())
     if rc != 0:
         raise ValueError(f"oracle_render_view failed ({rc})")
-    kinds = dict(zip(("near", "ellipse", "alpha", "transmittance"), (int(x) for x in stats[4:8])))
+    kinds = dict(zip(("near", "ellipse", "alpha", "transmittance", "order"),
+                     (int(x) for x in (*stats[4:8], stats[11]))))
     work = dict(contributions=int(stats[8]), reached=int(stats[9]), terminated_pixels=int(stats[10]))
     return ViewResult(rgb, depth, alpha, tr, td, na, alt[: int(stats[0])], int(stats[1]),
-                      int(np.uint64(stats[2].view(np.uint64))), int(stats[3]), kinds, work, ga.astype(bool))
+                      int(np.uint64(stats[2].view(np.uint64))), int(stats[3]), kinds, work, ga.astype(bool),
+                      ea, int(stats[12]))
 
 
 def _grad_buffers(pk, scene):
@@ -264,12 +269,3 @@ def sh_basis(deg: int, d) -> tuple:
     Y = np.zeros(16); dY = np.zeros((16, 3))
     lib.oracle_sh_basis(int(deg), _p(dd), _p(Y), _p(dY))
     return Y, dY
-
-
-def depth_key32(cam_from_world, world_from_node, mu) -> np.float32:
-    """Sec. III-A (depth sorting): the FP32 depth key (order and near cull) of a node-frame point."""
-    lib = _load()
-    a = np.ascontiguousarray(np.asarray(cam_from_world, np.float64).reshape(12))
-    b = np.ascontiguousarray(np.asarray(world_from_node, np.float64).reshape(12))
-    m = np.ascontiguousarray(np.asarray(mu, np.float64).reshape(3))
-    return np.float32(lib.oracle_depth_key32(_p(a), _p(b), _p(m)))

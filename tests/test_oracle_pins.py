@@ -159,20 +159,6 @@ def test_anisotropic_projection_matches_rotation_library():
         np.testing.assert_allclose(row[[7, 8, 9]], [cov[0, 0], cov[0, 1], cov[1, 1]], rtol=1e-10, atol=1e-14)
 
 
-def test_depth_key32_is_binary32_evaluation():
-    """z32 equals the specified sequence of binary32 operations evaluated by numpy."""
-    rng = np.random.default_rng(6)
-    f4 = np.float32
-    for _ in range(200):
-        W = U.rigid(Rotation.random(random_state=rng).as_matrix(), rng.normal(size=3) * 3).astype(f4)
-        P = U.rigid(Rotation.random(random_state=rng).as_matrix(), rng.normal(size=3)).astype(f4)
-        mu = rng.normal(size=3).astype(f4)
-        M = [f4(f4(W[2, 0] * P[0, j]) + f4(W[2, 1] * P[1, j])) + f4(W[2, 2] * P[2, j]) for j in range(3)]
-        M3 = f4(f4(f4(f4(W[2, 0] * P[0, 3]) + f4(W[2, 1] * P[1, 3])) + f4(W[2, 2] * P[2, 3])) + W[2, 3])
-        z = f4(f4(f4(f4(M[0] * mu[0]) + f4(M[1] * mu[1])) + f4(M[2] * mu[2])) + M3)
-        assert O.depth_key32(W.astype(np.float64), P.astype(np.float64), mu.astype(np.float64)) == z
-
-
 # --------------------------------------------------------------------------- compositing
 def test_peak_alpha_at_centre_pixel():
     for logit, expect in [(0.3, 1 / (1 + math.exp(-0.3))), (8.0, 0.99), (-2.0, 1 / (1 + math.exp(2.0)))]:
@@ -293,7 +279,7 @@ def test_bruteforce_agrees_on_fd_subset():
 def test_rigid_motion_of_scene_and_camera_leaves_image_unchanged():
     rng = np.random.default_rng(11)
     sc = S.config1(seed=11, n_bg=800, n_obj=200, res=40, f=34.4)
-    o = opts(order64=1)
+    o = BASE
     r = O.render_view(sc, 0, 0, o)
     for _ in range(3):
         G = U.rigid(Rotation.random(random_state=rng).as_matrix(), rng.normal(size=3) * 2)
@@ -331,7 +317,7 @@ def _branches(r, y, x):
     """Every branch's (r, g, b, d, a) at pixel (y, x): the primary result, then the alternatives."""
     p = y * r.rgb.shape[1] + x
     prim = np.r_[r.rgb[y, x], r.depth[y, x], r.alpha[y, x]]
-    return np.vstack([prim[None], r.alternatives(p)])
+    return np.vstack([prim[None], r.alternatives(p)[:, :5]])
 
 
 def _same_branches(got, want, tol=1e-12):
@@ -395,3 +381,102 @@ def test_ellipse_boundary_tie_returns_inside_and_outside_branches():
     for y, x in [(8, 11), (8, 5), (11, 8), (5, 8)]:
         assert r.n_alt[y, x] == 1
         _same_branches(_branches(r, y, x), [np.r_[a9 * C_FG + (1 - a9) * C_BG, a9 * z, a9], np.r_[C_BG, 0, 0]])
+
+
+# --------------------------------------------------------------------------- depth order and near plane
+# The method sorts by an FP32 depth key (Sec. III-A depth sorting); the oracle orders by the FP64
+# depth, so two Gaussians whose depths differ by less than the FP32 error bands of their depths
+# may come in either order, and a centre on the near plane may be culled or kept.
+def _two_on_axis(dz_rel, alphas=(0.6, 0.5), cols=(C_FG, np.array([0.1, 0.8, 0.5])), z=4.0):
+    logits = [math.log(a / (1 - a)) for a in alphas]
+    nd = U.node([[0, 0, z], [0, 0, z * (1 + dz_rel)]], log_scales=np.full((2, 3), math.log(0.08)), logits=logits,
+                sh=U.colour_sh(np.asarray(cols)), dtype=np.float64)
+    return U.single_view([nd], f=100.0, W=17, H=17, cx=8.5, cy=8.5)
+
+
+def _composite(seq, bg):
+    """Closed-form front-to-back composite of (alpha, colour, z) triples (no cutoff reached)."""
+    T, C, D = 1.0, np.zeros(3), 0.0
+    for a, c, z in seq:
+        C = C + a * T * np.asarray(c)
+        D += a * T * z
+        T *= 1 - a
+    return np.r_[C + T * np.asarray(bg), D, 1 - T]
+
+
+def test_near_tie_pair_returns_both_orders():
+    z, dz_rel = 4.0, 2.5e-8                       # 1e-7 m apart: inside the FP32 bands of the two depths
+    c1, c2 = C_FG, np.array([0.1, 0.8, 0.5])
+    sc = _two_on_axis(dz_rel, cols=(c1, c2), z=z)
+    r = O.render_view(sc, 0, 0, opts(bg=tuple(C_BG)))
+    assert r.ambiguous_by_kind["order"] >= 1 and r.n_alt[8, 8] == 1
+    g1, g2 = (0.6, c1, z), (0.5, c2, z * (1 + dz_rel))
+    _same_branches(_branches(r, 8, 8), [_composite([g1, g2], C_BG), _composite([g2, g1], C_BG)])
+    # the FP64 order (nearer first) is the primary branch
+    np.testing.assert_allclose(r.rgb[8, 8], _composite([g1, g2], C_BG)[:3], atol=1e-12)
+
+
+def test_separated_pair_is_not_an_order_tie():
+    sc = _two_on_axis(1e-3)                       # 4 mm apart: far outside the bands
+    r = O.render_view(sc, 0, 0, opts(bg=tuple(C_BG)))
+    assert r.ambiguous_by_kind["order"] == 0 and r.n_alt[8, 8] == 0
+
+
+def test_order_tie_with_a_skipped_gaussian_is_not_ambiguous():
+    # the second Gaussian's alpha (1e-3) is far below alpha_min: it is skipped in either order
+    sc = _two_on_axis(2.5e-8, alphas=(0.6, 1e-3))
+    r = O.render_view(sc, 0, 0, opts(bg=tuple(C_BG)))
+    assert r.ambiguous_by_kind["order"] == 0 and r.n_alt[8, 8] == 0
+
+
+def test_three_way_depth_tie_returns_every_order():
+    import itertools
+    z = 3.0
+    cols = [C_FG, np.array([0.1, 0.8, 0.5]), np.array([0.6, 0.6, 0.0])]
+    alphas = [0.6, 0.5, 0.4]
+    nd = U.node([[0, 0, z]] * 3, log_scales=np.full((3, 3), math.log(0.08)),
+                logits=[math.log(a / (1 - a)) for a in alphas], sh=U.colour_sh(np.asarray(cols)), dtype=np.float64)
+    sc = U.single_view([nd], f=100.0, W=17, H=17, cx=8.5, cy=8.5)
+    r = O.render_view(sc, 0, 0, opts(bg=tuple(C_BG)))
+    g = [(alphas[i], cols[i], z) for i in range(3)]
+    want = [_composite([g[i] for i in perm], C_BG) for perm in itertools.permutations(range(3))]
+    assert r.n_alt[8, 8] == 5
+    _same_branches(_branches(r, 8, 8), want)
+    # exact ties in FP64 take the id order on the primary branch
+    np.testing.assert_allclose(r.rgb[8, 8], want[0][:3], atol=1e-12)
+
+
+def test_branch_budget_widens_over_every_order():
+    # with no flips allowed the tolerance must cover the other order
+    sc = _two_on_axis(2.5e-8)
+    r = O.render_view(sc, 0, 0, opts(bg=tuple(C_BG), max_flips=0))
+    assert r.n_alt[8, 8] == 0 and r.widened_pixels >= 1
+    g1, g2 = (0.6, C_FG, 4.0), (0.5, np.array([0.1, 0.8, 0.5]), 4.0 * (1 + 2.5e-8))
+    other = _composite([g2, g1], C_BG)
+    here = np.r_[r.rgb[8, 8], r.depth[8, 8]]
+    assert r.tol_rgb[8, 8] >= np.abs(other[:3] - here[:3]).max() - 1e-15
+    assert r.tol_d[8, 8] >= abs(other[3] - here[3]) - 1e-15
+
+
+def test_centre_on_the_near_plane_returns_culled_and_kept_branches():
+    zn, p = 0.01, 0.4
+    # f sigma / z = 1 px at the near plane; the centre projects onto the centre of pixel (8, 8)
+    nd = U.node([[0, 0, zn]], log_scales=np.full((1, 3), math.log(1e-4)), logits=[math.log(p / (1 - p))],
+                sh=U.colour_sh([C_FG]), dtype=np.float64)
+    sc = U.single_view([nd], f=100.0, W=17, H=17, cx=8.5, cy=8.5)
+    r = O.render_view(sc, 0, 0, opts(z_near=zn, bg=tuple(C_BG)))
+    assert r.ambiguous_by_kind["near"] >= 1 and r.n_alt[8, 8] == 1
+    _same_branches(_branches(r, 8, 8), [np.r_[p * C_FG + (1 - p) * C_BG, p * zn, p], np.r_[C_BG, 0, 0]])
+    # a centre well in front of the plane is kept with no alternative
+    r2 = O.render_view(sc, 0, 0, opts(z_near=zn * 0.9, bg=tuple(C_BG)))
+    assert r2.ambiguous_by_kind["near"] == 0 and r2.n_alt[8, 8] == 0 and r2.alpha[8, 8] == pytest.approx(p, rel=1e-12)
+
+
+def test_coverage_error_bound_grows_with_the_composited_gaussians():
+    # the FP32 error bound of the coverage is zero on an empty pixel, positive where Gaussians are
+    # composited, and every branch carries its own
+    sc = _two_on_axis(2.5e-8)
+    r = O.render_view(sc, 0, 0, opts(bg=tuple(C_BG)))
+    assert r.err_a[0, 0] == 0.0 and r.alpha[0, 0] == 0.0
+    assert 0 < r.err_a[8, 8] < 1e-4
+    assert np.all(r.alternatives(8 * 17 + 8)[:, 5] > 0)
