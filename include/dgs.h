@@ -22,11 +22,13 @@
  *     alpha = min(alpha_max, opacity*exp(-q/2)); alpha < alpha_min is skipped; compositing
  *     stops, without the current Gaussian, once T*(1-alpha) < t_min.
  *     RGB = sum w_i rgb_i + bg*T_final, depth = sum w_i z_i (not normalised), alpha = 1 - T.
- *   - Depth order and near-plane cull use the FP32 key z32 = camera-space z evaluated in
- *     binary32 without fused multiply-adds in a fixed order (camera_from_node row 2 composed
- *     first); equal keys are ordered by global id = (sum of sizes of the preceding nodes in
- *     the node array) + index in the node.  Keys beyond 2^32 * 2^floor(log2 z_near) compare
- *     equal.
+ *   - Depth order and near-plane cull use the FP32 key z32 = the camera-space z of the
+ *     Gaussian's centre, faithfully rounded: within one unit in the last place of the exact
+ *     value for the FP32 inputs (camera_from_node is composed, and applied to the mean, with
+ *     compensated sums); the projected centre is computed from the camera-space point rounded
+ *     the same way.  Equal keys are ordered by global id = (sum of sizes of the preceding nodes
+ *     in the node array) + index in the node.  Keys beyond 2^28 units of 2^(floor(log2
+ *     z_near) - 23) above 2^floor(log2 z_near) compare equal.
  *
  * Memory: every array pointer marked DEVICE is a CUDA device pointer owned by the caller
  * and must stay valid until the work queued on `stream` has finished.  Arrays marked HOST are
@@ -102,12 +104,29 @@ typedef struct dgs_options {
     int32_t views_per_group;    /* batched mode: max views per group; 0 = automatic: a batch with at
                                    least 2^22 tile pairs (bound) runs as two view groups on two
                                    streams, one group's binning overlapping the other's compositing;
-                                   more groups only where the 2^30-pair limit needs them */
+                                   more groups only where the 2^30-pair or the 2^24-tile limit of a
+                                   group needs them */
+    int32_t spin_limit_us;      /* limit of every bounded device-side wait (the sort's look-back), in
+                                   microseconds, 0 = 1 s; a wait that runs out ends the call with
+                                   DGS_ERR_TIMEOUT (outputs invalid, the context stays usable) */
+    int32_t check_binning;      /* 1 = eager renders read each view group's tile lists back and check
+                                   them on the host before compositing: tiles non-decreasing and below
+                                   the group's tile count, sub-tile masks within the tile, the ranges
+                                   covering every pair once, and each tile's run in depth order (equal
+                                   depths by instance number); a violation ends the call with
+                                   DGS_ERR_CUDA and a description.  Slow: for tests and debugging */
+    int32_t test_fault;         /* fault injection for tests, 0 = none.  1: the first digit pass of the
+                                   depth sort leaves the look-back status of its second partition
+                                   unpublished, so the waits behind it run out (DGS_ERR_TIMEOUT after
+                                   about spin_limit_us per wave of resident blocks); 2: with
+                                   check_binning, the host copy of the first view group's tile keys is
+                                   corrupted (two adjacent pairs of different tiles exchanged) before
+                                   the check, which must then report it */
 } dgs_options;
 
 typedef struct dgs_ctx dgs_ctx;
 
-/* Per-call statistics of the most recent dgs_render on a context. */
+/* Per-call statistics of the most recent dgs_render (or dgs_render_backward) on a context. */
 typedef struct dgs_stats {
     int64_t n_views;
     int64_t n_pixels;
@@ -122,6 +141,8 @@ typedef struct dgs_stats {
     int64_t px_composited;      /* pairs composited */
     int32_t path;               /* dgs_path: how the call ran */
     int32_t graph_captures;     /* graphs captured by this context so far */
+    int64_t bwd_reductions;     /* dgs_render_backward with profile = 2: global atomic adds of the
+                                   compositing adjoint's per-instance partials */
 } dgs_stats;
 
 /* dgs_stats.path */
@@ -135,13 +156,15 @@ typedef enum dgs_path {
 /* Kernel classes timed when dgs_options.profile = 1 (milliseconds, summed over the call). */
 typedef enum dgs_kernel_class {
     DGS_K_SETUP = 0, DGS_K_COUNT = 1, DGS_K_SCAN = 2, DGS_K_EMIT = 3, DGS_K_SORT = 4,
-    DGS_K_RANGES = 5, DGS_K_COMPOSITE = 6, DGS_K_BACKWARD = 7,
+    DGS_K_RANGES = 5, DGS_K_COMPOSITE = 6,
+    DGS_K_BACKWARD = 7,         /* dgs_render_backward's compositing adjoint (per-instance partials) */
     DGS_K_GRAPH = 8,            /* a whole graph replay (DGS_MODE_GRAPH) */
     DGS_K_AUGMENT = 9,          /* dgs_augment_rgb's pass */
     DGS_K_LIDAR = 10,           /* dgs_lidar_trace (setup + trace) */
     DGS_K_MESH = 11,            /* dgs_mesh_to_gaussians */
     DGS_K_TSDF = 12,            /* dgs_tsdf_integrate */
-    DGS_K_COUNT_CLASSES = 13
+    DGS_K_BACKWARD_PROJECT = 13, /* dgs_render_backward's projection, colour and pose adjoint */
+    DGS_K_COUNT_CLASSES = 14
 } dgs_kernel_class;
 
 /* Fills *opt with the defaults listed above. */
@@ -151,14 +174,37 @@ void dgs_default_options(dgs_options* opt);
  * Returns DGS_ERR_INVALID_ARG for a null `out` or invalid options. */
 int dgs_context_create(dgs_ctx** out, const dgs_options* opt);
 
+/* Replaces the options of a context (validated as for dgs_context_create; DGS_ERR_INVALID_ARG
+ * keeps the old ones).  A captured graph (DGS_MODE_GRAPH) is dropped: the next render captures
+ * anew.  The workspace is kept. */
+int dgs_set_options(dgs_ctx* ctx, const dgs_options* opt);
+
 /* Frees the context and its workspace (synchronises the device first).  Null is a no-op. */
 int dgs_context_destroy(dgs_ctx* ctx);
 
 /* Message of the most recent failure on `ctx` ("" if none); valid until the next call. */
 const char* dgs_last_error(const dgs_ctx* ctx);
 
-/* Bytes of device workspace currently held by the context. */
+/* Bytes of device workspace currently held by the context (every buffer of every call made on it,
+ * with the 25 % growth slack its allocations keep).  For the need of a given batch see
+ * dgs_workspace_query_batch. */
 int dgs_workspace_query(const dgs_ctx* ctx, size_t* bytes);
+
+/*
+ * Device workspace a dgs_render of this batch needs (Sec. III-A: the per-view projection records,
+ * sort keys and tile lists scale with the visible instances and their tile pairs, which depend
+ * on the poses and cameras, so they cannot be sized from the shapes alone).  Validates the batch
+ * like dgs_render (arguments as there; no outputs needed), runs its setup, count and scan
+ * kernels on `stream` (allocating the tables they need in the context, as a render would),
+ * reads the totals back and writes to *bytes the sum of the count tables and of the tile lists of
+ * its view groups (two list sets when the batch runs as two or more groups), without allocating
+ * the lists.  The adjoint needs 40 bytes per visible instance of its largest view group on top.
+ * Synchronises `stream`.
+ */
+int dgs_workspace_query_batch(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids,
+                              int32_t n_envs, int32_t max_nodes, const float* node_poses, const dgs_camera* cams,
+                              const int32_t* cams_per_env, int32_t max_cams, const int64_t* view_pixel_offset,
+                              size_t* bytes, void* stream);
 
 /*
  * Renders every view of a batch of environments (Sec. III-A: tile-based splatting of RGB;
@@ -237,6 +283,22 @@ int dgs_render_backward(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes,
                         const float* grad_rgb, const float* grad_depth,
                         const dgs_node_grads* grads, float* grad_poses,
                         const int64_t* view_pixel_offset, void* stream);
+
+/*
+ * se(3) gradient of node poses (Sec. III-B: interactive nodes move rigidly with poses from
+ * physics; Sec. IV: the scene's parameters are fitted by gradient descent).  For each pose
+ * T = [R | t] (world_from_node, row-major 3x4) and its gradient G = dL/dT (3x4, as written to
+ * dgs_render_backward's grad_poses), writes the gradient of L with respect to the twist
+ * xi = (rho, phi) of a left perturbation T' = exp(xi^) T at xi = 0:
+ *   dL/drho = G_t,   dL/dphi = (A_21 - A_12, A_02 - A_20, A_10 - A_01),  A = G_R R^T + G_t t^T.
+ *
+ *   poses       DEVICE FP32 [n,12]
+ *   grad_poses  DEVICE FP32 [n,12]
+ *   out_twist   DEVICE FP32 [n,6] (rho then phi), overwritten
+ * Queued on `stream` without synchronising; needs no context.  Returns DGS_ERR_INVALID_ARG for
+ * n < 0 or a null pointer with n > 0, DGS_ERR_CUDA if the launch fails.
+ */
+int dgs_pose_twist_grad(const float* poses, const float* grad_poses, int64_t n, float* out_twist, void* stream);
 
 /* Statistics of the most recent successful dgs_render on ctx. */
 int dgs_last_stats(const dgs_ctx* ctx, dgs_stats* out);

@@ -169,29 +169,6 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 bool finite(float x) { return std::isfinite(x); }
 
-int check_options(const dgs_options* o, std::string& why) {
-    if (o->mode != DGS_MODE_PLAIN && o->mode != DGS_MODE_BATCHED && o->mode != DGS_MODE_GRAPH) {
-        why = "mode";
-        return 0;
-    }
-    const int area = o->tile_w * o->tile_h;
-    // w = 8a, h = 4b with 32ab in {64, 128, 256}: both are powers of two
-    if (o->tile_w < 8 || o->tile_h < 4 || o->tile_w % 8 || o->tile_h % 4 || (area != 64 && area != 128 && area != 256) ||
-        (o->tile_w & (o->tile_w - 1)) || (o->tile_h & (o->tile_h - 1))) {
-        why = "tile shape";
-        return 0;
-    }
-    if (!(o->z_near > 0) || !finite(o->z_near)) { why = "z_near"; return 0; }
-    if (!(o->lowpass >= 0) || !finite(o->lowpass)) { why = "lowpass"; return 0; }
-    if (!(o->alpha_min >= 0) || !(o->alpha_max > 0) || !(o->alpha_max <= 1)) { why = "alpha limits"; return 0; }
-    if (!(o->t_min >= 0) || !(o->t_min < 1)) { why = "t_min"; return 0; }
-    if (!(o->q_max > 0) || !finite(o->q_max)) { why = "q_max"; return 0; }
-    if (!(o->guard > 0) || !finite(o->guard)) { why = "guard"; return 0; }
-    for (int i = 0; i < 3; ++i) if (!finite(o->bg[i])) { why = "bg"; return 0; }
-    if (o->views_per_group < 0) { why = "views_per_group"; return 0; }
-    return 1;
-}
-
 cudaEvent_t take_event(dgs_ctx* ctx) {
     if (ctx->next_event == ctx->events.size()) {
         cudaEvent_t e;
@@ -232,12 +209,16 @@ void collect_times(dgs_ctx* ctx) {
     }
 }
 
+// Per-view exclusive offsets of instances and pairs into out[0, n) and out[n, 2n); out[2n + 1]
+// receives the 64-bit instance total of the count scan (the 32-bit offsets wrap beyond 2^32).
 __global__ void k_view_totals(const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off,
-                              const int64_t* __restrict__ view_tab, int n, uint64_t* out) {
+                              const int64_t* __restrict__ view_tab, int n, const ulonglong2* __restrict__ scan_total,
+                              uint64_t* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     out[i] = inst_off[view_tab[i]];
     out[n + i] = pair_off[view_tab[i]];
+    if (i == 0) out[2 * n + 1] = scan_total ? scan_total->x : 0ull;
 }
 
 constexpr uint64_t kPipelinePairs = 1ull << 22;   // batches with this many pairs run as two groups
@@ -250,74 +231,84 @@ int bits_for(uint64_t n) {   // smallest b with 2^b >= n (n >= 1)
 
 }  // namespace
 
-namespace {
+namespace dgs {
 
-// Everything one call needs after validation and the count pass.
-struct Batch {
-    int V = 0, K = 0, n_nodes = 0;
-    int dtype_mask = 0;
-    int64_t chunk_total = 0, tiles_total = 0, T = 0;
-    bool batched = true;
-    std::vector<ViewDesc> views;
-    std::vector<int64_t> view_tab;
-    std::vector<std::pair<int, int>> groups;
-    const uint64_t* inst_at = nullptr;     // per-view exclusive instance offsets (host, V+1)
-    const uint64_t* pair_at = nullptr;     // per-view exclusive pair offsets (host, V+1)
-    const NodeDesc* d_nodes = nullptr;
-    const ViewDesc* d_views = nullptr;
-    const NodeView* d_nv = nullptr;
-    const int32_t* d_nvoff = nullptr;
-    const int32_t* d_pmap = nullptr;
-    VNode* d_vnodes = nullptr;
-    uint2* d_counts = nullptr;
-    uint32_t* d_inst_off = nullptr;
-    uint64_t* d_pair_off = nullptr;
-    uint32_t* d_err = nullptr;
-    const dgs_node_grads* d_grads = nullptr;
-    const int32_t* d_slot = nullptr;
-    const int64_t* d_vtab = nullptr;
-    const int64_t* d_viewtab = nullptr;
-    const float* node_poses = nullptr;
-    int64_t n_parts = 0, n_nv = 0;
-    size_t upload_bytes = 0, meta_bytes = 0;
+int check_options(const dgs_options* o, std::string& why) {
+    if (o->mode != DGS_MODE_PLAIN && o->mode != DGS_MODE_BATCHED && o->mode != DGS_MODE_GRAPH) {
+        why = "mode";
+        return 0;
+    }
+    const int area = o->tile_w * o->tile_h;
+    // w = 8a, h = 4b with 32ab in {64, 128, 256}: both are powers of two
+    if (o->tile_w < 8 || o->tile_h < 4 || o->tile_w % 8 || o->tile_h % 4 || (area != 64 && area != 128 && area != 256) ||
+        (o->tile_w & (o->tile_w - 1)) || (o->tile_h & (o->tile_h - 1))) {
+        why = "tile shape";
+        return 0;
+    }
+    if (!(o->z_near > 0) || !finite(o->z_near)) { why = "z_near"; return 0; }
+    if (!(o->lowpass >= 0) || !finite(o->lowpass)) { why = "lowpass"; return 0; }
+    if (!(o->alpha_min >= 0) || !(o->alpha_max > 0) || !(o->alpha_max <= 1)) { why = "alpha limits"; return 0; }
+    if (!(o->t_min >= 0) || !(o->t_min < 1)) { why = "t_min"; return 0; }
+    if (!(o->q_max > 0) || !finite(o->q_max)) { why = "q_max"; return 0; }
+    if (!(o->guard > 0) || !finite(o->guard)) { why = "guard"; return 0; }
+    for (int i = 0; i < 3; ++i) if (!finite(o->bg[i])) { why = "bg"; return 0; }
+    if (o->views_per_group < 0) { why = "views_per_group"; return 0; }
+    if (o->spin_limit_us < 0) { why = "spin_limit_us"; return 0; }
+    if (o->check_binning < 0 || o->check_binning > 1) { why = "check_binning"; return 0; }
+    if (o->test_fault < 0 || o->test_fault > 2) { why = "test_fault"; return 0; }
+    return 1;
+}
+
+Params make_params(const dgs_options& o) {
     Params P{};
-};
+    P.z_near = o.z_near; P.lowpass = o.lowpass; P.alpha_min = o.alpha_min; P.alpha_max = o.alpha_max;
+    P.t_min = o.t_min; P.q_max = o.q_max; P.guard = o.guard;
+    P.bg0 = o.bg[0]; P.bg1 = o.bg[1]; P.bg2 = o.bg[2];
+    P.qbin = o.q_max * 1.001f + 1e-3f;
+    P.p_min = kHalfLog2e * o.q_max;
+    P.tile_w = o.tile_w; P.tile_h = o.tile_h;
+    while ((1 << P.tile_sx) < o.tile_w) ++P.tile_sx;
+    while ((1 << P.tile_sy) < o.tile_h) ++P.tile_sy;
+    P.exact_tile_test = o.exact_tile_test;
+    uint32_t b;
+    std::memcpy(&b, &o.z_near, 4);
+    P.zbase = b & 0x7F800000u;   // 2^floor(log2 z_near)
+    return P;
+}
 
-// Validation, host tables and their upload (one copy from pinned memory), workspace for the
-// count table.  Returns DGS_OK with B filled (B.V == 0: nothing to render).
-int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids, int32_t n_envs,
-            int32_t max_nodes, const float* node_poses, const dgs_camera* cams, const int32_t* cams_per_env,
-            int32_t max_cams, const float* out_rgb, const float* out_depth, const int64_t* view_pixel_offset,
-            const dgs_node_grads* grads, cudaStream_t stream, Timer& tm, Batch& B) {
-    const dgs_options& o = ctx->opt;
+// Argument validation and the host tables of one batch (see HostTables).  Returns DGS_OK, or
+// the status of the first failed check with its description in `why`.  No CUDA call.
+int build_host_tables(const dgs_options& o, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids,
+                      int32_t n_envs, int32_t max_nodes, const float* node_poses, const dgs_camera* cams,
+                      const int32_t* cams_per_env, int32_t max_cams, const int64_t* view_pixel_offset, HostTables& H,
+                      std::string& why) {
+    auto reject = [](std::string& w, int code, const std::string& msg) { w = msg; return code; };
     // ---------------------------------------------------------------- validation (synchronous)
-    if (n_nodes < 1 || !nodes) return fail(ctx, DGS_ERR_INVALID_ARG, "nodes: need n_nodes >= 1 and a node array");
-    if (n_envs < 1 || max_nodes < 1 || max_cams < 1) return fail(ctx, DGS_ERR_INVALID_ARG, "n_envs, max_nodes, max_cams must be >= 1");
-    if (!env_node_ids || !cams || !cams_per_env || !node_poses) return fail(ctx, DGS_ERR_INVALID_ARG, "null table pointer");
-    if (!out_rgb || !out_depth) return fail(ctx, DGS_ERR_INVALID_ARG, "out_rgb and out_depth are required");
-    (void)grads;
+    if (n_nodes < 1 || !nodes) return reject(why, DGS_ERR_INVALID_ARG, "nodes: need n_nodes >= 1 and a node array");
+    if (n_envs < 1 || max_nodes < 1 || max_cams < 1) return reject(why, DGS_ERR_INVALID_ARG, "n_envs, max_nodes, max_cams must be >= 1");
+    if (!env_node_ids || !cams || !cams_per_env || !node_poses) return reject(why, DGS_ERR_INVALID_ARG, "null table pointer");
     int64_t total_gauss = 0;
     for (int k = 0; k < n_nodes; ++k) {
         const dgs_node& nd = nodes[k];
         if (nd.n < 0 || nd.sh_degree < 0 || nd.sh_degree > 3 || nd.dtype < 0 || nd.dtype > 2)
-            return fail(ctx, DGS_ERR_INVALID_ARG, "node " + std::to_string(k) + ": bad n, sh_degree or dtype");
+            return reject(why, DGS_ERR_INVALID_ARG, "node " + std::to_string(k) + ": bad n, sh_degree or dtype");
         if (nd.n > 0 && (!nd.mean || !nd.log_scale || !nd.quat || !nd.opacity_logit || !nd.sh))
-            return fail(ctx, DGS_ERR_INVALID_ARG, "node " + std::to_string(k) + ": null attribute pointer");
+            return reject(why, DGS_ERR_INVALID_ARG, "node " + std::to_string(k) + ": null attribute pointer");
         total_gauss += nd.n;
     }
-    if (total_gauss >= (1ll << 32)) return fail(ctx, DGS_ERR_INVALID_ARG, "more than 2^32 Gaussians");
+    if (total_gauss >= (1ll << 32)) return reject(why, DGS_ERR_INVALID_ARG, "more than 2^32 Gaussians");
     const int E = n_envs, K = max_nodes, C = max_cams;
     std::vector<int> seen(n_nodes, -1);
     for (int e = 0; e < E; ++e) {
         for (int j = 0; j < K; ++j) {
             const int k = env_node_ids[(int64_t)e * K + j];
-            if (k < -1 || k >= n_nodes) return fail(ctx, DGS_ERR_INVALID_ARG, "env_node_ids out of range");
+            if (k < -1 || k >= n_nodes) return reject(why, DGS_ERR_INVALID_ARG, "env_node_ids out of range");
             if (k >= 0) {
-                if (seen[k] == e) return fail(ctx, DGS_ERR_INVALID_ARG, "a node appears twice in one env");
+                if (seen[k] == e) return reject(why, DGS_ERR_INVALID_ARG, "a node appears twice in one env");
                 seen[k] = e;
             }
         }
-        if (cams_per_env[e] < 0 || cams_per_env[e] > C) return fail(ctx, DGS_ERR_INVALID_ARG, "cams_per_env out of range");
+        if (cams_per_env[e] < 0 || cams_per_env[e] > C) return reject(why, DGS_ERR_INVALID_ARG, "cams_per_env out of range");
     }
     // views
     std::vector<ViewDesc> views;
@@ -327,16 +318,16 @@ int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* e
         for (int c = 0; c < cams_per_env[e]; ++c) {
             const dgs_camera& cm = cams[(int64_t)e * C + c];
             if (cm.width < 1 || cm.height < 1 || cm.width > 32768 || cm.height > 32768)
-                return fail(ctx, DGS_ERR_INVALID_ARG, "camera resolution");
+                return reject(why, DGS_ERR_INVALID_ARG, "camera resolution");
             if (!(cm.fx > 0) || !(cm.fy > 0) || !finite(cm.fx) || !finite(cm.fy) || !finite(cm.cx) || !finite(cm.cy))
-                return fail(ctx, DGS_ERR_INVALID_ARG, "camera intrinsics");
+                return reject(why, DGS_ERR_INVALID_ARG, "camera intrinsics");
             for (int a = 0; a < 12; ++a)
-                if (!finite(cm.cam_from_world[a])) return fail(ctx, DGS_ERR_INVALID_ARG, "camera pose not finite");
+                if (!finite(cm.cam_from_world[a])) return reject(why, DGS_ERR_INVALID_ARG, "camera pose not finite");
             for (int a = 0; a < 3; ++a)
                 for (int b = 0; b < 3; ++b) {
                     double s = 0;
                     for (int r = 0; r < 3; ++r) s += (double)cm.cam_from_world[r * 4 + a] * cm.cam_from_world[r * 4 + b];
-                    if (std::fabs(s - (a == b ? 1.0 : 0.0)) > 1e-4) return fail(ctx, DGS_ERR_INVALID_ARG, "camera rotation not orthonormal");
+                    if (std::fabs(s - (a == b ? 1.0 : 0.0)) > 1e-4) return reject(why, DGS_ERR_INVALID_ARG, "camera rotation not orthonormal");
                 }
             ViewDesc vd{};
             vd.fx = cm.fx; vd.fy = cm.fy; vd.cx = cm.cx; vd.cy = cm.cy;
@@ -349,26 +340,21 @@ int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* e
             vd.tile_base = (int32_t)tiles_total;
             std::memcpy(vd.cam, cm.cam_from_world, sizeof(vd.cam));
             tiles_total += (int64_t)vd.tiles_x * vd.tiles_y;
-            if (tiles_total >= (1ll << 31)) return fail(ctx, DGS_ERR_INVALID_ARG, "too many tiles");
+            if (tiles_total >= (1ll << 31)) return reject(why, DGS_ERR_INVALID_ARG, "too many tiles");
             const int64_t v = (int64_t)views.size();
             vd.pix_off = view_pixel_offset ? view_pixel_offset[v] : pix_total;
-            if (vd.pix_off < 0) return fail(ctx, DGS_ERR_INVALID_ARG, "negative view_pixel_offset");
+            if (vd.pix_off < 0) return reject(why, DGS_ERR_INVALID_ARG, "negative view_pixel_offset");
             pix_total += (int64_t)cm.width * cm.height;
             views.push_back(vd);
             view_env.push_back(e);
             view_cam.push_back(c);
         }
     const int V = (int)views.size();
-    const bool aug_on = !ctx->aug.empty();
-    if (aug_on && (int64_t)ctx->aug.size() != V)
-        return fail(ctx, DGS_ERR_INVALID_ARG, "the randomisation is set for " + std::to_string(ctx->aug.size()) +
-                                                  " views, the batch has " + std::to_string(V));
-    ctx->stats = dgs_stats{};
-    ctx->stats.n_views = V;
-    ctx->stats.n_pixels = pix_total;
-    for (float& t : ctx->ktimes) t = 0.f;
-    B.V = V;
-    if (V == 0) return DGS_OK;
+    H.pix_total = pix_total;
+    if (V == 0) {
+        H.views = std::move(views);
+        return DGS_OK;
+    }
 
     // ---------------------------------------------------------------- host tables
     std::vector<NodeDesc> nd(n_nodes);
@@ -384,7 +370,7 @@ int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* e
         gbase += nodes[k].n;
         if (nodes[k].n > 0) dtype_mask |= 1 << nodes[k].dtype;
     }
-    if (chunk_total >= (1ll << 31)) return fail(ctx, DGS_ERR_INVALID_ARG, "too many Gaussians");
+    if (chunk_total >= (1ll << 31)) return reject(why, DGS_ERR_INVALID_ARG, "too many Gaussians");
     // count table: per view, the chunks of its nodes in node-id order
     std::vector<int32_t> slot_node((size_t)V * K, -1);
     std::vector<int64_t> vnode_tab((size_t)V * K, 0), view_tab(V + 1, 0);
@@ -425,7 +411,96 @@ int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* e
         nv.insert(nv.end(), per_node[k].begin(), per_node[k].end());
     }
     nv_off[n_nodes] = (int32_t)nv.size();
-    ctx->stats.n_instances = n_instances;
+    H.nodes = std::move(nd);
+    H.views = std::move(views);
+    H.view_env = std::move(view_env);
+    H.view_cam = std::move(view_cam);
+    H.slot_node = std::move(slot_node);
+    H.vnode_tab = std::move(vnode_tab);
+    H.view_tab = std::move(view_tab);
+    H.pmap = std::move(pmap);
+    H.nv_off = std::move(nv_off);
+    H.nv = std::move(nv);
+    H.dtype_mask = dtype_mask;
+    H.chunk_total = chunk_total;
+    H.tiles_total = tiles_total;
+    H.n_instances = n_instances;
+    H.T = T;
+    return DGS_OK;
+}
+
+
+}  // namespace dgs
+
+namespace {
+
+// Everything one call needs after validation and the count pass.
+struct Batch {
+    int V = 0, K = 0, n_nodes = 0;
+    int dtype_mask = 0;
+    int64_t chunk_total = 0, tiles_total = 0, T = 0;
+    bool batched = true;
+    std::vector<ViewDesc> views;
+    std::vector<int64_t> view_tab;
+    std::vector<std::pair<int, int>> groups;
+    const uint64_t* inst_at = nullptr;     // per-view exclusive instance offsets (host, V+1)
+    const uint64_t* pair_at = nullptr;     // per-view exclusive pair offsets (host, V+1)
+    const NodeDesc* d_nodes = nullptr;
+    const ViewDesc* d_views = nullptr;
+    const NodeView* d_nv = nullptr;
+    const int32_t* d_nvoff = nullptr;
+    const int32_t* d_pmap = nullptr;
+    VNode* d_vnodes = nullptr;
+    uint2* d_counts = nullptr;
+    uint32_t* d_inst_off = nullptr;
+    uint64_t* d_pair_off = nullptr;
+    uint32_t* d_err = nullptr;
+    const dgs_node_grads* d_grads = nullptr;
+    const int32_t* d_slot = nullptr;
+    const int64_t* d_vtab = nullptr;
+    const int64_t* d_viewtab = nullptr;
+    const float* node_poses = nullptr;
+    int64_t n_parts = 0, n_nv = 0;
+    size_t upload_bytes = 0, meta_bytes = 0;
+    size_t front_bytes = 0;                // device bytes of the tables up to the count scan
+    Params P{};
+};
+
+// Validation, host tables and their upload (one copy from pinned memory), workspace for the
+// count table.  Returns DGS_OK with B filled (B.V == 0: nothing to render).
+int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids, int32_t n_envs,
+            int32_t max_nodes, const float* node_poses, const dgs_camera* cams, const int32_t* cams_per_env,
+            int32_t max_cams, const float* out_rgb, const float* out_depth, const int64_t* view_pixel_offset,
+            const dgs_node_grads* grads, cudaStream_t stream, Timer& tm, Batch& B, bool need_outputs = true) {
+    const dgs_options& o = ctx->opt;
+    HostTables H;
+    std::string why;
+    const int vrc = build_host_tables(o, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env,
+                                      max_cams, view_pixel_offset, H, why);
+    if (vrc != DGS_OK) return fail(ctx, vrc, why);
+    if (need_outputs && (!out_rgb || !out_depth)) return fail(ctx, DGS_ERR_INVALID_ARG, "out_rgb and out_depth are required");
+    const int V = (int)H.views.size(), K = max_nodes;
+    const bool aug_on = !ctx->aug.empty();
+    if (aug_on && (int64_t)ctx->aug.size() != V)
+        return fail(ctx, DGS_ERR_INVALID_ARG, "the randomisation is set for " + std::to_string(ctx->aug.size()) +
+                                                  " views, the batch has " + std::to_string(V));
+    ctx->stats = dgs_stats{};
+    ctx->stats.n_views = V;
+    ctx->stats.n_pixels = H.pix_total;
+    for (float& t : ctx->ktimes) t = 0.f;
+    B.V = V;
+    if (V == 0) return DGS_OK;
+    ctx->stats.n_instances = H.n_instances;
+    std::vector<NodeDesc>& nd = H.nodes;
+    std::vector<ViewDesc>& views = H.views;
+    std::vector<int32_t>& slot_node = H.slot_node;
+    std::vector<int64_t>& vnode_tab = H.vnode_tab;
+    std::vector<int64_t>& view_tab = H.view_tab;
+    std::vector<int32_t>& pmap = H.pmap;
+    std::vector<int32_t>& nv_off = H.nv_off;
+    std::vector<NodeView>& nv = H.nv;
+    const int dtype_mask = H.dtype_mask;
+    const int64_t chunk_total = H.chunk_total, tiles_total = H.tiles_total, T = H.T;
 
     // ---------------------------------------------------------------- upload (one copy)
     size_t off = 0;
@@ -482,28 +557,14 @@ int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* e
     if ((rc = ensure_host(ctx, ctx->h_read, ctx->h_read_bytes, sizeof(uint64_t) * 2 * (V + 1) + 64 + 4 * (V + 1))))
         return rc;
     if ((rc = ensure(ctx, ctx->totals, sizeof(uint32_t) * (V + 1)))) return rc;
+    B.front_bytes = meta_bytes + 64 + sizeof(uint2) * std::max<int64_t>(T, 1) + sizeof(uint32_t) * (T + 1) +
+                    sizeof(uint64_t) * (T + 1) + sizeof(ulonglong2) * (n_parts + 1) + sizeof(uint64_t) * 2 * (V + 1) +
+                    64 + sizeof(uint32_t) * (V + 1);
     uint32_t* d_err = static_cast<uint32_t*>(ctx->errword.p);
 
     DGS_CUDA(ctx, cudaMemcpyAsync(dm, hm, upload_bytes, cudaMemcpyHostToDevice, stream));
 
-    Params P{};
-    P.z_near = o.z_near; P.lowpass = o.lowpass; P.alpha_min = o.alpha_min; P.alpha_max = o.alpha_max;
-    P.t_min = o.t_min; P.q_max = o.q_max; P.guard = o.guard;
-    P.bg0 = o.bg[0]; P.bg1 = o.bg[1]; P.bg2 = o.bg[2];
-    P.qbin = o.q_max * 1.001f + 1e-3f;
-    P.p_min = kHalfLog2e * o.q_max;
-    P.tile_w = o.tile_w; P.tile_h = o.tile_h;
-    P.tile_sx = 0;
-    P.tile_sy = 0;
-    while ((1 << P.tile_sx) < o.tile_w) ++P.tile_sx;
-    while ((1 << P.tile_sy) < o.tile_h) ++P.tile_sy;
-    P.exact_tile_test = o.exact_tile_test;
-    P.tile0 = 0;
-    {
-        uint32_t b;
-        std::memcpy(&b, &o.z_near, 4);
-        P.zbase = b & 0x7F800000u;   // 2^floor(log2 z_near)
-    }
+    Params P = make_params(o);
     P.err = d_err;
     P.gate = nullptr;
     if (aug_on) {
@@ -553,41 +614,47 @@ void launch_front(dgs_ctx* ctx, const Batch& B, const Launch& L, Timer& tm) {
 }
 
 // Workspace of one set of group lists: n_inst instances, n_pairs tile pairs, n_tiles tiles.
-int ensure_lists(dgs_ctx* ctx, ListBufs& lb, uint64_t n_inst, uint64_t n_pairs, int64_t n_tiles) {
-    int rc;
+// Bytes of each buffer of ListBufs (in ListBufs::all order) for one view group of n_inst
+// instances, n_pairs tile pairs and n_tiles tiles.
+void list_bytes(uint64_t n_inst, uint64_t n_pairs, int64_t n_tiles, size_t out[17]) {
     n_inst = std::max<uint64_t>(n_inst, 1);
     n_pairs = std::max<uint64_t>(n_pairs, 1);
-    if ((rc = ensure(ctx, lb.records, sizeof(Record) * n_inst))) return rc;
-    if ((rc = ensure(ctx, lb.info, sizeof(InstInfo) * n_inst))) return rc;
-    DevBuf* inst_bufs[] = {&lb.dkey0, &lb.ival0, &lb.dkey1, &lb.ival1, &lb.ntile};
-    for (DevBuf* b : inst_bufs)
-        if ((rc = ensure(ctx, *b, sizeof(uint32_t) * n_inst))) return rc;
-    if ((rc = ensure(ctx, lb.poff, sizeof(uint32_t) * (n_inst + 1)))) return rc;
-    if ((rc = ensure(ctx, lb.tparts, sizeof(uint32_t) * tile_scan_parts((uint32_t)n_inst)))) return rc;
-    DevBuf* pair_bufs[] = {&lb.tkeys0, &lb.tvals0, &lb.tkeys1, &lb.tvals1};
-    for (DevBuf* b : pair_bufs)
-        if ((rc = ensure(ctx, *b, sizeof(uint32_t) * n_pairs))) return rc;
-    if ((rc = ensure(ctx, lb.hist, sizeof(uint32_t) * 4 * 1024))) return rc;
-    if ((rc = ensure(ctx, lb.counters, sizeof(uint32_t) * 8))) return rc;
-    const uint64_t most = std::max(n_inst, n_pairs);
-    if ((rc = ensure(ctx, lb.status, sizeof(uint32_t) * sort_status_words((uint32_t)most)))) return rc;
-    if ((rc = ensure(ctx, lb.ranges, sizeof(uint2) * (size_t)std::max<int64_t>(n_tiles, 1)))) return rc;
+    const size_t u = sizeof(uint32_t);
+    const size_t b[17] = {sizeof(Record) * n_inst, sizeof(InstInfo) * n_inst, u * n_inst, u * n_inst, u * n_inst,
+                          u * n_inst, u * n_inst, u * (n_inst + 1), u * tile_scan_parts((uint32_t)n_inst),
+                          u * n_pairs, u * n_pairs, u * n_pairs, u * n_pairs, u * 4 * 1024,
+                          u * sort_status_words((uint32_t)std::max(n_inst, n_pairs)), u * 8,
+                          sizeof(uint2) * (size_t)std::max<int64_t>(n_tiles, 1)};
+    for (int i = 0; i < 17; ++i) out[i] = b[i];
+}
+
+// Workspace of one set of group lists: n_inst instances, n_pairs tile pairs, n_tiles tiles.
+int ensure_lists(dgs_ctx* ctx, ListBufs& lb, uint64_t n_inst, uint64_t n_pairs, int64_t n_tiles) {
+    size_t bytes[17];
+    list_bytes(n_inst, n_pairs, n_tiles, bytes);
+    for (int i = 0; i < 17; ++i) {
+        const int rc = ensure(ctx, *lb.all[i], bytes[i]);
+        if (rc) return rc;
+    }
     return DGS_OK;
 }
 
 // Per-view totals read back once (one stream synchronisation), view groups and workspace
 // sizing for the eager sequence.
-int readback_groups(dgs_ctx* ctx, Batch& B, cudaStream_t stream, Timer& tm) {
+int readback_groups(dgs_ctx* ctx, Batch& B, cudaStream_t stream, Timer& tm, size_t* need = nullptr) {
     const dgs_options& o = ctx->opt;
     const int V = B.V;
     int rc;
     tm.begin(DGS_K_SCAN);
     {
         uint64_t* d_rb = static_cast<uint64_t*>(ctx->readback.p);
-        k_view_totals<<<(V + 1 + 127) / 128, 128, 0, stream>>>(B.d_inst_off, B.d_pair_off, B.d_viewtab, V + 1, d_rb);
+        const ulonglong2* scan_total = B.n_parts > 0 ? static_cast<ulonglong2*>(ctx->parts.p) + B.n_parts : nullptr;
+        k_view_totals<<<(V + 1 + 127) / 128, 128, 0, stream>>>(B.d_inst_off, B.d_pair_off, B.d_viewtab, V + 1,
+                                                               scan_total, d_rb);
         ++ctx->launches;
+        DGS_CUDA(ctx, cudaMemsetAsync(d_rb + 2 * (V + 1), 0, sizeof(uint64_t), stream));
         DGS_CUDA(ctx, cudaMemcpyAsync(d_rb + 2 * (V + 1), B.d_err, sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream));
-        DGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_read, d_rb, sizeof(uint64_t) * 2 * (V + 1) + 8, cudaMemcpyDeviceToHost, stream));
+        DGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_read, d_rb, sizeof(uint64_t) * 2 * (V + 1) + 16, cudaMemcpyDeviceToHost, stream));
     }
     tm.end();
     DGS_CUDA(ctx, cudaGetLastError());
@@ -597,8 +664,9 @@ int readback_groups(dgs_ctx* ctx, Batch& B, cudaStream_t stream, Timer& tm) {
     const uint64_t* pair_at = h_rb + (V + 1);
     uint32_t errw = (uint32_t)(h_rb[2 * (V + 1)] & 0xFFFFFFFFu);
     if (errw & kErrPose) return fail(ctx, DGS_ERR_INVALID_ARG, "a node pose is not finite or not rigid");
-    ctx->stats.n_visible = (int64_t)inst_at[V];
-    if (inst_at[V] >= (1ull << 32)) return fail(ctx, DGS_ERR_CAPACITY, "more than 2^32 visible instances");
+    const uint64_t n_vis64 = h_rb[2 * (V + 1) + 1];
+    ctx->stats.n_visible = (int64_t)n_vis64;
+    if (n_vis64 >= (1ull << 32)) return fail(ctx, DGS_ERR_CAPACITY, "2^32 or more visible instances");
 
     // ---------------------------------------------------------------- groups
     std::vector<std::pair<int, int>> groups;
@@ -614,10 +682,14 @@ int readback_groups(dgs_ctx* ctx, Batch& B, cudaStream_t stream, Timer& tm) {
             split_at = 1;
             while (split_at < V - 1 && pair_at[split_at] < pair_at[V] / 2) ++split_at;
         }
+        auto tile_end = [&](int v) { return v < V ? (int64_t)B.views[v].tile_base : B.tiles_total; };
         for (int v = 0; v < V; ++v) {
             if (pair_at[v + 1] - pair_at[v] > kMaxPairs)
                 return fail(ctx, DGS_ERR_CAPACITY, "one view has more than 2^30 tile pairs");
-            if (v > v0 && (pair_at[v + 1] - pair_at[v0] > kMaxPairs || v - v0 >= cap_views || v == split_at)) {
+            if (tile_end(v + 1) - tile_end(v) > kMaxGroupTiles)
+                return fail(ctx, DGS_ERR_CAPACITY, "one view has 2^24 tiles or more");
+            if (v > v0 && (pair_at[v + 1] - pair_at[v0] > kMaxPairs || tile_end(v + 1) - tile_end(v0) > kMaxGroupTiles ||
+                           v - v0 >= cap_views || v == split_at)) {
                 groups.push_back({v0, v});
                 v0 = v;
             }
@@ -637,9 +709,17 @@ int readback_groups(dgs_ctx* ctx, Batch& B, cudaStream_t stream, Timer& tm) {
             return fail(ctx, DGS_ERR_CAPACITY, "view group exceeds 2^30 tile pairs");
     }
     max_bits = bits_for((uint64_t)max_tiles + 1);
-    if (max_bits > 31) return fail(ctx, DGS_ERR_CAPACITY, "more than 2^31 tiles in a view group");
+    if (max_bits > kTileBits) return fail(ctx, DGS_ERR_CAPACITY, "more than 2^24 - 1 tiles in a view group");
     ctx->stats.n_groups = (int32_t)groups.size();
     ctx->stats.key_bits = max_bits;
+    if (need) {   // a workspace query: the bytes of the lists, nothing allocated
+        size_t bytes[17];
+        list_bytes(max_inst, max_pairs, max_tiles, bytes);
+        size_t s = 0;
+        for (size_t b : bytes) s += b;
+        *need = s * (groups.size() > 1 ? 2 : 1);
+        return DGS_OK;
+    }
     if ((rc = ensure_lists(ctx, ctx->lists[0], max_inst, max_pairs, max_tiles))) return rc;
     if (groups.size() > 1 && (rc = ensure_lists(ctx, ctx->lists[1], max_inst, max_pairs, max_tiles))) return rc;
     B.groups = std::move(groups);
@@ -669,8 +749,7 @@ int prepare(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t*
 // Returns the tile-sorted instance numbers in *vals.
 void enqueue_lists(dgs_ctx* ctx, ListBufs& lb, const Batch& B, const Launch& L, Timer& tm, int v0, int v1, int n_tiles,
                    uint32_t inst_base, uint32_t n_inst, uint32_t n_bound, const uint32_t* d_inst, uint32_t* d_pairs,
-                   const Params& P, const uint32_t** vals) {
-    (void)ctx;
+                   const Params& P, const uint32_t** keys, const uint32_t** vals) {
     const int K = B.K;
     auto u32 = [](DevBuf& b) { return static_cast<uint32_t*>(b.p); };
     Record* rec = static_cast<Record*>(lb.records.p);
@@ -682,19 +761,24 @@ void enqueue_lists(dgs_ctx* ctx, ListBufs& lb, const Batch& B, const Launch& L, 
     tm.end();
     tm.begin(DGS_K_SORT);
     uint32_t *dk = nullptr, *order = nullptr;
+    SortCtl ctl;
+    if (ctx->opt.spin_limit_us > 0) ctl.spin_ns = (uint64_t)ctx->opt.spin_limit_us * 1000ull;
+    SortCtl depth_ctl = ctl;
+    if (ctx->opt.test_fault == 1) depth_ctl.mute_part = 1;
     launch_sort(L, u32(lb.dkey0), u32(lb.ival0), u32(lb.dkey1), u32(lb.ival1), n_inst, kZBits, u32(lb.hist),
-                u32(lb.status), u32(lb.counters), B.d_err, &dk, &order, d_inst);
-    launch_tile_scan(L, order, u32(lb.ntile), n_inst, d_inst, u32(lb.poff), u32(lb.tparts), n_bound, d_pairs);
+                u32(lb.status), u32(lb.counters), B.d_err, &dk, &order, d_inst, depth_ctl);
+    launch_tile_scan(L, order, u32(lb.ntile), n_inst, d_inst, u32(lb.poff), u32(lb.tparts), n_bound, d_pairs, B.d_err);
     launch_pairs(L, B.d_views, K, order, u32(lb.poff), rec, info, n_inst, d_inst, P, u32(lb.tkeys0),
                  u32(lb.tvals0), n_bound);
     uint32_t *tk = nullptr, *tv = nullptr;
     launch_sort(L, u32(lb.tkeys0), u32(lb.tvals0), u32(lb.tkeys1), u32(lb.tvals1), n_bound,
                 bits_for((uint64_t)n_tiles + 1), u32(lb.hist), u32(lb.status), u32(lb.counters), B.d_err, &tk,
-                &tv, d_pairs);
+                &tv, d_pairs, ctl);
     tm.end();
     tm.begin(DGS_K_RANGES);
     launch_ranges(L, tk, n_bound, static_cast<uint2*>(lb.ranges.p), n_tiles, d_pairs);
     tm.end();
+    *keys = tk;
     *vals = tv;
 }
 
@@ -702,6 +786,7 @@ void enqueue_lists(dgs_ctx* ctx, ListBufs& lb, const Batch& B, const Launch& L, 
 struct GroupLists {
     int v0 = 0, v1 = 0, n_tiles = 0;
     uint32_t n_bound = 0, n_inst = 0;
+    const uint32_t* keys = nullptr;
     const uint32_t* vals = nullptr;
     ListBufs* lb = nullptr;
     Params P{};
@@ -721,7 +806,76 @@ void build_group_lists(dgs_ctx* ctx, const Batch& B, int g, ListBufs& lb, cudaSt
     G.P.tile0 = tile0;
     G.lb = &lb;
     enqueue_lists(ctx, lb, B, L, tm, v0, v1, G.n_tiles, (uint32_t)B.inst_at[v0], G.n_inst, G.n_bound, nullptr,
-                  static_cast<uint32_t*>(ctx->totals.p) + g, G.P, &G.vals);
+                  static_cast<uint32_t*>(ctx->totals.p) + g, G.P, &G.keys, &G.vals);
+}
+
+// dgs_options.check_binning: reads view group g's tile lists back and checks them on the host
+// (Sec. III-A: every tile must receive, in depth order, the instances that reach it).  A
+// violation synchronises the device and returns DGS_ERR_CUDA with a description.
+int check_lists(dgs_ctx* ctx, const Batch& B, int g, const GroupLists& G, cudaStream_t s) {
+    (void)B;
+    uint32_t n = 0;
+    DGS_CUDA(ctx, cudaMemcpyAsync(&n, static_cast<uint32_t*>(ctx->totals.p) + g, sizeof(uint32_t),
+                                  cudaMemcpyDeviceToHost, s));
+    DGS_CUDA(ctx, cudaStreamSynchronize(s));
+    n = std::min(n, G.n_bound);
+    std::vector<uint32_t> keys(n), vals(n);
+    std::vector<uint2> ranges((size_t)std::max(G.n_tiles, 0));
+    std::vector<Record> rec(G.n_inst);
+    if (n) {
+        DGS_CUDA(ctx, cudaMemcpy(keys.data(), G.keys, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+        DGS_CUDA(ctx, cudaMemcpy(vals.data(), G.vals, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+    }
+    if (!ranges.empty())
+        DGS_CUDA(ctx, cudaMemcpy(ranges.data(), G.lb->ranges.p, sizeof(uint2) * ranges.size(), cudaMemcpyDeviceToHost));
+    if (!rec.empty())
+        DGS_CUDA(ctx, cudaMemcpy(rec.data(), G.lb->records.p, sizeof(Record) * rec.size(), cudaMemcpyDeviceToHost));
+    if (ctx->opt.test_fault == 2 && g == 0)
+        for (uint32_t i = 0; i + 1 < n; ++i)
+            if ((keys[i] & kTileMask) != (keys[i + 1] & kTileMask)) {
+                std::swap(keys[i], keys[i + 1]);
+                std::swap(vals[i], vals[i + 1]);
+                break;
+            }
+    const uint32_t n_sub = (uint32_t)(ctx->opt.tile_w * ctx->opt.tile_h / 32);
+    std::string why;
+    auto bad = [&](const std::string& what, uint64_t i) {
+        why = "binning invariant violated in view group " + std::to_string(g) + ": " + what + " at pair " +
+              std::to_string(i);
+        return false;
+    };
+    auto check = [&]() {
+        uint64_t covered = 0;
+        for (uint32_t i = 0; i < n; ++i) {
+            const uint32_t t = keys[i] & kTileMask, m = keys[i] >> kTileBits;
+            if (t >= (uint32_t)G.n_tiles) return bad("tile beyond the group", i);
+            if (i && t < (keys[i - 1] & kTileMask)) return bad("tiles not in order", i);
+            // an empty mask is valid: the ellipse meets the tile's rectangle of pixel centres only
+            // between two rows or columns of them, so no warp stages the pair
+            if (m >= (1u << n_sub)) return bad("sub-tile mask", i);
+            if (vals[i] >= G.n_inst) return bad("instance beyond the group", i);
+        }
+        for (int t = 0; t < G.n_tiles; ++t) {
+            const uint2 r = ranges[t];
+            if (r.x == r.y) continue;
+            if (r.x > r.y || r.y > n) return bad("range of tile " + std::to_string(t), r.x);
+            if ((r.x > 0 && (keys[r.x - 1] & kTileMask) == (uint32_t)t) || (r.y < n && (keys[r.y] & kTileMask) == (uint32_t)t))
+                return bad("range of tile " + std::to_string(t) + " not maximal", r.x);
+            for (uint32_t i = r.x; i < r.y; ++i) {
+                if ((keys[i] & kTileMask) != (uint32_t)t) return bad("range of tile " + std::to_string(t), i);
+                if (i > r.x) {
+                    const float z0 = rec[vals[i - 1]].r0.w, z1 = rec[vals[i]].r0.w;
+                    if (z1 < z0 || (z1 == z0 && vals[i] <= vals[i - 1])) return bad("depth order in a tile", i);
+                }
+            }
+            covered += r.y - r.x;
+        }
+        if (covered != n) return bad("ranges cover " + std::to_string(covered) + " of the pairs", n);
+        return true;
+    };
+    if (check()) return DGS_OK;
+    cudaDeviceSynchronize();
+    return fail(ctx, DGS_ERR_CUDA, why);
 }
 
 // Final synchronisation, device error word and kernel times.
@@ -780,9 +934,10 @@ int run_eager(dgs_ctx* ctx, Batch& B, float* out_rgb, float* out_depth, float* o
         const int b = g & 1;
         GroupLists G;
         build_group_lists(ctx, B, g, ctx->lists[b], streams[b], tms[b], G);
+        if (ctx->opt.check_binning && (rc = check_lists(ctx, B, g, G, streams[b]))) return rc;
         Launch Lg{streams[b], &ctx->launches};
         tms[b].begin(DGS_K_COMPOSITE);
-        launch_composite(Lg, B.d_views, G.v0, G.v1 - G.v0, G.n_tiles, static_cast<uint2*>(G.lb->ranges.p), G.vals,
+        launch_composite(Lg, B.d_views, G.v0, G.v1 - G.v0, G.n_tiles, static_cast<uint2*>(G.lb->ranges.p), G.keys, G.vals,
                          static_cast<Record*>(G.lb->records.p), G.P, out_rgb, out_depth, out_alpha, work);
         tms[b].end();
         DGS_CUDA(ctx, cudaGetLastError());
@@ -809,6 +964,7 @@ int run_eager(dgs_ctx* ctx, Batch& B, float* out_rgb, float* out_depth, float* o
 struct GraphGroups {
     int64_t t0[2], t1[2];
     uint64_t cap_inst[2], cap_pairs[2];
+    const ulonglong2* scan_total;         // 64-bit totals of the count scan (null: no entries)
     int32_t ng;
 };
 
@@ -819,7 +975,8 @@ struct GraphGroups {
 __global__ void k_graph_sizes(const uint32_t* __restrict__ inst_off, const uint64_t* __restrict__ pair_off,
                               GraphGroups G, uint32_t* sizes, uint32_t* err) {
     uint64_t ni[2] = {0, 0}, np[2] = {0, 0};
-    bool over = false;
+    // the 32-bit instance offsets wrap at 2^32: the scan's 64-bit total decides first
+    bool over = G.scan_total && G.scan_total->x >= (1ull << 32);
     for (int g = 0; g < G.ng; ++g) {
         ni[g] = (uint64_t)inst_off[G.t1[g]] - inst_off[G.t0[g]];
         np[g] = pair_off[G.t1[g]] - pair_off[G.t0[g]];
@@ -875,6 +1032,7 @@ int enqueue_graph_body(dgs_ctx* ctx, const Batch& B, const Launch& L, float* out
     const int vb[3] = {0, ng == 2 ? ctx->gsplit : B.V, B.V};
     GraphGroups G{};
     G.ng = ng;
+    G.scan_total = B.n_parts > 0 ? static_cast<ulonglong2*>(ctx->parts.p) + B.n_parts : nullptr;
     for (int g = 0; g < ng; ++g) {
         G.t0[g] = B.view_tab[vb[g]];
         G.t1[g] = B.view_tab[vb[g + 1]];
@@ -900,10 +1058,10 @@ int enqueue_graph_body(dgs_ctx* ctx, const Batch& B, const Launch& L, float* out
         P.gate = sizes + 2;
         P.inst_base_dev = sizes + 8 * g + 4;
         ListBufs& lb = ctx->lists[g];
-        const uint32_t* vals = nullptr;
+        const uint32_t *keys = nullptr, *vals = nullptr;
         enqueue_lists(ctx, lb, B, Lg, tg, v0, v1, n_tiles, 0u, (uint32_t)ctx->cap_inst[g],
-                      (uint32_t)ctx->cap_pairs[g], sizes + 8 * g, sizes + 8 * g + 3, P, &vals);
-        launch_composite(Lg, B.d_views, v0, v1 - v0, n_tiles, static_cast<uint2*>(lb.ranges.p), vals,
+                      (uint32_t)ctx->cap_pairs[g], sizes + 8 * g, sizes + 8 * g + 3, P, &keys, &vals);
+        launch_composite(Lg, B.d_views, v0, v1 - v0, n_tiles, static_cast<uint2*>(lb.ranges.p), keys, vals,
                          static_cast<Record*>(lb.records.p), P, out_rgb, out_depth, out_alpha, nullptr);
     }
     if (ng == 2) {
@@ -933,7 +1091,7 @@ int capture_graph(dgs_ctx* ctx, const Batch& B, float* out_rgb, float* out_depth
         const uint64_t need_inst = B.inst_at[v1] - B.inst_at[v0], need_pairs = B.pair_at[v1] - B.pair_at[v0];
         const int64_t n_tiles = (v1 < B.V ? B.views[v1].tile_base : B.tiles_total) - B.views[v0].tile_base;
         bits = std::max(bits, bits_for((uint64_t)std::max<int64_t>(n_tiles, 1) + 1));
-        if (need_pairs > kMaxPairs || bits > 31 || need_inst >= (1ull << 31)) return DGS_OK;
+        if (need_pairs > kMaxPairs || bits > kTileBits || need_inst >= (1ull << 31)) return DGS_OK;
         const uint64_t ci = need_inst + need_inst / 4 + 1024;
         const uint64_t cp = std::min<uint64_t>(kMaxPairs, need_pairs + need_pairs / 4 + 4096);
         ctx->cap_inst[g] = same_split ? std::max(ctx->cap_inst[g], ci) : ci;
@@ -1075,6 +1233,15 @@ int dgs_context_create(dgs_ctx** out, const dgs_options* opt) {
     return DGS_OK;
 }
 
+int dgs_set_options(dgs_ctx* ctx, const dgs_options* opt) {
+    if (!ctx || !opt) return DGS_ERR_INVALID_ARG;
+    std::string why;
+    if (!check_options(opt, why)) return fail(ctx, DGS_ERR_INVALID_ARG, "options: " + why);
+    ctx->opt = *opt;
+    drop_graph(ctx);      // captured kernels carry the old options
+    return DGS_OK;
+}
+
 int dgs_context_destroy(dgs_ctx* ctx) {
     if (!ctx) return DGS_OK;
     cudaDeviceSynchronize();
@@ -1117,6 +1284,28 @@ int dgs_workspace_query(const dgs_ctx* ctx, size_t* bytes) {
     for (const ListBufs& lb : ctx->lists)
         for (const DevBuf* b : lb.all) s += b->bytes;
     *bytes = s;
+    return DGS_OK;
+}
+
+int dgs_workspace_query_batch(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids,
+                              int32_t n_envs, int32_t max_nodes, const float* node_poses, const dgs_camera* cams,
+                              const int32_t* cams_per_env, int32_t max_cams, const int64_t* view_pixel_offset,
+                              size_t* bytes, void* stream_) {
+    if (!ctx) return DGS_ERR_INVALID_ARG;
+    begin_call(ctx);
+    if (!bytes) return fail(ctx, DGS_ERR_INVALID_ARG, "bytes is required");
+    *bytes = 0;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    Timer tm{ctx, stream, false};
+    Batch B;
+    int rc = stage(ctx, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env, max_cams,
+                   nullptr, nullptr, view_pixel_offset, nullptr, stream, tm, B, false);
+    if (rc != DGS_OK || B.V == 0) return rc;
+    Launch L{stream, &ctx->launches};
+    launch_front(ctx, B, L, tm);
+    size_t lists = 0;
+    if ((rc = readback_groups(ctx, B, stream, tm, &lists))) return rc;
+    *bytes = B.front_bytes + lists;
     return DGS_OK;
 }
 
@@ -1239,21 +1428,42 @@ int dgs_render_backward(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, co
     uint64_t max_inst = 1;
     for (auto& g : B.groups) max_inst = std::max<uint64_t>(max_inst, B.inst_at[g.second] - B.inst_at[g.first]);
     if ((rc = ensure(ctx, ctx->inst_grad, sizeof(float) * 10 * max_inst))) return rc;
+    unsigned long long* n_red = nullptr;
+    if (ctx->opt.profile >= 2) {
+        n_red = reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->errword.p) + 56);
+        DGS_CUDA(ctx, cudaMemsetAsync(n_red, 0, sizeof(unsigned long long), stream));
+    }
     for (int g = 0; g < (int)B.groups.size(); ++g) {
         GroupLists G;
         build_group_lists(ctx, B, g, ctx->lists[0], stream, tm, G);
         tm.begin(DGS_K_BACKWARD);
         DGS_CUDA(ctx, cudaMemsetAsync(ctx->inst_grad.p, 0, sizeof(float) * 10 * std::max<uint32_t>(G.n_inst, 1), stream));
-        launch_composite_bwd(L, B.d_views, G.v0, G.v1 - G.v0, G.n_tiles, static_cast<uint2*>(G.lb->ranges.p), G.vals,
+        launch_composite_bwd(L, B.d_views, G.v0, G.v1 - G.v0, G.n_tiles, static_cast<uint2*>(G.lb->ranges.p), G.keys, G.vals,
                              static_cast<Record*>(G.lb->records.p), G.P, out_rgb, out_depth, grad_rgb, grad_depth,
-                             static_cast<float*>(ctx->inst_grad.p));
+                             static_cast<float*>(ctx->inst_grad.p), n_red);
+        tm.end();
+        tm.begin(DGS_K_BACKWARD_PROJECT);
         launch_project_bwd(L, B.dtype_mask, B.d_nodes, B.n_nodes, B.d_views, B.d_vnodes, B.K, node_poses,
                            static_cast<InstInfo*>(G.lb->info.p), static_cast<float*>(ctx->inst_grad.p), G.n_inst, G.P,
                            B.d_grads, grad_poses);
         tm.end();
         DGS_CUDA(ctx, cudaGetLastError());
     }
-    return finish(ctx, B, stream);
+    rc = finish(ctx, B, stream);
+    if (rc == DGS_OK && n_red) {
+        unsigned long long h = 0;
+        DGS_CUDA(ctx, cudaMemcpy(&h, n_red, sizeof(h), cudaMemcpyDeviceToHost));
+        ctx->stats.bwd_reductions = (int64_t)h;
+    }
+    return rc;
+}
+
+int dgs_pose_twist_grad(const float* poses, const float* grad_poses, int64_t n, float* out_twist, void* stream_) {
+    if (n < 0 || (n > 0 && (!poses || !grad_poses || !out_twist))) return DGS_ERR_INVALID_ARG;
+    if (n == 0) return DGS_OK;
+    int64_t launches = 0;
+    launch_pose_twist(Launch{reinterpret_cast<cudaStream_t>(stream_), &launches}, poses, grad_poses, n, out_twist);
+    return cudaGetLastError() == cudaSuccess ? DGS_OK : DGS_ERR_CUDA;
 }
 
 int dgs_set_augment(dgs_ctx* ctx, const dgs_augment* aug, int32_t n_views, const uint8_t* overlay,

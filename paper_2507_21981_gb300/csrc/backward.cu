@@ -56,14 +56,17 @@ __device__ __forceinline__ float warp_transpose_sum16(const float (&v)[16], int 
 
 // ------------------------------------------------------------------ K7
 __global__ void __launch_bounds__(256) k_composite_bwd(const ViewDesc* __restrict__ views, int v0, int nv,
-                                                       const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
+                                                       const uint2* __restrict__ ranges, const uint32_t* __restrict__ keys,
+                                                       const uint32_t* __restrict__ vals,
                                                        const Record* __restrict__ rec, Params P,
                                                        const float* __restrict__ out_rgb,
                                                        const float* __restrict__ out_depth,
                                                        const float* __restrict__ g_rgb,
-                                                       const float* __restrict__ g_depth, float* __restrict__ ig) {
+                                                       const float* __restrict__ g_depth, float* __restrict__ ig,
+                                                       unsigned long long* __restrict__ n_red) {
     __shared__ float4 s_rec[8][3][32];
     __shared__ uint32_t s_idx[8][32];
+    if (sort_failed(P.err)) return;
     const int gt = blockIdx.x;
     const int ga = gt + P.tile0;
     int lo = v0, hi = v0 + nv - 1;
@@ -92,35 +95,26 @@ __global__ void __launch_bounds__(256) k_composite_bwd(const ViewDesc* __restric
     }
     if (__all_sync(0xffffffffu, gC0 == 0.f && gC1 == 0.f && gC2 == 0.f && gD == 0.f)) return;
     const uint2 range = ranges[gt];
+    uint32_t reds = 0;
     float T = 1.f, P0 = 0.f, P1 = 0.f, P2 = 0.f, PD = 0.f;
     bool done = !inside;
     const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t wbit = 1u << (kTileBits + w);
     float4* const sr0 = s_rec[w][0];
     float4* const sr1 = s_rec[w][1];
     float4* const sr2 = s_rec[w][2];
     for (uint32_t base = range.x; base < range.y; base += 32) {
         if (__all_sync(0xffffffffu, done)) break;
         const uint32_t i = base + lane;
-        bool rel = false;
-        float4 a, q, col;
-        uint32_t idx = 0;
-        if (i < range.y) {
-            idx = vals[i];
-            const Record* r = rec + idx;
-            q = r->r1;
-            const uint32_t bx = __float_as_uint(q.w), by = __float_as_uint(r->r2.w);
-            if ((int)(bx & 0xFFFFu) <= wx1 && (int)(bx >> 16) >= wx0 && (int)(by & 0xFFFFu) <= wy1 && (int)(by >> 16) >= wy0) {
-                a = r->r0;
-                col = r->r2;
-                rel = ellipse_meets(q.x, q.y, q.z, P.qbin, (float)wx0 + 0.5f - a.x, (float)wx1 + 0.5f - a.x,
-                                      (float)wy0 + 0.5f - a.y, (float)wy1 + 0.5f - a.y);
-            }
-        }
+        // the forward pass's staging: entries whose sub-tile mask holds this warp's bit
+        const bool rel = i < range.y && (__ldg(keys + i) & wbit);
         const uint32_t m = __ballot_sync(0xffffffffu, rel);
         if (m == 0) continue;
         if (rel) {
+            const uint32_t idx = __ldg(vals + i);
+            const Record* r = rec + idx;
             const int pos = __popc(m & lt);
-            sr0[pos] = a; sr1[pos] = q; sr2[pos] = col;
+            sr0[pos] = r->r0; sr1[pos] = r->r1; sr2[pos] = r->r2;
             s_idx[w][pos] = idx;
         }
         __syncwarp();
@@ -176,10 +170,13 @@ __global__ void __launch_bounds__(256) k_composite_bwd(const ViewDesc* __restric
             for (int e = 0; e < 16; ++e) v16[e] = e < G_N ? g[e] : 0.f;
             const float tot = warp_transpose_sum16(v16, lane);
             const int e = lane >> 1;
-            if ((lane & 1) == 0 && e < G_N && tot != 0.f) atomicAdd(ig + (size_t)r * G_N + e, tot);
+            const bool add = (lane & 1) == 0 && e < G_N && tot != 0.f;
+            if (add) atomicAdd(ig + (size_t)r * G_N + e, tot);
+            if (n_red) reds += __popc(__ballot_sync(0xffffffffu, add));
         }
         __syncwarp();
     }
+    if (n_red && lane == 0 && reds) atomicAdd(n_red, (unsigned long long)reds);
 }
 
 // ------------------------------------------------------------------ K8
@@ -269,9 +266,9 @@ __global__ void __launch_bounds__(128) k_project_bwd(const NodeDesc* __restrict_
         R[1][0] = 2.f * (x_ * y_ + w_ * z_); R[1][1] = 1.f - 2.f * (x_ * x_ + z_ * z_); R[1][2] = 2.f * (y_ * z_ - w_ * x_);
         R[2][0] = 2.f * (x_ * z_ - w_ * y_); R[2][1] = 2.f * (y_ * z_ + w_ * x_); R[2][2] = 1.f - 2.f * (x_ * x_ + y_ * y_);
         const float s[3] = {s0, s1, s2};
-        const float z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[8], mx), __fmul_rn(M[9], my)), __fmul_rn(M[10], mz)), M[11]);
-        const float tx = fmaf(M[0], mx, fmaf(M[1], my, fmaf(M[2], mz, M[3])));
-        const float ty = fmaf(M[4], mx, fmaf(M[5], my, fmaf(M[6], mz, M[7])));
+        const float z = camera_depth(vn, mx, my, mz);
+        const float tx = camera_row(vn, 0, mx, my, mz);
+        const float ty = camera_row(vn, 1, mx, my, mz);
         const float iz = 1.f / z;
         const float xr = tx * iz, yr = ty * iz;
         const bool clx = xr > vd.limx || xr < -vd.limx, cly = yr > vd.limy || yr < -vd.limy;
@@ -460,15 +457,46 @@ __global__ void __launch_bounds__(128) k_project_bwd(const NodeDesc* __restrict_
     }
 }
 
+// Sec. III-B / IV: se(3) gradient of a rigid pose under a left perturbation.  With
+// T' = exp(xi^) T, xi = (rho, phi), to first order R' = R + [phi]x R and t' = t + [phi]x t + rho,
+// so dL = G_R : ([phi]x R) + G_t . ([phi]x t) + G_t . rho.  Writing A = G_R R^T + G_t t^T, the
+// phi part is sum_ij A_ij ([phi]x)_ij = phi . (A_21 - A_12, A_02 - A_20, A_10 - A_01) (0-based),
+// and the rho part is G_t.  One thread per pose.
+__global__ void k_pose_twist(const float* __restrict__ poses, const float* __restrict__ grads, int64_t n,
+                             float* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float* T = poses + i * 12;
+    const float* G = grads + i * 12;
+    float A[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            A[a][b] = fmaf(G[a * 4 + 0], T[b * 4 + 0], fmaf(G[a * 4 + 1], T[b * 4 + 1], fmaf(G[a * 4 + 2], T[b * 4 + 2],
+                                                                                        G[a * 4 + 3] * T[b * 4 + 3])));
+    float* o = out + i * 6;
+    o[0] = G[3]; o[1] = G[7]; o[2] = G[11];
+    o[3] = A[2][1] - A[1][2];
+    o[4] = A[0][2] - A[2][0];
+    o[5] = A[1][0] - A[0][1];
+}
+
 }  // namespace
 
+void launch_pose_twist(const Launch& L, const float* poses, const float* grads, int64_t n, float* out) {
+    if (n <= 0) return;
+    k_pose_twist<<<(unsigned)((n + 127) / 128), 128, 0, L.stream>>>(poses, grads, n, out);
+    ++*L.launches;
+}
+
 void launch_composite_bwd(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
-                          const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,
-                          const float* out_rgb, const float* out_depth, const float* g_rgb, const float* g_depth,
-                          float* inst_grad) {
+                          const uint2* ranges, const uint32_t* keys, const uint32_t* vals, const Record* records,
+                          const Params& P, const float* out_rgb, const float* out_depth, const float* g_rgb,
+                          const float* g_depth, float* inst_grad, unsigned long long* n_red) {
     if (n_tiles == 0) return;
-    k_composite_bwd<<<n_tiles, P.tile_w * P.tile_h, 0, L.stream>>>(views, v0, n_group_views, ranges, vals, records, P,
-                                                                   out_rgb, out_depth, g_rgb, g_depth, inst_grad);
+    k_composite_bwd<<<n_tiles, P.tile_w * P.tile_h, 0, L.stream>>>(views, v0, n_group_views, ranges, keys, vals, records, P,
+                                                                   out_rgb, out_depth, g_rgb, g_depth, inst_grad, n_red);
     ++*L.launches;
 }
 

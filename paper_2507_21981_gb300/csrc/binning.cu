@@ -29,7 +29,9 @@ __device__ __forceinline__ uint32_t block_sum(uint32_t x) {
 // parts[b] = sum of ntile[order[i]] over partition b
 __global__ void __launch_bounds__(kScanThreads) k_tscan_partial(const uint32_t* __restrict__ order,
                                                                const uint32_t* __restrict__ ntile, uint32_t n,
-                                                               const uint32_t* __restrict__ d_n, uint32_t* parts) {
+                                                               const uint32_t* __restrict__ d_n, uint32_t* parts,
+                                                               const uint32_t* err) {
+    if (sort_failed(err)) return;
     n = live(n, d_n);
     const uint32_t base = blockIdx.x * (uint32_t)kScanTile;
     if (base >= n) return;
@@ -82,8 +84,10 @@ __global__ void __launch_bounds__(kScanThreads) k_tscan_parts(uint32_t* parts, u
 __global__ void __launch_bounds__(kScanThreads) k_tscan_final(const uint32_t* __restrict__ order,
                                                              const uint32_t* __restrict__ ntile, uint32_t n,
                                                              const uint32_t* __restrict__ d_n,
-                                                             const uint32_t* __restrict__ parts, uint32_t* poff) {
+                                                             const uint32_t* __restrict__ parts, uint32_t* poff,
+                                                             const uint32_t* err) {
     __shared__ uint32_t s_w[kScanThreads / 32];
+    if (sort_failed(err)) return;
     n = live(n, d_n);
     const uint32_t base = blockIdx.x * (uint32_t)kScanTile;
     if (base >= n) return;
@@ -116,6 +120,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tscan_final(const uint32_t* __
 struct PairWarp {
     float4 a[32];          // (u, v, qa, qb)
     float4 b[32];          // (qc, x-box, y-box, tile origin)
+    float4 e[32];          // ellipse_extent of the instance
     int4 c[32];            // (rectangle width in tiles, first tile of the view in the group, view tiles_x, record)
     uint32_t excl[32], off[32], end[32], run[32];
 };
@@ -129,6 +134,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(const ViewDesc* __res
                                                           uint32_t* __restrict__ tkeys, uint32_t* __restrict__ tvals,
                                                           uint32_t cap) {
     __shared__ PairWarp pw[kPairWarps];
+    if (sort_failed(P.err)) return;
     n = live(n, d_n);
     const uint32_t w = (blockIdx.x * (uint32_t)blockDim.x + threadIdx.x) >> 5;
     if (w * 32u >= n) return;
@@ -148,6 +154,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(const ViewDesc* __res
         const ViewDesc& vd = views[info[r].view / (uint32_t)K];
         S.a[lane] = make_float4(r0.x, r0.y, r1.x, r1.y);
         S.b[lane] = make_float4(r1.z, r1.w, byf, pack_u16x2((uint32_t)tx0, (uint32_t)ty0));
+        S.e[lane] = ellipse_extent(r1.x, r1.y, r1.z, P.qbin);
         S.c[lane] = make_int4(tx1 - tx0 + 1, vd.tile_base - P.tile0, vd.tiles_x, (int)r);
         S.off[lane] = poff[item];
         S.end[lane] = poff[item + 1];
@@ -179,7 +186,11 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(const ViewDesc* __res
         if (hit) {
             const uint32_t pos = S.off[o] + S.run[o] + __popc(peers & lt);
             if (pos < S.end[o] && pos < cap) {
-                tkeys[pos] = (uint32_t)(cc.y + ty * cc.z + tx);
+                const float4 a = S.a[o], b = S.b[o];
+                const uint32_t bx = __float_as_uint(b.y), by = __float_as_uint(b.z);
+                const uint32_t sub = subtile_mask(a.x, a.y, a.z, a.w, b.x, S.e[o], (int)(bx & 0xFFFFu), (int)(bx >> 16),
+                                                  (int)(by & 0xFFFFu), (int)(by >> 16), tx, ty, P);
+                tkeys[pos] = (uint32_t)(cc.y + ty * cc.z + tx) | (sub << kTileBits);
                 tvals[pos] = (uint32_t)cc.w;
             } else {
                 atomicOr(P.err, pos < cap ? kErrMismatch : kErrCapacity);
@@ -204,11 +215,11 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(const ViewDesc* __res
 size_t tile_scan_parts(uint32_t n) { return ((size_t)n + kScanTile - 1) / kScanTile + 1; }
 
 void launch_tile_scan(const Launch& L, const uint32_t* order, const uint32_t* ntile, uint32_t n, const uint32_t* d_n,
-                      uint32_t* poff, uint32_t* parts, uint32_t cap, uint32_t* total) {
+                      uint32_t* poff, uint32_t* parts, uint32_t cap, uint32_t* total, const uint32_t* err) {
     const uint32_t blocks = (n + kScanTile - 1) / kScanTile;
-    if (blocks) k_tscan_partial<<<blocks, kScanThreads, 0, L.stream>>>(order, ntile, n, d_n, parts);
+    if (blocks) k_tscan_partial<<<blocks, kScanThreads, 0, L.stream>>>(order, ntile, n, d_n, parts, err);
     k_tscan_parts<<<1, kScanThreads, 0, L.stream>>>(parts, n, d_n, poff, cap, total);
-    if (blocks) k_tscan_final<<<blocks, kScanThreads, 0, L.stream>>>(order, ntile, n, d_n, parts, poff);
+    if (blocks) k_tscan_final<<<blocks, kScanThreads, 0, L.stream>>>(order, ntile, n, d_n, parts, poff, err);
     *L.launches += blocks ? 3 : 1;
 }
 

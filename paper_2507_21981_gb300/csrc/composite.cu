@@ -12,8 +12,8 @@
 namespace dgs {
 namespace {
 
-// Thread = 4 consecutive sorted keys (one 16-byte load); a run starts where the key differs
-// from the one before and ends where it differs from the one after.
+// Thread = 4 consecutive sorted keys (one 16-byte load); a run starts where the key's tile
+// differs from the one before and ends where it differs from the one after.
 __global__ void k_ranges(const uint32_t* __restrict__ keys, uint32_t n, const uint32_t* __restrict__ d_n,
                          uint2* __restrict__ ranges, int n_tiles) {
     const uint32_t i4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4u;
@@ -30,6 +30,8 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, uint32_t n, const ui
     k[0] = i4 > 0 ? keys[i4 - 1] : 0u;
     k[5] = i4 + 4 < n ? keys[i4 + 4] : 0u;
 #pragma unroll
+    for (int j = 0; j < 6; ++j) k[j] &= kTileMask;
+#pragma unroll
     for (int j = 0; j < 4; ++j) {
         const uint32_t i = i4 + j;
         if (i >= n) break;
@@ -42,17 +44,20 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, uint32_t n, const ui
 
 // Block = one tile, warp = one 8x4 sub-tile, lane = one pixel.  Warps are independent (no
 // block barrier): each walks the tile's list 32 entries at a time, keeps the entries whose
-// pixel box overlaps its sub-tile and whose ellipse reaches one of its pixel centres (exact
-// test with the binning margin), stages them in list order in its own shared memory and
-// composites them; it stops once its 32 pixels have terminated.  AUG: the view's image
-// randomisation is applied to the RGB before it is stored.
+// sub-tile mask (written by binning: the ellipse reaches a pixel centre of the sub-tile, exact
+// test with the binning margin) holds its bit -- one coalesced key load and a ballot per 32
+// entries -- gathers their records into its own shared memory in list order and composites
+// them; it stops once its 32 pixels have terminated.  AUG: the view's image randomisation is
+// applied to the RGB before it is stored.
 template <bool COUNT, bool AUG>
 __global__ void __launch_bounds__(256, 6) k_composite(const ViewDesc* __restrict__ views, int v0, int nv,
-                                                   const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
+                                                   const uint2* __restrict__ ranges, const uint32_t* __restrict__ keys,
+                                                   const uint32_t* __restrict__ vals,
                                                    const Record* __restrict__ rec, Params P, float* __restrict__ out_rgb,
                                                    float* __restrict__ out_depth, float* __restrict__ out_alpha,
                                                    unsigned long long* __restrict__ work) {
     __shared__ float4 s_rec[8][3][32];
+    if (sort_failed(P.err)) return;            // the lists are not valid: nothing to composite
     const int gt = blockIdx.x;                 // tile within the group
     const int ga = gt + P.tile0;               // tile within the call
     // view of this tile: last view of the group whose tile_base <= ga
@@ -76,6 +81,7 @@ __global__ void __launch_bounds__(256, 6) k_composite(const ViewDesc* __restrict
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
     bool done = !inside;
     const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t wbit = 1u << (kTileBits + w);
     float4* const sr0 = s_rec[w][0];
     float4* const sr1 = s_rec[w][1];
     float4* const sr2 = s_rec[w][2];
@@ -83,22 +89,12 @@ __global__ void __launch_bounds__(256, 6) k_composite(const ViewDesc* __restrict
     for (uint32_t base = range.x; base < range.y; base += 32) {
         if (__all_sync(0xffffffffu, done)) break;
         const uint32_t i = base + lane;
-        bool rel = false;
-        float4 a, q, col;
-        if (i < range.y) {
-            const Record* r = rec + vals[i];
-            q = r->r1;
-            const uint32_t bx = __float_as_uint(q.w), by = __float_as_uint(r->r2.w);
-            if ((int)(bx & 0xFFFFu) <= wx1 && (int)(bx >> 16) >= wx0 && (int)(by & 0xFFFFu) <= wy1 && (int)(by >> 16) >= wy0) {
-                a = r->r0;
-                col = r->r2;
-                rel = ellipse_meets(q.x, q.y, q.z, P.qbin, (float)wx0 + 0.5f - a.x, (float)wx1 + 0.5f - a.x,
-                                    (float)wy0 + 0.5f - a.y, (float)wy1 + 0.5f - a.y);
-            }
-        }
+        const bool rel = i < range.y && (__ldg(keys + i) & wbit);
         const uint32_t m = __ballot_sync(0xffffffffu, rel);
         if (m == 0) continue;
         if (rel) {
+            const Record* r = rec + __ldg(vals + i);
+            const float4 a = r->r0, q = r->r1, col = r->r2;
             const int pos = __popc(m & lt);
             sr0[pos] = a; sr2[pos] = col;
             sr1[pos] = make_float4(kHalfLog2e * q.x, q.y, kHalfLog2e * q.z, 0.f);
@@ -158,12 +154,12 @@ void launch_ranges(const Launch& L, const uint32_t* keys, uint32_t n, uint2* ran
 }
 
 void launch_composite(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
-                      const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,
-                      float* out_rgb, float* out_depth, float* out_alpha, unsigned long long* work) {
+                      const uint2* ranges, const uint32_t* keys, const uint32_t* vals, const Record* records,
+                      const Params& P, float* out_rgb, float* out_depth, float* out_alpha, unsigned long long* work) {
     if (n_tiles == 0) return;
     auto* kern = work ? (P.aug ? k_composite<true, true> : k_composite<true, false>)
                       : (P.aug ? k_composite<false, true> : k_composite<false, false>);
-    kern<<<n_tiles, P.tile_w * P.tile_h, 0, L.stream>>>(views, v0, n_group_views, ranges, vals, records, P, out_rgb,
+    kern<<<n_tiles, P.tile_w * P.tile_h, 0, L.stream>>>(views, v0, n_group_views, ranges, keys, vals, records, P, out_rgb,
                                                         out_depth, out_alpha, work);
     ++*L.launches;
 }

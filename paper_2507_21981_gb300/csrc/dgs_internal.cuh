@@ -7,6 +7,9 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <string>
+#include <vector>
+
 #include "dgs.h"
 
 namespace dgs {
@@ -15,6 +18,12 @@ constexpr int kWarp = 32;
 constexpr int kChunk = 32;           // Gaussians per chunk: one warp projects one chunk
 constexpr int kZBits = 28;           // bits of the depth field of a sort key
 constexpr uint32_t kMaxPairs = (1u << 30) - 1;   // per view group (30-bit scan counters)
+// Tile keys of the (tile, instance) pairs: bits 0..23 the tile within the view group, bits
+// 24..31 the mask of the tile's 8x4-pixel sub-tiles that the instance's ellipse reaches (bit
+// s = sub-tile (s mod (tile_w/8), s div (tile_w/8))).  The tile sort radixes bits 0..23 only.
+constexpr int kTileBits = 24;
+constexpr uint32_t kTileMask = (1u << kTileBits) - 1u;
+constexpr int64_t kMaxGroupTiles = (1ll << kTileBits) - 1;   // a view group's tiles (the dead key sorts last)
 
 // Device error word bits (ctx status).
 constexpr uint32_t kErrPose = 1u;       // non-finite or non-rigid node pose
@@ -50,11 +59,56 @@ struct ViewDesc {
 
 // Per (view, slot): the node and its camera_from_node transform.
 struct VNode {
-    float M[12];          // camera_from_node; row 2 composed in binary32 without FMA
+    float M[12];          // camera_from_node, row-major 3x4 (leading parts)
+    float Ml[12];         // trailing parts: camera_from_node = M + Ml to about 2^-48
     float o[3];           // camera centre in the node frame
     int32_t node;         // -1 = empty slot
     int64_t tab;          // count-table index of the node's first chunk in this view
 };
+
+// Error-free transformations in binary32 (Knuth's TwoSum; TwoProduct by a fused multiply-add):
+// a + b = s + e and a * b = p + e exactly, barring overflow and underflow.  The _rn intrinsics
+// keep the compiler from contracting or reassociating them.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// Row r of camera_from_node applied to a node-frame point, faithfully rounded.  With the row
+// held as M + Ml, the products M_j m_j and the sums are carried as unevaluated (value, error)
+// pairs (the compensated dot product of Ogita, Rump and Oishi, 2005); the Ml terms, of relative
+// size 2^-24, enter the error sum directly.  The result differs from the exact value for the
+// FP32 inputs by at most 2^-24 |result| plus terms of order 2^-48 times the magnitude of the
+// summands: within one unit in the last place, whatever the scene.
+__device__ __forceinline__ float camera_row(const VNode& vn, int r, float mx, float my, float mz) {
+    const float* M = vn.M + 4 * r;
+    const float* L = vn.Ml + 4 * r;
+    float p, s, h, e, q;
+    two_prod(M[0], mx, p, s);
+    two_prod(M[1], my, h, e);
+    two_sum(p, h, p, q);
+    s = __fadd_rn(s, __fadd_rn(q, e));
+    two_prod(M[2], mz, h, e);
+    two_sum(p, h, p, q);
+    s = __fadd_rn(s, __fadd_rn(q, e));
+    two_sum(p, M[3], p, q);
+    s = __fadd_rn(s, q);
+    s = __fmaf_rn(L[0], mx, s);
+    s = __fmaf_rn(L[1], my, s);
+    s = __fmaf_rn(L[2], mz, s);
+    s = __fadd_rn(s, L[3]);
+    return __fadd_rn(p, s);
+}
+
+// Sec. III-A (depth sorting): the depth key is the camera-space z, faithfully rounded.
+__device__ __forceinline__ float camera_depth(const VNode& vn, float mx, float my, float mz) {
+    return camera_row(vn, 2, mx, my, mz);
+}
 
 struct Params {
     float z_near, lowpass, alpha_min, alpha_max, t_min, q_max, guard;
@@ -96,6 +150,39 @@ struct NodeView {
     int32_t slot;
     int64_t tab;          // count-table index of the node's first chunk in this view
 };
+
+// Host side of one batch, shared by every entry point that renders: the validated arguments
+// as the tables the kernels read.  View v enumerates (env, camera) env-major; the count table
+// lists, per view, the 32-Gaussian chunks of its nodes in node-id order.
+struct HostTables {
+    std::vector<NodeDesc> nodes;
+    std::vector<ViewDesc> views;
+    std::vector<int> view_env, view_cam;
+    std::vector<int32_t> slot_node;    // [V*K] node drawn in slot j of view v's env (-1 = empty)
+    std::vector<int64_t> vnode_tab;    // [V*K] count-table entry of (view, slot)'s first chunk
+    std::vector<int64_t> view_tab;     // [V+1] first count-table entry of each view; [V] = T
+    std::vector<int32_t> pmap;         // [V*(2K+1)] plain mode: per view, chunk prefix and slot of
+                                       // each present node in node-id order
+    std::vector<int32_t> nv_off;       // [n_nodes+1] node -> its (view, slot) entries in nv
+    std::vector<NodeView> nv;
+    int dtype_mask = 0;                // storage types present (bit = dgs_dtype)
+    int64_t chunk_total = 0, tiles_total = 0, pix_total = 0, n_instances = 0;
+    int64_t T = 0;                     // count-table entries
+};
+
+// Validates options (0 = invalid, with the reason in `why`).
+int check_options(const dgs_options* o, std::string& why);
+
+// Kernel parameters from options (no group offset, error word or randomisation set).
+Params make_params(const dgs_options& o);
+
+// Validates a render call's arguments (everything that can be checked on the host: shapes, node
+// ids, camera intrinsics and extrinsics, pixel offsets) and builds its HostTables.  Returns
+// DGS_OK or the status to report, with the reason in `why`.  Makes no CUDA call.
+int build_host_tables(const dgs_options& o, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids,
+                      int32_t n_envs, int32_t max_nodes, const float* node_poses, const dgs_camera* cams,
+                      const int32_t* cams_per_env, int32_t max_cams, const int64_t* view_pixel_offset, HostTables& H,
+                      std::string& why);
 
 template <int DT>
 __device__ __forceinline__ float ld_attr(const void* p, int64_t i) {
@@ -247,6 +334,51 @@ __device__ __forceinline__ bool tile_hit(float u, float v, float qa, float qb, f
                          (float)py1 + 0.5f - v);
 }
 
+// Sec. III-A (tile binning at the compositor's granularity).  The ellipse {q <= qlim},
+// q = qa (dx + qb dy)^2 + qc dy^2, spans dy in [-ye, ye], ye = sqrt(qlim / qc); at a given dy its
+// x-section is -qb dy -+ sqrt((qlim - qc dy^2) / qa).  Its leftmost point lies at
+// dy_L = qb sqrt(qa qlim / (qc (qc + qa qb^2))) and its rightmost at -dy_L.  Per-instance
+// constants of the sub-tile test: (ye, dy_L, 1/qa).
+__device__ __forceinline__ float4 ellipse_extent(float qa, float qb, float qc, float qlim) {
+    const float ye = sqrtf(qlim / qc);
+    const float dyl = qb * sqrtf(qa * qlim / (qc * fmaf(qa * qb, qb, qc)));
+    return make_float4(ye, dyl, 1.f / qa, 0.f);
+}
+
+// Mask of the 8x4-pixel sub-tiles of tile (tx, ty) in which the ellipse holds a pixel centre's
+// rectangle point: per row of sub-tiles (a band of 4 pixel rows, clipped to the instance's pixel
+// box [y0, y1]) the part of the ellipse in the band is convex, so its x-extent is one interval,
+// [x_lo(clamp(dy_L)), x_hi(clamp(-dy_L))] with the lower boundary convex and the upper concave in
+// dy; a sub-tile of that row is hit iff its columns (clipped to [x0, x1]) meet the interval.
+// This is exact for the rectangles of pixel centres (the test of ellipse_meets on each sub-tile)
+// up to rounding, which the binning limit's 0.1 % + 1e-3 margin covers; without the exact test
+// every sub-tile the box overlaps is set.
+__device__ __forceinline__ uint32_t subtile_mask(float u, float v, float qa, float qb, float qc, const float4& ext,
+                                                 int x0, int x1, int y0, int y1, int tx, int ty, const Params& P) {
+    const int sub_cols = P.tile_w >> 3, sub_rows = P.tile_h >> 2;
+    uint32_t m = 0;
+    for (int sy = 0; sy < sub_rows; ++sy) {
+        const int ry = ty * P.tile_h + sy * 4;
+        const int py0 = max(ry, y0), py1 = min(ry + 3, y1);
+        if (py0 > py1) continue;
+        float xlo = -INFINITY, xhi = INFINITY;
+        if (P.exact_tile_test) {
+            const float Y0 = fmaxf((float)py0 + 0.5f - v, -ext.x), Y1 = fminf((float)py1 + 0.5f - v, ext.x);
+            if (Y0 > Y1) continue;
+            const float dl = fminf(Y1, fmaxf(Y0, ext.y)), dr = fminf(Y1, fmaxf(Y0, -ext.y));
+            xlo = fmaf(-qb, dl, -sqrtf(fmaxf(0.f, fmaf(-qc * dl, dl, P.qbin)) * ext.z));
+            xhi = fmaf(-qb, dr, sqrtf(fmaxf(0.f, fmaf(-qc * dr, dr, P.qbin)) * ext.z));
+        }
+        for (int sx = 0; sx < sub_cols; ++sx) {
+            const int rx = tx * P.tile_w + sx * 8;
+            const int px0 = max(rx, x0), px1 = min(rx + 7, x1);
+            if (px0 <= px1 && xlo <= (float)px1 + 0.5f - u && xhi >= (float)px0 + 0.5f - u)
+                m |= 1u << (sy * sub_cols + sx);
+        }
+    }
+    return m;
+}
+
 // floor(r / w), w >= 1: below 2^22 a float estimate (within one of the quotient) and one
 // integer correction each way; larger r (a rectangle of more than 4M tiles) divides exactly.
 __device__ __forceinline__ uint32_t small_div(uint32_t r, uint32_t w) {
@@ -300,12 +432,20 @@ void launch_emit(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_n
                  int64_t view_chunks, const uint2* counts, const uint32_t* inst_off, uint32_t inst_base,
                  Record* records, InstInfo* info, uint32_t* dkey, uint32_t* ival, uint32_t* ntile);
 
+// Bounded waits of the sort: the look-back spin limit, and a test of it (mute_part: the
+// partition of the first digit pass that publishes no status; ~0 = none).
+struct SortCtl {
+    uint64_t spin_ns = 1000000000ull;
+    uint32_t mute_part = 0xFFFFFFFFu;
+};
+
 // Stable LSD radix sort of (key, value) on the low key_bits bits.  With d_n non-null the
 // number of pairs is read on the device as min(*d_n, n), and n is the capacity the launches
-// are sized for.  *keys_out / *vals_out receive the buffers holding the result.
+// are sized for.  *keys_out / *vals_out receive the buffers holding the result.  A look-back
+// wait that runs out sets kErrTimeout in err (the output is then invalid).
 void launch_sort(const Launch& L, uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                  uint32_t n, int key_bits, uint32_t* hist, uint32_t* status, uint32_t* counters, uint32_t* err,
-                 uint32_t** keys_out, uint32_t** vals_out, const uint32_t* d_n = nullptr);
+                 uint32_t** keys_out, uint32_t** vals_out, const uint32_t* d_n = nullptr, SortCtl ctl = SortCtl{});
 
 // Sets the sort kernels' launch attributes; call before a stream capture that contains a sort.
 void sort_prepare();
@@ -314,23 +454,31 @@ void sort_prepare();
 // min(*d_n, n) if d_n), and *total = min(poff[n], cap).  parts: scratch of
 // tile_scan_parts(n) words.
 void launch_tile_scan(const Launch& L, const uint32_t* order, const uint32_t* ntile, uint32_t n, const uint32_t* d_n,
-                      uint32_t* poff, uint32_t* parts, uint32_t cap, uint32_t* total);
+                      uint32_t* poff, uint32_t* parts, uint32_t cap, uint32_t* total, const uint32_t* err);
+
+// Kernels that read sorted values as indices return at once after a sort timed out (the
+// sorted arrays are then not permutations).
+__device__ __forceinline__ bool sort_failed(const uint32_t* err) { return (*(volatile const uint32_t*)err & kErrTimeout) != 0; }
 size_t tile_scan_parts(uint32_t n);
 
 // K3c: the (tile, instance) pairs of the depth-ordered instances, instance by instance in
-// that order and each instance's tiles in row-major order: keys = tile within the group,
-// values = instance index.  Pairs at or beyond cap are not written (kErrCapacity).
+// that order and each instance's tiles in row-major order: keys = tile within the group (bits
+// 0..23) | sub-tile mask << 24, values = instance index.  Pairs at or beyond cap are not
+// written (kErrCapacity).
 void launch_pairs(const Launch& L, const ViewDesc* views, int K, const uint32_t* order, const uint32_t* poff,
                   const Record* records, const InstInfo* info, uint32_t n, const uint32_t* d_n, const Params& P,
                   uint32_t* tkeys, uint32_t* tvals, uint32_t cap);
 
-// K4: [start, end) of every tile's run in the tile-sorted keys (d_n: device pair count).
+// K4: [start, end) of every tile's run in the tile-sorted keys (d_n: device pair count); the
+// tile is the key's low kTileBits bits.
 void launch_ranges(const Launch& L, const uint32_t* keys, uint32_t n, uint2* ranges, int n_tiles,
                    const uint32_t* d_n = nullptr);
 
+// K5: keys/vals are the tile-sorted pairs (each key's sub-tile mask selects the warps that
+// stage the instance).
 void launch_composite(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
-                      const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,
-                      float* out_rgb, float* out_depth, float* out_alpha, unsigned long long* work);
+                      const uint2* ranges, const uint32_t* keys, const uint32_t* vals, const Record* records,
+                      const Params& P, float* out_rgb, float* out_depth, float* out_alpha, unsigned long long* work);
 
 // Image randomisation of an RGB batch in place (the separate form of the compositor's
 // epilogue).  spans[V]: per view its first output pixel, its first quad in the view-by-view
@@ -398,14 +546,18 @@ void launch_tsdf(const Launch& L, float* F, float* W, int nx, int ny, int64_t n_
                  const TsdfView* views, int V, const float* depth, const float* alpha, float* dn, int64_t n_pix);
 
 void launch_composite_bwd(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
-                          const uint2* ranges, const uint32_t* vals, const Record* records, const Params& P,
+                          const uint2* ranges, const uint32_t* keys, const uint32_t* vals, const Record* records,
+                          const Params& P,
                           const float* out_rgb, const float* out_depth, const float* g_rgb, const float* g_depth,
-                          float* inst_grad);
+                          float* inst_grad, unsigned long long* n_red = nullptr);
 
 void launch_project_bwd(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_nodes, const ViewDesc* views,
                         const VNode* vnodes, int K, const float* node_poses, const InstInfo* info,
                         const float* inst_grad, uint32_t n_inst, const Params& P, const dgs_node_grads* grads,
                         float* grad_poses);
+
+// se(3) twists (rho, phi) [n,6] of n poses [n,12] and their 3x4 gradients [n,12].
+void launch_pose_twist(const Launch& L, const float* poses, const float* grads, int64_t n, float* out);
 
 size_t sort_status_words(uint32_t n);
 int sort_passes(int key_bits);

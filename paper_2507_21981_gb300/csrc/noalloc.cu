@@ -20,11 +20,11 @@
 // Set-up: the device address of g_scratch is resolved once per device, by the first call
 // made with that device current (cudaGetSymbolAddress); make that first call before any
 // stream capture begins on the device.
-#include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <string>
 #include <vector>
-#include <algorithm>
 
 #include "dgs_internal.cuh"
 
@@ -85,101 +85,27 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
                                   const int64_t* view_pixel_offset, void* stream_) {
     dgs_options o;
     if (opt) o = *opt; else dgs_default_options(&o);
-    {
-        const int area = o.tile_w * o.tile_h;
-        if (o.tile_w < 8 || o.tile_h < 4 || o.tile_w % 8 || o.tile_h % 4 || (area != 64 && area != 128 && area != 256))
-            return DGS_ERR_INVALID_ARG;
-        if (!(o.z_near > 0) || !(o.q_max > 0) || !(o.guard > 0) || !(o.lowpass >= 0)) return DGS_ERR_INVALID_ARG;
-    }
+    std::string why;
+    if (!check_options(&o, why)) return DGS_ERR_INVALID_ARG;
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-    if (n_nodes < 1 || !nodes || n_envs < 1 || max_nodes < 1 || max_cams < 1) return DGS_ERR_INVALID_ARG;
-    if (!env_node_ids || !cams || !cams_per_env || !node_poses || !out_rgb || !out_depth) return DGS_ERR_INVALID_ARG;
-    const int E = n_envs, K = max_nodes, C = max_cams;
-    // ---------------------------------------------------------------- host tables (as dgs_render)
-    std::vector<NodeDesc> nd(n_nodes);
-    int dtype_mask = 0;
-    int64_t chunk_total = 0, gbase = 0;
-    for (int k = 0; k < n_nodes; ++k) {
-        const dgs_node& n = nodes[k];
-        if (n.n < 0 || n.sh_degree < 0 || n.sh_degree > 3 || n.dtype < 0 || n.dtype > 2) return DGS_ERR_INVALID_ARG;
-        if (n.n > 0 && (!n.mean || !n.log_scale || !n.quat || !n.opacity_logit || !n.sh)) return DGS_ERR_INVALID_ARG;
-        nd[k] = NodeDesc{n.mean, n.log_scale, n.quat, n.opacity_logit, n.sh, n.n, gbase, n.sh_degree, n.dtype,
-                         (int32_t)chunk_total, (int32_t)((n.n + kChunk - 1) / kChunk)};
-        chunk_total += nd[k].nchunks;
-        gbase += n.n;
-        if (n.n > 0) dtype_mask |= 1 << n.dtype;
-    }
-    if (gbase >= (1ll << 32) || chunk_total >= (1ll << 31)) return DGS_ERR_INVALID_ARG;
-    std::vector<int> seen(n_nodes, -1);
-    for (int e = 0; e < E; ++e) {
-        for (int j = 0; j < K; ++j) {
-            const int k = env_node_ids[(int64_t)e * K + j];
-            if (k < -1 || k >= n_nodes) return DGS_ERR_INVALID_ARG;
-            if (k >= 0) { if (seen[k] == e) return DGS_ERR_INVALID_ARG; seen[k] = e; }
-        }
-        if (cams_per_env[e] < 0 || cams_per_env[e] > C) return DGS_ERR_INVALID_ARG;
-    }
-    std::vector<ViewDesc> views;
-    int64_t tiles_total = 0, pix_total = 0;
-    for (int e = 0; e < E; ++e)
-        for (int c = 0; c < cams_per_env[e]; ++c) {
-            const dgs_camera& cm = cams[(int64_t)e * C + c];
-            if (cm.width < 1 || cm.height < 1 || cm.width > 32768 || cm.height > 32768) return DGS_ERR_INVALID_ARG;
-            if (!(cm.fx > 0) || !(cm.fy > 0)) return DGS_ERR_INVALID_ARG;
-            for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b) {
-                    double s = 0;
-                    for (int r = 0; r < 3; ++r) s += (double)cm.cam_from_world[r * 4 + a] * cm.cam_from_world[r * 4 + b];
-                    if (!(std::fabs(s - (a == b ? 1.0 : 0.0)) <= 1e-4)) return DGS_ERR_INVALID_ARG;
-                }
-            ViewDesc vd{};
-            vd.fx = cm.fx; vd.fy = cm.fy; vd.cx = cm.cx; vd.cy = cm.cy;
-            vd.limx = o.guard * 0.5f * (float)cm.width / cm.fx;
-            vd.limy = o.guard * 0.5f * (float)cm.height / cm.fy;
-            vd.W = cm.width; vd.H = cm.height;
-            vd.tiles_x = (cm.width + o.tile_w - 1) / o.tile_w;
-            vd.tiles_y = (cm.height + o.tile_h - 1) / o.tile_h;
-            vd.env = e;
-            vd.tile_base = (int32_t)tiles_total;
-            std::memcpy(vd.cam, cm.cam_from_world, sizeof(vd.cam));
-            tiles_total += (int64_t)vd.tiles_x * vd.tiles_y;
-            if (tiles_total >= (1ll << 31)) return DGS_ERR_INVALID_ARG;
-            vd.pix_off = view_pixel_offset ? view_pixel_offset[views.size()] : pix_total;
-            if (vd.pix_off < 0) return DGS_ERR_INVALID_ARG;
-            pix_total += (int64_t)cm.width * cm.height;
-            views.push_back(vd);
-        }
-    const int V = (int)views.size();
+    // ---------------------------------------------------------------- validation and host tables (as dgs_render)
+    HostTables H;
+    const int vrc = build_host_tables(o, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env,
+                                      max_cams, view_pixel_offset, H, why);
+    if (vrc != DGS_OK) return vrc;
+    if (!out_rgb || !out_depth) return DGS_ERR_INVALID_ARG;
+    const int K = max_nodes;
+    const int V = (int)H.views.size();
     if (V == 0) return DGS_OK;
-    std::vector<int32_t> slot_node((size_t)V * K, -1);
-    std::vector<int64_t> vnode_tab((size_t)V * K, 0), view_tab(V + 1, 0);
-    std::vector<std::vector<NodeView>> per_node(n_nodes);
-    int64_t tab = 0;
-    for (int v = 0; v < V; ++v) {
-        const int e = views[v].env;
-        std::vector<std::pair<int, int>> present;
-        for (int j = 0; j < K; ++j) {
-            const int k = env_node_ids[(int64_t)e * K + j];
-            slot_node[(size_t)v * K + j] = k;
-            if (k >= 0) present.push_back({k, j});
-        }
-        std::sort(present.begin(), present.end());
-        view_tab[v] = tab;
-        for (auto& pk : present) {
-            vnode_tab[(size_t)v * K + pk.second] = tab;
-            tab += nd[pk.first].nchunks;
-            per_node[pk.first].push_back({v, pk.second, vnode_tab[(size_t)v * K + pk.second]});
-        }
-    }
-    view_tab[V] = tab;
-    const int64_t T = tab;
-    std::vector<int32_t> nv_off(n_nodes + 1, 0);
-    std::vector<NodeView> nv;
-    for (int k = 0; k < n_nodes; ++k) {
-        nv_off[k] = (int32_t)nv.size();
-        nv.insert(nv.end(), per_node[k].begin(), per_node[k].end());
-    }
-    nv_off[n_nodes] = (int32_t)nv.size();
+    const std::vector<NodeDesc>& nd = H.nodes;
+    const std::vector<ViewDesc>& views = H.views;
+    const std::vector<int32_t>& slot_node = H.slot_node;
+    const std::vector<int64_t>& vnode_tab = H.vnode_tab;
+    const std::vector<int64_t>& view_tab = H.view_tab;
+    const std::vector<int32_t>& nv_off = H.nv_off;
+    const std::vector<NodeView>& nv = H.nv;
+    const int dtype_mask = H.dtype_mask;
+    const int64_t chunk_total = H.chunk_total, tiles_total = H.tiles_total, T = H.T;
 
     // ---------------------------------------------------------------- phase 1 scratch
     unsigned char* base = nullptr;
@@ -213,21 +139,8 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
     NA_CUDA(cudaMemcpyAsync(d_viewtab, view_tab.data(), sizeof(int64_t) * (V + 1), cudaMemcpyHostToDevice, stream));
     NA_CUDA(cudaMemsetAsync(d_err, 0, 64, stream));
 
-    Params P{};
-    P.z_near = o.z_near; P.lowpass = o.lowpass; P.alpha_min = o.alpha_min; P.alpha_max = o.alpha_max;
-    P.t_min = o.t_min; P.q_max = o.q_max; P.guard = o.guard;
-    P.bg0 = o.bg[0]; P.bg1 = o.bg[1]; P.bg2 = o.bg[2];
-    P.qbin = o.q_max * 1.001f + 1e-3f;
-    P.p_min = kHalfLog2e * o.q_max;
-    P.tile_w = o.tile_w; P.tile_h = o.tile_h;
-    P.tile_sx = 0;
-    P.tile_sy = 0;
-    while ((1 << P.tile_sx) < o.tile_w) ++P.tile_sx;
-    while ((1 << P.tile_sy) < o.tile_h) ++P.tile_sy;
-    P.exact_tile_test = o.exact_tile_test;
-    P.tile0 = 0;
+    Params P = make_params(o);
     P.err = d_err;
-    { uint32_t b; std::memcpy(&b, &o.z_near, 4); P.zbase = b & 0x7F800000u; }
     int64_t launches = 0;
     Launch L{stream, &launches};
     launch_setup_views(L, d_views, V, node_poses, d_slot, K, d_vnodes, d_vtab, d_err);
@@ -236,16 +149,18 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
     launch_scan(L, d_counts, T, d_inst_off, d_pair_off, d_parts, n_parts + 1);
     // one view group: read back the grand totals and the error word
     NA_CUDA(cudaMemsetAsync(d_rb, 0, sizeof(uint64_t) * 3, stream));
-    NA_CUDA(cudaMemcpyAsync(d_rb, d_inst_off + T, sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream));
+    // the 64-bit instance total of the scan (its 32-bit offsets wrap beyond 2^32)
+    if (n_parts > 0)
+        NA_CUDA(cudaMemcpyAsync(d_rb, d_parts + n_parts, sizeof(uint64_t), cudaMemcpyDeviceToDevice, stream));
     NA_CUDA(cudaMemcpyAsync(d_rb + 1, d_pair_off + T, sizeof(uint64_t), cudaMemcpyDeviceToDevice, stream));
     NA_CUDA(cudaMemcpyAsync(d_rb + 2, d_err, sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream));
     uint64_t h_rb[3] = {0, 0, 0};
     NA_CUDA(cudaMemcpyAsync(h_rb, d_rb, sizeof(uint64_t) * 3, cudaMemcpyDeviceToHost, stream));
     NA_CUDA(cudaGetLastError());
     NA_CUDA(cudaStreamSynchronize(stream));
-    const uint64_t n_vis = h_rb[0] & 0xFFFFFFFFull, n_pairs = h_rb[1];
+    const uint64_t n_vis = h_rb[0], n_pairs = h_rb[1];
     if ((uint32_t)h_rb[2] & kErrPose) return DGS_ERR_INVALID_ARG;
-    if (n_pairs > kMaxPairs) return DGS_ERR_CAPACITY;
+    if (n_pairs > kMaxPairs || n_vis >= (1ull << 32)) return DGS_ERR_CAPACITY;
 
     // ---------------------------------------------------------------- phase 2 scratch
     const uint64_t ni = std::max<uint64_t>(n_vis, 1), np = std::max<uint64_t>(n_pairs, 1);
@@ -269,17 +184,17 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
     uint2* d_ranges = cv.take<uint2>((size_t)tiles_total);
     if (!cv.ok) return DGS_ERR_CAPACITY;
     const int tbits = bits_for_tiles((uint64_t)tiles_total + 1);
-    if (tbits > 31) return DGS_ERR_CAPACITY;
+    if (tbits > kTileBits) return DGS_ERR_CAPACITY;
     // depth-ordered tile lists, as in dgs_render with one view group
     launch_emit(L, dtype_mask, d_nodes, n_nodes, d_views, d_vnodes, K, d_nv, d_nvoff, (int)chunk_total, P, 0, V, true,
                 nullptr, 0, d_counts, d_inst_off, 0u, d_rec, d_info, d_dk0, d_iv0, d_ntile);
     uint32_t *dk, *order, *tk, *tv;
     launch_sort(L, d_dk0, d_iv0, d_dk1, d_iv1, (uint32_t)n_vis, kZBits, d_hist, d_status, d_cnt, d_err, &dk, &order);
-    launch_tile_scan(L, order, d_ntile, (uint32_t)n_vis, nullptr, d_poff, d_tparts, (uint32_t)n_pairs, d_total);
+    launch_tile_scan(L, order, d_ntile, (uint32_t)n_vis, nullptr, d_poff, d_tparts, (uint32_t)n_pairs, d_total, d_err);
     launch_pairs(L, d_views, K, order, d_poff, d_rec, d_info, (uint32_t)n_vis, nullptr, P, d_k0, d_v0, (uint32_t)n_pairs);
     launch_sort(L, d_k0, d_v0, d_k1, d_v1, (uint32_t)n_pairs, tbits, d_hist, d_status, d_cnt, d_err, &tk, &tv, d_total);
     launch_ranges(L, tk, (uint32_t)n_pairs, d_ranges, (int)tiles_total, d_total);
-    launch_composite(L, d_views, 0, V, (int)tiles_total, d_ranges, tv, d_rec, P, out_rgb, out_depth, out_alpha,
+    launch_composite(L, d_views, 0, V, (int)tiles_total, d_ranges, tk, tv, d_rec, P, out_rgb, out_depth, out_alpha,
                      nullptr);
     uint32_t h_err = 0;
     NA_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));

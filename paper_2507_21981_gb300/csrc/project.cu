@@ -22,8 +22,22 @@ namespace dgs {
 namespace {
 
 // ------------------------------------------------------------------ setup: camera_from_node
-// One thread per (view, slot).  Row 2 of camera_from_node is composed in binary32 with one
-// rounding per multiply and per add (no FMA), in the order of the depth-key definition.
+// One thread per (view, slot).  camera_from_node is composed with compensated sums and kept as
+// M + Ml, within about 2^-48 of the exact product of the two FP32 transforms, so that camera
+// space points (the depth key and the projected centre) can be faithfully rounded.
+
+// Compensated sum of n products a_k b_k as (hi, lo) with hi = fl(hi + lo).
+__device__ __forceinline__ void dot_hi_lo(const float* a, const float* b, int n, float& hi, float& lo) {
+    float p, s, h, r, q;
+    two_prod(a[0], b[0], p, s);
+    for (int k = 1; k < n; ++k) {
+        two_prod(a[k], b[k], h, r);
+        two_sum(p, h, p, q);
+        s = __fadd_rn(s, __fadd_rn(q, r));
+    }
+    hi = __fadd_rn(p, s);
+    lo = __fsub_rn(s, __fsub_rn(hi, p));
+}
 __global__ void k_setup_views(const ViewDesc* __restrict__ views, int n_views, const float* __restrict__ poses,
                               const int32_t* __restrict__ slot_node, int K, VNode* __restrict__ vnodes,
                               const int64_t* __restrict__ vnode_tab, uint32_t* err) {
@@ -55,18 +69,12 @@ __global__ void k_setup_views(const ViewDesc* __restrict__ views, int n_views, c
     }
     if (bad) atomicOr(err, kErrPose);
     const float* W = vd.cam;   // rows of [Wc | tc]
-    for (int a = 0; a < 3; ++a) {
-        for (int b = 0; b < 3; ++b) {
-            const float x = __fmul_rn(W[a * 4 + 0], R[0 * 3 + b]);
-            const float y = __fmul_rn(W[a * 4 + 1], R[1 * 3 + b]);
-            const float z = __fmul_rn(W[a * 4 + 2], R[2 * 3 + b]);
-            out.M[a * 4 + b] = __fadd_rn(__fadd_rn(x, y), z);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 4; ++b) {
+            const float wa[4] = {W[a * 4 + 0], W[a * 4 + 1], W[a * 4 + 2], W[a * 4 + 3]};
+            const float col[4] = {b < 3 ? R[0 * 3 + b] : t[0], b < 3 ? R[1 * 3 + b] : t[1], b < 3 ? R[2 * 3 + b] : t[2], 1.f};
+            dot_hi_lo(wa, col, b < 3 ? 3 : 4, out.M[a * 4 + b], out.Ml[a * 4 + b]);
         }
-        const float x = __fmul_rn(W[a * 4 + 0], t[0]);
-        const float y = __fmul_rn(W[a * 4 + 1], t[1]);
-        const float z = __fmul_rn(W[a * 4 + 2], t[2]);
-        out.M[a * 4 + 3] = __fadd_rn(__fadd_rn(__fadd_rn(x, y), z), W[a * 4 + 3]);
-    }
     // camera centre in the node frame: o = -M_R^T M_t
     for (int b = 0; b < 3; ++b)
         out.o[b] = -(out.M[0 * 4 + b] * out.M[3] + out.M[1 * 4 + b] * out.M[7] + out.M[2 * 4 + b] * out.M[11]);
@@ -133,11 +141,11 @@ struct Splat {
 // q = (cyy/det) (dx - (cxy/cyy) dy)^2 + dy^2 / cyy, a sum of two non-negative terms.
 __device__ __forceinline__ bool project(const Gauss& g, const VNode& vn, const ViewDesc& vd, const Params& P, Splat& s) {
     const float* M = vn.M;
-    // depth key: binary32, one rounding per operation, fixed order
-    const float z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[8], g.mx), __fmul_rn(M[9], g.my)), __fmul_rn(M[10], g.mz)), M[11]);
+    // camera-space centre, faithfully rounded (z is the depth key)
+    const float z = camera_depth(vn, g.mx, g.my, g.mz);
     if (!(z > P.z_near)) return false;
-    const float tx = fmaf(M[0], g.mx, fmaf(M[1], g.my, fmaf(M[2], g.mz, M[3])));
-    const float ty = fmaf(M[4], g.mx, fmaf(M[5], g.my, fmaf(M[6], g.mz, M[7])));
+    const float tx = camera_row(vn, 0, g.mx, g.my, g.mz);
+    const float ty = camera_row(vn, 1, g.mx, g.my, g.mz);
     const float iz = 1.f / z;
     const float xr = tx * iz, yr = ty * iz;
     const float xc = fminf(vd.limx, fmaxf(-vd.limx, xr));
@@ -193,21 +201,35 @@ __device__ __forceinline__ bool project(const Gauss& g, const VNode& vn, const V
 // 2D covariance satisfies Sigma_xx <= |T0|^2 smax + lowpass with |T0|^2 = (fx/z)^2 (1 + xc^2)
 // for the orthonormal rows of camera_from_node, so the ellipse box is bounded by
 // sqrt(qbin ((fx/z)^2 (1 + xc^2) smax + lowpass)) (2 % + 1e-3 px of slack for rounding).  The
-// centre u and the depth key are computed exactly as in project().
+// camera-space centre is taken from plain FMA chains over the leading parts M; against the
+// faithfully rounded centre of project() each coordinate differs by less than 6u S_i (three
+// roundings, the omitted trailing parts and the faithful rounding, u = 2^-24, S_i = sum of the
+// magnitudes of the row's terms), bounded here by e_i = 2^-20 S_i, which widens the near-plane
+// test and the box.
 __device__ __forceinline__ bool may_be_visible(const Gauss& g, const VNode& vn, const ViewDesc& vd, const Params& P) {
     const float* M = vn.M;
-    const float z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[8], g.mx), __fmul_rn(M[9], g.my)), __fmul_rn(M[10], g.mz)), M[11]);
-    if (!(z > P.z_near)) return false;
+    const float ax = fabsf(g.mx), ay = fabsf(g.my), az = fabsf(g.mz);
+    constexpr float k20 = 9.5367431640625e-07f;   // 2^-20
+    const float z = fmaf(M[8], g.mx, fmaf(M[9], g.my, fmaf(M[10], g.mz, M[11])));
+    const float ez = k20 * fmaf(fabsf(M[8]), ax, fmaf(fabsf(M[9]), ay, fmaf(fabsf(M[10]), az, fabsf(M[11]))));
+    if (!(z + ez > P.z_near)) return false;
+    const float zl = z - ez;
+    if (!(zl > 0.f)) return true;                  // at the camera plane: let the exact projection decide
     const float tx = fmaf(M[0], g.mx, fmaf(M[1], g.my, fmaf(M[2], g.mz, M[3])));
     const float ty = fmaf(M[4], g.mx, fmaf(M[5], g.my, fmaf(M[6], g.mz, M[7])));
+    const float ex = k20 * fmaf(fabsf(M[0]), ax, fmaf(fabsf(M[1]), ay, fmaf(fabsf(M[2]), az, fabsf(M[3]))));
+    const float ey = k20 * fmaf(fabsf(M[4]), ax, fmaf(fabsf(M[5]), ay, fmaf(fabsf(M[6]), az, fabsf(M[7]))));
     const float iz = 1.f / z;
     const float xr = tx * iz, yr = ty * iz;
     const float xc = fminf(vd.limx, fmaxf(-vd.limx, xr));
     const float yc = fminf(vd.limy, fmaxf(-vd.limy, yr));
     const float fxz = vd.fx * iz, fyz = vd.fy * iz;
     const float s = 1.02f * g.smax;
-    const float hx = sqrtf(P.qbin * fmaf(fxz * fxz * fmaf(xc, xc, 1.f), s, P.lowpass)) + 1e-3f;
-    const float hy = sqrtf(P.qbin * fmaf(fyz * fyz * fmaf(yc, yc, 1.f), s, P.lowpass)) + 1e-3f;
+    // centre error in pixels: |d(t/z)| <= (e_t + |t/z| e_z) / (z - e_z)
+    const float izl = 1.f / zl;
+    const float dux = vd.fx * fmaf(fabsf(xr), ez, ex) * izl, duy = vd.fy * fmaf(fabsf(yr), ez, ey) * izl;
+    const float hx = sqrtf(P.qbin * fmaf(fxz * fxz * fmaf(xc, xc, 1.f), s, P.lowpass)) + 1e-3f + dux;
+    const float hy = sqrtf(P.qbin * fmaf(fyz * fyz * fmaf(yc, yc, 1.f), s, P.lowpass)) + 1e-3f + duy;
     const float u = fmaf(vd.fx, xr, vd.cx), v = fmaf(vd.fy, yr, vd.cy);
     return u + hx - 0.5f >= 0.f && v + hy - 0.5f >= 0.f && u - hx - 0.5f <= (float)(vd.W - 1) &&
            v - hy - 0.5f <= (float)(vd.H - 1);

@@ -13,8 +13,10 @@
 // flag | 30-bit count).  Digits are D = ceil(bits / passes) bits wide with passes =
 // ceil(bits / 8): measured on this path, wider digits (fewer passes) lose what they save to
 // the scatter, whose runs per partition shrink to a few keys.  Look-back spins are bounded by
-// a wall-clock limit; on expiry the kernel sets kErrTimeout and finishes (the output is then
-// invalid and the host reports it).
+// a wall-clock limit (SortCtl::spin_ns, 1 s by default); on expiry the kernel sets
+// kErrTimeout and finishes: its output is then not a permutation of the input, the kernels
+// that use sorted values as indices return at once when they see kErrTimeout, and the host
+// reports the timeout.
 #include <algorithm>
 
 #include "dgs_internal.cuh"
@@ -30,7 +32,6 @@ constexpr int kMaxD = 8;                          // widest digit: 256 bins
 constexpr int kMaxR = 1 << kMaxD;
 constexpr int kWindow = 4;                        // predecessors read per digit and look-back round
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kCountMask = (1u << 30) - 1u;
-constexpr uint64_t kSpinLimitNs = 1000000000ull;  // 1 s
 constexpr int kSmem = kTile * 8 + kWarps * kMaxR * 4;
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
@@ -102,7 +103,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const uint32_t* __rest
                                                       uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t n,
                                                       const uint32_t* __restrict__ d_n, int shift,
                                                       const uint32_t* __restrict__ digit_off, uint32_t* status,
-                                                      uint32_t* counter, uint32_t* err) {
+                                                      uint32_t* counter, uint32_t* err, uint64_t spin_ns,
+                                                      uint32_t mute_part) {
     constexpr int R = 1 << D;
     constexpr uint32_t M = R - 1;
     constexpr int DPT = (R + kThreads - 1) / kThreads;   // digits per thread
@@ -163,12 +165,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const uint32_t* __rest
             }
         }
     }
-    // decoupled look-back over earlier partitions, all owned digits at once
+    // decoupled look-back over earlier partitions, all owned digits at once; partition
+    // mute_part (a test of the bounded wait, never a real partition index by default) publishes
+    // nothing, so the partitions after it wait for it until spin_ns runs out
+    const bool publish = part != mute_part;
     if (part == 0) {
 #pragma unroll
         for (int q = 0; q < DPT; ++q) {
             const int d = tid + q * kThreads;
-            if (d < R) st_relaxed(&status[d], kFlagInc | total[q]);
+            if (d < R && publish) st_relaxed(&status[d], kFlagInc | total[q]);
         }
     } else {
         int64_t p[DPT];
@@ -178,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const uint32_t* __rest
             const int d = tid + q * kThreads;
             done[q] = d >= R;
             p[q] = (int64_t)part - 1;
-            if (d < R) st_relaxed(&status[(size_t)part * R + d], kFlagAgg | total[q]);
+            if (d < R && publish) st_relaxed(&status[(size_t)part * R + d], kFlagAgg | total[q]);
         }
         uint64_t t0 = 0;
         uint32_t spins = 0;
@@ -209,13 +214,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const uint32_t* __rest
             if (stall && (++spins & 1023u) == 0) {
                 const uint64_t now = global_timer_ns();
                 if (t0 == 0) t0 = now;
-                else if (now - t0 > kSpinLimitNs) { atomicOr(err, kErrTimeout); break; }
+                else if (now - t0 > spin_ns) { atomicOr(err, kErrTimeout); break; }
             }
         }
 #pragma unroll
         for (int q = 0; q < DPT; ++q) {
             const int d = tid + q * kThreads;
-            if (d < R) st_relaxed(&status[(size_t)part * R + d], kFlagInc | (excl[q] + total[q]));
+            if (d < R && publish) st_relaxed(&status[(size_t)part * R + d], kFlagInc | (excl[q] + total[q]));
         }
     }
 #pragma unroll
@@ -265,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const uint32_t* __rest
 }
 
 using OnesweepFn = void (*)(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t, const uint32_t*, int,
-                            const uint32_t*, uint32_t*, uint32_t*, uint32_t*);
+                            const uint32_t*, uint32_t*, uint32_t*, uint32_t*, uint64_t, uint32_t);
 
 OnesweepFn onesweep_for(int D) {
     switch (D) {
@@ -281,6 +286,18 @@ OnesweepFn onesweep_for(int D) {
 }
 
 }  // namespace
+
+// Streaming multiprocessors of the current device (read once per process and device).
+uint32_t sm_count() {
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cached[dev]) {
+        int n = 0;
+        cached[dev] = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0 ? n : 152;
+    }
+    return (uint32_t)cached[dev];
+}
 
 int sort_passes(int key_bits) { return std::max(1, (key_bits + kMaxD - 1) / kMaxD); }
 
@@ -298,7 +315,7 @@ void sort_prepare() {
 // hist: [4 * 256] words, counters: [8] words, status: sort_status_words(n) words.
 void launch_sort(const Launch& L, uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, uint32_t n,
                  int key_bits, uint32_t* hist, uint32_t* status, uint32_t* counters, uint32_t* err,
-                 uint32_t** keys_out, uint32_t** vals_out, const uint32_t* d_n) {
+                 uint32_t** keys_out, uint32_t** vals_out, const uint32_t* d_n, SortCtl ctl) {
     *keys_out = keys;
     *vals_out = vals;
     // with a device-side count every pass runs (the output lands in the same buffer whatever
@@ -310,7 +327,7 @@ void launch_sort(const Launch& L, uint32_t* keys, uint32_t* vals, uint32_t* keys
     sort_prepare();
     cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kMaxR * passes, L.stream);
     cudaMemsetAsync(counters, 0, sizeof(uint32_t) * 8, L.stream);
-    const int hist_blocks = (int)std::min<uint32_t>(4 * 152, (n + kThreads * 8 - 1) / (kThreads * 8));
+    const int hist_blocks = (int)std::min<uint32_t>(4 * sm_count(), (n + kThreads * 8 - 1) / (kThreads * 8));
     k_hist<<<hist_blocks, kThreads, 0, L.stream>>>(keys, n, d_n, passes, D, hist);
     k_hist_scan<<<1, 256, 0, L.stream>>>(hist, passes, 1 << D);
     *L.launches += 2;
@@ -321,7 +338,7 @@ void launch_sort(const Launch& L, uint32_t* keys, uint32_t* vals, uint32_t* keys
     for (int p = 0; p < passes; ++p) {
         cudaMemsetAsync(status, 0, sizeof(uint32_t) * (size_t)(1 << D) * parts, L.stream);
         fn<<<parts, kThreads, kSmem, L.stream>>>(ki, vi, ko, vo, n, d_n, D * p, hist + p * kMaxR, status, counters + p,
-                                                 err);
+                                                 err, ctl.spin_ns, p == 0 ? ctl.mute_part : 0xFFFFFFFFu);
         ++*L.launches;
         uint32_t* tk = ki; ki = ko; ko = tk;
         uint32_t* tv = vi; vi = vo; vo = tv;

@@ -21,7 +21,7 @@ DGS_MODE_PLAIN, DGS_MODE_BATCHED, DGS_MODE_GRAPH = 0, 1, 2
 DGS_PATH_EAGER, DGS_PATH_GRAPH, DGS_PATH_CAPTURED, DGS_PATH_REGROWN = 0, 1, 2, 3
 DGS_TUNE_MAX = 16
 KERNEL_CLASSES = ("setup", "count", "scan", "emit", "sort", "ranges", "composite", "backward", "graph", "augment",
-                  "lidar", "mesh", "tsdf")
+                  "lidar", "mesh", "tsdf", "backward_project")
 STATUS_NAMES = {0: "DGS_OK", 1: "DGS_ERR_INVALID_ARG", 2: "DGS_ERR_CUDA", 3: "DGS_ERR_OOM", 4: "DGS_ERR_CAPACITY",
                 5: "DGS_ERR_TIMEOUT", 6: "DGS_ERR_UNSUPPORTED"}
 
@@ -41,7 +41,8 @@ class dgs_options(C.Structure):
     _fields_ = [("mode", C.c_int32), ("tile_w", C.c_int32), ("tile_h", C.c_int32), ("exact_tile_test", C.c_int32),
                 ("z_near", C.c_float), ("lowpass", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
                 ("t_min", C.c_float), ("q_max", C.c_float), ("guard", C.c_float), ("bg", C.c_float * 3),
-                ("profile", C.c_int32), ("views_per_group", C.c_int32)]
+                ("profile", C.c_int32), ("views_per_group", C.c_int32), ("spin_limit_us", C.c_int32),
+                ("check_binning", C.c_int32), ("test_fault", C.c_int32)]
 
 
 class dgs_node_grads(C.Structure):
@@ -53,7 +54,7 @@ class dgs_stats(C.Structure):
     _fields_ = [("n_views", C.c_int64), ("n_pixels", C.c_int64), ("n_instances", C.c_int64),
                 ("n_visible", C.c_int64), ("n_pairs", C.c_int64), ("n_groups", C.c_int32), ("key_bits", C.c_int32),
                 ("px_evaluated", C.c_int64), ("px_reached", C.c_int64), ("px_composited", C.c_int64),
-                ("path", C.c_int32), ("graph_captures", C.c_int32)]
+                ("path", C.c_int32), ("graph_captures", C.c_int32), ("bwd_reductions", C.c_int64)]
 
 
 class dgs_tune_result(C.Structure):
@@ -75,7 +76,7 @@ EXPORTED = ("dgs_default_options", "dgs_context_create", "dgs_context_destroy", 
             "dgs_workspace_query", "dgs_render", "dgs_last_stats", "dgs_kernel_times", "dgs_last_launches",
             "dgs_render_noalloc", "dgs_render_backward", "dgs_autotune", "dgs_spatial_order",
             "dgs_set_augment", "dgs_augment_rgb", "dgs_lidar_build", "dgs_lidar_trace", "dgs_mesh_to_gaussians",
-            "dgs_tsdf_integrate")
+            "dgs_tsdf_integrate", "dgs_pose_twist_grad", "dgs_set_options", "dgs_workspace_query_batch")
 
 _lib = None
 _lock = threading.Lock()
@@ -141,6 +142,13 @@ def load(path: str | None = None) -> C.CDLL:
         lib.dgs_mesh_to_gaussians.argtypes = [vp, vp, i64, vp, i64, vp, C.c_float, C.c_float, i32, vp, vp, vp, vp, vp,
                                               vp]
         lib.dgs_tsdf_integrate.restype = C.c_int
+        lib.dgs_pose_twist_grad.argtypes = [vp, vp, i64, vp, vp]
+        lib.dgs_set_options.argtypes = [vp, C.POINTER(dgs_options)]
+        lib.dgs_workspace_query_batch.argtypes = [vp, C.POINTER(dgs_node), i32, vp, i32, i32, vp,
+                                                  C.POINTER(dgs_camera), vp, i32, vp, C.POINTER(C.c_size_t), vp]
+        lib.dgs_workspace_query_batch.restype = C.c_int
+        lib.dgs_set_options.restype = C.c_int
+        lib.dgs_pose_twist_grad.restype = C.c_int
         lib.dgs_tsdf_integrate.argtypes = [vp, vp, vp, i32, i32, i32, vp, C.c_float, C.c_float, C.c_float, C.c_float,
                                            C.POINTER(dgs_camera), i32, vp, vp, vp, vp]
         if path is None:
@@ -163,6 +171,10 @@ def dgs_context_create(opt: dgs_options | None = None) -> C.c_void_p:
     return h
 
 
+def dgs_set_options(ctx, opt: dgs_options) -> int:
+    return load().dgs_set_options(ctx, C.byref(opt))
+
+
 def dgs_context_destroy(ctx) -> int:
     return load().dgs_context_destroy(ctx)
 
@@ -176,6 +188,16 @@ def dgs_workspace_query(ctx) -> int:
     b = C.c_size_t()
     load().dgs_workspace_query(ctx, C.byref(b))
     return int(b.value)
+
+
+def dgs_workspace_query_batch(ctx, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env,
+                              max_cams, view_pixel_offset, stream) -> tuple:
+    """Direct call of dgs_workspace_query_batch; returns (status, bytes)."""
+    b = C.c_size_t()
+    rc = load().dgs_workspace_query_batch(ctx, nodes, int(n_nodes), _ptr(env_node_ids), int(n_envs), int(max_nodes),
+                                          _ptr(node_poses), cams, _ptr(cams_per_env), int(max_cams),
+                                          _ptr(view_pixel_offset), C.byref(b), stream)
+    return rc, int(b.value)
 
 
 def _ptr(a):
@@ -328,3 +350,9 @@ def cameras(views) -> "C.Array":
         c.fx, c.fy, c.cx, c.cy, c.width, c.height = float(fx), float(fy), float(cx), float(cy), int(w), int(h)
         c.cam_from_world[:] = [float(x) for x in np.asarray(P, np.float32).reshape(12)]
     return arr
+
+
+def dgs_pose_twist_grad(poses, grad_poses, n, out_twist, stream) -> int:
+    """Direct call of dgs_pose_twist_grad: device poses [n,12], their 3x4 gradients [n,12] and the
+    output twists [n,6] (torch tensors or device addresses), stream an integer cudaStream_t."""
+    return load().dgs_pose_twist_grad(_ptr(poses), _ptr(grad_poses), int(n), _ptr(out_twist), stream)

@@ -115,6 +115,19 @@ class Renderer:
         self._aug = None
         self.ctx = D.dgs_context_create(o)
 
+    def set_options(self, **opts):
+        """Changes fields of the context's dgs_options (dgs_set_options); raises if invalid."""
+        o = D.dgs_options.from_buffer_copy(self.options)
+        for k, v in opts.items():
+            if k == "bg":
+                o.bg = (C.c_float * 3)(*[float(x) for x in v])
+            else:
+                setattr(o, k, v)
+        rc = D.dgs_set_options(self.ctx, o)
+        if rc != D.DGS_OK:
+            raise D.DgsError(rc, D.dgs_last_error(self.ctx))
+        self.options = o
+
     def close(self):
         if self.ctx:
             D.dgs_context_destroy(self.ctx)
@@ -326,3 +339,18 @@ def render_differentiable(renderer: Renderer, ds: DeviceScene, node_poses=None):
     requires_grad set) and to node_poses (defaults to the scene's current poses)."""
     poses = ds.node_poses if node_poses is None else node_poses
     return DGSRenderFn.apply(renderer, ds, poses, *ds.param_list())
+
+
+def pose_twist_grad(node_poses: torch.Tensor, grad_poses: torch.Tensor) -> torch.Tensor:
+    """se(3) gradient (rho, phi) of a left perturbation of each pose, from the 3x4 pose gradient
+    (dgs_pose_twist_grad on the current stream).  node_poses, grad_poses: CUDA FP32 [..., 3, 4]
+    (or [..., 12]); returns [..., 6]."""
+    p = node_poses.detach().reshape(-1, 12).to(torch.float32).contiguous()
+    g = grad_poses.detach().reshape(-1, 12).to(torch.float32).contiguous()
+    if p.shape != g.shape or not p.is_cuda or not g.is_cuda:
+        raise ValueError("pose_twist_grad: poses and gradients must be CUDA tensors of the same shape")
+    out = torch.empty((p.shape[0], 6), device=p.device, dtype=torch.float32)
+    rc = D.dgs_pose_twist_grad(p, g, p.shape[0], out, torch.cuda.current_stream(p.device).cuda_stream)
+    if rc != D.DGS_OK:
+        raise D.DgsError(rc, "dgs_pose_twist_grad")
+    return out.reshape(*node_poses.shape[:-2] if node_poses.shape[-2:] == (3, 4) else node_poses.shape[:-1], 6)
