@@ -55,8 +55,8 @@ def test_default_options(lib):
 def test_struct_sizes_match_header(lib):
     assert C.sizeof(D.dgs_node) == 56
     assert C.sizeof(D.dgs_camera) == 72
-    assert C.sizeof(D.dgs_options) == 64
-    assert C.sizeof(D.dgs_stats) == 80
+    assert C.sizeof(D.dgs_options) == 76
+    assert C.sizeof(D.dgs_stats) == 88
     assert C.sizeof(D.dgs_tune_result) == 8 + 3 * 4 * D.DGS_TUNE_MAX
     assert C.sizeof(D.dgs_augment) == 32
     assert C.sizeof(D.dgs_lidar) == 52
@@ -316,3 +316,9 @@ def test_product_never_reaches_the_oracle():
     for f in os.listdir(os.path.join(ROOT, "oracle")):
         if f.endswith((".py", ".cpp", ".h")):
             assert not back.search(open(os.path.join(ROOT, "oracle", f)).read()), f
+
+
+def test_pose_twist_validates_arguments_on_the_host(lib):
+    assert lib.dgs_pose_twist_grad(None, None, -1, None, None) == D.DGS_ERR_INVALID_ARG
+    assert lib.dgs_pose_twist_grad(None, None, 3, None, None) == D.DGS_ERR_INVALID_ARG
+    assert lib.dgs_pose_twist_grad(None, None, 0, None, None) == D.DGS_OK      # nothing to do, no device work

@@ -36,6 +36,8 @@ def _check_views(sc, ds, out, views, opts=OPTS, packed=None):
         rep["view"] = v
         reports.append(rep)
         assert bad == 0, rep
+        # the plain relative depth bound, without the coverage term, on every unambiguous pixel
+        assert rep["frac_depth_plain_over_1e4_unambiguous"] == 0.0, rep
     return reports
 
 
