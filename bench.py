@@ -30,10 +30,22 @@ METRIC = "Mpix/s RGB+depth batched vs plain per-view; fwd+bwd ms/view at 500k Ga
 # quadratic form 5, compare 1, exp argument + MUFU 2, opacity product + clamp 2, alpha test 1,
 # transmittance 2, termination test 1, weight 1, colour 3, depth 1 (about 20).
 OPS_PER_PAIR = 21
-# DRAM bytes (read + write) per launch on the full workload, from the ncu capture of the same
-# kernel on the 8-env case (profiles/kernels_config2_8envs_640x480.md: 120.7 + 70.4 MB) scaled
-# by the 8x views of the full launch; absent for a kernel that changed since its capture.
-TRAFFIC = {"composite": (116.2e6 + 68.6e6) * 8}
+# The adjoint of one composited (pixel, Gaussian) pair: the forward's evaluation replayed (21),
+# prefix sums (4), reciprocal and normalised remainders (5), dL/dalpha (8), colour and depth
+# partials (4), opacity and quadratic-form partials (8): about 50.
+BWD_OPS_PER_PAIR = 50
+# Projection of one visible instance: faithfully rounded camera-space centre (3 compensated dot
+# products, 105), guarded Jacobian and 2D covariance by Cauchy-Binet (75), conic, centre and
+# pixel box (20); spherical-harmonics colour of degree 3: basis (30), 48 FMA, direction (10);
+# one exact ellipse-versus-rectangle test of a candidate tile or sub-tile (45).
+PROJ_OPS, SH3_OPS, TILE_TEST_OPS = 200, 90, 45
+# The projection adjoint moves per visible instance: 40 B of partials, 236 B of FP32 attributes
+# read, 236 B of attribute gradients accumulated and 8 B of identity.
+PROJECT_BWD_BYTES = 40 + 236 + 236 + 8
+# DRAM bytes (read + write) per launch on the full workload, from an ncu capture of the same
+# kernel on the 8-env case (16 views) scaled by the 8x views of the full launch; None while the
+# kernel has changed since its capture.
+TRAFFIC = {"composite": None}
 # FP32 operations per (voxel, view) of the TSDF fusion: camera-space point (9 FMA), reciprocal,
 # projection (4), bounds (4 compares), coverage test, normalised depth (2), sdf, truncation,
 # clamp (2), running average (3), weight update (2)
@@ -158,7 +170,10 @@ def _peaks():
 
 def fwd_bwd_500k(dev, warmup, steps):
     """Forward + backward of one 800x800 view of 500k SH-3 Gaussians (300k room + 8 x 25k posed
-    objects): render, then dL/d(all attributes, poses) for a fixed upstream gradient."""
+    objects): render, then dL/d(all attributes, poses) for a fixed upstream gradient.  Kernel
+    times per class are summed by the library's events over the timed steps; one instrumented
+    forward and backward outside the timed region count the reached pairs and the adjoint's
+    atomics."""
     import torch
     from paper_2507_21981_gb300 import scenes
     from paper_2507_21981_gb300.render import DeviceScene, Renderer
@@ -177,14 +192,29 @@ def fwd_bwd_500k(dev, warmup, steps):
         step()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kt = {}
     e0.record(stream)
     for _ in range(steps):
-        step()
+        rgb, depth, _ = r.render(ds)
+        for k, v in r.kernel_times().items():
+            kt["fwd_" + k] = kt.get("fwd_" + k, 0.0) + v
+        r.backward(ds, rgb, depth, g_rgb, g_d)
+        for k, v in r.kernel_times().items():
+            kt["bwd_" + k] = kt.get("bwd_" + k, 0.0) + v
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / steps
+    r.close()
+    ri = Renderer(mode="batched", profile=2)
+    rgb, depth, _ = ri.render(ds)
+    fwd = ri.stats()
+    ri.backward(ds, rgb, depth, g_rgb, g_d)
+    bwd = ri.stats()
+    ri.close()
     return {"ms": ms, "views": 1, "gaussians": sc.n_gaussians, "resolution": "800x800", "steps": steps,
-            "backward_kernels_ms": r.kernel_times()["backward"]}
+            "kernel_ms": {k: v / steps for k, v in kt.items() if v > 0},
+            "work": {"visible": fwd["n_visible"], "pairs": fwd["n_pairs"], "pairs_reached": fwd["px_reached"],
+                     "pairs_composited": fwd["px_composited"], "bwd_reductions": bwd["bwd_reductions"]}}
 
 
 def _time_renders(r, ds, out, steps, stream):
@@ -469,13 +499,15 @@ def tsdf_leg(dev, sc, warmup, steps):
     upd = n ** 3 * 64
     seen = float((W > 0).float().mean())
     mhz = _peaks()[0].get("sm_max_mhz", 2070.0)
-    peak = 152 * 128 * mhz * 1e6 / 1e12
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = n_sm * 128 * mhz * 1e6 / 1e12
     ops = upd * TSDF_OPS
     res = {"workload": "64 rendered depth views (640x480) of env 0 -> 256^3 TSDF over a 1.2 m cube", "voxels": n ** 3,
            "views": 64, "kernel_ms": k_ms, "gupdates_s": upd / k_ms / 1e6, "observed_frac": seen,
            "roofline": {"bound": "alu", "achieved": ops / k_ms / 1e9, "peak": peak, "unit": "Tops/s FP32",
                         "frac": ops / k_ms / 1e9 / peak, "ops_per_voxel_view": TSDF_OPS,
-                        "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"}, "steps": steps}
+                        "peak_source": f"{n_sm} SMs (device properties) x 128 FP32 lanes x max SM clock"},
+           "steps": steps}
     # the oracle on a 24^3 block of the grid (numpy FP64, one thread)
     import oracle
     Dh = depth.cpu().numpy().reshape(64, 480, 640)
@@ -756,6 +788,13 @@ def main():
     barrier()
     ms_plain = max_over_ranks(ev0.elapsed_time(ev1) / args.plain_steps, world, dev)
     plain_value = px_per_step * world / (ms_plain / 1e3) / 1e6
+    rp.close()
+    # the plain form's projection passes, timed by the library's events (one call)
+    rpp = Renderer(mode="plain", profile=True)
+    rpp.render(ds, out=out)
+    plain_k = rpp.kernel_times()
+    plain_stats = rpp.stats()
+    rpp.close()
 
     # ---------------------------------------------------------------- fwd+bwd at 500k Gaussians (one 800x800 view)
     fb = fwd_bwd_500k(dev, args.warmup, max(3, args.steps // 4))
@@ -788,35 +827,59 @@ def main():
     work = rc_.stats()
     rc_.close()
     mhz = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * mhz * 1e6 / 1e12          # FP32 lane-ops per second (FMA counted once), T/s
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sm * 128 * mhz * 1e6 / 1e12         # FP32 lane-ops per second (FMA counted once), T/s
+    alu_src = f"{n_sm} SMs (device properties) x 128 FP32 lanes x max SM clock {mhz:.0f} MHz ({peak_kind} MEASURED_PEAKS.json)"
+    hbm_src = f"{peak_kind} MEASURED_PEAKS.json hbm_gbs"
+    alu = lambda ops, ms_: {"bound": "alu", "unit": "Tops/s FP32", "peak": fp32_peak, "peak_source": alu_src,
+                            "achieved": ops / (ms_ / 1e3) / 1e12}
+    hbm = lambda byt, ms_: {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"], "peak_source": hbm_src,
+                            "achieved": byt / (ms_ / 1e3) / 1e9}
     comp_ops = work["px_reached"] * OPS_PER_PAIR
+    n_inst = stats["n_instances"]
     kernels = {
-        "composite": {"bound": "alu", "unit": "Tops/s FP32", "peak": fp32_peak,
-                      "achieved": comp_ops / (per_step["composite"] / 1e3) / 1e12,
+        "composite": {**alu(comp_ops, per_step["composite"]),
                       "units": {"pairs_reached": work["px_reached"], "pairs_composited": work["px_composited"],
-                                "pairs_evaluated": work["px_evaluated"], "ops_per_pair": OPS_PER_PAIR}},
-        "sort": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
-                 "achieved": sort_bytes / (per_step["sort"] / 1e3) / 1e9,
+                                "pairs_evaluated": work["px_evaluated"],
+                                "evaluated_over_reached": work["px_evaluated"] / max(work["px_reached"], 1),
+                                "ops_per_pair": OPS_PER_PAIR}},
+        "sort": {**hbm(sort_bytes, per_step["sort"]),
                  "units": {"instances": NV, "pairs": P, "depth_passes": 4, "tile_passes": passes,
                            "bytes_per_instance": 4 + 4 * 16 + 16 + 68, "bytes_per_pair": 8 + 4 + passes * 16}},
-        "emit": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
-                 "achieved": (sc.n_gaussians * 236 + NV * (48 + 8 + 12)) / (per_step["emit"] / 1e3) / 1e9,
-                 "units": {"gaussians": sc.n_gaussians, "visible": NV, "bytes_per_visible": 68}},
-        "count": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
-                  "achieved": sc.n_gaussians * 40 / (per_step["count"] / 1e3) / 1e9,
-                  "units": {"gaussians": sc.n_gaussians, "bytes_per_gaussian": 40}},
+        "emit": {**alu(NV * (PROJ_OPS + SH3_OPS) + P * TILE_TEST_OPS, per_step["emit"]),
+                 "units": {"visible": NV, "pairs": P, "ops_per_visible": PROJ_OPS + SH3_OPS,
+                           "ops_per_pair": TILE_TEST_OPS}},
+        "count": {**alu(NV * PROJ_OPS + P * TILE_TEST_OPS, per_step["count"]),
+                  "units": {"visible": NV, "pairs": P, "ops_per_visible": PROJ_OPS, "ops_per_pair": TILE_TEST_OPS,
+                            "instances_considered": n_inst}},
+        # the plain per-view form reads every attribute again for every view
+        "plain_projection": {**hbm(n_inst * (40 + 236) + plain_stats["n_visible"] * 68,
+                                   plain_k["count"] + plain_k["emit"]),
+                             "units": {"instances": n_inst, "bytes_per_instance": 40 + 236,
+                                       "visible": plain_stats["n_visible"], "bytes_per_visible": 68,
+                                       "ms": plain_k["count"] + plain_k["emit"]}},
     }
+    fk, fw = fb.get("kernel_ms", {}), fb.get("work", {})
+    if fk.get("bwd_backward") and fk.get("bwd_backward_project"):
+        kernels["composite_bwd"] = {**alu(fw["pairs_composited"] * BWD_OPS_PER_PAIR, fk["bwd_backward"]),
+                                    "units": {"pairs_composited": fw["pairs_composited"],
+                                              "ops_per_pair": BWD_OPS_PER_PAIR,
+                                              "reductions": fw["bwd_reductions"],
+                                              "reductions_per_s": fw["bwd_reductions"] / (fk["bwd_backward"] / 1e3),
+                                              "workload": "800x800 view, 500k Gaussians"}}
+        kernels["project_bwd"] = {**hbm(fw["visible"] * PROJECT_BWD_BYTES, fk["bwd_backward_project"]),
+                                  "units": {"visible": fw["visible"], "bytes_per_visible": PROJECT_BWD_BYTES,
+                                            "workload": "800x800 view, 500k Gaussians"}}
     for k in kernels.values():
         k["frac"] = k["achieved"] / k["peak"]
     dk = dom if dom in kernels else "composite"
     d = kernels[dk]
     roof = {"kernel": dk, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
-            "frac": d["frac"], "traffic": TRAFFIC.get(dk),
-            "peak_source": ("152 SMs x 128 FP32 lanes x max SM clock" if d["bound"] == "alu"
-                            else f"{peak_kind} MEASURED_PEAKS.json hbm_gbs")}
+            "frac": d["frac"], "traffic": TRAFFIC.get(dk), "peak_source": d["peak_source"]}
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "sm_count": n_sm,
         "data": "synthetic (seeded room + objects; the paper's scanned scenes are not available)",
         "config": {"workload": WORKLOAD, "views": ds.n_views, "pixels_per_step": px_per_step, "gaussians": sc.n_gaussians,
                    "l2": "inputs larger than L2 (255 MB attributes, 629 MB outputs per step)", "mode": "batched",
