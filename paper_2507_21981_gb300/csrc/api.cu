@@ -763,8 +763,9 @@ void enqueue_lists(dgs_ctx* ctx, ListBufs& lb, const Batch& B, const Launch& L, 
     uint32_t *dk = nullptr, *order = nullptr;
     SortCtl ctl;
     if (ctx->opt.spin_limit_us > 0) ctl.spin_ns = (uint64_t)ctx->opt.spin_limit_us * 1000ull;
-    SortCtl depth_ctl = ctl;
+    SortCtl depth_ctl = ctl, tile_ctl = ctl;
     if (ctx->opt.test_fault == 1) depth_ctl.mute_part = 1;
+    tile_ctl.runs = true;   // an instance's pairs are consecutive tiles of one view
     launch_sort(L, u32(lb.dkey0), u32(lb.ival0), u32(lb.dkey1), u32(lb.ival1), n_inst, kZBits, u32(lb.hist),
                 u32(lb.status), u32(lb.counters), B.d_err, &dk, &order, d_inst, depth_ctl);
     launch_tile_scan(L, order, u32(lb.ntile), n_inst, d_inst, u32(lb.poff), u32(lb.tparts), n_bound, d_pairs, B.d_err);
@@ -773,7 +774,7 @@ void enqueue_lists(dgs_ctx* ctx, ListBufs& lb, const Batch& B, const Launch& L, 
     uint32_t *tk = nullptr, *tv = nullptr;
     launch_sort(L, u32(lb.tkeys0), u32(lb.tvals0), u32(lb.tkeys1), u32(lb.tvals1), n_bound,
                 bits_for((uint64_t)n_tiles + 1), u32(lb.hist), u32(lb.status), u32(lb.counters), B.d_err, &tk,
-                &tv, d_pairs, ctl);
+                &tv, d_pairs, tile_ctl);
     tm.end();
     tm.begin(DGS_K_RANGES);
     launch_ranges(L, tk, n_bound, static_cast<uint2*>(lb.ranges.p), n_tiles, d_pairs);

@@ -86,14 +86,20 @@ __global__ void __launch_bounds__(256, 6) k_composite(const ViewDesc* __restrict
     float4* const sr1 = s_rec[w][1];
     float4* const sr2 = s_rec[w][2];
     uint32_t n_eval = 0, n_reach = 0, n_comp = 0;
+    // the key and value of the next chunk are loaded while the current chunk composites, so a
+    // chunk waits on one level of loads (its records) instead of three
+    uint32_t key_n = 0, val_n = 0;
+    if (range.x + lane < range.y) { key_n = __ldg(keys + range.x + lane); val_n = __ldg(vals + range.x + lane); }
     for (uint32_t base = range.x; base < range.y; base += 32) {
         if (__all_sync(0xffffffffu, done)) break;
         const uint32_t i = base + lane;
-        const bool rel = i < range.y && (__ldg(keys + i) & wbit);
+        const bool rel = i < range.y && (key_n & wbit);
+        const uint32_t val = val_n;
+        if (i + 32 < range.y) { key_n = __ldg(keys + i + 32); val_n = __ldg(vals + i + 32); }
         const uint32_t m = __ballot_sync(0xffffffffu, rel);
         if (m == 0) continue;
         if (rel) {
-            const Record* r = rec + __ldg(vals + i);
+            const Record* r = rec + val;
             const float4 a = r->r0, q = r->r1, col = r->r2;
             const int pos = __popc(m & lt);
             sr0[pos] = a; sr2[pos] = col;

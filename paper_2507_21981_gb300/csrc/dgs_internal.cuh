@@ -339,10 +339,18 @@ __device__ __forceinline__ bool tile_hit(float u, float v, float qa, float qb, f
 // x-section is -qb dy -+ sqrt((qlim - qc dy^2) / qa).  Its leftmost point lies at
 // dy_L = qb sqrt(qa qlim / (qc (qc + qa qb^2))) and its rightmost at -dy_L.  Per-instance
 // constants of the sub-tile test: (ye, dy_L, 1/qa).
+// (The sub-tile test is a filter with the binning limit's margin of 0.1 % + 1e-3 on q: the
+// hardware's approximate square root and division, within a few units of 2^-23, are ample.)
+__device__ __forceinline__ float approx_sqrt(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float4 ellipse_extent(float qa, float qb, float qc, float qlim) {
-    const float ye = sqrtf(qlim / qc);
-    const float dyl = qb * sqrtf(qa * qlim / (qc * fmaf(qa * qb, qb, qc)));
-    return make_float4(ye, dyl, 1.f / qa, 0.f);
+    const float ye = approx_sqrt(__fdividef(qlim, qc));
+    const float dyl = qb * approx_sqrt(__fdividef(qa * qlim, qc * fmaf(qa * qb, qb, qc)));
+    return make_float4(ye, dyl, __fdividef(1.f, qa), 0.f);
 }
 
 // Mask of the 8x4-pixel sub-tiles of tile (tx, ty) in which the ellipse holds a pixel centre's
@@ -366,8 +374,8 @@ __device__ __forceinline__ uint32_t subtile_mask(float u, float v, float qa, flo
             const float Y0 = fmaxf((float)py0 + 0.5f - v, -ext.x), Y1 = fminf((float)py1 + 0.5f - v, ext.x);
             if (Y0 > Y1) continue;
             const float dl = fminf(Y1, fmaxf(Y0, ext.y)), dr = fminf(Y1, fmaxf(Y0, -ext.y));
-            xlo = fmaf(-qb, dl, -sqrtf(fmaxf(0.f, fmaf(-qc * dl, dl, P.qbin)) * ext.z));
-            xhi = fmaf(-qb, dr, sqrtf(fmaxf(0.f, fmaf(-qc * dr, dr, P.qbin)) * ext.z));
+            xlo = fmaf(-qb, dl, -approx_sqrt(fmaxf(0.f, fmaf(-qc * dl, dl, P.qbin)) * ext.z));
+            xhi = fmaf(-qb, dr, approx_sqrt(fmaxf(0.f, fmaf(-qc * dr, dr, P.qbin)) * ext.z));
         }
         for (int sx = 0; sx < sub_cols; ++sx) {
             const int rx = tx * P.tile_w + sx * 8;
@@ -437,6 +445,7 @@ void launch_emit(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_n
 struct SortCtl {
     uint64_t spin_ns = 1000000000ull;
     uint32_t mute_part = 0xFFFFFFFFu;
+    bool runs = false;    // neighbouring keys share their high digits (histogram by runs)
 };
 
 // Stable LSD radix sort of (key, value) on the low key_bits bits.  With d_n non-null the

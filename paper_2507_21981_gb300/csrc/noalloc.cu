@@ -192,7 +192,10 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
     launch_sort(L, d_dk0, d_iv0, d_dk1, d_iv1, (uint32_t)n_vis, kZBits, d_hist, d_status, d_cnt, d_err, &dk, &order);
     launch_tile_scan(L, order, d_ntile, (uint32_t)n_vis, nullptr, d_poff, d_tparts, (uint32_t)n_pairs, d_total, d_err);
     launch_pairs(L, d_views, K, order, d_poff, d_rec, d_info, (uint32_t)n_vis, nullptr, P, d_k0, d_v0, (uint32_t)n_pairs);
-    launch_sort(L, d_k0, d_v0, d_k1, d_v1, (uint32_t)n_pairs, tbits, d_hist, d_status, d_cnt, d_err, &tk, &tv, d_total);
+    SortCtl tile_ctl;
+    tile_ctl.runs = true;
+    launch_sort(L, d_k0, d_v0, d_k1, d_v1, (uint32_t)n_pairs, tbits, d_hist, d_status, d_cnt, d_err, &tk, &tv, d_total,
+                tile_ctl);
     launch_ranges(L, tk, (uint32_t)n_pairs, d_ranges, (int)tiles_total, d_total);
     launch_composite(L, d_views, 0, V, (int)tiles_total, d_ranges, tk, tv, d_rec, P, out_rgb, out_depth, out_alpha,
                      nullptr);
