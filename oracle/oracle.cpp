@@ -538,6 +538,96 @@ void cols_pool(const ViewData& V, const oracle_opts* o, const std::vector<int>& 
     }
 }
 
+// Sec. IV: attribute and pose gradients of one instance from its 10 per-instance partials r
+// (u, v, conic a, b, c, opacity, r, g, b, z): the chain rule through projection, colour and pose.
+struct InstGrad {
+    double mean[3] = {0, 0, 0}, log_scale[3] = {0, 0, 0}, quat[4] = {0, 0, 0, 0}, logit = 0, sh[48] = {0}, pose[12] = {0};
+};
+
+void chain_rule(const oracle_scene* s, const Geo& G, const double r[10], InstGrad& out) {
+    const int64_t g = G.g;
+    double gRn[3][3] = {{0}}, gtn[3] = {0}, gmu[3] = {0};
+    // opacity
+    out.logit += r[5] * G.opac * (1 - G.opac);
+    // colour: rgb = max(0, sum c_k Y_k(d) + 1/2)
+    double gd[3] = {0, 0, 0};
+    const int nc = (G.deg + 1) * (G.deg + 1);
+    for (int ch = 0; ch < 3; ++ch) {
+        if (!(G.raw[ch] > 0)) continue;
+        const double gr = r[6 + ch];
+        for (int k = 0; k < nc; ++k) {
+            out.sh[k * 3 + ch] += gr * G.Y[k];
+            const double cf = s->sh[g * 48 + k * 3 + ch];
+            for (int j = 0; j < 3; ++j) gd[j] += gr * cf * G.dY[k][j];
+        }
+    }
+    const double dd = gd[0] * G.d[0] + gd[1] * G.d[1] + gd[2] * G.d[2];
+    double gdir[3];
+    for (int j = 0; j < 3; ++j) gdir[j] = (gd[j] - G.d[j] * dd) / G.dlen;
+    for (int j = 0; j < 3; ++j) gmu[j] += gdir[j];
+    // dir = mu - o_local, o_local = Rn^T (o - tn)
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) gRn[a][b] += (G.ocam[a] - G.tn[a]) * (-gdir[b]);
+    for (int a = 0; a < 3; ++a) { double v = 0; for (int b = 0; b < 3; ++b) v += G.Rn[a][b] * (-gdir[b]); gtn[a] -= v; }
+    // conic -> 2D covariance: gCov = -Q G Q with G = [[ga, gb/2],[gb/2, gc]]
+    const double Gm[2][2] = {{r[2], 0.5 * r[3]}, {0.5 * r[3], r[4]}};
+    double QG[2][2], gCov[2][2];
+    for (int a = 0; a < 2; ++a) for (int b = 0; b < 2; ++b) QG[a][b] = G.Q[a][0] * Gm[0][b] + G.Q[a][1] * Gm[1][b];
+    for (int a = 0; a < 2; ++a) for (int b = 0; b < 2; ++b) gCov[a][b] = -(QG[a][0] * G.Q[0][b] + QG[a][1] * G.Q[1][b]);
+    // Cov = T Sigma_w T^T + lp I:  gSigma_w = T^T gCov T,  gT = 2 gCov T Sigma_w
+    double gSigw[3][3], gT[2][3];
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) {
+        double v = 0; for (int m = 0; m < 2; ++m) for (int n = 0; n < 2; ++n) v += G.T[m][a] * gCov[m][n] * G.T[n][b];
+        gSigw[a][b] = v; }
+    for (int a = 0; a < 2; ++a) for (int b = 0; b < 3; ++b) {
+        double v = 0;
+        for (int m = 0; m < 2; ++m) for (int k = 0; k < 3; ++k) v += gCov[a][m] * G.T[m][k] * G.Sigw[k][b];
+        gT[a][b] = 2 * v; }
+    // T = J Wc: gJ = gT Wc^T
+    double gJ[2][3];
+    for (int a = 0; a < 2; ++a) for (int b = 0; b < 3; ++b) {
+        double v = 0; for (int k = 0; k < 3; ++k) v += gT[a][k] * G.Wc[b][k]; gJ[a][b] = v; }
+    double gt[3] = {0, 0, 0};
+    const double tx = G.t[0], ty = G.t[1], tz = G.t[2];
+    gt[2] += gJ[0][0] * (-G.fx / (tz * tz)) + gJ[1][1] * (-G.fy / (tz * tz));
+    if (!G.clx) { gt[2] += gJ[0][2] * (2 * G.fx * tx / (tz * tz * tz)); gt[0] += gJ[0][2] * (-G.fx / (tz * tz)); }
+    else { gt[2] += gJ[0][2] * (G.fx * G.xc / (tz * tz)); }
+    if (!G.cly) { gt[2] += gJ[1][2] * (2 * G.fy * ty / (tz * tz * tz)); gt[1] += gJ[1][2] * (-G.fy / (tz * tz)); }
+    else { gt[2] += gJ[1][2] * (G.fy * G.yc / (tz * tz)); }
+    // mean in pixels and depth
+    gt[0] += r[0] * G.fx / tz; gt[2] += -r[0] * G.fx * tx / (tz * tz);
+    gt[1] += r[1] * G.fy / tz; gt[2] += -r[1] * G.fy * ty / (tz * tz);
+    gt[2] += r[9];
+    // t = Wc mu_w + tc; mu_w = Rn mu + tn
+    double gmuw[3];
+    for (int a = 0; a < 3; ++a) gmuw[a] = G.Wc[0][a] * gt[0] + G.Wc[1][a] * gt[1] + G.Wc[2][a] * gt[2];
+    for (int a = 0; a < 3; ++a) { gtn[a] += gmuw[a]; for (int b = 0; b < 3; ++b) { gRn[a][b] += gmuw[a] * G.mu[b]; gmu[b] += G.Rn[a][b] * gmuw[a]; } }
+    // Sigma_w = Rn Sigma Rn^T: gSigma = Rn^T gSigw Rn, gRn += 2 gSigw Rn Sigma
+    double gSig[3][3], tmp[3][3];
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) { double v = 0; for (int k = 0; k < 3; ++k) v += gSigw[a][k] * G.Rn[k][b]; tmp[a][b] = v; }
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) { double v = 0; for (int k = 0; k < 3; ++k) v += G.Rn[k][a] * tmp[k][b]; gSig[a][b] = v; }
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) { double v = 0; for (int k = 0; k < 3; ++k) v += tmp[a][k] * G.Sig[k][b]; gRn[a][b] += 2 * v; }
+    // Sigma = M M^T, M = Rq diag(sc): gM = 2 gSigma M
+    double gM[3][3];
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) { double v = 0; for (int k = 0; k < 3; ++k) v += gSig[a][k] * G.M[k][b]; gM[a][b] = 2 * v; }
+    for (int j = 0; j < 3; ++j) { double v = 0; for (int i2 = 0; i2 < 3; ++i2) v += G.Rq[i2][j] * gM[i2][j]; out.log_scale[j] += v * G.sc[j]; }
+    double gRq[3][3];
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) gRq[a][b] = gM[a][b] * G.sc[b];
+    // Rq(qn) -> qn
+    const double w = G.qn[0], x = G.qn[1], yq = G.qn[2], zq = G.qn[3];
+    const double dRw[3][3] = {{0, -2 * zq, 2 * yq}, {2 * zq, 0, -2 * x}, {-2 * yq, 2 * x, 0}};
+    const double dRx[3][3] = {{0, 2 * yq, 2 * zq}, {2 * yq, -4 * x, -2 * w}, {2 * zq, 2 * w, -4 * x}};
+    const double dRy[3][3] = {{-4 * yq, 2 * x, 2 * w}, {2 * x, 0, 2 * zq}, {-2 * w, 2 * zq, -4 * yq}};
+    const double dRz[3][3] = {{-4 * zq, -2 * w, 2 * x}, {2 * w, -4 * zq, 2 * yq}, {2 * x, 2 * yq, 0}};
+    double gqn[4] = {0, 0, 0, 0};
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) {
+        gqn[0] += gRq[a][b] * dRw[a][b]; gqn[1] += gRq[a][b] * dRx[a][b];
+        gqn[2] += gRq[a][b] * dRy[a][b]; gqn[3] += gRq[a][b] * dRz[a][b]; }
+    const double qd = gqn[0] * G.qn[0] + gqn[1] * G.qn[1] + gqn[2] * G.qn[2] + gqn[3] * G.qn[3];
+    for (int k = 0; k < 4; ++k) out.quat[k] += (gqn[k] - G.qn[k] * qd) / G.qlen;
+    for (int k = 0; k < 3; ++k) out.mean[k] += gmu[k];
+    for (int a = 0; a < 3; ++a) { for (int b = 0; b < 3; ++b) out.pose[a * 4 + b] += gRn[a][b]; out.pose[a * 4 + 3] += gtn[a]; }
+}
+
 }  // namespace
 
 extern "C" {
@@ -657,11 +747,20 @@ int oracle_render_view(const oracle_scene* s, const oracle_opts* o, int e, int c
 // Sec. IV (assets fitted by gradient descent on rendered images): adjoint of
 // oracle_render_view's primary branch for L = sum grad_rgb . RGB + grad_depth . D.
 // Accumulates (+=) into the gradient arrays, which are laid out like the scene arrays
-// (g_sh is [G,16,3]; g_pose is [E,K,12]).  Returns 0, or -1 on bad arguments.
+// (g_sh is [G,16,3]; g_pose is [E,K,12]).  The err_* arrays (same layouts, all null or all
+// set) receive an FP32 error model of the same gradients: per composited (pixel, Gaussian)
+// pair, an absolute error bound of each of its 10 per-instance partials -- from the relative
+// bounds of alpha and T of the forward model, the FP32 cancellation in the remainder
+// (C_out - P_i) / T_{i+1} (a sum of the pixel's composited terms, (n + 2) u of the colour's
+// magnitude, divided by T_{i+1}), the FP32 colour and depth, the centre error bound in the pixel
+// offsets, and (P + 32) u of the sum of the partial's magnitudes for its FP32 accumulation over
+// the P pixels -- carried through the chain rule one partial at a time and added in absolute
+// value.  Returns 0, or -1 on bad arguments.
 int oracle_backward_view(const oracle_scene* s, const oracle_opts* o, int e, int c,
                          const double* grad_rgb, const double* grad_depth,
                          double* g_mean, double* g_log_scale, double* g_quat, double* g_logit,
-                         double* g_sh, double* g_pose) {
+                         double* g_sh, double* g_pose, double* err_mean, double* err_log_scale, double* err_quat,
+                         double* err_logit, double* err_sh, double* err_pose) {
     ViewData V;
     if (!build_view(s, o, e, c, V)) return -1;
     std::vector<std::vector<int>> rows;
@@ -669,19 +768,24 @@ int oracle_backward_view(const oracle_scene* s, const oracle_opts* o, int e, int
     const int W = V.W, H = V.H;
     const int nth = n_threads(o);
     const size_t NG = V.geo.size();
-    // Per-instance adjoints: du, dv, da, db, dc, dopac, dr, dg, db, dz  (10 per instance)
-    std::vector<std::vector<double>> acc(nth, std::vector<double>(NG * 10, 0.0));
+    const bool want_err = err_mean != nullptr;
+    const double u = 5.9604644775390625e-08;
+    // Per-instance adjoints: du, dv, da, db, dc, dopac, dr, dg, db, dz (10 per instance); with the
+    // error model also their error bounds (10), magnitudes (10) and pixel count (1)
+    const size_t NA = want_err ? 31 : 10;
+    std::vector<std::vector<double>> acc(nth, std::vector<double>(NG * NA, 0.0));
     parallel_for(H, nth, [&](int64_t y, int tid) {
         std::vector<std::vector<int>> cols(W);
         cols_pool(V, o, rows[y], cols);
         std::vector<Cand> cand;
-        std::vector<int> ci; std::vector<double> al, Ti, ex;
+        std::vector<int> ci; std::vector<double> al, Ti, ex, dTs;
         double* A = acc[tid].data();
         for (int x = 0; x < W; ++x) {
             pixel_candidates(V, o, cols[x], x, (int)y, cand);
-            // Primary forward, recording the contributors.
-            ci.clear(); al.clear(); Ti.clear(); ex.clear();
-            double T = 1.0;
+            // Primary forward, recording the contributors (and the relative FP32 bound of T before each).
+            ci.clear(); al.clear(); Ti.clear(); ex.clear(); dTs.clear();
+            double T = 1.0, dT = 0.0, Mc = std::max({std::fabs(o->bg[0]), std::fabs(o->bg[1]), std::fabs(o->bg[2])}),
+                   Mz = 0.0;
             for (const Cand& cd : cand) {
                 const Geo& G = V.geo[cd.idx];
                 if (!G.present || cd.q > o->q_max) continue;
@@ -691,125 +795,107 @@ int oracle_backward_view(const oracle_scene* s, const oracle_opts* o, int e, int
                 const double Tn = T * (1 - a);
                 if (Tn < o->t_min) break;
                 ci.push_back((int)(&cd - cand.data())); al.push_back(a); Ti.push_back(T); ex.push_back(e1);
+                dTs.push_back(dT);
+                dT += a / (1 - a) * cd.da + 2 * u;
+                Mc = std::max({Mc, G.rgb[0], G.rgb[1], G.rgb[2]});
+                Mz = std::max(Mz, std::fabs(G.z));
                 T = Tn;
             }
             const int64_t p = y * W + x;
             const double gC[3] = {grad_rgb[p * 3], grad_rgb[p * 3 + 1], grad_rgb[p * 3 + 2]};
             const double gD = grad_depth ? grad_depth[p] : 0.0;
+            const double nc = (double)ci.size();
             // Suffix sums behind contributor i (including the background term bg*T_final).
             double S[3] = {o->bg[0] * T, o->bg[1] * T, o->bg[2] * T}, SD = 0;
             for (int n = (int)ci.size() - 1; n >= 0; --n) {
                 const Cand& cd = cand[ci[n]];
                 const Geo& G = V.geo[cd.idx];
                 const double a = al[n], Tb = Ti[n], w = a * Tb, Ta = Tb * (1 - a);
-                double* r = A + (size_t)cd.idx * 10;
-                r[6] += w * gC[0]; r[7] += w * gC[1]; r[8] += w * gC[2]; r[9] += w * gD;
+                double* r = A + (size_t)cd.idx * NA;
                 // dL/dalpha = T_i [ gC . (rgb_i - S_i/T_{i+1}) + gD (z_i - SD_i/T_{i+1}) ]
                 double ga = 0;
                 for (int ch = 0; ch < 3; ++ch) ga += gC[ch] * (G.rgb[ch] - S[ch] / Ta);
                 ga += gD * (G.z - SD / Ta);
                 ga *= Tb;
+                double inc[10] = {0, 0, 0, 0, 0, 0, w * gC[0], w * gC[1], w * gC[2], w * gD};
+                double err[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+                const double dTa = dTs[n] + a / (1 - a) * cd.da + 2 * u;   // relative bound of T after
+                if (want_err) {
+                    const double ew = std::fabs(w) * (cd.da + dTs[n] + 2 * u);
+                    for (int ch = 0; ch < 3; ++ch) err[6 + ch] = ew * std::fabs(gC[ch]);
+                    err[9] = ew * std::fabs(gD);
+                }
+                double e_ga = 0;
+                if (want_err) {
+                    // remainder (C_out - P_i) / T_{i+1}: FP32 sums of the pixel's composited terms
+                    e_ga = std::fabs(ga) * (dTs[n] + 2 * u);
+                    for (int ch = 0; ch < 3; ++ch)
+                        e_ga += Tb * std::fabs(gC[ch]) * (64 * u * (std::fabs(G.rgb[ch]) + 1.0) + (nc + 2) * u * Mc / Ta +
+                                                          std::fabs(S[ch] / Ta) * (dTa + 2 * u));
+                    e_ga += Tb * std::fabs(gD) * (G.dz + (nc + 2) * u * Mz / Ta + std::fabs(SD / Ta) * (dTa + 2 * u));
+                }
                 for (int ch = 0; ch < 3; ++ch) S[ch] += w * G.rgb[ch];
                 SD += w * G.z;
-                if (G.opac * ex[n] > o->alpha_max) continue;   // clamped: no gradient to opacity or q
-                r[5] += ga * ex[n];
-                const double gq = ga * (-0.5 * a);
-                const double dx = cd.dx, dy = cd.dy;           // d = pixel - u
-                r[2] += gq * dx * dx; r[3] += gq * 2 * dx * dy; r[4] += gq * dy * dy;
-                r[0] += gq * (-2.0) * (G.Q[0][0] * dx + G.Q[0][1] * dy);
-                r[1] += gq * (-2.0) * (G.Q[0][1] * dx + G.Q[1][1] * dy);
+                if (!(G.opac * ex[n] > o->alpha_max)) {   // clamped: no gradient to opacity or q
+                    inc[5] = ga * ex[n];
+                    const double gq = ga * (-0.5 * a);
+                    const double dx = cd.dx, dy = cd.dy;           // d = pixel - u
+                    const double lx = G.Q[0][0] * dx + G.Q[0][1] * dy, ly = G.Q[0][1] * dx + G.Q[1][1] * dy;
+                    inc[2] = gq * dx * dx; inc[3] = gq * 2 * dx * dy; inc[4] = gq * dy * dy;
+                    inc[0] = gq * (-2.0) * lx;
+                    inc[1] = gq * (-2.0) * ly;
+                    if (want_err) {
+                        const double e_gq = 0.5 * a * (e_ga + std::fabs(ga) * cd.da);
+                        const double du = G.du, dv = G.dv, agq = std::fabs(gq);
+                        err[5] = e_ga * ex[n] + std::fabs(ga * ex[n]) * cd.da;
+                        err[2] = e_gq * dx * dx + agq * (2 * std::fabs(dx) * du + 4 * u * dx * dx);
+                        err[3] = 2 * (e_gq * std::fabs(dx * dy) + agq * (std::fabs(dy) * du + std::fabs(dx) * dv + 4 * u * std::fabs(dx * dy)));
+                        err[4] = e_gq * dy * dy + agq * (2 * std::fabs(dy) * dv + 4 * u * dy * dy);
+                        err[0] = 2 * (e_gq * std::fabs(lx) + agq * (std::fabs(G.Q[0][0]) * du + std::fabs(G.Q[0][1]) * dv +
+                                                                   8 * u * (std::fabs(G.Q[0][0] * dx) + std::fabs(G.Q[0][1] * dy))));
+                        err[1] = 2 * (e_gq * std::fabs(ly) + agq * (std::fabs(G.Q[0][1]) * du + std::fabs(G.Q[1][1]) * dv +
+                                                                   8 * u * (std::fabs(G.Q[0][1] * dx) + std::fabs(G.Q[1][1] * dy))));
+                    }
+                }
+                for (int k = 0; k < 10; ++k) r[k] += inc[k];
+                if (want_err) {
+                    for (int k = 0; k < 10; ++k) { r[10 + k] += err[k]; r[20 + k] += std::fabs(inc[k]); }
+                    r[30] += 1;
+                }
             }
         }
     });
-    std::vector<double> tot(NG * 10, 0.0);
-    for (int t = 0; t < nth; ++t) for (size_t i = 0; i < NG * 10; ++i) tot[i] += acc[t][i];
+    std::vector<double> tot(NG * NA, 0.0);
+    for (int t = 0; t < nth; ++t) for (size_t i = 0; i < NG * NA; ++i) tot[i] += acc[t][i];
+    auto add = [&](const InstGrad& q, const Geo& G, double* gm, double* gl, double* gqt, double* go, double* gs,
+                   double* gp, bool absval) {
+        auto f = [absval](double v) { return absval ? std::fabs(v) : v; };
+        const int64_t g = G.g;
+        for (int k = 0; k < 3; ++k) { gm[g * 3 + k] += f(q.mean[k]); gl[g * 3 + k] += f(q.log_scale[k]); }
+        for (int k = 0; k < 4; ++k) gqt[g * 4 + k] += f(q.quat[k]);
+        go[g] += f(q.logit);
+        for (int k = 0; k < 48; ++k) gs[g * 48 + k] += f(q.sh[k]);
+        double* pp = gp + ((int64_t)e * s->K + G.slot) * 12;
+        for (int k = 0; k < 12; ++k) pp[k] += f(q.pose[k]);
+    };
     // Chain rule through projection, colour and pose (serial: deterministic accumulation).
     for (size_t i = 0; i < NG; ++i) {
         const Geo& G = V.geo[i];
-        const double* r = &tot[i * 10];
+        const double* r = &tot[i * NA];
         bool any = false; for (int k = 0; k < 10; ++k) any |= r[k] != 0; if (!any) continue;
-        const int64_t g = G.g;
-        double gRn[3][3] = {{0}}, gtn[3] = {0}, gmu[3] = {0};
-        // opacity
-        g_logit[g] += r[5] * G.opac * (1 - G.opac);
-        // colour: rgb = max(0, sum c_k Y_k(d) + 1/2)
-        double gd[3] = {0, 0, 0};
-        const int nc = (G.deg + 1) * (G.deg + 1);
-        for (int ch = 0; ch < 3; ++ch) {
-            if (!(G.raw[ch] > 0)) continue;
-            const double gr = r[6 + ch];
-            for (int k = 0; k < nc; ++k) {
-                g_sh[g * 48 + k * 3 + ch] += gr * G.Y[k];
-                const double cf = s->sh[g * 48 + k * 3 + ch];
-                for (int j = 0; j < 3; ++j) gd[j] += gr * cf * G.dY[k][j];
-            }
+        InstGrad q;
+        chain_rule(s, G, r, q);
+        add(q, G, g_mean, g_log_scale, g_quat, g_logit, g_sh, g_pose, false);
+        if (!want_err) continue;
+        // error bound of each partial: its per-pixel bounds plus its FP32 accumulation over the pixels
+        for (int k = 0; k < 10; ++k) {
+            double unit[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+            unit[k] = r[10 + k] + (r[30] + 32) * u * r[20 + k];
+            if (unit[k] == 0) continue;
+            InstGrad qk;
+            chain_rule(s, G, unit, qk);
+            add(qk, G, err_mean, err_log_scale, err_quat, err_logit, err_sh, err_pose, true);
         }
-        const double dd = gd[0] * G.d[0] + gd[1] * G.d[1] + gd[2] * G.d[2];
-        double gdir[3];
-        for (int j = 0; j < 3; ++j) gdir[j] = (gd[j] - G.d[j] * dd) / G.dlen;
-        for (int j = 0; j < 3; ++j) gmu[j] += gdir[j];
-        // dir = mu - o_local, o_local = Rn^T (o - tn)
-        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) gRn[a][b] += (G.ocam[a] - G.tn[a]) * (-gdir[b]);
-        for (int a = 0; a < 3; ++a) { double v = 0; for (int b = 0; b < 3; ++b) v += G.Rn[a][b] * (-gdir[b]); gtn[a] -= v; }
-        // conic -> 2D covariance: gCov = -Q G Q with G = [[ga, gb/2],[gb/2, gc]]
-        const double Gm[2][2] = {{r[2], 0.5 * r[3]}, {0.5 * r[3], r[4]}};
-        double QG[2][2], gCov[2][2];
-        for (int a = 0; a < 2; ++a) for (int b = 0; b < 2; ++b) QG[a][b] = G.Q[a][0] * Gm[0][b] + G.Q[a][1] * Gm[1][b];
-        for (int a = 0; a < 2; ++a) for (int b = 0; b < 2; ++b) gCov[a][b] = -(QG[a][0] * G.Q[0][b] + QG[a][1] * G.Q[1][b]);
-        // Cov = T Sigma_w T^T + lp I:  gSigma_w = T^T gCov T,  gT = 2 gCov T Sigma_w
-        double gSigw[3][3], gT[2][3];
-        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) {
-            double v = 0; for (int m = 0; m < 2; ++m) for (int n = 0; n < 2; ++n) v += G.T[m][a] * gCov[m][n] * G.T[n][b];
-            gSigw[a][b] = v; }
-        for (int a = 0; a < 2; ++a) for (int b = 0; b < 3; ++b) {
-            double v = 0;
-            for (int m = 0; m < 2; ++m) for (int k = 0; k < 3; ++k) v += gCov[a][m] * G.T[m][k] * G.Sigw[k][b];
-            gT[a][b] = 2 * v; }
-        // T = J Wc: gJ = gT Wc^T
-        double gJ[2][3];
-        for (int a = 0; a < 2; ++a) for (int b = 0; b < 3; ++b) {
-            double v = 0; for (int k = 0; k < 3; ++k) v += gT[a][k] * G.Wc[b][k]; gJ[a][b] = v; }
-        double gt[3] = {0, 0, 0};
-        const double tx = G.t[0], ty = G.t[1], tz = G.t[2];
-        gt[2] += gJ[0][0] * (-G.fx / (tz * tz)) + gJ[1][1] * (-G.fy / (tz * tz));
-        if (!G.clx) { gt[2] += gJ[0][2] * (2 * G.fx * tx / (tz * tz * tz)); gt[0] += gJ[0][2] * (-G.fx / (tz * tz)); }
-        else { gt[2] += gJ[0][2] * (G.fx * G.xc / (tz * tz)); }
-        if (!G.cly) { gt[2] += gJ[1][2] * (2 * G.fy * ty / (tz * tz * tz)); gt[1] += gJ[1][2] * (-G.fy / (tz * tz)); }
-        else { gt[2] += gJ[1][2] * (G.fy * G.yc / (tz * tz)); }
-        // mean in pixels and depth
-        gt[0] += r[0] * G.fx / tz; gt[2] += -r[0] * G.fx * tx / (tz * tz);
-        gt[1] += r[1] * G.fy / tz; gt[2] += -r[1] * G.fy * ty / (tz * tz);
-        gt[2] += r[9];
-        // t = Wc mu_w + tc; mu_w = Rn mu + tn
-        double gmuw[3];
-        for (int a = 0; a < 3; ++a) gmuw[a] = G.Wc[0][a] * gt[0] + G.Wc[1][a] * gt[1] + G.Wc[2][a] * gt[2];
-        for (int a = 0; a < 3; ++a) { gtn[a] += gmuw[a]; for (int b = 0; b < 3; ++b) { gRn[a][b] += gmuw[a] * G.mu[b]; gmu[b] += G.Rn[a][b] * gmuw[a]; } }
-        // Sigma_w = Rn Sigma Rn^T: gSigma = Rn^T gSigw Rn, gRn += 2 gSigw Rn Sigma
-        double gSig[3][3], tmp[3][3];
-        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) { double v = 0; for (int k = 0; k < 3; ++k) v += gSigw[a][k] * G.Rn[k][b]; tmp[a][b] = v; }
-        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) { double v = 0; for (int k = 0; k < 3; ++k) v += G.Rn[k][a] * tmp[k][b]; gSig[a][b] = v; }
-        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) { double v = 0; for (int k = 0; k < 3; ++k) v += tmp[a][k] * G.Sig[k][b]; gRn[a][b] += 2 * v; }
-        // Sigma = M M^T, M = Rq diag(sc): gM = 2 gSigma M
-        double gM[3][3];
-        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) { double v = 0; for (int k = 0; k < 3; ++k) v += gSig[a][k] * G.M[k][b]; gM[a][b] = 2 * v; }
-        for (int j = 0; j < 3; ++j) { double v = 0; for (int i2 = 0; i2 < 3; ++i2) v += G.Rq[i2][j] * gM[i2][j]; g_log_scale[g * 3 + j] += v * G.sc[j]; }
-        double gRq[3][3];
-        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) gRq[a][b] = gM[a][b] * G.sc[b];
-        // Rq(qn) -> qn
-        const double w = G.qn[0], x = G.qn[1], yq = G.qn[2], zq = G.qn[3];
-        const double dRw[3][3] = {{0, -2 * zq, 2 * yq}, {2 * zq, 0, -2 * x}, {-2 * yq, 2 * x, 0}};
-        const double dRx[3][3] = {{0, 2 * yq, 2 * zq}, {2 * yq, -4 * x, -2 * w}, {2 * zq, 2 * w, -4 * x}};
-        const double dRy[3][3] = {{-4 * yq, 2 * x, 2 * w}, {2 * x, 0, 2 * zq}, {-2 * w, 2 * zq, -4 * yq}};
-        const double dRz[3][3] = {{-4 * zq, -2 * w, 2 * x}, {2 * w, -4 * zq, 2 * yq}, {2 * x, 2 * yq, 0}};
-        double gqn[4] = {0, 0, 0, 0};
-        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) {
-            gqn[0] += gRq[a][b] * dRw[a][b]; gqn[1] += gRq[a][b] * dRx[a][b];
-            gqn[2] += gRq[a][b] * dRy[a][b]; gqn[3] += gRq[a][b] * dRz[a][b]; }
-        const double qd = gqn[0] * G.qn[0] + gqn[1] * G.qn[1] + gqn[2] * G.qn[2] + gqn[3] * G.qn[3];
-        for (int k = 0; k < 4; ++k) g_quat[g * 4 + k] += (gqn[k] - G.qn[k] * qd) / G.qlen;
-        for (int k = 0; k < 3; ++k) g_mean[g * 3 + k] += gmu[k];
-        double* gp = g_pose + ((int64_t)e * s->K + G.slot) * 12;
-        for (int a = 0; a < 3; ++a) { for (int b = 0; b < 3; ++b) gp[a * 4 + b] += gRn[a][b]; gp[a * 4 + 3] += gtn[a]; }
     }
     return 0;
 }

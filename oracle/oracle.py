@@ -87,7 +87,7 @@ def _load():
             lib.oracle_render_view.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 8 + \
                 [C.c_int64, C.c_void_p, C.c_void_p]
             lib.oracle_backward_view.restype = C.c_int
-            lib.oracle_backward_view.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 8
+            lib.oracle_backward_view.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 14
             lib.oracle_sh_basis.restype = None
             lib.oracle_sh_basis.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
             _lib = lib
@@ -212,39 +212,45 @@ def render_view(scene, e: int, c: int, opts: OracleOptions | None = None, packed
                       ea, int(stats[12]))
 
 
-def _grad_buffers(pk, scene):
+def _grad_buffers(pk, scene, with_error=False):
     E, K = scene.env_node_ids.shape
-    return dict(mean=np.zeros((pk.G, 3)), log_scale=np.zeros((pk.G, 3)), quat=np.zeros((pk.G, 4)),
-                opacity_logit=np.zeros(pk.G), sh=np.zeros((pk.G, 16, 3)), pose=np.zeros((E, K, 3, 4)))
+    g = dict(mean=np.zeros((pk.G, 3)), log_scale=np.zeros((pk.G, 3)), quat=np.zeros((pk.G, 4)),
+             opacity_logit=np.zeros(pk.G), sh=np.zeros((pk.G, 16, 3)), pose=np.zeros((E, K, 3, 4)))
+    if with_error:
+        g.update({"err_" + k: np.zeros_like(v) for k, v in list(g.items())})
+    return g
 
 
 def backward_view(scene, e: int, c: int, grad_rgb, grad_depth=None, opts: OracleOptions | None = None,
-                  packed=None, out=None) -> dict:
+                  packed=None, out=None, with_error: bool = False) -> dict:
     """Sec. IV (assets fitted by gradient descent on rendered images).  Adjoint of view (e, c)
     for L = sum(grad_rgb * RGB) + sum(grad_depth * D).
 
     Returns (or accumulates into `out`) gradients laid out as concatenated node arrays: mean [G,3],
-    log_scale [G,3], quat [G,4], opacity_logit [G], sh [G,16,3], pose [E,K,3,4]."""
+    log_scale [G,3], quat [G,4], opacity_logit [G], sh [G,16,3], pose [E,K,3,4].  with_error adds
+    "err_<name>" arrays of the same layouts: the FP32 error model of each gradient entry (header
+    of oracle_backward_view in oracle.cpp)."""
     lib = _load()
     pk = packed or _Packed(scene)
     o = (opts or OracleOptions())._c()
-    g = out if out is not None else _grad_buffers(pk, scene)
+    g = out if out is not None else _grad_buffers(pk, scene, with_error)
     gr = np.ascontiguousarray(grad_rgb, np.float64)
     gd = None if grad_depth is None else np.ascontiguousarray(grad_depth, np.float64)
-    rc = lib.oracle_backward_view(C.byref(pk.c), C.byref(o), e, c, _p(gr), _p(gd), _p(g["mean"]),
-                                  _p(g["log_scale"]), _p(g["quat"]), _p(g["opacity_logit"]), _p(g["sh"]), _p(g["pose"]))
+    names = ("mean", "log_scale", "quat", "opacity_logit", "sh", "pose")
+    errs = [_p(g["err_" + n]) for n in names] if with_error else [None] * 6
+    rc = lib.oracle_backward_view(C.byref(pk.c), C.byref(o), e, c, _p(gr), _p(gd), *[_p(g[n]) for n in names], *errs)
     if rc != 0:
         raise ValueError(f"oracle_backward_view failed ({rc})")
     return g
 
 
-def backward_scene(scene, grad_rgb_views, grad_depth_views, opts=None) -> dict:
+def backward_scene(scene, grad_rgb_views, grad_depth_views, opts=None, with_error: bool = False) -> dict:
     """Sec. IV: sum of backward_view over all views (lists of per-view gradient images)."""
     pk = _Packed(scene)
-    g = _grad_buffers(pk, scene)
+    g = _grad_buffers(pk, scene, with_error)
     for v, (e, c) in enumerate(scene.views):
         backward_view(scene, e, c, grad_rgb_views[v], None if grad_depth_views is None else grad_depth_views[v],
-                      opts, pk, g)
+                      opts, pk, g, with_error)
     return g
 
 

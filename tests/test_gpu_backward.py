@@ -6,12 +6,16 @@ checked branch by branch by the forward tests) or where a contributor's gradient
 alpha clamp, the Jacobian guard, the colour clamp at 0 -- lies within its FP32 band (the
 rendered value is continuous there but its derivative is not).
 
-Tolerance per gradient tensor: |g - g*| <= 1e-3 |g*| + 1e-5 max|g*| for every entry but at most a
-1e-5 fraction of them, those few within ten times that bound, and a relative L2 error of at most
-1e-4.  The outliers are thin, nearly opaque splats whose gradient is a sum of large per-pixel
-terms: an FP32 projected centre (error ~1e-4 px) moves it by (Hessian x 1e-4), which exceeds the
-element bound while the tensor stays accurate.
+Tolerance per gradient entry (no figure in the paper or the method's statement):
+|g - g*| <= 1e-3 |g*| + 1e-5 max|g*| + 2 e*, and per tensor a relative L2 error of at most 1e-4.
+e* is the oracle's FP32 error model of that entry (header of oracle_backward_view): every
+composited (pixel, Gaussian) pair contributes absolute error bounds of its per-instance partials
+(alpha and transmittance rounding, the cancellation in (C_out - P_i) / T_{i+1}, colour, depth and
+centre rounding, the FP32 accumulation over the pixels), carried through the chain rule in
+absolute value.  It matters where an entry is a small residue of large per-pixel terms of both
+signs (thin, nearly opaque splats), for which a bound relative to the entry itself is too tight.
 """
+
 import numpy as np
 import pytest
 
@@ -36,8 +40,8 @@ def _with_sh(sc, deg, seed):
 
 
 def _gradients(sc, seed=0, mode="batched", dtype="f32", oracle_scene=None):
-    """GPU gradients of `sc` stored as `dtype`, and the oracle's for `oracle_scene` (default sc)
-    under the same upstream gradients."""
+    """GPU gradients of `sc` stored as `dtype`, and the oracle's (with its FP32 error model) for
+    `oracle_scene` (default sc) under the same upstream gradients."""
     from paper_2507_21981_gb300.render import DeviceScene, Renderer
     osc = sc if oracle_scene is None else oracle_scene
     ds = DeviceScene(sc, device="cuda:0", dtype=dtype)
@@ -63,36 +67,40 @@ def _gradients(sc, seed=0, mode="batched", dtype="f32", oracle_scene=None):
         gDv.append(d.astype(np.float64))
     node_grads, gposes = r.backward(ds, rgb, depth, torch.from_numpy(gC).cuda(), torch.from_numpy(gD).cuda())
     torch.cuda.synchronize()
-    ref = O.backward_scene(osc, gCv, gDv, O.OracleOptions())
+    ref = O.backward_scene(osc, gCv, gDv, O.OracleOptions(), with_error=True)
     r.close()
     return node_grads, gposes, ref
 
 
-def _check(name, g, r):
+def _check(name, g, r, e, counts=None):
+    """Every entry within the bound; counts[name] = entries that needed the error-model term."""
     g = np.asarray(g, np.float64)
     scale = np.abs(r).max()
     err = np.abs(g - r)
-    tol = RTOL * np.abs(r) + ATOL_FRAC * scale
-    bad = err > tol
-    info = (name, int(bad.sum()), bad.size, float(err.max()), float(scale))
-    assert bad.sum() <= int(1e-5 * bad.size), info
-    assert np.all(err <= 10 * tol), info
+    r18 = RTOL * np.abs(r) + ATOL_FRAC * scale
+    tol = r18 + 2 * e
+    bad = np.argwhere(err > tol)
+    info = (name, len(bad), g.size, float(err.max()), float(scale),
+            [(tuple(int(x) for x in i), float(g[tuple(i)]), float(r[tuple(i)]), float(e[tuple(i)])) for i in bad[:3]])
+    assert len(bad) == 0, info
     assert np.linalg.norm(g - r) <= 1e-4 * max(np.linalg.norm(r), 1e-30), info
+    if counts is not None:
+        counts[name] = int((err > r18).sum())
 
 
-def _compare(sc, node_grads, gposes, ref):
+def _compare(sc, node_grads, gposes, ref, counts=None):
     off = 0
     for k, nd in enumerate(sc.nodes):
         sl = slice(off, off + nd.n)
-        off += nd.n
         nc = (nd.sh_degree + 1) ** 2
         G = {n: t.cpu().numpy() for n, t in node_grads[k].items()}
-        _check(f"node{k}.mean", G["mean"], ref["mean"][sl])
-        _check(f"node{k}.log_scale", G["log_scale"], ref["log_scale"][sl])
-        _check(f"node{k}.quat", G["quat"], ref["quat"][sl])
-        _check(f"node{k}.opacity_logit", G["opacity_logit"], ref["opacity_logit"][sl])
-        _check(f"node{k}.sh", G["sh"], ref["sh"][sl, :nc])
-    _check("poses", gposes.cpu().numpy(), ref["pose"])
+        for name in ("mean", "log_scale", "quat", "opacity_logit", "sh"):
+            r, e = ref[name][sl], ref["err_" + name][sl]
+            if name == "sh":
+                r, e = r[:, :nc], e[:, :nc]
+            _check(f"node{k}.{name}", G[name], r, e, counts)
+        off += nd.n
+    _check("poses", gposes.cpu().numpy(), ref["pose"], ref["err_pose"], counts)
 
 
 def test_backward_fd_subset_sh3():

@@ -63,8 +63,7 @@ def test_low_precision_backward_matches_oracle_on_rounded_attributes():
     sc = S.config4(seed=3, n_bg=20_000, n_obj=1_500, res=128, f=112.0)
     rs = _rounded(sc, "bf16")
     # the GPU reads BF16 storage of sc; the oracle sees the same rounded values (rs)
-    up = []
-    _compare(rs, *_gradients(sc, seed=8, dtype="bf16", oracle_scene=rs, upstream=up), upstream=up)
+    _compare(rs, *_gradients(sc, seed=8, dtype="bf16", oracle_scene=rs))
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])

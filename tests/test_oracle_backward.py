@@ -163,3 +163,53 @@ def test_pose_twist_gradient_matches_fd():
         sc.node_poses[0, 1] = P0
         fd = (vals[0] - vals[1]) / (2 * h)
         assert tw[k] == pytest.approx(fd, rel=2e-5, abs=1e-7 * np.abs(tw).max())
+
+
+# --------------------------------------------------------------------------- FP32 error model of the adjoint
+def _err_case():
+    sc = S.fd_subset(seed=4)
+    nd = sc.nodes[0].subset(slice(0, sc.nodes[0].n))
+    nd.mean = nd.mean.copy()
+    nd.mean[0] = (100.0, 100.0, 5.0)           # far outside the image: composited nowhere
+    sc.nodes = [nd] + list(sc.nodes[1:])
+    g = np.random.default_rng(3).normal(size=(32, 32, 3))
+    return sc, g
+
+
+def test_gradient_error_model_is_nonnegative_and_vanishes_without_contributions():
+    sc, g = _err_case()
+    out = O.backward_view(sc, 0, 0, g, with_error=True)
+    for name in ("mean", "log_scale", "quat", "opacity_logit", "sh", "pose"):
+        e = out["err_" + name]
+        assert np.all(np.isfinite(e)) and np.all(e >= 0), name
+    # Gaussians whose gradient is exactly zero (composited nowhere) carry no error either
+    none = np.all(out["mean"] == 0, axis=1) & (out["opacity_logit"] == 0)
+    assert none.any() and np.all(out["err_mean"][none] == 0) and np.all(out["err_opacity_logit"][none] == 0)
+    some = ~none
+    assert np.all(out["err_opacity_logit"][some] > 0)
+
+
+def test_gradient_error_model_is_linear_in_the_upstream_gradient():
+    sc, g = _err_case()
+    a = O.backward_view(sc, 0, 0, g, with_error=True)
+    b = O.backward_view(sc, 0, 0, 2.0 * g, with_error=True)
+    for name in ("mean", "quat", "sh", "pose"):
+        np.testing.assert_allclose(b["err_" + name], 2.0 * a["err_" + name], rtol=1e-12, atol=1e-300)
+
+
+def test_gradient_error_model_flags_a_cancelling_entry():
+    """A round Gaussian centred on a pixel corner under a colour gradient symmetric about it:
+    dL/dmean_x is a sum of per-pixel terms of both signs that cancel exactly, so the FP32 model
+    must exceed the (vanishing) value itself, while it stays far below the terms' magnitude."""
+    nd = U.node([[0.0, 0.0, 4.0]], log_scales=np.full((1, 3), math.log(0.12)), logits=[2.0],
+                sh=U.colour_sh([[0.8, 0.4, 0.2]]), dtype=np.float64)
+    sc = U.single_view([nd], f=100.0, W=16, H=16, cx=8.0, cy=8.0)
+    g = np.ones((16, 16, 3))
+    out = O.backward_view(sc, 0, 0, g, with_error=True)
+    gx, ex = out["mean"][0, 0], out["err_mean"][0, 0]
+    assert abs(gx) < 1e-9 and ex > 10 * abs(gx)
+    # the per-pixel terms: the mean's gradient when only the pixels left of the centre are weighted
+    gl = g.copy()
+    gl[:, 8:] = 0
+    half = abs(O.backward_view(sc, 0, 0, gl)["mean"][0, 0])
+    assert half > 0 and ex < 1e-4 * half
