@@ -617,8 +617,11 @@ def main():
     ap.add_argument("--only-batched", action="store_true",
                     help="time the batched render only (no e2e, plain or CPU legs): small profiling runs")
     ap.add_argument("--no-extra", action="store_true", help="skip the ragged and precision workloads")
-    ap.add_argument("--only-leg", choices=["augment", "lidar", "mesh", "tsdf", "fwd_bwd"], default=None,
-                    help="run one side workload alone on --envs envs and print its JSON (profiling runs)")
+    ap.add_argument("--only-leg", choices=["augment", "lidar", "mesh", "tsdf", "fwd_bwd", "render"], default=None,
+                    help="run one side workload alone on --envs envs and print its JSON (profiling runs); "
+                         "'render' renders the batch --renders times with the tile shape --tile as one view group")
+    ap.add_argument("--tile", default="16x16", help="tile shape of --only-leg render")
+    ap.add_argument("--renders", type=int, default=2, help="renders of --only-leg render")
     ap.add_argument("--views-per-group", type=int, default=0,
                     help="views per group of the batched sequence (0 = as few groups as the sort allows)")
     args = ap.parse_args()
@@ -648,6 +651,14 @@ def main():
             res = mesh_leg(dev, args.warmup, args.steps)
         elif args.only_leg == "fwd_bwd":
             res = fwd_bwd_500k(dev, args.warmup, args.steps)
+        elif args.only_leg == "render":
+            tw, th = (int(x) for x in args.tile.split("x"))
+            rr = Renderer(mode="batched", tile=(tw, th), views_per_group=ds.n_views)
+            for _ in range(args.renders):
+                rr.render(ds)
+            torch.cuda.synchronize(dev)
+            res = {"tile": args.tile, "renders": args.renders, "stats": rr.stats()}
+            rr.close()
         else:
             res = tsdf_leg(dev, sc, args.warmup, args.steps)
         if rank == 0:
