@@ -116,13 +116,48 @@ __global__ void __launch_bounds__(kScanThreads) k_tscan_final(const uint32_t* __
     }
 }
 
-// Per-warp state of the pair walk: item l is depth-ordered instance i0 + l.
+// Sub-tile mask of tile column tx from the sub-row intervals [L, R] of its tile row (SR rows x SC
+// columns of 8x4-pixel sub-tiles; bit s = sub-tile (s mod SC, s div SC)).
+template <int SR, int SC>
+__device__ __forceinline__ uint32_t row_mask(const float (&L)[8], const float (&R)[8], int tx, int tile_w) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int sy = 0; sy < SR; ++sy)
+#pragma unroll
+        for (int sx = 0; sx < SC; ++sx) {
+            const float c0 = (float)(tx * tile_w + sx * 8) + 0.5f;
+            if (L[sy] <= c0 + 7.f && R[sy] >= c0) m |= 1u << (sy * SC + sx);
+        }
+    return m;
+}
+
+__device__ __forceinline__ uint32_t row_mask_any(const float (&L)[8], const float (&R)[8], int tx, const Params& P) {
+    switch ((P.tile_h >> 2) * 16 + (P.tile_w >> 3)) {      // (sub-tile rows, columns), at most 8 sub-tiles
+        case 1 * 16 + 2: return row_mask<1, 2>(L, R, tx, P.tile_w);
+        case 1 * 16 + 4: return row_mask<1, 4>(L, R, tx, P.tile_w);
+        case 1 * 16 + 8: return row_mask<1, 8>(L, R, tx, P.tile_w);
+        case 2 * 16 + 1: return row_mask<2, 1>(L, R, tx, P.tile_w);
+        case 2 * 16 + 2: return row_mask<2, 2>(L, R, tx, P.tile_w);
+        case 2 * 16 + 4: return row_mask<2, 4>(L, R, tx, P.tile_w);
+        case 4 * 16 + 1: return row_mask<4, 1>(L, R, tx, P.tile_w);
+        case 4 * 16 + 2: return row_mask<4, 2>(L, R, tx, P.tile_w);
+        case 8 * 16 + 1: return row_mask<8, 1>(L, R, tx, P.tile_w);
+        default: return row_mask<1, 1>(L, R, tx, P.tile_w);
+    }
+}
+
+// Per-warp state of the pair writer: item l is depth-ordered instance i0 + l.  Its pairs are
+// written tile row by tile row: a row job (item, tile row) covers the run of tiles that row's
+// band of the ellipse reaches (tile_row_run), in row-major order, at the item's next positions.
+// Row jobs are taken 32 at a time, one per lane, and a lane writes its job's whole run (runs are
+// short: about three tiles on the benchmark batch).
 struct PairWarp {
-    float4 a[32];          // (u, v, qa, qb)
-    float4 b[32];          // (qc, x-box, y-box, tile origin)
-    float4 e[32];          // ellipse_extent of the instance
-    int4 c[32];            // (rectangle width in tiles, first tile of the view in the group, view tiles_x, record)
-    uint32_t excl[32], off[32], end[32], run[32];
+    float4 a[32];          // (u, v, qb, qc)
+    float4 e[32];          // ellipse_extent
+    int4 box[32];          // pixel box (x0, x1, y0, y1)
+    int4 c[32];            // (first tile row, view's first tile in the group, view tiles_x, record)
+    uint32_t rexcl[32];    // exclusive prefix of the items' tile-row counts
+    uint32_t off[32], end[32], run[32];
 };
 
 __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(const ViewDesc* __restrict__ views, int K,
@@ -139,68 +174,106 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(const ViewDesc* __res
     const uint32_t w = (blockIdx.x * (uint32_t)blockDim.x + threadIdx.x) >> 5;
     if (w * 32u >= n) return;
     const int lane = (int)lane_id();
+    const uint32_t full = 0xffffffffu;
     PairWarp& S = pw[threadIdx.x >> 5];
     const uint32_t item = w * 32u + (uint32_t)lane;
     const bool act = item < n;
-    uint32_t area = 0;
+    uint32_t nrows = 0;
     if (act) {
         const uint32_t r = order[item];
         const Record& R = rec[r];
         const float4 r0 = R.r0, r1 = R.r1;
-        const float byf = R.r2.w;
-        const uint32_t bx = __float_as_uint(r1.w), by = __float_as_uint(byf);
-        const int tx0 = (int)(bx & 0xFFFFu) >> P.tile_sx, tx1 = (int)(bx >> 16) >> P.tile_sx;
-        const int ty0 = (int)(by & 0xFFFFu) >> P.tile_sy, ty1 = (int)(by >> 16) >> P.tile_sy;
+        const uint32_t bx = __float_as_uint(r1.w), by = __float_as_uint(R.r2.w);
+        const int x0 = (int)(bx & 0xFFFFu), x1 = (int)(bx >> 16), y0 = (int)(by & 0xFFFFu), y1 = (int)(by >> 16);
+        const int ty0 = y0 >> P.tile_sy, ty1 = y1 >> P.tile_sy;
         const ViewDesc& vd = views[info[r].view / (uint32_t)K];
-        S.a[lane] = make_float4(r0.x, r0.y, r1.x, r1.y);
-        S.b[lane] = make_float4(r1.z, r1.w, byf, pack_u16x2((uint32_t)tx0, (uint32_t)ty0));
+        S.a[lane] = make_float4(r0.x, r0.y, r1.y, r1.z);
         S.e[lane] = ellipse_extent(r1.x, r1.y, r1.z, P.qbin);
-        S.c[lane] = make_int4(tx1 - tx0 + 1, vd.tile_base - P.tile0, vd.tiles_x, (int)r);
+        S.box[lane] = make_int4(x0, x1, y0, y1);
+        S.c[lane] = make_int4(ty0, vd.tile_base - P.tile0, vd.tiles_x, (int)r);
         S.off[lane] = poff[item];
         S.end[lane] = poff[item + 1];
         S.run[lane] = 0;
-        area = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+        nrows = (uint32_t)(ty1 - ty0 + 1);
     }
-    uint32_t incl = area;
+    uint32_t incl = nrows;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        const uint32_t t = __shfl_up_sync(full, incl, o);
         if (lane >= o) incl += t;
     }
-    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    const uint32_t my = incl - area;
-    S.excl[lane] = my;
+    const uint32_t total_rows = __shfl_sync(full, incl, 31);
+    const uint32_t my_rexcl = incl - nrows;
+    S.rexcl[lane] = my_rexcl;
     __syncwarp();
-    const uint32_t lt = (1u << lane) - 1u;
-    for (uint32_t base = 0; base < total; base += 32) {
-        const int o = walk_owner_of(lane, act, act ? my : total, base);
-        const uint32_t f = base + (uint32_t)lane;
-        bool hit = false;
-        int tx = 0, ty = 0;
-        int4 cc = make_int4(0, 0, 0, 0);
-        if (f < total) {
-            cc = S.c[o];
-            hit = walk_tile(S.a[o], S.b[o], cc.x, f - S.excl[o], P, tx, ty);
+    const int sub_rows = P.tile_h >> 2;
+    for (uint32_t rb = 0; rb < total_rows; rb += 32) {
+        // one row job per lane: its run of tiles and the sub-row intervals of its tile row
+        const uint32_t j = rb + (uint32_t)lane;
+        const bool jact = j < total_rows;
+        const int o = walk_owner_of(lane, act, act ? my_rexcl : total_rows, rb);
+        int nrun = 0, t0 = 0, row = 0;
+        float L[8], R[8];
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), e = a;
+        int4 bx = make_int4(0, 0, 0, 0);
+        if (jact) {
+            a = S.a[o]; e = S.e[o]; bx = S.box[o];
+            row = S.c[o].x + (int)(j - S.rexcl[o]);
+            nrun = tile_row_run(a.x, a.y, a.z, a.w, e, bx.x, bx.y, bx.z, bx.w, row, P, t0);
         }
-        const uint32_t peers = __match_any_sync(0xffffffffu, hit ? o : -1);
-        if (hit) {
-            const uint32_t pos = S.off[o] + S.run[o] + __popc(peers & lt);
-            if (pos < S.end[o] && pos < cap) {
-                const float4 a = S.a[o], b = S.b[o];
-                const uint32_t bx = __float_as_uint(b.y), by = __float_as_uint(b.z);
-                const uint32_t sub = subtile_mask(a.x, a.y, a.z, a.w, b.x, S.e[o], (int)(bx & 0xFFFFu), (int)(bx >> 16),
-                                                  (int)(by & 0xFFFFu), (int)(by >> 16), tx, ty, P);
-                tkeys[pos] = (uint32_t)(cc.y + ty * cc.z + tx) | (sub << kTileBits);
-                tvals[pos] = (uint32_t)cc.w;
-            } else {
-                atomicOr(P.err, pos < cap ? kErrMismatch : kErrCapacity);
+        // the job's first position: the item's pairs of earlier batches, plus the runs of its
+        // earlier jobs in this batch (an item's jobs are consecutive lanes)
+        uint32_t jincl = (uint32_t)nrun;
+#pragma unroll
+        for (int q = 1; q < 32; q <<= 1) {
+            const uint32_t t = __shfl_up_sync(full, jincl, q);
+            if (lane >= q) jincl += t;
+        }
+        const uint32_t jexcl = jincl - (uint32_t)nrun;
+        const int seg0 = jact ? (int)(max(rb, S.rexcl[o]) - rb) : lane;
+        const uint32_t seg_excl0 = __shfl_sync(full, jexcl, seg0);
+        const int next_o = __shfl_down_sync(full, o, 1);
+        const bool last_of_item = jact && (lane == 31 || j + 1 >= total_rows || next_o != o);
+        if (nrun > 0) {
+            const uint32_t first = S.off[o] + S.run[o] + (jexcl - seg_excl0);
+            const uint32_t end = min(S.end[o], cap);
+            const int4 cc = S.c[o];
+            const uint32_t tile_row = (uint32_t)(cc.y + row * cc.z);
+            // sub-row intervals of this tile row (unrolled to the largest tile height: registers)
+#pragma unroll
+            for (int sy = 0; sy < 8; ++sy) {
+                L[sy] = 1.f; R[sy] = 0.f;
+                if (sy < sub_rows) {
+                    const int ry = row * P.tile_h + sy * 4;
+                    const int py0 = max(ry, bx.z), py1 = min(ry + 3, bx.w);
+                    float l = (float)bx.x + 0.5f, rr = (float)bx.y + 0.5f;
+                    bool ok = py0 <= py1;
+                    if (ok && P.exact_tile_test) {
+                        float bl, br;
+                        ok = band_interval(a.x, a.y, a.z, a.w, e, (float)py0 + 0.5f, (float)py1 + 0.5f, P.qbin, bl, br);
+                        l = fmaxf(l, bl);
+                        rr = fminf(rr, br);
+                    }
+                    if (ok) { L[sy] = l; R[sy] = rr; }
+                }
+            }
+            for (int ti = 0; ti < nrun; ++ti) {
+                const int tx = t0 + ti;
+                const uint32_t sub = row_mask_any(L, R, tx, P);
+                const uint32_t pos = first + (uint32_t)ti;
+                if (pos < end) {
+                    tkeys[pos] = (tile_row + (uint32_t)tx) | (sub << kTileBits);
+                    tvals[pos] = (uint32_t)cc.w;
+                } else {
+                    atomicOr(P.err, pos < cap ? kErrMismatch : kErrCapacity);
+                }
             }
         }
         __syncwarp();
-        if (hit && (peers & lt) == 0) S.run[o] += __popc(peers);
+        if (last_of_item) S.run[o] += jincl - seg_excl0;
         __syncwarp();
     }
-    // the emission count and this walk take the same decisions; pad a shortfall with dead keys
+    // the emission count and these runs take the same decisions; pad a shortfall with dead keys
     if (act) {
         const uint32_t have = S.off[lane] + S.run[lane];
         if (have != S.end[lane]) {

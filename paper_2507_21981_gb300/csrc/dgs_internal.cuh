@@ -193,47 +193,11 @@ __device__ __forceinline__ float ld_attr(const void* p, int64_t i) {
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
-// Sec. III-A (a Gaussian's screen footprint, the 3-sigma ellipse).  Does the ellipse
-// {q <= qlim}, q = qa (dx + qb dy)^2 + qc dy^2, reach the rectangle of pixel
-// centres [X0, X1] x [Y0, Y1] (relative to the mean)?  Minimum of q over the rectangle: 0 if
-// the mean is inside; else the least of the edge minima -- on a horizontal edge dy = Y the
-// minimiser is dx = -qb Y, on a vertical edge dx = X it is dy = -qa qb X / (qa qb^2 + qc) --
-// each clamped to its edge.
-__device__ __forceinline__ bool ellipse_meets(float qa, float qb, float qc, float qlim, float X0, float X1, float Y0,
-                                              float Y1) {
-    if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return true;
-    // the slope of the vertical-edge minimiser needs no correct rounding: any point of the
-    // edge bounds the minimum from above, and the binning limit carries a 0.1 % + 1e-3 margin
-    const float k = __fdividef(-qa * qb, fmaf(qa * qb, qb, qc));
-    float m = INFINITY;
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const float Y = e ? Y1 : Y0;
-        const float X = fminf(X1, fmaxf(X0, -qb * Y));
-        const float t = fmaf(qb, Y, X);
-        m = fminf(m, fmaf(qa * t, t, qc * Y * Y));
-        const float Xv = e ? X1 : X0;
-        const float Yv = fminf(Y1, fmaxf(Y0, k * Xv));
-        const float tv = fmaf(qb, Yv, Xv);
-        m = fminf(m, fmaf(qa * tv, tv, qc * Yv * Yv));
-    }
-    return m <= qlim;
-}
-
-// Flattened tile-rectangle walk shared by the emission count and the pair writer.  An item is
-// one instance with a = (u, v, qa, qb) and b = (qc, x-box, y-box, tile origin), boxes packed
-// lo | hi << 16 and the origin tx0 | ty0 << 16; its rectangle is tw tiles wide.  Candidate r of
-// an item is tile (tx0 + r % tw, ty0 + r / tw).
-__device__ __forceinline__ float pack_u16x2(uint32_t lo, uint32_t hi) { return __uint_as_float(lo | (hi << 16)); }
-
-__device__ __forceinline__ bool walk_tile(const float4& a, const float4& b, int tw, uint32_t r, const Params& P,
-                                          int& tx, int& ty);
-
-// Items are dense (lane k of the warp holds item k for k < n_items) and my_excl is item
-// lane's exclusive prefix of rectangle areas (>= 1 each).  For the 32 candidates of a flush
-// starting at `base`, the owner of candidate base + lane is the last item whose prefix is
-// <= base + lane: the items at or before `base` (one ballot) plus those starting inside the
-// flush up to the candidate (one OR-reduction of start bits).
+// Flattened warp walk over the units of up to 32 items.  Items are dense (lane k of the warp
+// holds item k for k < n_items) and my_excl is item lane's exclusive prefix of unit counts (>= 1
+// each).  For the 32 units of a flush starting at `base`, the owner of unit base + lane is the
+// last item whose prefix is <= base + lane: the items at or before `base` (one ballot) plus
+// those starting inside the flush up to the unit (one OR-reduction of start bits).
 __device__ __forceinline__ int walk_owner_of(int lane, bool item, uint32_t my_excl, uint32_t base) {
     const int first = __popc(__ballot_sync(0xffffffffu, item && my_excl <= base)) - 1;
     const uint32_t d = my_excl - base;
@@ -321,19 +285,6 @@ __device__ __forceinline__ float pixel_exponent(float ca, float qb, float cc, fl
     return fmaf(ca * t, t, cc * dy * dy);
 }
 
-// Sec. III-A (tile binning).  Binning decision for tile (tx, ty) of an instance with centre (u, v), factored form
-// (qa, qb, qc) and ellipse pixel box [x0, x1] x [y0, y1]: the tile's part of the box holds a
-// pixel centre of the ellipse {q <= qbin}.  Emission counts and pair writing both call this
-// on the same stored record values, so they agree exactly.
-__device__ __forceinline__ bool tile_hit(float u, float v, float qa, float qb, float qc, int x0, int x1, int y0, int y1,
-                                         int tx, int ty, int tile_w, int tile_h, float qbin, int exact) {
-    if (!exact) return true;
-    const int px0 = max(tx * tile_w, x0), px1 = min(tx * tile_w + tile_w - 1, x1);
-    const int py0 = max(ty * tile_h, y0), py1 = min(ty * tile_h + tile_h - 1, y1);
-    return ellipse_meets(qa, qb, qc, qbin, (float)px0 + 0.5f - u, (float)px1 + 0.5f - u, (float)py0 + 0.5f - v,
-                         (float)py1 + 0.5f - v);
-}
-
 // Sec. III-A (tile binning at the compositor's granularity).  The ellipse {q <= qlim},
 // q = qa (dx + qb dy)^2 + qc dy^2, spans dy in [-ye, ye], ye = sqrt(qlim / qc); at a given dy its
 // x-section is -qb dy -+ sqrt((qlim - qc dy^2) / qa).  Its leftmost point lies at
@@ -353,58 +304,44 @@ __device__ __forceinline__ float4 ellipse_extent(float qa, float qb, float qc, f
     return make_float4(ye, dyl, __fdividef(1.f, qa), 0.f);
 }
 
-// Mask of the 8x4-pixel sub-tiles of tile (tx, ty) in which the ellipse holds a pixel centre's
-// rectangle point: per row of sub-tiles (a band of 4 pixel rows, clipped to the instance's pixel
-// box [y0, y1]) the part of the ellipse in the band is convex, so its x-extent is one interval,
-// [x_lo(clamp(dy_L)), x_hi(clamp(-dy_L))] with the lower boundary convex and the upper concave in
-// dy; a sub-tile of that row is hit iff its columns (clipped to [x0, x1]) meet the interval.
-// This is exact for the rectangles of pixel centres (the test of ellipse_meets on each sub-tile)
-// up to rounding, which the binning limit's 0.1 % + 1e-3 margin covers; without the exact test
-// every sub-tile the box overlaps is set.
-__device__ __forceinline__ uint32_t subtile_mask(float u, float v, float qa, float qb, float qc, const float4& ext,
-                                                 int x0, int x1, int y0, int y1, int tx, int ty, const Params& P) {
-    const int sub_cols = P.tile_w >> 3, sub_rows = P.tile_h >> 2;
-    uint32_t m = 0;
-    for (int sy = 0; sy < sub_rows; ++sy) {
-        const int ry = ty * P.tile_h + sy * 4;
-        const int py0 = max(ry, y0), py1 = min(ry + 3, y1);
-        if (py0 > py1) continue;
-        float xlo = -INFINITY, xhi = INFINITY;
-        if (P.exact_tile_test) {
-            const float Y0 = fmaxf((float)py0 + 0.5f - v, -ext.x), Y1 = fminf((float)py1 + 0.5f - v, ext.x);
-            if (Y0 > Y1) continue;
-            const float dl = fminf(Y1, fmaxf(Y0, ext.y)), dr = fminf(Y1, fmaxf(Y0, -ext.y));
-            xlo = fmaf(-qb, dl, -approx_sqrt(fmaxf(0.f, fmaf(-qc * dl, dl, P.qbin)) * ext.z));
-            xhi = fmaf(-qb, dr, approx_sqrt(fmaxf(0.f, fmaf(-qc * dr, dr, P.qbin)) * ext.z));
-        }
-        for (int sx = 0; sx < sub_cols; ++sx) {
-            const int rx = tx * P.tile_w + sx * 8;
-            const int px0 = max(rx, x0), px1 = min(rx + 7, x1);
-            if (px0 <= px1 && xlo <= (float)px1 + 0.5f - u && xhi >= (float)px0 + 0.5f - u)
-                m |= 1u << (sy * sub_cols + sx);
-        }
+// The ellipse's x-extent over the band of pixel-centre rows [yc0, yc1] (absolute): the part of
+// the ellipse in the band is convex, so it is one interval [L, R] of absolute x, with L at the
+// clamp of dy_L into the band and R at the clamp of -dy_L (the lower boundary is convex and the
+// upper concave in dy).  False if the band misses the ellipse's y-extent.
+__device__ __forceinline__ bool band_interval(float u, float v, float qb, float qc, const float4& ext, float yc0,
+                                              float yc1, float qlim, float& L, float& R) {
+    const float Y0 = fmaxf(yc0 - v, -ext.x), Y1 = fminf(yc1 - v, ext.x);
+    if (!(Y0 <= Y1)) return false;
+    const float dl = fminf(Y1, fmaxf(Y0, ext.y)), dr = fminf(Y1, fmaxf(Y0, -ext.y));
+    L = u + fmaf(-qb, dl, -approx_sqrt(fmaxf(0.f, fmaf(-qc * dl, dl, qlim)) * ext.z));
+    R = u + fmaf(-qb, dr, approx_sqrt(fmaxf(0.f, fmaf(-qc * dr, dr, qlim)) * ext.z));
+    return true;
+}
+
+// Sec. III-A (tile binning).  The tiles of tile row ty that an instance reaches: those whose
+// pixel-centre rectangle (clipped to the instance's pixel box [x0, x1] x [y0, y1]) meets the
+// ellipse {q <= qbin}.  Within the tile row's band of pixel-centre rows the ellipse's x-extent is
+// one interval [L, R] (band_interval), clipped to the box's centres; tile t's centres span
+// [t w + 1/2, t w + w - 1/2], so the tiles reached are the run t0 = ceil((L + 1/2) / w) - 1 ..
+// t1 = floor((R - 1/2) / w) (w a power of two: the divisions are exact).  Without the exact
+// test, every tile the box row covers.  Returns the run's length (0: none) and t0.  The emission
+// count and the pair writer call this on the same stored record values, so they agree exactly.
+__device__ __forceinline__ int tile_row_run(float u, float v, float qb, float qc, const float4& ext, int x0, int x1,
+                                            int y0, int y1, int ty, const Params& P, int& t0) {
+    const int py0 = max(ty * P.tile_h, y0), py1 = min(ty * P.tile_h + P.tile_h - 1, y1);
+    if (py0 > py1) return 0;
+    float L = (float)x0 + 0.5f, R = (float)x1 + 0.5f;
+    if (P.exact_tile_test) {
+        float l, r;
+        if (!band_interval(u, v, qb, qc, ext, (float)py0 + 0.5f, (float)py1 + 0.5f, P.qbin, l, r)) return 0;
+        L = fmaxf(L, l);
+        R = fminf(R, r);
+        if (!(L <= R)) return 0;
     }
-    return m;
-}
-
-// floor(r / w), w >= 1: below 2^22 a float estimate (within one of the quotient) and one
-// integer correction each way; larger r (a rectangle of more than 4M tiles) divides exactly.
-__device__ __forceinline__ uint32_t small_div(uint32_t r, uint32_t w) {
-    if (r >= (1u << 22)) return r / w;
-    uint32_t q = __float2uint_rz(__fdividef((float)r + 0.5f, (float)w));
-    if (q * w > r) --q;
-    if ((q + 1u) * w <= r) ++q;
-    return q;
-}
-
-__device__ __forceinline__ bool walk_tile(const float4& a, const float4& b, int tw, uint32_t r, const Params& P,
-                                          int& tx, int& ty) {
-    const uint32_t row = small_div(r, (uint32_t)tw);
-    const uint32_t org = __float_as_uint(b.w), bx = __float_as_uint(b.y), by = __float_as_uint(b.z);
-    tx = (int)(org & 0xFFFFu) + (int)(r - row * (uint32_t)tw);
-    ty = (int)(org >> 16) + (int)row;
-    return tile_hit(a.x, a.y, a.z, a.w, b.x, (int)(bx & 0xFFFFu), (int)(bx >> 16), (int)(by & 0xFFFFu),
-                    (int)(by >> 16), tx, ty, P.tile_w, P.tile_h, P.qbin, P.exact_tile_test);
+    const float iw = 1.f / (float)P.tile_w;
+    t0 = (int)ceilf((L + 0.5f) * iw) - 1;
+    const int t1 = (int)floorf((R - 0.5f) * iw);
+    return max(0, t1 - t0 + 1);
 }
 
 __device__ __forceinline__ uint64_t global_timer_ns() {

@@ -296,18 +296,6 @@ __device__ __forceinline__ bool chunk_may_be_visible(const ChunkBound& b, const 
     return !(fl + ex < 0.f || fr + ex < 0.f || ft + ey < 0.f || fb + ey < 0.f);
 }
 
-// Emission walk: the union of the tile rectangles of a flush's visible instances (dense items
-// in lane order), flattened in (item, row-major tile) order, is tested 32 candidates at a
-// time; S.hits[k] receives item k's number of tile pairs.  The pair kernel walks the same
-// rectangles with the same test on the same stored values.
-struct WarpSplats {
-    float4 a[32];          // (u, v, qa, qb)
-    float4 b[32];          // (qc, x-box, y-box, tile origin)
-    int32_t tw[32];        // rectangle width in tiles
-    uint32_t excl[32];     // exclusive prefix of the items' rectangle areas
-    uint32_t hits[32];     // tile pairs of the item
-};
-
 constexpr int kViewBlock = 8;
 
 struct WarpViews {
@@ -318,33 +306,6 @@ struct WarpViews {
     uint32_t hits[kViewBlock];    // count pass: tile-rectangle area of view j's visible lanes
     uint32_t ibase[kViewBlock];   // emit: first record of (view j, chunk) relative to the group
 };
-
-__device__ __forceinline__ void stash_splat(WarpSplats& S, int k, const Splat& s, uint32_t excl) {
-    S.a[k] = make_float4(s.u, s.v, s.qa, s.qb);
-    S.b[k] = make_float4(s.qc, pack_u16x2((uint32_t)s.x0, (uint32_t)s.x1), pack_u16x2((uint32_t)s.y0, (uint32_t)s.y1),
-                         pack_u16x2((uint32_t)s.tx0, (uint32_t)s.ty0));
-    S.tw[k] = s.tx1 - s.tx0 + 1;
-    S.excl[k] = excl;
-    S.hits[k] = 0;
-}
-
-__device__ __forceinline__ void walk_count(WarpSplats& S, int lane, int n_items, uint32_t total, const Params& P) {
-    const uint32_t lt = (1u << lane) - 1u;
-    const bool item = lane < n_items;
-    const uint32_t my = item ? S.excl[lane] : total;
-    for (uint32_t base = 0; base < total; base += 32) {
-        const int o = walk_owner_of(lane, item, my, base);
-        const uint32_t f = base + (uint32_t)lane;
-        bool hit = false;
-        if (f < total) {
-            int tx, ty;
-            hit = walk_tile(S.a[o], S.b[o], S.tw[o], f - S.excl[o], P, tx, ty);
-        }
-        const uint32_t peers = __match_any_sync(0xffffffffu, hit ? o : -1);
-        if (hit && (peers & lt) == 0) S.hits[o] += __popc(peers);
-        __syncwarp();
-    }
-}
 
 // ------------------------------------------------------------------ spherical harmonics colour
 // Real SH, Condon-Shortley phase, k = l^2 + l + m, for a unit direction (x, y, z):
@@ -447,7 +408,6 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x) {
 //      emit pass -- record, identity, depth key and exact tile-pair count of each instance at
 //      the scanned offset of its (view, chunk) entry.
 struct WarpWork {
-    WarpSplats S;
     WarpViews WV;
     float geo[kChunk * kGeoStride];     // staged geometry of the chunk's Gaussians
 };
@@ -585,11 +545,6 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
                     const uint32_t bits = __reduce_or_sync(peers, vis ? (1u << g) : 0u);
                     if (act && (peers & ((1u << lane) - 1u)) == 0) { WV.hits[j] += h; WV.vis[j] |= bits; }
                 } else {
-                    const uint32_t excl = warp_excl_scan(area);
-                    const uint32_t total = __shfl_sync(0xffffffffu, excl + area, 31);
-                    const uint32_t vmask = __ballot_sync(0xffffffffu, vis);
-                    const int slot = __popc(vmask & ((1u << lane) - 1u));   // dense item number
-                    if (vis) stash_splat(W.S, slot, s, excl);
                     uint32_t r = 0;
                     if (act && !vis) atomicOr(P.err, kErrMismatch);
                     if (vis) {
@@ -606,10 +561,16 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
                         out.info[r] = InstInfo{(uint32_t)(nd.gbase + i), (uint32_t)vvj};
                         out.dkey[r] = min(__float_as_uint(s.z) - P.zbase, (1u << kZBits) - 1u);
                         out.ival[r] = r;
+                        // exact tile pairs: the runs of tiles each tile row's band reaches
+                        const float4 ext = ellipse_extent(s.qa, s.qb, s.qc, P.qbin);
+                        uint32_t npairs = 0;
+                        for (int ty = s.ty0; ty <= s.ty1; ++ty) {
+                            int t0;
+                            npairs += (uint32_t)tile_row_run(s.u, s.v, s.qb, s.qc, ext, s.x0, s.x1, s.y0, s.y1, ty, P, t0);
+                        }
+                        out.ntile[r] = npairs;
                     }
-                    __syncwarp();
-                    walk_count(W.S, lane, __popc(vmask), total, P);
-                    if (vis) out.ntile[r] = W.S.hits[slot];
+                    (void)area;
                 }
                 __syncwarp();
             }

@@ -83,7 +83,7 @@ def test_config3_reduced_ragged_views(spatial_order):
 
 def test_ragged_tiles_and_tile_shapes():
     sc = S.config1(seed=4, res=100, f=86.0)     # 100x100: partial tiles at the right/bottom
-    for tile in [(16, 16), (32, 8), (8, 32), (16, 8), (8, 8)]:
+    for tile in [(16, 16), (32, 8), (8, 32), (16, 8), (8, 8), (64, 4), (32, 4), (16, 4)]:
         ds, out, _, _ = _render(sc, "batched", tile=tile)
         _check_views(sc, ds, out, [0])
 
