@@ -36,16 +36,18 @@ OPS_PER_PAIR = 21
 BWD_OPS_PER_PAIR = 50
 # Projection of one visible instance: faithfully rounded camera-space centre (3 compensated dot
 # products, 105), guarded Jacobian and 2D covariance by Cauchy-Binet (75), conic, centre and
-# pixel box (20); spherical-harmonics colour of degree 3: basis (30), 48 FMA, direction (10);
-# one exact ellipse-versus-rectangle test of a candidate tile or sub-tile (45).
-PROJ_OPS, SH3_OPS, TILE_TEST_OPS = 200, 90, 45
+# pixel box (20); spherical-harmonics colour of degree 3: basis (30), 48 FMA, direction (10).
+# The count and emit rates count only this per-visible work: the chunk and per-Gaussian culls
+# of the count pass and the tile-row runs of emission are left out, so their fractions are
+# lower bounds.
+PROJ_OPS, SH3_OPS = 200, 90
 # The projection adjoint moves per visible instance: 40 B of partials, 236 B of FP32 attributes
 # read, 236 B of attribute gradients accumulated and 8 B of identity.
 PROJECT_BWD_BYTES = 40 + 236 + 236 + 8
-# DRAM bytes (read + write) per launch on the full workload, from an ncu capture of the same
-# kernel on the 8-env case (16 views) scaled by the 8x views of the full launch; None while the
-# kernel has changed since its capture.
-TRAFFIC = {"composite": None}
+# DRAM bytes (read + write) per launch on the full workload, from a one-pass ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the full launch: 995.1 + 751.9 MB.  Set to
+# None whenever the kernel changes after its capture.
+TRAFFIC = {"composite": 1.747e9}
 # FP32 operations per (voxel, view) of the TSDF fusion: camera-space point (9 FMA), reciprocal,
 # projection (4), bounds (4 compares), coverage test, normalised depth (2), sdf, truncation,
 # clamp (2), running average (3), weight update (2)
@@ -829,9 +831,10 @@ def main():
     P, NV = stats["n_pairs"], stats["n_visible"]
     passes = (stats["key_bits"] + 7) // 8          # tile-sort passes (key_bits = tile key bits)
     # algorithmic bytes of the binning class: depth sort of the instances (28-bit keys, 4
-    # passes of 16 B plus the histogram read), tile-count scan (16 B), pair emission (record
-    # 48 + identity 8 + order/offsets 12 read; 8 B written per pair) and the tile sort
-    sort_bytes = NV * (4 + 4 * 16 + 16 + 68) + P * (8 + 4 + passes * 16)
+    # passes of 16 B plus the histogram read), tile-count scan (order and count read twice,
+    # offset written: 20 B), pair emission (record 48 + identity 8 + order 4 + offset 4 read;
+    # 8 B written per pair) and the tile sort (histogram read, passes of 16 B)
+    sort_bytes = NV * (4 + 4 * 16 + 20 + 64) + P * (8 + 4 + passes * 16)
     # compositor work of one step, counted by the instrumented compositor outside the timed region
     rc_ = Renderer(mode="batched", tile=tile, profile=2)
     rc_.render(ds, out=out)
@@ -856,12 +859,13 @@ def main():
                                 "ops_per_pair": OPS_PER_PAIR}},
         "sort": {**hbm(sort_bytes, per_step["sort"]),
                  "units": {"instances": NV, "pairs": P, "depth_passes": 4, "tile_passes": passes,
-                           "bytes_per_instance": 4 + 4 * 16 + 16 + 68, "bytes_per_pair": 8 + 4 + passes * 16}},
-        "emit": {**alu(NV * (PROJ_OPS + SH3_OPS) + P * TILE_TEST_OPS, per_step["emit"]),
-                 "units": {"visible": NV, "pairs": P, "ops_per_visible": PROJ_OPS + SH3_OPS,
-                           "ops_per_pair": TILE_TEST_OPS}},
-        "count": {**alu(NV * PROJ_OPS + P * TILE_TEST_OPS, per_step["count"]),
-                  "units": {"visible": NV, "pairs": P, "ops_per_visible": PROJ_OPS, "ops_per_pair": TILE_TEST_OPS,
+                           "bytes_per_instance": 4 + 4 * 16 + 20 + 64, "bytes_per_pair": 8 + 4 + passes * 16}},
+        "emit": {**alu(NV * (PROJ_OPS + SH3_OPS), per_step["emit"]),
+                 "units": {"visible": NV, "ops_per_visible": PROJ_OPS + SH3_OPS,
+                           "not_counted": "tile-row runs of the pair count"}},
+        "count": {**alu(NV * PROJ_OPS, per_step["count"]),
+                  "units": {"visible": NV, "ops_per_visible": PROJ_OPS,
+                            "not_counted": "chunk and per-Gaussian culls",
                             "instances_considered": n_inst}},
         # the plain per-view form reads every attribute again for every view
         "plain_projection": {**hbm(n_inst * (40 + 236) + plain_stats["n_visible"] * 68,

@@ -121,7 +121,12 @@ typedef struct dgs_options {
                                    about spin_limit_us per wave of resident blocks); 2: with
                                    check_binning, the host copy of the first view group's tile keys is
                                    corrupted (two adjacent pairs of different tiles exchanged) before
-                                   the check, which must then report it */
+                                   the check, which must then report it; 3 (DGS_DEBUG builds only,
+                                   DGS_ERR_INVALID_ARG otherwise): the compositors of an eager render
+                                   or backward are told that every view group holds half the records
+                                   it does, so the bounds check on tile-list entries fails
+                                   (DGS_ERR_CUDA naming the check) while every access it lets
+                                   through stays inside the records written */
 } dgs_options;
 
 typedef struct dgs_ctx dgs_ctx;
@@ -312,6 +317,18 @@ int dgs_kernel_times(const dgs_ctx* ctx, float* ms);
 /* Launches of library kernels queued by the most recent call (a graph replay counts the
  * kernel nodes it runs). */
 int64_t dgs_last_launches(const dgs_ctx* ctx);
+
+/*
+ * How this library was built: DGS_BUILD_DEBUG is set in a debug build (compiled with
+ * -DDGS_DEBUG: libdgs_debug.so next to libdgs.so).  Its kernels check every index they take
+ * from another kernel's output before using it -- record numbers from the scans, depth-sorted
+ * instance numbers, sort scatter destinations, tile-list entries, Gaussian ids of the adjoint --
+ * and a failed check skips the access and ends the call with DGS_ERR_CUDA and a description
+ * (dgs_last_error) of the check, its index and its bound.  Results are otherwise bit-identical
+ * to the release build's.  Needs no GPU.
+ */
+#define DGS_BUILD_DEBUG 1
+int32_t dgs_build_flags(void);
 
 /*
  * Storage order for a node (asset formatting, Sec. III-B: assets are converted once into the

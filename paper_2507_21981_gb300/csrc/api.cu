@@ -117,6 +117,33 @@ int fail(dgs_ctx* ctx, int code, const std::string& msg) {
     return code;
 }
 
+const char* dbg_site_name(uint32_t site) {
+    static const char* const names[kSiteCount] = {
+        "unknown site", "emission: record number of a visible instance",
+        "tile-count scan: depth-sorted instance number", "pair writer: depth-sorted instance number",
+        "radix sort: destination of a live key", "compositor: instance number of a tile-list entry",
+        "adjoint compositor: instance number of a tile-list entry",
+        "projection adjoint: Gaussian of an instance within its node"};
+    return site < kSiteCount ? names[site] : names[0];
+}
+
+std::string bounds_message(const uint32_t* block) {
+    uint64_t idx = 0, bound = 0;
+    std::memcpy(&idx, block + 2, sizeof(idx));
+    std::memcpy(&bound, block + 4, sizeof(bound));
+    return std::string("debug bounds check failed (") + dbg_site_name(block[0]) + "): index " + std::to_string(idx) +
+           ", bound " + std::to_string(bound);
+}
+
+// A failed debug bounds check (kErrBounds): reads the block's record of it back.
+int bounds_failure(dgs_ctx* ctx, const uint32_t* d_err) {
+    uint32_t block[6] = {};
+    cudaDeviceSynchronize();
+    if (cudaMemcpy(block, d_err + kDbgWord, sizeof(block), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(ctx, DGS_ERR_CUDA, "debug bounds check failed (site not readable)");
+    return fail(ctx, DGS_ERR_CUDA, bounds_message(block));
+}
+
 int cuda_fail(dgs_ctx* ctx, cudaError_t e, const char* what) {
     return fail(ctx, e == cudaErrorMemoryAllocation ? DGS_ERR_OOM : DGS_ERR_CUDA,
                 std::string(what) + ": " + cudaGetErrorString(e));
@@ -255,7 +282,8 @@ int check_options(const dgs_options* o, std::string& why) {
     if (o->views_per_group < 0) { why = "views_per_group"; return 0; }
     if (o->spin_limit_us < 0) { why = "spin_limit_us"; return 0; }
     if (o->check_binning < 0 || o->check_binning > 1) { why = "check_binning"; return 0; }
-    if (o->test_fault < 0 || o->test_fault > 2) { why = "test_fault"; return 0; }
+    if (o->test_fault < 0 || o->test_fault > 3) { why = "test_fault"; return 0; }
+    if (o->test_fault == 3 && !kDebugChecks) { why = "test_fault 3 (needs a DGS_DEBUG build)"; return 0; }
     return 1;
 }
 
@@ -546,7 +574,7 @@ int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* e
     const int64_t* d_viewtab = reinterpret_cast<const int64_t*>(dm + o_viewtab);
     VNode* d_vnodes = reinterpret_cast<VNode*>(dm + o_vnodes);
 
-    if ((rc = ensure(ctx, ctx->errword, 64))) return rc;
+    if ((rc = ensure(ctx, ctx->errword, kErrBlockBytes))) return rc;
     if ((rc = ensure(ctx, ctx->counts, sizeof(uint2) * std::max<int64_t>(T, 1)))) return rc;
     if ((rc = ensure(ctx, ctx->inst_off, sizeof(uint32_t) * (T + 1)))) return rc;
     if ((rc = ensure(ctx, ctx->pair_off, sizeof(uint64_t) * (T + 1)))) return rc;
@@ -593,7 +621,7 @@ int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* e
 
 // Clears the error word, then setup (K0), count (K1) and the exclusive scan of the count table.
 void launch_front(dgs_ctx* ctx, const Batch& B, const Launch& L, Timer& tm) {
-    cudaMemsetAsync(B.d_err, 0, 64, L.stream);
+    cudaMemsetAsync(B.d_err, 0, kErrBlockBytes, L.stream);
     tm.begin(DGS_K_SETUP);
     launch_setup_views(L, B.d_views, B.V, B.node_poses, B.d_slot, B.K, B.d_vnodes, B.d_vtab, B.d_err);
     tm.end();
@@ -805,9 +833,14 @@ void build_group_lists(dgs_ctx* ctx, const Batch& B, int g, ListBufs& lb, cudaSt
     G.n_tiles = (int)((v1 < V ? B.views[v1].tile_base : B.tiles_total) - tile0);
     G.P = B.P;
     G.P.tile0 = tile0;
+    G.P.n_rec = G.n_inst;
     G.lb = &lb;
     enqueue_lists(ctx, lb, B, L, tm, v0, v1, G.n_tiles, (uint32_t)B.inst_at[v0], G.n_inst, G.n_bound, nullptr,
                   static_cast<uint32_t*>(ctx->totals.p) + g, G.P, &G.keys, &G.vals);
+    // test_fault 3 (debug builds): the compositors' bound on instance numbers is half the
+    // records written, so the entries of the upper half fail the check while every access the
+    // check lets through stays inside the records of the group
+    if (ctx->opt.test_fault == 3) G.P.n_rec = G.n_inst / 2;
 }
 
 // dgs_options.check_binning: reads view group g's tile lists back and checks them on the host
@@ -898,6 +931,7 @@ int finish(dgs_ctx* ctx, const Batch& B, cudaStream_t stream) {
             if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) ctx->ktimes[r.cls] += ms;
         }
     }
+    if (errw & kErrBounds) return bounds_failure(ctx, B.d_err);
     if (errw & kErrTimeout) return fail(ctx, DGS_ERR_TIMEOUT, "a bounded device wait timed out (sort look-back)");
     if (errw & kErrMismatch) return fail(ctx, DGS_ERR_CUDA, "internal: count and emit passes disagree");
     if (errw & kErrCapacity) return fail(ctx, DGS_ERR_CUDA, "internal: tile pairs beyond their bound");
@@ -1058,6 +1092,7 @@ int enqueue_graph_body(dgs_ctx* ctx, const Batch& B, const Launch& L, float* out
         P.tile0 = tile0;
         P.gate = sizes + 2;
         P.inst_base_dev = sizes + 8 * g + 4;
+        P.n_rec = (uint32_t)ctx->cap_inst[g];
         ListBufs& lb = ctx->lists[g];
         const uint32_t *keys = nullptr, *vals = nullptr;
         enqueue_lists(ctx, lb, B, Lg, tg, v0, v1, n_tiles, 0u, (uint32_t)ctx->cap_inst[g],
@@ -1167,6 +1202,7 @@ int render_graph(dgs_ctx* ctx, Batch& B, float* out_rgb, float* out_depth, float
         ctx->stats.n_groups = ctx->gng;
         ctx->stats.key_bits = ctx->gbits;
         if (errw & kErrPose) return fail(ctx, DGS_ERR_INVALID_ARG, "a node pose is not finite or not rigid");
+        if (errw & kErrBounds) return bounds_failure(ctx, B.d_err);
         if (errw & kErrTimeout) return fail(ctx, DGS_ERR_TIMEOUT, "a bounded device wait timed out (sort look-back)");
         if (errw & kErrMismatch) return fail(ctx, DGS_ERR_CUDA, "internal: count and emit passes disagree");
         if (!(errw & kErrCapacity) || !sizes[2]) {
@@ -1323,6 +1359,8 @@ int dgs_kernel_times(const dgs_ctx* ctx, float* ms) {
 }
 
 int64_t dgs_last_launches(const dgs_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int32_t dgs_build_flags(void) { return kDebugChecks ? DGS_BUILD_DEBUG : 0; }
 
 
 int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids, int32_t n_envs,

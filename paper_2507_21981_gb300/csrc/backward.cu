@@ -107,11 +107,14 @@ __global__ void __launch_bounds__(256) k_composite_bwd(const ViewDesc* __restric
         if (__all_sync(0xffffffffu, done)) break;
         const uint32_t i = base + lane;
         // the forward pass's staging: entries whose sub-tile mask holds this warp's bit
-        const bool rel = i < range.y && (__ldg(keys + i) & wbit);
+        const bool sel = i < range.y && (__ldg(keys + i) & wbit);
+        // (debug builds check every entry of the range, whichever sub-tiles it reaches)
+        const bool chk = kDebugChecks && i < range.y;
+        const uint32_t idx = sel || chk ? __ldg(vals + i) : 0u;
+        const bool rel = sel && (!chk || in_bounds(idx, P.n_rec, P.err, kSiteBackwardRecord));
         const uint32_t m = __ballot_sync(0xffffffffu, rel);
         if (m == 0) continue;
         if (rel) {
-            const uint32_t idx = __ldg(vals + i);
             const Record* r = rec + idx;
             const int pos = __popc(m & lt);
             sr0[pos] = r->r0; sr1[pos] = r->r1; sr2[pos] = r->r2;
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(const NodeDesc* __restrict_
         vv = (int)inf.view;
         k = node_of_gid(nodes, n_nodes, inf.gid);
         i = (int64_t)inf.gid - nodes[k].gbase;
-        act = nodes[k].dtype == DT;
+        act = nodes[k].dtype == DT && in_bounds((uint64_t)i, (uint64_t)nodes[k].n, P.err, kSiteProjectBwdGaussian);
     }
     float gRn[9], gtn[3];
 #pragma unroll

@@ -30,7 +30,7 @@ __device__ __forceinline__ uint32_t block_sum(uint32_t x) {
 __global__ void __launch_bounds__(kScanThreads) k_tscan_partial(const uint32_t* __restrict__ order,
                                                                const uint32_t* __restrict__ ntile, uint32_t n,
                                                                const uint32_t* __restrict__ d_n, uint32_t* parts,
-                                                               const uint32_t* err) {
+                                                               uint32_t* err) {
     if (sort_failed(err)) return;
     n = live(n, d_n);
     const uint32_t base = blockIdx.x * (uint32_t)kScanTile;
@@ -39,7 +39,10 @@ __global__ void __launch_bounds__(kScanThreads) k_tscan_partial(const uint32_t* 
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
         const uint32_t i = base + j * kScanThreads + threadIdx.x;
-        if (i < n) s += ntile[order[i]];
+        if (i < n) {
+            const uint32_t r = order[i];
+            if (in_bounds(r, n, err, kSiteScanInstance)) s += ntile[r];
+        }
     }
     s = block_sum(s);
     if (threadIdx.x == 0) parts[blockIdx.x] = s;
@@ -85,7 +88,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tscan_final(const uint32_t* __
                                                              const uint32_t* __restrict__ ntile, uint32_t n,
                                                              const uint32_t* __restrict__ d_n,
                                                              const uint32_t* __restrict__ parts, uint32_t* poff,
-                                                             const uint32_t* err) {
+                                                             uint32_t* err) {
     __shared__ uint32_t s_w[kScanThreads / 32];
     if (sort_failed(err)) return;
     n = live(n, d_n);
@@ -95,7 +98,11 @@ __global__ void __launch_bounds__(kScanThreads) k_tscan_final(const uint32_t* __
     uint32_t v[kScanItems], sum = 0;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
-        v[j] = i0 + j < n ? ntile[order[i0 + j]] : 0u;
+        v[j] = 0u;
+        if (i0 + j < n) {
+            const uint32_t r = order[i0 + j];
+            if (in_bounds(r, n, err, kSiteScanInstance)) v[j] = ntile[r];
+        }
         sum += v[j];
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -177,10 +184,10 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(const ViewDesc* __res
     const uint32_t full = 0xffffffffu;
     PairWarp& S = pw[threadIdx.x >> 5];
     const uint32_t item = w * 32u + (uint32_t)lane;
-    const bool act = item < n;
+    const uint32_t r = item < n ? order[item] : 0u;
+    const bool act = item < n && in_bounds(r, n, P.err, kSitePairsInstance);
     uint32_t nrows = 0;
     if (act) {
-        const uint32_t r = order[item];
         const Record& R = rec[r];
         const float4 r0 = R.r0, r1 = R.r1;
         const uint32_t bx = __float_as_uint(r1.w), by = __float_as_uint(R.r2.w);
@@ -288,7 +295,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(const ViewDesc* __res
 size_t tile_scan_parts(uint32_t n) { return ((size_t)n + kScanTile - 1) / kScanTile + 1; }
 
 void launch_tile_scan(const Launch& L, const uint32_t* order, const uint32_t* ntile, uint32_t n, const uint32_t* d_n,
-                      uint32_t* poff, uint32_t* parts, uint32_t cap, uint32_t* total, const uint32_t* err) {
+                      uint32_t* poff, uint32_t* parts, uint32_t cap, uint32_t* total, uint32_t* err) {
     const uint32_t blocks = (n + kScanTile - 1) / kScanTile;
     if (blocks) k_tscan_partial<<<blocks, kScanThreads, 0, L.stream>>>(order, ntile, n, d_n, parts, err);
     k_tscan_parts<<<1, kScanThreads, 0, L.stream>>>(parts, n, d_n, poff, cap, total);

@@ -93,8 +93,10 @@ __global__ void __launch_bounds__(256, 6) k_composite(const ViewDesc* __restrict
     for (uint32_t base = range.x; base < range.y; base += 32) {
         if (__all_sync(0xffffffffu, done)) break;
         const uint32_t i = base + lane;
-        const bool rel = i < range.y && (key_n & wbit);
         const uint32_t val = val_n;
+        // (debug builds check every entry of the range, whichever sub-tiles it reaches)
+        const bool ok = i >= range.y || in_bounds(val, P.n_rec, P.err, kSiteCompositeRecord);
+        const bool rel = i < range.y && (key_n & wbit) && ok;
         if (i + 32 < range.y) { key_n = __ldg(keys + i + 32); val_n = __ldg(vals + i + 32); }
         const uint32_t m = __ballot_sync(0xffffffffu, rel);
         if (m == 0) continue;

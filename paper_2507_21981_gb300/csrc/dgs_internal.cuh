@@ -31,6 +31,34 @@ constexpr uint32_t kErrTimeout = 2u;    // a bounded spin gave up
 constexpr uint32_t kErrCapacity = 4u;   // a count exceeded its buffer
 constexpr uint32_t kErrMismatch = 8u;   // count and emit passes disagreed on a chunk
 constexpr uint32_t kErrIndex = 16u;     // an input index out of range (mesh faces)
+constexpr uint32_t kErrBounds = 32u;    // debug builds: a checked index fell outside its bound
+
+// Error block of a call: word 0 the bits above, words 2..15 counters, words 16..21 the first
+// failed bounds check (site, unused, index as u64, bound as u64).
+constexpr int kErrBlockBytes = 128;
+constexpr int kDbgWord = 16;
+
+// Debug builds (compiled with -DDGS_DEBUG).  The kernels of the render and its adjoint check
+// every index they take from another kernel's output -- record numbers from the scans, the
+// depth-sorted instance numbers, sort scatter destinations, tile-list entries, Gaussian ids --
+// against the bound of what it indexes, before the access.  A failed check skips the access,
+// sets kErrBounds and records the first failing site, index and bound; the call then returns
+// DGS_ERR_CUDA naming the site.  Release builds compile the checks out.
+#ifdef DGS_DEBUG
+constexpr bool kDebugChecks = true;
+#else
+constexpr bool kDebugChecks = false;
+#endif
+enum DbgSite : uint32_t {
+    kSiteEmitRecord = 1,      // emission: record number of a visible instance
+    kSiteScanInstance,        // tile-count scan: depth-sorted instance number
+    kSitePairsInstance,       // pair writer: depth-sorted instance number
+    kSiteSortScatter,         // radix sort: destination of a live key
+    kSiteCompositeRecord,     // compositor: instance number of a tile-list entry
+    kSiteBackwardRecord,      // adjoint compositor: instance number of a tile-list entry
+    kSiteProjectBwdGaussian,  // projection adjoint: Gaussian of an instance within its node
+    kSiteCount
+};
 
 struct NodeDesc {
     const float* mean;
@@ -122,6 +150,7 @@ struct Params {
     uint32_t* err;        // device error word
     const uint32_t* gate; // emission is skipped when non-null and *gate != 0 (capacity overflow)
     float p_min;          // kHalfLog2e * q_max: exponents below it are outside the 3-sigma ellipse
+    uint32_t n_rec;       // records of the current view group (bound of its instance numbers)
     const uint32_t* inst_base_dev;  // emission: first record of the group read on the device (graph replay)
     // image randomisation of the RGB output (null aug = none): per-view records, overlay clip
     const dgs_augment* aug;
@@ -400,10 +429,25 @@ void sort_prepare();
 // min(*d_n, n) if d_n), and *total = min(poff[n], cap).  parts: scratch of
 // tile_scan_parts(n) words.
 void launch_tile_scan(const Launch& L, const uint32_t* order, const uint32_t* ntile, uint32_t n, const uint32_t* d_n,
-                      uint32_t* poff, uint32_t* parts, uint32_t cap, uint32_t* total, const uint32_t* err);
+                      uint32_t* poff, uint32_t* parts, uint32_t cap, uint32_t* total, uint32_t* err);
 
 // Kernels that read sorted values as indices return at once after a sort timed out (the
 // sorted arrays are then not permutations).
+// Debug builds: i < n, else the failure is recorded (see kErrBounds) and false returned.
+__device__ __forceinline__ bool in_bounds(uint64_t i, uint64_t n, uint32_t* err, DbgSite site) {
+    if constexpr (!kDebugChecks) {
+        return true;
+    } else {
+        if (i < n) return true;
+        if (err && (atomicOr(err, kErrBounds) & kErrBounds) == 0) {
+            err[kDbgWord] = (uint32_t)site;
+            *reinterpret_cast<unsigned long long*>(err + kDbgWord + 2) = i;
+            *reinterpret_cast<unsigned long long*>(err + kDbgWord + 4) = n;
+        }
+        return false;
+    }
+}
+
 __device__ __forceinline__ bool sort_failed(const uint32_t* err) { return (*(volatile const uint32_t*)err & kErrTimeout) != 0; }
 size_t tile_scan_parts(uint32_t n);
 

@@ -119,7 +119,7 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
     int32_t* d_nvoff = cv.take<int32_t>(n_nodes + 1);
     int64_t* d_viewtab = cv.take<int64_t>(V + 1);
     VNode* d_vnodes = cv.take<VNode>((size_t)V * K);
-    uint32_t* d_err = cv.take<uint32_t>(16);
+    uint32_t* d_err = cv.take<uint32_t>(kErrBlockBytes / 4);
     uint2* d_counts = cv.take<uint2>(T);
     uint32_t* d_inst_off = cv.take<uint32_t>(T + 1);
     uint64_t* d_pair_off = cv.take<uint64_t>(T + 1);
@@ -137,7 +137,7 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
     if (!nv.empty()) NA_CUDA(cudaMemcpyAsync(d_nv, nv.data(), sizeof(NodeView) * nv.size(), cudaMemcpyHostToDevice, stream));
     NA_CUDA(cudaMemcpyAsync(d_nvoff, nv_off.data(), sizeof(int32_t) * (n_nodes + 1), cudaMemcpyHostToDevice, stream));
     NA_CUDA(cudaMemcpyAsync(d_viewtab, view_tab.data(), sizeof(int64_t) * (V + 1), cudaMemcpyHostToDevice, stream));
-    NA_CUDA(cudaMemsetAsync(d_err, 0, 64, stream));
+    NA_CUDA(cudaMemsetAsync(d_err, 0, kErrBlockBytes, stream));
 
     Params P = make_params(o);
     P.err = d_err;
@@ -186,6 +186,7 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
     const int tbits = bits_for_tiles((uint64_t)tiles_total + 1);
     if (tbits > kTileBits) return DGS_ERR_CAPACITY;
     // depth-ordered tile lists, as in dgs_render with one view group
+    P.n_rec = (uint32_t)n_vis;
     launch_emit(L, dtype_mask, d_nodes, n_nodes, d_views, d_vnodes, K, d_nv, d_nvoff, (int)chunk_total, P, 0, V, true,
                 nullptr, 0, d_counts, d_inst_off, 0u, d_rec, d_info, d_dk0, d_iv0, d_ntile);
     uint32_t *dk, *order, *tk, *tv;
@@ -204,7 +205,7 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
     NA_CUDA(cudaGetLastError());
     NA_CUDA(cudaStreamSynchronize(stream));
     if (h_err & kErrTimeout) return DGS_ERR_TIMEOUT;
-    if (h_err & (kErrMismatch | kErrCapacity)) return DGS_ERR_CUDA;
+    if (h_err & (kErrMismatch | kErrCapacity | kErrBounds)) return DGS_ERR_CUDA;
     if (h_err & kErrPose) return DGS_ERR_INVALID_ARG;
     return DGS_OK;
 #undef NA_CUDA

@@ -547,8 +547,8 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
                 } else {
                     uint32_t r = 0;
                     if (act && !vis) atomicOr(P.err, kErrMismatch);
-                    if (vis) {
-                        r = WV.ibase[j] + __popc(WV.mask[j] & ((1u << g) - 1u));
+                    if (vis) r = WV.ibase[j] + __popc(WV.mask[j] & ((1u << g) - 1u));
+                    if (vis && in_bounds(r, P.n_rec, P.err, kSiteEmitRecord)) {
                         float rgb[3];
                         sh_colour(nd.deg, shc + g * kShStride, gg, vnodes[vvj], rgb);
                         const int64_t i = (int64_t)c * kChunk + g;

@@ -311,6 +311,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint32_t* __rest
         const uint32_t key = s_keys[i];
         const uint32_t dj = (key >> shift) & M;
         const uint32_t g = s_gbase[dj] + (uint32_t)i - s_dexcl[dj];
+        // every live key lands below n (the padding keys, ~0, sort past the end and are dropped)
+        if (kDebugChecks && key != ~0u && !in_bounds(g, n, err, kSiteSortScatter)) continue;
         if (g < n) { kout[g] = key; vout[g] = s_vals[i]; }
     }
 }

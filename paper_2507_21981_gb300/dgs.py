@@ -6,6 +6,7 @@ there is no fallback implementation.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import threading
@@ -14,6 +15,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdgs.so")
+DEBUG_LIB_PATH = os.path.join(HERE, "libdgs_debug.so")   # -DDGS_DEBUG: device bounds checks
 
 DGS_OK, DGS_ERR_INVALID_ARG, DGS_ERR_CUDA, DGS_ERR_OOM, DGS_ERR_CAPACITY, DGS_ERR_TIMEOUT, DGS_ERR_UNSUPPORTED = range(7)
 DGS_F32, DGS_BF16, DGS_F16 = 0, 1, 2
@@ -76,7 +78,9 @@ EXPORTED = ("dgs_default_options", "dgs_context_create", "dgs_context_destroy", 
             "dgs_workspace_query", "dgs_render", "dgs_last_stats", "dgs_kernel_times", "dgs_last_launches",
             "dgs_render_noalloc", "dgs_render_backward", "dgs_autotune", "dgs_spatial_order",
             "dgs_set_augment", "dgs_augment_rgb", "dgs_lidar_build", "dgs_lidar_trace", "dgs_mesh_to_gaussians",
-            "dgs_tsdf_integrate", "dgs_pose_twist_grad", "dgs_set_options", "dgs_workspace_query_batch")
+            "dgs_tsdf_integrate", "dgs_pose_twist_grad", "dgs_set_options", "dgs_workspace_query_batch",
+            "dgs_build_flags")
+DGS_BUILD_DEBUG = 1
 
 _lib = None
 _lock = threading.Lock()
@@ -89,7 +93,8 @@ class DgsError(RuntimeError):
 
 
 def load(path: str | None = None) -> C.CDLL:
-    """Loads libdgs.so (built in-tree by build.py).  Raises if it is missing."""
+    """Loads libdgs.so (built in-tree by build.py).  Raises if it is missing.  With a path (for
+    instance DEBUG_LIB_PATH) that library is loaded and returned without replacing the default."""
     global _lib
     with _lock:
         if _lib is not None and path is None:
@@ -118,6 +123,8 @@ def load(path: str | None = None) -> C.CDLL:
         lib.dgs_kernel_times.argtypes = [vp, C.POINTER(C.c_float)]
         lib.dgs_last_launches.restype = C.c_int64
         lib.dgs_last_launches.argtypes = [vp]
+        lib.dgs_build_flags.restype = C.c_int32
+        lib.dgs_build_flags.argtypes = []
         lib.dgs_render_backward.restype = C.c_int
         lib.dgs_render_backward.argtypes = [vp, C.POINTER(dgs_node), i32, vp, i32, i32, vp, C.POINTER(dgs_camera), vp,
                                             i32, vp, vp, vp, vp, C.POINTER(dgs_node_grads), vp, vp, vp]
@@ -243,6 +250,26 @@ def dgs_kernel_times(ctx) -> dict:
 
 def dgs_last_launches(ctx) -> int:
     return int(load().dgs_last_launches(ctx))
+
+
+def dgs_build_flags() -> int:
+    return int(load().dgs_build_flags())
+
+
+@contextlib.contextmanager
+def using(lib: C.CDLL):
+    """Routes every wrapper of this module (and so Renderer and DeviceScene) to `lib`, for
+    instance load(DEBUG_LIB_PATH), inside the block.  Contexts made inside must be closed
+    inside."""
+    global _lib
+    prev = load()
+    with _lock:
+        _lib = lib
+    try:
+        yield lib
+    finally:
+        with _lock:
+            _lib = prev
 
 
 def dgs_render_noalloc(opt, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env,

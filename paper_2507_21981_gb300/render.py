@@ -113,6 +113,7 @@ class Renderer:
                 setattr(o, k, v)
         self.options = o
         self._aug = None
+        self._lib = D.load()            # the library the context belongs to (see dgs.using)
         self.ctx = D.dgs_context_create(o)
 
     def set_options(self, **opts):
@@ -130,7 +131,7 @@ class Renderer:
 
     def close(self):
         if self.ctx:
-            D.dgs_context_destroy(self.ctx)
+            self._lib.dgs_context_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):

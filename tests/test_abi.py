@@ -322,3 +322,23 @@ def test_pose_twist_validates_arguments_on_the_host(lib):
     assert lib.dgs_pose_twist_grad(None, None, -1, None, None) == D.DGS_ERR_INVALID_ARG
     assert lib.dgs_pose_twist_grad(None, None, 3, None, None) == D.DGS_ERR_INVALID_ARG
     assert lib.dgs_pose_twist_grad(None, None, 0, None, None) == D.DGS_OK      # nothing to do, no device work
+
+
+def test_debug_build_exports_every_call_and_reports_itself(lib):
+    dbg = D.load(B.build(debug=True))
+    for n in declared_functions():
+        assert hasattr(dbg, n), n
+    assert lib.dgs_build_flags() == 0
+    assert dbg.dgs_build_flags() == D.DGS_BUILD_DEBUG
+
+
+def test_bounds_fault_hook_needs_the_debug_build(lib):
+    dbg = D.load(B.build(debug=True))
+    o = D.dgs_default_options()
+    o.test_fault = 3
+    h = C.c_void_p()
+    assert lib.dgs_context_create(C.byref(h), C.byref(o)) == D.DGS_ERR_INVALID_ARG
+    assert dbg.dgs_context_create(C.byref(h), C.byref(o)) == D.DGS_OK
+    dbg.dgs_context_destroy(h)
+    o.test_fault = 4
+    assert dbg.dgs_context_create(C.byref(h), C.byref(o)) == D.DGS_ERR_INVALID_ARG
