@@ -127,6 +127,19 @@ typedef struct dgs_options {
                                    it does, so the bounds check on tile-list entries fails
                                    (DGS_ERR_CUDA naming the check) while every access it lets
                                    through stays inside the records written */
+    int32_t keep_lists;         /* 1 = an eager render (batched or plain mode) of at most two view
+                                   groups keeps its tile lists, records and device tables on the
+                                   context, and a dgs_render_backward of the same batch differentiates
+                                   them instead of binning again (stats.path = DGS_PATH_KEPT_LISTS).
+                                   "The same batch": equal node descriptors, env -> node table, node
+                                   pose pointer, cameras, per-env camera counts and pixel offsets, and
+                                   no call that stages a batch (dgs_render, dgs_render_backward
+                                   without a match, dgs_autotune, dgs_workspace_query_batch) nor
+                                   dgs_set_options on the context in between; otherwise the backward
+                                   bins again as without the option.  The caller must leave the
+                                   device data the render read (attributes and poses) unchanged
+                                   until that backward, as with any state saved for a backward.
+                                   Default 0 */
 } dgs_options;
 
 typedef struct dgs_ctx dgs_ctx;
@@ -155,7 +168,8 @@ typedef enum dgs_path {
     DGS_PATH_EAGER = 0,         /* launched kernel by kernel (with one mid-call readback) */
     DGS_PATH_GRAPH = 1,         /* replayed the captured graph */
     DGS_PATH_CAPTURED = 2,      /* ran eagerly, then captured a graph for the next calls */
-    DGS_PATH_REGROWN = 3        /* a replay overflowed its capacity: ran eagerly and recaptured */
+    DGS_PATH_REGROWN = 3,       /* a replay overflowed its capacity: ran eagerly and recaptured */
+    DGS_PATH_KEPT_LISTS = 4     /* dgs_render_backward used the lists its forward kept (keep_lists) */
 } dgs_path;
 
 /* Kernel classes timed when dgs_options.profile = 1 (milliseconds, summed over the call). */

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -61,8 +62,13 @@ struct ListBufs {
     ListBufs& operator=(const ListBufs&) = delete;
 };
 
+namespace {
+struct SavedForward;   // an eager render's lists kept for its backward (dgs_options.keep_lists)
+}  // namespace
+
 struct dgs_ctx {
     dgs_options opt{};
+    std::unique_ptr<SavedForward> saved;  // valid until the next call stages a batch
     std::string err;
     int device = 0;
     DevBuf meta, counts, inst_off, pair_off, parts, errword, readback, inst_grad, gsizes, totals;
@@ -284,6 +290,7 @@ int check_options(const dgs_options* o, std::string& why) {
     if (o->check_binning < 0 || o->check_binning > 1) { why = "check_binning"; return 0; }
     if (o->test_fault < 0 || o->test_fault > 3) { why = "test_fault"; return 0; }
     if (o->test_fault == 3 && !kDebugChecks) { why = "test_fault 3 (needs a DGS_DEBUG build)"; return 0; }
+    if (o->keep_lists < 0 || o->keep_lists > 1) { why = "keep_lists"; return 0; }
     return 1;
 }
 
@@ -494,6 +501,8 @@ struct Batch {
     Params P{};
 };
 
+void invalidate_saved(dgs_ctx* ctx);
+
 // Validation, host tables and their upload (one copy from pinned memory), workspace for the
 // count table.  Returns DGS_OK with B filled (B.V == 0: nothing to render).
 int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids, int32_t n_envs,
@@ -501,6 +510,7 @@ int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* e
             int32_t max_cams, const float* out_rgb, const float* out_depth, const int64_t* view_pixel_offset,
             const dgs_node_grads* grads, cudaStream_t stream, Timer& tm, Batch& B, bool need_outputs = true) {
     const dgs_options& o = ctx->opt;
+    invalidate_saved(ctx);   // the staging below overwrites the tables a kept forward refers to
     HostTables H;
     std::string why;
     const int vrc = build_host_tables(o, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env,
@@ -821,6 +831,53 @@ struct GroupLists {
     Params P{};
 };
 
+// dgs_options.keep_lists: what an eager render leaves for a backward of the same batch -- its
+// staged batch (device tables and host copy), the per-view counts it read back, every view
+// group's lists (records, identities, tile-sorted pairs, ranges; at most two groups, one per
+// list workspace), and the signature of the call's host-visible arguments.
+struct SavedForward {
+    bool valid = false;
+    std::vector<unsigned char> sig;
+    Batch B;
+    std::vector<uint64_t> inst_at, pair_at;
+    std::vector<GroupLists> groups;
+    dgs_stats stats{};
+};
+
+void invalidate_saved(dgs_ctx* ctx) {
+    if (ctx->saved) ctx->saved->valid = false;
+}
+
+// Bytes of every host-visible argument the lists depend on: the node descriptors (pointers,
+// sizes, types), the env -> node table, the node-pose pointer, the cameras, the per-env camera
+// counts and the pixel offsets.
+std::vector<unsigned char> call_signature(const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids,
+                                          int32_t n_envs, int32_t max_nodes, const float* node_poses,
+                                          const dgs_camera* cams, const int32_t* cams_per_env, int32_t max_cams,
+                                          const int64_t* view_pixel_offset) {
+    std::vector<unsigned char> sig;
+    auto put = [&](const void* p, size_t n) {
+        const unsigned char* c = static_cast<const unsigned char*>(p);
+        if (c) sig.insert(sig.end(), c, c + n);
+        else sig.insert(sig.end(), n, 0xFF);
+    };
+    const int32_t dims[4] = {n_nodes, n_envs, max_nodes, max_cams};
+    put(dims, sizeof(dims));
+    if (n_nodes < 0 || n_envs < 0 || max_nodes < 0 || max_cams < 0) return sig;
+    put(nodes, sizeof(dgs_node) * (size_t)n_nodes);
+    put(env_node_ids, sizeof(int32_t) * (size_t)n_envs * (size_t)max_nodes);
+    put(&node_poses, sizeof(node_poses));
+    put(cams, sizeof(dgs_camera) * (size_t)n_envs * (size_t)max_cams);
+    put(cams_per_env, sizeof(int32_t) * (size_t)n_envs);
+    int64_t V = 0;
+    if (cams_per_env)
+        for (int32_t e = 0; e < n_envs; ++e) V += std::min(std::max(cams_per_env[e], 0), max_cams);
+    const unsigned char has = view_pixel_offset ? 1 : 0;
+    put(&has, 1);
+    if (view_pixel_offset) put(view_pixel_offset, sizeof(int64_t) * (size_t)V);
+    return sig;
+}
+
 void build_group_lists(dgs_ctx* ctx, const Batch& B, int g, ListBufs& lb, cudaStream_t stream, Timer& tm,
                        GroupLists& G) {
     Launch L{stream, &ctx->launches};
@@ -943,7 +1000,7 @@ int finish(dgs_ctx* ctx, const Batch& B, cudaStream_t stream) {
 // Setup/count/scan, the readback, then per view group emit/sort/ranges/composite, and the
 // final synchronisation.  B must have been staged.
 int run_eager(dgs_ctx* ctx, Batch& B, float* out_rgb, float* out_depth, float* out_alpha, cudaStream_t stream,
-              Timer& tm) {
+              Timer& tm, std::vector<GroupLists>* keep = nullptr) {
     Launch L{stream, &ctx->launches};
     launch_front(ctx, B, L, tm);
     int rc = readback_groups(ctx, B, stream, tm);
@@ -976,6 +1033,7 @@ int run_eager(dgs_ctx* ctx, Batch& B, float* out_rgb, float* out_depth, float* o
                          static_cast<Record*>(G.lb->records.p), G.P, out_rgb, out_depth, out_alpha, work);
         tms[b].end();
         DGS_CUDA(ctx, cudaGetLastError());
+        if (keep) keep->push_back(G);
     }
     if (ng > 1) {
         cudaEvent_t join = take_event(ctx);
@@ -1276,6 +1334,7 @@ int dgs_set_options(dgs_ctx* ctx, const dgs_options* opt) {
     if (!check_options(opt, why)) return fail(ctx, DGS_ERR_INVALID_ARG, "options: " + why);
     ctx->opt = *opt;
     drop_graph(ctx);      // captured kernels carry the old options
+    invalidate_saved(ctx);
     return DGS_OK;
 }
 
@@ -1375,10 +1434,28 @@ int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32
     int rc = stage(ctx, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env, max_cams,
                    out_rgb, out_depth, view_pixel_offset, nullptr, stream, tm, B);
     if (rc != DGS_OK || B.V == 0) return rc;
-    if (ctx->opt.mode == DGS_MODE_GRAPH && B.T > 0)
+    if (ctx->opt.mode == DGS_MODE_GRAPH && B.T > 0) {
         rc = render_graph(ctx, B, out_rgb, out_depth, out_alpha, stream, tm);
-    else
-        rc = run_eager(ctx, B, out_rgb, out_depth, out_alpha, stream, tm);
+    } else {
+        // keep_lists: at most two view groups, one per list workspace, stay in place
+        const bool keep = ctx->opt.keep_lists && ctx->opt.mode != DGS_MODE_GRAPH;
+        std::vector<GroupLists> groups;
+        rc = run_eager(ctx, B, out_rgb, out_depth, out_alpha, stream, tm, keep ? &groups : nullptr);
+        if (rc == DGS_OK && keep && !groups.empty() && groups.size() <= 2 && groups.size() == B.groups.size()) {
+            if (!ctx->saved) ctx->saved.reset(new SavedForward);
+            SavedForward& S = *ctx->saved;
+            S.sig = call_signature(nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env,
+                                   max_cams, view_pixel_offset);
+            S.inst_at.assign(B.inst_at, B.inst_at + B.V + 1);
+            S.pair_at.assign(B.pair_at, B.pair_at + B.V + 1);
+            S.B = B;
+            S.B.inst_at = S.inst_at.data();
+            S.B.pair_at = S.pair_at.data();
+            S.groups = std::move(groups);
+            S.stats = ctx->stats;
+            S.valid = true;
+        }
+    }
     ctx->stats.graph_captures = ctx->captures;
     return rc;
 }
@@ -1446,6 +1523,30 @@ int dgs_autotune(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int
     return render();
 }
 
+namespace {
+
+// The adjoint of one view group whose lists are built (K7 then K8).
+int enqueue_adjoint(dgs_ctx* ctx, const Batch& B, const GroupLists& G, const float* out_rgb, const float* out_depth,
+                    const float* grad_rgb, const float* grad_depth, float* grad_poses, unsigned long long* n_red,
+                    cudaStream_t stream, Timer& tm) {
+    Launch L{stream, &ctx->launches};
+    tm.begin(DGS_K_BACKWARD);
+    DGS_CUDA(ctx, cudaMemsetAsync(ctx->inst_grad.p, 0, sizeof(float) * 10 * std::max<uint32_t>(G.n_inst, 1), stream));
+    launch_composite_bwd(L, B.d_views, G.v0, G.v1 - G.v0, G.n_tiles, static_cast<uint2*>(G.lb->ranges.p), G.keys, G.vals,
+                         static_cast<Record*>(G.lb->records.p), G.P, out_rgb, out_depth, grad_rgb, grad_depth,
+                         static_cast<float*>(ctx->inst_grad.p), n_red);
+    tm.end();
+    tm.begin(DGS_K_BACKWARD_PROJECT);
+    launch_project_bwd(L, B.dtype_mask, B.d_nodes, B.n_nodes, B.d_views, B.d_vnodes, B.K, B.node_poses,
+                       static_cast<InstInfo*>(G.lb->info.p), static_cast<float*>(ctx->inst_grad.p), G.n_inst, G.P,
+                       B.d_grads, grad_poses);
+    tm.end();
+    DGS_CUDA(ctx, cudaGetLastError());
+    return DGS_OK;
+}
+
+}  // namespace
+
 int dgs_render_backward(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* env_node_ids,
                         int32_t n_envs, int32_t max_nodes, const float* node_poses, const dgs_camera* cams,
                         const int32_t* cams_per_env, int32_t max_cams, const float* out_rgb, const float* out_depth,
@@ -1459,34 +1560,46 @@ int dgs_render_backward(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, co
                                               "outputs (clear it with dgs_set_augment(ctx, NULL, 0, ...))");
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     Timer tm{ctx, stream, ctx->opt.profile != 0};
-    Batch B;
-    int rc = prepare(ctx, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env, max_cams,
+    int rc;
+    unsigned long long* n_red = nullptr;
+    // keep_lists: the last render on this context kept the lists of this very batch
+    SavedForward* S = ctx->opt.keep_lists && ctx->saved && ctx->saved->valid ? ctx->saved.get() : nullptr;
+    if (S && S->sig != call_signature(nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams,
+                                      cams_per_env, max_cams, view_pixel_offset))
+        S = nullptr;
+    Batch fresh;
+    Batch& B = S ? S->B : fresh;
+    if (S) {
+        if (!out_rgb || !out_depth) return fail(ctx, DGS_ERR_INVALID_ARG, "out_rgb and out_depth are required");
+        ctx->stats = S->stats;
+        ctx->stats.path = DGS_PATH_KEPT_LISTS;
+        // the gradient table travels through the pinned staging buffer, whose previous upload
+        // ended before the previous call returned
+        const size_t bytes = sizeof(dgs_node_grads) * (size_t)B.n_nodes;
+        char* hm = static_cast<char*>(ctx->h_meta) + (reinterpret_cast<const char*>(B.d_grads) -
+                                                      static_cast<const char*>(ctx->meta.p));
+        if (grads) std::memcpy(hm, grads, bytes);
+        else std::memset(hm, 0, bytes);
+        DGS_CUDA(ctx, cudaMemcpyAsync(const_cast<dgs_node_grads*>(B.d_grads), hm, bytes, cudaMemcpyHostToDevice, stream));
+        DGS_CUDA(ctx, cudaMemsetAsync(B.d_err, 0, kErrBlockBytes, stream));
+    } else {
+        rc = prepare(ctx, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env, max_cams,
                      out_rgb, out_depth, view_pixel_offset, grads, stream, tm, B);
-    if (rc != DGS_OK || B.V == 0) return rc;
-    Launch L{stream, &ctx->launches};
+        if (rc != DGS_OK || B.V == 0) return rc;
+    }
     uint64_t max_inst = 1;
     for (auto& g : B.groups) max_inst = std::max<uint64_t>(max_inst, B.inst_at[g.second] - B.inst_at[g.first]);
     if ((rc = ensure(ctx, ctx->inst_grad, sizeof(float) * 10 * max_inst))) return rc;
-    unsigned long long* n_red = nullptr;
     if (ctx->opt.profile >= 2) {
         n_red = reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->errword.p) + 56);
         DGS_CUDA(ctx, cudaMemsetAsync(n_red, 0, sizeof(unsigned long long), stream));
     }
     for (int g = 0; g < (int)B.groups.size(); ++g) {
         GroupLists G;
-        build_group_lists(ctx, B, g, ctx->lists[0], stream, tm, G);
-        tm.begin(DGS_K_BACKWARD);
-        DGS_CUDA(ctx, cudaMemsetAsync(ctx->inst_grad.p, 0, sizeof(float) * 10 * std::max<uint32_t>(G.n_inst, 1), stream));
-        launch_composite_bwd(L, B.d_views, G.v0, G.v1 - G.v0, G.n_tiles, static_cast<uint2*>(G.lb->ranges.p), G.keys, G.vals,
-                             static_cast<Record*>(G.lb->records.p), G.P, out_rgb, out_depth, grad_rgb, grad_depth,
-                             static_cast<float*>(ctx->inst_grad.p), n_red);
-        tm.end();
-        tm.begin(DGS_K_BACKWARD_PROJECT);
-        launch_project_bwd(L, B.dtype_mask, B.d_nodes, B.n_nodes, B.d_views, B.d_vnodes, B.K, node_poses,
-                           static_cast<InstInfo*>(G.lb->info.p), static_cast<float*>(ctx->inst_grad.p), G.n_inst, G.P,
-                           B.d_grads, grad_poses);
-        tm.end();
-        DGS_CUDA(ctx, cudaGetLastError());
+        if (S) G = S->groups[g];
+        else build_group_lists(ctx, B, g, ctx->lists[0], stream, tm, G);
+        if ((rc = enqueue_adjoint(ctx, B, G, out_rgb, out_depth, grad_rgb, grad_depth, grad_poses, n_red, stream, tm)))
+            return rc;
     }
     rc = finish(ctx, B, stream);
     if (rc == DGS_OK && n_red) {

@@ -20,7 +20,7 @@ DEBUG_LIB_PATH = os.path.join(HERE, "libdgs_debug.so")   # -DDGS_DEBUG: device b
 DGS_OK, DGS_ERR_INVALID_ARG, DGS_ERR_CUDA, DGS_ERR_OOM, DGS_ERR_CAPACITY, DGS_ERR_TIMEOUT, DGS_ERR_UNSUPPORTED = range(7)
 DGS_F32, DGS_BF16, DGS_F16 = 0, 1, 2
 DGS_MODE_PLAIN, DGS_MODE_BATCHED, DGS_MODE_GRAPH = 0, 1, 2
-DGS_PATH_EAGER, DGS_PATH_GRAPH, DGS_PATH_CAPTURED, DGS_PATH_REGROWN = 0, 1, 2, 3
+DGS_PATH_EAGER, DGS_PATH_GRAPH, DGS_PATH_CAPTURED, DGS_PATH_REGROWN, DGS_PATH_KEPT_LISTS = 0, 1, 2, 3, 4
 DGS_TUNE_MAX = 16
 KERNEL_CLASSES = ("setup", "count", "scan", "emit", "sort", "ranges", "composite", "backward", "graph", "augment",
                   "lidar", "mesh", "tsdf", "backward_project")
@@ -44,7 +44,7 @@ class dgs_options(C.Structure):
                 ("z_near", C.c_float), ("lowpass", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
                 ("t_min", C.c_float), ("q_max", C.c_float), ("guard", C.c_float), ("bg", C.c_float * 3),
                 ("profile", C.c_int32), ("views_per_group", C.c_int32), ("spin_limit_us", C.c_int32),
-                ("check_binning", C.c_int32), ("test_fault", C.c_int32)]
+                ("check_binning", C.c_int32), ("test_fault", C.c_int32), ("keep_lists", C.c_int32)]
 
 
 class dgs_node_grads(C.Structure):

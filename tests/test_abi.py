@@ -55,7 +55,7 @@ def test_default_options(lib):
 def test_struct_sizes_match_header(lib):
     assert C.sizeof(D.dgs_node) == 56
     assert C.sizeof(D.dgs_camera) == 72
-    assert C.sizeof(D.dgs_options) == 76
+    assert C.sizeof(D.dgs_options) == 80
     assert C.sizeof(D.dgs_stats) == 88
     assert C.sizeof(D.dgs_tune_result) == 8 + 3 * 4 * D.DGS_TUNE_MAX
     assert C.sizeof(D.dgs_augment) == 32

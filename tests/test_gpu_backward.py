@@ -39,13 +39,13 @@ def _with_sh(sc, deg, seed):
     return sc
 
 
-def _gradients(sc, seed=0, mode="batched", dtype="f32", oracle_scene=None):
+def _gradients(sc, seed=0, mode="batched", dtype="f32", oracle_scene=None, **ropts):
     """GPU gradients of `sc` stored as `dtype`, and the oracle's (with its FP32 error model) for
-    `oracle_scene` (default sc) under the same upstream gradients."""
+    `oracle_scene` (default sc) under the same upstream gradients; ropts are Renderer options."""
     from paper_2507_21981_gb300.render import DeviceScene, Renderer
     osc = sc if oracle_scene is None else oracle_scene
     ds = DeviceScene(sc, device="cuda:0", dtype=dtype)
-    r = Renderer(mode=mode)
+    r = Renderer(mode=mode, **ropts)
     rgb, depth, _ = r.render(ds)
     rng = np.random.default_rng(seed)
     pk = O.oracle._Packed(osc)
