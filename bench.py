@@ -172,54 +172,57 @@ def _peaks():
 
 def fwd_bwd_500k(dev, warmup, steps):
     """Forward + backward of one 800x800 view of 500k SH-3 Gaussians (300k room + 8 x 25k posed
-    objects): render, then dL/d(all attributes, poses) for a fixed upstream gradient, the
-    backward differentiating the tile lists its forward kept (keep_lists), as a training step
-    does.  Kernel times per class are summed by the library's events over the timed steps; one
-    instrumented forward and backward outside the timed region count the reached pairs and the
-    adjoint's atomics."""
+    objects): render, then dL/d(all attributes, poses) for a fixed upstream gradient, as a
+    training step runs it: the forward a graph replay, the backward differentiating the tile
+    lists its forward kept (keep_lists) into gradient buffers made once.  Beside it, the same
+    step with an eager forward, and with the default backward that bins the batch again into
+    fresh buffers.  The timed steps run without per-kernel events; kernel times per class come
+    from a separate profiled run, and one instrumented forward and backward count the reached
+    pairs and the adjoint's atomics."""
     import torch
     from paper_2507_21981_gb300 import scenes
-    from paper_2507_21981_gb300.render import DeviceScene, Renderer
+    from paper_2507_21981_gb300.render import DeviceScene, GradBuffers, Renderer
     sc = scenes.config4(seed=1)
     ds = DeviceScene(sc, device=dev, spatial_order=True)
-    r = Renderer(mode="batched", profile=True, keep_lists=1)
     gen = torch.Generator(device=dev).manual_seed(0)
     g_rgb = torch.randn((ds.n_pixels, 3), device=dev, generator=gen)
     g_d = torch.randn((ds.n_pixels,), device=dev, generator=gen)
     stream = torch.cuda.current_stream(dev)
+    gb = GradBuffers(ds)
 
-    def step(rr):
-        rgb, depth, _ = rr.render(ds)
-        rr.backward(ds, rgb, depth, g_rgb, g_d)
-    # the same step with the lists binned again by the backward (keep_lists = 0)
-    rb = Renderer(mode="batched")
-    for _ in range(warmup):
-        step(rb)
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        step(rb)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_rebuild = e0.elapsed_time(e1) / steps
-    rb.close()
-    for _ in range(warmup):
-        step(r)
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    def timed(r, out, n):
+        def step():
+            rgb, depth, _ = r.render(ds)
+            r.backward(ds, rgb, depth, g_rgb, g_d, out=out)
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        path = r.stats()["path"]
+        r.close()
+        return e0.elapsed_time(e1) / n, path
+    ms, path = timed(Renderer(mode="graph", keep_lists=1), gb, steps)
+    assert path == 4, "the backward did not use the kept lists"
+    ms_eager, _ = timed(Renderer(mode="batched", keep_lists=1), gb, steps)
+    ms_rebuild, _ = timed(Renderer(mode="batched"), None, steps)
+    # kernel times per class (library events) of the eager kept-lists step
+    r = Renderer(mode="batched", profile=True, keep_lists=1)
     kt = {}
-    e0.record(stream)
-    for _ in range(steps):
+    for i in range(warmup + steps):
         rgb, depth, _ = r.render(ds)
-        for k, v in r.kernel_times().items():
-            kt["fwd_" + k] = kt.get("fwd_" + k, 0.0) + v
-        r.backward(ds, rgb, depth, g_rgb, g_d)
-        for k, v in r.kernel_times().items():
-            kt["bwd_" + k] = kt.get("bwd_" + k, 0.0) + v
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1) / steps
+        fk = r.kernel_times()
+        r.backward(ds, rgb, depth, g_rgb, g_d, out=gb)
+        bk = r.kernel_times()
+        if i >= warmup:
+            for k, v in fk.items():
+                kt["fwd_" + k] = kt.get("fwd_" + k, 0.0) + v
+            for k, v in bk.items():
+                kt["bwd_" + k] = kt.get("bwd_" + k, 0.0) + v
     r.close()
     ri = Renderer(mode="batched", profile=2, keep_lists=1)
     rgb, depth, _ = ri.render(ds)
@@ -227,9 +230,8 @@ def fwd_bwd_500k(dev, warmup, steps):
     ri.backward(ds, rgb, depth, g_rgb, g_d)
     bwd = ri.stats()
     ri.close()
-    assert bwd["path"] == 4, "the backward did not use the kept lists"
-    return {"ms": ms, "ms_lists_binned_again": ms_rebuild, "views": 1, "gaussians": sc.n_gaussians,
-            "resolution": "800x800", "steps": steps,
+    return {"ms": ms, "ms_eager_forward": ms_eager, "ms_lists_binned_again": ms_rebuild, "views": 1,
+            "gaussians": sc.n_gaussians, "resolution": "800x800", "steps": steps,
             "kernel_ms": {k: v / steps for k, v in kt.items() if v > 0},
             "work": {"visible": fwd["n_visible"], "pairs": fwd["n_pairs"], "pairs_reached": fwd["px_reached"],
                      "pairs_composited": fwd["px_composited"], "bwd_reductions": bwd["bwd_reductions"]}}

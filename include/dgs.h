@@ -127,10 +127,11 @@ typedef struct dgs_options {
                                    it does, so the bounds check on tile-list entries fails
                                    (DGS_ERR_CUDA naming the check) while every access it lets
                                    through stays inside the records written */
-    int32_t keep_lists;         /* 1 = an eager render (batched or plain mode) of at most two view
-                                   groups keeps its tile lists, records and device tables on the
-                                   context, and a dgs_render_backward of the same batch differentiates
-                                   them instead of binning again (stats.path = DGS_PATH_KEPT_LISTS).
+    int32_t keep_lists;         /* 1 = a render of at most two view groups -- eager, or a graph
+                                   replay (not the call that captures) -- keeps its tile lists,
+                                   records and device tables on the context, and a
+                                   dgs_render_backward of the same batch differentiates them instead
+                                   of binning again (stats.path = DGS_PATH_KEPT_LISTS).
                                    "The same batch": equal node descriptors, env -> node table, node
                                    pose pointer, cameras, per-env camera counts and pixel offsets, and
                                    no call that stages a batch (dgs_render, dgs_render_backward

@@ -84,6 +84,11 @@ struct dgs_ctx {
     uint64_t cap_inst[2] = {0, 0}, cap_pairs[2] = {0, 0};  // capacities of each captured group
     int gbits = 0;
     int64_t glaunches = 0;
+    // per captured group: its views, tiles, final sort buffers and parameters (keep_lists)
+    int gv0[2] = {0, 0}, gv1[2] = {0, 0}, gtiles[2] = {0, 0};
+    const uint32_t* gkeys[2] = {nullptr, nullptr};
+    const uint32_t* gvals[2] = {nullptr, nullptr};
+    Params gP[2]{};
     int32_t captures = 0;
     void* h_graph = nullptr;              // pinned: error word + live totals after a replay
     void* h_meta = nullptr;
@@ -1157,6 +1162,8 @@ int enqueue_graph_body(dgs_ctx* ctx, const Batch& B, const Launch& L, float* out
                       (uint32_t)ctx->cap_pairs[g], sizes + 8 * g, sizes + 8 * g + 3, P, &keys, &vals);
         launch_composite(Lg, B.d_views, v0, v1 - v0, n_tiles, static_cast<uint2*>(lb.ranges.p), keys, vals,
                          static_cast<Record*>(lb.records.p), P, out_rgb, out_depth, out_alpha, nullptr);
+        ctx->gv0[g] = v0; ctx->gv1[g] = v1; ctx->gtiles[g] = n_tiles;
+        ctx->gkeys[g] = keys; ctx->gvals[g] = vals; ctx->gP[g] = P;
     }
     if (ng == 2) {
         cudaEvent_t join = take_event(ctx);
@@ -1226,7 +1233,7 @@ int capture_graph(dgs_ctx* ctx, const Batch& B, float* out_rgb, float* out_depth
 // DGS_MODE_GRAPH: replay the captured sequence when the staged batch has the captured
 // structure; otherwise (or after an overflow) render eagerly and capture for the next call.
 int render_graph(dgs_ctx* ctx, Batch& B, float* out_rgb, float* out_depth, float* out_alpha, cudaStream_t stream,
-                 Timer& tm) {
+                 Timer& tm, std::vector<GroupLists>* keep = nullptr) {
     int rc;
     if (ctx->gexec && same_key(make_key(ctx, B, out_rgb, out_depth, out_alpha), ctx->gkey)) {
         cudaEvent_t a = nullptr;
@@ -1267,6 +1274,16 @@ int render_graph(dgs_ctx* ctx, Batch& B, float* out_rgb, float* out_depth, float
             if (errw & kErrCapacity) return fail(ctx, DGS_ERR_CUDA, "internal: tile pairs beyond their bound");
             ctx->stats.path = DGS_PATH_GRAPH;
             ctx->stats.graph_captures = ctx->captures;
+            for (int g = 0; keep && g < ctx->gng; ++g) {
+                GroupLists G;
+                G.v0 = ctx->gv0[g]; G.v1 = ctx->gv1[g]; G.n_tiles = ctx->gtiles[g];
+                G.n_bound = (uint32_t)ctx->cap_pairs[g];
+                G.n_inst = (uint32_t)raw[2 * g];      // the replay's live count (at most the capacity)
+                G.keys = ctx->gkeys[g]; G.vals = ctx->gvals[g];
+                G.lb = &ctx->lists[g];
+                G.P = ctx->gP[g];
+                keep->push_back(G);
+            }
             return DGS_OK;
         }
         // the replay's outputs are invalid: render again eagerly (the staged tables are still
@@ -1434,27 +1451,31 @@ int dgs_render(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32
     int rc = stage(ctx, nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env, max_cams,
                    out_rgb, out_depth, view_pixel_offset, nullptr, stream, tm, B);
     if (rc != DGS_OK || B.V == 0) return rc;
-    if (ctx->opt.mode == DGS_MODE_GRAPH && B.T > 0) {
-        rc = render_graph(ctx, B, out_rgb, out_depth, out_alpha, stream, tm);
-    } else {
-        // keep_lists: at most two view groups, one per list workspace, stay in place
-        const bool keep = ctx->opt.keep_lists && ctx->opt.mode != DGS_MODE_GRAPH;
-        std::vector<GroupLists> groups;
-        rc = run_eager(ctx, B, out_rgb, out_depth, out_alpha, stream, tm, keep ? &groups : nullptr);
-        if (rc == DGS_OK && keep && !groups.empty() && groups.size() <= 2 && groups.size() == B.groups.size()) {
-            if (!ctx->saved) ctx->saved.reset(new SavedForward);
-            SavedForward& S = *ctx->saved;
-            S.sig = call_signature(nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env,
-                                   max_cams, view_pixel_offset);
+    // keep_lists: the lists of at most two view groups (one per list workspace) stay in place;
+    // an eager render keeps them, and so does a graph replay (not the call that captures)
+    std::vector<GroupLists> groups;
+    std::vector<GroupLists>* keep = ctx->opt.keep_lists ? &groups : nullptr;
+    if (ctx->opt.mode == DGS_MODE_GRAPH && B.T > 0)
+        rc = render_graph(ctx, B, out_rgb, out_depth, out_alpha, stream, tm, keep);
+    else
+        rc = run_eager(ctx, B, out_rgb, out_depth, out_alpha, stream, tm, keep);
+    if (rc == DGS_OK && keep && !groups.empty() && groups.size() <= 2) {
+        if (!ctx->saved) ctx->saved.reset(new SavedForward);
+        SavedForward& S = *ctx->saved;
+        S.sig = call_signature(nodes, n_nodes, env_node_ids, n_envs, max_nodes, node_poses, cams, cams_per_env,
+                               max_cams, view_pixel_offset);
+        S.B = B;
+        S.inst_at.clear();
+        S.pair_at.clear();
+        if (B.inst_at) {
             S.inst_at.assign(B.inst_at, B.inst_at + B.V + 1);
             S.pair_at.assign(B.pair_at, B.pair_at + B.V + 1);
-            S.B = B;
-            S.B.inst_at = S.inst_at.data();
-            S.B.pair_at = S.pair_at.data();
-            S.groups = std::move(groups);
-            S.stats = ctx->stats;
-            S.valid = true;
         }
+        S.B.inst_at = B.inst_at ? S.inst_at.data() : nullptr;
+        S.B.pair_at = B.pair_at ? S.pair_at.data() : nullptr;
+        S.groups = std::move(groups);
+        S.stats = ctx->stats;
+        S.valid = true;
     }
     ctx->stats.graph_captures = ctx->captures;
     return rc;
@@ -1588,13 +1609,17 @@ int dgs_render_backward(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, co
         if (rc != DGS_OK || B.V == 0) return rc;
     }
     uint64_t max_inst = 1;
-    for (auto& g : B.groups) max_inst = std::max<uint64_t>(max_inst, B.inst_at[g.second] - B.inst_at[g.first]);
+    if (S)
+        for (const GroupLists& G : S->groups) max_inst = std::max<uint64_t>(max_inst, G.n_inst);
+    else
+        for (auto& g : B.groups) max_inst = std::max<uint64_t>(max_inst, B.inst_at[g.second] - B.inst_at[g.first]);
     if ((rc = ensure(ctx, ctx->inst_grad, sizeof(float) * 10 * max_inst))) return rc;
     if (ctx->opt.profile >= 2) {
         n_red = reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->errword.p) + 56);
         DGS_CUDA(ctx, cudaMemsetAsync(n_red, 0, sizeof(unsigned long long), stream));
     }
-    for (int g = 0; g < (int)B.groups.size(); ++g) {
+    const int ng = S ? (int)S->groups.size() : (int)B.groups.size();
+    for (int g = 0; g < ng; ++g) {
         GroupLists G;
         if (S) G = S->groups[g];
         else build_group_lists(ctx, B, g, ctx->lists[0], stream, tm, G);
@@ -1602,6 +1627,7 @@ int dgs_render_backward(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, co
             return rc;
     }
     rc = finish(ctx, B, stream);
+    if (S) ctx->stats.n_pairs = S->stats.n_pairs;
     if (rc == DGS_OK && n_red) {
         unsigned long long h = 0;
         DGS_CUDA(ctx, cudaMemcpy(&h, n_red, sizeof(h), cudaMemcpyDeviceToHost));

@@ -256,38 +256,25 @@ class Renderer:
         return best, times, (rgb, depth, alpha)
 
     def backward(self, ds: DeviceScene, out_rgb, out_depth, grad_rgb, grad_depth=None, want_poses: bool = True,
-                 stream=None):
+                 stream=None, out: "GradBuffers | None" = None):
         """Gradients of L = sum(grad_rgb * rgb) + sum(grad_depth * depth) for the render of `ds`.
 
         Returns (list of per-node dicts of FP32 tensors mean/log_scale/quat/opacity_logit/sh,
-        pose gradient [E,K,3,4] or None)."""
-        node_grads = []
-        arr = (D.dgs_node_grads * ds.n_nodes)()
-        # every gradient is a view of one zeroed buffer (one fill instead of one per tensor)
-        names = ("mean", "log_scale", "quat", "opacity_logit", "sh")
-        sizes = [t[name].numel() for t in ds.tensors for name in names]
-        flat = torch.zeros(sum(sizes) + (ds.n_envs * ds.max_nodes * 12 if want_poses else 0), dtype=torch.float32,
-                           device=ds.device)
-        off = 0
-        for k, t in enumerate(ds.tensors):
-            g = {}
-            for name in names:
-                n = t[name].numel()
-                g[name] = flat[off:off + n].view(t[name].shape)
-                off += n
-            node_grads.append(g)
-            arr[k].mean, arr[k].log_scale, arr[k].quat = g["mean"].data_ptr(), g["log_scale"].data_ptr(), g["quat"].data_ptr()
-            arr[k].opacity_logit, arr[k].sh = g["opacity_logit"].data_ptr(), g["sh"].data_ptr()
-        gposes = flat[off:].view(ds.n_envs, ds.max_nodes, 12) if want_poses else None
+        pose gradient [E,K,3,4] or None).  With `out` (GradBuffers(ds) made once) the
+        gradients are written into its buffers, zeroed first, and those are returned: the next
+        backward with the same `out` overwrites them."""
+        gb = GradBuffers(ds, want_poses) if out is None else out
+        if out is not None:
+            gb.flat.zero_()
         s = stream if stream is not None else torch.cuda.current_stream(ds.device)
         grad_rgb = grad_rgb.contiguous().float()
         grad_depth = None if grad_depth is None else grad_depth.contiguous().float()
         rc = D.dgs_render_backward(self.ctx, ds.nodes, ds.n_nodes, ds.env_node_ids, ds.n_envs, ds.max_nodes,
                                    ds.node_poses, ds.cams, ds.cams_per_env, ds.max_cams, out_rgb, out_depth, grad_rgb,
-                                   grad_depth, arr, gposes, None, s.cuda_stream)
+                                   grad_depth, gb.arr, gb.gposes, None, s.cuda_stream)
         if rc != D.DGS_OK:
             raise D.DgsError(rc, D.dgs_last_error(self.ctx))
-        return node_grads, (None if gposes is None else gposes.view(ds.n_envs, ds.max_nodes, 3, 4))
+        return gb.node_grads, (None if gb.gposes is None else gb.gposes.view(ds.n_envs, ds.max_nodes, 3, 4))
 
     def stats(self) -> dict:
         return D.dgs_last_stats(self.ctx)
@@ -300,6 +287,33 @@ class Renderer:
 
     def workspace_bytes(self) -> int:
         return D.dgs_workspace_query(self.ctx)
+
+
+class GradBuffers:
+    """Gradient outputs of Renderer.backward for one DeviceScene: one zero-filled FP32 buffer
+    holding every node's attribute gradients (and the pose gradient), its per-node views and
+    the dgs_node_grads table of their addresses.  Made once and passed as `out`, it spares each
+    backward the allocation and the view set-up."""
+
+    NAMES = ("mean", "log_scale", "quat", "opacity_logit", "sh")
+
+    def __init__(self, ds: DeviceScene, want_poses: bool = True):
+        sizes = [t[name].numel() for t in ds.tensors for name in self.NAMES]
+        n_pose = ds.n_envs * ds.max_nodes * 12 if want_poses else 0
+        self.flat = torch.zeros(sum(sizes) + n_pose, dtype=torch.float32, device=ds.device)
+        self.arr = (D.dgs_node_grads * ds.n_nodes)()
+        self.node_grads = []
+        parts = torch.split(self.flat, sizes + ([n_pose] if n_pose else []))
+        base = self.flat.data_ptr()
+        off = 0
+        for k, t in enumerate(ds.tensors):
+            g = {}
+            for j, name in enumerate(self.NAMES):
+                g[name] = parts[5 * k + j].view(t[name].shape)
+                setattr(self.arr[k], name, base + 4 * off)
+                off += sizes[5 * k + j]
+            self.node_grads.append(g)
+        self.gposes = parts[-1].view(ds.n_envs, ds.max_nodes, 12) if n_pose else None
 
 
 class DGSRenderFn(torch.autograd.Function):

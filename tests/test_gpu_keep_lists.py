@@ -58,6 +58,26 @@ def test_kept_lists_give_the_rebuilt_gradients(views_per_group):
     r.close()
 
 
+def test_graph_replay_keeps_its_lists():
+    from paper_2507_21981_gb300.render import DeviceScene, Renderer
+    sc = S.config2(seed=7, n_envs=2, n_bg=30_000, n_obj=1_000, width=160, height=120, f=125.0)
+    ds = DeviceScene(sc, device="cuda:0")
+    ref_r = Renderer(mode="batched")
+    rgb, depth, _ = ref_r.render(ds)
+    ref, _ = _grads(ref_r, ds, rgb, depth)
+    for vpg in (0, 2):
+        r = Renderer(mode="graph", keep_lists=1, views_per_group=vpg)
+        r.render(ds)                                   # renders eagerly and captures
+        rgb2, depth2, _ = r.render(ds)                 # replays
+        assert r.stats()["path"] == D.DGS_PATH_GRAPH
+        assert torch.equal(rgb, rgb2) and torch.equal(depth, depth2)
+        got, path = _grads(r, ds, rgb2, depth2)
+        assert path == D.DGS_PATH_KEPT_LISTS
+        _close(ref, got)
+        r.close()
+    ref_r.close()
+
+
 def test_another_batch_or_new_options_make_the_backward_bin_again():
     from paper_2507_21981_gb300.render import DeviceScene, Renderer
     sa = S.config2(seed=7, n_envs=2, n_bg=30_000, n_obj=1_000, width=160, height=120, f=125.0)
@@ -101,3 +121,23 @@ def test_three_view_groups_are_not_kept():
 def test_kept_lists_backward_against_the_oracle():
     sc = S.config4(seed=2, n_bg=30_000, n_obj=2_000, res=160, f=140.0)
     _compare(sc, *_gradients(sc, seed=4, keep_lists=1))
+
+
+def test_gradient_buffers_made_once_give_the_fresh_gradients():
+    from paper_2507_21981_gb300.render import DeviceScene, GradBuffers, Renderer
+    sc = S.config2(seed=7, n_envs=2, n_bg=30_000, n_obj=1_000, width=160, height=120, f=125.0)
+    ds = DeviceScene(sc, device="cuda:0")
+    r = Renderer(mode="batched", keep_lists=1)
+    rgb, depth, _ = r.render(ds)
+    ref, _ = _grads(r, ds, rgb, depth)
+    gb = GradBuffers(ds)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    gC = torch.randn(rgb.shape, device="cuda", generator=gen)
+    gD = torch.randn(depth.shape, device="cuda", generator=gen)
+    for _ in range(2):                      # the second call must start from zero again
+        ng, gp = r.backward(ds, rgb, depth, gC, gD, out=gb)
+        torch.cuda.synchronize()
+        got = [{k: v.cpu().numpy() for k, v in g.items()} for g in ng] + [gp.cpu().numpy()]
+        _close(ref, got)
+    assert ng is gb.node_grads
+    r.close()
