@@ -54,9 +54,11 @@ struct GraphKey {
 // tkeys/tvals: (tile, instance) pairs (tile sort, ping-pong); ranges: per tile.
 struct ListBufs {
     DevBuf records, info, dkey0, ival0, dkey1, ival1, ntile, poff, tparts, tkeys0, tvals0, tkeys1, tvals1, hist,
-        status, counters, ranges;
-    DevBuf* all[17] = {&records, &info, &dkey0, &ival0, &dkey1, &ival1, &ntile, &poff, &tparts, &tkeys0, &tvals0,
-                       &tkeys1, &tvals1, &hist, &status, &counters, &ranges};
+        status, counters, ranges, torder, ck_st, ck_off, ck_last, ck_jobs, ck_njobs;
+    static constexpr int kCount = 23;
+    DevBuf* all[kCount] = {&records, &info, &dkey0, &ival0, &dkey1, &ival1, &ntile, &poff, &tparts, &tkeys0, &tvals0,
+                           &tkeys1, &tvals1, &hist, &status, &counters, &ranges, &torder, &ck_st, &ck_off, &ck_last,
+                           &ck_jobs, &ck_njobs};
     ListBufs() = default;
     ListBufs(const ListBufs&) = delete;
     ListBufs& operator=(const ListBufs&) = delete;
@@ -88,7 +90,10 @@ struct dgs_ctx {
     int gv0[2] = {0, 0}, gv1[2] = {0, 0}, gtiles[2] = {0, 0};
     const uint32_t* gkeys[2] = {nullptr, nullptr};
     const uint32_t* gvals[2] = {nullptr, nullptr};
+    const uint32_t* gorder[2] = {nullptr, nullptr};
     Params gP[2]{};
+    Checkpoints gck[2]{};
+    uint32_t gjobs[2] = {0, 0};
     int32_t captures = 0;
     void* h_graph = nullptr;              // pinned: error word + live totals after a replay
     void* h_meta = nullptr;
@@ -659,23 +664,40 @@ void launch_front(dgs_ctx* ctx, const Batch& B, const Launch& L, Timer& tm) {
 // Workspace of one set of group lists: n_inst instances, n_pairs tile pairs, n_tiles tiles.
 // Bytes of each buffer of ListBufs (in ListBufs::all order) for one view group of n_inst
 // instances, n_pairs tile pairs and n_tiles tiles.
-void list_bytes(uint64_t n_inst, uint64_t n_pairs, int64_t n_tiles, size_t out[17]) {
+// Compositor checkpoints of a group (keep_lists): slots for every segment after a tile's first,
+// n_pairs / kSegEntries + 1 at most, of one CkState per pixel of each sub-tile; none beyond
+// kMaxCheckpointBytes or kOrderMaxTiles tiles.
+constexpr size_t kMaxCheckpointBytes = size_t(512) << 20;
+uint64_t ck_slots(uint64_t n_pairs) { return n_pairs / kSegEntries + 1; }
+size_t ck_state_bytes(uint64_t n_pairs, int64_t n_tiles, int tile_px) {
+    if (n_tiles > kOrderMaxTiles) return 0;
+    const size_t b = sizeof(CkState) * ck_slots(n_pairs) * (size_t)tile_px;
+    return b <= kMaxCheckpointBytes ? b : 0;
+}
+
+void list_bytes(uint64_t n_inst, uint64_t n_pairs, int64_t n_tiles, int tile_px, bool with_ck,
+                size_t out[ListBufs::kCount]) {
     n_inst = std::max<uint64_t>(n_inst, 1);
     n_pairs = std::max<uint64_t>(n_pairs, 1);
     const size_t u = sizeof(uint32_t);
-    const size_t b[17] = {sizeof(Record) * n_inst, sizeof(InstInfo) * n_inst, u * n_inst, u * n_inst, u * n_inst,
-                          u * n_inst, u * n_inst, u * (n_inst + 1), u * tile_scan_parts((uint32_t)n_inst),
-                          u * n_pairs, u * n_pairs, u * n_pairs, u * n_pairs, u * 4 * 1024,
-                          u * sort_status_words((uint32_t)std::max(n_inst, n_pairs)), u * 8,
-                          sizeof(uint2) * (size_t)std::max<int64_t>(n_tiles, 1)};
-    for (int i = 0; i < 17; ++i) out[i] = b[i];
+    const size_t nt = (size_t)std::max<int64_t>(n_tiles, 1);
+    const size_t ck = with_ck ? ck_state_bytes(n_pairs, n_tiles, tile_px) : 0;
+    const size_t n_sub = (size_t)tile_px / 32;
+    const size_t b[ListBufs::kCount] = {
+        sizeof(Record) * n_inst, sizeof(InstInfo) * n_inst, u * n_inst, u * n_inst, u * n_inst,
+        u * n_inst, u * n_inst, u * (n_inst + 1), u * tile_scan_parts((uint32_t)n_inst),
+        u * n_pairs, u * n_pairs, u * n_pairs, u * n_pairs, u * 4 * 1024,
+        u * sort_status_words((uint32_t)std::max(n_inst, n_pairs)), u * 8,
+        sizeof(uint2) * nt, n_tiles <= kOrderMaxTiles ? u * nt : 0,
+        ck, ck ? u * nt : 0, ck ? u * nt * n_sub : 0, ck ? sizeof(uint2) * (nt + ck_slots(n_pairs)) : 0, ck ? u : 0};
+    for (int i = 0; i < ListBufs::kCount; ++i) out[i] = b[i];
 }
 
 // Workspace of one set of group lists: n_inst instances, n_pairs tile pairs, n_tiles tiles.
 int ensure_lists(dgs_ctx* ctx, ListBufs& lb, uint64_t n_inst, uint64_t n_pairs, int64_t n_tiles) {
-    size_t bytes[17];
-    list_bytes(n_inst, n_pairs, n_tiles, bytes);
-    for (int i = 0; i < 17; ++i) {
+    size_t bytes[ListBufs::kCount];
+    list_bytes(n_inst, n_pairs, n_tiles, ctx->opt.tile_w * ctx->opt.tile_h, ctx->opt.keep_lists != 0, bytes);
+    for (int i = 0; i < ListBufs::kCount; ++i) {
         const int rc = ensure(ctx, *lb.all[i], bytes[i]);
         if (rc) return rc;
     }
@@ -756,8 +778,8 @@ int readback_groups(dgs_ctx* ctx, Batch& B, cudaStream_t stream, Timer& tm, size
     ctx->stats.n_groups = (int32_t)groups.size();
     ctx->stats.key_bits = max_bits;
     if (need) {   // a workspace query: the bytes of the lists, nothing allocated
-        size_t bytes[17];
-        list_bytes(max_inst, max_pairs, max_tiles, bytes);
+        size_t bytes[ListBufs::kCount];
+        list_bytes(max_inst, max_pairs, max_tiles, o.tile_w * o.tile_h, o.keep_lists != 0, bytes);
         size_t s = 0;
         for (size_t b : bytes) s += b;
         *need = s * (groups.size() > 1 ? 2 : 1);
@@ -789,10 +811,14 @@ int prepare(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t*
 //   n_bound  bound on its pairs (host; the capacity the pair buffers hold)
 //   d_inst   device count of instances (graph replay) or null
 //   d_pairs  device word receiving the group's exact pair count (at most n_bound)
-// Returns the tile-sorted instance numbers in *vals.
+// Returns the tile-sorted instance numbers in *vals and, for groups of at most kOrderMaxTiles
+// tiles, the tiles by descending list length in *tile_order (else null).  With want_ck and
+// keep_lists, and room for them, *ck receives the checkpoints that the group's compositor is to
+// write and the adjoint's (tile, segment) jobs (bounded by *n_jobs_bound); else ck->st is null.
 void enqueue_lists(dgs_ctx* ctx, ListBufs& lb, const Batch& B, const Launch& L, Timer& tm, int v0, int v1, int n_tiles,
                    uint32_t inst_base, uint32_t n_inst, uint32_t n_bound, const uint32_t* d_inst, uint32_t* d_pairs,
-                   const Params& P, const uint32_t** keys, const uint32_t** vals) {
+                   const Params& P, const uint32_t** keys, const uint32_t** vals, const uint32_t** tile_order,
+                   Checkpoints* ck, uint32_t* n_jobs_bound, bool want_ck = true) {
     const int K = B.K;
     auto u32 = [](DevBuf& b) { return static_cast<uint32_t*>(b.p); };
     Record* rec = static_cast<Record*>(lb.records.p);
@@ -821,6 +847,23 @@ void enqueue_lists(dgs_ctx* ctx, ListBufs& lb, const Batch& B, const Launch& L, 
     tm.end();
     tm.begin(DGS_K_RANGES);
     launch_ranges(L, tk, n_bound, static_cast<uint2*>(lb.ranges.p), n_tiles, d_pairs);
+    *tile_order = nullptr;
+    if (n_tiles <= kOrderMaxTiles && lb.torder.bytes >= sizeof(uint32_t) * (size_t)n_tiles) {
+        launch_tile_order(L, static_cast<uint2*>(lb.ranges.p), n_tiles, static_cast<uint32_t*>(lb.torder.p));
+        *tile_order = static_cast<uint32_t*>(lb.torder.p);
+    }
+    *ck = Checkpoints{};
+    *n_jobs_bound = 0;
+    const size_t ck_need = ck_state_bytes(n_bound, n_tiles, P.tile_w * P.tile_h);
+    if (want_ck && ctx->opt.keep_lists && ck_need && lb.ck_st.bytes >= ck_need) {
+        ck->st = static_cast<CkState*>(lb.ck_st.p);
+        ck->off = u32(lb.ck_off);
+        ck->last = u32(lb.ck_last);
+        ck->jobs = static_cast<uint2*>(lb.ck_jobs.p);
+        ck->n_jobs = u32(lb.ck_njobs);
+        *n_jobs_bound = (uint32_t)(n_tiles + ck_slots(n_bound));
+        launch_segment_jobs(L, static_cast<uint2*>(lb.ranges.p), n_tiles, *ck);
+    }
     tm.end();
     *keys = tk;
     *vals = tv;
@@ -832,6 +875,9 @@ struct GroupLists {
     uint32_t n_bound = 0, n_inst = 0;
     const uint32_t* keys = nullptr;
     const uint32_t* vals = nullptr;
+    const uint32_t* order = nullptr;      // tiles by descending list length, or null
+    Checkpoints ck{};                     // compositor checkpoints (keep_lists), or ck.st null
+    uint32_t n_jobs_bound = 0;            // bound on the adjoint's (tile, segment) jobs
     ListBufs* lb = nullptr;
     Params P{};
 };
@@ -884,7 +930,7 @@ std::vector<unsigned char> call_signature(const dgs_node* nodes, int32_t n_nodes
 }
 
 void build_group_lists(dgs_ctx* ctx, const Batch& B, int g, ListBufs& lb, cudaStream_t stream, Timer& tm,
-                       GroupLists& G) {
+                       GroupLists& G, bool for_forward = true) {
     Launch L{stream, &ctx->launches};
     const int V = B.V;
     const int v0 = B.groups[g].first, v1 = B.groups[g].second;
@@ -898,7 +944,8 @@ void build_group_lists(dgs_ctx* ctx, const Batch& B, int g, ListBufs& lb, cudaSt
     G.P.n_rec = G.n_inst;
     G.lb = &lb;
     enqueue_lists(ctx, lb, B, L, tm, v0, v1, G.n_tiles, (uint32_t)B.inst_at[v0], G.n_inst, G.n_bound, nullptr,
-                  static_cast<uint32_t*>(ctx->totals.p) + g, G.P, &G.keys, &G.vals);
+                  static_cast<uint32_t*>(ctx->totals.p) + g, G.P, &G.keys, &G.vals, &G.order, &G.ck,
+                  &G.n_jobs_bound, for_forward);
     // test_fault 3 (debug builds): the compositors' bound on instance numbers is half the
     // records written, so the entries of the upper half fail the check while every access the
     // check lets through stays inside the records of the group
@@ -1035,7 +1082,8 @@ int run_eager(dgs_ctx* ctx, Batch& B, float* out_rgb, float* out_depth, float* o
         Launch Lg{streams[b], &ctx->launches};
         tms[b].begin(DGS_K_COMPOSITE);
         launch_composite(Lg, B.d_views, G.v0, G.v1 - G.v0, G.n_tiles, static_cast<uint2*>(G.lb->ranges.p), G.keys, G.vals,
-                         static_cast<Record*>(G.lb->records.p), G.P, out_rgb, out_depth, out_alpha, work);
+                         static_cast<Record*>(G.lb->records.p), G.P, out_rgb, out_depth, out_alpha, work, G.order,
+                         G.ck);
         tms[b].end();
         DGS_CUDA(ctx, cudaGetLastError());
         if (keep) keep->push_back(G);
@@ -1157,13 +1205,17 @@ int enqueue_graph_body(dgs_ctx* ctx, const Batch& B, const Launch& L, float* out
         P.inst_base_dev = sizes + 8 * g + 4;
         P.n_rec = (uint32_t)ctx->cap_inst[g];
         ListBufs& lb = ctx->lists[g];
-        const uint32_t *keys = nullptr, *vals = nullptr;
+        const uint32_t *keys = nullptr, *vals = nullptr, *order = nullptr;
+        Checkpoints ck{};
+        uint32_t n_jobs_bound = 0;
         enqueue_lists(ctx, lb, B, Lg, tg, v0, v1, n_tiles, 0u, (uint32_t)ctx->cap_inst[g],
-                      (uint32_t)ctx->cap_pairs[g], sizes + 8 * g, sizes + 8 * g + 3, P, &keys, &vals);
+                      (uint32_t)ctx->cap_pairs[g], sizes + 8 * g, sizes + 8 * g + 3, P, &keys, &vals, &order, &ck,
+                      &n_jobs_bound);
         launch_composite(Lg, B.d_views, v0, v1 - v0, n_tiles, static_cast<uint2*>(lb.ranges.p), keys, vals,
-                         static_cast<Record*>(lb.records.p), P, out_rgb, out_depth, out_alpha, nullptr);
+                         static_cast<Record*>(lb.records.p), P, out_rgb, out_depth, out_alpha, nullptr, order, ck);
         ctx->gv0[g] = v0; ctx->gv1[g] = v1; ctx->gtiles[g] = n_tiles;
-        ctx->gkeys[g] = keys; ctx->gvals[g] = vals; ctx->gP[g] = P;
+        ctx->gkeys[g] = keys; ctx->gvals[g] = vals; ctx->gorder[g] = order; ctx->gP[g] = P;
+        ctx->gck[g] = ck; ctx->gjobs[g] = n_jobs_bound;
     }
     if (ng == 2) {
         cudaEvent_t join = take_event(ctx);
@@ -1279,7 +1331,8 @@ int render_graph(dgs_ctx* ctx, Batch& B, float* out_rgb, float* out_depth, float
                 G.v0 = ctx->gv0[g]; G.v1 = ctx->gv1[g]; G.n_tiles = ctx->gtiles[g];
                 G.n_bound = (uint32_t)ctx->cap_pairs[g];
                 G.n_inst = (uint32_t)raw[2 * g];      // the replay's live count (at most the capacity)
-                G.keys = ctx->gkeys[g]; G.vals = ctx->gvals[g];
+                G.keys = ctx->gkeys[g]; G.vals = ctx->gvals[g]; G.order = ctx->gorder[g];
+                G.ck = ctx->gck[g]; G.n_jobs_bound = ctx->gjobs[g];
                 G.lb = &ctx->lists[g];
                 G.P = ctx->gP[g];
                 keep->push_back(G);
@@ -1555,7 +1608,7 @@ int enqueue_adjoint(dgs_ctx* ctx, const Batch& B, const GroupLists& G, const flo
     DGS_CUDA(ctx, cudaMemsetAsync(ctx->inst_grad.p, 0, sizeof(float) * 10 * std::max<uint32_t>(G.n_inst, 1), stream));
     launch_composite_bwd(L, B.d_views, G.v0, G.v1 - G.v0, G.n_tiles, static_cast<uint2*>(G.lb->ranges.p), G.keys, G.vals,
                          static_cast<Record*>(G.lb->records.p), G.P, out_rgb, out_depth, grad_rgb, grad_depth,
-                         static_cast<float*>(ctx->inst_grad.p), n_red);
+                         static_cast<float*>(ctx->inst_grad.p), n_red, G.order, G.ck, G.n_jobs_bound);
     tm.end();
     tm.begin(DGS_K_BACKWARD_PROJECT);
     launch_project_bwd(L, B.dtype_mask, B.d_nodes, B.n_nodes, B.d_views, B.d_vnodes, B.K, B.node_poses,
@@ -1622,7 +1675,7 @@ int dgs_render_backward(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, co
     for (int g = 0; g < ng; ++g) {
         GroupLists G;
         if (S) G = S->groups[g];
-        else build_group_lists(ctx, B, g, ctx->lists[0], stream, tm, G);
+        else build_group_lists(ctx, B, g, ctx->lists[0], stream, tm, G, false);   // no forward: no checkpoints
         if ((rc = enqueue_adjoint(ctx, B, G, out_rgb, out_depth, grad_rgb, grad_depth, grad_poses, n_red, stream, tm)))
             return rc;
     }

@@ -55,7 +55,7 @@ __device__ __forceinline__ float warp_transpose_sum16(const float (&v)[16], int 
 }
 
 // ------------------------------------------------------------------ K7
-__global__ void __launch_bounds__(256) k_composite_bwd(const ViewDesc* __restrict__ views, int v0, int nv,
+__global__ void __launch_bounds__(kCompWarps * 32) k_composite_bwd(const ViewDesc* __restrict__ views, int v0, int nv,
                                                        const uint2* __restrict__ ranges, const uint32_t* __restrict__ keys,
                                                        const uint32_t* __restrict__ vals,
                                                        const Record* __restrict__ rec, Params P,
@@ -63,11 +63,25 @@ __global__ void __launch_bounds__(256) k_composite_bwd(const ViewDesc* __restric
                                                        const float* __restrict__ out_depth,
                                                        const float* __restrict__ g_rgb,
                                                        const float* __restrict__ g_depth, float* __restrict__ ig,
-                                                       unsigned long long* __restrict__ n_red) {
-    __shared__ float4 s_rec[8][3][32];
-    __shared__ uint32_t s_idx[8][32];
+                                                       unsigned long long* __restrict__ n_red,
+                                                       const uint32_t* __restrict__ tile_order, Checkpoints ck) {
+    __shared__ float4 s_rec[kCompWarps][3][32];
+    __shared__ uint32_t s_idx[kCompWarps][32];
     if (sort_failed(P.err)) return;
-    const int gt = blockIdx.x;
+    const int bpt = (P.tile_w * P.tile_h) / (32 * kCompWarps);   // blocks per tile, as the forward
+    const int tb = (int)blockIdx.x / bpt;
+    // with checkpoints a block replays one segment of one tile's list (jobs longest first),
+    // else the whole list of a tile
+    int gt;
+    uint32_t seg = 0;
+    if (ck.st) {
+        if ((uint32_t)tb >= *ck.n_jobs) return;
+        const uint2 job = ck.jobs[tb];
+        gt = (int)job.x;
+        seg = job.y;
+    } else {
+        gt = tile_order ? (int)tile_order[tb] : tb;
+    }
     const int ga = gt + P.tile0;
     int lo = v0, hi = v0 + nv - 1;
     while (lo < hi) {
@@ -77,7 +91,8 @@ __global__ void __launch_bounds__(256) k_composite_bwd(const ViewDesc* __restric
     const ViewDesc& vd = views[lo];
     const int tile = ga - vd.tile_base;
     const int tx = tile % vd.tiles_x, ty = tile / vd.tiles_x;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, bw = threadIdx.x >> 5;
+    const int w = ((int)blockIdx.x - tb * bpt) * kCompWarps + bw;   // sub-tile within the tile
     const int sub_cols = P.tile_w >> 3;
     const int wx0 = tx * P.tile_w + (w % sub_cols) * 8, wy0 = ty * P.tile_h + (w / sub_cols) * 4;
     const int wx1 = min(wx0 + 7, vd.W - 1), wy1 = min(wy0 + 3, vd.H - 1);
@@ -94,15 +109,27 @@ __global__ void __launch_bounds__(256) k_composite_bwd(const ViewDesc* __restric
         Do = out_depth[p];
     }
     if (__all_sync(0xffffffffu, gC0 == 0.f && gC1 == 0.f && gC2 == 0.f && gD == 0.f)) return;
-    const uint2 range = ranges[gt];
+    uint2 range = ranges[gt];
     uint32_t reds = 0;
     float T = 1.f, P0 = 0.f, P1 = 0.f, P2 = 0.f, PD = 0.f;
     bool done = !inside;
+    if (ck.st) {
+        const int n_sub = P.tile_w * P.tile_h / 32;
+        range.x += seg * kSegEntries;
+        range.y = min(range.y, range.x + kSegEntries);
+        if (seg > 0) {
+            // the forward warp's state where this segment starts, or nothing to do if it ended before
+            if (seg >= ck.last[(size_t)gt * n_sub + w]) return;
+            const CkState c = ck.st[((size_t)(ck.off[gt] + seg - 1) * n_sub + w) * 32 + lane];
+            T = c.T; P0 = c.c0; P1 = c.c1; P2 = c.c2; PD = c.d;
+            done = c.done != 0.f;
+        }
+    }
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t wbit = 1u << (kTileBits + w);
-    float4* const sr0 = s_rec[w][0];
-    float4* const sr1 = s_rec[w][1];
-    float4* const sr2 = s_rec[w][2];
+    float4* const sr0 = s_rec[bw][0];
+    float4* const sr1 = s_rec[bw][1];
+    float4* const sr2 = s_rec[bw][2];
     for (uint32_t base = range.x; base < range.y; base += 32) {
         if (__all_sync(0xffffffffu, done)) break;
         const uint32_t i = base + lane;
@@ -118,7 +145,7 @@ __global__ void __launch_bounds__(256) k_composite_bwd(const ViewDesc* __restric
             const Record* r = rec + idx;
             const int pos = __popc(m & lt);
             sr0[pos] = r->r0; sr1[pos] = r->r1; sr2[pos] = r->r2;
-            s_idx[w][pos] = idx;
+            s_idx[bw][pos] = idx;
         }
         __syncwarp();
         const int n = __popc(m);
@@ -167,7 +194,7 @@ __global__ void __launch_bounds__(256) k_composite_bwd(const ViewDesc* __restric
                 }
             }
             if (__ballot_sync(0xffffffffu, contrib) == 0) continue;
-            const uint32_t r = s_idx[w][k];
+            const uint32_t r = s_idx[bw][k];
             float v16[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e) v16[e] = e < G_N ? g[e] : 0.f;
@@ -496,10 +523,14 @@ void launch_pose_twist(const Launch& L, const float* poses, const float* grads, 
 void launch_composite_bwd(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
                           const uint2* ranges, const uint32_t* keys, const uint32_t* vals, const Record* records,
                           const Params& P, const float* out_rgb, const float* out_depth, const float* g_rgb,
-                          const float* g_depth, float* inst_grad, unsigned long long* n_red) {
+                          const float* g_depth, float* inst_grad, unsigned long long* n_red,
+                          const uint32_t* tile_order, const Checkpoints& ck, uint32_t n_jobs_bound) {
     if (n_tiles == 0) return;
-    k_composite_bwd<<<n_tiles, P.tile_w * P.tile_h, 0, L.stream>>>(views, v0, n_group_views, ranges, keys, vals, records, P,
-                                                                   out_rgb, out_depth, g_rgb, g_depth, inst_grad, n_red);
+    const int bpt = (P.tile_w * P.tile_h) / (32 * kCompWarps);
+    const uint32_t units = ck.st ? n_jobs_bound : (uint32_t)n_tiles;   // jobs beyond the live count exit
+    k_composite_bwd<<<units * bpt, kCompWarps * 32, 0, L.stream>>>(views, v0, n_group_views, ranges, keys, vals,
+                                                                   records, P, out_rgb, out_depth, g_rgb, g_depth,
+                                                                   inst_grad, n_red, tile_order, ck);
     ++*L.launches;
 }
 

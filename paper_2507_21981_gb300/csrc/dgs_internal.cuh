@@ -466,9 +466,42 @@ void launch_ranges(const Launch& L, const uint32_t* keys, uint32_t n, uint2* ran
 
 // K5: keys/vals are the tile-sorted pairs (each key's sub-tile mask selects the warps that
 // stage the instance).
+// Checkpoints of the compositor's per-pixel state, for an adjoint that replays the segments of
+// long tile lists in parallel (kept lists only).  A tile's list is cut into segments of
+// kSegEntries entries; at the start of every segment after the first, the forward warp of each
+// sub-tile stores its pixels' state, and at its end how many segments it entered.  The adjoint
+// replays each (tile, segment) job from the state the forward had there, so every job takes the
+// forward's FP32 decisions exactly as one sequential replay would.
+constexpr int kSegChunks = 16;                              // 32-entry chunks per segment
+constexpr uint32_t kSegEntries = 32u * (uint32_t)kSegChunks;
+struct CkState {
+    float T, c0, c1, c2, d, done;                           // transmittance, RGB and depth sums
+};
+struct Checkpoints {
+    CkState* st = nullptr;          // [slot][sub-tile][lane]; null: no checkpoints
+    uint32_t* off = nullptr;        // per tile: its first slot (segment s > 0 -> slot off + s - 1)
+    uint32_t* last = nullptr;       // per (tile, sub-tile): segments its forward warp entered
+    uint2* jobs = nullptr;          // (tile, segment) jobs, longest first
+    uint32_t* n_jobs = nullptr;     // device count of jobs
+};
+
 void launch_composite(const Launch& L, const ViewDesc* views, int v0, int n_group_views, int n_tiles,
                       const uint2* ranges, const uint32_t* keys, const uint32_t* vals, const Record* records,
-                      const Params& P, float* out_rgb, float* out_depth, float* out_alpha, unsigned long long* work);
+                      const Params& P, float* out_rgb, float* out_depth, float* out_alpha, unsigned long long* work,
+                      const uint32_t* tile_order = nullptr, const Checkpoints& ck = Checkpoints{});
+
+// The (tile, segment) jobs of a group's lists, longest first, and each tile's first checkpoint
+// slot (one block; groups of at most kOrderMaxTiles tiles).
+void launch_segment_jobs(const Launch& L, const uint2* ranges, int n_tiles, const Checkpoints& ck);
+
+// The group's tiles in descending order of list length (the compositors' block -> tile map), for
+// groups of at most kOrderMaxTiles tiles: with more, the many waves of blocks balance the SMs
+// without it.
+constexpr int kOrderMaxTiles = 32768;
+// Warps per compositor block (forward and adjoint): each warp one 8x4 sub-tile of the block's
+// tile; a tile of tile_w x tile_h pixels spans tile_w * tile_h / (32 kCompWarps) blocks.
+constexpr int kCompWarps = 2;
+void launch_tile_order(const Launch& L, const uint2* ranges, int n_tiles, uint32_t* order);
 
 // Image randomisation of an RGB batch in place (the separate form of the compositor's
 // epilogue).  spans[V]: per view its first output pixel, its first quad in the view-by-view
@@ -539,7 +572,8 @@ void launch_composite_bwd(const Launch& L, const ViewDesc* views, int v0, int n_
                           const uint2* ranges, const uint32_t* keys, const uint32_t* vals, const Record* records,
                           const Params& P,
                           const float* out_rgb, const float* out_depth, const float* g_rgb, const float* g_depth,
-                          float* inst_grad, unsigned long long* n_red = nullptr);
+                          float* inst_grad, unsigned long long* n_red = nullptr, const uint32_t* tile_order = nullptr,
+                          const Checkpoints& ck = Checkpoints{}, uint32_t n_jobs_bound = 0);
 
 void launch_project_bwd(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_nodes, const ViewDesc* views,
                         const VNode* vnodes, int K, const float* node_poses, const InstInfo* info,

@@ -141,3 +141,28 @@ def test_gradient_buffers_made_once_give_the_fresh_gradients():
         _close(ref, got)
     assert ng is gb.node_grads
     r.close()
+
+
+@pytest.mark.parametrize("mode", ["batched", "graph"])
+def test_long_lists_replay_in_checkpointed_segments(mode):
+    """A dense view whose tile lists run to thousands of entries: the kept-lists adjoint replays
+    512-entry segments in parallel from the forward's checkpoints and must give the gradients of
+    the sequential replay (the default backward, which bins again)."""
+    from paper_2507_21981_gb300.render import DeviceScene, Renderer
+    sc = S.config4(seed=3, n_bg=120_000, n_obj=4_000, res=128, f=110.0)
+    ds = DeviceScene(sc, device="cuda:0")
+    ref_r = Renderer(mode="batched")
+    rgb, depth, _ = ref_r.render(ds)
+    st = ref_r.stats()
+    assert st["n_pairs"] / (128 * 128 / 256) > 2 * 512      # lists of several segments on average
+    ref, path = _grads(ref_r, ds, rgb, depth)
+    assert path == D.DGS_PATH_EAGER
+    r = Renderer(mode=mode, keep_lists=1)
+    for _ in range(2 if mode == "graph" else 1):
+        rgb2, depth2, _ = r.render(ds)
+    assert torch.equal(rgb, rgb2) and torch.equal(depth, depth2)
+    got, path = _grads(r, ds, rgb2, depth2)
+    assert path == D.DGS_PATH_KEPT_LISTS
+    _close(ref, got)
+    ref_r.close()
+    r.close()
