@@ -114,6 +114,7 @@ class Renderer:
         self.options = o
         self._aug = None
         self._lib = D.load()            # the library the context belongs to (see dgs.using)
+        self.tune_cached = False        # the last autotune took its shape from a TuneCache
         self.ctx = D.dgs_context_create(o)
 
     def set_options(self, **opts):
@@ -239,12 +240,24 @@ class Renderer:
         return o
 
     def autotune(self, ds: DeviceScene, candidates=None, reps: int = 3, out=None, with_alpha: bool = True,
-                 stream=None):
+                 stream=None, cache: "TuneCache | None" = None):
         """Times dgs_render of `ds` with each candidate tile shape ((w, h) pairs; None = the
         library's list), keeps the fastest on this context and renders once with it.
-        Returns (best (w, h), {(w, h): ms per render}, (rgb, depth, alpha))."""
+        Returns (best (w, h), {(w, h): ms per render}, (rgb, depth, alpha)).  With `cache`, a
+        batch whose class (GPU, resolutions, Gaussian density) the cache holds takes the cached
+        shape and renders once without timing; a new class is timed and stored.
+        self.tune_cached tells which happened."""
         rgb, depth, alpha = out if out is not None else self._outputs(ds, with_alpha)
         s = stream if stream is not None else torch.cuda.current_stream(ds.device)
+        self.tune_cached = False
+        if cache is not None:
+            key = TuneCache.key(ds, torch.cuda.get_device_name(ds.device))
+            hit = cache.get(key)
+            if hit is not None:
+                best, times = hit
+                self.set_options(tile_w=best[0], tile_h=best[1])
+                self.tune_cached = True
+                return best, times, self.render(ds, out=(rgb, depth, alpha), stream=s)
         rc, res = D.dgs_autotune(self.ctx, ds.nodes, ds.n_nodes, ds.env_node_ids, ds.n_envs, ds.max_nodes,
                                  ds.node_poses, ds.cams, ds.cams_per_env, ds.max_cams, rgb, depth, alpha, None,
                                  candidates, reps, s.cuda_stream)
@@ -253,6 +266,8 @@ class Renderer:
         times = {(res.tile_w[i], res.tile_h[i]): float(res.ms[i]) for i in range(res.n)}
         best = (res.tile_w[res.best], res.tile_h[res.best])
         self.options.tile_w, self.options.tile_h = best
+        if cache is not None:
+            cache.put(key, best, times)
         return best, times, (rgb, depth, alpha)
 
     def backward(self, ds: DeviceScene, out_rgb, out_depth, grad_rgb, grad_depth=None, want_poses: bool = True,
@@ -287,6 +302,53 @@ class Renderer:
 
     def workspace_bytes(self) -> int:
         return D.dgs_workspace_query(self.ctx)
+
+
+class TuneCache:
+    """Tile shapes found by Renderer.autotune, kept in a JSON file keyed by (GPU name,
+    resolution class, Gaussian density).  The resolution class is the sorted set of the batch's
+    view resolutions and its view count rounded to a power of two; the density is the Gaussians
+    present per view, rounded to a power of two.  A batch of a known class then starts with its
+    tile shape without timing the candidates again.  The file is rewritten whole (through a
+    temporary file and a rename) on every store."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    @staticmethod
+    def key(ds: DeviceScene, device_name: str) -> str:
+        def p2(x: float) -> int:
+            return 1 << max(0, int(round(np.log2(max(x, 1.0)))))
+        res = ",".join(f"{w}x{h}" for w, h in sorted(set(ds.view_res)))
+        per_view = ds.scene.instances() / max(ds.n_views, 1)
+        return f"{device_name}|res={res}|views~{p2(ds.n_views)}|gaussians_per_view~{p2(per_view)}"
+
+    def _load(self) -> dict:
+        import json
+        import os
+        if not os.path.exists(self.path):
+            return {}
+        with open(self.path) as f:
+            return json.load(f)
+
+    def get(self, key: str):
+        """(best (w, h), {(w, h): ms}) stored for `key`, or None."""
+        e = self._load().get(key)
+        if e is None:
+            return None
+        times = {tuple(int(v) for v in k.split("x")): float(ms) for k, ms in e["ms"].items()}
+        return (int(e["best"][0]), int(e["best"][1])), times
+
+    def put(self, key: str, best, times) -> None:
+        import json
+        import os
+        data = self._load()
+        data[key] = {"best": [int(best[0]), int(best[1])],
+                     "ms": {f"{int(w)}x{int(h)}": float(ms) for (w, h), ms in times.items()}}
+        tmp = f"{self.path}.tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(tmp, self.path)
 
 
 class GradBuffers:

@@ -179,3 +179,27 @@ def test_config3_full_size_graph_sampled_views():
         bad, rep = compare_view(rgb[sl].reshape(h, w, 3), depth[sl].reshape(h, w), ref, alpha[sl].reshape(h, w))
         assert bad == 0, (w, h, rep)
     assert len(picked) == 3
+
+
+def test_autotune_cache_reuses_the_shape_of_a_known_class(tmp_path):
+    from paper_2507_21981_gb300.render import DeviceScene, Renderer, TuneCache
+    cache = TuneCache(str(tmp_path / "tune.json"))
+    sc = S.config1(seed=2)
+    ds = DeviceScene(sc, device="cuda:0")
+    r = Renderer(mode="batched")
+    best, times, _ = r.autotune(ds, candidates=[(16, 16), (8, 8), (32, 8)], reps=1, cache=cache)
+    assert not r.tune_cached and best in times
+    # another scene of the same class (same resolution, Gaussians per view within a factor of 2)
+    ds2 = DeviceScene(S.config1(seed=3), device="cuda:0")
+    r2 = Renderer(mode="batched")
+    best2, times2, out = r2.autotune(ds2, reps=1, cache=cache)
+    assert r2.tune_cached and best2 == best and times2 == times
+    assert (r2.options.tile_w, r2.options.tile_h) == best
+    rgb, depth, alpha = (t.cpu().numpy() for t in out)
+    torch.cuda.synchronize()
+    r3 = Renderer(mode="batched", tile=best)
+    ref = [t.cpu().numpy() for t in r3.render(ds2)]
+    for a, b in zip((rgb, depth, alpha), ref):
+        assert np.array_equal(a, b)
+    for x in (r, r2, r3):
+        x.close()
