@@ -311,6 +311,7 @@ Params make_params(const dgs_options& o) {
     P.bg0 = o.bg[0]; P.bg1 = o.bg[1]; P.bg2 = o.bg[2];
     P.qbin = o.q_max * 1.001f + 1e-3f;
     P.p_min = kHalfLog2e * o.q_max;
+    P.log2_amin = o.alpha_min > 0.f ? std::log2(o.alpha_min) : -INFINITY;
     P.tile_w = o.tile_w; P.tile_h = o.tile_h;
     while ((1 << P.tile_sx) < o.tile_w) ++P.tile_sx;
     while ((1 << P.tile_sy) < o.tile_h) ++P.tile_sy;

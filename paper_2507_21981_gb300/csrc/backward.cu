@@ -160,11 +160,11 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_bwd(const ViewDes
                 float t;
                 // the forward pass's decisions: same staged products, same exponent
                 const float pe = pixel_exponent(kHalfLog2e * g1.x, g1.y, kHalfLog2e * g1.z, dx, dy, t);
-                if (pe >= P.p_min) {
+                if (pe >= reach_threshold(P, g0.z)) {
                     const float ex = fast_exp2(pe);
                     const float a_raw = g0.z * ex;
                     const float alpha = fminf(P.alpha_max, a_raw);
-                    if (alpha >= P.alpha_min) {
+                    {
                         const float Tn = fmaf(-alpha, T, T);   // T (1 - alpha), one rounding
                         if (Tn < P.t_min) {
                             done = true;

@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kCompWarps * 32, (COUNT || AUG || CK) ? 20 : 2
             const float4 a = r->r0, q = r->r1, col = r->r2;
             const int pos = __popc(m & lt);
             sr0[pos] = a; sr2[pos] = col;
-            sr1[pos] = make_float4(kHalfLog2e * q.x, q.y, kHalfLog2e * q.z, 0.f);
+            sr1[pos] = make_float4(kHalfLog2e * q.x, q.y, kHalfLog2e * q.z, reach_threshold(P, a.z));
         }
         __syncwarp();
         const int n = __popc(m);
@@ -234,10 +234,9 @@ __global__ void __launch_bounds__(kCompWarps * 32, (COUNT || AUG || CK) ? 20 : 2
             const float4 g0 = sr0[k], g1 = sr1[k];
             float t;
             const float pe = pixel_exponent(g1.x, g1.y, g1.z, fx - g0.x, fy - g0.y, t);
-            if (pe < P.p_min) continue;
-            if (COUNT) ++n_reach;
+            if (COUNT && pe >= P.p_min) ++n_reach;
+            if (!(pe >= g1.w)) continue;           // outside the ellipse, or alpha below alpha_min
             const float alpha = fminf(P.alpha_max, g0.z * fast_exp2(pe));
-            if (alpha < P.alpha_min) continue;
             const float Tn = fmaf(-alpha, T, T);   // T (1 - alpha), one rounding
             if (Tn < P.t_min) { done = true; break; }
             if (COUNT) ++n_comp;

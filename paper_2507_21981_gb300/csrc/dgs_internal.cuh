@@ -150,6 +150,7 @@ struct Params {
     uint32_t* err;        // device error word
     const uint32_t* gate; // emission is skipped when non-null and *gate != 0 (capacity overflow)
     float p_min;          // kHalfLog2e * q_max: exponents below it are outside the 3-sigma ellipse
+    float log2_amin;      // log2(alpha_min) (-inf for alpha_min = 0)
     uint32_t n_rec;       // records of the current view group (bound of its instance numbers)
     const uint32_t* inst_base_dev;  // emission: first record of the group read on the device (graph replay)
     // image randomisation of the RGB output (null aug = none): per-view records, overlay clip
@@ -250,6 +251,16 @@ __device__ __forceinline__ float fast_log2(float x) {
     float y;
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// Sec. III-A cutoffs of a record at a pixel, as one threshold on the exponent p (alpha =
+// min(alpha_max, o 2^p)): the pixel is skipped unless p >= max(p_min, log2(alpha_min) - log2 o),
+// i.e. unless it lies inside the 3-sigma ellipse and its alpha reaches alpha_min.  Taken in the
+// log domain, the alpha_min decision moves by about 8 units of 2^-24 relative in alpha (the
+// rounding of p and of the two logarithms), inside the FP32 band of that decision; the
+// compositor and its adjoint both use this function, so they decide alike.
+__device__ __forceinline__ float reach_threshold(const Params& P, float opacity) {
+    return fmaxf(P.p_min, P.log2_amin - fast_log2(opacity));
 }
 
 // Image randomisation of one pixel (Sec. IV): clamp to [0, 1], linear blend with the overlay
