@@ -37,10 +37,12 @@ BWD_OPS_PER_PAIR = 50
 # Projection of one visible instance: faithfully rounded camera-space centre (3 compensated dot
 # products, 105), guarded Jacobian and 2D covariance by Cauchy-Binet (75), conic, centre and
 # pixel box (20); spherical-harmonics colour of degree 3: basis (30), 48 FMA, direction (10).
-# The count and emit rates count only this per-visible work: the chunk and per-Gaussian culls
-# of the count pass and the tile-row runs of emission are left out, so their fractions are
-# lower bounds.
-PROJ_OPS, SH3_OPS = 200, 90
+# The count pass runs the conservative per-Gaussian cull and box bound (35: three FMA chains and
+# their error bounds, a reciprocal, two square roots, the box and its tiles) instead of the exact
+# projection.  The count and emit rates count only per-emitted-instance work: the chunk culls,
+# the culled instances' tests and the tile-row runs of emission are left out, so their
+# fractions are lower bounds.
+PROJ_OPS, SH3_OPS, CULL_OPS = 200, 90, 35
 # The projection adjoint moves per visible instance: 40 B of partials, 236 B of FP32 attributes
 # read, 236 B of attribute gradients accumulated and 8 B of identity.
 PROJECT_BWD_BYTES = 40 + 236 + 236 + 8
@@ -881,8 +883,8 @@ def main():
         "emit": {**alu(NV * (PROJ_OPS + SH3_OPS), per_step["emit"]),
                  "units": {"visible": NV, "ops_per_visible": PROJ_OPS + SH3_OPS,
                            "not_counted": "tile-row runs of the pair count"}},
-        "count": {**alu(NV * PROJ_OPS, per_step["count"]),
-                  "units": {"visible": NV, "ops_per_visible": PROJ_OPS,
+        "count": {**alu(NV * CULL_OPS, per_step["count"]),
+                  "units": {"visible": NV, "ops_per_visible": CULL_OPS,
                             "not_counted": "chunk and per-Gaussian culls",
                             "instances_considered": n_inst}},
         # the plain per-view form reads every attribute again for every view

@@ -150,7 +150,8 @@ typedef struct dgs_stats {
     int64_t n_views;
     int64_t n_pixels;
     int64_t n_instances;        /* (Gaussian, view) pairs considered */
-    int64_t n_visible;          /* instances that passed the cull */
+    int64_t n_visible;          /* instances emitted: those the count pass's conservative cull keeps (the
+                                   few that the exact projection then rejects carry no tile pairs) */
     int64_t n_pairs;            /* (instance, tile) pairs sorted */
     int32_t n_groups;           /* view groups (batched) or views (plain) */
     int32_t key_bits;           /* significant sort-key bits of the largest group */

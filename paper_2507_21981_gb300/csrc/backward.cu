@@ -270,6 +270,16 @@ __global__ void __launch_bounds__(128) k_project_bwd(const NodeDesc* __restrict_
         i = (int64_t)inf.gid - nodes[k].gbase;
         act = nodes[k].dtype == DT && in_bounds((uint64_t)i, (uint64_t)nodes[k].n, P.err, kSiteProjectBwdGaussian);
     }
+    if (act) {
+        // an instance that no pixel composited adds nothing -- and a dead record of the count
+        // pass's conservative cull (never composited) may have a degenerate projection whose
+        // recomputed Jacobian would turn its zero partials into NaN
+        const float* pg = ig + (size_t)r * G_N;
+        bool any = false;
+#pragma unroll
+        for (int e = 0; e < G_N; ++e) any |= pg[e] != 0.f;
+        act = any;
+    }
     float gRn[9], gtn[3];
 #pragma unroll
     for (int e = 0; e < 9; ++e) gRn[e] = 0.f;
@@ -458,7 +468,10 @@ __global__ void __launch_bounds__(128) k_project_bwd(const NodeDesc* __restrict_
     }
     // ---------------------------------------------------------------- pose gradient, reduced per warp
     if (!grad_poses) return;
-    const int lead = __shfl_sync(0xffffffffu, act ? vv : -1, 0);
+    // the (view, slot) of the first active lane; a warp whose active lanes all share it reduces
+    // its pose partials with one transpose-sum instead of 12 atomics per lane
+    const uint32_t am = __ballot_sync(0xffffffffu, act);
+    const int lead = am ? __shfl_sync(0xffffffffu, vv, __ffs(am) - 1) : -1;
     const bool same = __all_sync(0xffffffffu, !act || vv == lead);
     if (same && lead >= 0) {
         const ViewDesc& vd0 = views[lead / K];

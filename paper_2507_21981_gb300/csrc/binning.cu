@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(const ViewDesc* __res
         S.off[lane] = poff[item];
         S.end[lane] = poff[item + 1];
         S.run[lane] = 0;
-        nrows = (uint32_t)(ty1 - ty0 + 1);
+        nrows = (uint32_t)(ty1 - ty0 + 1);     // >= 1: walk_owner_of needs a unit per item
     }
     uint32_t incl = nrows;
 #pragma unroll
@@ -226,7 +226,9 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(const ViewDesc* __res
         if (jact) {
             a = S.a[o]; e = S.e[o]; bx = S.box[o];
             row = S.c[o].x + (int)(j - S.rexcl[o]);
-            nrun = tile_row_run(a.x, a.y, a.z, a.w, e, bx.x, bx.y, bx.z, bx.w, row, P, t0);
+            // an instance without pairs (no row reaches a pixel centre, or a dead record of the
+            // count pass's conservative cull, whose conic is all zero) writes none
+            if (S.end[o] > S.off[o]) nrun = tile_row_run(a.x, a.y, a.z, a.w, e, bx.x, bx.y, bx.z, bx.w, row, P, t0);
         }
         // the job's first position: the item's pairs of earlier batches, plus the runs of its
         // earlier jobs in this batch (an item's jobs are consecutive lanes)

@@ -197,7 +197,8 @@ __device__ __forceinline__ bool project(const Gauss& g, const VNode& vn, const V
     return true;
 }
 
-// Conservative screen-space cull: false only if project() would certainly return false.  The
+// Conservative screen-space cull and pair bound: 0 only if project() would certainly return
+// false; else at least the number of tiles of project()'s pixel box.  The
 // 2D covariance satisfies Sigma_xx <= |T0|^2 smax + lowpass with |T0|^2 = (fx/z)^2 (1 + xc^2)
 // for the orthonormal rows of camera_from_node, so the ellipse box is bounded by
 // sqrt(qbin ((fx/z)^2 (1 + xc^2) smax + lowpass)) (2 % + 1e-3 px of slack for rounding).  The
@@ -205,16 +206,18 @@ __device__ __forceinline__ bool project(const Gauss& g, const VNode& vn, const V
 // faithfully rounded centre of project() each coordinate differs by less than 6u S_i (three
 // roundings, the omitted trailing parts and the faithful rounding, u = 2^-24, S_i = sum of the
 // magnitudes of the row's terms), bounded here by e_i = 2^-20 S_i, which widens the near-plane
-// test and the box.
-__device__ __forceinline__ bool may_be_visible(const Gauss& g, const VNode& vn, const ViewDesc& vd, const Params& P) {
+// test and the box.  The box, widened to whole pixels and clamped to the image, contains
+// project()'s; a centre that may lie at the camera plane counts every tile of the view.
+__device__ __forceinline__ uint32_t conservative_tiles(const Gauss& g, const VNode& vn, const ViewDesc& vd,
+                                                       const Params& P) {
     const float* M = vn.M;
     const float ax = fabsf(g.mx), ay = fabsf(g.my), az = fabsf(g.mz);
     constexpr float k20 = 9.5367431640625e-07f;   // 2^-20
     const float z = fmaf(M[8], g.mx, fmaf(M[9], g.my, fmaf(M[10], g.mz, M[11])));
     const float ez = k20 * fmaf(fabsf(M[8]), ax, fmaf(fabsf(M[9]), ay, fmaf(fabsf(M[10]), az, fabsf(M[11]))));
-    if (!(z + ez > P.z_near)) return false;
+    if (!(z + ez > P.z_near)) return 0u;
     const float zl = z - ez;
-    if (!(zl > 0.f)) return true;                  // at the camera plane: let the exact projection decide
+    if (!(zl > 0.f)) return (uint32_t)(vd.tiles_x * vd.tiles_y);   // at the camera plane: any tile
     const float tx = fmaf(M[0], g.mx, fmaf(M[1], g.my, fmaf(M[2], g.mz, M[3])));
     const float ty = fmaf(M[4], g.mx, fmaf(M[5], g.my, fmaf(M[6], g.mz, M[7])));
     const float ex = k20 * fmaf(fabsf(M[0]), ax, fmaf(fabsf(M[1]), ay, fmaf(fabsf(M[2]), az, fabsf(M[3]))));
@@ -231,8 +234,11 @@ __device__ __forceinline__ bool may_be_visible(const Gauss& g, const VNode& vn, 
     const float hx = sqrtf(P.qbin * fmaf(fxz * fxz * fmaf(xc, xc, 1.f), s, P.lowpass)) + 1e-3f + dux;
     const float hy = sqrtf(P.qbin * fmaf(fyz * fyz * fmaf(yc, yc, 1.f), s, P.lowpass)) + 1e-3f + duy;
     const float u = fmaf(vd.fx, xr, vd.cx), v = fmaf(vd.fy, yr, vd.cy);
-    return u + hx - 0.5f >= 0.f && v + hy - 0.5f >= 0.f && u - hx - 0.5f <= (float)(vd.W - 1) &&
-           v - hy - 0.5f <= (float)(vd.H - 1);
+    const float lx = u - hx - 0.5f, rx = u + hx - 0.5f, ly = v - hy - 0.5f, ry = v + hy - 0.5f;
+    if (!(rx >= 0.f && ry >= 0.f && lx <= (float)(vd.W - 1) && ly <= (float)(vd.H - 1))) return 0u;
+    const int x0 = (int)fmaxf(floorf(lx), 0.f), x1 = (int)fminf(ceilf(rx), (float)(vd.W - 1));
+    const int y0 = (int)fmaxf(floorf(ly), 0.f), y1 = (int)fminf(ceilf(ry), (float)(vd.H - 1));
+    return (uint32_t)(((x1 >> P.tile_sx) - (x0 >> P.tile_sx) + 1) * ((y1 >> P.tile_sy) - (y0 >> P.tile_sy) + 1));
 }
 
 // Bound of a 32-Gaussian chunk in the node frame: a ball of radius r around c holding every
@@ -514,15 +520,21 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
             for (int q = 0; q < nvb; ++q) surv &= surv - 1u;   // drop the views taken
             __syncwarp();
             if constexpr (!EMIT) {
+                // count pass: the conservative cull decides which instances are emitted and bounds
+                // their tile pairs; emission projects them exactly (and writes a dead record for
+                // the few, about 2 % on the benchmark batch, that the exact projection rejects)
                 for (int j = 0; j < nvb; ++j) {
                     const int vvj = WV.vv[j];
-                    const uint32_t m = __ballot_sync(full, valid && may_be_visible(gme, vnodes[vvj], views[vvj / K], P));
-                    if (lane == 0) WV.mask[j] = m;
+                    const uint32_t a = valid ? conservative_tiles(gme, vnodes[vvj], views[vvj / K], P) : 0u;
+                    const uint32_t m = __ballot_sync(full, a != 0u);
+                    const uint32_t h = __reduce_add_sync(full, a);
+                    if (lane == 0) { WV.mask[j] = m; WV.vis[j] = m; WV.hits[j] = h; }
                 }
             }
             __syncwarp();
             uint32_t n_items = 0;
-            for (int j = 0; j < nvb; ++j) n_items += __popc(WV.mask[j]);
+            if constexpr (EMIT)
+                for (int j = 0; j < nvb; ++j) n_items += __popc(WV.mask[j]);
             // 2. project the survivors 32 at a time
             for (uint32_t it = 0; it < n_items; it += 32) {
                 const uint32_t idx = it + (uint32_t)lane;
@@ -537,21 +549,22 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
                     get_geo(W.geo + g * kGeoStride, gg);
                     vis = project(gg, vnodes[vvj], views[vvj / K], P, s);
                 }
-                const uint32_t area = vis ? (uint32_t)((s.tx1 - s.tx0 + 1) * (s.ty1 - s.ty0 + 1)) : 0u;
-                if constexpr (!EMIT) {
-                    // per-view totals of this flush: items are view-sorted, reduce each view's run
-                    const uint32_t peers = __match_any_sync(0xffffffffu, act ? j : -1);
-                    const uint32_t h = __reduce_add_sync(peers, area);
-                    const uint32_t bits = __reduce_or_sync(peers, vis ? (1u << g) : 0u);
-                    if (act && (peers & ((1u << lane) - 1u)) == 0) { WV.hits[j] += h; WV.vis[j] |= bits; }
-                } else {
+                if constexpr (EMIT) {
                     uint32_t r = 0;
-                    if (act && !vis) atomicOr(P.err, kErrMismatch);
-                    if (vis) r = WV.ibase[j] + __popc(WV.mask[j] & ((1u << g) - 1u));
+                    if (act) r = WV.ibase[j] + __popc(WV.mask[j] & ((1u << g) - 1u));
+                    const int64_t i = (int64_t)c * kChunk + g;
+                    if (act && !vis && in_bounds(r, P.n_rec, P.err, kSiteEmitRecord)) {
+                        // kept by the count pass's conservative cull, rejected by the exact
+                        // projection: a dead record, last in depth order, with no tile pairs
+                        out.rec[r] = Record{};
+                        out.info[r] = InstInfo{(uint32_t)(nd.gbase + i), (uint32_t)vvj};
+                        out.dkey[r] = (1u << kZBits) - 1u;
+                        out.ival[r] = r;
+                        out.ntile[r] = 0u;
+                    }
                     if (vis && in_bounds(r, P.n_rec, P.err, kSiteEmitRecord)) {
                         float rgb[3];
                         sh_colour(nd.deg, shc + g * kShStride, gg, vnodes[vvj], rgb);
-                        const int64_t i = (int64_t)c * kChunk + g;
                         const float op = 1.f / (1.f + __expf(-__ldg(nd.opac + i)));
                         Record R;
                         R.r0 = make_float4(s.u, s.v, op, s.z);
@@ -570,7 +583,6 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
                         }
                         out.ntile[r] = npairs;
                     }
-                    (void)area;
                 }
                 __syncwarp();
             }
