@@ -90,3 +90,38 @@ def test_binning_checker_reports_a_corrupted_list():
     torch.cuda.synchronize()
     _check_oracle(sc, ds, out)
     r.close()
+
+
+@pytest.mark.parametrize("mode", ["batched", "graph"])
+@pytest.mark.parametrize("bad", ["nan", "scaled"])
+def test_corrupted_node_pose_is_reported_then_the_context_renders_again(mode, bad):
+    """Fault injection on the host: one node pose of the batch is made non-finite or non-rigid
+    (rotation scaled by 2) in the caller's pose array.  The device-side pose check must end the
+    render and the backward with DGS_ERR_INVALID_ARG, and the same context must render the
+    restored poses exactly as before."""
+    from paper_2507_21981_gb300.render import DeviceScene, Renderer
+    sc = S.config2(seed=4, n_envs=3, n_bg=30_000, n_obj=1_000, width=160, height=120, f=125.0)
+    ds = DeviceScene(sc, device="cuda:0")
+    r = Renderer(mode=mode)
+    ref = [t.cpu().numpy() for t in r.render(ds)]
+    if mode == "graph":
+        ref = [t.cpu().numpy() for t in r.render(ds)]      # a replay of the captured sequence
+    good = ds.node_poses.clone()
+    if bad == "nan":
+        ds.node_poses[1, 1, 3] = float("nan")
+    else:
+        ds.node_poses[1, 1, :] = ds.node_poses[1, 1, :] * torch.tensor([2, 2, 2, 1] * 3, dtype=torch.float32,
+                                                                         device=ds.device)
+    with pytest.raises(D.DgsError) as ei:
+        r.render(ds)
+    assert ei.value.code == D.DGS_ERR_INVALID_ARG and "not finite or not rigid" in str(ei.value)
+    rgb, depth = (torch.as_tensor(x, device=ds.device) for x in ref[:2])
+    with pytest.raises(D.DgsError) as ei:
+        r.backward(ds, rgb, depth, torch.ones_like(rgb), torch.ones_like(depth))
+    assert ei.value.code == D.DGS_ERR_INVALID_ARG
+    ds.node_poses.copy_(good)
+    out = [t.cpu().numpy() for t in r.render(ds)]
+    torch.cuda.synchronize()
+    for a, b in zip(ref, out):
+        assert np.array_equal(a, b)
+    r.close()
