@@ -54,11 +54,11 @@ struct GraphKey {
 // tkeys/tvals: (tile, instance) pairs (tile sort, ping-pong); ranges: per tile.
 struct ListBufs {
     DevBuf records, info, dkey0, ival0, dkey1, ival1, ntile, poff, tparts, tkeys0, tvals0, tkeys1, tvals1, hist,
-        status, counters, ranges, torder, ck_st, ck_off, ck_last, ck_jobs, ck_njobs;
-    static constexpr int kCount = 23;
+        status, counters, ranges, torder, ck_st, ck_off, ck_last, ck_jobs, ck_njobs, vig;
+    static constexpr int kCount = 24;
     DevBuf* all[kCount] = {&records, &info, &dkey0, &ival0, &dkey1, &ival1, &ntile, &poff, &tparts, &tkeys0, &tvals0,
                            &tkeys1, &tvals1, &hist, &status, &counters, &ranges, &torder, &ck_st, &ck_off, &ck_last,
-                           &ck_jobs, &ck_njobs};
+                           &ck_jobs, &ck_njobs, &vig};
     ListBufs() = default;
     ListBufs(const ListBufs&) = delete;
     ListBufs& operator=(const ListBufs&) = delete;
@@ -624,6 +624,11 @@ int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* e
     }
     B.K = K; B.n_nodes = n_nodes; B.dtype_mask = dtype_mask; B.chunk_total = chunk_total;
     B.tiles_total = tiles_total; B.T = T; B.batched = o.mode != DGS_MODE_PLAIN;
+    // tile keys hold the view in the group above the tile's index in its view: its bits leave
+    // the all-ones index (a dead pair's) above every real tile
+    int64_t max_view_tiles = 1;
+    for (const ViewDesc& vd : views) max_view_tiles = std::max<int64_t>(max_view_tiles, (int64_t)vd.tiles_x * vd.tiles_y);
+    const int tbits = bits_for((uint64_t)max_view_tiles + 1);
     B.views = std::move(views); B.view_tab = std::move(view_tab);
     B.d_nodes = d_nodes; B.d_views = d_views; B.d_nv = d_nv; B.d_nvoff = d_nvoff; B.d_pmap = d_pmap;
     B.d_vnodes = d_vnodes; B.d_slot = d_slot; B.d_vtab = d_vtab; B.d_viewtab = d_viewtab;
@@ -631,6 +636,7 @@ int stage(dgs_ctx* ctx, const dgs_node* nodes, int32_t n_nodes, const int32_t* e
     B.d_inst_off = static_cast<uint32_t*>(ctx->inst_off.p);
     B.d_pair_off = static_cast<uint64_t*>(ctx->pair_off.p);
     B.d_err = d_err; B.P = P;
+    B.P.tbits = tbits;
     B.d_grads = reinterpret_cast<const dgs_node_grads*>(dm + o_grads);
     B.node_poses = node_poses;
     B.n_parts = n_parts;
@@ -690,7 +696,8 @@ void list_bytes(uint64_t n_inst, uint64_t n_pairs, int64_t n_tiles, int tile_px,
         u * n_pairs, u * n_pairs, u * n_pairs, u * n_pairs, u * 4 * 1024,
         u * sort_status_words((uint32_t)std::max(n_inst, n_pairs)), u * 8,
         sizeof(uint2) * nt, n_tiles <= kOrderMaxTiles ? u * nt : 0,
-        ck, ck ? u * nt : 0, ck ? u * nt * n_sub : 0, ck ? sizeof(uint2) * (nt + ck_slots(n_pairs)) : 0, ck ? u : 0};
+        ck, ck ? u * nt : 0, ck ? u * nt * n_sub : 0, ck ? sizeof(uint2) * (nt + ck_slots(n_pairs)) : 0, ck ? u : 0,
+        u * n_inst};
     for (int i = 0; i < ListBufs::kCount; ++i) out[i] = b[i];
 }
 
@@ -740,7 +747,10 @@ int readback_groups(dgs_ctx* ctx, Batch& B, cudaStream_t stream, Timer& tm, size
         for (int v = 0; v < V; ++v) groups.push_back({v, v + 1});
     } else {
         int v0 = 0;
-        const int cap_views = o.views_per_group > 0 ? o.views_per_group : V;
+        // a group's views must fit above the tile bits of its keys (all-ones view: dead pairs)
+        if (B.P.tbits > kTileBits) return fail(ctx, DGS_ERR_CAPACITY, "one view has 2^24 tiles or more");
+        const int key_views = (int)std::min<int64_t>((1ll << (kTileBits - B.P.tbits)) - 1, V);
+        const int cap_views = std::min(o.views_per_group > 0 ? o.views_per_group : V, std::max(key_views, 1));
         // automatic grouping of a large batch: two groups of about half the tile pairs each, so
         // that the second group's binning overlaps the first group's compositing
         int split_at = -1;
@@ -774,8 +784,8 @@ int readback_groups(dgs_ctx* ctx, Batch& B, cudaStream_t stream, Timer& tm, size
         if (pair_at[g.second] - pair_at[g.first] > kMaxPairs)
             return fail(ctx, DGS_ERR_CAPACITY, "view group exceeds 2^30 tile pairs");
     }
-    max_bits = bits_for((uint64_t)max_tiles + 1);
-    if (max_bits > kTileBits) return fail(ctx, DGS_ERR_CAPACITY, "more than 2^24 - 1 tiles in a view group");
+    max_bits = B.P.tbits;                 // the tile sort radixes the tile-in-view bits only
+    if (max_tiles > kMaxGroupTiles) return fail(ctx, DGS_ERR_CAPACITY, "more than 2^24 - 1 tiles in a view group");
     ctx->stats.n_groups = (int32_t)groups.size();
     ctx->stats.key_bits = max_bits;
     if (need) {   // a workspace query: the bytes of the lists, nothing allocated
@@ -827,7 +837,8 @@ void enqueue_lists(dgs_ctx* ctx, ListBufs& lb, const Batch& B, const Launch& L, 
     tm.begin(DGS_K_EMIT);
     launch_emit(L, B.dtype_mask, B.d_nodes, B.n_nodes, B.d_views, B.d_vnodes, K, B.d_nv, B.d_nvoff, (int)B.chunk_total,
                 P, v0, v1, B.batched, B.d_pmap + (size_t)v0 * (2 * K + 1), B.view_tab[v0 + 1] - B.view_tab[v0],
-                B.d_counts, B.d_inst_off, inst_base, rec, info, u32(lb.dkey0), u32(lb.ival0), u32(lb.ntile));
+                B.d_counts, B.d_inst_off, inst_base, rec, info, u32(lb.dkey0), u32(lb.ival0), u32(lb.ntile),
+                u32(lb.vig));
     tm.end();
     tm.begin(DGS_K_SORT);
     uint32_t *dk = nullptr, *order = nullptr;
@@ -836,18 +847,21 @@ void enqueue_lists(dgs_ctx* ctx, ListBufs& lb, const Batch& B, const Launch& L, 
     SortCtl depth_ctl = ctl, tile_ctl = ctl;
     if (ctx->opt.test_fault == 1) depth_ctl.mute_part = 1;
     tile_ctl.runs = true;   // an instance's pairs are consecutive tiles of one view
+    // instances by depth, then by view (most significant, through the values): each view's
+    // instances in depth order, so that every instance's pairs come out view by view
     launch_sort(L, u32(lb.dkey0), u32(lb.ival0), u32(lb.dkey1), u32(lb.ival1), n_inst, kZBits, u32(lb.hist),
-                u32(lb.status), u32(lb.counters), B.d_err, &dk, &order, d_inst, depth_ctl);
+                u32(lb.status), u32(lb.counters), B.d_err, &dk, &order, d_inst, depth_ctl, u32(lb.vig),
+                bits_for((uint64_t)(v1 - v0)));
     launch_tile_scan(L, order, u32(lb.ntile), n_inst, d_inst, u32(lb.poff), u32(lb.tparts), n_bound, d_pairs, B.d_err);
     launch_pairs(L, B.d_views, K, order, u32(lb.poff), rec, info, n_inst, d_inst, P, u32(lb.tkeys0),
                  u32(lb.tvals0), n_bound);
     uint32_t *tk = nullptr, *tv = nullptr;
-    launch_sort(L, u32(lb.tkeys0), u32(lb.tvals0), u32(lb.tkeys1), u32(lb.tvals1), n_bound,
-                bits_for((uint64_t)n_tiles + 1), u32(lb.hist), u32(lb.status), u32(lb.counters), B.d_err, &tk,
-                &tv, d_pairs, tile_ctl);
+    // pairs by tile in view only: stability keeps them view by view within each tile index
+    launch_sort(L, u32(lb.tkeys0), u32(lb.tvals0), u32(lb.tkeys1), u32(lb.tvals1), n_bound, P.tbits, u32(lb.hist),
+                u32(lb.status), u32(lb.counters), B.d_err, &tk, &tv, d_pairs, tile_ctl);
     tm.end();
     tm.begin(DGS_K_RANGES);
-    launch_ranges(L, tk, n_bound, static_cast<uint2*>(lb.ranges.p), n_tiles, d_pairs);
+    launch_ranges(L, tk, n_bound, static_cast<uint2*>(lb.ranges.p), n_tiles, d_pairs, B.d_views, v1 - v0, P);
     *tile_order = nullptr;
     if (n_tiles <= kOrderMaxTiles && lb.torder.bytes >= sizeof(uint32_t) * (size_t)n_tiles) {
         launch_tile_order(L, static_cast<uint2*>(lb.ranges.p), n_tiles, static_cast<uint32_t*>(lb.torder.p));
@@ -942,6 +956,7 @@ void build_group_lists(dgs_ctx* ctx, const Batch& B, int g, ListBufs& lb, cudaSt
     G.n_tiles = (int)((v1 < V ? B.views[v1].tile_base : B.tiles_total) - tile0);
     G.P = B.P;
     G.P.tile0 = tile0;
+    G.P.view0 = (uint32_t)v0;
     G.P.n_rec = G.n_inst;
     G.lb = &lb;
     enqueue_lists(ctx, lb, B, L, tm, v0, v1, G.n_tiles, (uint32_t)B.inst_at[v0], G.n_inst, G.n_bound, nullptr,
@@ -988,12 +1003,24 @@ int check_lists(dgs_ctx* ctx, const Batch& B, int g, const GroupLists& G, cudaSt
               std::to_string(i);
         return false;
     };
+    // a key names (view in the group, tile in that view): sorted by tile in view, then view
+    const int tb = G.P.tbits, nv = G.v1 - G.v0;
+    const int64_t tile0 = B.views[G.v0].tile_base;
+    const uint32_t tmask = (1u << tb) - 1u;
+    auto group_tile = [&](uint32_t key) -> int64_t {   // tile in the group, -1 if none
+        const uint32_t f = key & kTileMask, vg = f >> tb, ti = f & tmask;
+        if (vg >= (uint32_t)nv) return -1;
+        const ViewDesc& vd = B.views[G.v0 + vg];
+        if (ti >= (uint32_t)(vd.tiles_x * vd.tiles_y)) return -1;
+        return vd.tile_base - tile0 + ti;
+    };
+    auto order_key = [&](uint32_t key) { return ((uint64_t)(key & tmask) << 32) | ((key & kTileMask) >> tb); };
     auto check = [&]() {
         uint64_t covered = 0;
         for (uint32_t i = 0; i < n; ++i) {
-            const uint32_t t = keys[i] & kTileMask, m = keys[i] >> kTileBits;
-            if (t >= (uint32_t)G.n_tiles) return bad("tile beyond the group", i);
-            if (i && t < (keys[i - 1] & kTileMask)) return bad("tiles not in order", i);
+            const uint32_t m = keys[i] >> kTileBits;
+            if (group_tile(keys[i]) < 0) return bad("tile beyond the group", i);
+            if (i && order_key(keys[i]) < order_key(keys[i - 1])) return bad("tiles not in order", i);
             // an empty mask is valid: the ellipse meets the tile's rectangle of pixel centres only
             // between two rows or columns of them, so no warp stages the pair
             if (m >= (1u << n_sub)) return bad("sub-tile mask", i);
@@ -1003,10 +1030,10 @@ int check_lists(dgs_ctx* ctx, const Batch& B, int g, const GroupLists& G, cudaSt
             const uint2 r = ranges[t];
             if (r.x == r.y) continue;
             if (r.x > r.y || r.y > n) return bad("range of tile " + std::to_string(t), r.x);
-            if ((r.x > 0 && (keys[r.x - 1] & kTileMask) == (uint32_t)t) || (r.y < n && (keys[r.y] & kTileMask) == (uint32_t)t))
+            if ((r.x > 0 && group_tile(keys[r.x - 1]) == t) || (r.y < n && group_tile(keys[r.y]) == t))
                 return bad("range of tile " + std::to_string(t) + " not maximal", r.x);
             for (uint32_t i = r.x; i < r.y; ++i) {
-                if ((keys[i] & kTileMask) != (uint32_t)t) return bad("range of tile " + std::to_string(t), i);
+                if (group_tile(keys[i]) != t) return bad("range of tile " + std::to_string(t), i);
                 if (i > r.x) {
                     const float z0 = rec[vals[i - 1]].r0.w, z1 = rec[vals[i]].r0.w;
                     if (z1 < z0 || (z1 == z0 && vals[i] <= vals[i - 1])) return bad("depth order in a tile", i);
@@ -1205,6 +1232,7 @@ int enqueue_graph_body(dgs_ctx* ctx, const Batch& B, const Launch& L, float* out
         P.gate = sizes + 2;
         P.inst_base_dev = sizes + 8 * g + 4;
         P.n_rec = (uint32_t)ctx->cap_inst[g];
+        P.view0 = (uint32_t)v0;
         ListBufs& lb = ctx->lists[g];
         const uint32_t *keys = nullptr, *vals = nullptr, *order = nullptr;
         Checkpoints ck{};
@@ -1244,8 +1272,8 @@ int capture_graph(dgs_ctx* ctx, const Batch& B, float* out_rgb, float* out_depth
         const int v0 = B.groups[g].first, v1 = B.groups[g].second;
         const uint64_t need_inst = B.inst_at[v1] - B.inst_at[v0], need_pairs = B.pair_at[v1] - B.pair_at[v0];
         const int64_t n_tiles = (v1 < B.V ? B.views[v1].tile_base : B.tiles_total) - B.views[v0].tile_base;
-        bits = std::max(bits, bits_for((uint64_t)std::max<int64_t>(n_tiles, 1) + 1));
-        if (need_pairs > kMaxPairs || bits > kTileBits || need_inst >= (1ull << 31)) return DGS_OK;
+        bits = B.P.tbits;
+        if (need_pairs > kMaxPairs || n_tiles > kMaxGroupTiles || need_inst >= (1ull << 31)) return DGS_OK;
         const uint64_t ci = need_inst + need_inst / 4 + 1024;
         const uint64_t cp = std::min<uint64_t>(kMaxPairs, need_pairs + need_pairs / 4 + 4096);
         ctx->cap_inst[g] = same_split ? std::max(ctx->cap_inst[g], ci) : ci;

@@ -193,11 +193,13 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(const ViewDesc* __res
         const uint32_t bx = __float_as_uint(r1.w), by = __float_as_uint(R.r2.w);
         const int x0 = (int)(bx & 0xFFFFu), x1 = (int)(bx >> 16), y0 = (int)(by & 0xFFFFu), y1 = (int)(by >> 16);
         const int ty0 = y0 >> P.tile_sy, ty1 = y1 >> P.tile_sy;
-        const ViewDesc& vd = views[info[r].view / (uint32_t)K];
+        const uint32_t view = info[r].view / (uint32_t)K;
+        const ViewDesc& vd = views[view];
         S.a[lane] = make_float4(r0.x, r0.y, r1.y, r1.z);
         S.e[lane] = ellipse_extent(r1.x, r1.y, r1.z, P.qbin);
         S.box[lane] = make_int4(x0, x1, y0, y1);
-        S.c[lane] = make_int4(ty0, vd.tile_base - P.tile0, vd.tiles_x, (int)r);
+        // tile keys: the view in the group above the tile's index in its view
+        S.c[lane] = make_int4(ty0, (int)((view - P.view0) << P.tbits), vd.tiles_x, (int)r);
         S.off[lane] = poff[item];
         S.end[lane] = poff[item + 1];
         S.run[lane] = 0;

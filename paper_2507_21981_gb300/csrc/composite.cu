@@ -13,9 +13,11 @@ namespace dgs {
 namespace {
 
 // Thread = 4 consecutive sorted keys (one 16-byte load); a run starts where the key's tile
-// differs from the one before and ends where it differs from the one after.
+// differs from the one before and ends where it differs from the one after.  A key names
+// (view in group, tile in view); its tile in the group is the view's first tile + tile in view.
 __global__ void k_ranges(const uint32_t* __restrict__ keys, uint32_t n, const uint32_t* __restrict__ d_n,
-                         uint2* __restrict__ ranges, int n_tiles) {
+                         uint2* __restrict__ ranges, int n_tiles, const ViewDesc* __restrict__ views, int v0, int nv,
+                         int tile0, int tbits) {
     const uint32_t i4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4u;
     if (d_n) n = min(n, *d_n);
     if (i4 >= n) return;
@@ -36,9 +38,12 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, uint32_t n, const ui
         const uint32_t i = i4 + j;
         if (i >= n) break;
         const uint32_t t = k[1 + j];
-        if (t >= (uint32_t)n_tiles) continue;       // dead pairs sort past every real tile
-        if (i == 0 || k[j] != t) ranges[t].x = i;
-        if (i + 1 == n || k[2 + j] != t) ranges[t].y = i + 1;
+        const uint32_t vg = t >> tbits;
+        if (vg >= (uint32_t)nv) continue;           // dead pairs sort past every real tile
+        const uint32_t gt = (uint32_t)(views[v0 + vg].tile_base - tile0) + (t & ((1u << tbits) - 1u));
+        if (gt >= (uint32_t)n_tiles) continue;      // (only keys of a sort that gave up waiting)
+        if (i == 0 || k[j] != t) ranges[gt].x = i;
+        if (i + 1 == n || k[2 + j] != t) ranges[gt].y = i + 1;
     }
 }
 
@@ -273,11 +278,12 @@ __global__ void __launch_bounds__(kCompWarps * 32, (COUNT || AUG || CK) ? 20 : 2
 }  // namespace
 
 void launch_ranges(const Launch& L, const uint32_t* keys, uint32_t n, uint2* ranges, int n_tiles,
-                   const uint32_t* d_n) {
+                   const uint32_t* d_n, const ViewDesc* views, int nv, const Params& P) {
     cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, L.stream);
     if (n == 0) return;
     const uint32_t threads = (n + 3) / 4;
-    k_ranges<<<(threads + 255) / 256, 256, 0, L.stream>>>(keys, n, d_n, ranges, n_tiles);
+    k_ranges<<<(threads + 255) / 256, 256, 0, L.stream>>>(keys, n, d_n, ranges, n_tiles, views, (int)P.view0, nv,
+                                                          P.tile0, P.tbits);
     ++*L.launches;
 }
 

@@ -18,9 +18,12 @@ constexpr int kWarp = 32;
 constexpr int kChunk = 32;           // Gaussians per chunk: one warp projects one chunk
 constexpr int kZBits = 28;           // bits of the depth field of a sort key
 constexpr uint32_t kMaxPairs = (1u << 30) - 1;   // per view group (30-bit scan counters)
-// Tile keys of the (tile, instance) pairs: bits 0..23 the tile within the view group, bits
-// 24..31 the mask of the tile's 8x4-pixel sub-tiles that the instance's ellipse reaches (bit
-// s = sub-tile (s mod (tile_w/8), s div (tile_w/8))).  The tile sort radixes bits 0..23 only.
+// Tile keys of the (tile, instance) pairs: bits 0..23 the view within the view group above the
+// tile's index within its view (Params::tbits bits), bits 24..31 the mask of the tile's
+// 8x4-pixel sub-tiles that the instance's ellipse reaches (bit s = sub-tile (s mod (tile_w/8),
+// s div (tile_w/8))).  The instances are sorted by view, then depth, so each instance's pairs
+// come out view by view; the tile sort then radixes the tbits bits only, and a tile's run is
+// in depth order.
 constexpr int kTileBits = 24;
 constexpr uint32_t kTileMask = (1u << kTileBits) - 1u;
 constexpr int64_t kMaxGroupTiles = (1ll << kTileBits) - 1;   // a view group's tiles (the dead key sorts last)
@@ -152,6 +155,8 @@ struct Params {
     float p_min;          // kHalfLog2e * q_max: exponents below it are outside the 3-sigma ellipse
     float log2_amin;      // log2(alpha_min) (-inf for alpha_min = 0)
     uint32_t n_rec;       // records of the current view group (bound of its instance numbers)
+    uint32_t view0;       // first view of the current view group
+    int32_t tbits;        // bits of a tile within its view (tile keys: view in group << tbits | tile)
     const uint32_t* inst_base_dev;  // emission: first record of the group read on the device (graph replay)
     // image randomisation of the RGB output (null aug = none): per-view records, overlay clip
     const dgs_augment* aug;
@@ -415,7 +420,7 @@ void launch_emit(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_n
                  const VNode* vnodes, int K, const NodeView* node_views, const int32_t* node_view_off,
                  int n_chunks_total, const Params& P, int v0, int v1, bool batched, const int32_t* view_chunk_nodes,
                  int64_t view_chunks, const uint2* counts, const uint32_t* inst_off, uint32_t inst_base,
-                 Record* records, InstInfo* info, uint32_t* dkey, uint32_t* ival, uint32_t* ntile);
+                 Record* records, InstInfo* info, uint32_t* dkey, uint32_t* ival, uint32_t* ntile, uint32_t* vig);
 
 // Bounded waits of the sort: the look-back spin limit, and a test of it (mute_part: the
 // partition of the first digit pass that publishes no status; ~0 = none).
@@ -428,10 +433,13 @@ struct SortCtl {
 // Stable LSD radix sort of (key, value) on the low key_bits bits.  With d_n non-null the
 // number of pairs is read on the device as min(*d_n, n), and n is the capacity the launches
 // are sized for.  *keys_out / *vals_out receive the buffers holding the result.  A look-back
-// wait that runs out sets kErrTimeout in err (the output is then invalid).
+// wait that runs out sets kErrTimeout in err (the output is then invalid).  With ind, the
+// values 0..n-1 are then sorted stably by ind[value] on its low ind_bits bits, as a more
+// significant key (the output keys are then those ind values).
 void launch_sort(const Launch& L, uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                  uint32_t n, int key_bits, uint32_t* hist, uint32_t* status, uint32_t* counters, uint32_t* err,
-                 uint32_t** keys_out, uint32_t** vals_out, const uint32_t* d_n = nullptr, SortCtl ctl = SortCtl{});
+                 uint32_t** keys_out, uint32_t** vals_out, const uint32_t* d_n = nullptr, SortCtl ctl = SortCtl{},
+                 const uint32_t* ind = nullptr, int ind_bits = 0);
 
 // Sets the sort kernels' launch attributes; call before a stream capture that contains a sort.
 void sort_prepare();
@@ -472,8 +480,11 @@ void launch_pairs(const Launch& L, const ViewDesc* views, int K, const uint32_t*
 
 // K4: [start, end) of every tile's run in the tile-sorted keys (d_n: device pair count); the
 // tile is the key's low kTileBits bits.
+// K4: ranges[tile of the group] = [first, last) entry of its run.  Keys are view in group <<
+// P.tbits | tile in its view (bits 0..23); a key whose view is not below nv (dead pairs) has no
+// tile.
 void launch_ranges(const Launch& L, const uint32_t* keys, uint32_t n, uint2* ranges, int n_tiles,
-                   const uint32_t* d_n = nullptr);
+                   const uint32_t* d_n, const ViewDesc* views, int nv, const Params& P);
 
 // K5: keys/vals are the tile-sorted pairs (each key's sub-tile mask selects the warps that
 // stage the instance).

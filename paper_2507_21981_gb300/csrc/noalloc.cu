@@ -171,33 +171,41 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
     uint32_t* d_dk1 = cv.take<uint32_t>(ni);
     uint32_t* d_iv1 = cv.take<uint32_t>(ni);
     uint32_t* d_ntile = cv.take<uint32_t>(ni);
+    uint32_t* d_vig = cv.take<uint32_t>(ni);
     uint32_t* d_poff = cv.take<uint32_t>(ni + 1);
     uint32_t* d_tparts = cv.take<uint32_t>(tile_scan_parts((uint32_t)ni));
     uint32_t* d_k0 = cv.take<uint32_t>(np);
     uint32_t* d_v0 = cv.take<uint32_t>(np);
     uint32_t* d_k1 = cv.take<uint32_t>(np);
     uint32_t* d_v1 = cv.take<uint32_t>(np);
-    uint32_t* d_hist = cv.take<uint32_t>(4 * 1024);
+    uint32_t* d_hist = cv.take<uint32_t>(8 * 256);
     uint32_t* d_cnt = cv.take<uint32_t>(8);
     uint32_t* d_total = cv.take<uint32_t>(1);
     uint32_t* d_status = cv.take<uint32_t>(sort_status_words((uint32_t)std::max(ni, np)));
     uint2* d_ranges = cv.take<uint2>((size_t)tiles_total);
     if (!cv.ok) return DGS_ERR_CAPACITY;
-    const int tbits = bits_for_tiles((uint64_t)tiles_total + 1);
-    if (tbits > kTileBits) return DGS_ERR_CAPACITY;
+    // tile keys: view << tbits | tile in view, as in dgs_render with one view group
+    int64_t max_view_tiles = 1;
+    for (const ViewDesc& vd : views) max_view_tiles = std::max<int64_t>(max_view_tiles, (int64_t)vd.tiles_x * vd.tiles_y);
+    const int tbits = bits_for_tiles((uint64_t)max_view_tiles + 1);
+    if (tbits > kTileBits || tiles_total > kMaxGroupTiles || (int64_t)V >= (1ll << (kTileBits - tbits)))
+        return DGS_ERR_CAPACITY;
     // depth-ordered tile lists, as in dgs_render with one view group
     P.n_rec = (uint32_t)n_vis;
+    P.view0 = 0;
+    P.tbits = tbits;
     launch_emit(L, dtype_mask, d_nodes, n_nodes, d_views, d_vnodes, K, d_nv, d_nvoff, (int)chunk_total, P, 0, V, true,
-                nullptr, 0, d_counts, d_inst_off, 0u, d_rec, d_info, d_dk0, d_iv0, d_ntile);
+                nullptr, 0, d_counts, d_inst_off, 0u, d_rec, d_info, d_dk0, d_iv0, d_ntile, d_vig);
     uint32_t *dk, *order, *tk, *tv;
-    launch_sort(L, d_dk0, d_iv0, d_dk1, d_iv1, (uint32_t)n_vis, kZBits, d_hist, d_status, d_cnt, d_err, &dk, &order);
+    launch_sort(L, d_dk0, d_iv0, d_dk1, d_iv1, (uint32_t)n_vis, kZBits, d_hist, d_status, d_cnt, d_err, &dk, &order,
+                nullptr, SortCtl{}, d_vig, bits_for_tiles((uint64_t)V));
     launch_tile_scan(L, order, d_ntile, (uint32_t)n_vis, nullptr, d_poff, d_tparts, (uint32_t)n_pairs, d_total, d_err);
     launch_pairs(L, d_views, K, order, d_poff, d_rec, d_info, (uint32_t)n_vis, nullptr, P, d_k0, d_v0, (uint32_t)n_pairs);
     SortCtl tile_ctl;
     tile_ctl.runs = true;
     launch_sort(L, d_k0, d_v0, d_k1, d_v1, (uint32_t)n_pairs, tbits, d_hist, d_status, d_cnt, d_err, &tk, &tv, d_total,
                 tile_ctl);
-    launch_ranges(L, tk, (uint32_t)n_pairs, d_ranges, (int)tiles_total, d_total);
+    launch_ranges(L, tk, (uint32_t)n_pairs, d_ranges, (int)tiles_total, d_total, d_views, V, P);
     launch_composite(L, d_views, 0, V, (int)tiles_total, d_ranges, tk, tv, d_rec, P, out_rgb, out_depth, out_alpha,
                      nullptr);
     uint32_t h_err = 0;

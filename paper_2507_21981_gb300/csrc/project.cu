@@ -449,6 +449,7 @@ struct EmitOut {
     uint32_t* dkey;       // depth key
     uint32_t* ival;       // the record number itself (value carried by the depth sort)
     uint32_t* ntile;      // tile pairs of the instance
+    uint32_t* vig;        // view of the instance within its view group (the depth sort's major key)
 };
 
 template <int DT>
@@ -561,6 +562,7 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
                         out.dkey[r] = (1u << kZBits) - 1u;
                         out.ival[r] = r;
                         out.ntile[r] = 0u;
+                        out.vig[r] = (uint32_t)vvj / (uint32_t)K - P.view0;
                     }
                     if (vis && in_bounds(r, P.n_rec, P.err, kSiteEmitRecord)) {
                         float rgb[3];
@@ -574,6 +576,7 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
                         out.info[r] = InstInfo{(uint32_t)(nd.gbase + i), (uint32_t)vvj};
                         out.dkey[r] = min(__float_as_uint(s.z) - P.zbase, (1u << kZBits) - 1u);
                         out.ival[r] = r;
+                        out.vig[r] = (uint32_t)vvj / (uint32_t)K - P.view0;
                         // exact tile pairs: the runs of tiles each tile row's band reaches
                         const float4 ext = ellipse_extent(s.qa, s.qb, s.qc, P.qbin);
                         uint32_t npairs = 0;
@@ -845,8 +848,8 @@ void launch_emit(const Launch& L, int dtype_mask, const NodeDesc* nodes, int n_n
                  const VNode* vnodes, int K, const NodeView* node_views, const int32_t* node_view_off,
                  int n_chunks_total, const Params& P, int v0, int v1, bool batched, const int32_t* pmap,
                  int64_t view_chunks, const uint2* counts, const uint32_t* inst_off, uint32_t inst_base,
-                 Record* records, InstInfo* info, uint32_t* dkey, uint32_t* ival, uint32_t* ntile) {
-    const EmitOut out{records, info, dkey, ival, ntile};
+                 Record* records, InstInfo* info, uint32_t* dkey, uint32_t* ival, uint32_t* ntile, uint32_t* vig) {
+    const EmitOut out{records, info, dkey, ival, ntile, vig};
     if (dtype_mask & (1 << DGS_F32))
         emit_launch<DGS_F32>(L, nodes, n_nodes, views, vnodes, K, node_views, node_view_off, n_chunks_total, P, v0, v1,
                              batched, pmap, view_chunks, counts, inst_off, inst_base, out);

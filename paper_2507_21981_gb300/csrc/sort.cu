@@ -13,7 +13,9 @@
 // 2-bit flag | 30-bit count).  Measured on the benchmark's key sets (17.9M depth keys, 59.7M tile
 // keys), the ballot ranking with 12 keys per thread at 4 blocks per SM sorts 13-17 % faster than
 // warp-match ranking with 16 keys at 3 blocks; either change alone gains nothing.  Digits are D = ceil(bits / passes) bits wide with passes =
-// ceil(bits / 8): measured on this path, wider digits (fewer passes) lose what they save to
+// ceil(bits / 8), the last pass taking the remaining bits so that exactly the requested key
+// bits are sorted (bits above them keep their input order: the tile keys hold the view there,
+// ordered by the depth sort before); measured on this path, wider digits (fewer passes) lose what they save to
 // the scatter, whose runs per partition shrink to a few keys.  Look-back spins are bounded by
 // a wall-clock limit (SortCtl::spin_ns, 1 s by default); on expiry the kernel sets
 // kErrTimeout and finishes: its output is then not a permutation of the input, the kernels
@@ -55,10 +57,12 @@ __device__ __forceinline__ uint32_t live_count(uint32_t n, const uint32_t* d_n) 
 template <bool RUNS>
 __global__ void __launch_bounds__(kThreads) k_hist(const uint32_t* __restrict__ keys, uint32_t n,
                                                    const uint32_t* __restrict__ d_n, int passes, int D,
-                                                   uint32_t* hist) {
+                                                   int last_bits, uint32_t* hist) {
     __shared__ uint32_t sh[4 * kMaxR];
     n = live_count(n, d_n);
-    const uint32_t R = 1u << D, mask = R - 1u;
+    // every pass's digit is D bits but the last one's, last_bits (the key bits above are not sorted)
+    const uint32_t R = 1u << D;
+    auto dmask = [&](int p) { return p == passes - 1 ? (1u << last_bits) - 1u : R - 1u; };
     for (int i = threadIdx.x; i < passes * (int)R; i += kThreads) sh[i] = 0;
     __syncthreads();
     if constexpr (RUNS) {
@@ -78,6 +82,7 @@ __global__ void __launch_bounds__(kThreads) k_hist(const uint32_t* __restrict__ 
             }
             const int cnt = (int)min(16u, n - base);
             for (int p = 0; p < passes; ++p) {
+                const uint32_t mask = dmask(p);
                 uint32_t cur = (k[0] >> (D * p)) & mask, run = 1;
 #pragma unroll
                 for (int j = 1; j < 16; ++j) {
@@ -94,7 +99,7 @@ __global__ void __launch_bounds__(kThreads) k_hist(const uint32_t* __restrict__ 
     } else {
         for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
             const uint32_t k = keys[i];
-            for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * R + ((k >> (D * p)) & mask)], 1u);
+            for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * R + ((k >> (D * p)) & dmask(p))], 1u);
         }
     }
     __syncthreads();
@@ -137,13 +142,16 @@ __global__ void __launch_bounds__(256) k_hist_scan(uint32_t* hist, int passes, i
 
 // One digit pass.  Thread t owns digits t, t + 256, ... (< 2^D) in the per-digit phases
 // (prefix over warps, look-back, block scan); digits are (key >> shift) & (2^D - 1).
-template <int D>
+// IND: the pass's key is read through the value, key = ind[value] (the keys sorted by the earlier
+// passes are dropped; the output keys are these), for a most significant key that the values
+// carry only by index.
+template <int D, bool IND>
 __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                       uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t n,
                                                       const uint32_t* __restrict__ d_n, int shift,
                                                       const uint32_t* __restrict__ digit_off, uint32_t* status,
                                                       uint32_t* counter, uint32_t* err, uint64_t spin_ns,
-                                                      uint32_t mute_part) {
+                                                      uint32_t mute_part, const uint32_t* __restrict__ ind) {
     constexpr int R = 1 << D;
     constexpr uint32_t M = R - 1;
     constexpr int DPT = (R + kThreads - 1) / kThreads;   // digits per thread
@@ -171,8 +179,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint32_t* __rest
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
         const uint32_t idx = base + warp * (kItems * 32) + j * 32 + lane;
-        if (idx < n) { k[j] = kin[idx]; v[j] = vin[idx]; }
-        else { k[j] = ~0u; v[j] = 0; }
+        if (idx < n) {
+            v[j] = vin[idx];
+            // (a value outside 0..n-1, left by an earlier pass that gave up waiting, reads nothing)
+            k[j] = IND ? (v[j] < n ? __ldg(ind + v[j]) : ~0u) : kin[idx];
+        } else {
+            k[j] = ~0u; v[j] = 0;
+        }
     }
     // rank within the warp, in original order (round j covers 32 consecutive keys); the lanes
     // holding the same digit are found by one ballot per digit bit
@@ -318,18 +331,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint32_t* __rest
 }
 
 using OnesweepFn = void (*)(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t, const uint32_t*, int,
-                            const uint32_t*, uint32_t*, uint32_t*, uint32_t*, uint64_t, uint32_t);
+                            const uint32_t*, uint32_t*, uint32_t*, uint32_t*, uint64_t, uint32_t, const uint32_t*);
 
+template <bool IND>
 OnesweepFn onesweep_for(int D) {
     switch (D) {
-        case 1: return k_onesweep<1>;
-        case 2: return k_onesweep<2>;
-        case 3: return k_onesweep<3>;
-        case 4: return k_onesweep<4>;
-        case 5: return k_onesweep<5>;
-        case 6: return k_onesweep<6>;
-        case 7: return k_onesweep<7>;
-        default: return k_onesweep<8>;
+        case 1: return k_onesweep<1, IND>;
+        case 2: return k_onesweep<2, IND>;
+        case 3: return k_onesweep<3, IND>;
+        case 4: return k_onesweep<4, IND>;
+        case 5: return k_onesweep<5, IND>;
+        case 6: return k_onesweep<6, IND>;
+        case 7: return k_onesweep<7, IND>;
+        default: return k_onesweep<8, IND>;
     }
 }
 
@@ -354,43 +368,71 @@ size_t sort_status_words(uint32_t n) { return ((size_t)n + kTile - 1) / kTile * 
 void sort_prepare() {
     static bool attr_set = false;
     if (!attr_set) {
-        for (int D = 1; D <= kMaxD; ++D)
-            cudaFuncSetAttribute(onesweep_for(D), cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        for (int D = 1; D <= kMaxD; ++D) {
+            cudaFuncSetAttribute(onesweep_for<false>(D), cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+            cudaFuncSetAttribute(onesweep_for<true>(D), cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        }
         attr_set = true;
     }
 }
 
-// hist: [4 * 256] words, counters: [8] words, status: sort_status_words(n) words.
+// hist: [8 * 256] words, counters: [8] words, status: sort_status_words(n) words.
 void launch_sort(const Launch& L, uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, uint32_t n,
                  int key_bits, uint32_t* hist, uint32_t* status, uint32_t* counters, uint32_t* err,
-                 uint32_t** keys_out, uint32_t** vals_out, const uint32_t* d_n, SortCtl ctl) {
+                 uint32_t** keys_out, uint32_t** vals_out, const uint32_t* d_n, SortCtl ctl, const uint32_t* ind,
+                 int ind_bits) {
     *keys_out = keys;
     *vals_out = vals;
     // with a device-side count every pass runs (the output lands in the same buffer whatever
     // the count); a host-known count of 0 or 1 is already sorted
     if (n <= 1 && !d_n) return;
     if (n == 0) return;
-    const int passes = sort_passes(key_bits);
-    const int D = (std::max(1, key_bits) + passes - 1) / passes;
+    const int bits = std::max(1, key_bits);
+    const int passes = sort_passes(bits);
+    const int D = (bits + passes - 1) / passes;
+    const int last_bits = bits - D * (passes - 1);      // exactly key_bits bits are sorted
     sort_prepare();
     cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kMaxR * passes, L.stream);
     cudaMemsetAsync(counters, 0, sizeof(uint32_t) * 8, L.stream);
     const int hist_blocks = (int)std::min<uint32_t>(4 * sm_count(), (n + kThreads * 8 - 1) / (kThreads * 8));
-    if (ctl.runs) k_hist<true><<<hist_blocks, kThreads, 0, L.stream>>>(keys, n, d_n, passes, D, hist);
-    else k_hist<false><<<hist_blocks, kThreads, 0, L.stream>>>(keys, n, d_n, passes, D, hist);
+    if (ctl.runs) k_hist<true><<<hist_blocks, kThreads, 0, L.stream>>>(keys, n, d_n, passes, D, last_bits, hist);
+    else k_hist<false><<<hist_blocks, kThreads, 0, L.stream>>>(keys, n, d_n, passes, D, last_bits, hist);
     k_hist_scan<<<1, 256, 0, L.stream>>>(hist, passes, 1 << D);
     *L.launches += 2;
     const uint32_t parts = (n + kTile - 1) / kTile;
-    const OnesweepFn fn = onesweep_for(D);
     uint32_t *ki = keys, *ko = keys_alt;
     uint32_t *vi = vals, *vo = vals_alt;
     for (int p = 0; p < passes; ++p) {
-        cudaMemsetAsync(status, 0, sizeof(uint32_t) * (size_t)(1 << D) * parts, L.stream);
+        const int Dp = p == passes - 1 ? last_bits : D;
+        const OnesweepFn fn = onesweep_for<false>(Dp);
+        cudaMemsetAsync(status, 0, sizeof(uint32_t) * (size_t)(1 << Dp) * parts, L.stream);
         fn<<<parts, kThreads, kSmem, L.stream>>>(ki, vi, ko, vo, n, d_n, D * p, hist + p * kMaxR, status, counters + p,
-                                                 err, ctl.spin_ns, p == 0 ? ctl.mute_part : 0xFFFFFFFFu);
+                                                 err, ctl.spin_ns, p == 0 ? ctl.mute_part : 0xFFFFFFFFu, nullptr);
         ++*L.launches;
         uint32_t* tk = ki; ki = ko; ko = tk;
         uint32_t* tv = vi; vi = vo; vo = tv;
+    }
+    // the most significant key, read through the values: ind[value] for values 0..n-1 (their
+    // histogram is that of ind itself, whatever the order the earlier passes left)
+    if (ind && ind_bits > 0) {
+        const int ip = sort_passes(ind_bits);
+        const int Di = (ind_bits + ip - 1) / ip;
+        const int ilast = ind_bits - Di * (ip - 1);
+        uint32_t* ih = hist + passes * kMaxR;
+        cudaMemsetAsync(ih, 0, sizeof(uint32_t) * kMaxR * ip, L.stream);
+        k_hist<false><<<hist_blocks, kThreads, 0, L.stream>>>(ind, n, d_n, ip, Di, ilast, ih);
+        k_hist_scan<<<1, 256, 0, L.stream>>>(ih, ip, 1 << Di);
+        *L.launches += 2;
+        for (int p = 0; p < ip; ++p) {
+            const int Dp = p == ip - 1 ? ilast : Di;
+            const OnesweepFn fi = onesweep_for<true>(Dp);
+            cudaMemsetAsync(status, 0, sizeof(uint32_t) * (size_t)(1 << Dp) * parts, L.stream);
+            fi<<<parts, kThreads, kSmem, L.stream>>>(ki, vi, ko, vo, n, d_n, Di * p, ih + p * kMaxR, status,
+                                                     counters + passes + p, err, ctl.spin_ns, 0xFFFFFFFFu, ind);
+            ++*L.launches;
+            uint32_t* tk = ki; ki = ko; ko = tk;
+            uint32_t* tv = vi; vi = vo; vo = tv;
+        }
     }
     *keys_out = ki;
     *vals_out = vi;
