@@ -776,22 +776,27 @@ def main():
     re2e = [Renderer(mode="graph", tile=tile), Renderer(mode="graph", tile=tile)]
     dposes = torch.empty_like(ds.node_poses)
     n_chunks = 4
+    # per step: the render's and the read-back's spans on their streams (events only)
+    spans = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.warmup + args.steps)]
 
     def e2e_step(i):
         b = i & 1
+        ev = spans[i]
         dposes.copy_(poses_host, non_blocking=True)
         ds.node_poses = dposes
         stream.wait_event(copied[b])               # buffer b's previous read-back is done
+        ev[0].record(stream)
         rgb, depth, _ = re2e[b].render(ds, out=(dev_out[b][0], dev_out[b][1], None))
-        ready = torch.cuda.Event()
-        ready.record(stream)
-        copy_stream.wait_event(ready)
+        ev[1].record(stream)
+        copy_stream.wait_event(ev[1])
         with torch.cuda.stream(copy_stream):
+            ev[2].record(copy_stream)
             for src, dst in ((rgb, host_out[b][0]), (depth, host_out[b][1])):
                 fs, fd = src.view(-1), dst.view(-1)
                 step = (fs.numel() + n_chunks - 1) // n_chunks
                 for c0 in range(0, fs.numel(), step):
                     fd[c0:c0 + step].copy_(fs[c0:c0 + step], non_blocking=True)
+            ev[3].record(copy_stream)
         copied[b].record(copy_stream)
     for i in range(args.warmup):
         e2e_step(i)
@@ -805,6 +810,9 @@ def main():
     barrier()
     host_rgb, host_depth = host_out[0]
     ms_e2e = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
+    timed = spans[args.warmup:]
+    e2e_render_ms = float(np.median([e[0].elapsed_time(e[1]) for e in timed]))
+    e2e_copy_ms = float(np.median([e[2].elapsed_time(e[3]) for e in timed]))
     e2e_value = px_per_step * world / (ms_e2e / 1e3) / 1e6
     h2d = poses_host.numel() * 4
     d2h = (host_rgb.numel() + host_depth.numel()) * 4
@@ -850,11 +858,20 @@ def main():
     dom = max(per_step, key=per_step.get)
     P, NV = stats["n_pairs"], stats["n_visible"]
     passes = (stats["key_bits"] + 7) // 8          # tile-sort passes (key_bits = tile key bits)
-    # algorithmic bytes of the binning class: depth sort of the instances (28-bit keys, 4
-    # passes of 16 B plus the histogram read), tile-count scan (order and count read twice,
-    # offset written: 20 B), pair emission (record 48 + identity 8 + order 4 + offset 4 read;
-    # 8 B written per pair) and the tile sort (histogram read, passes of 16 B)
-    sort_bytes = NV * (4 + 4 * 16 + 20 + 64) + P * (8 + 4 + passes * 16)
+    # passes of the depth sort's view key (the bits of the views per group; none for one view);
+    # the view rides in the instance numbers' high bits when both fit in 32 bits, else each
+    # view pass also gathers the view of every value (4 B)
+    vpg = -(-stats["n_views"] // max(stats["n_groups"], 1))
+    vbits = (vpg - 1).bit_length()
+    vpasses = (vbits + 7) // 8
+    packed = vbits > 0 and (max(NV // max(stats["n_groups"], 1), 1) - 1).bit_length() + vbits <= 32
+    # algorithmic bytes of the binning class: depth sort of the instances (28-bit keys: the
+    # histogram read, 4 passes of 16 B, the last writing no keys when view passes follow; each
+    # view pass reads and writes the value), tile-count scan (order and count read twice, offset
+    # written: 20 B), pair emission (record 48 + identity 8 + order 4 + offset 4 read; 8 B
+    # written per pair) and the tile sort (histogram read, passes of 16 B)
+    depth_b = 4 + 4 * 16 - (4 if vpasses else 0) + vpasses * (8 if packed else 12)
+    sort_bytes = NV * (depth_b + 20 + 64) + P * (8 + 4 + passes * 16)
     # compositor work of one step, counted by the instrumented compositor outside the timed region
     rc_ = Renderer(mode="batched", tile=tile, profile=2)
     rc_.render(ds, out=out)
@@ -878,8 +895,10 @@ def main():
                                 "evaluated_over_reached": work["px_evaluated"] / max(work["px_reached"], 1),
                                 "ops_per_pair": OPS_PER_PAIR}},
         "sort": {**hbm(sort_bytes, per_step["sort"]),
-                 "units": {"instances": NV, "pairs": P, "depth_passes": 4, "tile_passes": passes,
-                           "bytes_per_instance": 4 + 4 * 16 + 20 + 64, "bytes_per_pair": 8 + 4 + passes * 16}},
+                 "units": {"instances": NV, "pairs": P, "depth_passes": 4, "view_passes": vpasses,
+                           "view_key": "packed in the values" if packed else "gathered",
+                           "tile_passes": passes, "bytes_per_instance": depth_b + 20 + 64,
+                           "bytes_per_pair": 8 + 4 + passes * 16}},
         "emit": {**alu(NV * (PROJ_OPS + SH3_OPS), per_step["emit"]),
                  "units": {"visible": NV, "ops_per_visible": PROJ_OPS + SH3_OPS,
                            "not_counted": "tile-row runs of the pair count"}},
@@ -928,7 +947,9 @@ def main():
         "kernel_ms_per_step": per_step, "kernel_times_from": "one-view-group profiled region (kernels not overlapped)",
         "render_stats": stats,
         "roofline": roof, "kernel_rooflines": kernels,
-        "e2e": {"value": e2e_value, "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": ms_e2e, "render_ms_median": e2e_render_ms, "readback_ms_median": e2e_copy_ms,
+                "note": "the read-back of step i overlaps the render of step i + 1"},
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }

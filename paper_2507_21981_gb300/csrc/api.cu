@@ -834,11 +834,22 @@ void enqueue_lists(dgs_ctx* ctx, ListBufs& lb, const Batch& B, const Launch& L, 
     auto u32 = [](DevBuf& b) { return static_cast<uint32_t*>(b.p); };
     Record* rec = static_cast<Record*>(lb.records.p);
     InstInfo* info = static_cast<InstInfo*>(lb.info.p);
+    // the depth sort's view key: packed into the instance numbers where both fit in 32 bits
+    ViewKey vk;
+    vk.bits = bits_for((uint64_t)(v1 - v0));
+    if (vk.bits > 0 && bits_for((uint64_t)n_inst) + vk.bits <= 32) vk.vshift = 32 - vk.bits;
+    vk.vig = vk.bits > 0 && !vk.vshift ? u32(lb.vig) : nullptr;
+    vk.inst_off = B.d_inst_off;
+    vk.view_tab = B.d_viewtab;
+    vk.v0 = v0;
+    vk.nv = v1 - v0;
+    Params Pe = P;
+    Pe.vshift = vk.vshift;
     tm.begin(DGS_K_EMIT);
     launch_emit(L, B.dtype_mask, B.d_nodes, B.n_nodes, B.d_views, B.d_vnodes, K, B.d_nv, B.d_nvoff, (int)B.chunk_total,
-                P, v0, v1, B.batched, B.d_pmap + (size_t)v0 * (2 * K + 1), B.view_tab[v0 + 1] - B.view_tab[v0],
+                Pe, v0, v1, B.batched, B.d_pmap + (size_t)v0 * (2 * K + 1), B.view_tab[v0 + 1] - B.view_tab[v0],
                 B.d_counts, B.d_inst_off, inst_base, rec, info, u32(lb.dkey0), u32(lb.ival0), u32(lb.ntile),
-                u32(lb.vig));
+                const_cast<uint32_t*>(vk.vig));
     tm.end();
     tm.begin(DGS_K_SORT);
     uint32_t *dk = nullptr, *order = nullptr;
@@ -850,8 +861,7 @@ void enqueue_lists(dgs_ctx* ctx, ListBufs& lb, const Batch& B, const Launch& L, 
     // instances by depth, then by view (most significant, through the values): each view's
     // instances in depth order, so that every instance's pairs come out view by view
     launch_sort(L, u32(lb.dkey0), u32(lb.ival0), u32(lb.dkey1), u32(lb.ival1), n_inst, kZBits, u32(lb.hist),
-                u32(lb.status), u32(lb.counters), B.d_err, &dk, &order, d_inst, depth_ctl, u32(lb.vig),
-                bits_for((uint64_t)(v1 - v0)));
+                u32(lb.status), u32(lb.counters), B.d_err, &dk, &order, d_inst, depth_ctl, &vk);
     launch_tile_scan(L, order, u32(lb.ntile), n_inst, d_inst, u32(lb.poff), u32(lb.tparts), n_bound, d_pairs, B.d_err);
     launch_pairs(L, B.d_views, K, order, u32(lb.poff), rec, info, n_inst, d_inst, P, u32(lb.tkeys0),
                  u32(lb.tvals0), n_bound);

@@ -38,12 +38,14 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, uint32_t n, const ui
         const uint32_t i = i4 + j;
         if (i >= n) break;
         const uint32_t t = k[1 + j];
+        const bool first = i == 0 || k[j] != t, last = i + 1 == n || k[2 + j] != t;
+        if (!first && !last) continue;              // the view is decoded at run ends only
         const uint32_t vg = t >> tbits;
         if (vg >= (uint32_t)nv) continue;           // dead pairs sort past every real tile
         const uint32_t gt = (uint32_t)(views[v0 + vg].tile_base - tile0) + (t & ((1u << tbits) - 1u));
         if (gt >= (uint32_t)n_tiles) continue;      // (only keys of a sort that gave up waiting)
-        if (i == 0 || k[j] != t) ranges[gt].x = i;
-        if (i + 1 == n || k[2 + j] != t) ranges[gt].y = i + 1;
+        if (first) ranges[gt].x = i;
+        if (last) ranges[gt].y = i + 1;
     }
 }
 

@@ -157,6 +157,7 @@ struct Params {
     uint32_t n_rec;       // records of the current view group (bound of its instance numbers)
     uint32_t view0;       // first view of the current view group
     int32_t tbits;        // bits of a tile within its view (tile keys: view in group << tbits | tile)
+    int32_t vshift;       // > 0: emission writes instance numbers as r | view in group << vshift
     const uint32_t* inst_base_dev;  // emission: first record of the group read on the device (graph replay)
     // image randomisation of the RGB output (null aug = none): per-view records, overlay clip
     const dgs_augment* aug;
@@ -430,16 +431,30 @@ struct SortCtl {
     bool runs = false;    // neighbouring keys share their high digits (histogram by runs)
 };
 
+// The depth sort's most significant key: the view of each instance within its view group.
+// The instance numbers of a group are emitted view by view, view j of the group holding
+// inst_off[view_tab[v0 + j + 1]] - inst_off[view_tab[v0 + j]] of them (the count scan), which
+// gives the view key's histogram.  With vshift > 0 the values are packed, r | view << vshift
+// (r < 2^vshift), and the last view pass leaves r; else the view of value r is vig[r].
+struct ViewKey {
+    int bits = 0;                        // view bits; 0: no view passes
+    int vshift = 0;
+    const uint32_t* vig = nullptr;
+    const uint32_t* inst_off = nullptr;  // count-scan offsets (device)
+    const int64_t* view_tab = nullptr;   // first count-table entry of each view (device)
+    int v0 = 0, nv = 0;
+};
+
 // Stable LSD radix sort of (key, value) on the low key_bits bits.  With d_n non-null the
 // number of pairs is read on the device as min(*d_n, n), and n is the capacity the launches
 // are sized for.  *keys_out / *vals_out receive the buffers holding the result.  A look-back
-// wait that runs out sets kErrTimeout in err (the output is then invalid).  With ind, the
-// values 0..n-1 are then sorted stably by ind[value] on its low ind_bits bits, as a more
-// significant key (the output keys are then those ind values).
+// wait that runs out sets kErrTimeout in err (the output is then invalid).  With vk (bits > 0)
+// the values are then sorted stably by their view, as a more significant key; no sorted keys
+// are then written (*keys_out is null).
 void launch_sort(const Launch& L, uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                  uint32_t n, int key_bits, uint32_t* hist, uint32_t* status, uint32_t* counters, uint32_t* err,
                  uint32_t** keys_out, uint32_t** vals_out, const uint32_t* d_n = nullptr, SortCtl ctl = SortCtl{},
-                 const uint32_t* ind = nullptr, int ind_bits = 0);
+                 const ViewKey* vk = nullptr);
 
 // Sets the sort kernels' launch attributes; call before a stream capture that contains a sort.
 void sort_prepare();

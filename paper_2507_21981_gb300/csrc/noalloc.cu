@@ -191,14 +191,24 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
     if (tbits > kTileBits || tiles_total > kMaxGroupTiles || (int64_t)V >= (1ll << (kTileBits - tbits)))
         return DGS_ERR_CAPACITY;
     // depth-ordered tile lists, as in dgs_render with one view group
+    // the depth sort's view key, packed into the instance numbers where both fit in 32 bits
+    ViewKey vk;
+    vk.bits = bits_for_tiles((uint64_t)V);
+    if (vk.bits > 0 && bits_for_tiles(n_vis) + vk.bits <= 32) vk.vshift = 32 - vk.bits;
+    vk.vig = vk.bits > 0 && !vk.vshift ? d_vig : nullptr;
+    vk.inst_off = d_inst_off;
+    vk.view_tab = d_viewtab;
+    vk.v0 = 0;
+    vk.nv = V;
     P.n_rec = (uint32_t)n_vis;
     P.view0 = 0;
     P.tbits = tbits;
+    P.vshift = vk.vshift;
     launch_emit(L, dtype_mask, d_nodes, n_nodes, d_views, d_vnodes, K, d_nv, d_nvoff, (int)chunk_total, P, 0, V, true,
-                nullptr, 0, d_counts, d_inst_off, 0u, d_rec, d_info, d_dk0, d_iv0, d_ntile, d_vig);
+                nullptr, 0, d_counts, d_inst_off, 0u, d_rec, d_info, d_dk0, d_iv0, d_ntile, vk.vig ? d_vig : nullptr);
     uint32_t *dk, *order, *tk, *tv;
     launch_sort(L, d_dk0, d_iv0, d_dk1, d_iv1, (uint32_t)n_vis, kZBits, d_hist, d_status, d_cnt, d_err, &dk, &order,
-                nullptr, SortCtl{}, d_vig, bits_for_tiles((uint64_t)V));
+                nullptr, SortCtl{}, &vk);
     launch_tile_scan(L, order, d_ntile, (uint32_t)n_vis, nullptr, d_poff, d_tparts, (uint32_t)n_pairs, d_total, d_err);
     launch_pairs(L, d_views, K, order, d_poff, d_rec, d_info, (uint32_t)n_vis, nullptr, P, d_k0, d_v0, (uint32_t)n_pairs);
     SortCtl tile_ctl;

@@ -449,7 +449,7 @@ struct EmitOut {
     uint32_t* dkey;       // depth key
     uint32_t* ival;       // the record number itself (value carried by the depth sort)
     uint32_t* ntile;      // tile pairs of the instance
-    uint32_t* vig;        // view of the instance within its view group (the depth sort's major key)
+    uint32_t* vig;        // view of the instance within its view group (the depth sort's major key); null: not written
 };
 
 template <int DT>
@@ -560,9 +560,10 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
                         out.rec[r] = Record{};
                         out.info[r] = InstInfo{(uint32_t)(nd.gbase + i), (uint32_t)vvj};
                         out.dkey[r] = (1u << kZBits) - 1u;
-                        out.ival[r] = r;
+                        const uint32_t vg = (uint32_t)vvj / (uint32_t)K - P.view0;
+                        out.ival[r] = P.vshift ? r | vg << P.vshift : r;
                         out.ntile[r] = 0u;
-                        out.vig[r] = (uint32_t)vvj / (uint32_t)K - P.view0;
+                        if (out.vig) out.vig[r] = vg;
                     }
                     if (vis && in_bounds(r, P.n_rec, P.err, kSiteEmitRecord)) {
                         float rgb[3];
@@ -575,8 +576,9 @@ __device__ __forceinline__ void process_chunk(const NodeDesc& nd, int c, int lan
                         out.rec[r] = R;
                         out.info[r] = InstInfo{(uint32_t)(nd.gbase + i), (uint32_t)vvj};
                         out.dkey[r] = min(__float_as_uint(s.z) - P.zbase, (1u << kZBits) - 1u);
-                        out.ival[r] = r;
-                        out.vig[r] = (uint32_t)vvj / (uint32_t)K - P.view0;
+                        const uint32_t vg = (uint32_t)vvj / (uint32_t)K - P.view0;
+                        out.ival[r] = P.vshift ? r | vg << P.vshift : r;
+                        if (out.vig) out.vig[r] = vg;
                         // exact tile pairs: the runs of tiles each tile row's band reaches
                         const float4 ext = ellipse_extent(s.qa, s.qb, s.qc, P.qbin);
                         uint32_t npairs = 0;

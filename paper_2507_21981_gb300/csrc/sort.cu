@@ -37,6 +37,7 @@ constexpr int kMaxR = 1 << kMaxD;
 constexpr int kWindow = 4;                        // predecessors read per digit and look-back round
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kCountMask = (1u << 30) - 1u;
 constexpr int kSmem = kTile * 8 + kWarps * kMaxR * 4;
+constexpr int kKeysIn = 0, kKeysGather = 1, kKeysPacked = 2;   // where a pass's key comes from
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
     uint32_t v;
@@ -142,16 +143,19 @@ __global__ void __launch_bounds__(256) k_hist_scan(uint32_t* hist, int passes, i
 
 // One digit pass.  Thread t owns digits t, t + 256, ... (< 2^D) in the per-digit phases
 // (prefix over warps, look-back, block scan); digits are (key >> shift) & (2^D - 1).
-// IND: the pass's key is read through the value, key = ind[value] (the keys sorted by the earlier
-// passes are dropped; the output keys are these), for a most significant key that the values
-// carry only by index.
-template <int D, bool IND>
+// MODE kKeysIn reads the keys; the other two derive a more significant key from the value (the
+// keys sorted by the earlier passes are dropped): kKeysGather reads key = ind[value], kKeysPacked
+// takes the value's high bits, key = value >> vshift.  Those two write no keys.  Every mode
+// stores value & vmask (the last pass over packed values strips the key bits).  A null kout
+// also skips the key writes (keys that no later pass reads).
+template <int D, int MODE>
 __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                       uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t n,
                                                       const uint32_t* __restrict__ d_n, int shift,
                                                       const uint32_t* __restrict__ digit_off, uint32_t* status,
                                                       uint32_t* counter, uint32_t* err, uint64_t spin_ns,
-                                                      uint32_t mute_part, const uint32_t* __restrict__ ind) {
+                                                      uint32_t mute_part, const uint32_t* __restrict__ ind, int vshift,
+                                                      uint32_t vmask) {
     constexpr int R = 1 << D;
     constexpr uint32_t M = R - 1;
     constexpr int DPT = (R + kThreads - 1) / kThreads;   // digits per thread
@@ -182,7 +186,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint32_t* __rest
         if (idx < n) {
             v[j] = vin[idx];
             // (a value outside 0..n-1, left by an earlier pass that gave up waiting, reads nothing)
-            k[j] = IND ? (v[j] < n ? __ldg(ind + v[j]) : ~0u) : kin[idx];
+            k[j] = MODE == kKeysGather ? (v[j] < n ? __ldg(ind + v[j]) : ~0u)
+                   : MODE == kKeysPacked ? v[j] >> vshift
+                                         : kin[idx];
         } else {
             k[j] = ~0u; v[j] = 0;
         }
@@ -326,25 +332,51 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint32_t* __rest
         const uint32_t g = s_gbase[dj] + (uint32_t)i - s_dexcl[dj];
         // every live key lands below n (the padding keys, ~0, sort past the end and are dropped)
         if (kDebugChecks && key != ~0u && !in_bounds(g, n, err, kSiteSortScatter)) continue;
-        if (g < n) { kout[g] = key; vout[g] = s_vals[i]; }
+        if (g < n) {
+            if (MODE == kKeysIn && kout) kout[g] = key;
+            vout[g] = s_vals[i] & vmask;
+        }
     }
 }
 
 using OnesweepFn = void (*)(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t, const uint32_t*, int,
-                            const uint32_t*, uint32_t*, uint32_t*, uint32_t*, uint64_t, uint32_t, const uint32_t*);
+                            const uint32_t*, uint32_t*, uint32_t*, uint32_t*, uint64_t, uint32_t, const uint32_t*, int,
+                            uint32_t);
 
-template <bool IND>
+template <int MODE>
 OnesweepFn onesweep_for(int D) {
     switch (D) {
-        case 1: return k_onesweep<1, IND>;
-        case 2: return k_onesweep<2, IND>;
-        case 3: return k_onesweep<3, IND>;
-        case 4: return k_onesweep<4, IND>;
-        case 5: return k_onesweep<5, IND>;
-        case 6: return k_onesweep<6, IND>;
-        case 7: return k_onesweep<7, IND>;
-        default: return k_onesweep<8, IND>;
+        case 1: return k_onesweep<1, MODE>;
+        case 2: return k_onesweep<2, MODE>;
+        case 3: return k_onesweep<3, MODE>;
+        case 4: return k_onesweep<4, MODE>;
+        case 5: return k_onesweep<5, MODE>;
+        case 6: return k_onesweep<6, MODE>;
+        case 7: return k_onesweep<7, MODE>;
+        default: return k_onesweep<8, MODE>;
     }
+}
+
+// Histograms of the view passes' digits, from the count scan rather than from the values: view
+// j of the group holds inst_off[view_tab[v0 + j + 1]] - inst_off[view_tab[v0 + j]] instance
+// numbers.  One block; the bins are stored, not added.
+__global__ void __launch_bounds__(kThreads) k_view_hist(const uint32_t* __restrict__ inst_off,
+                                                        const int64_t* __restrict__ view_tab, int v0, int nv,
+                                                        int passes, int D, int last_bits, uint32_t* hist) {
+    __shared__ uint32_t sh[4 * kMaxR];
+    const uint32_t R = 1u << D;
+    for (int i = threadIdx.x; i < passes * (int)R; i += kThreads) sh[i] = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < nv; j += kThreads) {
+        const uint32_t c = inst_off[view_tab[v0 + j + 1]] - inst_off[view_tab[v0 + j]];
+        if (!c) continue;
+        for (int p = 0; p < passes; ++p) {
+            const uint32_t mask = p == passes - 1 ? (1u << last_bits) - 1u : R - 1u;
+            atomicAdd(&sh[p * R + (((uint32_t)j >> (D * p)) & mask)], c);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * (int)R; i += kThreads) hist[(i / R) * kMaxR + (i % R)] = sh[i];
 }
 
 }  // namespace
@@ -369,8 +401,9 @@ void sort_prepare() {
     static bool attr_set = false;
     if (!attr_set) {
         for (int D = 1; D <= kMaxD; ++D) {
-            cudaFuncSetAttribute(onesweep_for<false>(D), cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-            cudaFuncSetAttribute(onesweep_for<true>(D), cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+            cudaFuncSetAttribute(onesweep_for<kKeysIn>(D), cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+            cudaFuncSetAttribute(onesweep_for<kKeysGather>(D), cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+            cudaFuncSetAttribute(onesweep_for<kKeysPacked>(D), cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
         }
         attr_set = true;
     }
@@ -379,8 +412,7 @@ void sort_prepare() {
 // hist: [8 * 256] words, counters: [8] words, status: sort_status_words(n) words.
 void launch_sort(const Launch& L, uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, uint32_t n,
                  int key_bits, uint32_t* hist, uint32_t* status, uint32_t* counters, uint32_t* err,
-                 uint32_t** keys_out, uint32_t** vals_out, const uint32_t* d_n, SortCtl ctl, const uint32_t* ind,
-                 int ind_bits) {
+                 uint32_t** keys_out, uint32_t** vals_out, const uint32_t* d_n, SortCtl ctl, const ViewKey* vk) {
     *keys_out = keys;
     *vals_out = vals;
     // with a device-side count every pass runs (the output lands in the same buffer whatever
@@ -400,41 +432,47 @@ void launch_sort(const Launch& L, uint32_t* keys, uint32_t* vals, uint32_t* keys
     k_hist_scan<<<1, 256, 0, L.stream>>>(hist, passes, 1 << D);
     *L.launches += 2;
     const uint32_t parts = (n + kTile - 1) / kTile;
+    const bool by_view = vk && vk->bits > 0;
     uint32_t *ki = keys, *ko = keys_alt;
     uint32_t *vi = vals, *vo = vals_alt;
     for (int p = 0; p < passes; ++p) {
         const int Dp = p == passes - 1 ? last_bits : D;
         const OnesweepFn fn = onesweep_for<false>(Dp);
+        // the view passes read no keys: the last key pass before them writes none
+        uint32_t* kw = by_view && p == passes - 1 ? nullptr : ko;
         cudaMemsetAsync(status, 0, sizeof(uint32_t) * (size_t)(1 << Dp) * parts, L.stream);
-        fn<<<parts, kThreads, kSmem, L.stream>>>(ki, vi, ko, vo, n, d_n, D * p, hist + p * kMaxR, status, counters + p,
-                                                 err, ctl.spin_ns, p == 0 ? ctl.mute_part : 0xFFFFFFFFu, nullptr);
+        fn<<<parts, kThreads, kSmem, L.stream>>>(ki, vi, kw, vo, n, d_n, D * p, hist + p * kMaxR, status, counters + p,
+                                                 err, ctl.spin_ns, p == 0 ? ctl.mute_part : 0xFFFFFFFFu, nullptr, 0,
+                                                 0xFFFFFFFFu);
         ++*L.launches;
         uint32_t* tk = ki; ki = ko; ko = tk;
         uint32_t* tv = vi; vi = vo; vo = tv;
     }
-    // the most significant key, read through the values: ind[value] for values 0..n-1 (their
-    // histogram is that of ind itself, whatever the order the earlier passes left)
-    if (ind && ind_bits > 0) {
-        const int ip = sort_passes(ind_bits);
-        const int Di = (ind_bits + ip - 1) / ip;
-        const int ilast = ind_bits - Di * (ip - 1);
+    // the most significant key, the view, derived from the values (their high bits, or vig[value]);
+    // its histogram comes from the per-view counts of the count scan
+    if (by_view) {
+        const int ip = sort_passes(vk->bits);
+        const int Di = (vk->bits + ip - 1) / ip;
+        const int ilast = vk->bits - Di * (ip - 1);
         uint32_t* ih = hist + passes * kMaxR;
-        cudaMemsetAsync(ih, 0, sizeof(uint32_t) * kMaxR * ip, L.stream);
-        k_hist<false><<<hist_blocks, kThreads, 0, L.stream>>>(ind, n, d_n, ip, Di, ilast, ih);
+        k_view_hist<<<1, kThreads, 0, L.stream>>>(vk->inst_off, vk->view_tab, vk->v0, vk->nv, ip, Di, ilast, ih);
         k_hist_scan<<<1, 256, 0, L.stream>>>(ih, ip, 1 << Di);
         *L.launches += 2;
+        const bool packed = vk->vshift > 0;
         for (int p = 0; p < ip; ++p) {
             const int Dp = p == ip - 1 ? ilast : Di;
-            const OnesweepFn fi = onesweep_for<true>(Dp);
+            const OnesweepFn fi = packed ? onesweep_for<kKeysPacked>(Dp) : onesweep_for<kKeysGather>(Dp);
+            const uint32_t vmask = packed && p == ip - 1 ? (1u << vk->vshift) - 1u : 0xFFFFFFFFu;
             cudaMemsetAsync(status, 0, sizeof(uint32_t) * (size_t)(1 << Dp) * parts, L.stream);
             fi<<<parts, kThreads, kSmem, L.stream>>>(ki, vi, ko, vo, n, d_n, Di * p, ih + p * kMaxR, status,
-                                                     counters + passes + p, err, ctl.spin_ns, 0xFFFFFFFFu, ind);
+                                                     counters + passes + p, err, ctl.spin_ns, 0xFFFFFFFFu, vk->vig,
+                                                     vk->vshift, vmask);
             ++*L.launches;
             uint32_t* tk = ki; ki = ko; ko = tk;
             uint32_t* tv = vi; vi = vo; vo = tv;
         }
     }
-    *keys_out = ki;
+    *keys_out = by_view ? nullptr : ki;
     *vals_out = vi;
 }
 
