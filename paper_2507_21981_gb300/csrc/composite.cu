@@ -242,16 +242,20 @@ __global__ void __launch_bounds__(kCompWarps * 32, (COUNT || AUG || CK) ? 20 : 2
             float t;
             const float pe = pixel_exponent(g1.x, g1.y, g1.z, fx - g0.x, fy - g0.y, t);
             if (COUNT && pe >= P.p_min) ++n_reach;
-            if (!(pe >= g1.w)) continue;           // outside the ellipse, or alpha below alpha_min
-            const float alpha = fminf(P.alpha_max, g0.z * fast_exp2(pe));
+            // without branches: a record outside the ellipse or below alpha_min gets alpha = 0,
+            // and a step that would take T below t_min ends the pixel with weight 0; either
+            // leaves T, C and D bit for bit unchanged (T - 0 T = T, C + 0 c = C)
+            const bool hit = pe >= g1.w;
+            const float alpha = hit ? fminf(P.alpha_max, g0.z * fast_exp2(pe)) : 0.f;
             const float Tn = fmaf(-alpha, T, T);   // T (1 - alpha), one rounding
-            if (Tn < P.t_min) { done = true; break; }
-            if (COUNT) ++n_comp;
-            const float wgt = alpha * T;
+            const bool stop = Tn < P.t_min;
+            if (COUNT && hit && !stop) ++n_comp;
+            const float wgt = stop ? 0.f : alpha * T;
             const float4 g2 = sr2[k];
             C0 = fmaf(wgt, g2.x, C0); C1 = fmaf(wgt, g2.y, C1); C2 = fmaf(wgt, g2.z, C2);
             D = fmaf(wgt, g0.w, D);
-            T = Tn;
+            T = stop ? T : Tn;
+            done = stop;
         }
         __syncwarp();
     }
