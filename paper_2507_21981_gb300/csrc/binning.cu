@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tscan_final(const uint32_t* __
 // Sub-tile mask of tile column tx from the sub-row intervals [L, R] of its tile row (SR rows x SC
 // columns of 8x4-pixel sub-tiles; bit s = sub-tile (s mod SC, s div SC)).
 template <int SR, int SC>
-__device__ __forceinline__ uint32_t row_mask(const float (&L)[8], const float (&R)[8], int tx, int tile_w) {
+__device__ __forceinline__ uint32_t row_mask(const float (&L)[SR], const float (&R)[SR], int tx, int tile_w) {
     uint32_t m = 0;
 #pragma unroll
     for (int sy = 0; sy < SR; ++sy)
@@ -136,21 +136,6 @@ __device__ __forceinline__ uint32_t row_mask(const float (&L)[8], const float (&
             if (L[sy] <= c0 + 7.f && R[sy] >= c0) m |= 1u << (sy * SC + sx);
         }
     return m;
-}
-
-__device__ __forceinline__ uint32_t row_mask_any(const float (&L)[8], const float (&R)[8], int tx, const Params& P) {
-    switch ((P.tile_h >> 2) * 16 + (P.tile_w >> 3)) {      // (sub-tile rows, columns), at most 8 sub-tiles
-        case 1 * 16 + 2: return row_mask<1, 2>(L, R, tx, P.tile_w);
-        case 1 * 16 + 4: return row_mask<1, 4>(L, R, tx, P.tile_w);
-        case 1 * 16 + 8: return row_mask<1, 8>(L, R, tx, P.tile_w);
-        case 2 * 16 + 1: return row_mask<2, 1>(L, R, tx, P.tile_w);
-        case 2 * 16 + 2: return row_mask<2, 2>(L, R, tx, P.tile_w);
-        case 2 * 16 + 4: return row_mask<2, 4>(L, R, tx, P.tile_w);
-        case 4 * 16 + 1: return row_mask<4, 1>(L, R, tx, P.tile_w);
-        case 4 * 16 + 2: return row_mask<4, 2>(L, R, tx, P.tile_w);
-        case 8 * 16 + 1: return row_mask<8, 1>(L, R, tx, P.tile_w);
-        default: return row_mask<1, 1>(L, R, tx, P.tile_w);
-    }
 }
 
 // Per-warp state of the pair writer: item l is depth-ordered instance i0 + l.  Its pairs are
@@ -167,6 +152,8 @@ struct PairWarp {
     uint32_t off[32], end[32], run[32];
 };
 
+// SR x SC: sub-tile rows and columns of the tile shape (8x4-pixel sub-tiles).
+template <int SR, int SC>
 __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(const ViewDesc* __restrict__ views, int K,
                                                           const uint32_t* __restrict__ order,
                                                           const uint32_t* __restrict__ poff,
@@ -215,14 +202,13 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(const ViewDesc* __res
     const uint32_t my_rexcl = incl - nrows;
     S.rexcl[lane] = my_rexcl;
     __syncwarp();
-    const int sub_rows = P.tile_h >> 2;
     for (uint32_t rb = 0; rb < total_rows; rb += 32) {
         // one row job per lane: its run of tiles and the sub-row intervals of its tile row
         const uint32_t j = rb + (uint32_t)lane;
         const bool jact = j < total_rows;
         const int o = walk_owner_of(lane, act, act ? my_rexcl : total_rows, rb);
         int nrun = 0, t0 = 0, row = 0;
-        float L[8], R[8];
+        float L[SR], R[SR];
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f), e = a;
         int4 bx = make_int4(0, 0, 0, 0);
         if (jact) {
@@ -250,27 +236,25 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(const ViewDesc* __res
             const uint32_t end = min(S.end[o], cap);
             const int4 cc = S.c[o];
             const uint32_t tile_row = (uint32_t)(cc.y + row * cc.z);
-            // sub-row intervals of this tile row (unrolled to the largest tile height: registers)
+            // sub-row intervals of this tile row (unrolled: registers)
 #pragma unroll
-            for (int sy = 0; sy < 8; ++sy) {
+            for (int sy = 0; sy < SR; ++sy) {
                 L[sy] = 1.f; R[sy] = 0.f;
-                if (sy < sub_rows) {
-                    const int ry = row * P.tile_h + sy * 4;
-                    const int py0 = max(ry, bx.z), py1 = min(ry + 3, bx.w);
-                    float l = (float)bx.x + 0.5f, rr = (float)bx.y + 0.5f;
-                    bool ok = py0 <= py1;
-                    if (ok && P.exact_tile_test) {
-                        float bl, br;
-                        ok = band_interval(a.x, a.y, a.z, a.w, e, (float)py0 + 0.5f, (float)py1 + 0.5f, P.qbin, bl, br);
-                        l = fmaxf(l, bl);
-                        rr = fminf(rr, br);
-                    }
-                    if (ok) { L[sy] = l; R[sy] = rr; }
+                const int ry = row * (4 * SR) + sy * 4;
+                const int py0 = max(ry, bx.z), py1 = min(ry + 3, bx.w);
+                float l = (float)bx.x + 0.5f, rr = (float)bx.y + 0.5f;
+                bool ok = py0 <= py1;
+                if (ok && P.exact_tile_test) {
+                    float bl, br;
+                    ok = band_interval(a.x, a.y, a.z, a.w, e, (float)py0 + 0.5f, (float)py1 + 0.5f, P.qbin, bl, br);
+                    l = fmaxf(l, bl);
+                    rr = fminf(rr, br);
                 }
+                if (ok) { L[sy] = l; R[sy] = rr; }
             }
             for (int ti = 0; ti < nrun; ++ti) {
                 const int tx = t0 + ti;
-                const uint32_t sub = row_mask_any(L, R, tx, P);
+                const uint32_t sub = row_mask<SR, SC>(L, R, tx, 8 * SC);
                 const uint32_t pos = first + (uint32_t)ti;
                 if (pos < end) {
                     tkeys[pos] = (tile_row + (uint32_t)tx) | (sub << kTileBits);
@@ -313,7 +297,21 @@ void launch_pairs(const Launch& L, const ViewDesc* views, int K, const uint32_t*
     if (n == 0) return;
     const uint32_t warps = (n + 31) / 32;
     const uint32_t blocks = (warps + kPairWarps - 1) / kPairWarps;
-    k_pairs<<<blocks, kPairWarps * 32, 0, L.stream>>>(views, K, order, poff, records, info, n, d_n, P, tkeys, tvals, cap);
+    // one instantiation per tile shape (sub-tile rows x columns; at most 8 sub-tiles)
+    auto kern = k_pairs<1, 1>;
+    switch ((P.tile_h >> 2) * 16 + (P.tile_w >> 3)) {
+        case 1 * 16 + 2: kern = k_pairs<1, 2>; break;
+        case 1 * 16 + 4: kern = k_pairs<1, 4>; break;
+        case 1 * 16 + 8: kern = k_pairs<1, 8>; break;
+        case 2 * 16 + 1: kern = k_pairs<2, 1>; break;
+        case 2 * 16 + 2: kern = k_pairs<2, 2>; break;
+        case 2 * 16 + 4: kern = k_pairs<2, 4>; break;
+        case 4 * 16 + 1: kern = k_pairs<4, 1>; break;
+        case 4 * 16 + 2: kern = k_pairs<4, 2>; break;
+        case 8 * 16 + 1: kern = k_pairs<8, 1>; break;
+        default: break;
+    }
+    kern<<<blocks, kPairWarps * 32, 0, L.stream>>>(views, K, order, poff, records, info, n, d_n, P, tkeys, tvals, cap);
     ++*L.launches;
 }
 
