@@ -47,9 +47,9 @@ PROJ_OPS, SH3_OPS, CULL_OPS = 200, 90, 35
 # read, 236 B of attribute gradients accumulated and 8 B of identity.
 PROJECT_BWD_BYTES = 40 + 236 + 236 + 8
 # DRAM bytes (read + write) per launch on the full workload, from a one-pass ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum) of the full launch.  Set to
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the full launch: 1005.0 + 754.6 MB.  Set to
 # None whenever the kernel changes after its capture.
-TRAFFIC = {"composite": None}
+TRAFFIC = {"composite": 1.7596e9}
 # FP32 operations per (voxel, view) of the TSDF fusion: camera-space point (9 FMA), reciprocal,
 # projection (4), bounds (4 compares), coverage test, normalised depth (2), sdf, truncation,
 # clamp (2), running average (3), weight update (2)
