@@ -126,7 +126,10 @@ typedef struct dgs_options {
                                    or backward are told that every view group holds half the records
                                    it does, so the bounds check on tile-list entries fails
                                    (DGS_ERR_CUDA naming the check) while every access it lets
-                                   through stays inside the records written */
+                                   through stays inside the records written; 4: not a fault -- the
+                                   depth sort takes each instance's view from a separate array even
+                                   where it fits in the instance numbers' high bits (the form of
+                                   view groups too large for that), with identical results */
     int32_t keep_lists;         /* 1 = a render of at most two view groups -- eager, or a graph
                                    replay (not the call that captures) -- keeps its tile lists,
                                    records and device tables on the context, and a

@@ -298,7 +298,7 @@ int check_options(const dgs_options* o, std::string& why) {
     if (o->views_per_group < 0) { why = "views_per_group"; return 0; }
     if (o->spin_limit_us < 0) { why = "spin_limit_us"; return 0; }
     if (o->check_binning < 0 || o->check_binning > 1) { why = "check_binning"; return 0; }
-    if (o->test_fault < 0 || o->test_fault > 3) { why = "test_fault"; return 0; }
+    if (o->test_fault < 0 || o->test_fault > 4) { why = "test_fault"; return 0; }
     if (o->test_fault == 3 && !kDebugChecks) { why = "test_fault 3 (needs a DGS_DEBUG build)"; return 0; }
     if (o->keep_lists < 0 || o->keep_lists > 1) { why = "keep_lists"; return 0; }
     return 1;
@@ -837,7 +837,9 @@ void enqueue_lists(dgs_ctx* ctx, ListBufs& lb, const Batch& B, const Launch& L, 
     // the depth sort's view key: packed into the instance numbers where both fit in 32 bits
     ViewKey vk;
     vk.bits = bits_for((uint64_t)(v1 - v0));
-    if (vk.bits > 0 && bits_for((uint64_t)n_inst) + vk.bits <= 32) vk.vshift = 32 - vk.bits;
+    // (test_fault 4: the gathered form, as for groups whose numbers leave no room)
+    if (vk.bits > 0 && bits_for((uint64_t)n_inst) + vk.bits <= 32 && ctx->opt.test_fault != 4)
+        vk.vshift = 32 - vk.bits;
     vk.vig = vk.bits > 0 && !vk.vshift ? u32(lb.vig) : nullptr;
     vk.inst_off = B.d_inst_off;
     vk.view_tab = B.d_viewtab;

@@ -7,20 +7,23 @@
 // Two warps per block (two 8x4 sub-tiles of one tile), one thread per pixel.  A pixel stops at the
 // first Gaussian that would drive its transmittance below t_min (that Gaussian is not
 // composited); a warp stops once all of its pixels have.
+#include <algorithm>
+
 #include "dgs_internal.cuh"
 
 namespace dgs {
 namespace {
 
-// Thread = 4 consecutive sorted keys (one 16-byte load); a run starts where the key's tile
-// differs from the one before and ends where it differs from the one after.  A key names
+// Thread = 4 consecutive sorted keys at a time (one 16-byte load), grid-stride over the live
+// keys (the grid is sized for the capacity, at most a few waves); a run starts where the key's
+// tile differs from the one before and ends where it differs from the one after.  A key names
 // (view in group, tile in view); its tile in the group is the view's first tile + tile in view.
 __global__ void k_ranges(const uint32_t* __restrict__ keys, uint32_t n, const uint32_t* __restrict__ d_n,
                          uint2* __restrict__ ranges, int n_tiles, const ViewDesc* __restrict__ views, int v0, int nv,
                          int tile0, int tbits) {
-    const uint32_t i4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4u;
     if (d_n) n = min(n, *d_n);
-    if (i4 >= n) return;
+    const uint32_t stride = gridDim.x * blockDim.x * 4u;
+    for (uint32_t i4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4u; i4 < n; i4 += stride) {
     uint32_t k[6];                                  // k[0] = key before, k[5] = key after
     if (i4 + 4 <= n) {
         const uint4 q = *reinterpret_cast<const uint4*>(keys + i4);
@@ -46,6 +49,7 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, uint32_t n, const ui
         if (gt >= (uint32_t)n_tiles) continue;      // (only keys of a sort that gave up waiting)
         if (first) ranges[gt].x = i;
         if (last) ranges[gt].y = i + 1;
+    }
     }
 }
 
@@ -288,7 +292,8 @@ void launch_ranges(const Launch& L, const uint32_t* keys, uint32_t n, uint2* ran
     cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, L.stream);
     if (n == 0) return;
     const uint32_t threads = (n + 3) / 4;
-    k_ranges<<<(threads + 255) / 256, 256, 0, L.stream>>>(keys, n, d_n, ranges, n_tiles, views, (int)P.view0, nv,
+    const uint32_t blocks = std::min<uint32_t>((threads + 255) / 256, sm_count() * 8u);
+    k_ranges<<<blocks, 256, 0, L.stream>>>(keys, n, d_n, ranges, n_tiles, views, (int)P.view0, nv,
                                                           P.tile0, P.tbits);
     ++*L.launches;
 }

@@ -622,5 +622,7 @@ void launch_pose_twist(const Launch& L, const float* poses, const float* grads, 
 
 size_t sort_status_words(uint32_t n);
 int sort_passes(int key_bits);
+// Streaming multiprocessors of the current device (read once per process and device).
+uint32_t sm_count();
 
 }  // namespace dgs

@@ -340,5 +340,5 @@ def test_bounds_fault_hook_needs_the_debug_build(lib):
     assert lib.dgs_context_create(C.byref(h), C.byref(o)) == D.DGS_ERR_INVALID_ARG
     assert dbg.dgs_context_create(C.byref(h), C.byref(o)) == D.DGS_OK
     dbg.dgs_context_destroy(h)
-    o.test_fault = 4
+    o.test_fault = 5
     assert dbg.dgs_context_create(C.byref(h), C.byref(o)) == D.DGS_ERR_INVALID_ARG

@@ -125,3 +125,29 @@ def test_corrupted_node_pose_is_reported_then_the_context_renders_again(mode, ba
     for a, b in zip(ref, out):
         assert np.array_equal(a, b)
     r.close()
+
+
+@pytest.mark.parametrize("mode", ["batched", "graph"])
+def test_gathered_view_key_renders_what_the_packed_one_does(mode):
+    """The depth sort's view key rides in the instance numbers' high bits where both fit in 32
+    bits, else it is gathered from a per-instance view array (large view groups).  test_fault = 4
+    forces the gathered form on a small batch: the tile lists (checked on the host in the eager
+    render) and the images must equal the packed form's bit for bit, and the image the oracle's."""
+    from paper_2507_21981_gb300.render import DeviceScene, Renderer
+    sc = S.config2(seed=5, n_envs=6, n_bg=30_000, n_obj=1_000, width=160, height=120, f=125.0)
+    ds = DeviceScene(sc, device="cuda:0", spatial_order=True)
+    outs = []
+    for tf in (0, 4):
+        kw = {"check_binning": 1} if mode == "batched" else {}
+        r = Renderer(mode=mode, test_fault=tf, **kw)
+        out = r.render(ds)
+        if mode == "graph":
+            out = r.render(ds)                  # a replay of the captured sequence
+        torch.cuda.synchronize()
+        if mode == "batched":
+            assert r.stats()["n_groups"] == 1 and r.stats()["n_pairs"] > 0
+        outs.append([t.cpu().numpy() for t in out])
+        r.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    _check_oracle(ds.scene, ds, [torch.as_tensor(x) for x in outs[1]], v=3)
