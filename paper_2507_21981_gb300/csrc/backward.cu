@@ -142,56 +142,54 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_bwd(const ViewDes
         const uint32_t m = __ballot_sync(0xffffffffu, rel);
         if (m == 0) continue;
         if (rel) {
+            // staged as the forward stages them: the threshold and the scaled qa beside the raw
+            // coefficients that the gradients use
             const Record* r = rec + idx;
             const int pos = __popc(m & lt);
-            sr0[pos] = r->r0; sr1[pos] = r->r1; sr2[pos] = r->r2;
+            const float4 a = r->r0, q = r->r1, col = r->r2;
+            sr0[pos] = a;
+            sr1[pos] = make_float4(q.x, q.y, q.z, reach_threshold(P, a.z));
+            sr2[pos] = make_float4(col.x, col.y, col.z, kHalfLog2e * q.x);
             s_idx[bw][pos] = idx;
         }
         __syncwarp();
         const int n = __popc(m);
         for (int k = 0; k < n; ++k) {
+            // the forward pass's decisions, without branches: same staged products, same exponent
+            const float4 g0 = sr0[k], g1 = sr1[k], g2 = sr2[k];
+            const float dx = fx - g0.x, dy = fy - g0.y;
+            float t;
+            const float pe = pixel_exponent(g2.w, g1.y, kHalfLog2e * g1.z, dx, dy, t);
+            const bool hit = !done && pe >= g1.w;
+            const float ex = fast_exp2(pe);
+            const float a_raw = g0.z * ex;
+            const float alpha = fminf(P.alpha_max, a_raw);
+            const float Tn = fmaf(-alpha, T, T);       // T (1 - alpha), one rounding
+            const bool stop = hit && Tn < P.t_min;
+            const bool contrib = hit && !stop;
+            done = done || stop;
             float g[G_N];
 #pragma unroll
             for (int e = 0; e < G_N; ++e) g[e] = 0.f;
-            bool contrib = false;
-            if (!done) {
-                const float4 g0 = sr0[k], g1 = sr1[k];
-                const float dx = fx - g0.x, dy = fy - g0.y;
-                float t;
-                // the forward pass's decisions: same staged products, same exponent
-                const float pe = pixel_exponent(kHalfLog2e * g1.x, g1.y, kHalfLog2e * g1.z, dx, dy, t);
-                if (pe >= reach_threshold(P, g0.z)) {
-                    const float ex = fast_exp2(pe);
-                    const float a_raw = g0.z * ex;
-                    const float alpha = fminf(P.alpha_max, a_raw);
-                    {
-                        const float Tn = fmaf(-alpha, T, T);   // T (1 - alpha), one rounding
-                        if (Tn < P.t_min) {
-                            done = true;
-                        } else {
-                            contrib = true;
-                            const float wgt = alpha * T;
-                            const float4 g2 = sr2[k];
-                            P0 = fmaf(wgt, g2.x, P0); P1 = fmaf(wgt, g2.y, P1); P2 = fmaf(wgt, g2.z, P2);
-                            PD = fmaf(wgt, g0.w, PD);
-                            const float iTn = __fdividef(1.f, Tn);   // Tn >= t_min > 0
-                            const float S0 = (Co0 - P0) * iTn, S1 = (Co1 - P1) * iTn, S2 = (Co2 - P2) * iTn;
-                            const float SD = (Do - PD) * iTn;
-                            const float dal = T * (gC0 * (g2.x - S0) + gC1 * (g2.y - S1) + gC2 * (g2.z - S2) + gD * (g0.w - SD));
-                            g[G_R] = wgt * gC0; g[G_G] = wgt * gC1; g[G_B] = wgt * gC2; g[G_Z] = wgt * gD;
-                            if (!(a_raw > P.alpha_max)) {
-                                g[G_OP] = dal * ex;
-                                const float dq = -0.5f * alpha * dal;
-                                g[G_QA] = dq * t * t;
-                                g[G_QB] = dq * 2.f * g1.x * t * dy;
-                                g[G_QC] = dq * dy * dy;
-                                g[G_U] = dq * (-2.f * g1.x * t);
-                                g[G_V] = dq * (-2.f * fmaf(g1.x * t, g1.y, g1.z * dy));
-                            }
-                            T = Tn;
-                        }
-                    }
+            if (contrib) {
+                const float wgt = alpha * T;
+                P0 = fmaf(wgt, g2.x, P0); P1 = fmaf(wgt, g2.y, P1); P2 = fmaf(wgt, g2.z, P2);
+                PD = fmaf(wgt, g0.w, PD);
+                const float iTn = __fdividef(1.f, Tn);   // Tn >= t_min > 0
+                const float S0 = (Co0 - P0) * iTn, S1 = (Co1 - P1) * iTn, S2 = (Co2 - P2) * iTn;
+                const float SD = (Do - PD) * iTn;
+                const float dal = T * (gC0 * (g2.x - S0) + gC1 * (g2.y - S1) + gC2 * (g2.z - S2) + gD * (g0.w - SD));
+                g[G_R] = wgt * gC0; g[G_G] = wgt * gC1; g[G_B] = wgt * gC2; g[G_Z] = wgt * gD;
+                if (!(a_raw > P.alpha_max)) {
+                    g[G_OP] = dal * ex;
+                    const float dq = -0.5f * alpha * dal;
+                    g[G_QA] = dq * t * t;
+                    g[G_QB] = dq * 2.f * g1.x * t * dy;
+                    g[G_QC] = dq * dy * dy;
+                    g[G_U] = dq * (-2.f * g1.x * t);
+                    g[G_V] = dq * (-2.f * fmaf(g1.x * t, g1.y, g1.z * dy));
                 }
+                T = Tn;
             }
             if (__ballot_sync(0xffffffffu, contrib) == 0) continue;
             const uint32_t r = s_idx[bw][k];
