@@ -763,8 +763,8 @@ def main():
     # every step uploads its poses from pinned host memory and reads its RGB + depth back into
     # pinned host memory; the read-back of step i runs on a copy stream while step i + 1
     # renders (two output buffers, each with its own graph-mode context: a replay reads nothing
-    # back before its end, so no small read-back of the render queues behind the large copy),
-    # the copy split in chunks; the timed region ends after the last read-back
+    # back before its end, so no small read-back of the render queues behind the large copy);
+    # the timed region ends after the last read-back
     poses_host = torch.from_numpy(np.ascontiguousarray(sc.node_poses, np.float32).reshape(ds.n_envs, ds.max_nodes, 12)).pin_memory()
     host_out = [(torch.empty((px_per_step, 3), dtype=torch.float32).pin_memory(),
                  torch.empty((px_per_step,), dtype=torch.float32).pin_memory()) for _ in range(2)]
@@ -775,7 +775,7 @@ def main():
         e.record(copy_stream)
     re2e = [Renderer(mode="graph", tile=tile), Renderer(mode="graph", tile=tile)]
     dposes = torch.empty_like(ds.node_poses)
-    n_chunks = 4
+    n_chunks = 1                                   # one copy per tensor (measured: fewer host calls between steps)
     # per step: the render's and the read-back's spans on their streams (events only)
     spans = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.warmup + args.steps)]
 

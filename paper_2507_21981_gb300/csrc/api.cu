@@ -860,6 +860,7 @@ void enqueue_lists(dgs_ctx* ctx, ListBufs& lb, const Batch& B, const Launch& L, 
     SortCtl depth_ctl = ctl, tile_ctl = ctl;
     if (ctx->opt.test_fault == 1) depth_ctl.mute_part = 1;
     tile_ctl.runs = true;   // an instance's pairs are consecutive tiles of one view
+    depth_ctl.runs = true;  // emission order (view by view, Z-ordered nodes) keeps the high depth digits in runs
     // instances by depth, then by view (most significant, through the values): each view's
     // instances in depth order, so that every instance's pairs come out view by view
     launch_sort(L, u32(lb.dkey0), u32(lb.ival0), u32(lb.dkey1), u32(lb.ival1), n_inst, kZBits, u32(lb.hist),

@@ -207,8 +207,10 @@ extern "C" int dgs_render_noalloc(const dgs_options* opt, const dgs_node* nodes,
     launch_emit(L, dtype_mask, d_nodes, n_nodes, d_views, d_vnodes, K, d_nv, d_nvoff, (int)chunk_total, P, 0, V, true,
                 nullptr, 0, d_counts, d_inst_off, 0u, d_rec, d_info, d_dk0, d_iv0, d_ntile, vk.vig ? d_vig : nullptr);
     uint32_t *dk, *order, *tk, *tv;
+    SortCtl depth_ctl;
+    depth_ctl.runs = true;
     launch_sort(L, d_dk0, d_iv0, d_dk1, d_iv1, (uint32_t)n_vis, kZBits, d_hist, d_status, d_cnt, d_err, &dk, &order,
-                nullptr, SortCtl{}, &vk);
+                nullptr, depth_ctl, &vk);
     launch_tile_scan(L, order, d_ntile, (uint32_t)n_vis, nullptr, d_poff, d_tparts, (uint32_t)n_pairs, d_total, d_err);
     launch_pairs(L, d_views, K, order, d_poff, d_rec, d_info, (uint32_t)n_vis, nullptr, P, d_k0, d_v0, (uint32_t)n_pairs);
     SortCtl tile_ctl;
