@@ -270,8 +270,8 @@ __device__ __forceinline__ ChunkBound chunk_bound(const Gauss& g, bool valid) {
     return b;
 }
 
-// Conservative per-view cull of a whole chunk: false only if may_be_visible() is false for
-// every Gaussian of the chunk.  may_be_visible() keeps a Gaussian only if z > z_near and its
+// Conservative per-view cull of a whole chunk: false only if conservative_tiles() is 0 for
+// every Gaussian of the chunk.  conservative_tiles() keeps a Gaussian only if z > z_near and its
 // box reaches the image, e.g. u + hx - 1/2 >= 0 on the left, with
 //   hx <= k_x (fx / z) sigma + m,   k_x = sqrt(1.02 qbin (1 + limx^2)),  m = sqrt(qbin lowpass) + 1e-3
 // (sqrt(a + b) <= sqrt(a) + sqrt(b)).  Multiplied by z > 0 the left condition becomes the
