@@ -230,17 +230,49 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint32_t* __rest
             }
         }
     }
-    // decoupled look-back over earlier partitions, all owned digits at once; partition
-    // mute_part (a test of the bounded wait, never a real partition index by default) publishes
-    // nothing, so the partitions after it wait for it until spin_ns runs out
+    // publish this partition's digit counts at once (the inclusive prefix for partition 0);
+    // partition mute_part (a test of the bounded wait, never a real partition index by
+    // default) publishes nothing, so the partitions after it wait for it until spin_ns runs out
     const bool publish = part != mute_part;
-    if (part == 0) {
 #pragma unroll
-        for (int q = 0; q < DPT; ++q) {
-            const int d = tid + q * kThreads;
-            if (d < R && publish) st_relaxed(&status[d], kFlagInc | total[q]);
+    for (int q = 0; q < DPT; ++q) {
+        const int d = tid + q * kThreads;
+        if (d < R && publish) st_relaxed(&status[(size_t)part * R + d], (part == 0 ? kFlagInc : kFlagAgg) | total[q]);
+    }
+    // block exclusive scan of the digit totals in digit order -> local digit offsets; slab q
+    // holds digits [q * 256, q * 256 + 256)
+    uint32_t carry = 0;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+        uint32_t x = total[q];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-    } else {
+        if (lane == 31) s_wsum[warp] = x;
+        __syncthreads();
+        uint32_t wpre = 0, slab = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            if (w < warp) wpre += s_wsum[w];
+            slab += s_wsum[w];
+        }
+        const int d = tid + q * kThreads;
+        if (d < R) s_dexcl[d] = carry + wpre + x - total[q];
+        carry += slab;
+        __syncthreads();
+    }
+    // local scatter: digit-major order inside the partition
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const uint32_t dj = (k[j] >> shift) & M;
+        const uint32_t pos = s_dexcl[dj] + s_whist[warp * R + dj] + rank[j];
+        s_keys[pos] = k[j];
+        s_vals[pos] = v[j];
+    }
+    // decoupled look-back over earlier partitions, all owned digits at once, after the local
+    // scatter: the partitions before this one have had that long to publish their prefixes
+    if (part > 0) {
         int64_t p[DPT];
         bool done[DPT];
 #pragma unroll
@@ -248,7 +280,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint32_t* __rest
             const int d = tid + q * kThreads;
             done[q] = d >= R;
             p[q] = (int64_t)part - 1;
-            if (d < R && publish) st_relaxed(&status[(size_t)part * R + d], kFlagAgg | total[q]);
         }
         uint64_t t0 = 0;
         uint32_t spins = 0;
@@ -292,37 +323,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint32_t* __rest
     for (int q = 0; q < DPT; ++q) {
         const int d = tid + q * kThreads;
         if (d < R) s_gbase[d] = digit_off[d] + excl[q];
-    }
-    // block exclusive scan of the digit totals in digit order -> local digit offsets; slab q
-    // holds digits [q * 256, q * 256 + 256)
-    uint32_t carry = 0;
-#pragma unroll
-    for (int q = 0; q < DPT; ++q) {
-        uint32_t x = total[q];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_wsum[warp] = x;
-        __syncthreads();
-        uint32_t wpre = 0, slab = 0;
-        for (int w = 0; w < kWarps; ++w) {
-            if (w < warp) wpre += s_wsum[w];
-            slab += s_wsum[w];
-        }
-        const int d = tid + q * kThreads;
-        if (d < R) s_dexcl[d] = carry + wpre + x - total[q];
-        carry += slab;
-        __syncthreads();
-    }
-    // local scatter: digit-major order inside the partition
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-        const uint32_t dj = (k[j] >> shift) & M;
-        const uint32_t pos = s_dexcl[dj] + s_whist[warp * R + dj] + rank[j];
-        s_keys[pos] = k[j];
-        s_vals[pos] = v[j];
     }
     __syncthreads();
 #pragma unroll 4
