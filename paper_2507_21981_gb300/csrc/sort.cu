@@ -2,20 +2,24 @@
 //
 // Sec. III-A: the 3DGS rasterizer orders the (tile, depth) pairs of every view with a fast
 // GPU sort before blending.  Here the order is built in two stable sorts of 32-bit keys: the
-// projected instances by depth key (28 bits), then the (tile, instance) pairs -- emitted in
-// that depth order -- by tile.  Stability carries the depth order, and the id order of equal
-// depths, into every tile's run.
+// projected instances by depth key (28 bits) and then by their view in the view group (a more
+// significant key carried by the values), then the (tile, instance) pairs -- emitted in that
+// order -- by their tile within the view.  Stability carries the depth order, and the id order
+// of equal depths, into every (view, tile) run.
 //
 // Structure: one upfront pass builds the histograms of every digit at once; then each digit is
 // one kernel in which a block takes the next 3072-key partition from an atomic counter, ranks
-// its keys by digit inside the block (per-bit warp ballots + per-warp counters), and finds its
+// its keys by digit inside the block (per-bit warp ballots + per-warp counters), publishes its
+// digit counts, scatters its keys into shared memory in digit order, and only then finds its
 // global offset per digit by decoupled look-back over the partitions before it (status word =
-// 2-bit flag | 30-bit count).  Measured on the benchmark's key sets (17.9M depth keys, 59.7M tile
-// keys), the ballot ranking with 12 keys per thread at 4 blocks per SM sorts 13-17 % faster than
-// warp-match ranking with 16 keys at 3 blocks; either change alone gains nothing.  Digits are D = ceil(bits / passes) bits wide with passes =
-// ceil(bits / 8), the last pass taking the remaining bits so that exactly the requested key
-// bits are sorted (bits above them keep their input order: the tile keys hold the view there,
-// ordered by the depth sort before); measured on this path, wider digits (fewer passes) lose what they save to
+// 2-bit flag | 30-bit count), which have had that long to publish their prefixes.  Measured on
+// the benchmark's key sets (17.9M depth keys, 59.7M tile keys), the ballot ranking with 12 keys
+// per thread at 4 blocks per SM sorts 13-17 % faster than warp-match ranking with 16 keys at 3
+// blocks (either change alone gains nothing), and the late look-back 4 % faster than one right
+// after the ranking.  Digits are D = ceil(bits / passes) bits wide with passes = ceil(bits / 8),
+// the last pass taking the remaining bits so that exactly the requested key bits are sorted
+// (bits above them keep their input order: the tile keys hold the view there, ordered by the
+// depth sort before); measured on this path, wider digits (fewer passes) lose what they save to
 // the scatter, whose runs per partition shrink to a few keys.  Look-back spins are bounded by
 // a wall-clock limit (SortCtl::spin_ns, 1 s by default); on expiry the kernel sets
 // kErrTimeout and finishes: its output is then not a permutation of the input, the kernels
