@@ -610,7 +610,7 @@ __device__ __forceinline__ void stage_geometry(const NodeDesc& nd, int c, int la
     __syncwarp();
 }
 
-constexpr int kCountWarps = 8;
+constexpr int kCountWarps = 4;
 constexpr int kEmitWarps = 4;
 
 template <int DT>
