@@ -248,8 +248,35 @@ __device__ __forceinline__ int node_of_gid(const NodeDesc* nodes, int n_nodes, u
     return lo;
 }
 
+// Colour adjoint of one instance at SH degree DEG, known at compile time so that the basis and
+// its gradient stay in registers: rgb = max(0, sum_c Y_c(d) sh_c + 1/2) per channel; adds the
+// SH coefficients' gradients (where the channel is not clamped) and the direction gradient gd.
+template <int DEG, int DT>
+__device__ __forceinline__ void sh_colour_bwd(const NodeDesc& nd, int64_t i, float dx, float dy, float dz,
+                                              const float (&gcol)[3], float* gsh, float (&gd)[3]) {
+    constexpr int NC = (DEG + 1) * (DEG + 1);
+    float Y[16], dY[16][3];
+    sh_basis_grad(DEG, dx, dy, dz, Y, dY);
+    const int64_t sb = i * NC * 3;
+    float raw[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) raw[ch] = fmaf(Y[c], ld_attr<DT>(nd.sh, sb + c * 3 + ch), raw[ch]);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            if (!(raw[ch] > 0.f) || gcol[ch] == 0.f) continue;
+            if (gsh) atomicAdd(gsh + sb + c * 3 + ch, gcol[ch] * Y[c]);
+            const float cf = gcol[ch] * ld_attr<DT>(nd.sh, sb + c * 3 + ch);
+            gd[0] = fmaf(cf, dY[c][0], gd[0]); gd[1] = fmaf(cf, dY[c][1], gd[1]); gd[2] = fmaf(cf, dY[c][2], gd[2]);
+        }
+    }
+}
+
 template <int DT>
-__global__ void __launch_bounds__(128) k_project_bwd(const NodeDesc* __restrict__ nodes, int n_nodes,
+__global__ void __launch_bounds__(128, 5) k_project_bwd(const NodeDesc* __restrict__ nodes, int n_nodes,
                                                      const ViewDesc* __restrict__ views,
                                                      const VNode* __restrict__ vnodes, int K,
                                                      const float* __restrict__ node_poses,
@@ -338,25 +365,14 @@ __global__ void __launch_bounds__(128) k_project_bwd(const NodeDesc* __restrict_
             float dx = mx - vn.o[0], dy = my - vn.o[1], dz = mz - vn.o[2];
             const float dlen_inv = rsqrtf(dx * dx + dy * dy + dz * dz);
             dx *= dlen_inv; dy *= dlen_inv; dz *= dlen_inv;
-            float Y[16], dY[16][3];
-            sh_basis_grad(nd.deg, dx, dy, dz, Y, dY);
-            const int nc = (nd.deg + 1) * (nd.deg + 1);
-            const int64_t sb = i * nc * 3;
             const float gcol[3] = {gcr, gcg, gcb};
-            float raw[3] = {0.5f, 0.5f, 0.5f};
-            for (int c = 0; c < nc; ++c)
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) raw[ch] = fmaf(Y[c], ld_attr<DT>(nd.sh, sb + c * 3 + ch), raw[ch]);
             float gd[3] = {0.f, 0.f, 0.f};
             float* gsh = grads[k].sh;
-            for (int c = 0; c < nc; ++c) {
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    if (!(raw[ch] > 0.f) || gcol[ch] == 0.f) continue;
-                    if (gsh) atomicAdd(gsh + sb + c * 3 + ch, gcol[ch] * Y[c]);
-                    const float cf = gcol[ch] * ld_attr<DT>(nd.sh, sb + c * 3 + ch);
-                    gd[0] = fmaf(cf, dY[c][0], gd[0]); gd[1] = fmaf(cf, dY[c][1], gd[1]); gd[2] = fmaf(cf, dY[c][2], gd[2]);
-                }
+            switch (nd.deg) {
+                case 0: sh_colour_bwd<0, DT>(nd, i, dx, dy, dz, gcol, gsh, gd); break;
+                case 1: sh_colour_bwd<1, DT>(nd, i, dx, dy, dz, gcol, gsh, gd); break;
+                case 2: sh_colour_bwd<2, DT>(nd, i, dx, dy, dz, gcol, gsh, gd); break;
+                default: sh_colour_bwd<3, DT>(nd, i, dx, dy, dz, gcol, gsh, gd); break;
             }
             const float dd = gd[0] * dx + gd[1] * dy + gd[2] * dz;
             const float gdir[3] = {(gd[0] - dx * dd) * dlen_inv, (gd[1] - dy * dd) * dlen_inv, (gd[2] - dz * dd) * dlen_inv};
