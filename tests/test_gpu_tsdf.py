@@ -105,3 +105,17 @@ def test_full_grid_block_sampled():
                               100.0, 0.5, cams, Dv, Av)
     # the block's voxel centres differ from the grid's by the rounding of the shifted origin
     _check(gF[blk], gW[blk], rF, rW, amb, min_seen=500)
+
+
+def test_sphere_grid_whose_rows_are_not_a_multiple_of_four():
+    """Rows of nx = 47 voxels take the one-voxel-per-thread kernel (the four-voxel kernel needs
+    nx a multiple of 4); both must match the oracle."""
+    c = np.array([0.05, 0.1, -0.1])
+    cams, Dv, Av = S.sphere_depth_views(c, 0.2, n_views=8, width=96, height=80, f=90.0, dist=1.0, seed=7)
+    nz, ny, nx, vox = 40, 44, 47, 0.5 / 46
+    origin = (c - 0.25).astype(np.float32)
+    F0, W0 = np.zeros((nz, ny, nx)), np.zeros((nz, ny, nx))
+    gF, gW = _gpu(F0, W0, origin, vox, 0.04, 100.0, 0.5, cams, Dv.reshape(-1), Av.reshape(-1))
+    rF, rW, amb = T.integrate(F0, W0, origin.astype(np.float64), np.float32(vox), np.float32(0.04), 100.0, 0.5, cams,
+                              Dv, Av)
+    _check(gF, gW, rF, rW, amb, min_seen=500)
