@@ -3,8 +3,9 @@
 // that follows is not part of this library).
 //
 // A pre-pass writes every pixel's normalised depth d = D / A (NaN where A < min_alpha) into a
-// packed array.  Then one thread per voxel, x fastest (coalesced field reads and writes); each
-// thread loops over the views in order: project the voxel centre, read d at the pixel holding
+// packed array.  Then one thread per four consecutive voxels along x (one per voxel where the
+// rows are not a multiple of four), x fastest (coalesced field reads and writes); each voxel
+// takes the views in order: project the voxel centre, read d at the pixel holding
 // the projection, sdf = d - z, skip when sdf < -trunc, f = min(1, sdf / trunc),
 // F <- (W F + f) / (W + 1), W <- min(W + 1, max_weight).
 // The field is read and written once per call whatever the number of views, so a call with
