@@ -261,9 +261,18 @@ __global__ void __launch_bounds__(kTraceThreads) k_lidar_trace(const LidarTreeDe
                         if (k >= tr.P) {
                             const int64_t g0 = (k - tr.P) * kLeaf;
                             const int64_t g1 = min(g0 + kLeaf, tr.n);
+                            // the next Gaussian's record is loaded while this one is tested
+                            float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0, n2 = n0, n3 = n0;
+                            if (g0 < g1) {
+                                n0 = __ldg(tr.rec + 4 * g0); n1 = __ldg(tr.rec + 4 * g0 + 1);
+                                n2 = __ldg(tr.rec + 4 * g0 + 2); n3 = __ldg(tr.rec + 4 * g0 + 3);
+                            }
                             for (int64_t g = g0; g < g1; ++g) {
-                                const float4 r0 = __ldg(tr.rec + 4 * g), r1 = __ldg(tr.rec + 4 * g + 1),
-                                             r2 = __ldg(tr.rec + 4 * g + 2), r3 = __ldg(tr.rec + 4 * g + 3);
+                                const float4 r0 = n0, r1 = n1, r2 = n2, r3 = n3;
+                                if (g + 1 < g1) {
+                                    n0 = __ldg(tr.rec + 4 * (g + 1)); n1 = __ldg(tr.rec + 4 * (g + 1) + 1);
+                                    n2 = __ldg(tr.rec + 4 * (g + 1) + 2); n3 = __ldg(tr.rec + 4 * (g + 1) + 3);
+                                }
                                 if (!mine) continue;
                                 const float v0 = o[0] - r0.x, v1 = o[1] - r0.y, v2 = o[2] - r0.z;
                                 {
