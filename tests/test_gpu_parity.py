@@ -73,6 +73,21 @@ def test_batched_equals_plain_bitwise():
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("test_fault", [0, 4])
+def test_group_of_more_than_256_views_equals_plain_bitwise(test_fault):
+    """150 envs x 2 cameras of 64x48 in one view group: the view key of the depth sort has 9
+    bits and takes two passes (5 + 4 bits), carried in the instance numbers' high bits or, with
+    test_fault 4, gathered from the view array.  The batched render must equal the plain
+    per-view render (one view per group, no view passes) bit for bit, and match the oracle."""
+    sc = S.config2(seed=6, n_envs=150, n_bg=20_000, n_obj=500, width=64, height=48, f=50.0)
+    ds, a, st, _ = _render(sc, "batched", views_per_group=300, test_fault=test_fault)
+    assert st["n_views"] == 300 and st["n_groups"] == 1 and st["n_pairs"] > 0
+    _, b, _, _ = _render(sc, "plain")
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    _check_views(sc, ds, a, [0, 157, 299])
+
+
 @pytest.mark.parametrize("spatial_order", [False, True])
 def test_config3_reduced_ragged_views(spatial_order):
     sc = S.config3(seed=1, n_envs=6, n_bg=30_000, n_assets=8, asset_lo=500, asset_hi=4_000, max_nodes=4,
