@@ -390,16 +390,6 @@ __device__ __forceinline__ int find_node(const NodeDesc* nodes, int n_nodes, int
     return lo;
 }
 
-__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x) {
-    const uint32_t lane = lane_id();
-    uint32_t s = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-        if (lane >= (uint32_t)o) s += y;
-    }
-    return s - x;
-}
 
 // ------------------------------------------------------------------ count and emit passes
 // A warp owns a chunk of 32 consecutive Gaussians of one node and walks the (view, slot)
@@ -728,12 +718,28 @@ __device__ __forceinline__ void block_excl_scan2(uint64_t& a, uint64_t& b, uint6
     __syncthreads();
 }
 
+// The block's kScanTile entries are read warp-striped (coalesced) into shared memory, and each
+// thread then takes its kScanItems consecutive entries from there; one pad entry per 16 keeps
+// both access patterns free of bank conflicts.
+constexpr int kScanPadded = kScanTile + kScanTile / 16;
+__device__ __forceinline__ int scan_slot(int k) { return k + (k >> 4); }
+__device__ __forceinline__ void load_tile_counts(const uint2* __restrict__ counts, int64_t n, uint2* s_c) {
+    const int64_t b0 = (int64_t)blockIdx.x * kScanTile;
+#pragma unroll 4
+    for (int j = 0; j < kScanItems; ++j) {
+        const int k = j * kScanThreads + threadIdx.x;
+        s_c[scan_slot(k)] = b0 + k < n ? counts[b0 + k] : make_uint2(0u, 0u);
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kScanThreads) k_scan_partial(const uint2* __restrict__ counts, int64_t n, ulonglong2* parts) {
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    __shared__ uint2 s_c[kScanPadded];
+    load_tile_counts(counts, n, s_c);
     uint64_t a = 0, b = 0;
     for (int j = 0; j < kScanItems; ++j) {
-        const int64_t i = base + j;
-        if (i < n) { const uint2 c = counts[i]; a += __popc(c.x); b += c.y; }
+        const uint2 c = s_c[scan_slot(threadIdx.x * kScanItems + j)];
+        a += __popc(c.x); b += c.y;
     }
     uint64_t ta, tb;
     block_excl_scan2(a, b, ta, tb);
@@ -762,23 +768,46 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_parts(ulonglong2* parts, 
 __global__ void __launch_bounds__(kScanThreads) k_scan_final(const uint2* __restrict__ counts, int64_t n,
                                                             const ulonglong2* __restrict__ parts, uint32_t* inst_off,
                                                             uint64_t* pair_off) {
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    __shared__ uint2 s_c[kScanPadded];
+    load_tile_counts(counts, n, s_c);
     uint2 c[kScanItems];
     uint64_t a = 0, b = 0;
     for (int j = 0; j < kScanItems; ++j) {
-        const int64_t i = base + j;
-        c[j] = i < n ? counts[i] : make_uint2(0, 0);
+        c[j] = s_c[scan_slot(threadIdx.x * kScanItems + j)];
         a += __popc(c[j].x); b += c[j].y;
     }
     uint64_t ta, tb;
     block_excl_scan2(a, b, ta, tb);
     a += parts[blockIdx.x].x;
     b += parts[blockIdx.x].y;
+    // the offsets go back through shared memory so that the stores are warp-striped too; entry
+    // n, inside the tile or just past the last one, receives the totals
+    const int64_t b0 = (int64_t)blockIdx.x * kScanTile;
+    uint64_t* s_p = reinterpret_cast<uint64_t*>(s_c);
+    uint32_t* s_i = reinterpret_cast<uint32_t*>(s_c);
+    const uint64_t a0 = a;
+    __syncthreads();                            // every thread has read its counts
     for (int j = 0; j < kScanItems; ++j) {
-        const int64_t i = base + j;
-        if (i < n) { inst_off[i] = (uint32_t)a; pair_off[i] = b; }
-        if (i == n) { inst_off[i] = (uint32_t)a; pair_off[i] = b; }
-        a += __popc(c[j].x); b += c[j].y;
+        s_p[scan_slot(threadIdx.x * kScanItems + j)] = b;
+        b += c[j].y;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int j = 0; j < kScanItems; ++j) {
+        const int k = j * kScanThreads + threadIdx.x;
+        if (b0 + k <= n) pair_off[b0 + k] = s_p[scan_slot(k)];
+    }
+    __syncthreads();
+    a = a0;
+    for (int j = 0; j < kScanItems; ++j) {
+        s_i[scan_slot(threadIdx.x * kScanItems + j)] = (uint32_t)a;
+        a += __popc(c[j].x);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int j = 0; j < kScanItems; ++j) {
+        const int k = j * kScanThreads + threadIdx.x;
+        if (b0 + k <= n) inst_off[b0 + k] = s_i[scan_slot(k)];
     }
     if (n % kScanTile == 0 && blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) {
         inst_off[n] = (uint32_t)a; pair_off[n] = b;
