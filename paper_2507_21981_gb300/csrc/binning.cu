@@ -83,26 +83,37 @@ __global__ void __launch_bounds__(kScanThreads) k_tscan_parts(uint32_t* parts, u
     }
 }
 
-// poff[i] for i < n: thread t of block b scans 16 consecutive entries
+// poff[i] for i < n: thread t of block b scans the 16 consecutive entries from 16 t of its tile
 __global__ void __launch_bounds__(kScanThreads) k_tscan_final(const uint32_t* __restrict__ order,
                                                              const uint32_t* __restrict__ ntile, uint32_t n,
                                                              const uint32_t* __restrict__ d_n,
                                                              const uint32_t* __restrict__ parts, uint32_t* poff,
                                                              uint32_t* err) {
     __shared__ uint32_t s_w[kScanThreads / 32];
+    // the counts of the block's kScanTile instances, gathered warp-striped (coalesced order
+    // reads) into shared memory, one pad word per 16 against bank conflicts; each thread then
+    // scans its kScanItems consecutive counts, and the offsets go back the same way
+    __shared__ uint32_t s_v[kScanTile + kScanTile / 16];
+    auto slot = [](int k) { return k + (k >> 4); };
     if (sort_failed(err)) return;
     n = live(n, d_n);
     const uint32_t base = blockIdx.x * (uint32_t)kScanTile;
     if (base >= n) return;
-    const uint32_t i0 = base + threadIdx.x * kScanItems;
+#pragma unroll 4
+    for (int j = 0; j < kScanItems; ++j) {
+        const int k = j * kScanThreads + threadIdx.x;
+        uint32_t x = 0u;
+        if (base + k < n) {
+            const uint32_t r = order[base + k];
+            if (in_bounds(r, n, err, kSiteScanInstance)) x = ntile[r];
+        }
+        s_v[slot(k)] = x;
+    }
+    __syncthreads();
     uint32_t v[kScanItems], sum = 0;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
-        v[j] = 0u;
-        if (i0 + j < n) {
-            const uint32_t r = order[i0 + j];
-            if (in_bounds(r, n, err, kSiteScanInstance)) v[j] = ntile[r];
-        }
+        v[j] = s_v[slot(threadIdx.x * kScanItems + j)];
         sum += v[j];
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -118,8 +129,14 @@ __global__ void __launch_bounds__(kScanThreads) k_tscan_final(const uint32_t* __
     for (int w = 0; w < warp; ++w) run += s_w[w];
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
-        if (i0 + j < n) poff[i0 + j] = run;
+        s_v[slot(threadIdx.x * kScanItems + j)] = run;
         run += v[j];
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int j = 0; j < kScanItems; ++j) {
+        const int k = j * kScanThreads + threadIdx.x;
+        if (base + k < n) poff[base + k] = s_v[slot(k)];
     }
 }
 
