@@ -63,12 +63,13 @@ template <bool RUNS>
 __global__ void __launch_bounds__(kThreads) k_hist(const uint32_t* __restrict__ keys, uint32_t n,
                                                    const uint32_t* __restrict__ d_n, int passes, int D,
                                                    int last_bits, uint32_t* hist) {
-    __shared__ uint32_t sh[4 * kMaxR];
+    __shared__ uint32_t sh_all[kWarps][4 * kMaxR];   // one private histogram per warp
+    uint32_t* sh = sh_all[threadIdx.x >> 5];
     n = live_count(n, d_n);
     // every pass's digit is D bits but the last one's, last_bits (the key bits above are not sorted)
     const uint32_t R = 1u << D;
     auto dmask = [&](int p) { return p == passes - 1 ? (1u << last_bits) - 1u : R - 1u; };
-    for (int i = threadIdx.x; i < passes * (int)R; i += kThreads) sh[i] = 0;
+    for (int i = threadIdx.x; i < kWarps * 4 * kMaxR; i += kThreads) (&sh_all[0][0])[i] = 0;
     __syncthreads();
     if constexpr (RUNS) {
         const uint32_t stride = gridDim.x * kThreads * 16u;
@@ -108,8 +109,12 @@ __global__ void __launch_bounds__(kThreads) k_hist(const uint32_t* __restrict__ 
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * (int)R; i += kThreads)
-        if (sh[i]) atomicAdd(&hist[(i / R) * kMaxR + (i % R)], sh[i]);
+    for (int i = threadIdx.x; i < passes * (int)R; i += kThreads) {
+        uint32_t t = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) t += sh_all[w][i];
+        if (t) atomicAdd(&hist[(i / R) * kMaxR + (i % R)], t);
+    }
 }
 
 // one block, 256 threads: exclusive scan of each pass's R bins, in place (4 bins per thread)
