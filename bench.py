@@ -812,9 +812,11 @@ def main():
     for w in workers:
         w["s"].wait_event(ev0)
     errors = []
+    start = threading.Barrier(n_workers)         # both host threads start their steps together
 
     def run_worker(w):
         try:
+            start.wait()
             for _ in range(per_worker):
                 e2e_step(w)
         except Exception as exc:                 # reported after the join
