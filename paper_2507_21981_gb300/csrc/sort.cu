@@ -55,10 +55,11 @@ __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
 __device__ __forceinline__ uint32_t live_count(uint32_t n, const uint32_t* d_n) { return d_n ? min(*d_n, n) : n; }
 
 // Histograms of every pass's digit (digit width D) in one read of the keys; hist[p * kMaxR + b].
-// RUNS: each thread counts 16 consecutive keys (four 16-byte loads) and issues one shared atomic
-// per run of equal digits -- for keys whose high digits repeat over neighbours (tile keys emitted
-// instance by instance), whose lanes would otherwise all add to one counter; else a grid-stride
-// loop with one atomic per key and pass.
+// Each warp counts into its own shared-memory copy (the copies are summed at the end).  RUNS:
+// each thread counts 16 consecutive keys (four 16-byte loads) and issues one shared atomic per
+// run of equal digits -- for keys whose high digits repeat over neighbours (tile keys emitted
+// instance by instance, depth keys emitted node chunk by node chunk), whose lanes would
+// otherwise all add to one counter; else a grid-stride loop with one atomic per key and pass.
 template <bool RUNS>
 __global__ void __launch_bounds__(kThreads) k_hist(const uint32_t* __restrict__ keys, uint32_t n,
                                                    const uint32_t* __restrict__ d_n, int passes, int D,
